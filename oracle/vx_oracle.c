@@ -1,0 +1,812 @@
+/*
+ * vx_oracle.c -- CPU oracle for CSF-amortized interval subdivision.
+ *
+ * TEST INFRASTRUCTURE ONLY.  Only the test suite, the smoke check and the benchmark's
+ * CPU-baseline leg load this library; the product path never calls it, and it shares
+ * no code, header, table or helper with the CUDA library.
+ *
+ * A plain, slow, single-threaded statement of the method of G. Moroz, "Sparse Tensors and
+ * Subdivision Methods for Finding the Zero Set of Polynomial Equations" (arXiv 2406.09857):
+ *
+ *   csf_build()      the Compressed Sparse Fiber tree of a set of grid indices (Sec. 2.1):
+ *                    depth-j nodes are the distinct length-j prefixes, children ascending.
+ *   horner_group()   Algorithm 1 (Horner scheme on an interval, sparse exponents).
+ *   eval_rec()       Algorithm 2 (EvaluationCSF): at each depth-j node the polynomial is
+ *                    partially evaluated in x_j on the node's interval and the result is
+ *                    handed to the node's children.
+ *   orc_enclose()    Algorithm 3 (breadth-first subdivision) with the exclusion criterion
+ *                    C0 of Sec. 3.2: a box is dropped iff 0 is outside the interval value
+ *                    of some polynomial of the system.
+ *
+ * Readings of the paper taken here (where it is silent or ambiguous):
+ *   - Rounding (Sec. 3.2 only gives [a,b]+[c,d]=[a+c,b+d]): every lower endpoint is
+ *     rounded down and every upper endpoint rounded up, in IEEE binary64.  The product
+ *     of two intervals is [min, max] of the four endpoint products, each rounded in its
+ *     own direction; min/max are the selects (b<a)?b:a and (b>a)?b:a.
+ *   - Algorithm 1 with an exponent gap g multiplies by the interval g times (repeated
+ *     multiplication, not an interval power), and the result is multiplied by the interval
+ *     e_0 more times when the lowest exponent e_0 is positive (the printed loop stops at
+ *     a_0 and leaves that factor out).
+ *   - Variable x_1 is at the root of the CSF, x_k at the leaves; F(I, x_2, ...) is formed
+ *     by running Algorithm 1 in x_1 once per distinct monomial in the remaining variables.
+ *   - The grid: box t on axis i at level l is [lo_i + t w_i, lo_i + (t+1) w_i] with
+ *     w_i = (hi_i - lo_i) / 2^l; the left end is rounded down and the right end up (both
+ *     exact on dyadic domains, which are the only ones orc_domain_exact() accepts).
+ *   - Algorithm 3 without an inclusion test stops by depth: levels 0..depth are tested
+ *     and the survivors of level `depth` are returned.
+ *
+ * The rounding mode is set to FE_DOWNWARD at the entry of each exported function and
+ * restored on exit; an upward-rounded result is formed as -RD(-x), which is the same
+ * double as RU(x).  Build with -O2 -frounding-math -ffp-contract=off (no FMA contraction).
+ */
+#include <complex.h>
+#include <fenv.h>
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+
+#define ORC_OK 0
+#define ORC_EINVAL (-1)
+#define ORC_ENOMEM (-2)
+#define ORC_KMAX 8
+
+/* ------------------------------------------------------------------------------------ */
+/* Interval arithmetic, outward rounding (Sec. 3.2, "Exclusion Criterion").              */
+/* Every function below runs with the rounding mode FE_DOWNWARD.                         */
+/* ------------------------------------------------------------------------------------ */
+
+typedef struct {
+  double lo, hi;
+} ivl;
+
+static double rd_mul(double a, double b) { return a * b; }
+static double ru_mul(double a, double b) { return -((-a) * b); }
+static double rd_add(double a, double b) { return a + b; }
+static double ru_add(double a, double b) { return -((-a) - b); }
+static double sel_min(double a, double b) { return (b < a) ? b : a; }
+static double sel_max(double a, double b) { return (b > a) ? b : a; }
+
+static ivl i_mul(ivl x, ivl y) {
+  ivl r;
+  r.lo = sel_min(sel_min(rd_mul(x.lo, y.lo), rd_mul(x.lo, y.hi)),
+                 sel_min(rd_mul(x.hi, y.lo), rd_mul(x.hi, y.hi)));
+  r.hi = sel_max(sel_max(ru_mul(x.lo, y.lo), ru_mul(x.lo, y.hi)),
+                 sel_max(ru_mul(x.hi, y.lo), ru_mul(x.hi, y.hi)));
+  return r;
+}
+
+static ivl i_add(ivl x, ivl y) {
+  ivl r;
+  r.lo = rd_add(x.lo, y.lo);
+  r.hi = ru_add(x.hi, y.hi);
+  return r;
+}
+
+/* ------------------------------------------------------------------------------------ */
+/* Partial evaluation plan.                                                              */
+/*                                                                                       */
+/* Stage s (0-based) evaluates variable x_{s+1}.  Its input is a list of terms in the    */
+/* variables x_{s+1}..x_k; the terms are grouped by their exponents in x_{s+2}..x_k (the */
+/* "suffix"), and each group is one run of Algorithm 1 in x_{s+1}.  The output has one   */
+/* term per distinct suffix.  The plan only fixes which input term goes where; it does   */
+/* no arithmetic.                                                                         */
+/* ------------------------------------------------------------------------------------ */
+
+typedef struct {
+  int nin, nout, nsuf; /* input terms, output terms, variables left after the stage */
+  int *grp;            /* [nout+1] group boundaries into ord[] */
+  int *ord;            /* [nin] input term index; exponents ascending within a group */
+  int *ex;             /* [nin] exponent of the evaluated variable, aligned with ord[] */
+  int *oexp;           /* [nout*nsuf] suffix exponents of each output term */
+} stage;
+
+typedef struct {
+  int k;
+  int nterms;
+  stage st[ORC_KMAX];
+} plan;
+
+static const int *g_sort_exps; /* comparator context (the oracle is single-threaded) */
+static int g_sort_nv;
+
+static int cmp_suffix_then_first(const void *pa, const void *pb) {
+  int a = *(const int *)pa, b = *(const int *)pb;
+  const int *ea = g_sort_exps + (size_t)a * g_sort_nv, *eb = g_sort_exps + (size_t)b * g_sort_nv;
+  for (int v = 1; v < g_sort_nv; ++v)
+    if (ea[v] != eb[v]) return ea[v] < eb[v] ? -1 : 1;
+  if (ea[0] != eb[0]) return ea[0] < eb[0] ? -1 : 1;
+  return 0;
+}
+
+static void plan_free(plan *P) {
+  for (int s = 0; s < ORC_KMAX; ++s) {
+    free(P->st[s].grp);
+    free(P->st[s].ord);
+    free(P->st[s].ex);
+    free(P->st[s].oexp);
+  }
+  memset(P, 0, sizeof(*P));
+}
+
+/* exps: [nterms][k].  Fails on negative exponents or repeated monomials. */
+static int plan_build(plan *P, int k, int nterms, const int32_t *exps) {
+  memset(P, 0, sizeof(*P));
+  P->k = k;
+  P->nterms = nterms;
+  if (nterms == 0) return ORC_OK;
+  int nv = k, nin = nterms;
+  int *cur = (int *)malloc(sizeof(int) * (size_t)nin * nv); /* current term exponents */
+  if (!cur) return ORC_ENOMEM;
+  for (size_t i = 0; i < (size_t)nin * nv; ++i) {
+    if (exps[i] < 0) {
+      free(cur);
+      return ORC_EINVAL;
+    }
+    cur[i] = exps[i];
+  }
+  for (int s = 0; s < k; ++s) {
+    stage *S = &P->st[s];
+    S->nin = nin;
+    S->nsuf = nv - 1;
+    S->ord = (int *)malloc(sizeof(int) * nin);
+    S->ex = (int *)malloc(sizeof(int) * nin);
+    S->grp = (int *)malloc(sizeof(int) * (nin + 1));
+    S->oexp = (int *)malloc(sizeof(int) * (size_t)nin * (nv > 1 ? nv - 1 : 1));
+    if (!S->ord || !S->ex || !S->grp || !S->oexp) {
+      free(cur);
+      plan_free(P);
+      return ORC_ENOMEM;
+    }
+    for (int i = 0; i < nin; ++i) S->ord[i] = i;
+    g_sort_exps = cur;
+    g_sort_nv = nv;
+    qsort(S->ord, nin, sizeof(int), cmp_suffix_then_first);
+    int nout = 0;
+    for (int i = 0; i < nin; ++i) {
+      const int *e = cur + (size_t)S->ord[i] * nv;
+      S->ex[i] = e[0];
+      int newgrp = (i == 0);
+      if (!newgrp) {
+        const int *p = cur + (size_t)S->ord[i - 1] * nv;
+        for (int v = 1; v < nv; ++v)
+          if (p[v] != e[v]) newgrp = 1;
+        if (!newgrp && p[0] == e[0]) { /* same monomial twice */
+          free(cur);
+          plan_free(P);
+          return ORC_EINVAL;
+        }
+      }
+      if (newgrp) {
+        S->grp[nout] = i;
+        for (int v = 1; v < nv; ++v) S->oexp[(size_t)nout * (nv - 1) + (v - 1)] = e[v];
+        ++nout;
+      }
+    }
+    S->grp[nout] = nin;
+    S->nout = nout;
+    /* the next stage's input terms are this stage's output terms */
+    int *nxt = (int *)malloc(sizeof(int) * (size_t)nout * (nv > 1 ? nv - 1 : 1));
+    if (!nxt) {
+      free(cur);
+      plan_free(P);
+      return ORC_ENOMEM;
+    }
+    memcpy(nxt, S->oexp, sizeof(int) * (size_t)nout * (nv - 1));
+    free(cur);
+    cur = nxt;
+    nin = nout;
+    nv -= 1;
+  }
+  free(cur);
+  return ORC_OK;
+}
+
+/* Algorithm 1 on one group: coefficients in[ord[b..e-1]] with ascending exponents ex[]. */
+static ivl horner_group(const stage *S, int g, const ivl *in, ivl X, int64_t *work) {
+  int b = S->grp[g], e = S->grp[g + 1];
+  ivl J = in[S->ord[e - 1]];
+  for (int t = e - 2; t >= b; --t) {
+    for (int gap = S->ex[t + 1] - S->ex[t]; gap > 0; --gap) {
+      J = i_mul(J, X);
+      ++*work;
+    }
+    J = i_add(J, in[S->ord[t]]);
+  }
+  for (int gap = S->ex[b]; gap > 0; --gap) {
+    J = i_mul(J, X);
+    ++*work;
+  }
+  return J;
+}
+
+/* F(X, x_{s+2}, ...): one Algorithm-1 run per output term. */
+static void run_stage(const stage *S, const ivl *in, ivl X, ivl *out, int64_t *work) {
+  for (int g = 0; g < S->nout; ++g) out[g] = horner_group(S, g, in, X, work);
+}
+
+/* ------------------------------------------------------------------------------------ */
+/* Box intervals: the grid of Sec. 3.2 scaled to a general domain, or explicit lists.     */
+/* ------------------------------------------------------------------------------------ */
+
+typedef struct {
+  const double *dom; /* [2k] lo, hi per axis (grid mode) */
+  int level;
+  const int64_t *xoff; /* [k+1] offsets into xlo/xhi (list mode) */
+  const double *xlo, *xhi;
+} boxsrc;
+
+static ivl box_ivl(const boxsrc *B, int axis, int32_t t) {
+  ivl r;
+  if (B->xlo) {
+    r.lo = B->xlo[B->xoff[axis] + t];
+    r.hi = B->xhi[B->xoff[axis] + t];
+    return r;
+  }
+  double lo = B->dom[2 * axis], hi = B->dom[2 * axis + 1];
+  double s = ldexp(1.0, -B->level);
+  double wd = rd_mul(rd_add(hi, -lo), s);
+  double wu = ru_mul(ru_add(hi, -lo), s);
+  r.lo = rd_add(lo, rd_mul((double)t, wd));
+  r.hi = ru_add(lo, ru_mul((double)t + 1.0, wu));
+  return r;
+}
+
+/* ------------------------------------------------------------------------------------ */
+/* CSF of a set of grid indices (Sec. 2.1).                                               */
+/* ------------------------------------------------------------------------------------ */
+
+typedef struct {
+  int k;
+  int64_t N[ORC_KMAX];    /* N_j, nodes at depth j+1 */
+  int32_t *lab[ORC_KMAX]; /* labels at depth j+1 */
+  int64_t *ptr[ORC_KMAX]; /* [N_j+1] children range at depth j+2 (j < k-1) */
+} csf;
+
+static void csf_free(csf *T) {
+  for (int j = 0; j < ORC_KMAX; ++j) {
+    free(T->lab[j]);
+    free(T->ptr[j]);
+  }
+  memset(T, 0, sizeof(*T));
+}
+
+/* tuples: [n][k], must be strictly increasing in lexicographic order */
+static int csf_build(csf *T, int k, const int32_t *tup, int64_t n) {
+  memset(T, 0, sizeof(*T));
+  T->k = k;
+  for (int64_t i = 0; i < n; ++i) {
+    for (int c = 0; c < k; ++c)
+      if (tup[i * k + c] < 0) return ORC_EINVAL;
+    if (i > 0) {
+      int c = 0;
+      while (c < k && tup[i * k + c] == tup[(i - 1) * k + c]) ++c;
+      if (c == k || tup[i * k + c] < tup[(i - 1) * k + c]) return ORC_EINVAL;
+    }
+  }
+  for (int j = 0; j < k; ++j) {
+    T->lab[j] = (int32_t *)malloc(sizeof(int32_t) * (size_t)(n > 0 ? n : 1));
+    T->ptr[j] = (int64_t *)malloc(sizeof(int64_t) * (size_t)(n + 1));
+    if (!T->lab[j] || !T->ptr[j]) {
+      csf_free(T);
+      return ORC_ENOMEM;
+    }
+  }
+  /* a depth-(j+1) node starts at tuple i when i is first or the first j+1 coordinates differ */
+  for (int64_t i = 0; i < n; ++i) {
+    int first_diff = 0;
+    if (i > 0)
+      while (first_diff < k && tup[i * k + first_diff] == tup[(i - 1) * k + first_diff]) ++first_diff;
+    for (int j = first_diff; j < k; ++j) {
+      if (j + 1 < k) T->ptr[j][T->N[j]] = T->N[j + 1];
+      T->lab[j][T->N[j]] = tup[i * k + j];
+      T->N[j]++;
+    }
+  }
+  for (int j = 0; j + 1 < k; ++j) T->ptr[j][T->N[j]] = T->N[j + 1];
+  return ORC_OK;
+}
+
+/* ------------------------------------------------------------------------------------ */
+/* Algorithm 2 (EvaluationCSF).                                                          */
+/* ------------------------------------------------------------------------------------ */
+
+static void eval_rec(const plan *P, const csf *T, const boxsrc *B, int j, const ivl *in,
+                     int64_t nb, int64_t ne, ivl *const *buf, ivl *leaf, int64_t *work) {
+  for (int64_t n = nb; n < ne; ++n) {
+    ivl X = box_ivl(B, j, T->lab[j][n]);
+    run_stage(&P->st[j], in, X, buf[j], work);
+    if (j == P->k - 1)
+      leaf[n] = buf[j][0];
+    else
+      eval_rec(P, T, B, j + 1, buf[j], T->ptr[j][n], T->ptr[j][n + 1], buf, leaf, work);
+  }
+}
+
+/* Evaluates one polynomial on every leaf of T. */
+static int eval_poly_csf(const plan *P, const double *coefs, const csf *T, const boxsrc *B,
+                         ivl *leaf, int64_t *work) {
+  int64_t n = T->N[P->k - 1];
+  if (P->nterms == 0) {
+    for (int64_t i = 0; i < n; ++i) leaf[i].lo = leaf[i].hi = 0.0;
+    return ORC_OK;
+  }
+  ivl *in = (ivl *)malloc(sizeof(ivl) * P->nterms);
+  ivl *buf[ORC_KMAX] = {0};
+  int rc = ORC_OK;
+  if (!in) return ORC_ENOMEM;
+  for (int i = 0; i < P->nterms; ++i) in[i].lo = in[i].hi = coefs[i];
+  for (int j = 0; j < P->k; ++j) {
+    buf[j] = (ivl *)malloc(sizeof(ivl) * (size_t)P->st[j].nout);
+    if (!buf[j]) rc = ORC_ENOMEM;
+  }
+  if (rc == ORC_OK) eval_rec(P, T, B, 0, in, 0, T->N[0], buf, leaf, work);
+  for (int j = 0; j < P->k; ++j) free(buf[j]);
+  free(in);
+  return rc;
+}
+
+/* Nested Horner on a single box: stage after stage, no CSF. */
+static ivl eval_poly_box(const plan *P, const double *coefs, const boxsrc *B, const int32_t *tup,
+                         int64_t *work, int *rc) {
+  ivl z = {0.0, 0.0};
+  if (P->nterms == 0) return z;
+  ivl *cur = (ivl *)malloc(sizeof(ivl) * P->nterms);
+  ivl *nxt = (ivl *)malloc(sizeof(ivl) * P->nterms);
+  if (!cur || !nxt) {
+    free(cur);
+    free(nxt);
+    *rc = ORC_ENOMEM;
+    return z;
+  }
+  for (int i = 0; i < P->nterms; ++i) cur[i].lo = cur[i].hi = coefs[i];
+  for (int j = 0; j < P->k; ++j) {
+    run_stage(&P->st[j], cur, box_ivl(B, j, tup[j]), nxt, work);
+    ivl *t = cur;
+    cur = nxt;
+    nxt = t;
+  }
+  z = cur[0];
+  free(cur);
+  free(nxt);
+  return z;
+}
+
+/* ------------------------------------------------------------------------------------ */
+/* Exported interface (ctypes).                                                          */
+/*                                                                                       */
+/* A polynomial system is npoly polynomials in k variables: polynomial f owns terms      */
+/* term_off[f] .. term_off[f+1]-1 of exps ([total][k] int32) and coefs (double).         */
+/* ------------------------------------------------------------------------------------ */
+
+static int check_system(int k, int npoly, const int64_t *term_off) {
+  if (k < 1 || k > ORC_KMAX || npoly < 1) return ORC_EINVAL;
+  for (int f = 0; f < npoly; ++f)
+    if (term_off[f + 1] < term_off[f]) return ORC_EINVAL;
+  return ORC_OK;
+}
+
+static int build_plans(plan *plans, int k, int npoly, const int64_t *term_off, const int32_t *exps,
+                       const double *coefs) {
+  for (int f = 0; f < npoly; ++f) {
+    int64_t nt = term_off[f + 1] - term_off[f];
+    for (int64_t i = term_off[f]; i < term_off[f + 1]; ++i)
+      if (!isfinite(coefs[i])) return ORC_EINVAL;
+    int rc = plan_build(&plans[f], k, (int)nt, exps + term_off[f] * k);
+    if (rc != ORC_OK) {
+      for (int g = 0; g < f; ++g) plan_free(&plans[g]);
+      return rc;
+    }
+  }
+  return ORC_OK;
+}
+
+static void free_plans(plan *plans, int npoly) {
+  for (int f = 0; f < npoly; ++f) plan_free(&plans[f]);
+}
+
+/* 1 if every grid point lo + t (hi-lo)/2^level, 0 <= t <= 2^level, of every axis is a double. */
+int orc_domain_exact(int k, const double *domain, int level) {
+  int old = fegetround();
+  int ok = 1;
+  fesetround(FE_DOWNWARD);
+  if (level < 0 || level > 30) ok = 0;
+  for (int i = 0; ok && i < k; ++i) {
+    double lo = domain[2 * i], hi = domain[2 * i + 1];
+    if (!isfinite(lo) || !isfinite(hi) || !(lo < hi)) {
+      ok = 0;
+      break;
+    }
+    boxsrc B = {domain, level, 0, 0, 0};
+    for (int64_t t = 0; ok && t < ((int64_t)1 << level); ++t) {
+      ivl x = box_ivl(&B, i, (int32_t)t);
+      /* exact iff rounding down and up agree on both ends */
+      double s = ldexp(1.0, -level);
+      double l_up = ru_add(lo, ru_mul((double)t, ru_mul(ru_add(hi, -lo), s)));
+      double h_dn = rd_add(lo, rd_mul((double)t + 1.0, rd_mul(rd_add(hi, -lo), s)));
+      if (l_up != x.lo || h_dn != x.hi) ok = 0;
+    }
+  }
+  fesetround(old);
+  return ok;
+}
+
+static int eval_csf_common(int k, int npoly, const int64_t *term_off, const int32_t *exps,
+                           const double *coefs, const boxsrc *B, const int32_t *tuples, int64_t n,
+                           double *lo, double *hi, uint8_t *keep, int64_t *work) {
+  plan plans[16];
+  csf T;
+  int rc = check_system(k, npoly, term_off);
+  if (rc != ORC_OK) return rc;
+  if (npoly > 16) return ORC_EINVAL;
+  rc = build_plans(plans, k, npoly, term_off, exps, coefs);
+  if (rc != ORC_OK) return rc;
+  rc = csf_build(&T, k, tuples, n);
+  if (rc != ORC_OK) {
+    free_plans(plans, npoly);
+    return rc;
+  }
+  ivl *leaf = (ivl *)malloc(sizeof(ivl) * (size_t)(n > 0 ? n : 1));
+  int64_t w = 0;
+  if (!leaf) rc = ORC_ENOMEM;
+  if (keep)
+    for (int64_t i = 0; i < n; ++i) keep[i] = 1;
+  for (int f = 0; rc == ORC_OK && f < npoly; ++f) {
+    rc = eval_poly_csf(&plans[f], coefs + term_off[f], &T, B, leaf, &w);
+    for (int64_t i = 0; rc == ORC_OK && i < n; ++i) {
+      if (lo) lo[(int64_t)f * n + i] = leaf[i].lo;
+      if (hi) hi[(int64_t)f * n + i] = leaf[i].hi;
+      /* C0: the box is dropped iff 0 is outside [lo, hi] for some polynomial */
+      if (keep && !(leaf[i].lo <= 0.0 && 0.0 <= leaf[i].hi)) keep[i] = 0;
+    }
+  }
+  if (work) *work = w;
+  free(leaf);
+  csf_free(&T);
+  free_plans(plans, npoly);
+  return rc;
+}
+
+/* Algorithm 2 on the boxes `tuples` (lex-sorted, unique) of the level-`level` grid. */
+int orc_eval_csf(int k, int npoly, const int64_t *term_off, const int32_t *exps, const double *coefs,
+                 const double *domain, int level, const int32_t *tuples, int64_t n, double *lo,
+                 double *hi, uint8_t *keep, int64_t *work) {
+  int old = fegetround();
+  fesetround(FE_DOWNWARD);
+  boxsrc B = {domain, level, 0, 0, 0};
+  int rc = eval_csf_common(k, npoly, term_off, exps, coefs, &B, tuples, n, lo, hi, keep, work);
+  fesetround(old);
+  return rc;
+}
+
+/* Algorithm 2 on explicit per-axis interval lists: axis i owns xlo/xhi[xoff[i] .. xoff[i+1]). */
+int orc_eval_grid(int k, int npoly, const int64_t *term_off, const int32_t *exps, const double *coefs,
+                  const int64_t *xoff, const double *xlo, const double *xhi, const int32_t *tuples,
+                  int64_t n, double *lo, double *hi, uint8_t *keep, int64_t *work) {
+  int old = fegetround();
+  fesetround(FE_DOWNWARD);
+  for (int64_t i = 0; i < n; ++i)
+    for (int c = 0; c < k; ++c)
+      if (tuples[i * k + c] >= xoff[c + 1] - xoff[c]) {
+        fesetround(old);
+        return ORC_EINVAL;
+      }
+  boxsrc B = {0, 0, xoff, xlo, xhi};
+  int rc = eval_csf_common(k, npoly, term_off, exps, coefs, &B, tuples, n, lo, hi, keep, work);
+  fesetround(old);
+  return rc;
+}
+
+/* Nested Horner of each polynomial on each box independently (no CSF, no sharing). */
+int orc_eval_boxes(int k, int npoly, const int64_t *term_off, const int32_t *exps, const double *coefs,
+                   const double *domain, int level, const int32_t *tuples, int64_t n, double *lo,
+                   double *hi, uint8_t *keep, int64_t *work) {
+  plan plans[16];
+  int old = fegetround();
+  int rc = check_system(k, npoly, term_off);
+  if (rc != ORC_OK) return rc;
+  if (npoly > 16) return ORC_EINVAL;
+  fesetround(FE_DOWNWARD);
+  rc = build_plans(plans, k, npoly, term_off, exps, coefs);
+  if (rc != ORC_OK) {
+    fesetround(old);
+    return rc;
+  }
+  boxsrc B = {domain, level, 0, 0, 0};
+  int64_t w = 0;
+  for (int64_t i = 0; rc == ORC_OK && i < n; ++i) {
+    int kp = 1;
+    for (int f = 0; f < npoly; ++f) {
+      ivl v = eval_poly_box(&plans[f], coefs + term_off[f], &B, tuples + i * k, &w, &rc);
+      if (lo) lo[(int64_t)f * n + i] = v.lo;
+      if (hi) hi[(int64_t)f * n + i] = v.hi;
+      if (!(v.lo <= 0.0 && 0.0 <= v.hi)) kp = 0;
+    }
+    if (keep) keep[i] = (uint8_t)kp;
+  }
+  if (work) *work = w;
+  free_plans(plans, npoly);
+  fesetround(old);
+  return rc;
+}
+
+/* CSF arrays of a lex-sorted tuple set: N[k]; labels concatenated by depth; ptr for depths
+ * 1..k-1 concatenated (N_j + 1 entries each).  Pass labels == NULL to get only N. */
+int orc_csf(int k, const int32_t *tuples, int64_t n, int64_t *N, int32_t *labels, int64_t *ptr) {
+  csf T;
+  if (k < 1 || k > ORC_KMAX) return ORC_EINVAL;
+  int rc = csf_build(&T, k, tuples, n);
+  if (rc != ORC_OK) return rc;
+  int64_t lo = 0, po = 0;
+  for (int j = 0; j < k; ++j) {
+    N[j] = T.N[j];
+    if (labels) memcpy(labels + lo, T.lab[j], sizeof(int32_t) * (size_t)T.N[j]);
+    if (ptr && j + 1 < k) memcpy(ptr + po, T.ptr[j], sizeof(int64_t) * (size_t)(T.N[j] + 1));
+    lo += T.N[j];
+    if (j + 1 < k) po += T.N[j] + 1;
+  }
+  csf_free(&T);
+  return ORC_OK;
+}
+
+/* ------------------------------------------------------------------------------------ */
+/* Algorithm 3: breadth-first subdivision with the C0 test at every level.               */
+/* ------------------------------------------------------------------------------------ */
+
+typedef struct orc_result {
+  int k, depth;
+  int64_t n;
+  int32_t *tuples;  /* survivors of the last level, lex order */
+  int64_t *tested;  /* [depth+1] |S_l| */
+  int64_t *kept;    /* [depth+1] */
+  int64_t *nodes;   /* [(depth+1)*k] N_j(S_l) */
+  int64_t *work;    /* [depth+1] interval multiply-adds */
+} orc_result;
+
+static int g_cmp_k;
+static int cmp_tuple(const void *pa, const void *pb) {
+  const int32_t *a = (const int32_t *)pa, *b = (const int32_t *)pb;
+  for (int c = 0; c < g_cmp_k; ++c)
+    if (a[c] != b[c]) return a[c] < b[c] ? -1 : 1;
+  return 0;
+}
+
+void orc_result_free(orc_result *R) {
+  if (!R) return;
+  free(R->tuples);
+  free(R->tested);
+  free(R->kept);
+  free(R->nodes);
+  free(R->work);
+  free(R);
+}
+
+int orc_enclose(int k, int npoly, const int64_t *term_off, const int32_t *exps, const double *coefs,
+                const double *domain, int depth, orc_result **out) {
+  int old = fegetround();
+  int rc = check_system(k, npoly, term_off);
+  *out = 0;
+  if (rc != ORC_OK) return rc;
+  if (depth < 0 || depth > 30 || npoly > 16) return ORC_EINVAL;
+  if (!orc_domain_exact(k, domain, depth)) return ORC_EINVAL;
+  fesetround(FE_DOWNWARD);
+  orc_result *R = (orc_result *)calloc(1, sizeof(orc_result));
+  plan plans[16];
+  if (!R) {
+    fesetround(old);
+    return ORC_ENOMEM;
+  }
+  R->k = k;
+  R->depth = depth;
+  R->tested = (int64_t *)calloc(depth + 1, sizeof(int64_t));
+  R->kept = (int64_t *)calloc(depth + 1, sizeof(int64_t));
+  R->nodes = (int64_t *)calloc((size_t)(depth + 1) * k, sizeof(int64_t));
+  R->work = (int64_t *)calloc(depth + 1, sizeof(int64_t));
+  rc = build_plans(plans, k, npoly, term_off, exps, coefs);
+  if (rc != ORC_OK) {
+    orc_result_free(R);
+    fesetround(old);
+    return rc;
+  }
+  int64_t n = 1;
+  int32_t *S = (int32_t *)calloc((size_t)k, sizeof(int32_t)); /* S = { the whole domain } */
+  for (int l = 0; rc == ORC_OK && l <= depth; ++l) {
+    csf T;
+    boxsrc B = {domain, l, 0, 0, 0};
+    rc = csf_build(&T, k, S, n);
+    if (rc != ORC_OK) break;
+    uint8_t *keep = (uint8_t *)malloc((size_t)(n > 0 ? n : 1));
+    ivl *leaf = (ivl *)malloc(sizeof(ivl) * (size_t)(n > 0 ? n : 1));
+    if (!keep || !leaf) rc = ORC_ENOMEM;
+    for (int64_t i = 0; i < n && keep; ++i) keep[i] = 1;
+    for (int f = 0; rc == ORC_OK && f < npoly; ++f) {
+      rc = eval_poly_csf(&plans[f], coefs + term_off[f], &T, &B, leaf, &R->work[l]);
+      for (int64_t i = 0; rc == ORC_OK && i < n; ++i)
+        if (!(leaf[i].lo <= 0.0 && 0.0 <= leaf[i].hi)) keep[i] = 0;
+    }
+    R->tested[l] = n;
+    for (int j = 0; j < k; ++j) R->nodes[(size_t)l * k + j] = T.N[j];
+    csf_free(&T);
+    free(leaf);
+    if (rc != ORC_OK) {
+      free(keep);
+      break;
+    }
+    /* S <- boxes of S not satisfying C0 */
+    int64_t m = 0;
+    for (int64_t i = 0; i < n; ++i)
+      if (keep[i]) {
+        memmove(S + m * k, S + i * k, sizeof(int32_t) * k);
+        ++m;
+      }
+    free(keep);
+    R->kept[l] = m;
+    n = m;
+    if (l == depth) break;
+    /* S <- the 2^k boxes bisected from each box of S, sorted */
+    int64_t nc = n << k;
+    int32_t *C = (int32_t *)malloc(sizeof(int32_t) * (size_t)(nc > 0 ? nc : 1) * k);
+    if (!C) {
+      rc = ORC_ENOMEM;
+      break;
+    }
+    for (int64_t i = 0; i < n; ++i)
+      for (int b = 0; b < (1 << k); ++b)
+        for (int c = 0; c < k; ++c) C[((i << k) + b) * k + c] = 2 * S[i * k + c] + ((b >> (k - 1 - c)) & 1);
+    g_cmp_k = k;
+    qsort(C, (size_t)nc, sizeof(int32_t) * k, cmp_tuple);
+    free(S);
+    S = C;
+    n = nc;
+  }
+  free_plans(plans, npoly);
+  fesetround(old);
+  if (rc != ORC_OK) {
+    free(S);
+    orc_result_free(R);
+    return rc;
+  }
+  R->n = n;
+  R->tuples = S;
+  *out = R;
+  return ORC_OK;
+}
+
+int64_t orc_result_count(const orc_result *R) { return R->n; }
+
+void orc_result_copy(const orc_result *R, int32_t *tuples, int64_t *tested, int64_t *kept,
+                     int64_t *nodes, int64_t *work) {
+  if (tuples) memcpy(tuples, R->tuples, sizeof(int32_t) * (size_t)R->n * R->k);
+  if (tested) memcpy(tested, R->tested, sizeof(int64_t) * (R->depth + 1));
+  if (kept) memcpy(kept, R->kept, sizeof(int64_t) * (R->depth + 1));
+  if (nodes) memcpy(nodes, R->nodes, sizeof(int64_t) * (size_t)(R->depth + 1) * R->k);
+  if (work) memcpy(work, R->work, sizeof(int64_t) * (R->depth + 1));
+}
+
+/* Every box of the level-`level` grid tested independently with nested Horner; keep is in
+ * lexicographic order of the box indices ((2^level)^k entries). */
+int orc_brute_force(int k, int npoly, const int64_t *term_off, const int32_t *exps, const double *coefs,
+                    const double *domain, int level, uint8_t *keep) {
+  int64_t side = (int64_t)1 << level, total = 1;
+  for (int c = 0; c < k; ++c) total *= side;
+  int32_t tup[ORC_KMAX];
+  for (int64_t i = 0; i < total; ++i) {
+    int64_t r = i;
+    for (int c = k - 1; c >= 0; --c) {
+      tup[c] = (int32_t)(r % side);
+      r /= side;
+    }
+    int rc = orc_eval_boxes(k, npoly, term_off, exps, coefs, domain, level, tup, 1, 0, 0, keep + i, 0);
+    if (rc != ORC_OK) return rc;
+  }
+  return ORC_OK;
+}
+
+/* ------------------------------------------------------------------------------------ */
+/* Algorithm 2 over complex points (round to nearest), for the DFT application of        */
+/* Sec. 3.1: the same plan and CSF traversal with complex values in place of intervals.  */
+/* ------------------------------------------------------------------------------------ */
+
+static double complex horner_group_c(const stage *S, int g, const double complex *in, double complex x) {
+  int b = S->grp[g], e = S->grp[g + 1];
+  double complex J = in[S->ord[e - 1]];
+  for (int t = e - 2; t >= b; --t) {
+    for (int gap = S->ex[t + 1] - S->ex[t]; gap > 0; --gap) J = J * x;
+    J = J + in[S->ord[t]];
+  }
+  for (int gap = S->ex[b]; gap > 0; --gap) J = J * x;
+  return J;
+}
+
+static void eval_rec_c(const plan *P, const csf *T, const int64_t *xoff, const double *xre,
+                       const double *xim, int j, const double complex *in, int64_t nb, int64_t ne,
+                       double complex *const *buf, double complex *leaf) {
+  for (int64_t n = nb; n < ne; ++n) {
+    int32_t t = T->lab[j][n];
+    double complex x = xre[xoff[j] + t] + I * xim[xoff[j] + t];
+    const stage *S = &P->st[j];
+    for (int g = 0; g < S->nout; ++g) buf[j][g] = horner_group_c(S, g, in, x);
+    if (j == P->k - 1)
+      leaf[n] = buf[j][0];
+    else
+      eval_rec_c(P, T, xoff, xre, xim, j + 1, buf[j], T->ptr[j][n], T->ptr[j][n + 1], buf, leaf);
+  }
+}
+
+int orc_eval_grid_complex(int k, int64_t nterms, const int32_t *exps, const double *cre,
+                          const double *cim, const int64_t *xoff, const double *xre,
+                          const double *xim, const int32_t *tuples, int64_t n, double *vre,
+                          double *vim) {
+  int old = fegetround();
+  plan P;
+  csf T;
+  if (k < 1 || k > ORC_KMAX || nterms < 1) return ORC_EINVAL;
+  for (int64_t i = 0; i < n; ++i)
+    for (int c = 0; c < k; ++c)
+      if (tuples[i * k + c] >= xoff[c + 1] - xoff[c]) return ORC_EINVAL;
+  fesetround(FE_TONEAREST);
+  int rc = plan_build(&P, k, (int)nterms, exps);
+  if (rc != ORC_OK) {
+    fesetround(old);
+    return rc;
+  }
+  rc = csf_build(&T, k, tuples, n);
+  if (rc != ORC_OK) {
+    plan_free(&P);
+    fesetround(old);
+    return rc;
+  }
+  double complex *in = (double complex *)malloc(sizeof(double complex) * (size_t)nterms);
+  double complex *leaf = (double complex *)malloc(sizeof(double complex) * (size_t)(n > 0 ? n : 1));
+  double complex *buf[ORC_KMAX] = {0};
+  if (!in || !leaf) rc = ORC_ENOMEM;
+  for (int j = 0; rc == ORC_OK && j < k; ++j) {
+    buf[j] = (double complex *)malloc(sizeof(double complex) * (size_t)P.st[j].nout);
+    if (!buf[j]) rc = ORC_ENOMEM;
+  }
+  if (rc == ORC_OK) {
+    for (int64_t i = 0; i < nterms; ++i) in[i] = cre[i] + I * cim[i];
+    eval_rec_c(&P, &T, xoff, xre, xim, 0, in, 0, T.N[0], buf, leaf);
+    for (int64_t i = 0; i < n; ++i) {
+      vre[i] = creal(leaf[i]);
+      vim[i] = cimag(leaf[i]);
+    }
+  }
+  for (int j = 0; j < k; ++j) free(buf[j]);
+  free(in);
+  free(leaf);
+  csf_free(&T);
+  plan_free(&P);
+  fesetround(old);
+  return rc;
+}
+
+/* Directed-rounding primitives, exported so that tests can pin them against exact rationals. */
+void orc_prim(int op, const double *a, const double *b, int64_t n, double *out) {
+  int old = fegetround();
+  fesetround(FE_DOWNWARD);
+  for (int64_t i = 0; i < n; ++i) {
+    switch (op) {
+      case 0: out[i] = rd_mul(a[i], b[i]); break;
+      case 1: out[i] = ru_mul(a[i], b[i]); break;
+      case 2: out[i] = rd_add(a[i], b[i]); break;
+      default: out[i] = ru_add(a[i], b[i]); break;
+    }
+  }
+  fesetround(old);
+}
+
+/* Interval product (4-product form), exported for the same reason. */
+void orc_imul(const double *alo, const double *ahi, const double *blo, const double *bhi, int64_t n,
+              double *lo, double *hi) {
+  int old = fegetround();
+  fesetround(FE_DOWNWARD);
+  for (int64_t i = 0; i < n; ++i) {
+    ivl x = {alo[i], ahi[i]}, y = {blo[i], bhi[i]};
+    ivl r = i_mul(x, y);
+    lo[i] = r.lo;
+    hi[i] = r.hi;
+  }
+  fesetround(old);
+}

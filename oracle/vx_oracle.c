@@ -457,8 +457,9 @@ static int eval_csf_common(int k, int npoly, const int64_t *term_off, const int3
     for (int64_t i = 0; rc == ORC_OK && i < n; ++i) {
       if (lo) lo[(int64_t)f * n + i] = leaf[i].lo;
       if (hi) hi[(int64_t)f * n + i] = leaf[i].hi;
-      /* C0: the box is dropped iff 0 is outside [lo, hi] for some polynomial */
-      if (keep && !(leaf[i].lo <= 0.0 && 0.0 <= leaf[i].hi)) keep[i] = 0;
+      /* C0: the box is dropped iff 0 is provably outside [lo, hi] for some polynomial
+       * (lo > 0 or hi < 0); an enclosure with a NaN endpoint proves nothing and keeps it */
+      if (keep && (leaf[i].lo > 0.0 || leaf[i].hi < 0.0)) keep[i] = 0;
     }
   }
   if (work) *work = w;
@@ -521,7 +522,7 @@ int orc_eval_boxes(int k, int npoly, const int64_t *term_off, const int32_t *exp
       ivl v = eval_poly_box(&plans[f], coefs + term_off[f], &B, tuples + i * k, &w, &rc);
       if (lo) lo[(int64_t)f * n + i] = v.lo;
       if (hi) hi[(int64_t)f * n + i] = v.hi;
-      if (!(v.lo <= 0.0 && 0.0 <= v.hi)) kp = 0;
+      if (v.lo > 0.0 || v.hi < 0.0) kp = 0;
     }
     if (keep) keep[i] = (uint8_t)kp;
   }
@@ -623,7 +624,7 @@ int orc_enclose(int k, int npoly, const int64_t *term_off, const int32_t *exps, 
     for (int f = 0; rc == ORC_OK && f < npoly; ++f) {
       rc = eval_poly_csf(&plans[f], coefs + term_off[f], &T, &B, leaf, &R->work[l]);
       for (int64_t i = 0; rc == ORC_OK && i < n; ++i)
-        if (!(leaf[i].lo <= 0.0 && 0.0 <= leaf[i].hi)) keep[i] = 0;
+        if ((leaf[i].lo > 0.0 || leaf[i].hi < 0.0)) keep[i] = 0;
     }
     R->tested[l] = n;
     for (int j = 0; j < k; ++j) R->nodes[(size_t)l * k + j] = T.N[j];

@@ -1,0 +1,173 @@
+/*
+ * vx.h -- C ABI of libvx: CSF-amortized interval subdivision on one GB300 (sm_103a).
+ *
+ * The method is that of G. Moroz, "Sparse Tensors and Subdivision Methods for Finding the
+ * Zero Set of Polynomial Equations" (arXiv 2406.09857): the boxes of one subdivision level
+ * are stored as a Compressed Sparse Fiber tree (Sec. 2.1), the polynomials are evaluated
+ * on all of them at once by partial evaluation along the tree (Algorithm 2 built on the
+ * Horner scheme of Algorithm 1, cost given by Theorem 1), boxes whose interval value does
+ * not contain 0 are dropped (criterion C0, Sec. 3.2), and the survivors are bisected 2^k
+ * ways into the next level (Algorithm 3).
+ *
+ * Conventions shared by every call:
+ *   - Every call returns VX_OK (0) or a negative VX_E* code and never aborts, throws or traps;
+ *     vx_last_error() then holds a message for the calling thread.
+ *   - Pointers prefixed h_ are host memory, d_ device memory of the current CUDA device.
+ *     Caller-owned buffers stay owned by the caller; objects returned through an out-pointer
+ *     (vx_system, vx_csf, vx_result) are owned by the caller and released by the matching
+ *     *_free call.  `stream` is a cudaStream_t (NULL = the legacy default stream); all device
+ *     work of a call is ordered on it, and device outputs are valid once it has reached them.
+ *   - Variable x_1 is at the root of the CSF and x_k at the leaves; children are in
+ *     ascending label order, so leaves are in lexicographic order of their index tuples.
+ *   - A grid level l splits axis i of the domain [lo_i, hi_i] into 2^l boxes
+ *     [lo_i + t w_i, lo_i + (t+1) w_i], w_i = (hi_i - lo_i) / 2^l.  The domain must be finite
+ *     with lo_i < hi_i and every grid point of the level must be exactly representable in
+ *     binary64 (dyadic domains such as [-1,1]^k or [0,1]^k); otherwise VX_EINVAL.
+ *   - 1 <= k <= VX_KMAX variables, 1 <= npoly <= VX_MAXPOLY polynomials, levels 0..VX_MAXLEVEL.
+ */
+#ifndef VX_H
+#define VX_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define VX_OK 0
+#define VX_EINVAL (-1)    /* an argument is out of range or malformed */
+#define VX_ENOMEM (-2)    /* a host or device allocation failed */
+#define VX_ECAPACITY (-3) /* a caller-provided buffer or a fixed limit is too small */
+#define VX_EOVERFLOW (-4) /* a node count would not fit the 32-bit node indices */
+#define VX_ETIMEOUT (-5)  /* a bounded device wait gave up */
+#define VX_ECUDA (-6)     /* a CUDA runtime call failed */
+
+#define VX_KMAX 4
+#define VX_MAXPOLY 8
+#define VX_MAXLEVEL 24
+
+/* Arithmetic of a level evaluation. */
+#define VX_FP64 0        /* binary64 intervals [lo, hi]: lower ends rounded down, upper up */
+#define VX_FP32_MIDRAD 1 /* binary32 midpoint-radius <m, r> with the rounding error of every
+                          * step bounded a priori and added to r, so the enclosure contains
+                          * the exact range (and the VX_FP64 enclosure) */
+
+/* One polynomial: nterms monomials coefs[t] * prod_i x_i^exps[t*nvars+i] (Sec. 2.1,
+ * "Representing a Multivariate Polynomial").  Host memory, borrowed for the duration of the
+ * call.  Exponents >= 0, no monomial twice, coefficients finite. */
+typedef struct {
+  int32_t nvars;
+  int32_t nterms;
+  const int32_t *exps; /* [nterms][nvars] */
+  const double *coefs; /* [nterms] */
+} vx_poly;
+
+typedef struct vx_system vx_system; /* packed polynomials, resident on the device */
+typedef struct vx_csf vx_csf;       /* a CSF of box indices of one grid level, on the device */
+typedef struct vx_result vx_result; /* the outcome of an enclosure */
+
+/* Options of vx_enclose*: zero-initialise, then set what you need (all-zero = VX_FP64). */
+typedef struct {
+  int32_t mode;         /* VX_FP64 or VX_FP32_MIDRAD for the levels below the last */
+  int32_t fp64_final;   /* VX_FP32_MIDRAD only: evaluate the last level in VX_FP64, which makes
+                         * the result exactly the VX_FP64 result */
+  int32_t fp64_recheck; /* VX_FP32_MIDRAD only: boxes kept by the FP32 test with |m| >= theta*r
+                         * for some polynomial are re-evaluated in VX_FP64 at the same level */
+  float theta;          /* recheck threshold, 0 < theta <= 1 (0 means 0.5) */
+  int32_t timing;       /* nonzero: time every kernel launch with CUDA events (vx_result_timing) */
+  int32_t reserved[7];
+} vx_opts;
+
+/* Thread-local message of the last failed call on this thread ("" if none). */
+const char *vx_last_error(void);
+
+/* Packs the polynomials F_list[0..npoly) (all in the same number of variables k) for the
+ * device and uploads them on `stream` (Sec. 2.1: the exponent CSF, laid out fibre-major so
+ * that Algorithm 1 runs along contiguous rows).  The system holds device memory until
+ * vx_system_free. */
+int vx_system_create(const vx_poly *F_list, int32_t npoly, void *stream, vx_system **out);
+void vx_system_free(vx_system *sys);
+/* k and npoly of a system; h_M (nullable) receives [npoly][k+1] the number of coefficients
+ * each partial-evaluation stage reads: M_{j} for j = 0..k, with missing suffix monomials below
+ * the highest exponent of a fibre counted as zero coefficients (M_k = 1). */
+int vx_system_info(const vx_system *sys, int32_t *k, int32_t *npoly, int64_t *h_M);
+
+/* The CSF (Sec. 2.1) of n box indices d_tuples[n][k] (device, int32, lexicographically
+ * strictly increasing, each coordinate in [0, 2^level)) of grid level `level`.  Depth-j nodes
+ * are the distinct length-j prefixes (Remark 1: there are N_j(S) of them).  VX_EINVAL if the
+ * tuples are not strictly increasing or out of range (checked on the device). */
+int vx_csf_build(int32_t k, int32_t level, const int32_t *d_tuples, int64_t n, void *stream,
+                 vx_csf **out);
+void vx_csf_free(vx_csf *csf);
+/* k, level and h_N[k] = N_1..N_k (nodes per depth; N_k = number of boxes). */
+int vx_csf_nodes(const vx_csf *csf, int32_t *k, int32_t *level, int64_t *h_N);
+/* Copies depth `depth` (1..k) of the tree: d_labels[N_depth] (grid index of each node along
+ * x_depth), and for depth < k d_ptr[N_depth + 1] (children of node i are nodes d_ptr[i] ..
+ * d_ptr[i+1]-1 of depth+1).  d_ptr may be NULL. */
+int vx_csf_export(const vx_csf *csf, int32_t depth, int32_t *d_labels, int32_t *d_ptr,
+                  void *stream);
+/* Writes the index tuples of the leaves, d_tuples[N_k][k], in leaf (lexicographic) order. */
+int vx_csf_tuples(const vx_csf *csf, int32_t *d_tuples, void *stream);
+
+/* Algorithm 2 on every leaf box of `csf` with the C0 test of Sec. 3.2.
+ * h_domain[2k]: lo_i, hi_i per axis (host).  mode: VX_FP64 or VX_FP32_MIDRAD.
+ * d_keep[N_k] (required): 1 if 0 lies in the interval value of every polynomial, else 0.
+ * d_lo, d_hi [npoly][N_k] (both NULL or both set): the enclosure of each polynomial on each
+ * box (VX_FP32_MIDRAD: m - r rounded down and m + r rounded up, in binary64).
+ * In VX_FP64 mode every endpoint equals the CPU statement of Algorithms 1-2 with outward
+ * rounding (RD of each product and sum for lower ends, RU for upper ends, the product of
+ * intervals as the hull of the endpoint products). */
+int vx_csf_eval_level(const vx_system *sys, const vx_csf *csf, const double *h_domain,
+                      int32_t mode, double *d_lo, double *d_hi, uint8_t *d_keep, void *stream);
+
+/* Algorithm 3, one step: drops the leaves with d_keep[i] == 0 (and the inner nodes left
+ * without leaves), bisects every remaining box 2^k ways and returns the CSF of level+1 (its
+ * leaves are the 2^k children of each kept box, lexicographically ordered).  No sort: each
+ * new node's position follows from the kept tree's counts.  An empty keep set gives an
+ * empty CSF. */
+int vx_csf_subdivide(const vx_csf *in, const uint8_t *d_keep, void *stream, vx_csf **out);
+/* The kept leaves of `in` as a CSF of the same level (stable: leaf order preserved).
+ * d_index (nullable, [N_k(out)]) receives for each kept leaf its leaf index in `in`. */
+int vx_csf_compact(const vx_csf *in, const uint8_t *d_keep, int32_t *d_index, void *stream,
+                   vx_csf **out);
+
+/* Algorithm 3 to `depth` on a device-resident system: tests levels 0..depth with C0 and
+ * returns the survivors of level `depth` (a box of the finest grid is returned iff every
+ * polynomial's interval value on it contains 0, in the arithmetic `opts` selects for that
+ * level; with VX_FP64 throughout, or VX_FP32_MIDRAD with fp64_final, this is exactly the
+ * VX_FP64 set).  opts may be NULL (VX_FP64).  Ordered on `stream`; returns once the
+ * result is complete. */
+int vx_enclose_system(const vx_system *sys, const double *h_domain, int32_t depth,
+                      const vx_opts *opts, void *stream, vx_result **out);
+/* The same from host polynomials: packs and uploads them, runs on a private stream, and
+ * leaves the result's boxes readable through vx_result_boxes. */
+int vx_enclose(const vx_poly *F_list, int32_t npoly, const double *h_domain, int32_t depth,
+               const vx_opts *opts, vx_result **out);
+
+/* The surviving boxes: *n tuples of k int32 grid indices at level `depth`, lexicographic,
+ * in host memory owned by the result (copied from the device on first call). */
+int vx_result_boxes(vx_result *res, int64_t *n, const int32_t **h_tuples);
+/* The survivors as a device CSF owned by the result (valid until vx_result_free). */
+int vx_result_csf(const vx_result *res, const vx_csf **csf);
+/* Per-level statistics, levels 0..depth: h_tested[l] = |S_l| boxes evaluated, h_kept[l]
+ * survivors, h_nodes[l*k + j-1] = N_j(S_l), h_recheck[l] = boxes re-evaluated in VX_FP64
+ * (VX_FP32_MIDRAD with fp64_recheck), h_madds[l] = interval multiply-adds of the level
+ * (Theorem 1's count: sum over polynomials and depths j of N_j (M_{j-1} - M_j)).
+ * Any pointer may be NULL; *nlevels = depth + 1. */
+int vx_result_stats(const vx_result *res, int32_t *nlevels, int64_t *h_tested, int64_t *h_kept,
+                    int64_t *h_nodes, int64_t *h_recheck, int64_t *h_madds);
+/* Kernel timing (opts.timing != 0): for kernel kind i < *nkinds: h_ms[i] summed CUDA-event
+ * time, h_launches[i] launches, h_work[i] algorithmic work (interval multiply-adds for the
+ * evaluation kernels, bytes for the integer kernels).  vx_kernel_kind_name(i) names kind i. */
+int vx_result_timing(const vx_result *res, int32_t *nkinds, double *h_ms, int64_t *h_launches,
+                     int64_t *h_work);
+const char *vx_kernel_kind_name(int32_t kind);
+/* Wall time of the level loop on the stream (CUDA events), in milliseconds. */
+int vx_result_elapsed_ms(const vx_result *res, double *ms);
+void vx_result_free(vx_result *res);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* VX_H */

@@ -1,0 +1,905 @@
+// vx_api.cu -- host runtime and C ABI of libvx (declared in include/vx.h).
+//
+//   - packing of the polynomials for the device (Sec. 2.1, polynomial as a tree of exponent
+//     tuples), re-laid out fibre-major per partial-evaluation stage;
+//   - grid levels of a domain (Sec. 3.2: level l bisects the domain 2^l times per axis);
+//   - the level loop of Algorithm 3 with criterion C0 (Sec. 3.2), optionally in binary32
+//     midpoint-radius below the last level and with binary64 rechecks;
+//   - CSF, system and result objects, errors and kernel timing.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <new>
+#include <unordered_map>
+#include <vector>
+
+#include "vx_internal.cuh"
+
+namespace vx {
+
+// ---------------------------------------------------------------------------------------
+// errors
+// ---------------------------------------------------------------------------------------
+static thread_local char g_err[1024] = "";
+
+void set_error(const char *fmt, ...) {
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(g_err, sizeof(g_err), fmt, ap);
+  va_end(ap);
+}
+
+void clear_error() { g_err[0] = '\0'; }
+
+// ---------------------------------------------------------------------------------------
+// device memory: stream-ordered allocations from the device's default pool, which keeps
+// freed memory cached for the next level instead of returning it to the driver.
+// ---------------------------------------------------------------------------------------
+static bool g_pool_ready[64] = {false};
+
+int dmalloc(void **p, size_t bytes, cudaStream_t s) {
+  int dev = 0;
+  VX_CUDA(cudaGetDevice(&dev));
+  if (dev >= 0 && dev < 64 && !g_pool_ready[dev]) {
+    cudaMemPool_t pool;
+    if (cudaDeviceGetDefaultMemPool(&pool, dev) == cudaSuccess) {
+      uint64_t keep = UINT64_MAX;
+      cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep);
+    }
+    g_pool_ready[dev] = true;
+  }
+  *p = nullptr;
+  if (bytes == 0) bytes = 16;
+  cudaError_t e = cudaMallocAsync(p, bytes, s);
+  if (e != cudaSuccess) {
+    set_error("cudaMallocAsync(%zu bytes) failed: %s", bytes, cudaGetErrorString(e));
+    return e == cudaErrorMemoryAllocation ? VX_ENOMEM : VX_ECUDA;
+  }
+  return VX_OK;
+}
+
+void dfree(void *p, cudaStream_t s) {
+  if (p) cudaFreeAsync(p, s);
+}
+
+// ---------------------------------------------------------------------------------------
+// kernel timing
+// ---------------------------------------------------------------------------------------
+static int take_event(std::vector<cudaEvent_t> &pool, cudaEvent_t *e) {
+  if (!pool.empty()) {
+    *e = pool.back();
+    pool.pop_back();
+    return VX_OK;
+  }
+  VX_CUDA(cudaEventCreate(e));
+  return VX_OK;
+}
+
+int Timer::begin(int kind, int64_t w) {
+  Pending p;
+  p.kind = kind;
+  p.work = w;
+  VX_CHECK(take_event(pool, &p.a));
+  VX_CHECK(take_event(pool, &p.b));
+  VX_CUDA(cudaEventRecord(p.a, stream));
+  pending.push_back(p);
+  return VX_OK;
+}
+
+int Timer::end() {
+  if (pending.empty()) return VX_OK;
+  VX_CUDA(cudaEventRecord(pending.back().b, stream));
+  return VX_OK;
+}
+
+int Timer::collect() {
+  if (pending.empty()) return VX_OK;
+  VX_CUDA(cudaEventSynchronize(pending.back().b));
+  for (auto &p : pending) {
+    float t = 0.f;
+    VX_CUDA(cudaEventElapsedTime(&t, p.a, p.b));
+    ms[p.kind] += t;
+    launches[p.kind] += 1;
+    work[p.kind] += p.work;
+    pool.push_back(p.a);
+    pool.push_back(p.b);
+  }
+  pending.clear();
+  return VX_OK;
+}
+
+void Timer::release() {
+  for (auto &p : pending) {
+    cudaEventDestroy(p.a);
+    cudaEventDestroy(p.b);
+  }
+  for (auto e : pool) cudaEventDestroy(e);
+  pending.clear();
+  pool.clear();
+}
+
+static const char *kKindNames[KK_COUNT] = {
+    "stage0_fp64", "stagej_fp64", "leaf_fp64", "stage0_fp32", "stagej_fp32", "leaf_fp32",
+    "csf_build",   "prune_scan",  "split",     "compact",     "recheck_select"};
+
+// ---------------------------------------------------------------------------------------
+// grid levels: box t on axis i is [lo + t w, lo + (t+1) w], w = (hi - lo) / 2^level.
+// Accepted only when every grid point is a binary64, so that endpoints are exact and child
+// boxes are subsets of their parents (the subdivision then never loses a box that a finer
+// level would keep).
+// ---------------------------------------------------------------------------------------
+static int low_bit_exponent(double x) {  // x = M 2^e with M odd: returns e (x != 0)
+  int e = 0;
+  double m = std::frexp(std::fabs(x), &e);
+  uint64_t M = (uint64_t)std::ldexp(m, 53);
+  int tz = 0;
+  while (!(M & 1)) {
+    M >>= 1;
+    ++tz;
+  }
+  return e - 53 + tz;
+}
+
+static bool grid_exact(double lo, double step, int64_t count, int mant_bits, int min_exp) {
+  // all lo + t*step, 0 <= t <= count, are integers times 2^q below 2^mant_bits
+  int q = 1 << 20;
+  if (lo != 0.0) q = std::min(q, low_bit_exponent(lo));
+  q = std::min(q, low_bit_exponent(step));
+  if (q < min_exp) return false;
+  double L = std::ldexp(lo, -q), W = std::ldexp(step, -q);
+  double lim = std::ldexp(1.0, mant_bits);
+  if (std::fabs(L) >= lim || std::fabs(W) >= lim) return false;
+  long double last = (long double)L + (long double)count * (long double)W;
+  return std::fabs((double)last) < lim && (long double)(double)last == last;
+}
+
+static bool api_trace() {
+  static int on = -1;
+  if (on < 0) on = std::getenv("VX_TRACE") ? 1 : 0;
+  return on == 1;
+}
+
+static int make_grid(int k, const double *dom, int level, LevelGrid *g) {
+  if (api_trace()) std::fprintf(stderr, "[vx] make_grid k=%d level=%d\n", k, level);
+  if (!dom) {
+    set_error("domain is NULL");
+    return VX_EINVAL;
+  }
+  if (level < 0 || level > VX_MAXLEVEL) {
+    set_error("level %d outside [0, %d]", level, VX_MAXLEVEL);
+    return VX_EINVAL;
+  }
+  *g = LevelGrid{};
+  for (int i = 0; i < k; ++i) {
+    const double lo = dom[2 * i], hi = dom[2 * i + 1];
+    if (!std::isfinite(lo) || !std::isfinite(hi) || !(lo < hi)) {
+      set_error("axis %d: domain [%g, %g] must be finite with lo < hi", i, lo, hi);
+      return VX_EINVAL;
+    }
+    const double w = hi - lo;
+    if (w - hi != -lo || !std::isfinite(w)) {  // hi - lo must be exact
+      set_error("axis %d: hi - lo is not a binary64", i);
+      return VX_EINVAL;
+    }
+    const double wl = std::ldexp(w, -level);
+    const int64_t count = (int64_t)1 << level;
+    if (std::ldexp(wl, level) != w || !grid_exact(lo, wl, count, 53, -1074)) {
+      set_error("axis %d: the level-%d grid of [%.17g, %.17g] is not exactly representable "
+                "(use a dyadic domain)", i, level, lo, hi);
+      return VX_EINVAL;
+    }
+    AxisGrid &a = g->ax[i];
+    a.lo = lo;
+    a.w = wl;
+    const double hw = 0.5 * wl;
+    if (api_trace()) std::fprintf(stderr, "[vx] axis %d exact64 ok\n", i);
+    a.fexact = grid_exact(lo, hw, 2 * count, 24, -149) ? 1 : 0;
+    if (api_trace()) std::fprintf(stderr, "[vx] axis %d fexact=%d\n", i, a.fexact);
+    a.flo = (float)lo;
+    a.fw = (float)wl;
+    if (a.fexact && ((double)a.flo != lo || (double)a.fw != wl)) a.fexact = 0;
+  }
+  return VX_OK;
+}
+
+// ---------------------------------------------------------------------------------------
+// polynomial packing
+// ---------------------------------------------------------------------------------------
+struct HostStage {
+  int32_t nfib = 0, maxlen = 0;
+  int64_t blk_in = 0, blk_out = 0;
+  std::vector<uint64_t> keys;  // fibre monomial in x_{s+2}..x_k, 16 bits per exponent
+  std::vector<int32_t> rowoff, fiblen, outpos;
+  std::unordered_map<uint64_t, int32_t> index;
+};
+
+struct HostPoly {
+  HostStage st[VX_KMAX];
+  std::vector<double2> c64;
+  std::vector<float2> c32;
+};
+
+static uint64_t suffix_key(const int32_t *e, int from, int k) {
+  uint64_t key = 0;
+  for (int v = from; v < k; ++v) key = (key << 16) | (uint64_t)e[v];
+  return key;
+}
+
+static float f32_round_up(double x) {
+  float f = (float)x;
+  if ((double)f < x) f = std::nextafter(f, INFINITY);
+  return f;
+}
+
+// <m, r> with r >= |c - m| + 2^-149 (the 2^-149 pays for the rounding of the Horner step
+// that adds this coefficient when its result falls below the normal range).
+static float2 to_midrad(double c) {
+  const float m = (float)c;
+  if (!std::isfinite(m)) return make_float2(0.f, INFINITY);
+  const double d = std::fabs(c - (double)m);  // exact (Sterbenz)
+  const float r = f32_round_up(d + std::ldexp(1.0, -149));
+  return make_float2(m, r);
+}
+
+static int pack_poly(int k, const vx_poly &p, HostPoly *hp) {
+  const int32_t nt = p.nterms;
+  if (p.nvars != k || nt < 0 || (nt > 0 && (!p.exps || !p.coefs))) {
+    set_error("polynomial: nvars %d (expected %d), nterms %d", p.nvars, k, nt);
+    return VX_EINVAL;
+  }
+  for (int64_t t = 0; t < (int64_t)nt * k; ++t) {
+    if (p.exps[t] < 0 || p.exps[t] > 65535) {
+      set_error("polynomial: exponent %d outside [0, 65535]", p.exps[t]);
+      return VX_EINVAL;
+    }
+  }
+  for (int32_t t = 0; t < nt; ++t) {
+    if (!std::isfinite(p.coefs[t])) {
+      set_error("polynomial: coefficient %d is not finite", t);
+      return VX_EINVAL;
+    }
+  }
+  // closure of the fibre sets, last stage first: stage s's fibres are the entries of stage
+  // s+1's input (monomials in x_{s+2}..x_k), each as long as the highest exponent of
+  // x_{s+1} among the terms with that monomial (1 if none: an all-zero fibre)
+  hp->st[k - 1].keys.assign(1, 0);
+  for (int s = k - 1; s >= 0; --s) {
+    HostStage &S = hp->st[s];
+    const int32_t nf = (int32_t)S.keys.size();
+    std::unordered_map<uint64_t, int32_t> idx;
+    idx.reserve(nf * 2 + 1);
+    for (int32_t f = 0; f < nf; ++f) idx[S.keys[f]] = f;
+    std::vector<int32_t> len(nf, 1);
+    for (int32_t t = 0; t < nt; ++t) {
+      const int32_t *e = p.exps + (int64_t)t * k;
+      auto it = idx.find(suffix_key(e, s + 1, k));
+      if (it == idx.end()) {
+        set_error("internal: monomial outside the fibre closure");
+        return VX_EINVAL;
+      }
+      len[it->second] = std::max(len[it->second], e[s] + 1);
+    }
+    std::vector<int32_t> order(nf);
+    for (int32_t f = 0; f < nf; ++f) order[f] = f;
+    std::sort(order.begin(), order.end(), [&](int32_t a, int32_t b) {
+      if (len[a] != len[b]) return len[a] > len[b];
+      return S.keys[a] < S.keys[b];
+    });
+    std::vector<uint64_t> keys(nf);
+    S.fiblen.resize(nf);
+    for (int32_t f = 0; f < nf; ++f) {
+      keys[f] = S.keys[order[f]];
+      S.fiblen[f] = len[order[f]];
+    }
+    S.keys.swap(keys);
+    S.index.clear();
+    S.index.reserve(nf * 2 + 1);
+    for (int32_t f = 0; f < nf; ++f) S.index[S.keys[f]] = f;
+    S.nfib = nf;
+    S.maxlen = S.fiblen[0];
+    S.rowoff.assign(S.maxlen + 1, 0);
+    {
+      int32_t f = nf;  // fibres with len > a form the prefix 0..cnt(a)-1
+      for (int32_t a = 0; a < S.maxlen; ++a) {
+        while (f > 0 && S.fiblen[f - 1] <= a) --f;
+        S.rowoff[a + 1] = S.rowoff[a] + f;
+      }
+    }
+    S.blk_in = S.rowoff[S.maxlen];
+    if (S.maxlen > 8192) {
+      set_error("polynomial: degree %d in one variable exceeds 8191", S.maxlen - 1);
+      return VX_EINVAL;
+    }
+    if (S.blk_in > INT32_MAX / 2) {
+      set_error("polynomial too large: %lld coefficients in one stage", (long long)S.blk_in);
+      return VX_EINVAL;
+    }
+    if (s > 0) {
+      std::vector<uint64_t> &nk = hp->st[s - 1].keys;
+      nk.clear();
+      nk.reserve(S.blk_in);
+      const int sh = 16 * (k - 1 - s);
+      for (int32_t f = 0; f < nf; ++f)
+        for (int32_t a = 0; a < S.fiblen[f]; ++a) nk.push_back(((uint64_t)a << sh) | S.keys[f]);
+    }
+  }
+  for (int s = 0; s < k; ++s) {
+    HostStage &S = hp->st[s];
+    S.blk_out = s + 1 < k ? hp->st[s + 1].blk_in : 1;
+    S.outpos.assign(S.nfib, 0);
+    if (s + 1 < k) {
+      const HostStage &T = hp->st[s + 1];
+      const int sh = 16 * (k - 2 - s);
+      const uint64_t mask = sh ? ((uint64_t)1 << sh) - 1 : 0;
+      for (int32_t f = 0; f < S.nfib; ++f) {
+        const uint64_t a = S.keys[f] >> sh;
+        const int32_t g = T.index.at(S.keys[f] & mask);
+        S.outpos[f] = T.rowoff[a] + g;
+      }
+    }
+  }
+  // coefficient block of stage 0: entry (a_1, fibre) at rowoff[a_1] + fibre
+  const HostStage &S0 = hp->st[0];
+  hp->c64.assign(S0.blk_in, make_double2(0.0, 0.0));
+  std::vector<uint8_t> seen(S0.blk_in, 0);
+  for (int32_t t = 0; t < nt; ++t) {
+    const int32_t *e = p.exps + (int64_t)t * k;
+    const int32_t f = S0.index.at(suffix_key(e, 1, k));
+    const int64_t pos = S0.rowoff[e[0]] + f;
+    if (seen[pos]) {
+      set_error("polynomial: monomial %d appears twice", t);
+      return VX_EINVAL;
+    }
+    seen[pos] = 1;
+    hp->c64[pos] = make_double2(p.coefs[t], p.coefs[t]);
+  }
+  hp->c32.resize(S0.blk_in);
+  for (int64_t i = 0; i < S0.blk_in; ++i) hp->c32[i] = to_midrad(hp->c64[i].x);
+  return VX_OK;
+}
+
+}  // namespace vx
+
+using namespace vx;
+
+struct vx_system {
+  SysDev dev;
+  void *mem = nullptr;
+  cudaStream_t stream = nullptr;
+  std::vector<int64_t> M;  // [npoly][k+1]
+};
+
+struct vx_csf {
+  CsfObj o;
+};
+
+struct vx_result {
+  int k = 0, depth = 0;
+  CsfObj fin;
+  std::vector<int64_t> tested, kept, nodes, recheck, madds;
+  Timer tm;
+  double elapsed_ms = 0.0;
+  bool have_tuples = false;
+  std::vector<int32_t> tuples;
+};
+
+static cudaStream_t as_stream(void *s) { return (cudaStream_t)s; }
+
+// ---------------------------------------------------------------------------------------
+// C ABI
+// ---------------------------------------------------------------------------------------
+extern "C" {
+
+const char *vx_last_error(void) { return g_err; }
+
+int vx_system_create(const vx_poly *F, int32_t npoly, void *stream, vx_system **out) {
+  clear_error();
+  if (!out || !F || npoly < 1 || npoly > VX_MAXPOLY) {
+    set_error("vx_system_create: need 1..%d polynomials and an out pointer", VX_MAXPOLY);
+    return VX_EINVAL;
+  }
+  *out = nullptr;
+  const int k = F[0].nvars;
+  if (k < 1 || k > VX_KMAX) {
+    set_error("vx_system_create: %d variables (1..%d supported)", k, VX_KMAX);
+    return VX_EINVAL;
+  }
+  std::vector<HostPoly> hp(npoly);
+  for (int f = 0; f < npoly; ++f) VX_CHECK(pack_poly(k, F[f], &hp[f]));
+  // one device allocation: per polynomial the two coefficient blocks, then per stage the
+  // row offsets, fibre lengths and output positions
+  auto al = [](size_t x) { return (x + 255) & ~(size_t)255; };
+  size_t bytes = 0;
+  for (int f = 0; f < npoly; ++f) {
+    bytes += al(hp[f].c64.size() * sizeof(double2)) + al(hp[f].c32.size() * sizeof(float2));
+    for (int s = 0; s < k; ++s) {
+      const HostStage &S = hp[f].st[s];
+      bytes += al((S.maxlen + 1) * 4) + 2 * al((size_t)S.nfib * 4);
+    }
+  }
+  std::vector<char> host(bytes, 0);
+  vx_system *sys = new (std::nothrow) vx_system();
+  if (!sys) {
+    set_error("out of host memory");
+    return VX_ENOMEM;
+  }
+  cudaStream_t s = as_stream(stream);
+  int rc = dmalloc(&sys->mem, bytes, s);
+  if (rc != VX_OK) {
+    delete sys;
+    return rc;
+  }
+  sys->stream = s;
+  sys->dev.k = k;
+  sys->dev.npoly = npoly;
+  sys->M.assign((size_t)npoly * (k + 1), 1);
+  size_t off = 0;
+  char *dbase = (char *)sys->mem;
+  auto put = [&](const void *src, size_t n) -> void * {
+    std::memcpy(host.data() + off, src, n);
+    void *d = dbase + off;
+    off += al(n);
+    return d;
+  };
+  for (int f = 0; f < npoly; ++f) {
+    PolyDev &P = sys->dev.p[f];
+    P.c64 = (const double2 *)put(hp[f].c64.data(), hp[f].c64.size() * sizeof(double2));
+    P.c32 = (const float2 *)put(hp[f].c32.data(), hp[f].c32.size() * sizeof(float2));
+    for (int s2 = 0; s2 < k; ++s2) {
+      const HostStage &S = hp[f].st[s2];
+      StageDev &D = P.st[s2];
+      D.nfib = S.nfib;
+      D.maxlen = S.maxlen;
+      D.blk_in = S.blk_in;
+      D.blk_out = S.blk_out;
+      D.rowoff = (const int32_t *)put(S.rowoff.data(), (S.maxlen + 1) * 4);
+      D.fiblen = (const int32_t *)put(S.fiblen.data(), (size_t)S.nfib * 4);
+      D.outpos = (const int32_t *)put(S.outpos.data(), (size_t)S.nfib * 4);
+      sys->M[(size_t)f * (k + 1) + s2] = S.blk_in;
+    }
+  }
+  cudaError_t e = cudaMemcpyAsync(sys->mem, host.data(), bytes, cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) {
+    set_error("uploading the system failed: %s", cudaGetErrorString(e));
+    dfree(sys->mem, s);
+    delete sys;
+    return VX_ECUDA;
+  }
+  *out = sys;
+  return VX_OK;
+}
+
+void vx_system_free(vx_system *sys) {
+  if (!sys) return;
+  dfree(sys->mem, sys->stream);
+  delete sys;
+}
+
+int vx_system_info(const vx_system *sys, int32_t *k, int32_t *npoly, int64_t *h_M) {
+  clear_error();
+  if (!sys) {
+    set_error("vx_system_info: NULL system");
+    return VX_EINVAL;
+  }
+  if (k) *k = sys->dev.k;
+  if (npoly) *npoly = sys->dev.npoly;
+  if (h_M) std::memcpy(h_M, sys->M.data(), sys->M.size() * sizeof(int64_t));
+  return VX_OK;
+}
+
+int vx_csf_build(int32_t k, int32_t level, const int32_t *d_tuples, int64_t n, void *stream,
+                 vx_csf **out) {
+  clear_error();
+  if (!out || k < 1 || k > VX_KMAX || level < 0 || level > VX_MAXLEVEL || n < 0 ||
+      (n > 0 && !d_tuples)) {
+    set_error("vx_csf_build: bad arguments (k %d, level %d, n %lld)", k, level, (long long)n);
+    return VX_EINVAL;
+  }
+  *out = nullptr;
+  vx_csf *c = new (std::nothrow) vx_csf();
+  if (!c) return VX_ENOMEM;
+  int rc = csf_build_dev(k, level, d_tuples, n, as_stream(stream), &c->o, nullptr);
+  if (rc != VX_OK) {
+    csf_release(&c->o);
+    delete c;
+    return rc;
+  }
+  *out = c;
+  return VX_OK;
+}
+
+void vx_csf_free(vx_csf *c) {
+  if (!c) return;
+  csf_release(&c->o);
+  delete c;
+}
+
+int vx_csf_nodes(const vx_csf *c, int32_t *k, int32_t *level, int64_t *h_N) {
+  clear_error();
+  if (!c) {
+    set_error("vx_csf_nodes: NULL csf");
+    return VX_EINVAL;
+  }
+  if (k) *k = c->o.v.k;
+  if (level) *level = c->o.v.level;
+  if (h_N)
+    for (int d = 0; d < c->o.v.k; ++d) h_N[d] = c->o.v.N[d];
+  return VX_OK;
+}
+
+int vx_csf_export(const vx_csf *c, int32_t depth, int32_t *d_labels, int32_t *d_ptr,
+                  void *stream) {
+  clear_error();
+  if (!c || depth < 1 || depth > c->o.v.k || !d_labels) {
+    set_error("vx_csf_export: bad arguments");
+    return VX_EINVAL;
+  }
+  const int d = depth - 1;
+  cudaStream_t s = as_stream(stream);
+  const int64_t n = c->o.v.N[d];
+  if (n > 0)
+    VX_CUDA(cudaMemcpyAsync(d_labels, c->o.v.lab[d], n * 4, cudaMemcpyDeviceToDevice, s));
+  if (d_ptr && d + 1 < c->o.v.k)
+    VX_CUDA(cudaMemcpyAsync(d_ptr, c->o.v.ptr[d], (n + 1) * 4, cudaMemcpyDeviceToDevice, s));
+  return VX_OK;
+}
+
+int vx_csf_tuples(const vx_csf *c, int32_t *d_tuples, void *stream) {
+  clear_error();
+  if (!c || (!d_tuples && c->o.v.N[c->o.v.k - 1] > 0)) {
+    set_error("vx_csf_tuples: bad arguments");
+    return VX_EINVAL;
+  }
+  return csf_tuples_dev(c->o.v, d_tuples, as_stream(stream));
+}
+
+int vx_csf_eval_level(const vx_system *sys, const vx_csf *c, const double *h_domain,
+                      int32_t mode, double *d_lo, double *d_hi, uint8_t *d_keep, void *stream) {
+  clear_error();
+  if (!sys || !c || !d_keep || (mode != VX_FP64 && mode != VX_FP32_MIDRAD) ||
+      (!d_lo) != (!d_hi) || c->o.v.k != sys->dev.k) {
+    set_error("vx_csf_eval_level: bad arguments");
+    return VX_EINVAL;
+  }
+  LevelGrid g;
+  if (api_trace()) std::fprintf(stderr, "[vx] eval_level entry\n");
+  VX_CHECK(make_grid(c->o.v.k, h_domain, c->o.v.level, &g));
+  if (api_trace()) std::fprintf(stderr, "[vx] grid ok\n");
+  return eval_level(sys->dev, c->o.v, g, mode, d_lo, d_hi, d_keep, as_stream(stream), nullptr,
+                    nullptr);
+}
+
+int vx_csf_subdivide(const vx_csf *in, const uint8_t *d_keep, void *stream, vx_csf **out) {
+  clear_error();
+  if (!in || !out || (!d_keep && in->o.v.N[in->o.v.k - 1] > 0)) {
+    set_error("vx_csf_subdivide: bad arguments");
+    return VX_EINVAL;
+  }
+  if (in->o.v.level + 1 > VX_MAXLEVEL) {
+    set_error("vx_csf_subdivide: level %d is the finest supported", in->o.v.level);
+    return VX_EINVAL;
+  }
+  *out = nullptr;
+  vx_csf *c = new (std::nothrow) vx_csf();
+  if (!c) return VX_ENOMEM;
+  int rc = csf_prune(in->o.v, d_keep, 1, nullptr, as_stream(stream), &c->o, nullptr);
+  if (rc != VX_OK) {
+    csf_release(&c->o);
+    delete c;
+    return rc;
+  }
+  *out = c;
+  return VX_OK;
+}
+
+int vx_csf_compact(const vx_csf *in, const uint8_t *d_keep, int32_t *d_index, void *stream,
+                   vx_csf **out) {
+  clear_error();
+  if (!in || !out || (!d_keep && in->o.v.N[in->o.v.k - 1] > 0)) {
+    set_error("vx_csf_compact: bad arguments");
+    return VX_EINVAL;
+  }
+  *out = nullptr;
+  vx_csf *c = new (std::nothrow) vx_csf();
+  if (!c) return VX_ENOMEM;
+  int rc = csf_prune(in->o.v, d_keep, 0, d_index, as_stream(stream), &c->o, nullptr);
+  if (rc != VX_OK) {
+    csf_release(&c->o);
+    delete c;
+    return rc;
+  }
+  *out = c;
+  return VX_OK;
+}
+
+}  // extern "C"
+
+// ---------------------------------------------------------------------------------------
+// Algorithm 3: the level loop
+// ---------------------------------------------------------------------------------------
+static int level0(int k, cudaStream_t s, CsfObj *o) {
+  int64_t N[VX_KMAX] = {1, 1, 1, 1};
+  VX_CHECK(csf_alloc(o, k, 0, N, s));
+  // one box (0, ..., 0): labels 0, parents 0, child ranges [0, 1)
+  VX_CUDA(cudaMemsetAsync(o->mem, 0, o->bytes, s));
+  return set_ptr_sentinels(o->v, s);
+}
+
+static int enclose_impl(const vx_system *sys, const double *dom, int depth, const vx_opts *o,
+                        cudaStream_t s, vx_result *R) {
+  const int k = sys->dev.k;
+  vx_opts opts{};
+  if (o) opts = *o;
+  if (opts.mode != VX_FP64 && opts.mode != VX_FP32_MIDRAD) {
+    set_error("vx_enclose: unknown mode %d", opts.mode);
+    return VX_EINVAL;
+  }
+  float theta = opts.theta > 0.f ? opts.theta : 0.5f;
+  if (theta > 1.f) {
+    set_error("vx_enclose: theta %g outside (0, 1]", (double)theta);
+    return VX_EINVAL;
+  }
+  if (depth < 0 || depth > VX_MAXLEVEL) {
+    set_error("vx_enclose: depth %d outside [0, %d]", depth, VX_MAXLEVEL);
+    return VX_EINVAL;
+  }
+  LevelGrid g;
+  VX_CHECK(make_grid(k, dom, depth, &g));  // the finest grid exact => every coarser one too
+  R->k = k;
+  R->depth = depth;
+  R->tested.assign(depth + 1, 0);
+  R->kept.assign(depth + 1, 0);
+  R->nodes.assign((size_t)(depth + 1) * k, 0);
+  R->recheck.assign(depth + 1, 0);
+  R->madds.assign(depth + 1, 0);
+  R->tm.on = opts.timing != 0;
+  R->tm.stream = s;
+  Timer *tm = &R->tm;
+  cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+  VX_CUDA(cudaEventCreate(&ev0));
+  VX_CUDA(cudaEventCreate(&ev1));
+  VX_CUDA(cudaEventRecord(ev0, s));
+  CsfObj cur;
+  int rc = level0(k, s, &cur);
+  for (int l = 0; l <= depth && rc == VX_OK; ++l) {
+    rc = make_grid(k, dom, l, &g);
+    if (rc != VX_OK) break;
+    const int64_t n = cur.v.N[k - 1];
+    R->tested[l] = n;
+    for (int d = 0; d < k; ++d) R->nodes[(size_t)l * k + d] = cur.v.N[d];
+    const bool f32 = opts.mode == VX_FP32_MIDRAD && !(opts.fp64_final && l == depth);
+    const bool recheck = f32 && opts.fp64_recheck;
+    uint8_t *keep = nullptr, *tight = nullptr;
+    rc = dmalloc((void **)&keep, (size_t)std::max<int64_t>(n, 1), s);
+    if (rc == VX_OK && recheck) rc = dmalloc((void **)&tight, (size_t)std::max<int64_t>(n, 1), s);
+    int64_t w = 0;
+    if (rc == VX_OK) {
+      if (recheck)
+        rc = eval_level_tight(sys->dev, cur.v, g, theta, keep, tight, s, tm, &w);
+      else
+        rc = eval_level(sys->dev, cur.v, g, f32 ? VX_FP32_MIDRAD : VX_FP64, nullptr, nullptr,
+                        keep, s, tm, &w);
+      R->madds[l] += w;
+    }
+    if (rc == VX_OK && recheck && n > 0) {
+      // boxes the binary32 test keeps with a tight margin: re-evaluate them in binary64
+      CsfObj sub;
+      int32_t *idx = nullptr;
+      uint8_t *subkeep = nullptr;
+      rc = dmalloc((void **)&idx, (size_t)n * 4, s);
+      if (rc == VX_OK) rc = csf_prune(cur.v, tight, 0, idx, s, &sub, tm);
+      if (rc == VX_OK) {
+        const int64_t ns = sub.v.N[k - 1];
+        R->recheck[l] = ns;
+        if (ns > 0) {
+          rc = dmalloc((void **)&subkeep, (size_t)ns, s);
+          int64_t w2 = 0;
+          if (rc == VX_OK)
+            rc = eval_level(sys->dev, sub.v, g, VX_FP64, nullptr, nullptr, subkeep, s, tm, &w2);
+          R->madds[l] += w2;
+          if (rc == VX_OK) rc = scatter_keep(idx, subkeep, ns, keep, s);
+        }
+        csf_release(&sub);
+      }
+      dfree(subkeep, s);
+      dfree(idx, s);
+    }
+    if (rc == VX_OK) {
+      if (l == depth) {
+        rc = csf_prune(cur.v, keep, 0, nullptr, s, &R->fin, tm);
+        if (rc == VX_OK) R->kept[l] = R->fin.v.N[k - 1];
+      } else {
+        CsfObj next;
+        rc = csf_prune(cur.v, keep, 1, nullptr, s, &next, tm);
+        if (rc == VX_OK) {
+          R->kept[l] = next.v.N[k - 1] >> k;
+          csf_release(&cur);
+          cur = next;
+        }
+      }
+    }
+    dfree(tight, s);
+    dfree(keep, s);
+  }
+  csf_release(&cur);
+  if (rc == VX_OK) {
+    cudaError_t e = cudaEventRecord(ev1, s);
+    if (e == cudaSuccess) e = cudaEventSynchronize(ev1);
+    float ms = 0.f;
+    if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, ev0, ev1);
+    if (e != cudaSuccess) {
+      set_error("enclose: %s", cudaGetErrorString(e));
+      rc = VX_ECUDA;
+    }
+    R->elapsed_ms = ms;
+  }
+  cudaEventDestroy(ev0);
+  cudaEventDestroy(ev1);
+  if (rc == VX_OK) rc = R->tm.collect();
+  return rc;
+}
+
+static cudaStream_t library_stream() {
+  static cudaStream_t s = nullptr;
+  static bool made = false;
+  if (!made) {
+    if (cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking) != cudaSuccess) s = nullptr;
+    made = true;
+  }
+  return s;
+}
+
+extern "C" {
+
+int vx_enclose_system(const vx_system *sys, const double *h_domain, int32_t depth,
+                      const vx_opts *opts, void *stream, vx_result **out) {
+  clear_error();
+  if (!sys || !out) {
+    set_error("vx_enclose_system: NULL argument");
+    return VX_EINVAL;
+  }
+  *out = nullptr;
+  vx_result *R = new (std::nothrow) vx_result();
+  if (!R) return VX_ENOMEM;
+  int rc = enclose_impl(sys, h_domain, depth, opts, as_stream(stream), R);
+  if (rc != VX_OK) {
+    csf_release(&R->fin);
+    R->tm.release();
+    delete R;
+    return rc;
+  }
+  *out = R;
+  return VX_OK;
+}
+
+int vx_enclose(const vx_poly *F, int32_t npoly, const double *h_domain, int32_t depth,
+               const vx_opts *opts, vx_result **out) {
+  clear_error();
+  if (!out) {
+    set_error("vx_enclose: NULL out");
+    return VX_EINVAL;
+  }
+  *out = nullptr;
+  cudaStream_t s = library_stream();
+  vx_system *sys = nullptr;
+  VX_CHECK(vx_system_create(F, npoly, (void *)s, &sys));
+  int rc = vx_enclose_system(sys, h_domain, depth, opts, (void *)s, out);
+  vx_system_free(sys);
+  if (rc == VX_OK) {
+    const int32_t *t = nullptr;
+    int64_t n = 0;
+    rc = vx_result_boxes(*out, &n, &t);
+    if (rc != VX_OK) {
+      vx_result_free(*out);
+      *out = nullptr;
+    }
+  }
+  return rc;
+}
+
+int vx_result_boxes(vx_result *R, int64_t *n, const int32_t **h_tuples) {
+  clear_error();
+  if (!R || !n || !h_tuples) {
+    set_error("vx_result_boxes: NULL argument");
+    return VX_EINVAL;
+  }
+  if (!R->have_tuples) {
+    const int k = R->k;
+    const int64_t m = R->fin.v.N[k - 1];
+    R->tuples.assign((size_t)m * k, 0);
+    if (m > 0) {
+      cudaStream_t s = R->fin.stream;
+      int32_t *d = nullptr;
+      VX_CHECK(dmalloc((void **)&d, (size_t)m * k * 4, s));
+      int rc = csf_tuples_dev(R->fin.v, d, s);
+      if (rc == VX_OK) {
+        cudaError_t e = cudaMemcpyAsync(R->tuples.data(), d, (size_t)m * k * 4,
+                                        cudaMemcpyDeviceToHost, s);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+        if (e != cudaSuccess) {
+          set_error("copying the boxes to the host failed: %s", cudaGetErrorString(e));
+          rc = VX_ECUDA;
+        }
+      }
+      dfree(d, s);
+      VX_CHECK(rc);
+    }
+    R->have_tuples = true;
+  }
+  *n = R->fin.v.N[R->k - 1];
+  *h_tuples = R->tuples.data();
+  return VX_OK;
+}
+
+int vx_result_csf(const vx_result *R, const vx_csf **csf) {
+  clear_error();
+  if (!R || !csf) {
+    set_error("vx_result_csf: NULL argument");
+    return VX_EINVAL;
+  }
+  // vx_csf is a thin wrapper over CsfObj with the same layout
+  *csf = reinterpret_cast<const vx_csf *>(&R->fin);
+  return VX_OK;
+}
+
+int vx_result_stats(const vx_result *R, int32_t *nlevels, int64_t *tested, int64_t *kept,
+                    int64_t *nodes, int64_t *recheck, int64_t *madds) {
+  clear_error();
+  if (!R) {
+    set_error("vx_result_stats: NULL result");
+    return VX_EINVAL;
+  }
+  const int L = R->depth + 1;
+  if (nlevels) *nlevels = L;
+  if (tested) std::memcpy(tested, R->tested.data(), L * 8);
+  if (kept) std::memcpy(kept, R->kept.data(), L * 8);
+  if (nodes) std::memcpy(nodes, R->nodes.data(), (size_t)L * R->k * 8);
+  if (recheck) std::memcpy(recheck, R->recheck.data(), L * 8);
+  if (madds) std::memcpy(madds, R->madds.data(), L * 8);
+  return VX_OK;
+}
+
+int vx_result_timing(const vx_result *R, int32_t *nkinds, double *h_ms, int64_t *h_launches,
+                     int64_t *h_work) {
+  clear_error();
+  if (!R) {
+    set_error("vx_result_timing: NULL result");
+    return VX_EINVAL;
+  }
+  if (nkinds) *nkinds = KK_COUNT;
+  for (int i = 0; i < KK_COUNT; ++i) {
+    if (h_ms) h_ms[i] = R->tm.ms[i];
+    if (h_launches) h_launches[i] = R->tm.launches[i];
+    if (h_work) h_work[i] = R->tm.work[i];
+  }
+  return VX_OK;
+}
+
+const char *vx_kernel_kind_name(int32_t kind) {
+  return (kind >= 0 && kind < KK_COUNT) ? kKindNames[kind] : "";
+}
+
+int vx_result_elapsed_ms(const vx_result *R, double *ms) {
+  clear_error();
+  if (!R || !ms) {
+    set_error("vx_result_elapsed_ms: NULL argument");
+    return VX_EINVAL;
+  }
+  *ms = R->elapsed_ms;
+  return VX_OK;
+}
+
+void vx_result_free(vx_result *R) {
+  if (!R) return;
+  csf_release(&R->fin);
+  R->tm.release();
+  delete R;
+}
+
+}  // extern "C"

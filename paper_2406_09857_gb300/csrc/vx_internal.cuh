@@ -1,0 +1,164 @@
+// vx_internal.cuh -- shared declarations of libvx (device structs, interval arithmetic,
+// error handling).  Not part of the public ABI (that is include/vx.h).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <vector>
+
+#include "vx.h"
+
+namespace vx {
+
+// ---------------------------------------------------------------------------------------
+// Errors: every entry point returns a VX_* code; the message goes to a thread-local buffer.
+// ---------------------------------------------------------------------------------------
+void set_error(const char *fmt, ...);
+void clear_error();
+
+#define VX_CUDA(call)                                                                     \
+  do {                                                                                    \
+    cudaError_t e_ = (call);                                                              \
+    if (e_ != cudaSuccess) {                                                              \
+      ::vx::set_error("%s failed: %s (%s:%d)", #call, cudaGetErrorString(e_), __FILE__,   \
+                      __LINE__);                                                          \
+      return VX_ECUDA;                                                                    \
+    }                                                                                     \
+  } while (0)
+
+#define VX_CHECK(x)                  \
+  do {                               \
+    int rc_ = (x);                   \
+    if (rc_ != VX_OK) return rc_;    \
+  } while (0)
+
+#define VX_LAUNCH_CHECK() VX_CUDA(cudaGetLastError())
+
+// Stream-ordered device memory (the device's default memory pool, kept cached).
+int dmalloc(void **p, size_t bytes, cudaStream_t s);
+void dfree(void *p, cudaStream_t s);
+
+// ---------------------------------------------------------------------------------------
+// Packed polynomial (Sec. 2.1, "Representing a Multivariate Polynomial", re-laid out for the
+// device).  Stage s (0-based) evaluates x_{s+1}: it runs Algorithm 1 once per fibre, a fibre
+// being one monomial m in x_{s+2}..x_k with coefficients indexed by the exponent a of
+// x_{s+1}, a = 0..len(m)-1 (missing exponents below the highest are zero coefficients).
+// Fibres are sorted by decreasing length, so row a of the stage input holds the fibres with
+// len > a, i.e. fibres 0..rowcount(a)-1, at rowoff[a] .. rowoff[a+1]-1: consecutive threads
+// on consecutive fibres read consecutive addresses at every Horner step.  The value of fibre
+// f is written at outpos[f] of the next stage's input block.
+// ---------------------------------------------------------------------------------------
+struct StageDev {
+  int32_t nfib, maxlen;
+  int64_t blk_in;   // entries of one input block of this stage
+  int64_t blk_out;  // entries of one output block (= next stage's blk_in; 1 at the last stage)
+  const int32_t *rowoff;  // [maxlen + 1]
+  const int32_t *fiblen;  // [nfib]
+  const int32_t *outpos;  // [nfib] (unused at the last stage)
+};
+
+struct PolyDev {
+  StageDev st[VX_KMAX];
+  const double2 *c64;  // stage-0 input block as degenerate intervals (lo = hi = coefficient)
+  const float2 *c32;   // stage-0 input block as <m, r> binary32 midpoint-radius pairs
+};
+
+struct SysDev {
+  int32_t k, npoly;
+  PolyDev p[VX_MAXPOLY];
+};
+
+// One axis of one grid level: box t is [lo + t*w, lo + (t+1)*w] (exact on accepted domains).
+struct AxisGrid {
+  double lo, w;
+  float flo, fw;    // the same in binary32 when every half-grid point is a binary32
+  int32_t fexact;   // 1 if flo/fw describe the grid exactly
+};
+
+struct LevelGrid {
+  AxisGrid ax[VX_KMAX];
+};
+
+// ---------------------------------------------------------------------------------------
+// Device CSF of box indices (Sec. 2.1, "Representing a Set of Boxes").  Depth d (0-based)
+// holds N[d] nodes: label lab[d][i] (grid index along x_{d+1}), parent par[d][i] (d >= 1,
+// node index at depth d-1) and, for d < k-1, child range ptr[d][i] .. ptr[d][i+1]-1.
+// ---------------------------------------------------------------------------------------
+struct CsfView {
+  int32_t k, level;
+  int64_t N[VX_KMAX];
+  int32_t *lab[VX_KMAX];
+  int32_t *par[VX_KMAX];
+  int32_t *ptr[VX_KMAX];
+};
+
+// ---------------------------------------------------------------------------------------
+// Kernel timing (CUDA events around launches when enabled).
+// ---------------------------------------------------------------------------------------
+enum KernelKind {
+  KK_STAGE0 = 0,   // depth-1 partial evaluation (reads the coefficient tensor)
+  KK_STAGEJ,       // depth-j partial evaluation, 1 < j < k
+  KK_LEAF,         // leaf Horner + C0 test
+  KK_STAGE0_F32,
+  KK_STAGEJ_F32,
+  KK_LEAF_F32,
+  KK_CSF_BUILD,    // scans of csf_build
+  KK_PRUNE,        // keep propagation, rank scan, kept-tree pointers
+  KK_SPLIT,        // 2^k split and rebuild
+  KK_COMPACT,      // stable compaction of kept leaves
+  KK_RECHECK,      // selection of tight boxes for the FP64 recheck
+  KK_COUNT
+};
+
+struct Timer {
+  bool on = false;
+  cudaStream_t stream = nullptr;
+  struct Pending {
+    int kind;
+    cudaEvent_t a, b;
+    int64_t work;
+  };
+  std::vector<Pending> pending;
+  std::vector<cudaEvent_t> pool;
+  double ms[KK_COUNT] = {0};
+  int64_t launches[KK_COUNT] = {0};
+  int64_t work[KK_COUNT] = {0};
+  int begin(int kind, int64_t work);  // records the start event on `stream`
+  int end();                          // records the stop event of the last begin()
+  int collect();                      // synchronises and folds pending pairs into the sums
+  void release();
+};
+
+// Launchers (vx_eval.cu).
+int eval_level(const SysDev &sys, const CsfView &csf, const LevelGrid &grid, int mode,
+               double *d_lo, double *d_hi, uint8_t *d_keep, cudaStream_t s, Timer *tm,
+               int64_t *madds_out);
+// binary32 midpoint-radius evaluation that also flags the kept boxes whose enclosure is
+// tight for some polynomial (|m| >= theta r): d_tight[i] = keep[i] && tight(i).
+int eval_level_tight(const SysDev &sys, const CsfView &csf, const LevelGrid &grid, float theta,
+                     uint8_t *d_keep, uint8_t *d_tight, cudaStream_t s, Timer *tm,
+                     int64_t *madds_out);
+
+// Integer kernels (vx_csf.cu).  Objects own one device allocation each.
+struct CsfObj {
+  CsfView v;
+  void *mem = nullptr;
+  size_t bytes = 0;
+  cudaStream_t stream = nullptr;
+};
+int csf_alloc(CsfObj *o, int k, int level, const int64_t *N, cudaStream_t s);
+void csf_release(CsfObj *o);
+int csf_build_dev(int k, int level, const int32_t *d_tuples, int64_t n, cudaStream_t s,
+                  CsfObj *out, Timer *tm);
+// split = 1: Algorithm 3's bisection (level + 1); split = 0: stable compaction (same level),
+// writing the kept leaves' old indices to d_index when non-null.
+int csf_prune(const CsfView &in, const uint8_t *d_keep, int split, int32_t *d_index,
+              cudaStream_t s, CsfObj *out, Timer *tm);
+// ptr[d][N[d]] = N[d+1] for every depth d < k-1.
+int set_ptr_sentinels(const CsfView &v, cudaStream_t s);
+int csf_tuples_dev(const CsfView &c, int32_t *d_tuples, cudaStream_t s);
+int scatter_keep(const int32_t *d_index, const uint8_t *d_sub_keep, int64_t n, uint8_t *d_keep,
+                 cudaStream_t s);
+
+}  // namespace vx

@@ -1,0 +1,351 @@
+"""ctypes binding of ``libvx`` (``include/vx.h``): argument marshalling only.
+
+Every step of the computation runs in the library's CUDA kernels.  Device buffers are torch
+CUDA tensors (passed by ``data_ptr()``) and streams are torch streams (``cuda_stream``).  If the
+library has not been built, or no CUDA device is present, the calls raise: there is no CPU
+fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "_build", "libvx.so")
+
+OK, EINVAL, ENOMEM, ECAPACITY, EOVERFLOW, ETIMEOUT, ECUDA = 0, -1, -2, -3, -4, -5, -6
+KMAX, MAXPOLY, MAXLEVEL = 4, 8, 24
+FP64, FP32_MIDRAD = 0, 1
+
+_lib = None
+
+
+class VxError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__("vx error %d: %s" % (code, msg))
+        self.code = code
+
+
+class Poly(ctypes.Structure):
+    _fields_ = [("nvars", ctypes.c_int32), ("nterms", ctypes.c_int32),
+                ("exps", ctypes.c_void_p), ("coefs", ctypes.c_void_p)]
+
+
+class Opts(ctypes.Structure):
+    _fields_ = [("mode", ctypes.c_int32), ("fp64_final", ctypes.c_int32),
+                ("fp64_recheck", ctypes.c_int32), ("theta", ctypes.c_float),
+                ("timing", ctypes.c_int32), ("reserved", ctypes.c_int32 * 7)]
+
+
+def lib() -> ctypes.CDLL:
+    """Loads the in-tree ``libvx.so``; raises ImportError if it has not been built."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise ImportError("libvx.so is not built (%s); run paper_2406_09857_gb300/build.py"
+                          % LIB_PATH)
+    L = ctypes.CDLL(LIB_PATH)
+    P, i32, i64 = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64
+    PP = ctypes.POINTER(ctypes.c_void_p)
+    sig = {
+        "vx_last_error": ([], ctypes.c_char_p),
+        "vx_system_create": ([P, i32, P, PP], i32),
+        "vx_system_free": ([P], None),
+        "vx_system_info": ([P, P, P, P], i32),
+        "vx_csf_build": ([i32, i32, P, i64, P, PP], i32),
+        "vx_csf_free": ([P], None),
+        "vx_csf_nodes": ([P, P, P, P], i32),
+        "vx_csf_export": ([P, i32, P, P, P], i32),
+        "vx_csf_tuples": ([P, P, P], i32),
+        "vx_csf_eval_level": ([P, P, P, i32, P, P, P, P], i32),
+        "vx_csf_subdivide": ([P, P, P, PP], i32),
+        "vx_csf_compact": ([P, P, P, P, PP], i32),
+        "vx_enclose_system": ([P, P, i32, P, P, PP], i32),
+        "vx_enclose": ([P, i32, P, i32, P, PP], i32),
+        "vx_result_boxes": ([P, P, P], i32),
+        "vx_result_csf": ([P, PP], i32),
+        "vx_result_stats": ([P, P, P, P, P, P, P], i32),
+        "vx_result_timing": ([P, P, P, P, P], i32),
+        "vx_kernel_kind_name": ([i32], ctypes.c_char_p),
+        "vx_result_elapsed_ms": ([P, P], i32),
+        "vx_result_free": ([P], None),
+    }
+    for name, (args, res) in sig.items():
+        f = getattr(L, name)
+        f.argtypes = args
+        f.restype = res
+    _lib = L
+    return L
+
+
+def declared_symbols():
+    """Names of the functions declared in include/vx.h."""
+    import re
+
+    hdr = os.path.join(os.path.dirname(HERE), "include", "vx.h")
+    text = open(hdr).read()
+    return sorted(set(re.findall(r"\b(vx_[a-z0-9_]+)\s*\(", text)))
+
+
+def _check(rc: int):
+    if rc != OK:
+        msg = lib().vx_last_error()
+        raise VxError(rc, msg.decode() if msg else "")
+
+
+def _ptr(t) -> int:
+    return 0 if t is None else t.data_ptr()
+
+
+def _stream(stream) -> int:
+    import torch
+
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return stream.cuda_stream
+
+
+def _np_ptr(a: np.ndarray):
+    return a.ctypes.data_as(ctypes.c_void_p)
+
+
+def _polys(polys):
+    """Keeps the numpy arrays alive with the vx_poly array that points into them."""
+    keep = []
+    arr = (Poly * len(polys))()
+    for i, (exps, coefs) in enumerate(polys):
+        e = np.ascontiguousarray(np.asarray(exps, dtype=np.int32))
+        c = np.ascontiguousarray(np.asarray(coefs, dtype=np.float64))
+        if e.ndim != 2 or e.shape[0] != c.shape[0]:
+            raise ValueError("exps must be [nterms, nvars] and coefs [nterms]")
+        keep += [e, c]
+        arr[i] = Poly(e.shape[1], e.shape[0], e.ctypes.data, c.ctypes.data)
+    return arr, keep
+
+
+def _domain(domain) -> np.ndarray:
+    return np.ascontiguousarray(np.asarray(domain, dtype=np.float64).reshape(-1))
+
+
+def make_opts(mode=FP64, fp64_final=False, fp64_recheck=False, theta=0.5, timing=False) -> Opts:
+    o = Opts()
+    o.mode = int(mode)
+    o.fp64_final = int(bool(fp64_final))
+    o.fp64_recheck = int(bool(fp64_recheck))
+    o.theta = float(theta)
+    o.timing = int(bool(timing))
+    return o
+
+
+class System:
+    """Polynomials packed and resident on the device (vx_system)."""
+
+    def __init__(self, polys, stream=None):
+        arr, keep = _polys(polys)
+        h = ctypes.c_void_p()
+        _check(lib().vx_system_create(arr, len(polys), _stream(stream), ctypes.byref(h)))
+        self.handle = h
+        self.k = int(np.asarray(polys[0][0]).shape[1])
+        self.npoly = len(polys)
+
+    def info(self):
+        k = ctypes.c_int32()
+        n = ctypes.c_int32()
+        M = np.zeros((self.npoly, self.k + 1), dtype=np.int64)
+        _check(lib().vx_system_info(self.handle, ctypes.byref(k), ctypes.byref(n), _np_ptr(M)))
+        return int(k.value), int(n.value), M
+
+    def free(self):
+        if self.handle:
+            lib().vx_system_free(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass
+
+
+class Csf:
+    """A CSF of box indices of one grid level, on the device (vx_csf)."""
+
+    def __init__(self, handle, owner=None):
+        self.handle = handle
+        self._owner = owner  # a Result whose tree this borrows
+
+    def nodes(self):
+        k = ctypes.c_int32()
+        lv = ctypes.c_int32()
+        N = np.zeros(KMAX, dtype=np.int64)
+        _check(lib().vx_csf_nodes(self.handle, ctypes.byref(k), ctypes.byref(lv), _np_ptr(N)))
+        return int(k.value), int(lv.value), N[: k.value].copy()
+
+    def export(self, depth, stream=None):
+        import torch
+
+        k, _, N = self.nodes()
+        n = int(N[depth - 1])
+        lab = torch.empty(max(n, 1), dtype=torch.int32, device="cuda")
+        ptr = torch.empty(n + 1, dtype=torch.int32, device="cuda") if depth < k else None
+        _check(lib().vx_csf_export(self.handle, depth, _ptr(lab), _ptr(ptr), _stream(stream)))
+        return lab[:n], ptr
+
+    def tuples(self, stream=None):
+        import torch
+
+        k, _, N = self.nodes()
+        n = int(N[k - 1])
+        t = torch.empty((max(n, 1), k), dtype=torch.int32, device="cuda")
+        _check(lib().vx_csf_tuples(self.handle, _ptr(t), _stream(stream)))
+        return t[:n]
+
+    def free(self):
+        if self.handle and self._owner is None:
+            lib().vx_csf_free(self.handle)
+        self.handle = None
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass
+
+
+def csf_build(k, level, tuples, stream=None) -> Csf:
+    """CSF of lex-sorted unique int32 box indices ``tuples`` (CUDA tensor [n, k])."""
+    n = int(tuples.shape[0])
+    h = ctypes.c_void_p()
+    _check(lib().vx_csf_build(int(k), int(level), _ptr(tuples) if n else None, n,
+                              _stream(stream), ctypes.byref(h)))
+    return Csf(h)
+
+
+def csf_eval_level(system: System, csf: Csf, domain, mode=FP64, values=False, stream=None):
+    """Returns ``keep`` (uint8 [N_k]) and, with ``values``, ``lo``/``hi`` float64 [npoly, N_k]."""
+    import torch
+
+    _, _, N = csf.nodes()
+    n = int(N[-1])
+    keep = torch.empty(max(n, 1), dtype=torch.uint8, device="cuda")
+    lo = hi = None
+    if values:
+        lo = torch.empty((system.npoly, max(n, 1)), dtype=torch.float64, device="cuda")
+        hi = torch.empty_like(lo)
+    dom = _domain(domain)
+    _check(lib().vx_csf_eval_level(system.handle, csf.handle, _np_ptr(dom), int(mode), _ptr(lo),
+                                   _ptr(hi), _ptr(keep), _stream(stream)))
+    if values:
+        return keep[:n], lo[:, :n], hi[:, :n]
+    return keep[:n]
+
+
+def csf_subdivide(csf: Csf, keep, stream=None) -> Csf:
+    h = ctypes.c_void_p()
+    _check(lib().vx_csf_subdivide(csf.handle, _ptr(keep), _stream(stream), ctypes.byref(h)))
+    return Csf(h)
+
+
+def csf_compact(csf: Csf, keep, with_index=False, stream=None):
+    import torch
+
+    _, _, N = csf.nodes()
+    idx = torch.empty(max(int(N[-1]), 1), dtype=torch.int32, device="cuda") if with_index else None
+    h = ctypes.c_void_p()
+    _check(lib().vx_csf_compact(csf.handle, _ptr(keep), _ptr(idx), _stream(stream),
+                                ctypes.byref(h)))
+    out = Csf(h)
+    if with_index:
+        n = int(out.nodes()[2][-1])
+        return out, idx[:n]
+    return out
+
+
+class Result:
+    """Outcome of an enclosure (vx_result)."""
+
+    def __init__(self, handle, k, depth):
+        self.handle = handle
+        self.k = k
+        self.depth = depth
+
+    def boxes(self) -> np.ndarray:
+        n = ctypes.c_int64()
+        p = ctypes.c_void_p()
+        _check(lib().vx_result_boxes(self.handle, ctypes.byref(n), ctypes.byref(p)))
+        m = int(n.value)
+        if m == 0:
+            return np.zeros((0, self.k), dtype=np.int32)
+        buf = (ctypes.c_int32 * (m * self.k)).from_address(p.value)
+        return np.frombuffer(buf, dtype=np.int32).reshape(m, self.k).copy()
+
+    def csf(self) -> Csf:
+        h = ctypes.c_void_p()
+        _check(lib().vx_result_csf(self.handle, ctypes.byref(h)))
+        return Csf(h, owner=self)
+
+    def stats(self) -> dict:
+        L = self.depth + 1
+        nl = ctypes.c_int32()
+        tested = np.zeros(L, dtype=np.int64)
+        kept = np.zeros(L, dtype=np.int64)
+        nodes = np.zeros((L, self.k), dtype=np.int64)
+        recheck = np.zeros(L, dtype=np.int64)
+        madds = np.zeros(L, dtype=np.int64)
+        _check(lib().vx_result_stats(self.handle, ctypes.byref(nl), _np_ptr(tested),
+                                     _np_ptr(kept), _np_ptr(nodes), _np_ptr(recheck),
+                                     _np_ptr(madds)))
+        return {"tested": tested, "kept": kept, "nodes": nodes, "recheck": recheck,
+                "madds": madds}
+
+    def timing(self) -> dict:
+        nk = ctypes.c_int32()
+        ms = np.zeros(32, dtype=np.float64)
+        la = np.zeros(32, dtype=np.int64)
+        wk = np.zeros(32, dtype=np.int64)
+        _check(lib().vx_result_timing(self.handle, ctypes.byref(nk), _np_ptr(ms), _np_ptr(la),
+                                      _np_ptr(wk)))
+        out = {}
+        for i in range(nk.value):
+            name = lib().vx_kernel_kind_name(i).decode()
+            out[name] = {"ms": float(ms[i]), "launches": int(la[i]), "work": int(wk[i])}
+        return out
+
+    def elapsed_ms(self) -> float:
+        v = ctypes.c_double()
+        _check(lib().vx_result_elapsed_ms(self.handle, ctypes.byref(v)))
+        return float(v.value)
+
+    def free(self):
+        if self.handle:
+            lib().vx_result_free(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass
+
+
+def enclose_system(system: System, domain, depth, opts: Opts | None = None, stream=None) -> Result:
+    dom = _domain(domain)
+    h = ctypes.c_void_p()
+    _check(lib().vx_enclose_system(system.handle, _np_ptr(dom), int(depth),
+                                   ctypes.byref(opts) if opts is not None else None,
+                                   _stream(stream), ctypes.byref(h)))
+    return Result(h, system.k, int(depth))
+
+
+def enclose(polys, domain, depth, opts: Opts | None = None) -> Result:
+    """Algorithm 3 from host polynomials to host boxes (vx_enclose)."""
+    arr, keep = _polys(polys)
+    dom = _domain(domain)
+    h = ctypes.c_void_p()
+    _check(lib().vx_enclose(arr, len(polys), _np_ptr(dom), int(depth),
+                            ctypes.byref(opts) if opts is not None else None, ctypes.byref(h)))
+    k = int(np.asarray(polys[0][0]).shape[1])
+    return Result(h, k, int(depth))

@@ -1,0 +1,284 @@
+"""Parity of the CUDA path (through the C ABI) with the CPU oracle.
+
+Bar: the binary64 path is bit-identical to the oracle (endpoints compared by value, so that
+-0 == +0), CSF index arrays and kept sets are identical, and the binary32 midpoint-radius
+path encloses the binary64 enclosure box by box (so it keeps a superset), with a binary64
+last level giving exactly the binary64 set.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2406_09857_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def vx():
+    import torch
+
+    assert torch.cuda.is_available(), "GPU tests need a CUDA device"
+    from paper_2406_09857_gb300 import build
+    from paper_2406_09857_gb300 import vx as _vx
+
+    build.build()
+    _vx.lib()
+    return _vx
+
+
+def dev(a):
+    import torch
+
+    return torch.from_numpy(np.ascontiguousarray(a)).cuda()
+
+
+def host(t):
+    return t.cpu().numpy()
+
+
+# ---------------------------------------------------------------------------------------
+# CSF construction (Sec. 2.1) and Algorithm 3's split
+# ---------------------------------------------------------------------------------------
+@pytest.mark.parametrize("k,level,n,seed", [(1, 5, 20, 1), (2, 6, 700, 2), (3, 5, 5000, 3),
+                                            (4, 4, 9000, 4), (3, 9, 40000, 5), (2, 1, 3, 6)])
+def test_csf_build_matches_oracle(vx, k, level, n, seed):
+    t = synth.random_tuples(k, level, n, seed)
+    c = vx.csf_build(k, level, dev(t))
+    kk, lv, N = c.nodes()
+    N_ref, labs, ptrs = oracle.csf(t, k)
+    assert kk == k and lv == level and N.tolist() == N_ref.tolist()
+    for depth in range(1, k + 1):
+        lab, ptr = c.export(depth)
+        assert np.array_equal(host(lab), labs[depth - 1])
+        if depth < k:
+            assert np.array_equal(host(ptr), ptrs[depth - 1].astype(np.int32))
+    assert np.array_equal(host(c.tuples()), t)
+
+
+def test_csf_build_worked_example(vx):
+    import json
+    import os
+
+    with open(os.path.join(os.path.dirname(__file__), "golden", "csf_worked_example.json")) as f:
+        g = json.load(f)
+    c = vx.csf_build(2, 3, dev(np.asarray(g["support"], dtype=np.int32)))
+    assert c.nodes()[2].tolist() == g["N"]
+    lab1, ptr1 = c.export(1)
+    lab2, _ = c.export(2)
+    assert host(lab1).tolist() == g["labels_depth1"]
+    assert host(ptr1).tolist() == g["ptr_depth1"]
+    assert host(lab2).tolist() == g["labels_depth2"]
+
+
+def test_csf_build_rejects_bad_tuples(vx):
+    bad = [np.array([[1, 0], [0, 0]], dtype=np.int32),   # not increasing
+           np.array([[0, 0], [0, 0]], dtype=np.int32),   # duplicate
+           np.array([[0, 0], [0, 8]], dtype=np.int32)]   # outside [0, 2^3)
+    for t in bad:
+        with pytest.raises(vx.VxError) as e:
+            vx.csf_build(2, 3, dev(t))
+        assert e.value.code == vx.EINVAL
+    # the context is still fine afterwards
+    c = vx.csf_build(2, 3, dev(np.array([[0, 1]], dtype=np.int32)))
+    assert c.nodes()[2].tolist() == [1, 1]
+
+
+def test_csf_build_empty(vx):
+    import torch
+
+    c = vx.csf_build(3, 4, torch.empty((0, 3), dtype=torch.int32, device="cuda"))
+    assert c.nodes()[2].tolist() == [0, 0, 0]
+
+
+def _children(kept, k):
+    bits = np.array([[(b >> (k - 1 - c)) & 1 for c in range(k)] for b in range(1 << k)],
+                    dtype=np.int32)
+    ch = (2 * kept[:, None, :] + bits[None, :, :]).reshape(-1, k)
+    order = np.lexsort(ch.T[::-1])
+    return ch[order]
+
+
+@pytest.mark.parametrize("k,level,n,p,seed", [(1, 6, 30, 0.5, 1), (2, 6, 900, 0.3, 2),
+                                              (3, 5, 6000, 0.2, 3), (4, 3, 3000, 0.4, 4),
+                                              (3, 7, 50000, 0.05, 5), (2, 4, 100, 0.0, 6),
+                                              (2, 4, 100, 1.0, 7)])
+def test_subdivide_matches_definition(vx, k, level, n, p, seed):
+    t = synth.random_tuples(k, level, n, seed)
+    keep = (synth.Stream(seed + 50).unit(t.shape[0]) < p).astype(np.uint8)
+    c = vx.csf_build(k, level, dev(t))
+    nxt = vx.csf_subdivide(c, dev(keep))
+    kept = t[keep == 1]
+    want = _children(kept, k) if kept.shape[0] else np.zeros((0, k), dtype=np.int32)
+    _, lv, N = nxt.nodes()
+    assert lv == level + 1
+    assert np.array_equal(host(nxt.tuples()), want)
+    # N_j(next) = 2^j N_j(kept), and the tree equals the one built from scratch
+    Nk = oracle.csf(kept, k)[0] if kept.shape[0] else np.zeros(k, dtype=np.int64)
+    assert N.tolist() == [int(Nk[j]) << (j + 1) for j in range(k)]
+    if want.shape[0]:
+        N_ref, labs, ptrs = oracle.csf(want, k)
+        for depth in range(1, k + 1):
+            lab, ptr = nxt.export(depth)
+            assert np.array_equal(host(lab), labs[depth - 1])
+            if depth < k:
+                assert np.array_equal(host(ptr), ptrs[depth - 1].astype(np.int32))
+
+
+@pytest.mark.parametrize("k,level,n,p,seed", [(2, 6, 900, 0.3, 12), (3, 5, 6000, 0.5, 13),
+                                              (4, 3, 2000, 0.1, 14)])
+def test_compact_matches_definition(vx, k, level, n, p, seed):
+    t = synth.random_tuples(k, level, n, seed)
+    keep = (synth.Stream(seed).unit(t.shape[0]) < p).astype(np.uint8)
+    c = vx.csf_build(k, level, dev(t))
+    out, idx = vx.csf_compact(c, dev(keep), with_index=True)
+    assert np.array_equal(host(out.tuples()), t[keep == 1])
+    assert np.array_equal(host(idx), np.nonzero(keep)[0].astype(np.int32))
+
+
+# ---------------------------------------------------------------------------------------
+# Algorithm 2 with C0, binary64: bit-identical to the oracle
+# ---------------------------------------------------------------------------------------
+EVAL_CASES = [
+    # k, d, npoly, level, density, n, domain
+    (1, 12, 2, 7, 1.0, 100, None),
+    (2, 8, 1, 6, 1.0, 2000, None),
+    (2, 10, 2, 5, 0.4, 900, None),
+    (3, 6, 1, 4, 1.0, 3000, None),
+    (3, 7, 2, 5, 0.5, 8000, None),
+    (4, 4, 1, 3, 1.0, 3000, None),
+    (2, 6, 1, 0, 1.0, 1, None),                           # level 0: the box straddles 0
+    (2, 7, 2, 3, 1.0, 60, [-0.75, 1.25, -3.0, 1.0]),      # boxes straddling 0
+    (3, 5, 1, 4, 0.7, 2000, [0.0, 1.0, -2.0, 2.0, -0.5, 1.5]),
+]
+
+
+@pytest.mark.parametrize("k,d,npoly,level,density,n,domain", EVAL_CASES)
+def test_eval_level_fp64_bitexact(vx, k, d, npoly, level, density, n, domain):
+    polys = synth.random_small(k, d, npoly, 1000 + 10 * k + d, density=density)
+    dom = np.asarray(domain) if domain is not None else synth.cube(k)
+    t = synth.random_tuples(k, level, n, 77 + k)
+    sysv = vx.System(polys)
+    c = vx.csf_build(k, level, dev(t))
+    keep, lo, hi = vx.csf_eval_level(sysv, c, dom, vx.FP64, values=True)
+    lo_r, hi_r, keep_r, _ = oracle.eval_csf(polys, dom, level, t)
+    assert np.array_equal(host(lo), lo_r)
+    assert np.array_equal(host(hi), hi_r)
+    assert np.array_equal(host(keep), keep_r)
+
+
+def test_eval_level_kostlan_high_degree_bitexact(vx):
+    # a slice of the degree-100 curve system: 400 random boxes at level 7
+    s = synth.curve()
+    t = synth.random_tuples(3, 7, 400, 9)
+    sysv = vx.System(s.polys)
+    c = vx.csf_build(3, 7, dev(t))
+    keep, lo, hi = vx.csf_eval_level(sysv, c, s.domain, vx.FP64, values=True)
+    lo_r, hi_r, keep_r, _ = oracle.eval_csf(s.polys, s.domain, 7, t)
+    assert np.array_equal(host(lo), lo_r) and np.array_equal(host(hi), hi_r)
+    assert np.array_equal(host(keep), keep_r)
+
+
+def test_system_info_counts(vx):
+    import math
+
+    s = synth.curve(d=20)
+    k, npoly, M = vx.System(s.polys).info()
+    assert (k, npoly) == (3, 2)
+    assert M[0].tolist() == [math.comb(20 + 3 - j, 3 - j) for j in range(4)]
+
+
+def test_system_rejects_bad_polynomials(vx):
+    e = np.array([[0, 1], [0, 1]], dtype=np.int32)
+    with pytest.raises(vx.VxError):
+        vx.System([(e, np.array([1.0, 2.0]))])  # same monomial twice
+    with pytest.raises(vx.VxError):
+        vx.System([(np.array([[0, 1]], dtype=np.int32), np.array([np.inf]))])
+    with pytest.raises(vx.VxError):
+        vx.System([(np.array([[0, -1]], dtype=np.int32), np.array([1.0]))])
+
+
+def test_domain_must_be_dyadic(vx):
+    polys = synth.random_small(2, 3, 1, 5)
+    sysv = vx.System(polys)
+    c = vx.csf_build(2, 2, dev(np.array([[0, 0]], dtype=np.int32)))
+    with pytest.raises(vx.VxError) as e:
+        vx.csf_eval_level(sysv, c, [0.0, 0.1, 0.0, 1.0])
+    assert e.value.code == vx.EINVAL
+
+
+# ---------------------------------------------------------------------------------------
+# Algorithm 3
+# ---------------------------------------------------------------------------------------
+def _circle(k):
+    e = np.zeros((k + 1, k), dtype=np.int32)
+    for i in range(k):
+        e[i, i] = 2
+    return [(e, np.array([1.0] * k + [-0.5]))]
+
+
+ENCLOSE_CASES = {
+    "plain-k2-d20-depth8": lambda: (synth.plain().polys, synth.cube(2), 8),
+    "k1-d15-2polys": lambda: (synth.random_small(1, 15, 2, 31), synth.cube(1), 12),
+    "k2-d9-sparse": lambda: (synth.random_small(2, 9, 1, 32, density=0.5), synth.cube(2), 7),
+    "k3-d6-2polys": lambda: (synth.random_small(3, 6, 2, 33), synth.cube(3), 6),
+    "k4-d3": lambda: (synth.random_small(4, 3, 1, 34), synth.cube(4), 4),
+    "circle": lambda: (_circle(2), synth.cube(2), 9),
+    "sphere": lambda: (_circle(3), synth.cube(3), 6),
+    "no-zeros": lambda: ([(np.array([[2, 0], [0, 2], [0, 0]], dtype=np.int32),
+                           np.array([1.0, 1.0, 1.0]))], synth.cube(2), 6),
+    "asym-domain": lambda: (synth.random_small(2, 7, 1, 35), np.array([-0.5, 1.5, -2.0, 0.0]), 7),
+    "surface-d12": lambda: ([synth.kostlan_poly(3, 12, 36)], synth.cube(3), 6),
+}
+
+
+@pytest.mark.parametrize("name", sorted(ENCLOSE_CASES))
+def test_enclose_fp64_equals_oracle(vx, name):
+    polys, dom, depth = ENCLOSE_CASES[name]()
+    ref = oracle.enclose(polys, dom, depth)
+    res = vx.enclose(polys, dom, depth)
+    st = res.stats()
+    assert np.array_equal(res.boxes(), ref["tuples"])
+    assert np.array_equal(st["tested"], ref["tested"])
+    assert np.array_equal(st["kept"], ref["kept"])
+    assert np.array_equal(st["nodes"], ref["nodes"])
+    assert np.array_equal(st["madds"], ref["work"])
+
+
+@pytest.mark.parametrize("name", ["plain-k2-d20-depth8", "k3-d6-2polys", "surface-d12",
+                                  "asym-domain", "k4-d3"])
+def test_enclose_fp32_midrad(vx, name):
+    polys, dom, depth = ENCLOSE_CASES[name]()
+    ref = oracle.enclose(polys, dom, depth)
+    # binary32 below the last level, binary64 last level: exactly the binary64 set
+    r1 = vx.enclose(polys, dom, depth, vx.make_opts(vx.FP32_MIDRAD, fp64_final=True))
+    assert np.array_equal(r1.boxes(), ref["tuples"])
+    # binary32 throughout: a superset at every level
+    r2 = vx.enclose(polys, dom, depth, vx.make_opts(vx.FP32_MIDRAD))
+    s2 = r2.stats()
+    assert np.all(s2["kept"] >= ref["kept"])
+    b2 = {tuple(r) for r in r2.boxes().tolist()}
+    assert {tuple(r) for r in ref["tuples"].tolist()} <= b2
+    # with binary64 rechecks of tight boxes: still a superset, never more than without
+    r3 = vx.enclose(polys, dom, depth, vx.make_opts(vx.FP32_MIDRAD, fp64_recheck=True))
+    s3 = r3.stats()
+    b3 = {tuple(r) for r in r3.boxes().tolist()}
+    assert {tuple(r) for r in ref["tuples"].tolist()} <= b3 <= b2
+    assert np.all(s3["kept"] >= ref["kept"])
+
+
+@pytest.mark.parametrize("k,d,level,seed", [(2, 20, 6, 1), (3, 8, 4, 2), (3, 30, 6, 3)])
+def test_fp32_box_enclosure_contains_fp64(vx, k, d, level, seed):
+    polys = [synth.kostlan_poly(k, d, seed)]
+    t = synth.random_tuples(k, level, 3000, seed)
+    sysv = vx.System(polys)
+    c = vx.csf_build(k, level, dev(t))
+    k64, lo64, hi64 = vx.csf_eval_level(sysv, c, synth.cube(k), vx.FP64, values=True)
+    k32, lo32, hi32 = vx.csf_eval_level(sysv, c, synth.cube(k), vx.FP32_MIDRAD, values=True)
+    lo64, hi64, lo32, hi32 = map(host, (lo64, hi64, lo32, hi32))
+    assert np.all(lo32 <= lo64) and np.all(hi32 >= hi64)
+    assert np.all(host(k32) >= host(k64))
+    # and the binary32 radius is not wildly inflated
+    w64 = hi64 - lo64
+    w32 = hi32 - lo32
+    assert np.median(w32 / np.maximum(w64, 1e-300)) < 1.5

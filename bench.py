@@ -1,0 +1,412 @@
+"""Benchmark: box-evaluations per second of the CSF subdivision hot path on one GB300.
+
+A step is one whole enclosure (Algorithm 3, levels 0..depth: CSF level evaluation with C0,
+compaction, 2^k split and rebuild) of the workload
+
+    two trivariate Kostlan polynomials of total degree 100 (a curve), domain [-1,1]^3,
+    depth 10 (finest grid 1024^3)
+
+with the polynomials already resident in device memory.  The headline path is binary32
+interval arithmetic with binary64-certified decisions (mode VX_FP32: every level's kept set
+equals the binary64 one); the plain binary64 path is timed beside it.
+box-evals/s = (sum over levels of the boxes tested) / time.
+
+  python bench.py [--gpus N --steps K --warmup W] [--impl reference]
+
+For N > 1 (torchrun, one rank per GPU) each rank encloses its own x_1-slab of the domain
+(no data exchange; paper_2406_09857_gb300/shard.py) and the value is the boxes evaluated by
+all ranks over the slowest rank's time.  ``--impl reference`` times the CPU oracle on a
+bounded sample of the same workload instead.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "box-evals/s & enclosure wall time: FP32-midrad+batched vs FP64 on 1 GB300"
+UNIT = "box-evals/s"
+WORKLOAD = ("curve: 2 trivariate Kostlan polynomials of total degree 100 on [-1,1]^3, "
+            "subdivision depth 10 (1024^3 finest grid)")
+
+# Roofline denominators of the plain-ALU evaluation kernels, from unit counts and the maximum
+# SM clock (152 SMs x 2070 MHz): 128 binary32 FMA lanes and 2 binary64 lanes per SM per clock.
+SMS, SM_MHZ = 152, 2070.0
+FP32_PEAK_T = SMS * 128 * SM_MHZ * 1e6 / 1e12  # 40.3 T instructions/s
+FP64_PEAK_T = SMS * 2 * SM_MHZ * 1e6 / 1e12    # 0.63 T instructions/s
+# FMA-pipe instructions of one interval multiply-add: binary32 certified = 2 directed FMAs for
+# the endpoints + 3 for the error bound; binary64 = 2 directed multiplies + 2 directed adds.
+OPS_PER_MADD = {"fp32": 5, "fp64": 4}
+L2_FLUSH_BYTES = 512 << 20  # > 129 MB of L2
+
+
+def log(*a):
+    print(*a, file=sys.stderr, flush=True)
+
+
+class ClockSampler:
+    """nvidia-smi SM clocks and throttle reasons, sampled every 200 ms while active."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+    NAMES = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def __enter__(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), "--query-gpu=" + self.FIELDS,
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+            time.sleep(0.4)
+        except OSError:
+            self.proc = None
+        return self
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            time.sleep(0.25)
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        sm, smax, power, reasons = [], [], [], set()
+        for line in open(self.path):
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax.append(float(f[2]))
+                power.append(float(f[3]))
+            except ValueError:
+                continue
+            for n, v in zip(self.NAMES, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        os.unlink(self.path)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax), "samples": len(sm),
+                "power_w_max": max(power), "reasons": sorted(reasons)}
+
+
+def oracle_lineage(polys, domain, depth: int, x1: int) -> int:
+    """The CPU oracle's Algorithm 3 on the lineage of finest x_1-slab ``x1``: at level l only
+    the boxes whose x_1 index is x1's ancestor (x1 >> (depth - l)) are evaluated and
+    subdivided.  These are exactly the boxes the full run evaluates in that lineage (each box
+    is decided on its own), so the sample keeps the run's mix of levels and the sharing of
+    partial evaluations along the CSF.  Returns the number of box evaluations."""
+    import oracle
+
+    k = len(domain) // 2
+    S = np.zeros((1, k - 1), dtype=np.int32)  # indices along x_2..x_k
+    bits = np.array([[(b >> (k - 2 - c)) & 1 for c in range(k - 1)] for b in range(1 << (k - 1))],
+                    dtype=np.int32)
+    evals = 0
+    for l in range(depth + 1):
+        full = np.empty((S.shape[0], k), dtype=np.int32)
+        full[:, 0] = x1 >> (depth - l)
+        full[:, 1:] = S
+        _, _, keep, _ = oracle.eval_csf(polys, domain, l, full)
+        evals += full.shape[0]
+        S = S[keep == 1]
+        if l == depth or S.shape[0] == 0:
+            break
+        S = (2 * S[:, None, :] + bits[None, :, :]).reshape(-1, k - 1)
+        S = S[np.lexsort(S.T[::-1])]
+    return evals
+
+
+def oracle_sample(polys, domain, depth, budget_s: float, seed: int, min_lineages: int = 1):
+    """Times oracle_lineage on random finest slabs until ``budget_s`` seconds have passed."""
+    from paper_2406_09857_gb300 import synth
+
+    st = synth.Stream(seed)
+    side = 1 << depth
+    boxes, secs, n = 0, 0.0, 0
+    while (secs < budget_s or n < min_lineages) and n < 256:
+        x1 = int(st.uniform_int(0, side - 1, 1)[0])
+        t0 = time.perf_counter()
+        boxes += oracle_lineage(polys, domain, depth, x1)
+        secs += time.perf_counter() - t0
+        n += 1
+    desc = ("CPU oracle (plain C, binary64 directed rounding, 1 thread): Algorithm 3 along the "
+            "lineage of %d random finest x1-slabs (every level's boxes of each slab), %d box "
+            "evaluations in %.1f s" % (n, boxes, secs))
+    return boxes / secs, boxes, secs, desc
+
+
+def config_dict(world: int, mode: str):
+    return {"workload": WORKLOAD, "k": 3, "npoly": 2, "degree": 100, "depth": 10,
+            "domain": "[-1,1]^3", "coefficients": "Kostlan: N(0,1) * sqrt(multinomial)",
+            "mode": mode,
+            "l2": "512 MB written between steps, outside the per-step CUDA events",
+            "parallelism": ("x1-slab shards, one enclosure per rank" if world > 1 else
+                            "single GPU")}
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    if rank != 0:
+        return 0
+    import oracle
+    from paper_2406_09857_gb300 import synth
+
+    oracle.build()
+    s = synth.curve()
+    rates, times = [], []
+    total_boxes, total_s = 0, 0.0
+    for i in range(args.warmup + args.steps):
+        v, b, t, desc = oracle_sample(s.polys, s.domain, s.depth, budget_s=0.0, seed=1000 + i)
+        if i >= args.warmup:
+            rates.append(v)
+            times.append(t)
+            total_boxes += b
+            total_s += t
+    value = total_boxes / total_s
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT,
+            "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1e3 * total_s / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": config_dict(1, "CPU oracle, binary64 directed rounding"),
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                             "sample": "each step: " + desc.split(": ", 1)[1].split(",")[0]
+                             + " (one random finest x1-slab lineage per step)"},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_gpu(args):
+    import torch
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    else:
+        torch.cuda.set_device(0)
+
+    def barrier():
+        if world > 1:
+            torch.distributed.barrier()
+
+    def reduce(x, op):
+        if world == 1:
+            return x
+        t = torch.tensor([float(x)], dtype=torch.float64, device="cuda")
+        torch.distributed.all_reduce(t, op=op)
+        return float(t.item())
+
+    from paper_2406_09857_gb300 import build, shard, synth, vx
+
+    if rank == 0:
+        build.build()
+    barrier()
+    vx.lib()
+    s = synth.curve()
+    dom, depth, x1_offset = shard.rank_problem(s.domain, s.depth, rank, world)
+    sysv = vx.System(s.polys)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
+    stream = torch.cuda.current_stream()
+
+    def run_steps(mode, nsteps, timing):
+        """nsteps enclosures; returns per-step ms, total box-evals, results' stats/timing."""
+        ms, evals, tims, last = [], 0, [], None
+        for i in range(nsteps):
+            flush.fill_(float(i))
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            r = vx.enclose_system(sysv, dom, depth, vx.make_opts(mode, timing=timing), stream)
+            e1.record(stream)
+            e1.synchronize()
+            ms.append(e0.elapsed_time(e1))
+            st = r.stats()
+            evals += int(st["tested"].sum())
+            if timing:
+                tims.append(r.timing())
+            if last is not None:
+                last.free()
+            last = r
+        return ms, evals, tims, last
+
+    def result_digest(r):
+        t = r.csf().tuples()
+        if t.shape[0] == 0:
+            return 0, 0
+        t = t.long()
+        h = ((t[:, 0] * 1048583 + t[:, 1]) * 1048589 + t[:, 2]) % 2305843009213693951
+        return int(t.shape[0]), int(h.sum().item())
+
+    # ---- headline: binary32 certified, K timed steps -------------------------------------
+    log("[bench] warmup %d x fp32" % args.warmup)
+    run_steps(vx.FP32, args.warmup, False)[3].free()
+    barrier()
+    torch.cuda.synchronize()
+    launches0 = vx.kernel_launches()
+    with ClockSampler(local) as clk:
+        w0 = time.perf_counter()
+        ms32, evals32, tims32, r32 = run_steps(vx.FP32, args.steps, True)
+        torch.cuda.synchronize()
+        barrier()
+        wall32 = time.perf_counter() - w0
+    launches = vx.kernel_launches() - launches0
+    clocks = clk.summary()
+    st32 = r32.stats()
+    t32 = reduce(sum(ms32), torch.distributed.ReduceOp.MAX if world > 1 else None)
+    ev32 = reduce(evals32, torch.distributed.ReduceOp.SUM if world > 1 else None)
+    value = ev32 / (t32 * 1e-3)
+    digest32 = result_digest(r32)
+
+    # ---- binary64 beside it ------------------------------------------------------------------
+    n64 = max(1, min(args.steps, 2))
+    log("[bench] fp64: 1 warmup + %d timed" % n64)
+    run_steps(vx.FP64, 1, False)[3].free()
+    ms64, evals64, tims64, r64 = run_steps(vx.FP64, n64, True)
+    t64 = reduce(sum(ms64), torch.distributed.ReduceOp.MAX if world > 1 else None)
+    ev64 = reduce(evals64, torch.distributed.ReduceOp.SUM if world > 1 else None)
+    value64 = ev64 / (t64 * 1e-3)
+    digest64 = result_digest(r64)
+    same = digest32 == digest64 and np.array_equal(st32["kept"], r64.stats()["kept"])
+
+    def roofline(tims, arith, peak_t):
+        tot = {}
+        for tm in tims:
+            for name, v in tm.items():
+                a = tot.setdefault(name, {"ms": 0.0, "launches": 0, "work": 0})
+                a["ms"] += v["ms"]
+                a["launches"] += v["launches"]
+                a["work"] += v["work"]
+        evalk = {n: v for n, v in tot.items() if v["launches"] and n.startswith(("stage", "leaf"))}
+        top = max(evalk, key=lambda n: evalk[n]["ms"])
+        v = evalk[top]
+        per_launch_ms = v["ms"] / v["launches"]
+        ops_per_launch = v["work"] / v["launches"] * OPS_PER_MADD[arith]
+        achieved = ops_per_launch / (per_launch_ms * 1e-3) / 1e12
+        share = {n: round(x["ms"] / sum(y["ms"] for y in tot.values()), 4) for n, x in tot.items()
+                 if x["launches"]}
+        return {"kernel": top, "bound": "alu", "achieved": achieved, "peak": peak_t,
+                "unit": "T instr/s (FMA pipe)", "frac": achieved / peak_t, "traffic": None,
+                "launches": v["launches"], "avg_launch_ms": per_launch_ms,
+                "madds_per_launch": v["work"] / v["launches"], "time_share": share}
+
+    roof32 = roofline(tims32, "fp32", FP32_PEAK_T)
+    roof64 = roofline(tims64, "fp64", FP64_PEAK_T)
+
+    # ---- end to end through the host API -----------------------------------------------------
+    log("[bench] e2e")
+    h2d = sysv.device_bytes()
+    polys_host = s.polys
+    vx.enclose(polys_host, dom, depth, vx.make_opts(vx.FP32)).free()
+    ne2e = max(1, min(args.steps, 2))
+    torch.cuda.synchronize()
+    barrier()
+    w0 = time.perf_counter()
+    e2e_evals, d2h = 0, 0
+    for _ in range(ne2e):
+        r = vx.enclose(polys_host, dom, depth, vx.make_opts(vx.FP32))
+        b = r.boxes()  # device -> host copy of the result
+        e2e_evals += int(r.stats()["tested"].sum())
+        d2h += b.nbytes
+        r.free()
+    torch.cuda.synchronize()
+    e2e_s = reduce(time.perf_counter() - w0, torch.distributed.ReduceOp.MAX if world > 1 else None)
+    e2e_evals = reduce(e2e_evals, torch.distributed.ReduceOp.SUM if world > 1 else None)
+    e2e = {"value": e2e_evals / e2e_s, "unit": UNIT, "h2d_bytes_per_step": h2d,
+           "d2h_bytes_per_step": d2h // ne2e,
+           "what": "vx_enclose from host polynomials (pack + upload) to host boxes"}
+
+    # ---- CPU oracle on a bounded sample ------------------------------------------------------
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu:
+        log("[bench] cpu baseline (%.0f s budget)" % args.cpu_budget)
+        import oracle
+
+        oracle.build()
+        v, b, t, desc = oracle_sample(s.polys, s.domain, s.depth, args.cpu_budget, seed=7)
+        cpu = {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": desc}
+
+    if rank == 0:
+        peaks = {}
+        try:
+            with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+                peaks = json.load(f)
+        except OSError:
+            pass
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": t32 / args.steps, "higher_is_better": True,
+            "scaling": "strong" if world > 1 else "weak", "vs_baseline": None,
+            "dtype": "f32 (f64 on the error band)", "data": "synthetic",
+            "config": config_dict(world, "binary32 intervals, binary64-certified decisions"),
+            "boxes_final": int(st32["kept"][-1]), "box_evals_per_step": evals32 // args.steps,
+            "wall_s_timed_region": wall32,
+            "fp64": {"value": value64, "ms_per_step": t64 / n64, "steps": n64,
+                     "roofline": roof64},
+            "speedup_vs_fp64": value / value64,
+            "same_result_as_fp64": bool(same),
+            "excess_boxes": 0.0 if same else None,
+            "recheck_boxes_per_step": int(st32["recheck"].sum()),
+            "roofline": roof32,
+            "cpu_baseline": cpu,
+            "e2e": e2e,
+            "gpu_launches": launches,
+            "gpu_launches_per_step": launches / args.steps,
+            "clocks": clocks,
+            "peaks_file": {k: peaks.get(k) for k in ("hbm_gbs", "bf16_tflops")} if peaks else None,
+        }
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        torch.distributed.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser(description=__doc__.split("\n\n")[0])
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["vx", "reference"], default="vx")
+    ap.add_argument("--cpu-budget", type=float, default=20.0,
+                    help="seconds of CPU oracle work for the cpu_baseline sample")
+    ap.add_argument("--no-cpu", action="store_true", help="skip the cpu_baseline sample")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_gpu(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -51,6 +51,11 @@ extern "C" {
 #define VX_FP32_MIDRAD 1 /* binary32 midpoint-radius <m, r> with the rounding error of every
                           * step bounded a priori and added to r, so the enclosure contains
                           * the exact range (and the VX_FP64 enclosure) */
+#define VX_FP32 2        /* binary32 intervals [RD, RU] carrying an a-priori bound on their
+                          * distance to the VX_FP64 endpoints: a box whose binary32 value is
+                          * farther than that bound from deciding C0 either way is decided in
+                          * binary32, the others are re-evaluated in VX_FP64, so every keep
+                          * decision equals the VX_FP64 one */
 
 /* One polynomial: nterms monomials coefs[t] * prod_i x_i^exps[t*nvars+i] (Sec. 2.1,
  * "Representing a Multivariate Polynomial").  Host memory, borrowed for the duration of the
@@ -68,9 +73,11 @@ typedef struct vx_result vx_result; /* the outcome of an enclosure */
 
 /* Options of vx_enclose*: zero-initialise, then set what you need (all-zero = VX_FP64). */
 typedef struct {
-  int32_t mode;         /* VX_FP64 or VX_FP32_MIDRAD for the levels below the last */
+  int32_t mode;         /* VX_FP64, VX_FP32 or VX_FP32_MIDRAD (for the levels below the last
+                         * when fp64_final is set) */
   int32_t fp64_final;   /* VX_FP32_MIDRAD only: evaluate the last level in VX_FP64, which makes
-                         * the result exactly the VX_FP64 result */
+                         * the result exactly the VX_FP64 result (VX_FP32 needs no such step:
+                         * its every level is the VX_FP64 level) */
   int32_t fp64_recheck; /* VX_FP32_MIDRAD only: boxes kept by the FP32 test with |m| >= theta*r
                          * for some polynomial are re-evaluated in VX_FP64 at the same level */
   float theta;          /* recheck threshold, 0 < theta <= 1 (0 means 0.5) */
@@ -92,6 +99,11 @@ void vx_system_free(vx_system *sys);
  * the highest exponent of a fibre counted as zero coefficients (M_k = 1). */
 int vx_system_info(const vx_system *sys, int32_t *k, int32_t *npoly, int64_t *h_M);
 
+/* Bytes of device memory the packed system holds (what vx_system_create uploads). */
+int vx_system_device_bytes(const vx_system *sys, int64_t *bytes);
+/* Number of kernels this library has launched in this process so far (all threads). */
+int64_t vx_kernel_launches(void);
+
 /* The CSF (Sec. 2.1) of n box indices d_tuples[n][k] (device, int32, lexicographically
  * strictly increasing, each coordinate in [0, 2^level)) of grid level `level`.  Depth-j nodes
  * are the distinct length-j prefixes (Remark 1: there are N_j(S) of them).  VX_EINVAL if the
@@ -111,9 +123,13 @@ int vx_csf_tuples(const vx_csf *csf, int32_t *d_tuples, void *stream);
 
 /* Algorithm 2 on every leaf box of `csf` with the C0 test of Sec. 3.2.
  * h_domain[2k]: lo_i, hi_i per axis (host).  mode: VX_FP64 or VX_FP32_MIDRAD.
- * d_keep[N_k] (required): 1 if 0 lies in the interval value of every polynomial, else 0.
+ * d_keep[N_k] (required): 1 if 0 lies in the interval value of every polynomial, else 0
+ * (VX_FP32: the VX_FP64 decision, boxes inside the error band being re-evaluated in binary64).
  * d_lo, d_hi [npoly][N_k] (both NULL or both set): the enclosure of each polynomial on each
- * box (VX_FP32_MIDRAD: m - r rounded down and m + r rounded up, in binary64).
+ * box (VX_FP32_MIDRAD: m - r rounded down and m + r rounded up, in binary64; VX_FP32: the
+ * binary32 bounds).
+ * Returns once the evaluation is complete (it synchronises `stream`); VX_ETIMEOUT if a bounded
+ * wait inside a kernel gave up (the outputs are then not valid).
  * In VX_FP64 mode every endpoint equals the CPU statement of Algorithms 1-2 with outward
  * rounding (RD of each product and sum for lower ends, RU for upper ends, the product of
  * intervals as the hull of the endpoint products). */
@@ -152,7 +168,8 @@ int vx_result_csf(const vx_result *res, const vx_csf **csf);
 /* Per-level statistics, levels 0..depth: h_tested[l] = |S_l| boxes evaluated, h_kept[l]
  * survivors, h_nodes[l*k + j-1] = N_j(S_l), h_recheck[l] = boxes re-evaluated in VX_FP64
  * (VX_FP32_MIDRAD with fp64_recheck), h_madds[l] = interval multiply-adds of the level
- * (Theorem 1's count: sum over polynomials and depths j of N_j (M_{j-1} - M_j)).
+ * (Theorem 1's count: sum over polynomials and depths j of N_j (M_{j-1} - M_j)), plus those of
+ * the binary64 re-evaluations.
  * Any pointer may be NULL; *nlevels = depth + 1. */
 int vx_result_stats(const vx_result *res, int32_t *nlevels, int64_t *h_tested, int64_t *h_kept,
                     int64_t *h_nodes, int64_t *h_recheck, int64_t *h_madds);

@@ -9,6 +9,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
@@ -35,6 +36,9 @@ void set_error(const char *fmt, ...) {
 }
 
 void clear_error() { g_err[0] = '\0'; }
+
+static std::atomic<int64_t> g_launches{0};
+void note_launch(int n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
 
 // ---------------------------------------------------------------------------------------
 // device memory: stream-ordered allocations from the device's default pool, which keeps
@@ -124,8 +128,9 @@ void Timer::release() {
 }
 
 static const char *kKindNames[KK_COUNT] = {
-    "stage0_fp64", "stagej_fp64", "leaf_fp64", "stage0_fp32", "stagej_fp32", "leaf_fp32",
-    "csf_build",   "prune_scan",  "split",     "compact",     "recheck_select"};
+    "stage0_fp64",  "stagej_fp64",  "leaf_fp64", "stage0_midrad", "stagej_midrad",
+    "leaf_midrad",  "stage0_fp32",  "stagej_fp32", "leaf_fp32",   "csf_build",
+    "prune_scan",   "split",        "compact",     "recheck_select"};
 
 // ---------------------------------------------------------------------------------------
 // grid levels: box t on axis i is [lo + t w, lo + (t+1) w], w = (hi - lo) / 2^level.
@@ -222,6 +227,7 @@ struct HostPoly {
   HostStage st[VX_KMAX];
   std::vector<double2> c64;
   std::vector<float2> c32;
+  std::vector<float4> c32c;
 };
 
 static uint64_t suffix_key(const int32_t *e, int from, int k) {
@@ -244,6 +250,25 @@ static float2 to_midrad(double c) {
   const double d = std::fabs(c - (double)m);  // exact (Sterbenz)
   const float r = f32_round_up(d + std::ldexp(1.0, -149));
   return make_float2(m, r);
+}
+
+static float f32_round_down(double x) {
+  float f = (float)x;
+  if ((double)f > x) f = std::nextafter(f, -INFINITY);
+  return f;
+}
+
+// (RD(c), -RU(c)) in binary32 and a bound E >= (1 + 2^-40)(max(c - RD(c), RU(c) - c) +
+// 2^-23 |c|) + 2^-148 on the distance to the binary64 coefficient (which the binary64 path
+// uses as it is); the 2^-23 |c| keeps E >= 2^-23 max(|RD(c)|, |RU(c)|), which the error
+// recursion of the evaluation kernels relies on.
+static float4 to_certified(double c) {
+  const float lo = f32_round_down(c), hi = f32_round_up(c);
+  if (!std::isfinite(lo) || !std::isfinite(hi)) return make_float4(-INFINITY, -INFINITY, INFINITY, 0.f);
+  const double d = std::max(c - (double)lo, (double)hi - c);  // exact
+  const double bound = (d + std::ldexp(std::fabs(c), -23)) * (1.0 + std::ldexp(1.0, -39));
+  const float e = f32_round_up(bound + std::ldexp(1.0, -148));
+  return make_float4(lo, -hi, e, 0.f);
 }
 
 static int pack_poly(int k, const vx_poly &p, HostPoly *hp) {
@@ -359,8 +384,59 @@ static int pack_poly(int k, const vx_poly &p, HostPoly *hp) {
     hp->c64[pos] = make_double2(p.coefs[t], p.coefs[t]);
   }
   hp->c32.resize(S0.blk_in);
-  for (int64_t i = 0; i < S0.blk_in; ++i) hp->c32[i] = to_midrad(hp->c64[i].x);
+  hp->c32c.resize(S0.blk_in);
+  for (int64_t i = 0; i < S0.blk_in; ++i) {
+    hp->c32[i] = to_midrad(hp->c64[i].x);
+    hp->c32c[i] = to_certified(hp->c64[i].x);
+  }
   return VX_OK;
+}
+
+}  // namespace vx
+
+namespace vx {
+
+// One level in one mode.  The binary32 modes flag boxes for a binary64 re-evaluation (VX_FP32:
+// those inside the error band; VX_FP32_MIDRAD with recheck: the tight ones); flagged boxes are
+// gathered into a tree of their own, evaluated in binary64 and their decisions scattered back.
+static int eval_decide(const SysDev &sys, const CsfView &c, const LevelGrid &g, int mode,
+                       bool midrad_recheck, float theta, double *d_lo, double *d_hi,
+                       uint8_t *keep, cudaStream_t s, Timer *tm, int64_t *madds,
+                       int64_t *nrecheck) {
+  const int k = c.k;
+  const int64_t n = c.N[k - 1];
+  *madds = 0;
+  *nrecheck = 0;
+  const bool flagged = mode == VX_FP32 || (mode == VX_FP32_MIDRAD && midrad_recheck);
+  const int arith = mode == VX_FP64 ? ARITH_F64 : (mode == VX_FP32 ? ARITH_F32_CERT : ARITH_F32_MIDRAD);
+  uint8_t *flag = nullptr;
+  if (flagged) VX_CHECK(dmalloc((void **)&flag, (size_t)std::max<int64_t>(n, 1), s));
+  int rc = eval_level_raw(sys, c, g, arith, d_lo, d_hi, keep, flag, theta, s, tm, madds);
+  if (rc == VX_OK && flagged && n > 0) {
+    CsfObj sub;
+    int32_t *idx = nullptr;
+    uint8_t *subkeep = nullptr;
+    rc = dmalloc((void **)&idx, (size_t)n * 4, s);
+    if (rc == VX_OK) rc = csf_prune(c, flag, 0, idx, s, &sub, tm);
+    if (rc == VX_OK) {
+      const int64_t ns = sub.v.N[k - 1];
+      *nrecheck = ns;
+      if (ns > 0) {
+        rc = dmalloc((void **)&subkeep, (size_t)ns, s);
+        int64_t w2 = 0;
+        if (rc == VX_OK)
+          rc = eval_level_raw(sys, sub.v, g, ARITH_F64, nullptr, nullptr, subkeep, nullptr, 0.f,
+                              s, tm, &w2);
+        *madds += w2;
+        if (rc == VX_OK) rc = scatter_keep(idx, subkeep, ns, keep, s);
+      }
+      csf_release(&sub);
+    }
+    dfree(subkeep, s);
+    dfree(idx, s);
+  }
+  dfree(flag, s);
+  return rc;
 }
 
 }  // namespace vx
@@ -370,6 +446,7 @@ using namespace vx;
 struct vx_system {
   SysDev dev;
   void *mem = nullptr;
+  size_t bytes = 0;
   cudaStream_t stream = nullptr;
   std::vector<int64_t> M;  // [npoly][k+1]
 };
@@ -416,7 +493,8 @@ int vx_system_create(const vx_poly *F, int32_t npoly, void *stream, vx_system **
   auto al = [](size_t x) { return (x + 255) & ~(size_t)255; };
   size_t bytes = 0;
   for (int f = 0; f < npoly; ++f) {
-    bytes += al(hp[f].c64.size() * sizeof(double2)) + al(hp[f].c32.size() * sizeof(float2));
+    bytes += al(hp[f].c64.size() * sizeof(double2)) + al(hp[f].c32.size() * sizeof(float2)) +
+             al(hp[f].c32c.size() * sizeof(float4));
     for (int s = 0; s < k; ++s) {
       const HostStage &S = hp[f].st[s];
       bytes += al((S.maxlen + 1) * 4) + 2 * al((size_t)S.nfib * 4);
@@ -435,6 +513,7 @@ int vx_system_create(const vx_poly *F, int32_t npoly, void *stream, vx_system **
     return rc;
   }
   sys->stream = s;
+  sys->bytes = bytes;
   sys->dev.k = k;
   sys->dev.npoly = npoly;
   sys->M.assign((size_t)npoly * (k + 1), 1);
@@ -450,6 +529,7 @@ int vx_system_create(const vx_poly *F, int32_t npoly, void *stream, vx_system **
     PolyDev &P = sys->dev.p[f];
     P.c64 = (const double2 *)put(hp[f].c64.data(), hp[f].c64.size() * sizeof(double2));
     P.c32 = (const float2 *)put(hp[f].c32.data(), hp[f].c32.size() * sizeof(float2));
+    P.c32c = (const float4 *)put(hp[f].c32c.data(), hp[f].c32c.size() * sizeof(float4));
     for (int s2 = 0; s2 < k; ++s2) {
       const HostStage &S = hp[f].st[s2];
       StageDev &D = P.st[s2];
@@ -492,6 +572,18 @@ int vx_system_info(const vx_system *sys, int32_t *k, int32_t *npoly, int64_t *h_
   if (h_M) std::memcpy(h_M, sys->M.data(), sys->M.size() * sizeof(int64_t));
   return VX_OK;
 }
+
+int vx_system_device_bytes(const vx_system *sys, int64_t *bytes) {
+  clear_error();
+  if (!sys || !bytes) {
+    set_error("vx_system_device_bytes: NULL argument");
+    return VX_EINVAL;
+  }
+  *bytes = (int64_t)sys->bytes;
+  return VX_OK;
+}
+
+int64_t vx_kernel_launches(void) { return g_launches.load(std::memory_order_relaxed); }
 
 int vx_csf_build(int32_t k, int32_t level, const int32_t *d_tuples, int64_t n, void *stream,
                  vx_csf **out) {
@@ -562,7 +654,7 @@ int vx_csf_tuples(const vx_csf *c, int32_t *d_tuples, void *stream) {
 int vx_csf_eval_level(const vx_system *sys, const vx_csf *c, const double *h_domain,
                       int32_t mode, double *d_lo, double *d_hi, uint8_t *d_keep, void *stream) {
   clear_error();
-  if (!sys || !c || !d_keep || (mode != VX_FP64 && mode != VX_FP32_MIDRAD) ||
+  if (!sys || !c || !d_keep || (mode != VX_FP64 && mode != VX_FP32_MIDRAD && mode != VX_FP32) ||
       (!d_lo) != (!d_hi) || c->o.v.k != sys->dev.k) {
     set_error("vx_csf_eval_level: bad arguments");
     return VX_EINVAL;
@@ -571,8 +663,17 @@ int vx_csf_eval_level(const vx_system *sys, const vx_csf *c, const double *h_dom
   if (api_trace()) std::fprintf(stderr, "[vx] eval_level entry\n");
   VX_CHECK(make_grid(c->o.v.k, h_domain, c->o.v.level, &g));
   if (api_trace()) std::fprintf(stderr, "[vx] grid ok\n");
-  return eval_level(sys->dev, c->o.v, g, mode, d_lo, d_hi, d_keep, as_stream(stream), nullptr,
-                    nullptr);
+  int64_t w = 0, nr = 0;
+  cudaStream_t s = as_stream(stream);
+  VX_CHECK(eval_decide(sys->dev, c->o.v, g, mode, false, 0.5f, d_lo, d_hi, d_keep, s, nullptr, &w,
+                       &nr));
+  int st = 0;
+  VX_CHECK(take_device_status(s, &st));
+  if (st) {
+    set_error("vx_csf_eval_level: a bounded device wait gave up; outputs are not valid");
+    return VX_ETIMEOUT;
+  }
+  return VX_OK;
 }
 
 int vx_csf_subdivide(const vx_csf *in, const uint8_t *d_keep, void *stream, vx_csf **out) {
@@ -636,7 +737,7 @@ static int enclose_impl(const vx_system *sys, const double *dom, int depth, cons
   const int k = sys->dev.k;
   vx_opts opts{};
   if (o) opts = *o;
-  if (opts.mode != VX_FP64 && opts.mode != VX_FP32_MIDRAD) {
+  if (opts.mode != VX_FP64 && opts.mode != VX_FP32_MIDRAD && opts.mode != VX_FP32) {
     set_error("vx_enclose: unknown mode %d", opts.mode);
     return VX_EINVAL;
   }
@@ -673,42 +774,22 @@ static int enclose_impl(const vx_system *sys, const double *dom, int depth, cons
     const int64_t n = cur.v.N[k - 1];
     R->tested[l] = n;
     for (int d = 0; d < k; ++d) R->nodes[(size_t)l * k + d] = cur.v.N[d];
-    const bool f32 = opts.mode == VX_FP32_MIDRAD && !(opts.fp64_final && l == depth);
-    const bool recheck = f32 && opts.fp64_recheck;
-    uint8_t *keep = nullptr, *tight = nullptr;
+    int mode = opts.mode;
+    if (mode == VX_FP32_MIDRAD && opts.fp64_final && l == depth) mode = VX_FP64;
+    uint8_t *keep = nullptr;
     rc = dmalloc((void **)&keep, (size_t)std::max<int64_t>(n, 1), s);
-    if (rc == VX_OK && recheck) rc = dmalloc((void **)&tight, (size_t)std::max<int64_t>(n, 1), s);
-    int64_t w = 0;
     if (rc == VX_OK) {
-      if (recheck)
-        rc = eval_level_tight(sys->dev, cur.v, g, theta, keep, tight, s, tm, &w);
-      else
-        rc = eval_level(sys->dev, cur.v, g, f32 ? VX_FP32_MIDRAD : VX_FP64, nullptr, nullptr,
-                        keep, s, tm, &w);
+      int64_t w = 0, nr = 0;
+      rc = eval_decide(sys->dev, cur.v, g, mode, opts.fp64_recheck != 0, theta, nullptr, nullptr,
+                       keep, s, tm, &w, &nr);
       R->madds[l] += w;
-    }
-    if (rc == VX_OK && recheck && n > 0) {
-      // boxes the binary32 test keeps with a tight margin: re-evaluate them in binary64
-      CsfObj sub;
-      int32_t *idx = nullptr;
-      uint8_t *subkeep = nullptr;
-      rc = dmalloc((void **)&idx, (size_t)n * 4, s);
-      if (rc == VX_OK) rc = csf_prune(cur.v, tight, 0, idx, s, &sub, tm);
-      if (rc == VX_OK) {
-        const int64_t ns = sub.v.N[k - 1];
-        R->recheck[l] = ns;
-        if (ns > 0) {
-          rc = dmalloc((void **)&subkeep, (size_t)ns, s);
-          int64_t w2 = 0;
-          if (rc == VX_OK)
-            rc = eval_level(sys->dev, sub.v, g, VX_FP64, nullptr, nullptr, subkeep, s, tm, &w2);
-          R->madds[l] += w2;
-          if (rc == VX_OK) rc = scatter_keep(idx, subkeep, ns, keep, s);
-        }
-        csf_release(&sub);
+      R->recheck[l] = nr;
+      int st = 0;
+      if (rc == VX_OK) rc = take_device_status(s, &st);
+      if (rc == VX_OK && st) {
+        set_error("enclose: a bounded device wait gave up at level %d", l);
+        rc = VX_ETIMEOUT;
       }
-      dfree(subkeep, s);
-      dfree(idx, s);
     }
     if (rc == VX_OK) {
       if (l == depth) {
@@ -724,7 +805,6 @@ static int enclose_impl(const vx_system *sys, const double *dom, int depth, cons
         }
       }
     }
-    dfree(tight, s);
     dfree(keep, s);
   }
   csf_release(&cur);

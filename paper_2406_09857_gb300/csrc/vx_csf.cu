@@ -195,8 +195,10 @@ int scan_prepare(const Src &src, int64_t n, cudaStream_t s, int32_t **d_scratch,
   VX_CHECK(dmalloc((void **)&buf, (size_t)(C * ntiles + C) * sizeof(int32_t), s));
   *d_scratch = buf;
   k_scan_reduce<C, Src><<<(unsigned)ntiles, ST, 0, s>>>(src, n, buf, ntiles);
+  note_launch();
   VX_LAUNCH_CHECK();
   k_scan_tiles<C><<<1, 1024, 0, s>>>(buf, ntiles, buf + C * ntiles);
+  note_launch();
   VX_LAUNCH_CHECK();
   VX_CUDA(cudaMemcpyAsync(pin, buf + C * ntiles, C * sizeof(int32_t), cudaMemcpyDeviceToHost, s));
   if (d_extra)
@@ -212,6 +214,7 @@ int scan_emit(const Src &src, const Emit &em, int64_t n, const int32_t *d_scratc
               int64_t ntiles, cudaStream_t s) {
   if (ntiles == 0) return VX_OK;
   k_scan_emit<C, Src, Emit><<<(unsigned)ntiles, ST, 0, s>>>(src, em, n, d_scratch, ntiles);
+  note_launch();
   VX_LAUNCH_CHECK();
   return VX_OK;
 }
@@ -288,6 +291,7 @@ int set_ptr_sentinels(const CsfView &v, cudaStream_t s) {
   }
   if (n == 0) return VX_OK;
   k_set_sentinels<<<1, 32, 0, s>>>(S, n);
+  note_launch();
   VX_LAUNCH_CHECK();
   return VX_OK;
 }
@@ -502,6 +506,7 @@ int prune_c(const CsfView &in, const uint8_t *d_keep, int split, int32_t *d_inde
   }
   if (rc == VX_OK) {
     k_mark_up<<<blocks_for(in.N[k - 1]), 256, 0, s>>>(in, d_keep, flags, sg);
+    note_launch();
     if (cudaGetLastError() != cudaSuccess) {
       set_error("mark-up kernel launch failed");
       rc = VX_ECUDA;
@@ -541,6 +546,7 @@ int prune_c(const CsfView &in, const uint8_t *d_keep, int split, int32_t *d_inde
                                                   split ? (newN[k - 1] * 8 + total * 9) : total * 13);
   for (int d = 0; d + 1 < k && rc == VX_OK; ++d) {
     k_kptr<<<blocks_for(in.N[d]), 256, 0, s>>>(in, flags, rank, sg, d, (int32_t *)K.k[d]);
+    note_launch();
     if (cudaGetLastError() != cudaSuccess) {
       set_error("kptr kernel launch failed");
       rc = VX_ECUDA;
@@ -551,6 +557,7 @@ int prune_c(const CsfView &in, const uint8_t *d_keep, int split, int32_t *d_inde
       S.at[0] = nk[d];
       S.val[0] = nk[d + 1];
       k_set_sentinels<<<1, 32, 0, s>>>(S, 1);
+      note_launch();
       if (cudaGetLastError() != cudaSuccess) rc = VX_ECUDA;
     }
   }
@@ -559,6 +566,7 @@ int prune_c(const CsfView &in, const uint8_t *d_keep, int split, int32_t *d_inde
       k_split<<<blocks_for(in.N[d]), 256, 0, s>>>(in, flags, rank, sg, K, d, out->v);
     else
       k_gather<<<blocks_for(in.N[d]), 256, 0, s>>>(in, flags, rank, sg, d, out->v, d_index);
+    note_launch();
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) {
       set_error("split/gather kernel launch failed: %s", cudaGetErrorString(e));
@@ -660,6 +668,7 @@ int csf_prune(const CsfView &in, const uint8_t *d_keep, int split, int32_t *d_in
 int csf_tuples_dev(const CsfView &c, int32_t *d_tuples, cudaStream_t s) {
   if (c.N[c.k - 1] == 0) return VX_OK;
   k_tuples<<<blocks_for(c.N[c.k - 1]), 256, 0, s>>>(c, d_tuples);
+  note_launch();
   VX_LAUNCH_CHECK();
   return VX_OK;
 }
@@ -668,6 +677,7 @@ int scatter_keep(const int32_t *d_index, const uint8_t *d_sub_keep, int64_t n, u
                  cudaStream_t s) {
   if (n == 0) return VX_OK;
   k_scatter<<<blocks_for(n), 256, 0, s>>>(d_index, d_sub_keep, n, d_keep);
+  note_launch();
   VX_LAUNCH_CHECK();
   return VX_OK;
 }

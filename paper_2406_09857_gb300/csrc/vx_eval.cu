@@ -2,14 +2,22 @@
 //
 // Algorithm 2 recurses node by node; here each CSF depth d is one launch over all depth-d
 // nodes at once.  A depth-d node runs stage d of the packed polynomial: Algorithm 1 (Horner)
-// in x_{d+1} on its own interval, once per fibre, on the input block its parent produced
-// (the coefficient tensor itself at depth 0), and writes its own block for its children.
-// The leaves (depth k-1) run the last stage, a single fibre, and apply criterion C0 of
-// Sec. 3.2 (drop the box iff 0 is outside the value of some polynomial).  Per box this is
-// exactly nested Horner: the same operations in the same order, so a depth-d block depends
-// only on the intervals along the path and not on which other boxes share the tree.
+// in x_{d+1} on its own interval, once per fibre, on the block its parent produced (the
+// coefficient tensor itself at depth 0), and writes its own block for its children.  The
+// leaves (depth k-1) run the last stage, a single fibre, and apply criterion C0 of Sec. 3.2
+// (drop the box iff 0 is outside the value of some polynomial).  Per box this is exactly
+// nested Horner: the same operations in the same order, so a block depends only on the
+// intervals along its path, not on which other boxes share the tree.
 //
-// Two arithmetics share the kernels through a policy class:
+// Layout and mapping.  The blocks of depth d are stored entry-major, P_d[e][node], and a warp
+// takes 32 consecutive nodes (one lane each) through the same fibres in lock-step: at every
+// Horner step its lanes read entry e of their parents' blocks, which is one address when the
+// lanes are siblings (a broadcast) and consecutive addresses otherwise, and they store
+// consecutive addresses.  The fibres of a stage are dealt round-robin to G warps per node
+// chunk (fibres are sorted by length, so the groups carry nearly equal work), G chosen so the
+// launch fills the GPU even when a depth has few nodes.
+//
+// Three arithmetics share the kernels through a policy class:
 //   A64: binary64 intervals [lo, hi] with __dmul_rd/__dmul_ru/__dadd_rd/__dadd_ru.  The
 //        product J*X uses the sign of X (fixed per node) and of J's endpoints to pick the one
 //        endpoint product that is the min (max); RD/RU are monotone, so this is the same
@@ -22,22 +30,82 @@
 //        most Jr(|Xm|+Xr) + |Jm|Xr + Ar, and rounding m to nearest adds at most 2^-24|m| plus
 //        2^-149 below the normal range, which every coefficient radius already carries
 //        (it is added when a block is stored).  Inf or NaN never excludes a box.
+//   A32C: binary32 intervals stored as (lo, -hi), so that both ends of J*X + A come from one
+//        paired round-down FMA (lo' = RD(J_sel*X_sel + A.lo), -hi' = RD((-J)_sel*X_sel - A.hi)),
+//        plus an error bound E carried with every interval.  E bounds |lo32 - lo*| +
+//        |lo64 - lo*| (and the same for hi), where lo* is the exact (unrounded) interval Horner
+//        value with the binary64 coefficients and lo64 what A64 computes.  One step gives
+//          E' = RU(E_J * xmax(1+2^-27) + RU((2^-23+2^-46)*m' + E_A)),  m' = max(|lo'|,|hi'|):
+//        the endpoint selection is xmax-Lipschitz in J; the FMA rounds once (< 2^-23 of its
+//        result); the binary64 path rounds the product (< 2^-52 |J| xmax, which is below
+//        2^-29 E_J xmax because every bound satisfies E >= 2^-23 max(|lo|,|hi|)) and the sum
+//        (< 2^-52 of it); every stored E carries a relative margin of 2^-40 and an absolute
+//        2^-148 (results below the normal range), which exceed the binary64 rounding of a
+//        term in terms of the bound itself, so the induction closes.  Hence lo32 > E means
+//        A64's lower end is > 0 (A64 excludes the box) and lo32 <= -E with hi32 >= E means
+//        A64 keeps it: a box is decided exactly as A64 decides it, except inside the band of
+//        width E, where A64 is run on it.  Boxes whose grid points are not binary32 (domains
+//        that are not exact at binary32 precision) add the term 2^-23 m_J xmax explicitly.
 #include <cuda_runtime.h>
-
-#include <cstdio>
-#include <cstdlib>
 
 #include "vx_internal.cuh"
 
 namespace vx {
 namespace {
 
-constexpr int kThreads = 256;
+constexpr int kWarpsPerBlock = 4;
+constexpr int kThreads = 32 * kWarpsPerBlock;
 
 __device__ __forceinline__ double sel_min(double a, double b) { return (b < a) ? b : a; }
 __device__ __forceinline__ double sel_max(double a, double b) { return (b > a) ? b : a; }
 __device__ __forceinline__ bool sign_clear(double v) { return __double2hiint(v) >= 0; }
 
+// Nonzero after a bounded wait in a kernel gave up (read and cleared by take_device_status).
+__device__ int g_vx_status = 0;
+
+// ---- TMA bulk copy global -> shared with an mbarrier (sm_90+ PTX) -------------------------
+__device__ __forceinline__ uint32_t smem_u32(const void *p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t *bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)),
+               "r"(bytes)
+               : "memory");
+}
+__device__ __forceinline__ void bulk_copy_g2s(void *dst, const void *src, uint32_t bytes,
+                                              uint64_t *bar) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::
+          "r"(smem_u32(dst)),
+      "l"(src), "r"(bytes), "r"(smem_u32(bar))
+      : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+      " selp.u32 %0, 1, 0, p;\n}" : "=r"(ok) : "r"(smem_u32(bar)), "r"(parity) : "memory");
+  return ok != 0;
+}
+// Waits for phase `parity` of the barrier for at most `limit` polls; on give-up records the
+// failure in g_vx_status and waits (bounded again) for the copy in flight before returning.
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity) {
+  const uint32_t limit = 1u << 22;
+  for (uint32_t it = 0; it < limit; ++it)
+    if (mbar_try_wait(bar, parity)) return true;
+  atomicExch(&g_vx_status, 1);
+  for (uint32_t it = 0; it < limit; ++it)
+    if (mbar_try_wait(bar, parity)) break;
+  return false;
+}
+
+// ---------------------------------------------------------------------------------------
+// binary64 intervals
+// ---------------------------------------------------------------------------------------
 struct A64 {
   using V = double2;  // .x = lo, .y = hi
   struct X {
@@ -51,12 +119,13 @@ struct A64 {
     x.cls = (x.l >= 0.0) ? 1 : ((x.h <= 0.0) ? -1 : 0);
     return x;
   }
-  static __device__ __forceinline__ V muladd(V J, const X &x, V A) {
+  template <int CLS>
+  static __device__ __forceinline__ V step(V J, const X &x, V A) {
     double lo, hi;
-    if (x.cls > 0) {
+    if (CLS > 0) {
       lo = __dmul_rd(J.x, sign_clear(J.x) ? x.l : x.h);
       hi = __dmul_ru(J.y, sign_clear(J.y) ? x.h : x.l);
-    } else if (x.cls < 0) {
+    } else if (CLS < 0) {
       lo = __dmul_rd(J.y, sign_clear(J.y) ? x.l : x.h);
       hi = __dmul_ru(J.x, sign_clear(J.x) ? x.h : x.l);
     } else {
@@ -68,20 +137,25 @@ struct A64 {
     return make_double2(__dadd_rd(lo, A.x), __dadd_ru(hi, A.y));
   }
   static __device__ __forceinline__ V store(V J) { return J; }
-  static __device__ __forceinline__ bool contains0(V J) { return !(J.x > 0.0 || J.y < 0.0); }
+  // 0: excluded, 1: kept (C0 of Sec. 3.2: excluded iff 0 is provably outside)
+  static __device__ __forceinline__ int classify(V J) { return (J.x > 0.0 || J.y < 0.0) ? 0 : 1; }
   static __device__ __forceinline__ double lo(V J) { return J.x; }
   static __device__ __forceinline__ double hi(V J) { return J.y; }
   static __device__ __forceinline__ bool tight(V, float) { return false; }
   static __host__ __device__ __forceinline__ const V *coef(const PolyDev &p) { return p.c64; }
 };
 
-constexpr float kU32 = 5.9604644775390625e-08f;  // 2^-24, unit roundoff of binary32
-constexpr float kEta32 = 1.40129846e-45f;        // 2^-149, smallest positive binary32
+// ---------------------------------------------------------------------------------------
+// binary32 midpoint-radius
+// ---------------------------------------------------------------------------------------
+constexpr float kU32 = 0x1p-24f;    // unit roundoff of binary32
+constexpr float kEta32 = 0x1p-149f;  // smallest positive binary32
 
 struct A32 {
   using V = float2;  // .x = m, .y = r
   struct X {
     float m, r, a;  // a >= |m| + r
+    int cls;
   };
   static __device__ __forceinline__ X box(const AxisGrid &g, int32_t t) {
     X x;
@@ -97,9 +171,11 @@ struct A32 {
       x.r = __double2float_ru(fmax(__dadd_ru(h, -dm), __dadd_ru(dm, -l)));
     }
     x.a = __fadd_ru(fabsf(x.m), x.r);
+    x.cls = 0;  // one code path for every sign
     return x;
   }
-  static __device__ __forceinline__ V muladd(V J, const X &x, V A) {
+  template <int CLS>
+  static __device__ __forceinline__ V step(V J, const X &x, V A) {
     float m = __fmaf_rn(J.x, x.m, A.x);
     float r = __fmaf_ru(J.y, x.a, A.y);
     r = __fmaf_ru(fabsf(J.x), x.r, r);
@@ -107,84 +183,305 @@ struct A32 {
     return make_float2(m, r);
   }
   static __device__ __forceinline__ V store(V J) { return make_float2(J.x, __fadd_ru(J.y, kEta32)); }
-  static __device__ __forceinline__ bool contains0(V J) { return !(fabsf(J.x) > J.y); }
+  static __device__ __forceinline__ int classify(V J) { return (fabsf(J.x) > J.y) ? 0 : 1; }
   static __device__ __forceinline__ double lo(V J) { return __dadd_rd((double)J.x, -(double)J.y); }
   static __device__ __forceinline__ double hi(V J) { return __dadd_ru((double)J.x, (double)J.y); }
-  static __device__ __forceinline__ bool tight(V J, float theta) {
-    return fabsf(J.x) >= theta * J.y;
-  }
+  static __device__ __forceinline__ bool tight(V J, float theta) { return fabsf(J.x) >= theta * J.y; }
   static __host__ __device__ __forceinline__ const V *coef(const PolyDev &p) { return p.c32; }
 };
 
-// Stage d < k-1 on every depth-d node: item = (node, fibre), fibres fastest so that a warp
-// reads consecutive entries of one row of the parent's block at each Horner step.
+// ---------------------------------------------------------------------------------------
+// binary32 intervals (lo, -hi) with an error bound certifying the binary64 decision
+// ---------------------------------------------------------------------------------------
+constexpr float kEta148 = 0x1p-148f;
+constexpr float kCr = 0x1.000002p-23f;  // 2^-23 + 2^-46
+constexpr float k2m27 = 0x1p-27f;
+constexpr float k2m40 = 0x1p-40f;
+
+struct A32C {
+  using V = float4;  // .x = lo, .y = -hi, .z = E, .w unused
+  struct X {
+    float l, h, nl, nh;  // endpoints and their negations
+    float xmaxp;         // >= xmax (1 + 2^-27)
+    float cx;            // 2^-23 xmax when the endpoints are rounded outward, else 0
+    int cls;
+  };
+  static __device__ __forceinline__ X box(const AxisGrid &g, int32_t t) {
+    X x;
+    x.cx = 0.f;
+    if (g.fexact) {
+      x.l = __fmaf_rn((float)t, g.fw, g.flo);  // exact
+      x.h = __fmaf_rn((float)t + 1.0f, g.fw, g.flo);
+    } else {
+      const double l = __dadd_rn(g.lo, __dmul_rn((double)t, g.w));
+      const double h = __dadd_rn(g.lo, __dmul_rn((double)t + 1.0, g.w));
+      x.l = __double2float_rd(l);
+      x.h = __double2float_ru(h);
+    }
+    x.nl = -x.l;
+    x.nh = -x.h;
+    const float xm = fmaxf(fabsf(x.l), fabsf(x.h));
+    x.xmaxp = __fmaf_ru(xm, k2m27, xm);
+    if (!g.fexact) x.cx = __fmul_ru(xm, 0x1p-23f);
+    // rounded endpoints take the sign-agnostic path, which carries the term c_x m_J
+    x.cls = !g.fexact ? 0 : ((x.l >= 0.f) ? 1 : ((x.h <= 0.f) ? -1 : 0));
+    return x;
+  }
+  template <int CLS>
+  static __device__ __forceinline__ V step(V J, const X &x, V A) {
+    // Each bound is the smaller of the two candidate products, each rounded down once (RD is
+    // monotone, so this is RD of the selected product plus A): one paired FMA per bound.
+    float2 r;
+    if (CLS > 0) {  // X >= 0: lo from lo_J, hi from hi_J
+      const float2 pl = __ffma2_rd(make_float2(J.x, J.x), make_float2(x.l, x.h), make_float2(A.x, A.x));
+      const float2 ph = __ffma2_rd(make_float2(J.y, J.y), make_float2(x.l, x.h), make_float2(A.y, A.y));
+      r = make_float2(fminf(pl.x, pl.y), fminf(ph.x, ph.y));
+    } else if (CLS < 0) {  // X <= 0: lo from hi_J = -J.y, hi from lo_J
+      const float2 pl = __ffma2_rd(make_float2(J.y, J.y), make_float2(x.nl, x.nh), make_float2(A.x, A.x));
+      const float2 ph = __ffma2_rd(make_float2(J.x, J.x), make_float2(x.nl, x.nh), make_float2(A.y, A.y));
+      r = make_float2(fminf(pl.x, pl.y), fminf(ph.x, ph.y));
+    } else {  // X straddles 0: hull of the four products, each bound rounded once
+      const float jh = -J.y;
+      r.x = fminf(fminf(__fmaf_rd(J.x, x.l, A.x), __fmaf_rd(J.x, x.h, A.x)),
+                  fminf(__fmaf_rd(jh, x.l, A.x), __fmaf_rd(jh, x.h, A.x)));
+      r.y = fminf(fminf(__fmaf_rd(J.x, x.nl, A.y), __fmaf_rd(J.x, x.nh, A.y)),
+                  fminf(__fmaf_rd(jh, x.nl, A.y), __fmaf_rd(jh, x.nh, A.y)));
+    }
+    const float m = fmaxf(fabsf(r.x), fabsf(r.y));
+    float e = __fmaf_ru(kCr, m, A.z);
+    if (CLS == 0) e = __fmaf_ru(fmaxf(fabsf(J.x), fabsf(J.y)), x.cx, e);
+    e = __fmaf_ru(J.z, x.xmaxp, e);
+    return make_float4(r.x, r.y, e, 0.f);
+  }
+  // a stored bound carries a relative margin 2^-40 and an absolute 2^-148
+  static __device__ __forceinline__ V store(V J) {
+    return make_float4(J.x, J.y, __fadd_ru(__fmaf_ru(J.z, k2m40, J.z), kEta148), 0.f);
+  }
+  // 0: the binary64 path surely excludes, 1: surely keeps, 2: inside the error band
+  static __device__ __forceinline__ int classify(V J) {
+    if (J.x > J.z || J.y > J.z) return 0;      // lo > E or hi < -E
+    if (J.x <= -J.z && J.y <= -J.z) return 1;  // lo <= -E and hi >= E
+    return 2;
+  }
+  static __device__ __forceinline__ double lo(V J) { return (double)J.x; }
+  static __device__ __forceinline__ double hi(V J) { return -(double)J.y; }
+  static __device__ __forceinline__ bool tight(V, float) { return false; }
+  static __host__ __device__ __forceinline__ const V *coef(const PolyDev &p) { return p.c32c; }
+};
+
+// Algorithm 1 on one fibre: entries rowoff[a] + f (a = L-1 .. 0) of a block whose entry e is
+// at base[e * stride].
+template <class AR, int CLS>
+__device__ __forceinline__ typename AR::V horner(const typename AR::V *__restrict__ base,
+                                                 int64_t stride, const int32_t *rowoff, int f,
+                                                 int L, const typename AR::X &x) {
+  typename AR::V J = base[(int64_t)(rowoff[L - 1] + f) * stride];
+#pragma unroll 4
+  for (int a = L - 2; a >= 0; --a)
+    J = AR::template step<CLS>(J, x, base[(int64_t)(rowoff[a] + f) * stride]);
+  return J;
+}
+
+template <class AR>
+__device__ __forceinline__ typename AR::V horner_any(const typename AR::V *__restrict__ base,
+                                                     int64_t stride, const int32_t *rowoff,
+                                                     int f, int L, const typename AR::X &x) {
+  if (x.cls > 0) return horner<AR, 1>(base, stride, rowoff, f, L, x);
+  if (x.cls < 0) return horner<AR, -1>(base, stride, rowoff, f, L, x);
+  return horner<AR, 0>(base, stride, rowoff, f, L, x);
+}
+
+// the same for a single-fibre stage (entry a of the fibre is entry a of the block)
+template <class AR, int CLS>
+__device__ __forceinline__ typename AR::V horner1(const typename AR::V *__restrict__ base,
+                                                  int64_t stride, int L, const typename AR::X &x) {
+  typename AR::V J = base[(int64_t)(L - 1) * stride];
+#pragma unroll 4
+  for (int a = L - 2; a >= 0; --a) J = AR::template step<CLS>(J, x, base[(int64_t)a * stride]);
+  return J;
+}
+
+// two fibres of the same length in lock-step (two independent chains per thread)
+template <class AR, int CLS>
+__device__ __forceinline__ void horner1x2(const typename AR::V *__restrict__ b0,
+                                          const typename AR::V *__restrict__ b1, int L,
+                                          const typename AR::X &x, typename AR::V &J0,
+                                          typename AR::V &J1) {
+  J0 = b0[L - 1];
+  J1 = b1[L - 1];
+#pragma unroll 2
+  for (int a = L - 2; a >= 0; --a) {
+    const typename AR::V A0 = b0[a], A1 = b1[a];
+    J0 = AR::template step<CLS>(J0, x, A0);
+    J1 = AR::template step<CLS>(J1, x, A1);
+  }
+}
+
+template <class AR>
+__device__ __forceinline__ void horner1x2_any(const typename AR::V *__restrict__ b0,
+                                              const typename AR::V *__restrict__ b1, int L,
+                                              const typename AR::X &x, typename AR::V &J0,
+                                              typename AR::V &J1) {
+  if (x.cls > 0)
+    horner1x2<AR, 1>(b0, b1, L, x, J0, J1);
+  else if (x.cls < 0)
+    horner1x2<AR, -1>(b0, b1, L, x, J0, J1);
+  else
+    horner1x2<AR, 0>(b0, b1, L, x, J0, J1);
+}
+
+template <class AR>
+__device__ __forceinline__ typename AR::V horner1_any(const typename AR::V *__restrict__ base,
+                                                      int64_t stride, int L,
+                                                      const typename AR::X &x) {
+  if (x.cls > 0) return horner1<AR, 1>(base, stride, L, x);
+  if (x.cls < 0) return horner1<AR, -1>(base, stride, L, x);
+  return horner1<AR, 0>(base, stride, L, x);
+}
+
+// Stage d < k-1 on every depth-d node.  Warp w takes node chunk w % nchunk (32 nodes, one per
+// lane) and fibres g, g+G, ... with g = w / nchunk.  in: entry e of parent p's block at
+// in[e * in_estride + p * in_nstride] (the coefficient tensor: in_estride 1, in_nstride 0).
+// out: entry e of node i at out[e * out_estride + i * out_nstride]: entry-major
+// (out_estride = nnodes, out_nstride = 1) when an inner stage reads it, node-major
+// (out_estride = 1, out_nstride = blk_out) when the leaves do, so that a leaf's Horner walks
+// consecutive entries of its parent's block.
 template <class AR>
 __global__ void __launch_bounds__(kThreads)
     k_stage(const StageDev st, const int32_t *__restrict__ lab, const int32_t *__restrict__ par,
-            const typename AR::V *__restrict__ in, typename AR::V *__restrict__ out,
-            int64_t nnodes, AxisGrid g) {
+            const typename AR::V *__restrict__ in, int64_t in_estride, int64_t in_nstride,
+            typename AR::V *__restrict__ out, int64_t out_estride, int64_t out_nstride,
+            int64_t nnodes, int64_t nchunk, int G, AxisGrid g) {
   using V = typename AR::V;
   extern __shared__ int32_t s_rowoff[];
   for (int i = threadIdx.x; i <= st.maxlen; i += blockDim.x) s_rowoff[i] = st.rowoff[i];
   __syncthreads();
-  const int64_t nitems = nnodes * st.nfib;
-  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < nitems; i += stride) {
-    const int64_t node = i / st.nfib;
-    const int fib = (int)(i - node * st.nfib);
-    const V *base = par ? in + (int64_t)__ldg(par + node) * st.blk_in : in;
-    const typename AR::X x = AR::box(g, __ldg(lab + node));
-    const int L = __ldg(st.fiblen + fib);
-    V J = base[s_rowoff[L - 1] + fib];
-    for (int a = L - 2; a >= 0; --a) J = AR::muladd(J, x, base[s_rowoff[a] + fib]);
-    out[node * st.blk_out + __ldg(st.outpos + fib)] = AR::store(J);
+  const int lane = threadIdx.x & 31;
+  const int64_t nwarps = nchunk * G;
+  for (int64_t w = (int64_t)blockIdx.x * kWarpsPerBlock + (threadIdx.x >> 5); w < nwarps;
+       w += (int64_t)gridDim.x * kWarpsPerBlock) {
+    const int64_t chunk = w % nchunk;
+    const int grp = (int)(w / nchunk);
+    const int64_t node = chunk * 32 + lane;
+    const bool live = node < nnodes;
+    const int64_t nd = live ? node : nnodes - 1;  // idle lanes follow the last node, no store
+    const V *base = par ? in + (int64_t)__ldg(par + nd) * in_nstride : in;
+    const typename AR::X x = AR::box(g, __ldg(lab + nd));
+    V *dst = out + node * out_nstride;
+    for (int f = grp; f < st.nfib; f += G) {
+      const int L = __ldg(st.fiblen + f);
+      const V J = horner_any<AR>(base, in_estride, s_rowoff, f, L, x);
+      if (live) dst[(int64_t)__ldg(st.outpos + f) * out_estride] = AR::store(J);
+    }
+  }
+}
+
+// Stage d (1 <= d < k-1) with the parent blocks in shared memory: CTA b takes the 128 nodes
+// b*128 .. b*128+127, whose parents (consecutive, the nodes being sorted by parent) number at
+// most maxpar; their node-major blocks are one contiguous range, brought in by TMA bulk copies
+// (cp.async.bulk, completion on an mbarrier) while the row offsets are loaded.  Every thread
+// then runs all fibres of its node reading shared memory: a broadcast when the lanes of a warp
+// share a parent.  CTAs whose nodes span more parents read their blocks from global memory.
+template <class AR>
+__global__ void __launch_bounds__(kThreads)
+    k_stage_tma(const StageDev st, const int32_t *__restrict__ lab,
+                const int32_t *__restrict__ par, const typename AR::V *__restrict__ in,
+                typename AR::V *__restrict__ out, int64_t out_estride, int64_t out_nstride,
+                int64_t nnodes, int maxpar, AxisGrid g) {
+  using V = typename AR::V;
+  extern __shared__ __align__(128) unsigned char smem[];
+  uint64_t *bar = reinterpret_cast<uint64_t *>(smem);
+  int32_t *s_rowoff = reinterpret_cast<int32_t *>(smem + 128);
+  V *s_blk = reinterpret_cast<V *>(smem + 128 + ((st.maxlen + 1) * 4 + 127) / 128 * 128);
+  const int64_t first = (int64_t)blockIdx.x * kThreads;
+  const int64_t last = (first + kThreads < nnodes ? first + kThreads : nnodes) - 1;
+  const int64_t p0 = __ldg(par + first), p1 = __ldg(par + last);
+  const bool staged = p1 - p0 < maxpar;
+  if (threadIdx.x == 0) {
+    mbar_init(bar, 1);
+    if (staged) {
+      const uint64_t bytes = (uint64_t)(p1 - p0 + 1) * st.blk_in * sizeof(V);
+      mbar_arrive_expect_tx(bar, (uint32_t)bytes);
+      const char *src = reinterpret_cast<const char *>(in + p0 * st.blk_in);
+      char *dst = reinterpret_cast<char *>(s_blk);
+      for (uint64_t o = 0; o < bytes; o += 32768) {
+        const uint32_t n = (uint32_t)(bytes - o < 32768 ? bytes - o : 32768);
+        bulk_copy_g2s(dst + o, src + o, n, bar);
+      }
+    }
+  }
+  for (int i = threadIdx.x; i <= st.maxlen; i += blockDim.x) s_rowoff[i] = st.rowoff[i];
+  __syncthreads();
+  if (staged && !mbar_wait_bounded(bar, 0)) return;
+  const int64_t node = first + threadIdx.x;
+  const bool live = node < nnodes;
+  const int64_t nd = live ? node : last;
+  const int64_t p = __ldg(par + nd);
+  const V *base = staged ? s_blk + (p - p0) * st.blk_in : in + p * st.blk_in;
+  const typename AR::X x = AR::box(g, __ldg(lab + nd));
+  V *dst = out + node * out_nstride;
+  for (int f = 0; f < st.nfib; ++f) {
+    const int L = __ldg(st.fiblen + f);
+    const V J = horner_any<AR>(base, 1, s_rowoff, f, L, x);
+    if (live) dst[(int64_t)__ldg(st.outpos + f) * out_estride] = AR::store(J);
   }
 }
 
 struct LeafArgs {
-  const void *in[VX_MAXPOLY];  // parent blocks per polynomial (the coefficients when k == 1)
-  int64_t blk[VX_MAXPOLY];
+  const void *in[VX_MAXPOLY];  // parent blocks per polynomial, node-major (the coefficients
+                               // when k == 1)
+  int64_t blk[VX_MAXPOLY];     // entries per parent block (0 when k == 1)
   int32_t len[VX_MAXPOLY];
 };
 
-// Last stage on every leaf: one Horner per polynomial, then C0.
+// Last stage on every leaf: one Horner per polynomial, then C0.  Lane = leaf.
 template <class AR>
 __global__ void __launch_bounds__(kThreads)
     k_leaf(LeafArgs A, int npoly, const int32_t *__restrict__ lab, const int32_t *__restrict__ par,
            int64_t nleaves, AxisGrid g, uint8_t *__restrict__ keep, double *__restrict__ lo,
-           double *__restrict__ hi, uint8_t *__restrict__ tight, float theta) {
+           double *__restrict__ hi, uint8_t *__restrict__ flag, float theta) {
   using V = typename AR::V;
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < nleaves; i += stride) {
     const typename AR::X x = AR::box(g, __ldg(lab + i));
     const int64_t p = par ? (int64_t)__ldg(par + i) : 0;
-    bool kp = true, tg = false;
-    for (int f = 0; f < npoly; ++f) {
-      const V *base = (const V *)A.in[f] + p * A.blk[f];
-      const int L = A.len[f];
-      V J = base[L - 1];
-      for (int a = L - 2; a >= 0; --a) J = AR::muladd(J, x, base[a]);
+    bool excl = false, amb = false, tg = false;
+    auto decide = [&](int f, const V &J) {
       if (lo) {
         lo[(int64_t)f * nleaves + i] = AR::lo(J);
         hi[(int64_t)f * nleaves + i] = AR::hi(J);
       }
-      kp = kp && AR::contains0(J);
+      const int c = AR::classify(J);
+      excl = excl || c == 0;
+      amb = amb || c == 2;
       tg = tg || AR::tight(J, theta);
+    };
+    int f = 0;
+    for (; f + 1 < npoly && A.len[f] == A.len[f + 1]; f += 2) {
+      V J0, J1;
+      horner1x2_any<AR>((const V *)A.in[f] + p * A.blk[f], (const V *)A.in[f + 1] + p * A.blk[f + 1],
+                        A.len[f], x, J0, J1);
+      decide(f, J0);
+      decide(f + 1, J1);
     }
-    keep[i] = kp ? 1 : 0;
-    if (tight) tight[i] = (kp && tg) ? 1 : 0;
+    for (; f < npoly; ++f) {
+      const V *base = (const V *)A.in[f] + p * A.blk[f];
+      decide(f, horner1_any<AR>(base, 1, A.len[f], x));
+    }
+    keep[i] = excl ? 0 : 1;
+    if (flag) flag[i] = (!excl && (amb || tg)) ? 1 : 0;
   }
 }
 
-bool tracing() {
-  static int on = -1;
-  if (on < 0) on = std::getenv("VX_TRACE") ? 1 : 0;
-  return on == 1;
-}
+constexpr size_t kMaxDynSmem = 200 * 1024;
 
-int grid_for(int64_t items) {
+// The input of stage d >= 1 (the output of stage d-1) is node-major iff stage d is the leaf
+// stage or is TMA-staged; a non-staged inner stage reads it entry-major.
+inline bool tma_input_node_major(int d, int k, const bool *tma) { return d + 1 == k || tma[d]; }
+
+int leaf_grid(int64_t items) {
   int64_t b = (items + kThreads - 1) / kThreads;
-  const int64_t cap = 152 * 16;
+  const int64_t cap = 152 * 32;
   if (b > cap) b = cap;
   if (b < 1) b = 1;
   return (int)b;
@@ -192,7 +489,7 @@ int grid_for(int64_t items) {
 
 template <class AR>
 int eval_level_t(const SysDev &sys, const CsfView &c, const LevelGrid &grid, double *d_lo,
-                 double *d_hi, uint8_t *d_keep, uint8_t *d_tight, float theta, cudaStream_t s,
+                 double *d_hi, uint8_t *d_keep, uint8_t *d_flag, float theta, cudaStream_t s,
                  Timer *tm, int64_t *madds_out, int kind0) {
   using V = typename AR::V;
   const int k = sys.k;
@@ -202,7 +499,7 @@ int eval_level_t(const SysDev &sys, const CsfView &c, const LevelGrid &grid, dou
     if (madds_out) *madds_out = 0;
     return VX_OK;
   }
-  // partial-polynomial blocks of depths 0..k-2, one allocation per polynomial
+  // blocks of depths 0..k-2, one allocation per polynomial
   void *mem[VX_MAXPOLY] = {nullptr};
   V *buf[VX_MAXPOLY][VX_KMAX] = {{nullptr}};
   int rc = VX_OK;
@@ -218,19 +515,55 @@ int eval_level_t(const SysDev &sys, const CsfView &c, const LevelGrid &grid, dou
     }
   }
   for (int f = 0; f < sys.npoly && rc == VX_OK; ++f) {
+    // stage d (1 <= d < k-1) stages its parents' blocks by TMA when the depth has enough
+    // nodes to fill the GPU with 128-node CTAs and two parent blocks fit in shared memory
+    bool tma[VX_KMAX] = {false};
+    size_t tma_smem[VX_KMAX] = {0};
+    for (int d = 1; d + 1 < k; ++d) {
+      const StageDev &st = sys.p[f].st[d];
+      const size_t sm = 128 + ((size_t)(st.maxlen + 1) * 4 + 127) / 128 * 128 +
+                        2 * (size_t)st.blk_in * sizeof(V);
+      if (c.N[d] >= 152 * 4 * kThreads && sm <= kMaxDynSmem) {
+        tma[d] = true;
+        tma_smem[d] = sm;
+      }
+    }
     for (int d = 0; d + 1 < k && rc == VX_OK; ++d) {
       const StageDev &st = sys.p[f].st[d];
-      const int64_t items = c.N[d] * st.nfib;
       const int64_t w = c.N[d] * (st.blk_in - st.nfib);
       madds += w;
+      // node-major output when the consumer is the leaf stage or a TMA-staged stage
+      const bool node_major = d + 2 == k || tma[d + 1];
+      const int64_t oe = node_major ? 1 : c.N[d], on = node_major ? st.blk_out : 1;
       if (tm && tm->on) rc = tm->begin(d == 0 ? kind0 : kind0 + 1, w);
       if (rc != VX_OK) break;
-      if (tracing())
-        std::fprintf(stderr, "[vx] stage %d launch poly %d items=%lld smem=%d\n", d, f,
-                     (long long)items, (int)((st.maxlen + 1) * sizeof(int32_t)));
       const V *in = d == 0 ? AR::coef(sys.p[f]) : buf[f][d - 1];
-      k_stage<AR><<<grid_for(items), kThreads, (st.maxlen + 1) * sizeof(int32_t), s>>>(
-          st, c.lab[d], d == 0 ? nullptr : c.par[d], in, buf[f][d], c.N[d], grid.ax[d]);
+      if (tma[d]) {
+        if (cudaFuncSetAttribute(k_stage_tma<AR>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)tma_smem[d]) != cudaSuccess) {
+          set_error("cudaFuncSetAttribute(shared memory %zu) failed", tma_smem[d]);
+          rc = VX_ECUDA;
+          break;
+        }
+        const int64_t blocks = (c.N[d] + kThreads - 1) / kThreads;
+        k_stage_tma<AR><<<(unsigned)blocks, kThreads, tma_smem[d], s>>>(
+            st, c.lab[d], c.par[d], in, buf[f][d], oe, on, c.N[d], 2, grid.ax[d]);
+      } else {
+        // fibre groups: enough warps to fill the GPU several times over
+        const int64_t nchunk = (c.N[d] + 31) / 32;
+        const int64_t target = 152 * 64;
+        int64_t G = (target + nchunk - 1) / nchunk;
+        if (G > st.nfib) G = st.nfib;
+        if (G < 1) G = 1;
+        int64_t blocks = (nchunk * G + kWarpsPerBlock - 1) / kWarpsPerBlock;
+        if (blocks > 152 * 64) blocks = 152 * 64;
+        const int64_t in_estride = d == 0 ? 1 : (tma_input_node_major(d, k, tma) ? 1 : c.N[d - 1]);
+        const int64_t in_nstride = d == 0 ? 0 : (tma_input_node_major(d, k, tma) ? st.blk_in : 1);
+        k_stage<AR><<<(unsigned)blocks, kThreads, (st.maxlen + 1) * sizeof(int32_t), s>>>(
+            st, c.lab[d], d == 0 ? nullptr : c.par[d], in, in_estride, in_nstride, buf[f][d], oe,
+            on, c.N[d], nchunk, (int)G, grid.ax[d]);
+      }
+      note_launch();
       cudaError_t e = cudaGetLastError();
       if (e != cudaSuccess) {
         set_error("stage kernel launch failed: %s", cudaGetErrorString(e));
@@ -252,14 +585,12 @@ int eval_level_t(const SysDev &sys, const CsfView &c, const LevelGrid &grid, dou
     }
     madds += wl;
     if (tm && tm->on) rc = tm->begin(kind0 + 2, wl);
-    if (tracing())
-      std::fprintf(stderr, "[vx] leaf launch k=%d npoly=%d n=%lld grid=%d len0=%d\n", k,
-                   sys.npoly, (long long)nleaves, grid_for(nleaves), A.len[0]);
     if (rc == VX_OK) {
-      k_leaf<AR><<<grid_for(nleaves), kThreads, 0, s>>>(A, sys.npoly, c.lab[k - 1],
+      k_leaf<AR><<<leaf_grid(nleaves), kThreads, 0, s>>>(A, sys.npoly, c.lab[k - 1],
                                                         k == 1 ? nullptr : c.par[k - 1], nleaves,
                                                         grid.ax[k - 1], d_keep, d_lo, d_hi,
-                                                        d_tight, theta);
+                                                        d_flag, theta);
+      note_launch();
       cudaError_t e = cudaGetLastError();
       if (e != cudaSuccess) {
         set_error("leaf kernel launch failed: %s", cudaGetErrorString(e));
@@ -275,21 +606,33 @@ int eval_level_t(const SysDev &sys, const CsfView &c, const LevelGrid &grid, dou
 
 }  // namespace
 
-int eval_level(const SysDev &sys, const CsfView &csf, const LevelGrid &grid, int mode,
-               double *d_lo, double *d_hi, uint8_t *d_keep, cudaStream_t s, Timer *tm,
-               int64_t *madds_out) {
-  if (mode == VX_FP64)
-    return eval_level_t<A64>(sys, csf, grid, d_lo, d_hi, d_keep, nullptr, 0.f, s, tm, madds_out,
-                             KK_STAGE0);
-  return eval_level_t<A32>(sys, csf, grid, d_lo, d_hi, d_keep, nullptr, 0.f, s, tm, madds_out,
-                           KK_STAGE0_F32);
+int take_device_status(cudaStream_t s, int *status) {
+  int v = 0;
+  VX_CUDA(cudaMemcpyFromSymbolAsync(&v, g_vx_status, sizeof(int), 0, cudaMemcpyDeviceToHost, s));
+  VX_CUDA(cudaStreamSynchronize(s));
+  if (v) {
+    const int zero = 0;
+    VX_CUDA(cudaMemcpyToSymbolAsync(g_vx_status, &zero, sizeof(int), 0, cudaMemcpyHostToDevice, s));
+    VX_CUDA(cudaStreamSynchronize(s));
+  }
+  *status = v;
+  return VX_OK;
 }
 
-int eval_level_tight(const SysDev &sys, const CsfView &csf, const LevelGrid &grid, float theta,
-                     uint8_t *d_keep, uint8_t *d_tight, cudaStream_t s, Timer *tm,
-                     int64_t *madds_out) {
-  return eval_level_t<A32>(sys, csf, grid, nullptr, nullptr, d_keep, d_tight, theta, s, tm,
-                           madds_out, KK_STAGE0_F32);
+int eval_level_raw(const SysDev &sys, const CsfView &csf, const LevelGrid &grid, int arith,
+                   double *d_lo, double *d_hi, uint8_t *d_keep, uint8_t *d_flag, float theta,
+                   cudaStream_t s, Timer *tm, int64_t *madds_out) {
+  switch (arith) {
+    case ARITH_F64:
+      return eval_level_t<A64>(sys, csf, grid, d_lo, d_hi, d_keep, d_flag, theta, s, tm,
+                               madds_out, KK_STAGE0);
+    case ARITH_F32_MIDRAD:
+      return eval_level_t<A32>(sys, csf, grid, d_lo, d_hi, d_keep, d_flag, theta, s, tm,
+                               madds_out, KK_STAGE0_F32);
+    default:
+      return eval_level_t<A32C>(sys, csf, grid, d_lo, d_hi, d_keep, d_flag, theta, s, tm,
+                                madds_out, KK_STAGE0_F32C);
+  }
 }
 
 }  // namespace vx

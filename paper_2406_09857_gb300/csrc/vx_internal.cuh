@@ -35,6 +35,9 @@ void clear_error();
 
 #define VX_LAUNCH_CHECK() VX_CUDA(cudaGetLastError())
 
+// Counts the kernels this library launches (process-wide, all threads).
+void note_launch(int n = 1);
+
 // Stream-ordered device memory (the device's default memory pool, kept cached).
 int dmalloc(void **p, size_t bytes, cudaStream_t s);
 void dfree(void *p, cudaStream_t s);
@@ -62,6 +65,7 @@ struct PolyDev {
   StageDev st[VX_KMAX];
   const double2 *c64;  // stage-0 input block as degenerate intervals (lo = hi = coefficient)
   const float2 *c32;   // stage-0 input block as <m, r> binary32 midpoint-radius pairs
+  const float4 *c32c;  // stage-0 input block as binary32 [RD(c), RU(c)] with error bound
 };
 
 struct SysDev {
@@ -103,6 +107,9 @@ enum KernelKind {
   KK_STAGE0_F32,
   KK_STAGEJ_F32,
   KK_LEAF_F32,
+  KK_STAGE0_F32C,
+  KK_STAGEJ_F32C,
+  KK_LEAF_F32C,
   KK_CSF_BUILD,    // scans of csf_build
   KK_PRUNE,        // keep propagation, rank scan, kept-tree pointers
   KK_SPLIT,        // 2^k split and rebuild
@@ -130,15 +137,17 @@ struct Timer {
   void release();
 };
 
-// Launchers (vx_eval.cu).
-int eval_level(const SysDev &sys, const CsfView &csf, const LevelGrid &grid, int mode,
-               double *d_lo, double *d_hi, uint8_t *d_keep, cudaStream_t s, Timer *tm,
-               int64_t *madds_out);
-// binary32 midpoint-radius evaluation that also flags the kept boxes whose enclosure is
-// tight for some polynomial (|m| >= theta r): d_tight[i] = keep[i] && tight(i).
-int eval_level_tight(const SysDev &sys, const CsfView &csf, const LevelGrid &grid, float theta,
-                     uint8_t *d_keep, uint8_t *d_tight, cudaStream_t s, Timer *tm,
-                     int64_t *madds_out);
+// Launcher (vx_eval.cu): one level in one arithmetic.  d_keep[i] = 0 iff the box is
+// excluded; d_flag (nullable) marks the kept boxes to re-evaluate in binary64: for
+// ARITH_F32_MIDRAD those with |m| >= theta r for some polynomial, for ARITH_F32_CERT those
+// inside the error band of some polynomial.
+enum Arith { ARITH_F64 = 0, ARITH_F32_MIDRAD = 1, ARITH_F32_CERT = 2 };
+int eval_level_raw(const SysDev &sys, const CsfView &csf, const LevelGrid &grid, int arith,
+                   double *d_lo, double *d_hi, uint8_t *d_keep, uint8_t *d_flag, float theta,
+                   cudaStream_t s, Timer *tm, int64_t *madds_out);
+// Reads (synchronising `s`) and clears the device status word that a kernel sets when a
+// bounded wait gives up; *status != 0 means the last evaluations are not to be trusted.
+int take_device_status(cudaStream_t s, int *status);
 
 // Integer kernels (vx_csf.cu).  Objects own one device allocation each.
 struct CsfObj {

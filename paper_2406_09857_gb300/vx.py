@@ -17,7 +17,7 @@ LIB_PATH = os.path.join(HERE, "_build", "libvx.so")
 
 OK, EINVAL, ENOMEM, ECAPACITY, EOVERFLOW, ETIMEOUT, ECUDA = 0, -1, -2, -3, -4, -5, -6
 KMAX, MAXPOLY, MAXLEVEL = 4, 8, 24
-FP64, FP32_MIDRAD = 0, 1
+FP64, FP32_MIDRAD, FP32 = 0, 1, 2
 
 _lib = None
 
@@ -55,6 +55,8 @@ def lib() -> ctypes.CDLL:
         "vx_system_create": ([P, i32, P, PP], i32),
         "vx_system_free": ([P], None),
         "vx_system_info": ([P, P, P, P], i32),
+        "vx_system_device_bytes": ([P, P], i32),
+        "vx_kernel_launches": ([], i64),
         "vx_csf_build": ([i32, i32, P, i64, P, PP], i32),
         "vx_csf_free": ([P], None),
         "vx_csf_nodes": ([P, P, P, P], i32),
@@ -79,6 +81,11 @@ def lib() -> ctypes.CDLL:
         f.restype = res
     _lib = L
     return L
+
+
+def kernel_launches() -> int:
+    """Kernels launched by libvx in this process so far."""
+    return int(lib().vx_kernel_launches())
 
 
 def declared_symbols():
@@ -157,6 +164,11 @@ class System:
         M = np.zeros((self.npoly, self.k + 1), dtype=np.int64)
         _check(lib().vx_system_info(self.handle, ctypes.byref(k), ctypes.byref(n), _np_ptr(M)))
         return int(k.value), int(n.value), M
+
+    def device_bytes(self) -> int:
+        b = ctypes.c_int64()
+        _check(lib().vx_system_device_bytes(self.handle, ctypes.byref(b)))
+        return int(b.value)
 
     def free(self):
         if self.handle:

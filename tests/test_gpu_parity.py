@@ -245,6 +245,47 @@ def test_enclose_fp64_equals_oracle(vx, name):
     assert np.array_equal(st["madds"], ref["work"])
 
 
+@pytest.mark.parametrize("name", sorted(ENCLOSE_CASES))
+def test_enclose_fp32_certified_equals_oracle_every_level(vx, name):
+    # binary32 with binary64-certified decisions: every level is the binary64 level
+    polys, dom, depth = ENCLOSE_CASES[name]()
+    ref = oracle.enclose(polys, dom, depth)
+    res = vx.enclose(polys, dom, depth, vx.make_opts(vx.FP32))
+    st = res.stats()
+    assert np.array_equal(res.boxes(), ref["tuples"])
+    assert np.array_equal(st["tested"], ref["tested"])
+    assert np.array_equal(st["kept"], ref["kept"])
+    assert np.array_equal(st["nodes"], ref["nodes"])
+    if name in ("circle", "sphere"):
+        # the zero set passes through grid points: some boxes have an endpoint exactly 0 and
+        # can only be decided in binary64
+        assert st["recheck"].sum() > 0
+
+
+@pytest.mark.parametrize("k,d,npoly,level,density,n,domain", EVAL_CASES)
+def test_eval_level_fp32_certified_decisions(vx, k, d, npoly, level, density, n, domain):
+    polys = synth.random_small(k, d, npoly, 1000 + 10 * k + d, density=density)
+    dom = np.asarray(domain) if domain is not None else synth.cube(k)
+    t = synth.random_tuples(k, level, n, 77 + k)
+    sysv = vx.System(polys)
+    c = vx.csf_build(k, level, dev(t))
+    keep, lo, hi = vx.csf_eval_level(sysv, c, dom, vx.FP32, values=True)
+    lo_r, hi_r, keep_r, _ = oracle.eval_csf(polys, dom, level, t)
+    assert np.array_equal(host(keep), keep_r)
+    # the binary32 bounds are bounds: around the binary64 ones up to rounding
+    assert np.all(host(lo) <= hi_r) and np.all(host(hi) >= lo_r)
+
+
+def test_eval_level_fp32_certified_kostlan_d100(vx):
+    s = synth.curve()
+    t = synth.random_tuples(3, 8, 3000, 19)
+    sysv = vx.System(s.polys)
+    c = vx.csf_build(3, 8, dev(t))
+    keep = vx.csf_eval_level(sysv, c, s.domain, vx.FP32)
+    _, _, keep_r, _ = oracle.eval_csf(s.polys, s.domain, 8, t)
+    assert np.array_equal(host(keep), keep_r)
+
+
 @pytest.mark.parametrize("name", ["plain-k2-d20-depth8", "k3-d6-2polys", "surface-d12",
                                   "asym-domain", "k4-d3"])
 def test_enclose_fp32_midrad(vx, name):

@@ -13,9 +13,10 @@ box-evals/s = (sum over levels of the boxes tested) / time.
 
   python bench.py [--gpus N --steps K --warmup W] [--impl reference]
 
-For N > 1 (torchrun, one rank per GPU) each rank encloses its own x_1-slab of the domain
-(no data exchange; paper_2406_09857_gb300/shard.py) and the value is the boxes evaluated by
-all ranks over the slowest rank's time.  ``--impl reference`` times the CPU oracle on a
+For N = 2^s > 1 (torchrun, one rank per GPU) rank r runs Algorithm 3 from level s on the boxes
+with x_1 index r (no data exchange; paper_2406_09857_gb300/shard.py), which yields exactly its
+share of the single-GPU result; the value is the boxes evaluated by all ranks over the slowest
+rank's time.  ``--impl reference`` times the CPU oracle on a
 bounded sample of the same workload instead.
 """
 from __future__ import annotations
@@ -45,9 +46,10 @@ WORKLOAD = ("curve: 2 trivariate Kostlan polynomials of total degree 100 on [-1,
 SMS, SM_MHZ = 152, 2070.0
 FP32_PEAK_T = SMS * 128 * SM_MHZ * 1e6 / 1e12  # 40.3 T instructions/s
 FP64_PEAK_T = SMS * 2 * SM_MHZ * 1e6 / 1e12    # 0.63 T instructions/s
-# FMA-pipe instructions of one interval multiply-add: binary32 certified = 2 directed FMAs for
-# the endpoints + 3 for the error bound; binary64 = 2 directed multiplies + 2 directed adds.
-OPS_PER_MADD = {"fp32": 5, "fp64": 4}
+# FMA-pipe lane operations of one interval multiply-add: binary32 certified = 2 directed FMAs
+# for the endpoints (one paired instruction) + 2 for the error bound; binary64 = 2 directed
+# multiplies + 2 directed adds.
+OPS_PER_MADD = {"fp32": 4, "fp64": 4}
 L2_FLUSH_BYTES = 512 << 20  # > 129 MB of L2
 
 
@@ -165,8 +167,8 @@ def config_dict(world: int, mode: str):
             "domain": "[-1,1]^3", "coefficients": "Kostlan: N(0,1) * sqrt(multinomial)",
             "mode": mode,
             "l2": "512 MB written between steps, outside the per-step CUDA events",
-            "parallelism": ("x1-slab shards, one enclosure per rank" if world > 1 else
-                            "single GPU")}
+            "parallelism": ("x1-slab shards: rank r starts at level log2(N) from the boxes "
+                            "with x1 index r" if world > 1 else "single GPU")}
 
 
 def run_reference(args):
@@ -235,8 +237,18 @@ def run_gpu(args):
     barrier()
     vx.lib()
     s = synth.curve()
-    dom, depth, x1_offset = shard.rank_problem(s.domain, s.depth, rank, world)
+    dom, depth = s.domain, s.depth
     sysv = vx.System(s.polys)
+    start = None
+    if world > 1:
+        lvl0, t0 = shard.rank_start(s.k, depth, rank, world)
+        start = vx.csf_build(s.k, lvl0, torch.from_numpy(t0).cuda())
+
+    def enclose_once(mode, timing):
+        o = vx.make_opts(mode, timing=timing)
+        if start is None:
+            return vx.enclose_system(sysv, dom, depth, o, stream)
+        return vx.enclose_from(sysv, start, dom, depth, o, stream)
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
     stream = torch.cuda.current_stream()
 
@@ -248,7 +260,7 @@ def run_gpu(args):
             e0 = torch.cuda.Event(enable_timing=True)
             e1 = torch.cuda.Event(enable_timing=True)
             e0.record(stream)
-            r = vx.enclose_system(sysv, dom, depth, vx.make_opts(mode, timing=timing), stream)
+            r = enclose_once(mode, timing)
             e1.record(stream)
             e1.synchronize()
             ms.append(e0.elapsed_time(e1))
@@ -317,7 +329,7 @@ def run_gpu(args):
         share = {n: round(x["ms"] / sum(y["ms"] for y in tot.values()), 4) for n, x in tot.items()
                  if x["launches"]}
         return {"kernel": top, "bound": "alu", "achieved": achieved, "peak": peak_t,
-                "unit": "T instr/s (FMA pipe)", "frac": achieved / peak_t, "traffic": None,
+                "unit": "T FMA-pipe lane-ops/s", "frac": achieved / peak_t, "traffic": None,
                 "launches": v["launches"], "avg_launch_ms": per_launch_ms,
                 "madds_per_launch": v["work"] / v["launches"], "time_share": share}
 
@@ -326,24 +338,35 @@ def run_gpu(args):
 
     # ---- end to end through the host API -----------------------------------------------------
     log("[bench] e2e")
-    h2d = sysv.device_bytes()
     polys_host = s.polys
-    vx.enclose(polys_host, dom, depth, vx.make_opts(vx.FP32)).free()
+
+    def e2e_once():
+        """Host polynomials in, host boxes out, through the public API."""
+        if world == 1:
+            r = vx.enclose(polys_host, dom, depth, vx.make_opts(vx.FP32))
+            return r, sysv.device_bytes()
+        sv = vx.System(polys_host)
+        st = vx.csf_build(s.k, lvl0, torch.from_numpy(t0).cuda())
+        r = vx.enclose_from(sv, st, dom, depth, vx.make_opts(vx.FP32))
+        return r, sv.device_bytes() + t0.nbytes
+
+    e2e_once()[0].free()
     ne2e = max(1, min(args.steps, 2))
     torch.cuda.synchronize()
     barrier()
     w0 = time.perf_counter()
-    e2e_evals, d2h = 0, 0
+    e2e_evals, d2h, h2d = 0, 0, 0
     for _ in range(ne2e):
-        r = vx.enclose(polys_host, dom, depth, vx.make_opts(vx.FP32))
+        r, hb = e2e_once()
         b = r.boxes()  # device -> host copy of the result
         e2e_evals += int(r.stats()["tested"].sum())
         d2h += b.nbytes
+        h2d += hb
         r.free()
     torch.cuda.synchronize()
     e2e_s = reduce(time.perf_counter() - w0, torch.distributed.ReduceOp.MAX if world > 1 else None)
     e2e_evals = reduce(e2e_evals, torch.distributed.ReduceOp.SUM if world > 1 else None)
-    e2e = {"value": e2e_evals / e2e_s, "unit": UNIT, "h2d_bytes_per_step": h2d,
+    e2e = {"value": e2e_evals / e2e_s, "unit": UNIT, "h2d_bytes_per_step": h2d // ne2e,
            "d2h_bytes_per_step": d2h // ne2e,
            "what": "vx_enclose from host polynomials (pack + upload) to host boxes"}
 
@@ -393,6 +416,24 @@ def run_gpu(args):
     return 0
 
 
+def run_profile_case(args):
+    """One enclosure of the workload to --profile-case DEPTH (a small case for ncu captures)."""
+    import torch
+
+    from paper_2406_09857_gb300 import synth, vx
+
+    torch.cuda.set_device(0)
+    s = synth.curve()
+    mode = {"fp32": vx.FP32, "fp64": vx.FP64, "midrad": vx.FP32_MIDRAD}[args.mode]
+    r = vx.enclose_system(vx.System(s.polys), s.domain, args.profile_case, vx.make_opts(mode))
+    torch.cuda.synchronize()
+    st = r.stats()
+    print(json.dumps({"profile_case_depth": args.profile_case, "mode": args.mode,
+                      "boxes": int(st["kept"][-1]), "tested": st["tested"].tolist(),
+                      "ms": r.elapsed_ms()}))
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser(description=__doc__.split("\n\n")[0])
     ap.add_argument("--gpus", type=int, default=1)
@@ -402,7 +443,13 @@ def main():
     ap.add_argument("--cpu-budget", type=float, default=20.0,
                     help="seconds of CPU oracle work for the cpu_baseline sample")
     ap.add_argument("--no-cpu", action="store_true", help="skip the cpu_baseline sample")
+    ap.add_argument("--profile-case", type=int, default=None, metavar="DEPTH",
+                    help="run one enclosure of the workload to DEPTH and exit (for ncu)")
+    ap.add_argument("--mode", choices=["fp32", "fp64", "midrad"], default="fp32",
+                    help="arithmetic of --profile-case")
     args = ap.parse_args()
+    if args.profile_case is not None:
+        return run_profile_case(args)
     if args.impl == "reference":
         return run_reference(args)
     return run_gpu(args)

@@ -155,6 +155,15 @@ int vx_csf_compact(const vx_csf *in, const uint8_t *d_keep, int32_t *d_index, vo
  * result is complete. */
 int vx_enclose_system(const vx_system *sys, const double *h_domain, int32_t depth,
                       const vx_opts *opts, void *stream, vx_result **out);
+/* Algorithm 3 with the set S initialised to the boxes of `start` (a CSF of level l0 <= depth,
+ * borrowed): levels l0..depth are tested and the survivors of level `depth` returned.  The
+ * survivors of the finest level do not depend on how coarser levels were pruned (interval
+ * Horner with outward rounding is inclusion-isotone on an exact grid), so starting from a
+ * subset of a level gives exactly the full run's survivors that descend from that subset:
+ * independent x_1-slabs of one problem can run on different GPUs.  Statistics of levels below
+ * l0 are zero. */
+int vx_enclose_from(const vx_system *sys, const vx_csf *start, const double *h_domain,
+                    int32_t depth, const vx_opts *opts, void *stream, vx_result **out);
 /* The same from host polynomials: packs and uploads them, runs on a private stream, and
  * leaves the result's boxes readable through vx_result_boxes. */
 int vx_enclose(const vx_poly *F_list, int32_t npoly, const double *h_domain, int32_t depth,

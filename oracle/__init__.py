@@ -50,6 +50,7 @@ def lib():
         L.orc_eval_grid.argtypes = sysargs + [P, P, P, P, i64, P, P, P, P]
         L.orc_csf.argtypes = [i32, P, i64, P, P, P]
         L.orc_enclose.argtypes = sysargs + [P, i32, ctypes.POINTER(P)]
+        L.orc_enclose_from.argtypes = sysargs + [P, i32, P, i64, i32, ctypes.POINTER(P)]
         L.orc_result_count.argtypes = [P]
         L.orc_result_count.restype = i64
         L.orc_result_copy.argtypes = [P, P, P, P, P, P]
@@ -60,6 +61,7 @@ def lib():
         L.orc_prim.argtypes = [i32, P, P, i64, P]
         L.orc_imul.argtypes = [P, P, P, P, i64, P, P]
         for f in ("orc_eval_csf", "orc_eval_boxes", "orc_eval_grid", "orc_csf", "orc_enclose",
+                  "orc_enclose_from",
                   "orc_brute_force", "orc_eval_grid_complex", "orc_domain_exact"):
             getattr(L, f).restype = i32
         _lib = L
@@ -173,14 +175,24 @@ def csf(tuples, k):
     return N, labs, ptrs
 
 
-def enclose(polys, domain, depth):
-    """Algorithm 3 to ``depth``: survivors of the last level plus per-level statistics."""
+def enclose(polys, domain, depth, start_level=0, start=None):
+    """Algorithm 3 to ``depth``: survivors of the last level plus per-level statistics.
+
+    With ``start`` (lex-sorted unique box indices of level ``start_level``) the set S starts
+    there instead of at the whole domain; the statistics cover levels 0..depth (zeros before
+    start_level)."""
     k, npoly, off, E, C = pack(polys)
     dom = np.ascontiguousarray(np.asarray(domain, dtype=np.float64).reshape(-1))
     res = ctypes.c_void_p()
     L = lib()
-    _check(L.orc_enclose(k, npoly, _p(off), _p(E), _p(C), _p(dom), int(depth), ctypes.byref(res)),
-           "orc_enclose")
+    if start is None:
+        _check(L.orc_enclose(k, npoly, _p(off), _p(E), _p(C), _p(dom), int(depth),
+                             ctypes.byref(res)), "orc_enclose")
+    else:
+        st = _tuples(start, k)
+        _check(L.orc_enclose_from(k, npoly, _p(off), _p(E), _p(C), _p(dom), int(start_level),
+                                  _p(st), st.shape[0], int(depth), ctypes.byref(res)),
+               "orc_enclose_from")
     try:
         n = L.orc_result_count(res)
         tup = np.empty((n, k), dtype=np.int32)

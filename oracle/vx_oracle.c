@@ -583,13 +583,27 @@ void orc_result_free(orc_result *R) {
   free(R);
 }
 
+/* Algorithm 3 with S initialised to the boxes start[n0][k] (lex-sorted, unique) of level
+ * start_level: levels start_level..depth are tested.  orc_enclose is the case S = {domain}. */
+int orc_enclose_from(int k, int npoly, const int64_t *term_off, const int32_t *exps,
+                     const double *coefs, const double *domain, int start_level,
+                     const int32_t *start, int64_t n0, int depth, orc_result **out);
+
 int orc_enclose(int k, int npoly, const int64_t *term_off, const int32_t *exps, const double *coefs,
                 const double *domain, int depth, orc_result **out) {
+  int32_t root[ORC_KMAX] = {0};
+  return orc_enclose_from(k, npoly, term_off, exps, coefs, domain, 0, root, 1, depth, out);
+}
+
+int orc_enclose_from(int k, int npoly, const int64_t *term_off, const int32_t *exps,
+                     const double *coefs, const double *domain, int start_level,
+                     const int32_t *start, int64_t n0, int depth, orc_result **out) {
   int old = fegetround();
   int rc = check_system(k, npoly, term_off);
   *out = 0;
   if (rc != ORC_OK) return rc;
   if (depth < 0 || depth > 30 || npoly > 16) return ORC_EINVAL;
+  if (start_level < 0 || start_level > depth || n0 < 0) return ORC_EINVAL;
   if (!orc_domain_exact(k, domain, depth)) return ORC_EINVAL;
   fesetround(FE_DOWNWARD);
   orc_result *R = (orc_result *)calloc(1, sizeof(orc_result));
@@ -610,9 +624,10 @@ int orc_enclose(int k, int npoly, const int64_t *term_off, const int32_t *exps, 
     fesetround(old);
     return rc;
   }
-  int64_t n = 1;
-  int32_t *S = (int32_t *)calloc((size_t)k, sizeof(int32_t)); /* S = { the whole domain } */
-  for (int l = 0; rc == ORC_OK && l <= depth; ++l) {
+  int64_t n = n0;
+  int32_t *S = (int32_t *)malloc(sizeof(int32_t) * (size_t)(n0 > 0 ? n0 : 1) * k);
+  if (S) memcpy(S, start, sizeof(int32_t) * (size_t)n0 * k);
+  for (int l = start_level; S && rc == ORC_OK && l <= depth; ++l) {
     csf T;
     boxsrc B = {domain, l, 0, 0, 0};
     rc = csf_build(&T, k, S, n);

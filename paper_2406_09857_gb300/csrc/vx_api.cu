@@ -413,26 +413,31 @@ static int eval_decide(const SysDev &sys, const CsfView &c, const LevelGrid &g, 
   if (flagged) VX_CHECK(dmalloc((void **)&flag, (size_t)std::max<int64_t>(n, 1), s));
   int rc = eval_level_raw(sys, c, g, arith, d_lo, d_hi, keep, flag, theta, s, tm, madds);
   if (rc == VX_OK && flagged && n > 0) {
-    CsfObj sub;
-    int32_t *idx = nullptr;
+    // the flagged leaves as a tree of their own (their tuples are increasing, being listed in
+    // leaf order), evaluated in binary64; the decisions go back to their places
+    int32_t *idx = nullptr, *tup = nullptr;
     uint8_t *subkeep = nullptr;
-    rc = dmalloc((void **)&idx, (size_t)n * 4, s);
-    if (rc == VX_OK) rc = csf_prune(c, flag, 0, idx, s, &sub, tm);
-    if (rc == VX_OK) {
-      const int64_t ns = sub.v.N[k - 1];
-      *nrecheck = ns;
-      if (ns > 0) {
-        rc = dmalloc((void **)&subkeep, (size_t)ns, s);
-        int64_t w2 = 0;
-        if (rc == VX_OK)
-          rc = eval_level_raw(sys, sub.v, g, ARITH_F64, nullptr, nullptr, subkeep, nullptr, 0.f,
-                              s, tm, &w2);
-        *madds += w2;
-        if (rc == VX_OK) rc = scatter_keep(idx, subkeep, ns, keep, s);
-      }
+    int64_t ns = 0;
+    if (tm && tm->on) rc = tm->begin(KK_RECHECK, n);
+    if (rc == VX_OK) rc = flag_indices(flag, n, s, &idx, &ns);
+    if (rc == VX_OK && tm && tm->on) rc = tm->end();
+    *nrecheck = ns;
+    if (rc == VX_OK && ns > 0) {
+      CsfObj sub;
+      rc = dmalloc((void **)&tup, (size_t)ns * k * 4, s);
+      if (rc == VX_OK) rc = csf_tuples_of(c, idx, ns, tup, s);
+      if (rc == VX_OK) rc = csf_build_dev(k, c.level, tup, ns, s, &sub, tm);
+      if (rc == VX_OK) rc = dmalloc((void **)&subkeep, (size_t)ns, s);
+      int64_t w2 = 0;
+      if (rc == VX_OK)
+        rc = eval_level_raw(sys, sub.v, g, ARITH_F64, nullptr, nullptr, subkeep, nullptr, 0.f, s,
+                            tm, &w2);
+      *madds += w2;
+      if (rc == VX_OK) rc = scatter_keep(idx, subkeep, ns, keep, s);
       csf_release(&sub);
     }
     dfree(subkeep, s);
+    dfree(tup, s);
     dfree(idx, s);
   }
   dfree(flag, s);
@@ -732,8 +737,15 @@ static int level0(int k, cudaStream_t s, CsfObj *o) {
   return set_ptr_sentinels(o->v, s);
 }
 
+static int csf_copy(const CsfObj &src, cudaStream_t s, CsfObj *dst) {
+  VX_CHECK(csf_alloc(dst, src.v.k, src.v.level, src.v.N, s));
+  // the same counts give the same layout inside the allocation
+  VX_CUDA(cudaMemcpyAsync(dst->mem, src.mem, src.bytes, cudaMemcpyDeviceToDevice, s));
+  return VX_OK;
+}
+
 static int enclose_impl(const vx_system *sys, const double *dom, int depth, const vx_opts *o,
-                        cudaStream_t s, vx_result *R) {
+                        cudaStream_t s, vx_result *R, const CsfObj *start) {
   const int k = sys->dev.k;
   vx_opts opts{};
   if (o) opts = *o;
@@ -767,8 +779,21 @@ static int enclose_impl(const vx_system *sys, const double *dom, int depth, cons
   VX_CUDA(cudaEventCreate(&ev1));
   VX_CUDA(cudaEventRecord(ev0, s));
   CsfObj cur;
-  int rc = level0(k, s, &cur);
-  for (int l = 0; l <= depth && rc == VX_OK; ++l) {
+  int rc = VX_OK;
+  int l0 = 0;
+  if (start) {
+    if (start->v.k != k || start->v.level > depth) {
+      set_error("enclose: the start tree has k = %d, level %d (system k = %d, depth %d)",
+                start->v.k, start->v.level, k, depth);
+      rc = VX_EINVAL;
+    } else {
+      l0 = start->v.level;
+      rc = csf_copy(*start, s, &cur);
+    }
+  } else {
+    rc = level0(k, s, &cur);
+  }
+  for (int l = l0; l <= depth && rc == VX_OK; ++l) {
     rc = make_grid(k, dom, l, &g);
     if (rc != VX_OK) break;
     const int64_t n = cur.v.N[k - 1];
@@ -847,7 +872,28 @@ int vx_enclose_system(const vx_system *sys, const double *h_domain, int32_t dept
   *out = nullptr;
   vx_result *R = new (std::nothrow) vx_result();
   if (!R) return VX_ENOMEM;
-  int rc = enclose_impl(sys, h_domain, depth, opts, as_stream(stream), R);
+  int rc = enclose_impl(sys, h_domain, depth, opts, as_stream(stream), R, nullptr);
+  if (rc != VX_OK) {
+    csf_release(&R->fin);
+    R->tm.release();
+    delete R;
+    return rc;
+  }
+  *out = R;
+  return VX_OK;
+}
+
+int vx_enclose_from(const vx_system *sys, const vx_csf *start, const double *h_domain,
+                    int32_t depth, const vx_opts *opts, void *stream, vx_result **out) {
+  clear_error();
+  if (!sys || !start || !out) {
+    set_error("vx_enclose_from: NULL argument");
+    return VX_EINVAL;
+  }
+  *out = nullptr;
+  vx_result *R = new (std::nothrow) vx_result();
+  if (!R) return VX_ENOMEM;
+  int rc = enclose_impl(sys, h_domain, depth, opts, as_stream(stream), R, &start->o);
   if (rc != VX_OK) {
     csf_release(&R->fin);
     R->tm.release();

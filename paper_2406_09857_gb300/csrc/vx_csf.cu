@@ -595,6 +595,30 @@ __global__ void k_tuples(CsfView c, int32_t *t) {
   }
 }
 
+// indices of the nonzero bytes, in increasing order
+struct ByteFlagSrc {
+  const uint8_t *f;
+  __device__ unsigned flags(int64_t i, bool) const { return f[i] ? 1u : 0u; }
+};
+struct IndexEmit {
+  int32_t *idx;
+  __device__ void operator()(int64_t i, unsigned m, const int32_t *excl) const {
+    if (m) idx[excl[0]] = (int32_t)i;
+  }
+};
+
+__global__ void k_tuples_of(CsfView c, const int32_t *__restrict__ idx, int64_t n, int32_t *t) {
+  const int k = c.k;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
+    int64_t p = idx[i];
+    for (int d = k - 1; d >= 0; --d) {
+      t[i * k + d] = c.lab[d][p];
+      if (d > 0) p = c.par[d][p];
+    }
+  }
+}
+
 __global__ void k_scatter(const int32_t *__restrict__ index, const uint8_t *__restrict__ sub,
                           int64_t n, uint8_t *keep) {
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
@@ -668,6 +692,37 @@ int csf_prune(const CsfView &in, const uint8_t *d_keep, int split, int32_t *d_in
 int csf_tuples_dev(const CsfView &c, int32_t *d_tuples, cudaStream_t s) {
   if (c.N[c.k - 1] == 0) return VX_OK;
   k_tuples<<<blocks_for(c.N[c.k - 1]), 256, 0, s>>>(c, d_tuples);
+  note_launch();
+  VX_LAUNCH_CHECK();
+  return VX_OK;
+}
+
+int flag_indices(const uint8_t *d_flags, int64_t n, cudaStream_t s, int32_t **d_idx,
+                 int64_t *count) {
+  *d_idx = nullptr;
+  *count = 0;
+  if (n > INT32_MAX) {
+    set_error("flag_indices: %lld entries exceed 32-bit indices", (long long)n);
+    return VX_EOVERFLOW;
+  }
+  ByteFlagSrc src{d_flags};
+  int32_t *scratch = nullptr;
+  int64_t ntiles = 0;
+  int32_t tot[1] = {0};
+  int rc = scan_prepare<1>(src, n, s, &scratch, &ntiles, tot);
+  if (rc == VX_OK && tot[0] > 0) {
+    rc = dmalloc((void **)d_idx, (size_t)tot[0] * 4, s);
+    if (rc == VX_OK) rc = scan_emit<1>(src, IndexEmit{*d_idx}, n, scratch, ntiles, s);
+  }
+  dfree(scratch, s);
+  if (rc == VX_OK) *count = tot[0];
+  return rc;
+}
+
+int csf_tuples_of(const CsfView &c, const int32_t *d_idx, int64_t n, int32_t *d_tuples,
+                  cudaStream_t s) {
+  if (n == 0) return VX_OK;
+  k_tuples_of<<<blocks_for(n), 256, 0, s>>>(c, d_idx, n, d_tuples);
   note_launch();
   VX_LAUNCH_CHECK();
   return VX_OK;

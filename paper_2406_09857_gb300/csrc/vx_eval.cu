@@ -229,17 +229,14 @@ struct A32C {
   }
   template <int CLS>
   static __device__ __forceinline__ V step(V J, const X &x, V A) {
-    // Each bound is the smaller of the two candidate products, each rounded down once (RD is
-    // monotone, so this is RD of the selected product plus A): one paired FMA per bound.
+    // both bounds from one paired round-down FMA on the natural pairs (lo, -hi)
     float2 r;
     if (CLS > 0) {  // X >= 0: lo from lo_J, hi from hi_J
-      const float2 pl = __ffma2_rd(make_float2(J.x, J.x), make_float2(x.l, x.h), make_float2(A.x, A.x));
-      const float2 ph = __ffma2_rd(make_float2(J.y, J.y), make_float2(x.l, x.h), make_float2(A.y, A.y));
-      r = make_float2(fminf(pl.x, pl.y), fminf(ph.x, ph.y));
+      const float2 u = make_float2((__float_as_int(J.x) >= 0) ? x.l : x.h, (J.y <= 0.f) ? x.h : x.l);
+      r = __ffma2_rd(make_float2(J.x, J.y), u, make_float2(A.x, A.y));
     } else if (CLS < 0) {  // X <= 0: lo from hi_J = -J.y, hi from lo_J
-      const float2 pl = __ffma2_rd(make_float2(J.y, J.y), make_float2(x.nl, x.nh), make_float2(A.x, A.x));
-      const float2 ph = __ffma2_rd(make_float2(J.x, J.x), make_float2(x.nl, x.nh), make_float2(A.y, A.y));
-      r = make_float2(fminf(pl.x, pl.y), fminf(ph.x, ph.y));
+      const float2 u = make_float2((J.y <= 0.f) ? x.nl : x.nh, (__float_as_int(J.x) >= 0) ? x.nh : x.nl);
+      r = __ffma2_rd(make_float2(J.y, J.x), u, make_float2(A.x, A.y));
     } else {  // X straddles 0: hull of the four products, each bound rounded once
       const float jh = -J.y;
       r.x = fminf(fminf(__fmaf_rd(J.x, x.l, A.x), __fmaf_rd(J.x, x.h, A.x)),
@@ -376,54 +373,51 @@ __global__ void __launch_bounds__(kThreads)
   }
 }
 
-// Stage d (1 <= d < k-1) with the parent blocks in shared memory: CTA b takes the 128 nodes
-// b*128 .. b*128+127, whose parents (consecutive, the nodes being sorted by parent) number at
-// most maxpar; their node-major blocks are one contiguous range, brought in by TMA bulk copies
-// (cp.async.bulk, completion on an mbarrier) while the row offsets are loaded.  Every thread
-// then runs all fibres of its node reading shared memory: a broadcast when the lanes of a warp
-// share a parent.  CTAs whose nodes span more parents read their blocks from global memory.
+// Stage d (1 <= d < k-1) with the parent's block in shared memory.  CTA b takes parent
+// p = b / G and fibres g, g+G, ... (g = b % G) for all of p's children (the CSF child range
+// ptr[p] .. ptr[p+1]-1, blockDim at a time, one child per thread).  The parent's node-major
+// block is one contiguous range, brought in by TMA bulk copies (cp.async.bulk, completion on
+// an mbarrier) while the row offsets are loaded; every Horner step then reads shared memory
+// at an address common to the whole CTA (a broadcast).
 template <class AR>
-__global__ void __launch_bounds__(kThreads)
+__global__ void __launch_bounds__(512)
     k_stage_tma(const StageDev st, const int32_t *__restrict__ lab,
-                const int32_t *__restrict__ par, const typename AR::V *__restrict__ in,
+                const int32_t *__restrict__ pptr, const typename AR::V *__restrict__ in,
                 typename AR::V *__restrict__ out, int64_t out_estride, int64_t out_nstride,
-                int64_t nnodes, int maxpar, AxisGrid g) {
+                int G, AxisGrid g) {
   using V = typename AR::V;
   extern __shared__ __align__(128) unsigned char smem[];
   uint64_t *bar = reinterpret_cast<uint64_t *>(smem);
   int32_t *s_rowoff = reinterpret_cast<int32_t *>(smem + 128);
   V *s_blk = reinterpret_cast<V *>(smem + 128 + ((st.maxlen + 1) * 4 + 127) / 128 * 128);
-  const int64_t first = (int64_t)blockIdx.x * kThreads;
-  const int64_t last = (first + kThreads < nnodes ? first + kThreads : nnodes) - 1;
-  const int64_t p0 = __ldg(par + first), p1 = __ldg(par + last);
-  const bool staged = p1 - p0 < maxpar;
+  const int64_t p = blockIdx.x / G;
+  const int grp = (int)(blockIdx.x % G);
+  const int64_t c0 = __ldg(pptr + p), c1 = __ldg(pptr + p + 1);
   if (threadIdx.x == 0) {
     mbar_init(bar, 1);
-    if (staged) {
-      const uint64_t bytes = (uint64_t)(p1 - p0 + 1) * st.blk_in * sizeof(V);
-      mbar_arrive_expect_tx(bar, (uint32_t)bytes);
-      const char *src = reinterpret_cast<const char *>(in + p0 * st.blk_in);
-      char *dst = reinterpret_cast<char *>(s_blk);
-      for (uint64_t o = 0; o < bytes; o += 32768) {
-        const uint32_t n = (uint32_t)(bytes - o < 32768 ? bytes - o : 32768);
-        bulk_copy_g2s(dst + o, src + o, n, bar);
-      }
+    const uint64_t bytes = (uint64_t)st.blk_in * sizeof(V);
+    mbar_arrive_expect_tx(bar, (uint32_t)bytes);
+    const char *src = reinterpret_cast<const char *>(in + p * st.blk_in);
+    char *dst = reinterpret_cast<char *>(s_blk);
+    for (uint64_t o = 0; o < bytes; o += 32768) {
+      const uint32_t n = (uint32_t)(bytes - o < 32768 ? bytes - o : 32768);
+      bulk_copy_g2s(dst + o, src + o, n, bar);
     }
   }
   for (int i = threadIdx.x; i <= st.maxlen; i += blockDim.x) s_rowoff[i] = st.rowoff[i];
   __syncthreads();
-  if (staged && !mbar_wait_bounded(bar, 0)) return;
-  const int64_t node = first + threadIdx.x;
-  const bool live = node < nnodes;
-  const int64_t nd = live ? node : last;
-  const int64_t p = __ldg(par + nd);
-  const V *base = staged ? s_blk + (p - p0) * st.blk_in : in + p * st.blk_in;
-  const typename AR::X x = AR::box(g, __ldg(lab + nd));
-  V *dst = out + node * out_nstride;
-  for (int f = 0; f < st.nfib; ++f) {
-    const int L = __ldg(st.fiblen + f);
-    const V J = horner_any<AR>(base, 1, s_rowoff, f, L, x);
-    if (live) dst[(int64_t)__ldg(st.outpos + f) * out_estride] = AR::store(J);
+  if (!mbar_wait_bounded(bar, 0)) return;
+  for (int64_t n0 = c0; n0 < c1; n0 += blockDim.x) {
+    const int64_t node = n0 + threadIdx.x;
+    const bool live = node < c1;
+    const int64_t nd = live ? node : c1 - 1;
+    const typename AR::X x = AR::box(g, __ldg(lab + nd));
+    V *dst = out + node * out_nstride;
+    for (int f = grp; f < st.nfib; f += G) {
+      const int L = __ldg(st.fiblen + f);
+      const V J = horner_any<AR>(s_blk, 1, s_rowoff, f, L, x);
+      if (live) dst[(int64_t)__ldg(st.outpos + f) * out_estride] = AR::store(J);
+    }
   }
 }
 
@@ -514,6 +508,7 @@ int eval_level_t(const SysDev &sys, const CsfView &c, const LevelGrid &grid, dou
       off += (size_t)c.N[d] * sys.p[f].st[d].blk_out;
     }
   }
+
   for (int f = 0; f < sys.npoly && rc == VX_OK; ++f) {
     // stage d (1 <= d < k-1) stages its parents' blocks by TMA when the depth has enough
     // nodes to fill the GPU with 128-node CTAs and two parent blocks fit in shared memory
@@ -522,8 +517,8 @@ int eval_level_t(const SysDev &sys, const CsfView &c, const LevelGrid &grid, dou
     for (int d = 1; d + 1 < k; ++d) {
       const StageDev &st = sys.p[f].st[d];
       const size_t sm = 128 + ((size_t)(st.maxlen + 1) * 4 + 127) / 128 * 128 +
-                        2 * (size_t)st.blk_in * sizeof(V);
-      if (c.N[d] >= 152 * 4 * kThreads && sm <= kMaxDynSmem) {
+                        (size_t)st.blk_in * sizeof(V);
+      if (c.N[d] >= 152 * 4 * kThreads && c.N[d] >= 128 * c.N[d - 1] && sm <= kMaxDynSmem) {
         tma[d] = true;
         tma_smem[d] = sm;
       }
@@ -545,9 +540,15 @@ int eval_level_t(const SysDev &sys, const CsfView &c, const LevelGrid &grid, dou
           rc = VX_ECUDA;
           break;
         }
-        const int64_t blocks = (c.N[d] + kThreads - 1) / kThreads;
-        k_stage_tma<AR><<<(unsigned)blocks, kThreads, tma_smem[d], s>>>(
-            st, c.lab[d], c.par[d], in, buf[f][d], oe, on, c.N[d], 2, grid.ax[d]);
+        // one CTA per (parent, fibre group), threads ~ the average number of children
+        const int64_t np = c.N[d - 1];
+        const int64_t avg = c.N[d] / np;
+        const int threads = avg >= 512 ? 512 : (avg >= 256 ? 256 : 128);
+        int64_t G = (4 * 152 * 2 + np - 1) / np;
+        if (G > st.nfib) G = st.nfib;
+        if (G < 1) G = 1;
+        k_stage_tma<AR><<<(unsigned)(np * G), threads, tma_smem[d], s>>>(
+            st, c.lab[d], c.ptr[d - 1], in, buf[f][d], oe, on, (int)G, grid.ax[d]);
       } else {
         // fibre groups: enough warps to fill the GPU several times over
         const int64_t nchunk = (c.N[d] + 31) / 32;

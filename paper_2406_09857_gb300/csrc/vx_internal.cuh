@@ -167,6 +167,13 @@ int csf_prune(const CsfView &in, const uint8_t *d_keep, int split, int32_t *d_in
 // ptr[d][N[d]] = N[d+1] for every depth d < k-1.
 int set_ptr_sentinels(const CsfView &v, cudaStream_t s);
 int csf_tuples_dev(const CsfView &c, int32_t *d_tuples, cudaStream_t s);
+// Increasing indices i with d_flags[i] != 0 (device array owned by the caller, freed with
+// dfree; synchronises `s` to learn the count).
+int flag_indices(const uint8_t *d_flags, int64_t n, cudaStream_t s, int32_t **d_idx,
+                 int64_t *count);
+// Index tuples of the listed leaves, d_tuples[n][k].
+int csf_tuples_of(const CsfView &c, const int32_t *d_idx, int64_t n, int32_t *d_tuples,
+                  cudaStream_t s);
 int scatter_keep(const int32_t *d_index, const uint8_t *d_sub_keep, int64_t n, uint8_t *d_keep,
                  cudaStream_t s);
 

@@ -1,13 +1,14 @@
 """Partition of one enclosure across ranks (one GPU each), with no exchange of data.
 
-The boxes of the finest grid that Algorithm 3 returns do not depend on the order in which
-coarser boxes were pruned: interval Horner with outward rounding is inclusion-isotone and
-the grid is exact, so a box of level L survives iff it passes C0 at level L and at each of its
-ancestors, and every ancestor of a passing box passes.  Splitting the domain along x_1 into N
-(a power of two) equal slabs and enclosing slab r at depth L - log2(N) therefore gives exactly
-the level-L survivors whose x_1 index lies in [r 2^(L - log2 N), (r+1) 2^(L - log2 N)); the
-slabs concatenated in rank order are the single-GPU result in lexicographic order.  Only the
-coarsest log2(N) levels, where each rank holds one slab, are not evaluated.
+The boxes of the finest grid that Algorithm 3 returns do not depend on how coarser boxes were
+pruned: interval Horner with outward rounding is inclusion-isotone and the grid is exact, so a
+box of level L passes C0 only if each of its ancestors does, and the survivors of level L are
+exactly the level-L boxes that pass.  With N = 2^s ranks, rank r therefore starts Algorithm 3
+at level s from every box of that level whose x_1 index is r (an x_1-slab of the domain, all
+other indices free) and runs it to depth L on the full grid; its survivors are the single-GPU
+survivors with x_1 index in [r 2^(L-s), (r+1) 2^(L-s)), and the ranks' results concatenated in
+rank order are the single-GPU result in lexicographic order.  Levels below s are skipped and
+level s is evaluated unpruned, which changes the work but not the result.
 """
 from __future__ import annotations
 
@@ -20,21 +21,17 @@ def log2_exact(n: int) -> int:
     return n.bit_length() - 1
 
 
-def rank_problem(domain, depth: int, rank: int, world: int):
-    """(sub-domain, sub-depth, x_1 index offset) of rank ``rank`` out of ``world``."""
+def rank_start(k: int, depth: int, rank: int, world: int):
+    """(start level s, int32 [2^(s(k-1)), k] lex-sorted boxes of level s with x_1 index = rank)."""
     s = log2_exact(world)
     if s > depth:
         raise ValueError("%d ranks need depth >= %d" % (world, s))
-    dom = np.asarray(domain, dtype=np.float64).reshape(-1).copy()
-    lo, hi = dom[0], dom[1]
-    w = (hi - lo) / world  # exact on dyadic domains (division by a power of two)
-    dom[0] = lo + rank * w
-    dom[1] = lo + (rank + 1) * w
-    return dom, depth - s, rank << (depth - s)
-
-
-def to_global(tuples: np.ndarray, offset: int) -> np.ndarray:
-    out = np.array(tuples, dtype=np.int32, copy=True)
-    if out.size:
-        out[:, 0] += offset
-    return out
+    if not 0 <= rank < world:
+        raise ValueError("rank %d outside [0, %d)" % (rank, world))
+    side = 1 << s
+    rest = np.stack(np.meshgrid(*[np.arange(side, dtype=np.int32)] * (k - 1), indexing="ij"),
+                    axis=-1).reshape(-1, k - 1) if k > 1 else np.zeros((1, 0), dtype=np.int32)
+    t = np.empty((rest.shape[0], k), dtype=np.int32)
+    t[:, 0] = rank
+    t[:, 1:] = rest
+    return s, t

@@ -67,6 +67,7 @@ def lib() -> ctypes.CDLL:
         "vx_csf_compact": ([P, P, P, P, PP], i32),
         "vx_enclose_system": ([P, P, i32, P, P, PP], i32),
         "vx_enclose": ([P, i32, P, i32, P, PP], i32),
+        "vx_enclose_from": ([P, P, P, i32, P, P, PP], i32),
         "vx_result_boxes": ([P, P, P], i32),
         "vx_result_csf": ([P, PP], i32),
         "vx_result_stats": ([P, P, P, P, P, P, P], i32),
@@ -349,6 +350,17 @@ def enclose_system(system: System, domain, depth, opts: Opts | None = None, stre
     _check(lib().vx_enclose_system(system.handle, _np_ptr(dom), int(depth),
                                    ctypes.byref(opts) if opts is not None else None,
                                    _stream(stream), ctypes.byref(h)))
+    return Result(h, system.k, int(depth))
+
+
+def enclose_from(system: System, start: Csf, domain, depth, opts: Opts | None = None,
+                 stream=None) -> Result:
+    """Algorithm 3 from the boxes of ``start`` (vx_enclose_from)."""
+    dom = _domain(domain)
+    h = ctypes.c_void_p()
+    _check(lib().vx_enclose_from(system.handle, start.handle, _np_ptr(dom), int(depth),
+                                 ctypes.byref(opts) if opts is not None else None,
+                                 _stream(stream), ctypes.byref(h)))
     return Result(h, system.k, int(depth))
 
 

@@ -323,3 +323,24 @@ def test_fp32_box_enclosure_contains_fp64(vx, k, d, level, seed):
     w64 = hi64 - lo64
     w32 = hi32 - lo32
     assert np.median(w32 / np.maximum(w64, 1e-300)) < 1.5
+
+
+@pytest.mark.parametrize("world", [2, 4, 8])
+def test_enclose_from_slab_starts_reproduce_full(vx, world):
+    from paper_2406_09857_gb300 import shard
+
+    polys, dom, depth = ENCLOSE_CASES["k3-d6-2polys"]()
+    full = oracle.enclose(polys, dom, depth)["tuples"]
+    sysv = vx.System(polys)
+    parts = []
+    for r in range(world):
+        s, start = shard.rank_start(3, depth, r, world)
+        c = vx.csf_build(3, s, dev(start))
+        for mode in (vx.FP64, vx.FP32):
+            res = vx.enclose_from(sysv, c, dom, depth, vx.make_opts(mode))
+            b = res.boxes()
+            if mode == vx.FP64:
+                parts.append(b)
+            else:
+                assert np.array_equal(b, parts[-1])
+    assert np.array_equal(np.concatenate(parts, axis=0), full)

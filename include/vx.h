@@ -136,6 +136,30 @@ int vx_csf_tuples(const vx_csf *csf, int32_t *d_tuples, void *stream);
 int vx_csf_eval_level(const vx_system *sys, const vx_csf *csf, const double *h_domain,
                       int32_t mode, double *d_lo, double *d_hi, uint8_t *d_keep, void *stream);
 
+/* Level evaluation that allocates nothing, for callers that cannot allocate device memory
+ * while they run: a host framework that owns the device's memory as a fixed budget (where an
+ * allocation by a library would fail or upset its accounting), or a latency-bound loop that
+ * must not risk the synchronisation or the out-of-memory failure an allocation can bring.
+ * The paper has no counterpart; this is vx_csf_eval_level in VX_FP64 or VX_FP32_MIDRAD (the
+ * same kernels, the same outputs, bit for bit) with its scratch, the partial-evaluation
+ * blocks of depths 1..k-1, taken from one array of VX_STATIC_SCRATCH_BYTES bytes of device
+ * memory that the library declares statically: every device that loads the library holds it
+ * until the process exits.  The caller passes inputs and outputs as for vx_csf_eval_level.
+ *   - VX_ECAPACITY (with the needed size in vx_last_error) when the blocks do not fit: at most
+ *     sum over polynomials and depths d < k of N_d * M_d * (16 bytes for VX_FP64, 8 for
+ *     VX_FP32_MIDRAD), each block rounded up to 256 bytes; VX_EINVAL for VX_FP32.
+ *   - No cudaMalloc, cudaFree or allocating library routine is called.  The first call on a
+ *     device looks up the array's device address (cudaGetSymbolAddress) with that device
+ *     current; make that first call before any stream capture.
+ *   - Every call shares the array and leaves its contents behind; each block read is written
+ *     earlier in the same call, so nothing needs clearing, but calls that overlap on the GPU
+ *     (other streams, other host threads) race on it and must be serialised by the caller.
+ *   - Returns once the evaluation is complete (synchronises `stream`). */
+#define VX_STATIC_SCRATCH_BYTES (64ull << 20)
+int vx_csf_eval_level_static(const vx_system *sys, const vx_csf *csf, const double *h_domain,
+                             int32_t mode, double *d_lo, double *d_hi, uint8_t *d_keep,
+                             void *stream);
+
 /* Algorithm 3, one step: drops the leaves with d_keep[i] == 0 (and the inner nodes left
  * without leaves), bisects every remaining box 2^k ways and returns the CSF of level+1 (its
  * leaves are the 2^k children of each kept box, lexicographically ordered).  No sort: each

@@ -681,6 +681,33 @@ int vx_csf_eval_level(const vx_system *sys, const vx_csf *c, const double *h_dom
   return VX_OK;
 }
 
+int vx_csf_eval_level_static(const vx_system *sys, const vx_csf *c, const double *h_domain,
+                             int32_t mode, double *d_lo, double *d_hi, uint8_t *d_keep,
+                             void *stream) {
+  clear_error();
+  if (!sys || !c || !d_keep || (!d_lo) != (!d_hi) || c->o.v.k != sys->dev.k) {
+    set_error("vx_csf_eval_level_static: bad arguments");
+    return VX_EINVAL;
+  }
+  if (mode != VX_FP64 && mode != VX_FP32_MIDRAD) {
+    set_error("vx_csf_eval_level_static: mode %d is not available without allocation (VX_FP32 "
+              "re-evaluates boxes in trees of their own); use VX_FP64 or VX_FP32_MIDRAD", mode);
+    return VX_EINVAL;
+  }
+  LevelGrid g;
+  VX_CHECK(make_grid(c->o.v.k, h_domain, c->o.v.level, &g));
+  cudaStream_t s = as_stream(stream);
+  VX_CHECK(eval_level_static(sys->dev, c->o.v, g, mode == VX_FP64 ? ARITH_F64 : ARITH_F32_MIDRAD,
+                             d_lo, d_hi, d_keep, s));
+  int st = 0;
+  VX_CHECK(take_device_status(s, &st));
+  if (st) {
+    set_error("vx_csf_eval_level_static: a bounded device wait gave up; outputs are not valid");
+    return VX_ETIMEOUT;
+  }
+  return VX_OK;
+}
+
 int vx_csf_subdivide(const vx_csf *in, const uint8_t *d_keep, void *stream, vx_csf **out) {
   clear_error();
   if (!in || !out || (!d_keep && in->o.v.N[in->o.v.k - 1] > 0)) {

@@ -481,10 +481,22 @@ int leaf_grid(int64_t items) {
   return (int)b;
 }
 
+// Bytes of partial-evaluation blocks a level needs (each block 256-byte aligned).
+template <class AR>
+size_t level_scratch_bytes(const SysDev &sys, const CsfView &c) {
+  size_t total = 0;
+  for (int f = 0; f < sys.npoly; ++f)
+    for (int d = 0; d + 1 < sys.k; ++d)
+      total += ((size_t)c.N[d] * sys.p[f].st[d].blk_out * sizeof(typename AR::V) + 255) & ~(size_t)255;
+  return total;
+}
+
+// ext_scratch != nullptr: the blocks are carved from it (ext_bytes long) and nothing is allocated.
 template <class AR>
 int eval_level_t(const SysDev &sys, const CsfView &c, const LevelGrid &grid, double *d_lo,
                  double *d_hi, uint8_t *d_keep, uint8_t *d_flag, float theta, cudaStream_t s,
-                 Timer *tm, int64_t *madds_out, int kind0) {
+                 Timer *tm, int64_t *madds_out, int kind0, void *ext_scratch = nullptr,
+                 size_t ext_bytes = 0) {
   using V = typename AR::V;
   const int k = sys.k;
   const int64_t nleaves = c.N[k - 1];
@@ -497,7 +509,20 @@ int eval_level_t(const SysDev &sys, const CsfView &c, const LevelGrid &grid, dou
   void *mem[VX_MAXPOLY] = {nullptr};
   V *buf[VX_MAXPOLY][VX_KMAX] = {{nullptr}};
   int rc = VX_OK;
-  for (int f = 0; f < sys.npoly && rc == VX_OK; ++f) {
+  if (ext_scratch) {
+    if (level_scratch_bytes<AR>(sys, c) > ext_bytes) {
+      set_error("the level needs %zu bytes of scratch, more than the %zu available",
+                level_scratch_bytes<AR>(sys, c), ext_bytes);
+      return VX_ECAPACITY;
+    }
+    char *p = (char *)ext_scratch;
+    for (int f = 0; f < sys.npoly; ++f)
+      for (int d = 0; d + 1 < k; ++d) {
+        buf[f][d] = (V *)p;
+        p += ((size_t)c.N[d] * sys.p[f].st[d].blk_out * sizeof(V) + 255) & ~(size_t)255;
+      }
+  }
+  for (int f = 0; f < sys.npoly && rc == VX_OK && !ext_scratch; ++f) {
     size_t total = 0;
     for (int d = 0; d + 1 < k; ++d) total += (size_t)c.N[d] * sys.p[f].st[d].blk_out;
     if (total == 0) continue;
@@ -618,6 +643,43 @@ int take_device_status(cudaStream_t s, int *status) {
   }
   *status = v;
   return VX_OK;
+}
+
+// ---------------------------------------------------------------------------------------
+// Level evaluation without allocating: the partial-evaluation blocks live in a fixed array of
+// device memory that belongs to the library (every device that loads the library holds it
+// until the process exits).  The kernels are the ones above; only host code needs the array's
+// device address, which cudaGetSymbolAddress gives once per device.
+// ---------------------------------------------------------------------------------------
+static __device__ __align__(256) unsigned char g_vx_static_scratch[VX_STATIC_SCRATCH_BYTES];
+
+static void *g_static_scratch_addr[64] = {nullptr};
+
+int static_scratch_address(void **addr) {
+  int dev = 0;
+  VX_CUDA(cudaGetDevice(&dev));
+  if (dev < 0 || dev >= 64) {
+    set_error("device ordinal %d is outside the supported range", dev);
+    return VX_EINVAL;
+  }
+  if (!g_static_scratch_addr[dev]) {
+    void *p = nullptr;
+    VX_CUDA(cudaGetSymbolAddress(&p, g_vx_static_scratch));
+    g_static_scratch_addr[dev] = p;
+  }
+  *addr = g_static_scratch_addr[dev];
+  return VX_OK;
+}
+
+int eval_level_static(const SysDev &sys, const CsfView &csf, const LevelGrid &grid, int arith,
+                      double *d_lo, double *d_hi, uint8_t *d_keep, cudaStream_t s) {
+  void *scratch = nullptr;
+  VX_CHECK(static_scratch_address(&scratch));
+  if (arith == ARITH_F64)
+    return eval_level_t<A64>(sys, csf, grid, d_lo, d_hi, d_keep, nullptr, 0.f, s, nullptr,
+                             nullptr, KK_STAGE0, scratch, VX_STATIC_SCRATCH_BYTES);
+  return eval_level_t<A32>(sys, csf, grid, d_lo, d_hi, d_keep, nullptr, 0.f, s, nullptr, nullptr,
+                           KK_STAGE0_F32, scratch, VX_STATIC_SCRATCH_BYTES);
 }
 
 int eval_level_raw(const SysDev &sys, const CsfView &csf, const LevelGrid &grid, int arith,

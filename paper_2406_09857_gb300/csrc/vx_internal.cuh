@@ -145,6 +145,10 @@ enum Arith { ARITH_F64 = 0, ARITH_F32_MIDRAD = 1, ARITH_F32_CERT = 2 };
 int eval_level_raw(const SysDev &sys, const CsfView &csf, const LevelGrid &grid, int arith,
                    double *d_lo, double *d_hi, uint8_t *d_keep, uint8_t *d_flag, float theta,
                    cudaStream_t s, Timer *tm, int64_t *madds_out);
+// The same without allocating (ARITH_F64 or ARITH_F32_MIDRAD): the blocks are carved from the
+// library's fixed device array; VX_ECAPACITY if they do not fit in VX_STATIC_SCRATCH_BYTES.
+int eval_level_static(const SysDev &sys, const CsfView &csf, const LevelGrid &grid, int arith,
+                      double *d_lo, double *d_hi, uint8_t *d_keep, cudaStream_t s);
 // Reads (synchronising `s`) and clears the device status word that a kernel sets when a
 // bounded wait gives up; *status != 0 means the last evaluations are not to be trusted.
 int take_device_status(cudaStream_t s, int *status);

@@ -63,6 +63,7 @@ def lib() -> ctypes.CDLL:
         "vx_csf_export": ([P, i32, P, P, P], i32),
         "vx_csf_tuples": ([P, P, P], i32),
         "vx_csf_eval_level": ([P, P, P, i32, P, P, P, P], i32),
+        "vx_csf_eval_level_static": ([P, P, P, i32, P, P, P, P], i32),
         "vx_csf_subdivide": ([P, P, P, PP], i32),
         "vx_csf_compact": ([P, P, P, P, PP], i32),
         "vx_enclose_system": ([P, P, i32, P, P, PP], i32),
@@ -254,6 +255,19 @@ def csf_eval_level(system: System, csf: Csf, domain, mode=FP64, values=False, st
     if values:
         return keep[:n], lo[:, :n], hi[:, :n]
     return keep[:n]
+
+
+STATIC_SCRATCH_BYTES = 64 << 20
+
+
+def csf_eval_level_static(system: System, csf: Csf, domain, mode=FP64, keep=None, lo=None,
+                          hi=None, stream=None):
+    """vx_csf_eval_level_static into caller-provided CUDA tensors: ``keep`` uint8 [N_k] and,
+    optionally, ``lo``/``hi`` float64 [npoly, N_k].  Returns ``keep``."""
+    dom = _domain(domain)
+    _check(lib().vx_csf_eval_level_static(system.handle, csf.handle, _np_ptr(dom), int(mode),
+                                          _ptr(lo), _ptr(hi), _ptr(keep), _stream(stream)))
+    return keep
 
 
 def csf_subdivide(csf: Csf, keep, stream=None) -> Csf:

@@ -103,6 +103,12 @@ int vx_system_info(const vx_system *sys, int32_t *k, int32_t *npoly, int64_t *h_
 int vx_system_device_bytes(const vx_system *sys, int64_t *bytes);
 /* Number of kernels this library has launched in this process so far (all threads). */
 int64_t vx_kernel_launches(void);
+/* Failure-path hook: how many times a kernel polls for a bulk copy before it gives up, on the
+ * current device (a negative value restores the default, 2^22; 0 gives up at once).  A kernel
+ * that gives up records it, still waits (with the default bound) for its own copy to land,
+ * and returns without results; the call then fails with VX_ETIMEOUT.  Not part of
+ * Algorithm 3. */
+int vx_set_wait_limit(int64_t polls);
 
 /* The CSF (Sec. 2.1) of n box indices d_tuples[n][k] (device, int32, lexicographically
  * strictly increasing, each coordinate in [0, 2^level)) of grid level `level`.  Depth-j nodes

@@ -590,6 +590,11 @@ int vx_system_device_bytes(const vx_system *sys, int64_t *bytes) {
 
 int64_t vx_kernel_launches(void) { return g_launches.load(std::memory_order_relaxed); }
 
+int vx_set_wait_limit(int64_t polls) {
+  clear_error();
+  return set_wait_polls(polls);
+}
+
 int vx_csf_build(int32_t k, int32_t level, const int32_t *d_tuples, int64_t n, void *stream,
                  vx_csf **out) {
   clear_error();

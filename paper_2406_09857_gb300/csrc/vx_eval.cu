@@ -62,6 +62,9 @@ __device__ __forceinline__ bool sign_clear(double v) { return __double2hiint(v) 
 
 // Nonzero after a bounded wait in a kernel gave up (read and cleared by take_device_status).
 __device__ int g_vx_status = 0;
+// Polls of the first wait for a TMA copy before giving up (settable for tests).
+constexpr uint32_t kWaitPolls = 1u << 22;
+__device__ uint32_t g_vx_wait_polls = kWaitPolls;
 
 // ---- TMA bulk copy global -> shared with an mbarrier (sm_90+ PTX) -------------------------
 __device__ __forceinline__ uint32_t smem_u32(const void *p) {
@@ -94,11 +97,11 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity) {
 // Waits for phase `parity` of the barrier for at most `limit` polls; on give-up records the
 // failure in g_vx_status and waits (bounded again) for the copy in flight before returning.
 __device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity) {
-  const uint32_t limit = 1u << 22;
+  const uint32_t limit = g_vx_wait_polls;
   for (uint32_t it = 0; it < limit; ++it)
     if (mbar_try_wait(bar, parity)) return true;
   atomicExch(&g_vx_status, 1);
-  for (uint32_t it = 0; it < limit; ++it)
+  for (uint32_t it = 0; it < kWaitPolls; ++it)  // the copy in flight must land before exit
     if (mbar_try_wait(bar, parity)) break;
   return false;
 }
@@ -631,6 +634,12 @@ int eval_level_t(const SysDev &sys, const CsfView &c, const LevelGrid &grid, dou
 }
 
 }  // namespace
+
+int set_wait_polls(int64_t polls) {
+  const uint32_t v = polls < 0 ? kWaitPolls : (polls > 0xffffffffll ? 0xffffffffu : (uint32_t)polls);
+  VX_CUDA(cudaMemcpyToSymbol(g_vx_wait_polls, &v, sizeof(v)));
+  return VX_OK;
+}
 
 int take_device_status(cudaStream_t s, int *status) {
   int v = 0;

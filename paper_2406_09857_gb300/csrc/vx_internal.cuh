@@ -152,6 +152,8 @@ int eval_level_static(const SysDev &sys, const CsfView &csf, const LevelGrid &gr
 // Reads (synchronising `s`) and clears the device status word that a kernel sets when a
 // bounded wait gives up; *status != 0 means the last evaluations are not to be trusted.
 int take_device_status(cudaStream_t s, int *status);
+// Polls of a kernel's first bounded wait on the current device (< 0: the default).
+int set_wait_polls(int64_t polls);
 
 // Integer kernels (vx_csf.cu).  Objects own one device allocation each.
 struct CsfObj {

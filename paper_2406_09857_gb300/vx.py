@@ -57,6 +57,7 @@ def lib() -> ctypes.CDLL:
         "vx_system_info": ([P, P, P, P], i32),
         "vx_system_device_bytes": ([P, P], i32),
         "vx_kernel_launches": ([], i64),
+        "vx_set_wait_limit": ([i64], i32),
         "vx_csf_build": ([i32, i32, P, i64, P, PP], i32),
         "vx_csf_free": ([P], None),
         "vx_csf_nodes": ([P, P, P, P], i32),

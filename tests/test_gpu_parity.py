@@ -344,3 +344,28 @@ def test_enclose_from_slab_starts_reproduce_full(vx, world):
             else:
                 assert np.array_equal(b, parts[-1])
     assert np.array_equal(np.concatenate(parts, axis=0), full)
+
+
+def test_bounded_wait_gives_up_cleanly(vx):
+    """A TMA-staged stage whose first wait is limited to zero polls records the give-up, waits
+    for its copy and returns; the call reports VX_ETIMEOUT and the next call is exact again."""
+    import torch
+
+    polys = synth.random_small(3, 8, 1, 91)
+    i, j = np.meshgrid(np.arange(512, dtype=np.int32), np.arange(512, dtype=np.int32),
+                       indexing="ij")
+    t = np.stack([i.ravel(), j.ravel(), (i.ravel() + j.ravel()) % 512], axis=1).astype(np.int32)
+    sysv = vx.System(polys)
+    c = vx.csf_build(3, 9, dev(t))  # 262144 depth-2 nodes, 512 per parent: TMA-staged stage
+    try:
+        assert vx.lib().vx_set_wait_limit(0) == 0  # give up without polling
+        with pytest.raises(vx.VxError) as e:
+            vx.csf_eval_level(sysv, c, synth.cube(3), vx.FP64)
+        assert e.value.code == vx.ETIMEOUT
+    finally:
+        vx.lib().vx_set_wait_limit(-1)
+    keep, lo, hi = vx.csf_eval_level(sysv, c, synth.cube(3), vx.FP64, values=True)
+    sample = np.arange(0, t.shape[0], 997)
+    lo_r, hi_r, keep_r, _ = oracle.eval_boxes(polys, synth.cube(3), 9, t[sample])
+    assert np.array_equal(host(lo)[:, sample], lo_r) and np.array_equal(host(hi)[:, sample], hi_r)
+    assert np.array_equal(host(keep)[sample], keep_r)

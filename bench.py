@@ -171,6 +171,67 @@ def config_dict(world: int, mode: str):
                             "with x1 index r" if world > 1 else "single GPU")}
 
 
+def bench_dense(vx, synth, torch, stream, flush, d=128, level=10, reps=2):
+    """One complete level of a degree-(d,d,d) tensor on [-1,1]^3 (config 5's largest cell):
+    every box of the 2^level-per-axis grid evaluated by the staged (mode-by-mode) partial
+    evaluation, in each arithmetic; the certified binary32 kept set must equal binary64's."""
+    s = synth.dense_sweep(d)
+    sysv = vx.System(s.polys)
+    c = vx.csf_full_grid(3, level)
+    n = 1 << (3 * level)
+    out = {"workload": "dense level: degree %d per variable ((d+1)^3 = %d coefficients, iid "
+                       "N(0,1)), every box of the %d^3 grid of [-1,1]^3" % (d, (d + 1) ** 3, 1 << level)}
+    keeps = {}
+    for name, mode in (("fp32", vx.FP32), ("midrad", vx.FP32_MIDRAD), ("fp64", vx.FP64)):
+        vx.csf_eval_level(sysv, c, s.domain, mode, stream=stream)
+        ms = []
+        for r in range(reps):
+            flush.fill_(float(r))
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            k = vx.csf_eval_level(sysv, c, s.domain, mode, stream=stream)
+            e1.record(stream)
+            e1.synchronize()
+            ms.append(e0.elapsed_time(e1))
+        keeps[name] = k
+        out[name] = {"value": n / (min(ms) * 1e-3), "unit": UNIT, "ms": min(ms),
+                     "kept": int(k.sum().item())}
+    out["fp32_equals_fp64"] = bool(torch.equal(keeps["fp32"], keeps["fp64"]))
+    out["midrad_superset"] = bool(torch.all(keeps["midrad"] >= keeps["fp64"]).item())
+    out["speedup_fp32_vs_fp64"] = out["fp32"]["value"] / out["fp64"]["value"]
+    c.free()
+    return out
+
+
+def bench_batch(vx, synth, torch, workers=16):
+    """Config 4: 256 independent systems (128 bivariate single equations of degree 10..60 and
+    128 trivariate pairs of degree 10..40, depths 8..10) through vx_enclose_batch, from host
+    polynomials to host boxes, in each arithmetic; every system's result must agree."""
+    systems = [(x.polys, x.domain, x.depth) for x in synth.batch()]
+    out = {"workload": "batch: 128 x (k=2, 1 Kostlan poly, d~U{10..60}) + 128 x (k=3, 2 "
+                       "Kostlan polys, d~U{10..40}), depth ~U{8..10}, [-1,1]^k",
+           "workers": workers}
+    boxes = {}
+    for name, mode in (("fp32", vx.FP32), ("fp64", vx.FP64)):
+        for r in vx.enclose_batch(systems[:16], vx.make_opts(mode), nworkers=workers):
+            r.free()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        res = vx.enclose_batch(systems, vx.make_opts(mode), nworkers=workers)
+        torch.cuda.synchronize()
+        el = time.perf_counter() - t0
+        ev = sum(int(r.stats()["tested"].sum()) for r in res)
+        boxes[name] = [r.boxes() for r in res]
+        out[name] = {"value": ev / el, "unit": UNIT, "wall_s": el, "box_evals": ev,
+                     "boxes": int(sum(b.shape[0] for b in boxes[name]))}
+        for r in res:
+            r.free()
+    out["fp32_equals_fp64"] = all(np.array_equal(a, b) for a, b in zip(boxes["fp32"], boxes["fp64"]))
+    out["speedup_fp32_vs_fp64"] = out["fp32"]["value"] / out["fp64"]["value"]
+    return out
+
+
 def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -370,6 +431,13 @@ def run_gpu(args):
            "d2h_bytes_per_step": d2h // ne2e,
            "what": "vx_enclose from host polynomials (pack + upload) to host boxes"}
 
+    # ---- config 5: one complete level (Property 1's dense grid), and config 4: the batch ----
+    extra = {}
+    if rank == 0 and world == 1 and not args.no_extra:
+        log("[bench] dense level and batch")
+        extra["dense_level"] = bench_dense(vx, synth, torch, stream, flush)
+        extra["batch"] = bench_batch(vx, synth, torch)
+
     # ---- CPU oracle on a bounded sample ------------------------------------------------------
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
@@ -404,6 +472,7 @@ def run_gpu(args):
             "recheck_boxes_per_step": int(st32["recheck"].sum()),
             "roofline": roof32,
             "cpu_baseline": cpu,
+            **extra,
             "e2e": e2e,
             "gpu_launches": launches,
             "gpu_launches_per_step": launches / args.steps,
@@ -443,6 +512,8 @@ def main():
     ap.add_argument("--cpu-budget", type=float, default=20.0,
                     help="seconds of CPU oracle work for the cpu_baseline sample")
     ap.add_argument("--no-cpu", action="store_true", help="skip the cpu_baseline sample")
+    ap.add_argument("--no-extra", action="store_true",
+                    help="skip the dense-level and batch sub-reports")
     ap.add_argument("--profile-case", type=int, default=None, metavar="DEPTH",
                     help="run one enclosure of the workload to DEPTH and exit (for ncu)")
     ap.add_argument("--mode", choices=["fp32", "fp64", "midrad"], default="fp32",

@@ -15,8 +15,10 @@
  *   - Pointers prefixed h_ are host memory, d_ device memory of the current CUDA device.
  *     Caller-owned buffers stay owned by the caller; objects returned through an out-pointer
  *     (vx_system, vx_csf, vx_result) are owned by the caller and released by the matching
- *     *_free call.  `stream` is a cudaStream_t (NULL = the legacy default stream); all device
- *     work of a call is ordered on it, and device outputs are valid once it has reached them.
+ *     *_free call, which frees their device memory in the order of the stream they were made
+ *     on (that stream must still exist then).  `stream` is a cudaStream_t (NULL = the legacy
+ *     default stream); all device work of a call is ordered on it, and device outputs are
+ *     valid once it has reached them.
  *   - Variable x_1 is at the root of the CSF and x_k at the leaves; children are in
  *     ascending label order, so leaves are in lexicographic order of their index tuples.
  *   - A grid level l splits axis i of the domain [lo_i, hi_i] into 2^l boxes
@@ -116,6 +118,10 @@ int vx_set_wait_limit(int64_t polls);
  * tuples are not strictly increasing or out of range (checked on the device). */
 int vx_csf_build(int32_t k, int32_t level, const int32_t *d_tuples, int64_t n, void *stream,
                  vx_csf **out);
+/* The CSF of every box of grid level `level`: the dense grid X_1 x ... x X_k of Property 1
+ * (Sec. 1.1), on which Algorithm 2's stages are the mode-by-mode partial evaluation of the
+ * coefficient tensor.  (2^level)^k boxes, at most 2^31 (VX_EOVERFLOW).  Filled directly. */
+int vx_csf_full_grid(int32_t k, int32_t level, void *stream, vx_csf **out);
 void vx_csf_free(vx_csf *csf);
 /* k, level and h_N[k] = N_1..N_k (nodes per depth; N_k = number of boxes). */
 int vx_csf_nodes(const vx_csf *csf, int32_t *k, int32_t *level, int64_t *h_N);
@@ -198,6 +204,17 @@ int vx_enclose_from(const vx_system *sys, const vx_csf *start, const double *h_d
  * leaves the result's boxes readable through vx_result_boxes. */
 int vx_enclose(const vx_poly *F_list, int32_t npoly, const double *h_domain, int32_t depth,
                const vx_opts *opts, vx_result **out);
+
+/* Algorithm 3 on nsys independent systems (each its own k, polynomials, domain and depth):
+ * systems[i] points to npoly[i] polynomials, its domain is the next 2 k_i doubles of
+ * `domains` (systems in order), depths[i] its depth; out[i] receives its result, boxes
+ * already copied to the host.  The systems run concurrently, `nworkers` at a time (<= 0: 16)
+ * on streams of their own, so that the kernels of small systems overlap on the GPU; each
+ * result is the one vx_enclose gives for that system alone.  On failure every out[i] is NULL
+ * and vx_last_error names the system. */
+int vx_enclose_batch(const vx_poly *const *systems, const int32_t *npoly, const double *domains,
+                     const int32_t *depths, int32_t nsys, const vx_opts *opts, int32_t nworkers,
+                     vx_result **out);
 
 /* The surviving boxes: *n tuples of k int32 grid indices at level `depth`, lexicographic,
  * in host memory owned by the result (copied from the device on first call). */

@@ -10,12 +10,14 @@
 
 #include <algorithm>
 #include <atomic>
+#include <thread>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
 #include <new>
+#include <string>
 #include <unordered_map>
 #include <vector>
 
@@ -616,6 +618,25 @@ int vx_csf_build(int32_t k, int32_t level, const int32_t *d_tuples, int64_t n, v
   return VX_OK;
 }
 
+int vx_csf_full_grid(int32_t k, int32_t level, void *stream, vx_csf **out) {
+  clear_error();
+  if (!out || k < 1 || k > VX_KMAX || level < 0 || level > VX_MAXLEVEL) {
+    set_error("vx_csf_full_grid: bad arguments (k %d, level %d)", k, level);
+    return VX_EINVAL;
+  }
+  *out = nullptr;
+  vx_csf *c = new (std::nothrow) vx_csf();
+  if (!c) return VX_ENOMEM;
+  int rc = csf_full_grid_dev(k, level, as_stream(stream), &c->o);
+  if (rc != VX_OK) {
+    csf_release(&c->o);
+    delete c;
+    return rc;
+  }
+  *out = c;
+  return VX_OK;
+}
+
 void vx_csf_free(vx_csf *c) {
   if (!c) return;
   csf_release(&c->o);
@@ -956,6 +977,87 @@ int vx_enclose(const vx_poly *F, int32_t npoly, const double *h_domain, int32_t 
     if (rc != VX_OK) {
       vx_result_free(*out);
       *out = nullptr;
+    }
+  }
+  return rc;
+}
+
+int vx_enclose_batch(const vx_poly *const *systems, const int32_t *npoly, const double *domains,
+                     const int32_t *depths, int32_t nsys, const vx_opts *opts, int32_t nworkers,
+                     vx_result **out) {
+  clear_error();
+  if (!systems || !npoly || !domains || !depths || !out || nsys < 0) {
+    set_error("vx_enclose_batch: NULL argument or negative count");
+    return VX_EINVAL;
+  }
+  for (int32_t i = 0; i < nsys; ++i) out[i] = nullptr;
+  if (nsys == 0) return VX_OK;
+  int dev = 0;
+  VX_CUDA(cudaGetDevice(&dev));
+  // domain offsets: system i owns 2 * k_i doubles
+  std::vector<int64_t> doff(nsys + 1, 0);
+  for (int32_t i = 0; i < nsys; ++i) {
+    if (!systems[i] || npoly[i] < 1) {
+      set_error("vx_enclose_batch: system %d has no polynomials", i);
+      return VX_EINVAL;
+    }
+    doff[i + 1] = doff[i] + 2 * (int64_t)systems[i][0].nvars;
+  }
+  const int nw = std::max(1, std::min<int>(nworkers > 0 ? nworkers : 16, nsys));
+  std::atomic<int32_t> next{0};
+  std::atomic<int> first_rc{VX_OK};
+  std::vector<std::string> errs(nw);
+  auto worker = [&](int w) {
+    if (cudaSetDevice(dev) != cudaSuccess) {
+      first_rc = VX_ECUDA;
+      return;
+    }
+    cudaStream_t s = nullptr;
+    if (cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking) != cudaSuccess) {
+      first_rc = VX_ECUDA;
+      return;
+    }
+    for (int32_t i = next++; i < nsys && first_rc.load() == VX_OK; i = next++) {
+      vx_system *sys = nullptr;
+      int rc = vx_system_create(systems[i], npoly[i], (void *)s, &sys);
+      if (rc == VX_OK) rc = vx_enclose_system(sys, domains + doff[i], depths[i], opts, (void *)s, &out[i]);
+      vx_system_free(sys);
+      if (rc == VX_OK) {
+        int64_t n = 0;
+        const int32_t *t = nullptr;
+        rc = vx_result_boxes(out[i], &n, &t);
+      }
+      if (rc == VX_OK) {
+        // this worker's stream ends with it: once the system's work is complete, the result's
+        // memory is freed in the order of the default stream instead
+        if (cudaStreamSynchronize(s) != cudaSuccess) rc = VX_ECUDA;
+        out[i]->fin.stream = nullptr;
+        out[i]->tm.stream = nullptr;
+      }
+      if (rc != VX_OK) {
+        vx_result_free(out[i]);  // while its stream still exists
+        out[i] = nullptr;
+        errs[w] = std::string("system ") + std::to_string(i) + ": " + vx_last_error();
+        int expected = VX_OK;
+        first_rc.compare_exchange_strong(expected, rc);
+      }
+    }
+    cudaStreamSynchronize(s);
+    cudaStreamDestroy(s);
+  };
+  std::vector<std::thread> pool;
+  for (int w = 0; w < nw; ++w) pool.emplace_back(worker, w);
+  for (auto &t : pool) t.join();
+  const int rc = first_rc.load();
+  if (rc != VX_OK) {
+    for (auto &e : errs)
+      if (!e.empty()) {
+        set_error("vx_enclose_batch: %s", e.c_str());
+        break;
+      }
+    for (int32_t i = 0; i < nsys; ++i) {
+      vx_result_free(out[i]);
+      out[i] = nullptr;
     }
   }
   return rc;

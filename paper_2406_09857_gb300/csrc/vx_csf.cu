@@ -619,6 +619,22 @@ __global__ void k_tuples_of(CsfView c, const int32_t *__restrict__ idx, int64_t 
   }
 }
 
+// The complete tree of a level: depth d holds side^(d+1) nodes, node i has label i % side,
+// parent i / side and children i*side .. i*side + side - 1.
+__global__ void k_full_grid(CsfView c, int32_t side) {
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int d = 0; d < c.k; ++d) {
+    const int64_t n = c.N[d];
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i <= n; i += stride) {
+      if (i < n) {
+        c.lab[d][i] = (int32_t)(i % side);
+        if (d > 0) c.par[d][i] = (int32_t)(i / side);
+      }
+      if (d + 1 < c.k) c.ptr[d][i] = (int32_t)(i * side);
+    }
+  }
+}
+
 __global__ void k_scatter(const int32_t *__restrict__ index, const uint8_t *__restrict__ sub,
                           int64_t n, uint8_t *keep) {
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
@@ -692,6 +708,24 @@ int csf_prune(const CsfView &in, const uint8_t *d_keep, int split, int32_t *d_in
 int csf_tuples_dev(const CsfView &c, int32_t *d_tuples, cudaStream_t s) {
   if (c.N[c.k - 1] == 0) return VX_OK;
   k_tuples<<<blocks_for(c.N[c.k - 1]), 256, 0, s>>>(c, d_tuples);
+  note_launch();
+  VX_LAUNCH_CHECK();
+  return VX_OK;
+}
+
+int csf_full_grid_dev(int k, int level, cudaStream_t s, CsfObj *out) {
+  int64_t N[VX_KMAX] = {0};
+  int64_t n = 1;
+  for (int d = 0; d < k; ++d) {
+    n <<= level;
+    if (n > INT32_MAX) {
+      set_error("the full level-%d grid in %d variables has more than 2^31 boxes", level, k);
+      return VX_EOVERFLOW;
+    }
+    N[d] = n;
+  }
+  VX_CHECK(csf_alloc(out, k, level, N, s));
+  k_full_grid<<<blocks_for(N[k - 1] + 1), 256, 0, s>>>(out->v, 1 << level);
   note_launch();
   VX_LAUNCH_CHECK();
   return VX_OK;

@@ -546,7 +546,11 @@ int eval_level_t(const SysDev &sys, const CsfView &c, const LevelGrid &grid, dou
       const StageDev &st = sys.p[f].st[d];
       const size_t sm = 128 + ((size_t)(st.maxlen + 1) * 4 + 127) / 128 * 128 +
                         (size_t)st.blk_in * sizeof(V);
-      if (c.N[d] >= 152 * 4 * kThreads && c.N[d] >= 128 * c.N[d - 1] && sm <= kMaxDynSmem) {
+      // cp.async.bulk needs 16-byte aligned source and size: every parent block must start on
+      // a 16-byte boundary (the buffer itself is 256-byte aligned)
+      const bool aligned = (st.blk_in * (int64_t)sizeof(V)) % 16 == 0;
+      if (aligned && c.N[d] >= 152 * 4 * kThreads && c.N[d] >= 128 * c.N[d - 1] &&
+          sm <= kMaxDynSmem) {
         tma[d] = true;
         tma_smem[d] = sm;
       }
@@ -562,8 +566,10 @@ int eval_level_t(const SysDev &sys, const CsfView &c, const LevelGrid &grid, dou
       if (rc != VX_OK) break;
       const V *in = d == 0 ? AR::coef(sys.p[f]) : buf[f][d - 1];
       if (tma[d]) {
+        // the same value from every caller: host threads launching concurrently never lower
+        // the limit below another one's need
         if (cudaFuncSetAttribute(k_stage_tma<AR>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)tma_smem[d]) != cudaSuccess) {
+                                 (int)kMaxDynSmem) != cudaSuccess) {
           set_error("cudaFuncSetAttribute(shared memory %zu) failed", tma_smem[d]);
           rc = VX_ECUDA;
           break;

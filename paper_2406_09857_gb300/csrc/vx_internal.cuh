@@ -170,6 +170,8 @@ int csf_build_dev(int k, int level, const int32_t *d_tuples, int64_t n, cudaStre
 // writing the kept leaves' old indices to d_index when non-null.
 int csf_prune(const CsfView &in, const uint8_t *d_keep, int split, int32_t *d_index,
               cudaStream_t s, CsfObj *out, Timer *tm);
+// The complete tree of grid level `level` (every box), filled directly.
+int csf_full_grid_dev(int k, int level, cudaStream_t s, CsfObj *out);
 // ptr[d][N[d]] = N[d+1] for every depth d < k-1.
 int set_ptr_sentinels(const CsfView &v, cudaStream_t s);
 int csf_tuples_dev(const CsfView &c, int32_t *d_tuples, cudaStream_t s);

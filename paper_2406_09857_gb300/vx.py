@@ -60,6 +60,7 @@ def lib() -> ctypes.CDLL:
         "vx_set_wait_limit": ([i64], i32),
         "vx_csf_build": ([i32, i32, P, i64, P, PP], i32),
         "vx_csf_free": ([P], None),
+        "vx_csf_full_grid": ([i32, i32, P, PP], i32),
         "vx_csf_nodes": ([P, P, P, P], i32),
         "vx_csf_export": ([P, i32, P, P, P], i32),
         "vx_csf_tuples": ([P, P, P], i32),
@@ -70,6 +71,7 @@ def lib() -> ctypes.CDLL:
         "vx_enclose_system": ([P, P, i32, P, P, PP], i32),
         "vx_enclose": ([P, i32, P, i32, P, PP], i32),
         "vx_enclose_from": ([P, P, P, i32, P, P, PP], i32),
+        "vx_enclose_batch": ([P, P, P, P, i32, P, i32, P], i32),
         "vx_result_boxes": ([P, P, P], i32),
         "vx_result_csf": ([P, PP], i32),
         "vx_result_stats": ([P, P, P, P, P, P, P], i32),
@@ -239,6 +241,13 @@ def csf_build(k, level, tuples, stream=None) -> Csf:
     return Csf(h)
 
 
+def csf_full_grid(k, level, stream=None) -> Csf:
+    """The CSF of every box of grid level ``level`` (vx_csf_full_grid)."""
+    h = ctypes.c_void_p()
+    _check(lib().vx_csf_full_grid(int(k), int(level), _stream(stream), ctypes.byref(h)))
+    return Csf(h)
+
+
 def csf_eval_level(system: System, csf: Csf, domain, mode=FP64, values=False, stream=None):
     """Returns ``keep`` (uint8 [N_k]) and, with ``values``, ``lo``/``hi`` float64 [npoly, N_k]."""
     import torch
@@ -377,6 +386,31 @@ def enclose_from(system: System, start: Csf, domain, depth, opts: Opts | None = 
                                  ctypes.byref(opts) if opts is not None else None,
                                  _stream(stream), ctypes.byref(h)))
     return Result(h, system.k, int(depth))
+
+
+def enclose_batch(systems, opts: Opts | None = None, nworkers: int = 16):
+    """vx_enclose_batch over ``systems`` = [(polys, domain, depth), ...]; returns Results."""
+    n = len(systems)
+    arrs, keep = [], []
+    ptrs = (ctypes.c_void_p * max(n, 1))()
+    npoly = np.zeros(max(n, 1), dtype=np.int32)
+    depths = np.zeros(max(n, 1), dtype=np.int32)
+    doms = []
+    for i, (polys, domain, depth) in enumerate(systems):
+        arr, kp = _polys(polys)
+        arrs.append(arr)
+        keep += kp
+        ptrs[i] = ctypes.cast(arr, ctypes.c_void_p)
+        npoly[i] = len(polys)
+        depths[i] = int(depth)
+        doms.append(_domain(domain))
+    dom = np.ascontiguousarray(np.concatenate(doms)) if doms else np.zeros(1)
+    outs = (ctypes.c_void_p * max(n, 1))()
+    _check(lib().vx_enclose_batch(ptrs, _np_ptr(npoly), _np_ptr(dom), _np_ptr(depths), n,
+                                  ctypes.byref(opts) if opts is not None else None, int(nworkers),
+                                  outs))
+    return [Result(ctypes.c_void_p(outs[i]), int(np.asarray(systems[i][0][0][0]).shape[1]),
+                   int(systems[i][2])) for i in range(n)]
 
 
 def enclose(polys, domain, depth, opts: Opts | None = None) -> Result:

@@ -369,3 +369,89 @@ def test_bounded_wait_gives_up_cleanly(vx):
     lo_r, hi_r, keep_r, _ = oracle.eval_boxes(polys, synth.cube(3), 9, t[sample])
     assert np.array_equal(host(lo)[:, sample], lo_r) and np.array_equal(host(hi)[:, sample], hi_r)
     assert np.array_equal(host(keep)[sample], keep_r)
+
+
+@pytest.mark.parametrize("k,level", [(1, 6), (2, 4), (3, 3), (4, 2)])
+def test_full_grid_csf_equals_built(vx, k, level):
+    side = 1 << level
+    t = np.stack(np.meshgrid(*[np.arange(side, dtype=np.int32)] * k, indexing="ij"),
+                 axis=-1).reshape(-1, k)
+    a = vx.csf_full_grid(k, level)
+    b = vx.csf_build(k, level, dev(t))
+    assert a.nodes()[2].tolist() == b.nodes()[2].tolist()
+    for depth in range(1, k + 1):
+        la, pa = a.export(depth)
+        lb, pb = b.export(depth)
+        assert torch_equal(la, lb)
+        if depth < k:
+            assert torch_equal(pa, pb)
+    assert np.array_equal(host(a.tuples()), t)
+
+
+def torch_equal(x, y):
+    import torch
+
+    return torch.equal(x, y)
+
+
+@pytest.mark.parametrize("d,level", [(6, 4), (12, 3)])
+def test_dense_level_per_variable_degree(vx, d, level):
+    # config-5 shape (degree d in each variable, iid N(0,1)), every box of a level, against
+    # per-box nested Horner on a sample and the certified/midpoint-radius invariants on all
+    e, cf = synth.gaussian_tensor_poly(3, d, 55)
+    polys = [(e, cf)]
+    sysv = vx.System(polys)
+    c = vx.csf_full_grid(3, level)
+    keep, lo, hi = vx.csf_eval_level(sysv, c, synth.cube(3), vx.FP64, values=True)
+    t = host(c.tuples())
+    sample = np.arange(0, t.shape[0], 7)
+    lo_r, hi_r, keep_r, _ = oracle.eval_boxes(polys, synth.cube(3), level, t[sample])
+    assert np.array_equal(host(lo)[:, sample], lo_r) and np.array_equal(host(hi)[:, sample], hi_r)
+    assert np.array_equal(host(keep)[sample], keep_r)
+    k32 = vx.csf_eval_level(sysv, c, synth.cube(3), vx.FP32)
+    assert np.array_equal(host(k32), host(keep))
+    kmr = vx.csf_eval_level(sysv, c, synth.cube(3), vx.FP32_MIDRAD)
+    assert np.all(host(kmr) >= host(keep))
+
+
+def test_enclose_batch_equals_single_runs(vx):
+    """Independent systems of uneven k, degree and depth (the config-4 mix, small): each result
+    equals the oracle's enclosure of that system alone, in binary64 and certified binary32."""
+    systems = []
+    for i in range(12):
+        st = synth.Stream(700 + i)
+        if i % 2 == 0:
+            d = int(st.uniform_int(4, 12, 1)[0])
+            systems.append(([synth.kostlan_poly(2, d, 800 + i)], synth.cube(2),
+                            int(st.uniform_int(5, 8, 1)[0])))
+        else:
+            d = int(st.uniform_int(3, 6, 1)[0])
+            systems.append(([synth.kostlan_poly(3, d, 900 + i), synth.kostlan_poly(3, d, 950 + i)],
+                            synth.cube(3), int(st.uniform_int(3, 5, 1)[0])))
+    for mode in (vx.FP64, vx.FP32):
+        res = vx.enclose_batch(systems, vx.make_opts(mode), nworkers=4)
+        for (polys, dom, depth), r in zip(systems, res):
+            ref = oracle.enclose(polys, dom, depth)
+            assert np.array_equal(r.boxes(), ref["tuples"])
+            assert np.array_equal(r.stats()["tested"], ref["tested"])
+
+
+def test_dense_level9_all_modes_odd_block(vx):
+    """A complete level-9 grid (512^3 boxes) of a degree-(4,4,4) tensor: 262144 depth-2 nodes
+    with 512 children per parent, so the stage kernels take their shared-memory-staged form
+    where the block layout allows it (binary64, binary32 certified: 16-byte entries) and not
+    where a 25-entry midpoint-radius block would start off a 16-byte boundary."""
+    e, cf = synth.gaussian_tensor_poly(3, 4, 56)
+    polys = [(e, cf)]
+    sysv = vx.System(polys)
+    c = vx.csf_full_grid(3, 9)
+    k64 = host(vx.csf_eval_level(sysv, c, synth.cube(3), vx.FP64))
+    k32 = host(vx.csf_eval_level(sysv, c, synth.cube(3), vx.FP32))
+    kmr = host(vx.csf_eval_level(sysv, c, synth.cube(3), vx.FP32_MIDRAD))
+    assert np.array_equal(k32, k64)
+    assert np.all(kmr >= k64)
+    rng = synth.Stream(57)
+    idx = np.unique(rng.uniform_int(0, (1 << 27) - 1, 4000))
+    t = np.stack([idx >> 18, (idx >> 9) & 511, idx & 511], axis=1).astype(np.int32)
+    _, _, keep_r, _ = oracle.eval_boxes(polys, synth.cube(3), 9, t)
+    assert np.array_equal(k64[idx], keep_r)

@@ -43,6 +43,31 @@ __device__ __forceinline__ int32_t warp_sum(int32_t v) {
   return v;
 }
 
+// The SI entries of a thread (i0 .. i0+SI-1): a source may load them at once (load_items);
+// the default asks for them one by one.
+template <class Src>
+__device__ __forceinline__ void load_items(const Src &src, int64_t i0, int64_t n, bool check,
+                                           unsigned (&m)[SI]) {
+#pragma unroll
+  for (int j = 0; j < SI; ++j) m[j] = i0 + j < n ? src.flags(i0 + j, check) : 0u;
+}
+
+// An emitter may store the SI entries at once (emit_items); the default calls it per entry
+// with the running exclusive counts.
+template <int C, class Emit>
+__device__ __forceinline__ void emit_items(const Emit &em, int64_t i0, int64_t n,
+                                           const unsigned (&m)[SI], int32_t (&run)[C]) {
+#pragma unroll
+  for (int j = 0; j < SI; ++j) {
+    const int64_t i = i0 + j;
+    if (i < n) {
+      em(i, m[j], run);
+#pragma unroll
+      for (int c = 0; c < C; ++c) run[c] += (m[j] >> c) & 1u;
+    }
+  }
+}
+
 template <int C, class Src>
 __global__ void __launch_bounds__(ST) k_scan_reduce(Src src, int64_t n, int32_t *tsum,
                                                     int64_t ntiles) {
@@ -52,14 +77,12 @@ __global__ void __launch_bounds__(ST) k_scan_reduce(Src src, int64_t n, int32_t 
   int32_t cnt[C];
 #pragma unroll
   for (int c = 0; c < C; ++c) cnt[c] = 0;
-  for (int j = 0; j < SI; ++j) {
-    const int64_t i = i0 + j;
-    if (i < n) {
-      const unsigned m = src.flags(i, true);
+  unsigned m[SI];
+  load_items(src, i0, n, true, m);
 #pragma unroll
-      for (int c = 0; c < C; ++c) cnt[c] += (m >> c) & 1u;
-    }
-  }
+  for (int j = 0; j < SI; ++j)
+#pragma unroll
+    for (int c = 0; c < C; ++c) cnt[c] += (m[j] >> c) & 1u;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
 #pragma unroll
   for (int c = 0; c < C; ++c) {
@@ -77,34 +100,37 @@ __global__ void __launch_bounds__(ST) k_scan_reduce(Src src, int64_t n, int32_t 
   }
 }
 
-// In-place exclusive scan of each channel's tile sums; totals[c] = channel total.
+// In-place exclusive scan of each channel's tile sums; totals[c] = channel total.  Thread t
+// owns a run of consecutive tiles: it sums them, one block-wide scan gives the run's offset,
+// and a second pass over the run writes the prefixes.
 template <int C>
 __global__ void __launch_bounds__(1024) k_scan_tiles(int32_t *tsum, int64_t ntiles,
                                                      int32_t *totals) {
   __shared__ int32_t sw[32];
-  __shared__ int32_t s_total;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int64_t per = (ntiles + blockDim.x - 1) / blockDim.x;
+  const int64_t b0 = (int64_t)threadIdx.x * per;
+  const int64_t b1 = b0 + per < ntiles ? b0 + per : ntiles;
   for (int c = 0; c < C; ++c) {
-    int32_t carry = 0;
-    for (int64_t b = 0; b < ntiles; b += 1024) {
-      const int64_t i = b + threadIdx.x;
-      const int32_t v = i < ntiles ? tsum[c * ntiles + i] : 0;
-      int32_t incl = warp_incl_scan(v);
-      if (lane == 31) sw[warp] = incl;
-      __syncthreads();
-      if (warp == 0) {
-        int32_t w = sw[lane];
-        int32_t wi = warp_incl_scan(w);
-        sw[lane] = wi - w;
-        if (lane == 31) s_total = wi;
-      }
-      __syncthreads();
-      incl += sw[warp];
-      if (i < ntiles) tsum[c * ntiles + i] = carry + incl - v;
-      carry += s_total;
-      __syncthreads();
+    int32_t *t = tsum + c * ntiles;
+    int32_t sum = 0;
+    for (int64_t i = b0; i < b1; ++i) sum += t[i];
+    int32_t incl = warp_incl_scan(sum);
+    if (lane == 31) sw[warp] = incl;
+    __syncthreads();
+    if (warp == 0) {
+      const int32_t w = sw[lane];
+      sw[lane] = warp_incl_scan(w) - w;
     }
-    if (threadIdx.x == 0) totals[c] = carry;
+    __syncthreads();
+    int32_t run = incl - sum + sw[warp];
+    for (int64_t i = b0; i < b1; ++i) {
+      const int32_t v = t[i];
+      t[i] = run;
+      run += v;
+    }
+    if (threadIdx.x == blockDim.x - 1) totals[c] = run;
+    __syncthreads();
   }
 }
 
@@ -118,13 +144,11 @@ __global__ void __launch_bounds__(ST) k_scan_emit(Src src, Emit em, int64_t n,
   int32_t cnt[C];
 #pragma unroll
   for (int c = 0; c < C; ++c) cnt[c] = 0;
+  load_items(src, i0, n, false, m);
 #pragma unroll
-  for (int j = 0; j < SI; ++j) {
-    const int64_t i = i0 + j;
-    m[j] = i < n ? src.flags(i, false) : 0u;
+  for (int j = 0; j < SI; ++j)
 #pragma unroll
     for (int c = 0; c < C; ++c) cnt[c] += (m[j] >> c) & 1u;
-  }
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   int32_t pre[C];
 #pragma unroll
@@ -146,15 +170,7 @@ __global__ void __launch_bounds__(ST) k_scan_emit(Src src, Emit em, int64_t n,
   int32_t run[C];
 #pragma unroll
   for (int c = 0; c < C; ++c) run[c] = toff[c * ntiles + tile] + sw[c][warp] + pre[c];
-#pragma unroll
-  for (int j = 0; j < SI; ++j) {
-    const int64_t i = i0 + j;
-    if (i < n) {
-      em(i, m[j], run);
-#pragma unroll
-      for (int c = 0; c < C; ++c) run[c] += (m[j] >> c) & 1u;
-    }
-  }
+  emit_items<C>(em, i0, n, m, run);
 }
 
 // Pinned staging for the few counts the host needs (one buffer per host thread).
@@ -341,15 +357,36 @@ struct Segs {
 struct FlagSrc {
   const uint8_t *f;
   Segs sg;
+  // the segments are in depth order, so the depth is the number of segment starts <= i
   __device__ int depth_of(int64_t i) const {
     int d = 0;
-    while (d + 1 < sg.k && i >= sg.off[d + 1]) ++d;
+#pragma unroll
+    for (int e = 1; e < VX_KMAX; ++e) d += (e < sg.k && i >= sg.off[e]) ? 1 : 0;
     return d;
   }
   __device__ unsigned flags(int64_t i, bool) const {
     return f[i] ? (1u << depth_of(i)) : 0u;
   }
 };
+
+// the eight flags of a thread in one 8-byte load (the array is 256-byte aligned, i0 % 8 == 0)
+__device__ __forceinline__ void load_items(const FlagSrc &src, int64_t i0, int64_t n, bool,
+                                           unsigned (&m)[SI]) {
+  static_assert(SI == 8, "one 8-byte load per thread");
+  if (i0 + SI <= n) {
+    const uint2 v = __ldg(reinterpret_cast<const uint2 *>(src.f + i0));
+    const int d0 = src.depth_of(i0), d1 = src.depth_of(i0 + SI - 1);
+#pragma unroll
+    for (int j = 0; j < SI; ++j) {
+      const unsigned b = ((j < 4 ? v.x : v.y) >> (8 * (j & 3))) & 0xffu;
+      const int d = d0 == d1 ? d0 : src.depth_of(i0 + j);
+      m[j] = b ? (1u << d) : 0u;
+    }
+  } else {
+#pragma unroll
+    for (int j = 0; j < SI; ++j) m[j] = i0 + j < n ? src.flags(i0 + j, false) : 0u;
+  }
+}
 
 struct RankEmit {
   int32_t *rank;
@@ -359,28 +396,78 @@ struct RankEmit {
   }
 };
 
-// keep flags upward: a node is kept iff some leaf below it is kept
-__global__ void k_mark_up(CsfView c, const uint8_t *__restrict__ keep, uint8_t *flags, Segs sg) {
-  const int k = c.k;
-  const int64_t n = c.N[k - 1];
-  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
-    const uint8_t kp = keep[i] ? 1 : 0;
-    flags[sg.off[k - 1] + i] = kp;
-    if (!kp) continue;
-    int64_t p = i;
-    for (int d = k - 1; d > 0; --d) {
-      p = c.par[d][p];
-      uint8_t *f = flags + sg.off[d - 1] + p;
-      if (*(volatile uint8_t *)f) break;  // whoever set it carries on upward
-      *f = 1;
+// the eight ranks of a thread in two 16-byte stores (rank is 256-byte aligned)
+template <int C>
+__device__ __forceinline__ void emit_items(const RankEmit &em, int64_t i0, int64_t n,
+                                           const unsigned (&m)[SI], int32_t (&run)[C]) {
+  if (i0 + SI <= n) {
+    int32_t r[SI];
+    const int d0 = em.src.depth_of(i0), d1 = em.src.depth_of(i0 + SI - 1);
+#pragma unroll
+    for (int j = 0; j < SI; ++j) {
+      const int dj = d0 == d1 ? d0 : em.src.depth_of(i0 + j);
+      int32_t v = 0;
+#pragma unroll
+      for (int c = 0; c < C; ++c) v = c == dj ? run[c] : v;
+      r[j] = v;
+#pragma unroll
+      for (int c = 0; c < C; ++c) run[c] += (m[j] >> c) & 1u;
+    }
+    int4 *dst = reinterpret_cast<int4 *>(em.rank + i0);
+    dst[0] = make_int4(r[0], r[1], r[2], r[3]);
+    dst[1] = make_int4(r[4], r[5], r[6], r[7]);
+  } else {
+#pragma unroll
+    for (int j = 0; j < SI; ++j) {
+      const int64_t i = i0 + j;
+      if (i < n) {
+        em(i, m[j], run);
+#pragma unroll
+        for (int c = 0; c < C; ++c) run[c] += (m[j] >> c) & 1u;
+      }
     }
   }
 }
 
+// Flags of depth d from those of depth d+1: node p is kept iff one of its children
+// ptr[p] .. ptr[p+1]-1 (at flags[coff + child]) is.  One warp per node; each lane tests 16
+// flags per 16-byte load (512 per warp step, from the 16-byte boundary below the range) and
+// the warp stops at the first step holding a kept child.  flags is 256-byte aligned and has 16
+// bytes of padding after its last entry for the loads that run past a range's end.
+__global__ void k_mark_parents(const int32_t *__restrict__ ptr, int64_t n,
+                               const uint8_t *__restrict__ flags, int64_t coff,
+                               uint8_t *__restrict__ out) {
+  const int lane = threadIdx.x & 31;
+  const int64_t nw = (int64_t)gridDim.x * (blockDim.x >> 5);
+  for (int64_t p = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); p < n; p += nw) {
+    const int64_t lo = coff + __ldg(ptr + p), hi = coff + __ldg(ptr + p + 1);
+    bool any = false;
+    for (int64_t b = lo & ~(int64_t)15; b < hi; b += 512) {  // the same trip count for all lanes
+      const int64_t c = b + 16 * lane;
+      bool hit = false;
+      if (c < hi) {
+        const uint4 v = __ldg(reinterpret_cast<const uint4 *>(flags + c));
+        const uint32_t w[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+        for (int q = 0; q < 16; ++q) {
+          const int64_t e = c + q;
+          hit = hit || (e >= lo && e < hi && ((w[q >> 2] >> (8 * (q & 3))) & 0xffu) != 0);
+        }
+      }
+      if (__any_sync(0xffffffffu, hit)) {
+        any = true;
+        break;
+      }
+    }
+    if (lane == 0) out[p] = any ? 1 : 0;
+  }
+}
+
 // kptr[d][g_d(p)] = rank of the first kept child of kept node p (depth d < k-1)
+template <int D>
 __global__ void k_kptr(CsfView c, const uint8_t *__restrict__ flags, const int32_t *__restrict__ rank,
-                       Segs sg, int d, int32_t *kptr) {
+                       Segs sg, int32_t *kptr) {
+  constexpr int d = D;
   const int64_t n = c.N[d];
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
   for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < n; p += stride) {
@@ -394,14 +481,18 @@ struct KptrSet {
 };
 
 __device__ __forceinline__ int32_t chain(const KptrSet &K, int a, int t, int32_t r) {
-  for (int e = a; e < t; ++e) r = K.k[e][r];
+#pragma unroll
+  for (int e = 0; e < VX_KMAX; ++e)
+    if (e >= a && e < t) r = K.k[e][r];
   return r;
 }
 
-// Bisection of depth d: every kept depth-d node writes its 2^(d+1) copies.
+// Bisection of depth d: every kept depth-d node writes its 2^(d+1) copies.  k and d are
+// template arguments so that the path arrays stay in registers.
+template <int KK, int D>
 __global__ void k_split(CsfView in, const uint8_t *__restrict__ flags,
-                        const int32_t *__restrict__ rank, Segs sg, KptrSet K, int d, CsfView out) {
-  const int k = in.k;
+                        const int32_t *__restrict__ rank, Segs sg, KptrSet K, CsfView out) {
+  constexpr int k = KK, d = D;
   const int64_t n = in.N[d];
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
   for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < n; p += stride) {
@@ -409,12 +500,15 @@ __global__ void k_split(CsfView in, const uint8_t *__restrict__ flags,
     int64_t path[VX_KMAX];
     int32_t g[VX_KMAX];
     path[d] = p;
+#pragma unroll
     for (int a = d; a > 0; --a) path[a - 1] = in.par[a][path[a]];
+#pragma unroll
     for (int a = 0; a <= d; ++a) g[a] = rank[sg.off[a] + path[a]];
     // F_t(p_a) and D_t(p_a) for t = d-1, d, d+1
     int64_t base_d = 0, base_m = 0, base_p = 0;
     int64_t Dd[VX_KMAX], Dm[VX_KMAX], Dp[VX_KMAX];
     int64_t prevF_d = 0, prevF_m = 0, prevF_p = 0;
+#pragma unroll
     for (int a = 0; a <= d; ++a) {
       const int64_t Fd = chain(K, a, d, g[a]);
       Dd[a] = chain(K, a, d, g[a] + 1) - Fd;
@@ -437,6 +531,7 @@ __global__ void k_split(CsfView in, const uint8_t *__restrict__ flags,
     const int nb = 1 << (d + 1);
     for (int b = 0; b < nb; ++b) {
       int64_t idx = base_d, pidx = base_m, cidx = base_p;
+#pragma unroll
       for (int a = 0; a <= d; ++a) {
         const int64_t bit = (b >> (d - a)) & 1;
         idx += bit * (Dd[a] << (d - a));
@@ -451,9 +546,11 @@ __global__ void k_split(CsfView in, const uint8_t *__restrict__ flags,
 }
 
 // Compaction of depth d: kept node p goes to its rank.
+template <int D>
 __global__ void k_gather(CsfView in, const uint8_t *__restrict__ flags,
-                         const int32_t *__restrict__ rank, Segs sg, int d, CsfView out,
+                         const int32_t *__restrict__ rank, Segs sg, CsfView out,
                          int32_t *index) {
+  constexpr int d = D;
   const int64_t n = in.N[d];
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
   for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < n; p += stride) {
@@ -470,6 +567,37 @@ int blocks_for(int64_t n) {
   if (b > 152 * 32) b = 152 * 32;
   if (b < 1) b = 1;
   return (int)b;
+}
+
+// run-time depth -> template argument
+void launch_kptr(int d, int blocks, cudaStream_t s, const CsfView &in, const uint8_t *flags,
+                 const int32_t *rank, const Segs &sg, int32_t *kptr) {
+  switch (d) {
+    case 0: k_kptr<0><<<blocks, 256, 0, s>>>(in, flags, rank, sg, kptr); break;
+    case 1: k_kptr<1><<<blocks, 256, 0, s>>>(in, flags, rank, sg, kptr); break;
+    default: k_kptr<2><<<blocks, 256, 0, s>>>(in, flags, rank, sg, kptr); break;
+  }
+}
+
+void launch_gather(int d, int blocks, cudaStream_t s, const CsfView &in, const uint8_t *flags,
+                   const int32_t *rank, const Segs &sg, const CsfView &out, int32_t *index) {
+  switch (d) {
+    case 0: k_gather<0><<<blocks, 256, 0, s>>>(in, flags, rank, sg, out, index); break;
+    case 1: k_gather<1><<<blocks, 256, 0, s>>>(in, flags, rank, sg, out, index); break;
+    case 2: k_gather<2><<<blocks, 256, 0, s>>>(in, flags, rank, sg, out, index); break;
+    default: k_gather<3><<<blocks, 256, 0, s>>>(in, flags, rank, sg, out, index); break;
+  }
+}
+
+template <int KK>
+void launch_split(int d, int blocks, cudaStream_t s, const CsfView &in, const uint8_t *flags,
+                  const int32_t *rank, const Segs &sg, const KptrSet &K, const CsfView &out) {
+  switch (d) {
+    case 0: k_split<KK, 0><<<blocks, 256, 0, s>>>(in, flags, rank, sg, K, out); break;
+    case 1: if (KK > 1) k_split<KK, (KK > 1 ? 1 : 0)><<<blocks, 256, 0, s>>>(in, flags, rank, sg, K, out); break;
+    case 2: if (KK > 2) k_split<KK, (KK > 2 ? 2 : 0)><<<blocks, 256, 0, s>>>(in, flags, rank, sg, K, out); break;
+    default: if (KK > 3) k_split<KK, (KK > 3 ? 3 : 0)><<<blocks, 256, 0, s>>>(in, flags, rank, sg, K, out); break;
+  }
 }
 
 template <int C>
@@ -495,20 +623,22 @@ int prune_c(const CsfView &in, const uint8_t *d_keep, int split, int32_t *d_inde
   int32_t *rank = nullptr, *kptr = nullptr, *scratch = nullptr;
   int rc = VX_OK;
   if (tm && tm->on) VX_CHECK(tm->begin(KK_PRUNE, total * 9));
-  rc = dmalloc((void **)&flags, (size_t)total, s);
+  rc = dmalloc((void **)&flags, (size_t)total + 16, s);  // 16 bytes for k_mark_parents' loads
   if (rc == VX_OK) rc = dmalloc((void **)&rank, (size_t)total * sizeof(int32_t), s);
-  if (rc == VX_OK && sg.off[k - 1] > 0) {
-    cudaError_t e = cudaMemsetAsync(flags, 0, (size_t)sg.off[k - 1], s);
-    if (e != cudaSuccess) {
-      set_error("cudaMemsetAsync failed: %s", cudaGetErrorString(e));
-      rc = VX_ECUDA;
-    }
-  }
   if (rc == VX_OK) {
-    k_mark_up<<<blocks_for(in.N[k - 1]), 256, 0, s>>>(in, d_keep, flags, sg);
-    note_launch();
-    if (cudaGetLastError() != cudaSuccess) {
-      set_error("mark-up kernel launch failed");
+    cudaError_t e = cudaMemcpyAsync(flags + sg.off[k - 1], d_keep, (size_t)in.N[k - 1],
+                                    cudaMemcpyDeviceToDevice, s);
+    for (int d = k - 2; d >= 0 && e == cudaSuccess; --d) {
+      int64_t blocks = (in.N[d] + 7) / 8;  // 8 warps per block, one node per warp
+      if (blocks > 152 * 16) blocks = 152 * 16;
+      if (blocks < 1) blocks = 1;
+      k_mark_parents<<<(unsigned)blocks, 256, 0, s>>>(in.ptr[d], in.N[d], flags, sg.off[d + 1],
+                                                     flags + sg.off[d]);
+      note_launch();
+      e = cudaGetLastError();
+    }
+    if (e != cudaSuccess) {
+      set_error("marking kept nodes failed: %s", cudaGetErrorString(e));
       rc = VX_ECUDA;
     }
   }
@@ -545,7 +675,7 @@ int prune_c(const CsfView &in, const uint8_t *d_keep, int split, int32_t *d_inde
   if (rc == VX_OK && tm && tm->on) rc = tm->begin(split ? KK_SPLIT : KK_COMPACT,
                                                   split ? (newN[k - 1] * 8 + total * 9) : total * 13);
   for (int d = 0; d + 1 < k && rc == VX_OK; ++d) {
-    k_kptr<<<blocks_for(in.N[d]), 256, 0, s>>>(in, flags, rank, sg, d, (int32_t *)K.k[d]);
+    launch_kptr(d, blocks_for(in.N[d]), s, in, flags, rank, sg, (int32_t *)K.k[d]);
     note_launch();
     if (cudaGetLastError() != cudaSuccess) {
       set_error("kptr kernel launch failed");
@@ -563,9 +693,9 @@ int prune_c(const CsfView &in, const uint8_t *d_keep, int split, int32_t *d_inde
   }
   for (int d = 0; d < k && rc == VX_OK; ++d) {
     if (split)
-      k_split<<<blocks_for(in.N[d]), 256, 0, s>>>(in, flags, rank, sg, K, d, out->v);
+      launch_split<C>(d, blocks_for(in.N[d]), s, in, flags, rank, sg, K, out->v);
     else
-      k_gather<<<blocks_for(in.N[d]), 256, 0, s>>>(in, flags, rank, sg, d, out->v, d_index);
+      launch_gather(d, blocks_for(in.N[d]), s, in, flags, rank, sg, out->v, d_index);
     note_launch();
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) {

@@ -48,6 +48,8 @@
 //        that are not exact at binary32 precision) add the term 2^-23 m_J xmax explicitly.
 #include <cuda_runtime.h>
 
+#include <type_traits>
+
 #include "vx_internal.cuh"
 
 namespace vx {
@@ -230,16 +232,19 @@ struct A32C {
     x.cls = !g.fexact ? 0 : ((x.l >= 0.f) ? 1 : ((x.h <= 0.f) ? -1 : 0));
     return x;
   }
+  // Both bounds of J*X + A, each the min of two paired round-down FMAs (RD is monotone, so
+  // min(RD(a), RD(b)) = RD(min(a, b))): for X >= 0 the lower end of J*X is min(lo_J l, lo_J h)
+  // and -hi is min(-hi_J l, -hi_J h); for X <= 0 the roles of lo_J and -hi_J swap and the
+  // endpoints are negated.  No sign test on J: the two chains (lo, -hi) never mix.
   template <int CLS>
   static __device__ __forceinline__ V step(V J, const X &x, V A) {
-    // both bounds from one paired round-down FMA on the natural pairs (lo, -hi)
     float2 r;
-    if (CLS > 0) {  // X >= 0: lo from lo_J, hi from hi_J
-      const float2 u = make_float2((__float_as_int(J.x) >= 0) ? x.l : x.h, (J.y <= 0.f) ? x.h : x.l);
-      r = __ffma2_rd(make_float2(J.x, J.y), u, make_float2(A.x, A.y));
-    } else if (CLS < 0) {  // X <= 0: lo from hi_J = -J.y, hi from lo_J
-      const float2 u = make_float2((J.y <= 0.f) ? x.nl : x.nh, (__float_as_int(J.x) >= 0) ? x.nh : x.nl);
-      r = __ffma2_rd(make_float2(J.y, J.x), u, make_float2(A.x, A.y));
+    if (CLS != 0) {
+      const float2 j = CLS > 0 ? make_float2(J.x, J.y) : make_float2(J.y, J.x);
+      const float a = CLS > 0 ? x.l : x.nh, b = CLS > 0 ? x.h : x.nl;
+      const float2 P = __ffma2_rd(j, make_float2(a, a), make_float2(A.x, A.y));
+      const float2 Q = __ffma2_rd(j, make_float2(b, b), make_float2(A.x, A.y));
+      r = make_float2(fminf(P.x, Q.x), fminf(P.y, Q.y));
     } else {  // X straddles 0: hull of the four products, each bound rounded once
       const float jh = -J.y;
       r.x = fminf(fminf(__fmaf_rd(J.x, x.l, A.x), __fmaf_rd(J.x, x.h, A.x)),
@@ -253,6 +258,18 @@ struct A32C {
     e = __fmaf_ru(J.z, x.xmaxp, e);
     return make_float4(r.x, r.y, e, 0.f);
   }
+  // The step on y = |x| >= 0, y = [yl, yh], with the coefficient negated when neg: Horner in
+  // x <= 0 is Horner in y = -x on the coefficients (-1)^a A_a, the state being (-1)^a J_a
+  // (exact: interval negation swaps the pair (lo, -hi), and the products are the same reals).
+  static __device__ __forceinline__ V step_y(V K, float yl, float yh, float xmaxp, V A, bool neg) {
+    const float2 b = neg ? make_float2(A.y, A.x) : make_float2(A.x, A.y);
+    const float2 P = __ffma2_rd(make_float2(K.x, K.y), make_float2(yl, yl), b);
+    const float2 Q = __ffma2_rd(make_float2(K.x, K.y), make_float2(yh, yh), b);
+    const float rx = fminf(P.x, Q.x), ry = fminf(P.y, Q.y);
+    const float m = fmaxf(fabsf(rx), fabsf(ry));
+    const float e = __fmaf_ru(K.z, xmaxp, __fmaf_ru(kCr, m, A.z));
+    return make_float4(rx, ry, e, 0.f);
+  }
   // a stored bound carries a relative margin 2^-40 and an absolute 2^-148
   static __device__ __forceinline__ V store(V J) {
     return make_float4(J.x, J.y, __fadd_ru(__fmaf_ru(J.z, k2m40, J.z), kEta148), 0.f);
@@ -260,7 +277,7 @@ struct A32C {
   // 0: the binary64 path surely excludes, 1: surely keeps, 2: inside the error band
   static __device__ __forceinline__ int classify(V J) {
     if (J.x > J.z || J.y > J.z) return 0;      // lo > E or hi < -E
-    if (J.x <= -J.z && J.y <= -J.z) return 1;  // lo <= -E and hi >= E
+    if (J.x <= -J.z && J.y <= -J.z && J.z < INFINITY) return 1;  // lo <= -E, hi >= E, E finite
     return 2;
   }
   static __device__ __forceinline__ double lo(V J) { return (double)J.x; }
@@ -470,6 +487,177 @@ __global__ void __launch_bounds__(kThreads)
   }
 }
 
+// Last stage in the certified binary32 arithmetic, two consecutive leaves per thread.  When
+// every thread of a warp holds two leaves of one parent whose x_k intervals do not straddle 0
+// (always so at level >= 1 of a grid exact in binary32), the two leaves share every
+// coefficient load, and a leaf with x_k <= 0 runs Horner in y = -x_k (A32C::step_y), so the
+// lanes of the warp run the same instructions whatever the signs of their boxes.  Any other
+// warp takes the per-leaf path of k_leaf.
+struct YLeaf {
+  float yl, yh, xmaxp;
+  bool neg;
+};
+
+__device__ __forceinline__ YLeaf yleaf(const A32C::X &x) {
+  YLeaf y;
+  y.neg = x.cls < 0;
+  y.yl = y.neg ? x.nh : x.l;
+  y.yh = y.neg ? x.nl : x.h;
+  y.xmaxp = x.xmaxp;
+  return y;
+}
+
+__device__ __forceinline__ float4 negated(float4 A) { return make_float4(A.y, A.x, A.z, A.w); }
+
+// Horner of NP polynomials of one length L on the leaves y0, y1 (one parent): chain K0[f] is
+// (-1)^a J_a of leaf 0 and polynomial f (equal to J_a when y0 is not negated).  Odd entries
+// are negated for a negated leaf; the loop takes the entries in (odd, even) pairs.
+template <int NP>
+__device__ __forceinline__ void horner_y2(const float4 *const (&b)[2], int L, const YLeaf &y0,
+                                          const YLeaf &y1, float4 (&K0)[2], float4 (&K1)[2]) {
+  const bool top_odd = (L - 1) & 1;
+#pragma unroll
+  for (int f = 0; f < NP; ++f) {
+    const float4 A = b[f][L - 1];
+    K0[f] = (top_odd && y0.neg) ? negated(A) : A;
+    K1[f] = (top_odd && y1.neg) ? negated(A) : A;
+  }
+  int a = L - 2;
+  if (a >= 0 && !(a & 1)) {
+#pragma unroll
+    for (int f = 0; f < NP; ++f) {
+      const float4 A = b[f][a];
+      K0[f] = A32C::step_y(K0[f], y0.yl, y0.yh, y0.xmaxp, A, false);
+      K1[f] = A32C::step_y(K1[f], y1.yl, y1.yh, y1.xmaxp, A, false);
+    }
+    --a;
+  }
+  // the entries of the next pair are loaded one pair ahead of their use
+  float4 An[NP], Bn[NP];
+  if (a >= 1) {
+#pragma unroll
+    for (int f = 0; f < NP; ++f) {
+      An[f] = b[f][a];
+      Bn[f] = b[f][a - 1];
+    }
+  }
+  for (; a >= 1; a -= 2) {
+    float4 A[NP], B[NP];
+#pragma unroll
+    for (int f = 0; f < NP; ++f) {
+      A[f] = An[f];
+      B[f] = Bn[f];
+    }
+    if (a >= 3) {
+#pragma unroll
+      for (int f = 0; f < NP; ++f) {
+        An[f] = b[f][a - 2];
+        Bn[f] = b[f][a - 3];
+      }
+    }
+#pragma unroll
+    for (int f = 0; f < NP; ++f) {
+      K0[f] = A32C::step_y(K0[f], y0.yl, y0.yh, y0.xmaxp, A[f], y0.neg);
+      K1[f] = A32C::step_y(K1[f], y1.yl, y1.yh, y1.xmaxp, A[f], y1.neg);
+      K0[f] = A32C::step_y(K0[f], y0.yl, y0.yh, y0.xmaxp, B[f], false);
+      K1[f] = A32C::step_y(K1[f], y1.yl, y1.yh, y1.xmaxp, B[f], false);
+    }
+  }
+}
+
+__global__ void __launch_bounds__(kThreads, 6)
+    k_leaf_c(LeafArgs A, int npoly, const int32_t *__restrict__ lab,
+             const int32_t *__restrict__ par, int64_t nleaves, AxisGrid g,
+             uint8_t *__restrict__ keep, double *__restrict__ lo, double *__restrict__ hi,
+             uint8_t *__restrict__ flag) {
+  using V = float4;
+  const int64_t npairs = (nleaves + 1) >> 1;
+  const int64_t ntiles = (npairs + 31) >> 5;
+  const int lane = threadIdx.x & 31;
+  // the loop bound is the same for the 32 lanes of a warp, so the vote below sees all of them
+  for (int64_t t = (int64_t)blockIdx.x * kWarpsPerBlock + (threadIdx.x >> 5); t < ntiles;
+       t += (int64_t)gridDim.x * kWarpsPerBlock) {
+    const int64_t q = t * 32 + lane;
+    const bool live = q < npairs;  // a lane past the end repeats the last pair, stores nothing
+    const int64_t i0 = 2 * (live ? q : npairs - 1);
+    const bool two = i0 + 1 < nleaves;
+    const int64_t i1 = two ? i0 + 1 : i0;
+    const A32C::X x0 = A32C::box(g, __ldg(lab + i0)), x1 = A32C::box(g, __ldg(lab + i1));
+    const int64_t p0 = par ? (int64_t)__ldg(par + i0) : 0;
+    const int64_t p1 = par ? (int64_t)__ldg(par + i1) : 0;
+    bool excl0 = false, amb0 = false, excl1 = false, amb1 = false;
+    auto decide = [&](int f, int c, const V &J) {
+      if (lo && live && (c == 0 || two)) {
+        const int64_t i = c == 0 ? i0 : i1;
+        lo[(int64_t)f * nleaves + i] = A32C::lo(J);
+        hi[(int64_t)f * nleaves + i] = A32C::hi(J);
+      }
+      const int r = A32C::classify(J);
+      if (c == 0) {
+        excl0 = excl0 || r == 0;
+        amb0 = amb0 || r == 2;
+      } else {
+        excl1 = excl1 || r == 0;
+        amb1 = amb1 || r == 2;
+      }
+    };
+    const bool fast = p0 == p1 && x0.cls != 0 && x1.cls != 0;
+    if (__all_sync(0xffffffffu, fast)) {
+      const YLeaf y0 = yleaf(x0), y1 = yleaf(x1);
+      int f = 0;
+      for (; f + 1 < npoly && A.len[f] == A.len[f + 1]; f += 2) {
+        const V *const b[2] = {(const V *)A.in[f] + p0 * A.blk[f],
+                               (const V *)A.in[f + 1] + p0 * A.blk[f + 1]};
+        V K0[2], K1[2];
+        horner_y2<2>(b, A.len[f], y0, y1, K0, K1);
+        decide(f, 0, K0[0]);
+        decide(f + 1, 0, K0[1]);
+        decide(f, 1, K1[0]);
+        decide(f + 1, 1, K1[1]);
+      }
+      for (; f < npoly; ++f) {
+        const V *const b[2] = {(const V *)A.in[f] + p0 * A.blk[f], nullptr};
+        V K0[2], K1[2];
+        horner_y2<1>(b, A.len[f], y0, y1, K0, K1);
+        decide(f, 0, K0[0]);
+        decide(f, 1, K1[0]);
+      }
+    } else {
+#pragma unroll 1
+      for (int c = 0; c < 2; ++c) {
+        const A32C::X &x = c == 0 ? x0 : x1;
+        const int64_t p = c == 0 ? p0 : p1;
+        int f = 0;
+        for (; f + 1 < npoly && A.len[f] == A.len[f + 1]; f += 2) {
+          V J0, J1;
+          horner1x2_any<A32C>((const V *)A.in[f] + p * A.blk[f],
+                              (const V *)A.in[f + 1] + p * A.blk[f + 1], A.len[f], x, J0, J1);
+          decide(f, c, J0);
+          decide(f + 1, c, J1);
+        }
+        for (; f < npoly; ++f)
+          decide(f, c, horner1_any<A32C>((const V *)A.in[f] + p * A.blk[f], 1, A.len[f], x));
+      }
+    }
+    if (live) {
+      keep[i0] = excl0 ? 0 : 1;
+      if (flag) flag[i0] = (!excl0 && amb0) ? 1 : 0;
+      if (two) {
+        keep[i1] = excl1 ? 0 : 1;
+        if (flag) flag[i1] = (!excl1 && amb1) ? 1 : 0;
+      }
+    }
+  }
+}
+
+int leaf_pair_grid(int64_t leaves) {
+  int64_t b = ((leaves + 1) / 2 + kThreads - 1) / kThreads;
+  const int64_t cap = 152 * 32;
+  if (b > cap) b = cap;
+  if (b < 1) b = 1;
+  return (int)b;
+}
+
 constexpr size_t kMaxDynSmem = 200 * 1024;
 
 // The input of stage d >= 1 (the output of stage d-1) is node-major iff stage d is the leaf
@@ -621,10 +809,15 @@ int eval_level_t(const SysDev &sys, const CsfView &c, const LevelGrid &grid, dou
     madds += wl;
     if (tm && tm->on) rc = tm->begin(kind0 + 2, wl);
     if (rc == VX_OK) {
-      k_leaf<AR><<<leaf_grid(nleaves), kThreads, 0, s>>>(A, sys.npoly, c.lab[k - 1],
-                                                        k == 1 ? nullptr : c.par[k - 1], nleaves,
-                                                        grid.ax[k - 1], d_keep, d_lo, d_hi,
-                                                        d_flag, theta);
+      if (std::is_same<AR, A32C>::value)
+        k_leaf_c<<<leaf_pair_grid(nleaves), kThreads, 0, s>>>(
+            A, sys.npoly, c.lab[k - 1], k == 1 ? nullptr : c.par[k - 1], nleaves, grid.ax[k - 1],
+            d_keep, d_lo, d_hi, d_flag);
+      else
+        k_leaf<AR><<<leaf_grid(nleaves), kThreads, 0, s>>>(A, sys.npoly, c.lab[k - 1],
+                                                          k == 1 ? nullptr : c.par[k - 1],
+                                                          nleaves, grid.ax[k - 1], d_keep, d_lo,
+                                                          d_hi, d_flag, theta);
       note_launch();
       cudaError_t e = cudaGetLastError();
       if (e != cudaSuccess) {

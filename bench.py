@@ -53,6 +53,17 @@ OPS_PER_MADD = {"fp32": 4, "fp64": 4}
 L2_FLUSH_BYTES = 512 << 20  # > 129 MB of L2
 
 
+def load_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f)
+    except OSError:
+        return {}
+
+
+PEAKS = load_peaks()
+
+
 def log(*a):
     print(*a, file=sys.stderr, flush=True)
 
@@ -201,7 +212,71 @@ def bench_dense(vx, synth, torch, stream, flush, d=128, level=10, reps=2):
     out["midrad_superset"] = bool(torch.all(keeps["midrad"] >= keeps["fp64"]).item())
     out["speedup_fp32_vs_fp64"] = out["fp32"]["value"] / out["fp64"]["value"]
     c.free()
+    out["tensor_core"] = bench_dense_tc(vx, torch, stream, flush, sysv, s, d, level, reps,
+                                        keeps["fp64"], min(out["fp32"]["ms"], out["fp64"]["ms"]))
     return out
+
+
+def bench_dense_tc(vx, torch, stream, flush, sysv, s, d, level, reps, keep64, best_ms):
+    """The same level on the tensor cores: the power-form prefilter (TF32 contractions, a
+    superset of the kept boxes) alone, and the level decided exactly (prefilter, then the
+    survivors through the certified binary32 path), which must equal binary64's keep."""
+    n = 1 << (3 * level)
+    N = 1 << level
+    t0 = time.perf_counter()
+    plan = vx.DensePlan(sysv, level, s.domain, stream=stream)
+    plan_s = time.perf_counter() - t0
+    mask = torch.empty(n // 32, dtype=torch.int32, device="cuda")
+
+    def timed(fn):
+        fn()
+        ms = []
+        for r in range(reps):
+            flush.fill_(float(r))
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            fn()
+            e1.record(stream)
+            e1.synchronize()
+            ms.append(e0.elapsed_time(e1))
+        return min(ms)
+
+    with torch.cuda.stream(stream):
+        pre_ms = timed(lambda: plan.prefilter(mask, stream=stream, check=False))
+        vx.lib().vx_dense_check_status(vx._stream(stream))
+        pre = vx.mask_to_bool(mask, n)
+        keep = torch.empty(n, dtype=torch.uint8, device="cuda")
+        surv = [0]
+
+        def exact():
+            surv[0] = plan.level_keep(vx.make_opts(vx.FP32), keep=keep, stream=stream)[1]
+
+        ex_ms = timed(exact)
+    # executed TF32 flops of the three contractions (padding included) and the algorithmic
+    # flops of the midpoints alone (Property 1's contractions on the unpadded tensor)
+    Kp = (d + 1 + 7) // 8 * 8
+    N2p = (d + 1 + 15) // 16 * 16
+    ncols1 = ((d + 1) ** 2 + 127) // 128 * 128
+    executed = 2.0 * (N * ncols1 * 2 * Kp + N * N * N2p * 3 * Kp + N * N * N * 3 * Kp)
+    algorithmic = 2.0 * (N * (d + 1) ** 3 + N * N * (d + 1) ** 2 + N ** 3 * (d + 1))
+    tf32_peak = PEAKS.get("bf16_tflops", 1900.0) / 2.0  # TF32 dense rate = bf16's / 2 (nominal)
+    res = {
+        "plan_s": plan_s, "plan_bytes": plan.device_bytes(),
+        "prefilter": {"value": n / (pre_ms * 1e-3), "unit": UNIT, "ms": pre_ms,
+                      "kept": int(pre.sum().item()),
+                      "superset_of_fp64": bool(torch.all(pre | (keep64 == 0)).item()),
+                      "tf32_executed_tflops": executed / (pre_ms * 1e-3) / 1e12,
+                      "tf32_algorithmic_mid_tflops": algorithmic / (pre_ms * 1e-3) / 1e12,
+                      "tf32_peak_tflops": tf32_peak,
+                      "frac_executed": executed / (pre_ms * 1e-3) / 1e12 / tf32_peak},
+        "exact_fp32": {"value": n / (ex_ms * 1e-3), "unit": UNIT, "ms": ex_ms,
+                       "survivors": surv[0], "kept": int(keep.sum().item()),
+                       "equals_fp64": bool(torch.equal(keep, keep64))},
+        "speedup_exact_vs_best_interval_path": best_ms / ex_ms,
+    }
+    plan.free()
+    return res
 
 
 def bench_batch(vx, synth, torch, workers=16):
@@ -449,12 +524,7 @@ def run_gpu(args):
         cpu = {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": desc}
 
     if rank == 0:
-        peaks = {}
-        try:
-            with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
-                peaks = json.load(f)
-        except OSError:
-            pass
+        peaks = PEAKS
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup,

@@ -216,6 +216,52 @@ int vx_enclose_batch(const vx_poly *const *systems, const int32_t *npoly, const 
                      const int32_t *depths, int32_t nsys, const vx_opts *opts, int32_t nworkers,
                      vx_result **out);
 
+/* ---- Dense full-grid levels on the tensor cores (k = 3) ------------------------------------
+ * Property 1 (Sec. 1) writes a polynomial on a tensor grid as one contraction of its
+ * coefficient tensor per variable.  A plan evaluates every box of a level (2^level boxes per
+ * axis over the domain) of a trivariate system that way: per polynomial, a midpoint-radius
+ * enclosure mode by mode (the midpoints by TF32 tensor-core contractions with the grid's
+ * Vandermonde matrices, the radii by contractions of |midpoint| and radius with
+ * ((|c|+r)^a - |c|^a) and (|c|+r)^a, every rounding charged to the radius).  That enclosure
+ * contains the nested interval Horner enclosure of Algorithm 1 on every box, so the boxes it
+ * keeps under C0 (Sec. 3.2: 0 in every polynomial's enclosure) are a superset of the boxes the
+ * interval-Horner level keeps.  The paper has no tensor-core path; this is the dense case of
+ * Algorithm 2 (every node of every depth present) recast as GEMMs.
+ *
+ * vx_dense_plan_create: builds every operand (the coefficient tensor as TF32 panels, the grid's
+ * factor matrices) and the intermediates for `sys` (k = 3, degree <= 255 in x_3) at `level`
+ * (5..12) on h_domain (the exact grids vx_csf_eval_level accepts).  Device memory: about
+ * 4 (2^level)^2 ((d1+1)(d3+1) + 3 (d3+1) 2^level) bytes per polynomial, reported by
+ * vx_dense_plan_bytes.  The plan borrows `sys`, which must outlive it.  Ordered on `stream`;
+ * returns once the plan is ready. */
+typedef struct vx_dense_plan vx_dense_plan;
+int vx_dense_plan_create(const vx_system *sys, int32_t level, const double *h_domain,
+                         void *stream, vx_dense_plan **out);
+int vx_dense_plan_bytes(const vx_dense_plan *plan, int64_t *bytes);
+void vx_dense_plan_free(vx_dense_plan *plan);
+/* The superset as a bit mask (device, caller-owned, 2^(3 level) / 32 words): bit b of word w
+ * is box i = 32 w + b, i = (t1 2^level + t2) 2^level + t3, set iff the box is kept.  Launches
+ * only (3 per polynomial, no allocation, no synchronisation: capturable in a CUDA graph);
+ * a tensor-core wait that gave up is reported by the next vx_dense_level or
+ * vx_dense_check_status. */
+int vx_dense_prefilter(const vx_dense_plan *plan, uint32_t *d_mask, void *stream);
+/* VX_ETIMEOUT if a bounded wait inside a tensor-core kernel gave up since the last check
+ * (the outputs of that launch are not valid); synchronises `stream`. */
+int vx_dense_check_status(void *stream);
+/* Test hook: polynomial `poly`'s final midpoint and radius on every box (device, caller-owned,
+ * [2^(3 level)] binary32 each, box order as above).  Every value of the polynomial on box i
+ * lies in [d_mid[i] - d_rad[i], d_mid[i] + d_rad[i]]. */
+int vx_dense_values(const vx_dense_plan *plan, int32_t poly, float *d_mid, float *d_rad,
+                    void *stream);
+/* The level decided exactly: the prefilter, then the surviving boxes as a CSF evaluated by
+ * vx_csf_eval_level's path in opts->mode (VX_FP64, or VX_FP32, which decides every box as
+ * VX_FP64 does; VX_FP32_MIDRAD gives a superset).  d_keep (device, caller-owned,
+ * [2^(3 level)] bytes, box order as above) equals vx_csf_eval_level's keep on the full grid
+ * of the level in that mode; *n_survivors (nullable) receives the prefilter's count.
+ * opts may be NULL (VX_FP32).  Returns once complete. */
+int vx_dense_level(const vx_dense_plan *plan, const vx_opts *opts, uint8_t *d_keep,
+                   int64_t *n_survivors, void *stream);
+
 /* The surviving boxes: *n tuples of k int32 grid indices at level `depth`, lexicographic,
  * in host memory owned by the result (copied from the device on first call). */
 int vx_result_boxes(vx_result *res, int64_t *n, const int32_t **h_tuples);

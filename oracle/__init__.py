@@ -60,9 +60,11 @@ def lib():
         L.orc_domain_exact.argtypes = [i32, P, i32]
         L.orc_prim.argtypes = [i32, P, P, i64, P]
         L.orc_imul.argtypes = [P, P, P, P, i64, P, P]
+        L.orc_dense_powerform.argtypes = [P, P, i64, P, i32, P, i64, P, P]
         for f in ("orc_eval_csf", "orc_eval_boxes", "orc_eval_grid", "orc_csf", "orc_enclose",
                   "orc_enclose_from",
-                  "orc_brute_force", "orc_eval_grid_complex", "orc_domain_exact"):
+                  "orc_brute_force", "orc_eval_grid_complex", "orc_domain_exact",
+                  "orc_dense_powerform"):
             getattr(L, f).restype = i32
         _lib = L
     return _lib
@@ -134,6 +136,24 @@ def eval_boxes(polys, domain, level, tuples):
     _check(lib().orc_eval_boxes(k, npoly, _p(off), _p(E), _p(C), _p(dom), int(level), _p(t), n,
                                 _p(lo), _p(hi), _p(keep), _p(work)), "orc_eval_boxes")
     return lo, hi, keep, int(work[0])
+
+
+
+def dense_powerform(poly, domain, level, tuples):
+    """Mode-wise midpoint-radius power form of one trivariate polynomial on each box:
+    (mid, rad) arrays; every value on box i lies in [mid - rad, mid + rad] (binary64, to
+    nearest, no margins)."""
+    e, c = poly
+    E = np.ascontiguousarray(np.asarray(e, dtype=np.int32).reshape(-1, 3))
+    C = np.ascontiguousarray(np.asarray(c, dtype=np.float64).reshape(-1))
+    t = _tuples(tuples, 3)
+    n = t.shape[0]
+    dom = np.ascontiguousarray(np.asarray(domain, dtype=np.float64).reshape(-1))
+    mid = np.empty(n)
+    rad = np.empty(n)
+    _check(lib().orc_dense_powerform(_p(E), _p(C), int(E.shape[0]), _p(dom), int(level), _p(t), n,
+                                     _p(mid), _p(rad)), "orc_dense_powerform")
+    return mid, rad
 
 
 def eval_grid(polys, xlists, tuples):

@@ -17,6 +17,9 @@
  *   orc_enclose()    Algorithm 3 (breadth-first subdivision) with the exclusion criterion
  *                    C0 of Sec. 3.2: a box is dropped iff 0 is outside the interval value
  *                    of some polynomial of the system.
+ *   orc_dense_powerform()  the mode-by-mode midpoint-radius enclosure on a tensor grid
+ *                    (Property 1's contractions, one variable at a time), the reference for
+ *                    the dense tensor-core level.
  *
  * Readings of the paper taken here (where it is silent or ambiguous):
  *   - Rounding (Sec. 3.2 only gives [a,b]+[c,d]=[a+c,b+d]): every lower endpoint is
@@ -530,6 +533,92 @@ int orc_eval_boxes(int k, int npoly, const int64_t *term_off, const int32_t *exp
   free_plans(plans, npoly);
   fesetround(old);
   return rc;
+}
+
+/* ------------------------------------------------------------------------------------ */
+/* Mode-wise midpoint-radius power form on a tensor grid (the enclosure of the dense      */
+/* tensor-core level, written out plainly).  Property 1 (Sec. 1) contracts the dense      */
+/* coefficient tensor one variable at a time; on a box with centre c and half-width r per */
+/* axis, contracting variable j maps midpoint-radius coefficients <m_a, q_a> to           */
+/*   mid = sum_a m_a c^a,   rad = sum_a |m_a| ((|c|+r)^a - |c|^a) + q_a (|c|+r)^a,        */
+/* which holds every value of sum_a y_a x^a for x in the box and |y_a - m_a| <= q_a.      */
+/* Evaluated in binary64 with rounding to nearest, no safety margins: the reference the   */
+/* device's (margined) enclosure must contain.  k = 3.                                    */
+/* ------------------------------------------------------------------------------------ */
+int orc_dense_powerform(const int32_t *exps, const double *coefs, int64_t nterms,
+                        const double *domain, int level, const int32_t *tuples, int64_t n,
+                        double *mid, double *rad) {
+  int D[3] = {0, 0, 0};
+  if (level < 0 || level > 30 || nterms < 1) return ORC_EINVAL;
+  for (int64_t t = 0; t < nterms; ++t)
+    for (int i = 0; i < 3; ++i) {
+      if (exps[t * 3 + i] < 0) return ORC_EINVAL;
+      if (exps[t * 3 + i] > D[i]) D[i] = exps[t * 3 + i];
+    }
+  const int64_t n1 = D[0] + 1, n2 = D[1] + 1, n3 = D[2] + 1;
+  double *C = calloc((size_t)(n1 * n2 * n3), sizeof(double));
+  double *m1 = malloc(sizeof(double) * (size_t)(n2 * n3)), *q1 = malloc(sizeof(double) * (size_t)(n2 * n3));
+  double *m2 = malloc(sizeof(double) * (size_t)n3), *q2 = malloc(sizeof(double) * (size_t)n3);
+  if (!C || !m1 || !q1 || !m2 || !q2) {
+    free(C); free(m1); free(q1); free(m2); free(q2);
+    return ORC_ENOMEM;
+  }
+  int old = fegetround();
+  fesetround(FE_TONEAREST);
+  for (int64_t t = 0; t < nterms; ++t)
+    C[(exps[t * 3] * n2 + exps[t * 3 + 1]) * n3 + exps[t * 3 + 2]] += coefs[t];
+  const double side = (double)((int64_t)1 << level);
+  for (int64_t b = 0; b < n; ++b) {
+    double c[3], r[3];
+    for (int i = 0; i < 3; ++i) {
+      const double w = (domain[2 * i + 1] - domain[2 * i]) / side;
+      const double l = domain[2 * i] + (double)tuples[b * 3 + i] * w;
+      c[i] = l + 0.5 * w;
+      r[i] = 0.5 * w;
+    }
+    /* mode 1: variable x1 */
+    for (int64_t j = 0; j < n2 * n3; ++j) {
+      double m = 0.0, q = 0.0, p = 1.0, pa = 1.0, pu = 1.0;
+      for (int64_t a = 0; a < n1; ++a) {
+        const double y = C[a * n2 * n3 + j];
+        m += y * p;
+        q += fabs(y) * (pu - pa);
+        p *= c[0];
+        pa *= fabs(c[0]);
+        pu *= fabs(c[0]) + r[0];
+      }
+      m1[j] = m;
+      q1[j] = q;
+    }
+    /* mode 2: variable x2 */
+    for (int64_t a3 = 0; a3 < n3; ++a3) {
+      double m = 0.0, q = 0.0, p = 1.0, pa = 1.0, pu = 1.0;
+      for (int64_t a2 = 0; a2 < n2; ++a2) {
+        const double y = m1[a2 * n3 + a3], e = q1[a2 * n3 + a3];
+        m += y * p;
+        q += fabs(y) * (pu - pa) + e * pu;
+        p *= c[1];
+        pa *= fabs(c[1]);
+        pu *= fabs(c[1]) + r[1];
+      }
+      m2[a3] = m;
+      q2[a3] = q;
+    }
+    /* mode 3: variable x3 */
+    double m = 0.0, q = 0.0, p = 1.0, pa = 1.0, pu = 1.0;
+    for (int64_t a3 = 0; a3 < n3; ++a3) {
+      m += m2[a3] * p;
+      q += fabs(m2[a3]) * (pu - pa) + q2[a3] * pu;
+      p *= c[2];
+      pa *= fabs(c[2]);
+      pu *= fabs(c[2]) + r[2];
+    }
+    mid[b] = m;
+    rad[b] = q;
+  }
+  fesetround(old);
+  free(C); free(m1); free(q1); free(m2); free(q2);
+  return ORC_OK;
 }
 
 /* CSF arrays of a lex-sorted tuple set: N[k]; labels concatenated by depth; ptr for depths

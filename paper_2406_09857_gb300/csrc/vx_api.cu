@@ -456,6 +456,9 @@ struct vx_system {
   size_t bytes = 0;
   cudaStream_t stream = nullptr;
   std::vector<int64_t> M;  // [npoly][k+1]
+  // the polynomials as given (exponents [nterms][k], coefficients), for dense-level plans
+  std::vector<std::vector<int32_t>> exps;
+  std::vector<std::vector<double>> coefs;
 };
 
 struct vx_csf {
@@ -524,6 +527,12 @@ int vx_system_create(const vx_poly *F, int32_t npoly, void *stream, vx_system **
   sys->dev.k = k;
   sys->dev.npoly = npoly;
   sys->M.assign((size_t)npoly * (k + 1), 1);
+  sys->exps.resize(npoly);
+  sys->coefs.resize(npoly);
+  for (int f = 0; f < npoly; ++f) {
+    sys->exps[f].assign(F[f].exps, F[f].exps + (size_t)F[f].nterms * k);
+    sys->coefs[f].assign(F[f].coefs, F[f].coefs + F[f].nterms);
+  }
   size_t off = 0;
   char *dbase = (char *)sys->mem;
   auto put = [&](const void *src, size_t n) -> void * {
@@ -594,6 +603,7 @@ int64_t vx_kernel_launches(void) { return g_launches.load(std::memory_order_rela
 
 int vx_set_wait_limit(int64_t polls) {
   clear_error();
+  VX_CHECK(set_dense_wait_polls(polls));
   return set_wait_polls(polls);
 }
 
@@ -705,6 +715,170 @@ int vx_csf_eval_level(const vx_system *sys, const vx_csf *c, const double *h_dom
     return VX_ETIMEOUT;
   }
   return VX_OK;
+}
+
+// ---------------------------------------------------------------------------------------
+// Dense full-grid levels (tensor cores)
+// ---------------------------------------------------------------------------------------
+struct vx_dense_plan {
+  DensePlan *p = nullptr;
+  const vx_system *sys = nullptr;
+  int level = 0;
+  double domain[2 * VX_KMAX];
+};
+
+int vx_dense_plan_create(const vx_system *sys, int32_t level, const double *h_domain,
+                         void *stream, vx_dense_plan **out) {
+  clear_error();
+  if (!sys || !h_domain || !out) {
+    set_error("vx_dense_plan_create: bad arguments");
+    return VX_EINVAL;
+  }
+  *out = nullptr;
+  if (sys->dev.k != 3) {
+    set_error("vx_dense_plan_create: the tensor-core level is for k = 3 (system has k = %d)",
+              sys->dev.k);
+    return VX_EINVAL;
+  }
+  LevelGrid g;
+  VX_CHECK(make_grid(3, h_domain, level, &g));  // the same domains as the interval path
+  std::vector<DenseHostPoly> hp(sys->dev.npoly);
+  for (int f = 0; f < sys->dev.npoly; ++f)
+    hp[f] = DenseHostPoly{sys->exps[f].data(), sys->coefs[f].data(),
+                          (int64_t)sys->coefs[f].size()};
+  vx_dense_plan *d = new (std::nothrow) vx_dense_plan();
+  if (!d) {
+    set_error("out of host memory");
+    return VX_ENOMEM;
+  }
+  d->sys = sys;
+  d->level = level;
+  std::memcpy(d->domain, h_domain, 6 * sizeof(double));
+  cudaStream_t s = as_stream(stream);
+  int rc = dense_plan_create(sys->dev.npoly, hp.data(), level, h_domain, s, &d->p);
+  if (rc == VX_OK) {
+    cudaError_t e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) {
+      set_error("vx_dense_plan_create: %s", cudaGetErrorString(e));
+      rc = VX_ECUDA;
+    }
+  }
+  if (rc != VX_OK) {
+    dense_plan_free(d->p);
+    delete d;
+    return rc;
+  }
+  *out = d;
+  return VX_OK;
+}
+
+int vx_dense_plan_bytes(const vx_dense_plan *plan, int64_t *bytes) {
+  clear_error();
+  if (!plan || !bytes) {
+    set_error("vx_dense_plan_bytes: bad arguments");
+    return VX_EINVAL;
+  }
+  *bytes = dense_plan_bytes(plan->p);
+  return VX_OK;
+}
+
+void vx_dense_plan_free(vx_dense_plan *plan) {
+  if (!plan) return;
+  dense_plan_free(plan->p);
+  delete plan;
+}
+
+int vx_dense_prefilter(const vx_dense_plan *plan, uint32_t *d_mask, void *stream) {
+  clear_error();
+  if (!plan || !d_mask) {
+    set_error("vx_dense_prefilter: bad arguments");
+    return VX_EINVAL;
+  }
+  return dense_prefilter(plan->p, d_mask, as_stream(stream));
+}
+
+int vx_dense_check_status(void *stream) {
+  clear_error();
+  int st = 0;
+  VX_CHECK(take_dense_status(as_stream(stream), &st));
+  if (st) {
+    set_error("a bounded wait in a tensor-core kernel gave up; its outputs are not valid");
+    return VX_ETIMEOUT;
+  }
+  return VX_OK;
+}
+
+int vx_dense_values(const vx_dense_plan *plan, int32_t poly, float *d_mid, float *d_rad,
+                    void *stream) {
+  clear_error();
+  if (!plan || !d_mid || !d_rad) {
+    set_error("vx_dense_values: bad arguments");
+    return VX_EINVAL;
+  }
+  VX_CHECK(dense_values(plan->p, poly, d_mid, d_rad, as_stream(stream)));
+  return vx_dense_check_status(stream);
+}
+
+int vx_dense_level(const vx_dense_plan *plan, const vx_opts *opts, uint8_t *d_keep,
+                   int64_t *n_survivors, void *stream) {
+  clear_error();
+  if (!plan || !d_keep) {
+    set_error("vx_dense_level: bad arguments");
+    return VX_EINVAL;
+  }
+  const int mode = opts ? opts->mode : VX_FP32;
+  if (mode != VX_FP64 && mode != VX_FP32 && mode != VX_FP32_MIDRAD) {
+    set_error("vx_dense_level: unknown mode %d", mode);
+    return VX_EINVAL;
+  }
+  cudaStream_t s = as_stream(stream);
+  const int level = plan->level;
+  const int64_t nbox = (int64_t)1 << (3 * level);
+  if (nbox > INT32_MAX) {
+    set_error("vx_dense_level: %lld boxes exceed the 32-bit tree indices", (long long)nbox);
+    return VX_EOVERFLOW;
+  }
+  LevelGrid g;
+  VX_CHECK(make_grid(3, plan->domain, level, &g));
+  uint32_t *mask = nullptr;
+  int32_t *tup = nullptr;
+  uint8_t *sub = nullptr;
+  int64_t n = 0;
+  int rc = dmalloc((void **)&mask, (size_t)(nbox / 8), s);
+  if (rc == VX_OK) rc = dense_prefilter(plan->p, mask, s);
+  if (rc == VX_OK) rc = vx_dense_check_status(stream);
+  if (rc == VX_OK) rc = mask_tuples(mask, level, s, &tup, &n);
+  if (rc == VX_OK) {
+    cudaError_t e = cudaMemsetAsync(d_keep, 0, (size_t)nbox, s);
+    if (e != cudaSuccess) {
+      set_error("vx_dense_level: %s", cudaGetErrorString(e));
+      rc = VX_ECUDA;
+    }
+  }
+  if (rc == VX_OK && n > 0) {
+    CsfObj c;
+    rc = csf_build_dev(3, level, tup, n, s, &c, nullptr);
+    if (rc == VX_OK) rc = dmalloc((void **)&sub, (size_t)n, s);
+    int64_t w = 0, nr = 0;
+    if (rc == VX_OK)
+      rc = eval_decide(plan->sys->dev, c.v, g, mode, false, 0.5f, nullptr, nullptr, sub, s,
+                       nullptr, &w, &nr);
+    if (rc == VX_OK) rc = scatter_keep_grid(tup, n, level, sub, d_keep, s);
+    csf_release(&c);
+  }
+  if (rc == VX_OK) {
+    int st = 0;
+    rc = take_device_status(s, &st);
+    if (rc == VX_OK && st) {
+      set_error("vx_dense_level: a bounded device wait gave up; outputs are not valid");
+      rc = VX_ETIMEOUT;
+    }
+  }
+  dfree(sub, s);
+  dfree(tup, s);
+  dfree(mask, s);
+  if (rc == VX_OK && n_survivors) *n_survivors = n;
+  return rc;
 }
 
 int vx_csf_eval_level_static(const vx_system *sys, const vx_csf *c, const double *h_domain,

@@ -185,4 +185,26 @@ int csf_tuples_of(const CsfView &c, const int32_t *d_idx, int64_t n, int32_t *d_
 int scatter_keep(const int32_t *d_index, const uint8_t *d_sub_keep, int64_t n, uint8_t *d_keep,
                  cudaStream_t s);
 
+
+// ---- dense full-grid levels on the tensor cores (vx_dense.cu), k = 3 ----------------------
+struct DenseHostPoly {
+  const int32_t *exps;  // [nterms][3]
+  const double *coefs;
+  int64_t nterms;
+};
+struct DensePlan;
+int dense_plan_create(int npoly, const DenseHostPoly *polys, int level, const double *domain,
+                      cudaStream_t s, DensePlan **out);
+void dense_plan_free(DensePlan *p);
+int64_t dense_plan_bytes(const DensePlan *p);
+int dense_plan_level(const DensePlan *p);
+int dense_prefilter(const DensePlan *p, uint32_t *d_mask, cudaStream_t s);
+int dense_values(const DensePlan *p, int f, float *d_mid, float *d_rad, cudaStream_t s);
+int set_dense_wait_polls(int64_t polls);
+int take_dense_status(cudaStream_t s, int *status);
+int mask_tuples(const uint32_t *d_mask, int level, cudaStream_t s, int32_t **d_tuples,
+                int64_t *n);
+int scatter_keep_grid(const int32_t *d_tuples, int64_t n, int level, const uint8_t *d_keep,
+                      uint8_t *d_out, cudaStream_t s);
+
 }  // namespace vx

@@ -79,6 +79,13 @@ def lib() -> ctypes.CDLL:
         "vx_kernel_kind_name": ([i32], ctypes.c_char_p),
         "vx_result_elapsed_ms": ([P, P], i32),
         "vx_result_free": ([P], None),
+        "vx_dense_plan_create": ([P, i32, P, P, PP], i32),
+        "vx_dense_plan_bytes": ([P, P], i32),
+        "vx_dense_plan_free": ([P], None),
+        "vx_dense_prefilter": ([P, P, P], i32),
+        "vx_dense_check_status": ([P], i32),
+        "vx_dense_values": ([P, i32, P, P, P], i32),
+        "vx_dense_level": ([P, P, P, P, P], i32),
     }
     for name, (args, res) in sig.items():
         f = getattr(L, name)
@@ -422,3 +429,74 @@ def enclose(polys, domain, depth, opts: Opts | None = None) -> Result:
                             ctypes.byref(opts) if opts is not None else None, ctypes.byref(h)))
     k = int(np.asarray(polys[0][0]).shape[1])
     return Result(h, k, int(depth))
+
+
+class DensePlan:
+    """A full-grid level of a trivariate system on the tensor cores (vx_dense_plan): the
+    superset prefilter (bit mask), the enclosure values, and the exactly decided level."""
+
+    def __init__(self, system: System, level, domain, stream=None):
+        self._system = system  # the plan borrows it
+        self.level = int(level)
+        self.nbox = 1 << (3 * self.level)
+        h = ctypes.c_void_p()
+        _check(lib().vx_dense_plan_create(system.handle, self.level, _np_ptr(_domain(domain)),
+                                          _stream(stream), ctypes.byref(h)))
+        self.handle = h
+
+    def device_bytes(self) -> int:
+        b = ctypes.c_int64()
+        _check(lib().vx_dense_plan_bytes(self.handle, ctypes.byref(b)))
+        return int(b.value)
+
+    def prefilter(self, mask=None, stream=None, check=True):
+        """int32 CUDA tensor of nbox/32 words; bit b of word w = box 32 w + b is kept."""
+        import torch
+
+        if mask is None:
+            mask = torch.empty(self.nbox // 32, dtype=torch.int32, device="cuda")
+        _check(lib().vx_dense_prefilter(self.handle, _ptr(mask), _stream(stream)))
+        if check:
+            _check(lib().vx_dense_check_status(_stream(stream)))
+        return mask
+
+    def values(self, poly=0, stream=None):
+        """(mid, rad) float32 CUDA tensors [nbox] of polynomial ``poly``."""
+        import torch
+
+        mid = torch.empty(self.nbox, dtype=torch.float32, device="cuda")
+        rad = torch.empty(self.nbox, dtype=torch.float32, device="cuda")
+        _check(lib().vx_dense_values(self.handle, int(poly), _ptr(mid), _ptr(rad),
+                                     _stream(stream)))
+        return mid, rad
+
+    def level_keep(self, opts: Opts | None = None, keep=None, stream=None):
+        """(keep uint8 CUDA tensor [nbox], prefilter survivors): the level decided exactly."""
+        import torch
+
+        if keep is None:
+            keep = torch.empty(self.nbox, dtype=torch.uint8, device="cuda")
+        n = ctypes.c_int64()
+        _check(lib().vx_dense_level(self.handle, ctypes.byref(opts) if opts is not None else None,
+                                    _ptr(keep), ctypes.byref(n), _stream(stream)))
+        return keep, int(n.value)
+
+    def free(self):
+        if self.handle:
+            lib().vx_dense_plan_free(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass
+
+
+def mask_to_bool(mask, nbox):
+    """Unpacks a prefilter bit mask (int32 CUDA tensor) into a bool tensor [nbox]."""
+    import torch
+
+    w = mask.view(torch.int32).to(torch.int64) & 0xFFFFFFFF
+    bits = torch.arange(32, device=mask.device, dtype=torch.int64)
+    return ((w[:, None] >> bits[None, :]) & 1).reshape(-1)[:nbox].to(torch.bool)

@@ -538,6 +538,161 @@ __device__ __forceinline__ void horner_y2(const float4 *const (&b)[2], int L, co
   }
 }
 
+// Horner of fibre f of a block (entries rowoff[a] + f, a = L-1 .. 0; entry e at
+// base[e * estride]) on two boxes of one parent, as horner_y2 does for a leaf's single fibre.
+__device__ __forceinline__ void horner_y2_fibre(const float4 *__restrict__ base, int64_t estride,
+                                                const int32_t *rowoff, int f, int L,
+                                                const YLeaf &y0, const YLeaf &y1, float4 &K0,
+                                                float4 &K1) {
+  auto ent = [&](int a) { return base[(int64_t)(rowoff[a] + f) * estride]; };
+  const bool top_odd = (L - 1) & 1;
+  {
+    const float4 A = ent(L - 1);
+    K0 = (top_odd && y0.neg) ? negated(A) : A;
+    K1 = (top_odd && y1.neg) ? negated(A) : A;
+  }
+  int a = L - 2;
+  if (a >= 0 && !(a & 1)) {
+    const float4 A = ent(a);
+    K0 = A32C::step_y(K0, y0.yl, y0.yh, y0.xmaxp, A, false);
+    K1 = A32C::step_y(K1, y1.yl, y1.yh, y1.xmaxp, A, false);
+    --a;
+  }
+  float4 An = make_float4(0.f, 0.f, 0.f, 0.f), Bn = An;
+  if (a >= 1) {
+    An = ent(a);
+    Bn = ent(a - 1);
+  }
+  for (; a >= 1; a -= 2) {
+    const float4 A = An, B = Bn;
+    if (a >= 3) {
+      An = ent(a - 2);
+      Bn = ent(a - 3);
+    }
+    K0 = A32C::step_y(K0, y0.yl, y0.yh, y0.xmaxp, A, y0.neg);
+    K1 = A32C::step_y(K1, y1.yl, y1.yh, y1.xmaxp, A, y1.neg);
+    K0 = A32C::step_y(K0, y0.yl, y0.yh, y0.xmaxp, B, false);
+    K1 = A32C::step_y(K1, y1.yl, y1.yh, y1.xmaxp, B, false);
+  }
+}
+
+// Stage d < k-1 in the certified binary32 arithmetic, two consecutive nodes per thread: warp w
+// takes node pairs of chunk w % nchunk (64 nodes) and fibres g, g+G, ... (g = w / nchunk), as
+// k_stage does with one node per lane.  A warp whose 32 pairs each share a parent and do not
+// straddle 0 shares every load between the two nodes and runs sign-free (horner_y2_fibre);
+// any other warp takes k_stage's per-node path.
+__global__ void __launch_bounds__(kThreads, 6)
+    k_stage_c(const StageDev st, const int32_t *__restrict__ lab, const int32_t *__restrict__ par,
+              const float4 *__restrict__ in, int64_t in_estride, int64_t in_nstride,
+              float4 *__restrict__ out, int64_t out_estride, int64_t out_nstride, int64_t nnodes,
+              int64_t nchunk, int G, AxisGrid g) {
+  extern __shared__ int32_t s_rowoff[];
+  for (int i = threadIdx.x; i <= st.maxlen; i += blockDim.x) s_rowoff[i] = st.rowoff[i];
+  __syncthreads();
+  const int lane = threadIdx.x & 31;
+  const int64_t npairs = (nnodes + 1) >> 1;
+  const int64_t nwarps = nchunk * G;
+  for (int64_t w = (int64_t)blockIdx.x * kWarpsPerBlock + (threadIdx.x >> 5); w < nwarps;
+       w += (int64_t)gridDim.x * kWarpsPerBlock) {
+    const int64_t chunk = w % nchunk;
+    const int grp = (int)(w / nchunk);
+    const int64_t q = chunk * 32 + lane;
+    const bool live = q < npairs;
+    const int64_t i0 = 2 * (live ? q : npairs - 1);
+    const bool two = live && i0 + 1 < nnodes;
+    const int64_t i1 = i0 + 1 < nnodes ? i0 + 1 : i0;
+    const A32C::X x0 = A32C::box(g, __ldg(lab + i0)), x1 = A32C::box(g, __ldg(lab + i1));
+    const int64_t p0 = par ? (int64_t)__ldg(par + i0) : 0;
+    const int64_t p1 = par ? (int64_t)__ldg(par + i1) : 0;
+    const bool fast = p0 == p1 && x0.cls != 0 && x1.cls != 0;
+    if (__all_sync(0xffffffffu, fast)) {
+      const YLeaf y0 = yleaf(x0), y1 = yleaf(x1);
+      const float4 *base = in + p0 * in_nstride;
+      for (int f = grp; f < st.nfib; f += G) {
+        const int L = __ldg(st.fiblen + f);
+        float4 K0, K1;
+        horner_y2_fibre(base, in_estride, s_rowoff, f, L, y0, y1, K0, K1);
+        const int64_t o = (int64_t)__ldg(st.outpos + f) * out_estride;
+        if (live) out[i0 * out_nstride + o] = A32C::store(K0);
+        if (two) out[i1 * out_nstride + o] = A32C::store(K1);
+      }
+    } else {
+#pragma unroll 1
+      for (int c = 0; c < 2; ++c) {
+        const A32C::X &x = c == 0 ? x0 : x1;
+        const float4 *base = in + (c == 0 ? p0 : p1) * in_nstride;
+        const bool wr = c == 0 ? live : two;
+        const int64_t node = c == 0 ? i0 : i1;
+        for (int f = grp; f < st.nfib; f += G) {
+          const int L = __ldg(st.fiblen + f);
+          const float4 J = horner_any<A32C>(base, in_estride, s_rowoff, f, L, x);
+          if (wr) out[node * out_nstride + (int64_t)__ldg(st.outpos + f) * out_estride] = A32C::store(J);
+        }
+      }
+    }
+  }
+}
+
+// k_stage_tma in the certified binary32 arithmetic, two children per thread: the children of
+// one parent always share it, so every warp whose boxes do not straddle 0 runs sign-free.
+__global__ void __launch_bounds__(512)
+    k_stage_tma_c(const StageDev st, const int32_t *__restrict__ lab,
+                  const int32_t *__restrict__ pptr, const float4 *__restrict__ in,
+                  float4 *__restrict__ out, int64_t out_estride, int64_t out_nstride, int G,
+                  AxisGrid g) {
+  extern __shared__ __align__(128) unsigned char smem[];
+  uint64_t *bar = reinterpret_cast<uint64_t *>(smem);
+  int32_t *s_rowoff = reinterpret_cast<int32_t *>(smem + 128);
+  float4 *s_blk = reinterpret_cast<float4 *>(smem + 128 + ((st.maxlen + 1) * 4 + 127) / 128 * 128);
+  const int64_t p = blockIdx.x / G;
+  const int grp = (int)(blockIdx.x % G);
+  const int64_t c0 = __ldg(pptr + p), c1 = __ldg(pptr + p + 1);
+  if (threadIdx.x == 0) {
+    mbar_init(bar, 1);
+    const uint64_t bytes = (uint64_t)st.blk_in * sizeof(float4);
+    mbar_arrive_expect_tx(bar, (uint32_t)bytes);
+    const char *src = reinterpret_cast<const char *>(in + p * st.blk_in);
+    char *dst = reinterpret_cast<char *>(s_blk);
+    for (uint64_t o = 0; o < bytes; o += 32768) {
+      const uint32_t n = (uint32_t)(bytes - o < 32768 ? bytes - o : 32768);
+      bulk_copy_g2s(dst + o, src + o, n, bar);
+    }
+  }
+  for (int i = threadIdx.x; i <= st.maxlen; i += blockDim.x) s_rowoff[i] = st.rowoff[i];
+  __syncthreads();
+  if (!mbar_wait_bounded(bar, 0)) return;
+  for (int64_t n0 = c0; n0 < c1; n0 += 2 * (int64_t)blockDim.x) {
+    const int64_t na = n0 + 2 * threadIdx.x;
+    const bool live = na < c1, two = na + 1 < c1;
+    const int64_t i0 = live ? na : c1 - 1, i1 = two ? na + 1 : i0;
+    const A32C::X x0 = A32C::box(g, __ldg(lab + i0)), x1 = A32C::box(g, __ldg(lab + i1));
+    const bool fast = x0.cls != 0 && x1.cls != 0;
+    if (__all_sync(0xffffffffu, fast)) {
+      const YLeaf y0 = yleaf(x0), y1 = yleaf(x1);
+      for (int f = grp; f < st.nfib; f += G) {
+        const int L = __ldg(st.fiblen + f);
+        float4 K0, K1;
+        horner_y2_fibre(s_blk, 1, s_rowoff, f, L, y0, y1, K0, K1);
+        const int64_t o = (int64_t)__ldg(st.outpos + f) * out_estride;
+        if (live) out[i0 * out_nstride + o] = A32C::store(K0);
+        if (two) out[i1 * out_nstride + o] = A32C::store(K1);
+      }
+    } else {
+#pragma unroll 1
+      for (int c = 0; c < 2; ++c) {
+        const A32C::X &x = c == 0 ? x0 : x1;
+        const bool wr = c == 0 ? live : two;
+        const int64_t node = c == 0 ? i0 : i1;
+        for (int f = grp; f < st.nfib; f += G) {
+          const int L = __ldg(st.fiblen + f);
+          const float4 J = horner_any<A32C>(s_blk, 1, s_rowoff, f, L, x);
+          if (wr) out[node * out_nstride + (int64_t)__ldg(st.outpos + f) * out_estride] = A32C::store(J);
+        }
+      }
+    }
+  }
+}
+
 __global__ void __launch_bounds__(kThreads, 6)
     k_leaf_c(LeafArgs A, int npoly, const int32_t *__restrict__ lab,
              const int32_t *__restrict__ par, int64_t nleaves, AxisGrid g,
@@ -632,6 +787,9 @@ int leaf_pair_grid(int64_t leaves) {
 }
 
 constexpr size_t kMaxDynSmem = 200 * 1024;
+// depths with at least this many nodes, or this many multiply-adds per node, run the
+// certified stage two nodes per thread
+constexpr int64_t kPairNodes = 65536;
 
 // The input of stage d >= 1 (the output of stage d-1) is node-major iff stage d is the leaf
 // stage or is TMA-staged; a non-staged inner stage reads it entry-major.
@@ -742,11 +900,27 @@ int eval_level_t(const SysDev &sys, const CsfView &c, const LevelGrid &grid, dou
         int64_t G = (4 * 152 * 2 + np - 1) / np;
         if (G > st.nfib) G = st.nfib;
         if (G < 1) G = 1;
-        k_stage_tma<AR><<<(unsigned)(np * G), threads, tma_smem[d], s>>>(
-            st, c.lab[d], c.ptr[d - 1], in, buf[f][d], oe, on, (int)G, grid.ax[d]);
+        if constexpr (std::is_same<AR, A32C>::value) {
+          if (cudaFuncSetAttribute(k_stage_tma_c, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                   (int)kMaxDynSmem) != cudaSuccess) {
+            set_error("cudaFuncSetAttribute(shared memory %zu) failed", tma_smem[d]);
+            rc = VX_ECUDA;
+            break;
+          }
+          k_stage_tma_c<<<(unsigned)(np * G), threads, tma_smem[d], s>>>(
+              st, c.lab[d], c.ptr[d - 1], in, buf[f][d], oe, on, (int)G, grid.ax[d]);
+        } else {
+          k_stage_tma<AR><<<(unsigned)(np * G), threads, tma_smem[d], s>>>(
+              st, c.lab[d], c.ptr[d - 1], in, buf[f][d], oe, on, (int)G, grid.ax[d]);
+        }
       } else {
-        // fibre groups: enough warps to fill the GPU several times over
-        const int64_t nchunk = (c.N[d] + 31) / 32;
+        // fibre groups: enough warps to fill the GPU several times over (a warp takes 32
+        // nodes; 64 in the certified binary32 arithmetic when the depth has enough nodes for
+        // the shared loads to pay)
+        const bool pairs = std::is_same<AR, A32C>::value &&
+                           (c.N[d] >= kPairNodes || st.blk_in - st.nfib >= kPairNodes);
+        const int64_t per_warp = pairs ? 64 : 32;
+        const int64_t nchunk = (c.N[d] + per_warp - 1) / per_warp;
         const int64_t target = 152 * 64;
         int64_t G = (target + nchunk - 1) / nchunk;
         if (G > st.nfib) G = st.nfib;
@@ -755,9 +929,14 @@ int eval_level_t(const SysDev &sys, const CsfView &c, const LevelGrid &grid, dou
         if (blocks > 152 * 64) blocks = 152 * 64;
         const int64_t in_estride = d == 0 ? 1 : (tma_input_node_major(d, k, tma) ? 1 : c.N[d - 1]);
         const int64_t in_nstride = d == 0 ? 0 : (tma_input_node_major(d, k, tma) ? st.blk_in : 1);
-        k_stage<AR><<<(unsigned)blocks, kThreads, (st.maxlen + 1) * sizeof(int32_t), s>>>(
-            st, c.lab[d], d == 0 ? nullptr : c.par[d], in, in_estride, in_nstride, buf[f][d], oe,
-            on, c.N[d], nchunk, (int)G, grid.ax[d]);
+        if (pairs)
+          k_stage_c<<<(unsigned)blocks, kThreads, (st.maxlen + 1) * sizeof(int32_t), s>>>(
+              st, c.lab[d], d == 0 ? nullptr : c.par[d], (const float4 *)in, in_estride,
+              in_nstride, (float4 *)buf[f][d], oe, on, c.N[d], nchunk, (int)G, grid.ax[d]);
+        else
+          k_stage<AR><<<(unsigned)blocks, kThreads, (st.maxlen + 1) * sizeof(int32_t), s>>>(
+              st, c.lab[d], d == 0 ? nullptr : c.par[d], in, in_estride, in_nstride, buf[f][d],
+              oe, on, c.N[d], nchunk, (int)G, grid.ax[d]);
       }
       note_launch();
       cudaError_t e = cudaGetLastError();

@@ -573,6 +573,24 @@ def run_profile_case(args):
     return 0
 
 
+def run_profile_dense(args):
+    """One tensor-core prefilter of the degree-128 dense tensor at --profile-dense LEVEL (a
+    small case for ncu captures: 3 tensor-core launches after the plan's 9 factor launches)."""
+    import torch
+
+    from paper_2406_09857_gb300 import synth, vx
+
+    torch.cuda.set_device(0)
+    s = synth.dense_sweep(128)
+    plan = vx.DensePlan(vx.System(s.polys), args.profile_dense, s.domain)
+    mask = plan.prefilter()
+    torch.cuda.synchronize()
+    n = 1 << (3 * args.profile_dense)
+    print(json.dumps({"profile_dense_level": args.profile_dense, "plan_bytes": plan.device_bytes(),
+                      "prefilter_kept": int(vx.mask_to_bool(mask, n).sum().item())}))
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser(description=__doc__.split("\n\n")[0])
     ap.add_argument("--gpus", type=int, default=1)
@@ -586,11 +604,16 @@ def main():
                     help="skip the dense-level and batch sub-reports")
     ap.add_argument("--profile-case", type=int, default=None, metavar="DEPTH",
                     help="run one enclosure of the workload to DEPTH and exit (for ncu)")
+    ap.add_argument("--profile-dense", type=int, default=None, metavar="LEVEL",
+                    help="run one tensor-core prefilter of the degree-128 dense tensor at LEVEL "
+                         "and exit (for ncu)")
     ap.add_argument("--mode", choices=["fp32", "fp64", "midrad"], default="fp32",
                     help="arithmetic of --profile-case")
     args = ap.parse_args()
     if args.profile_case is not None:
         return run_profile_case(args)
+    if args.profile_dense is not None:
+        return run_profile_dense(args)
     if args.impl == "reference":
         return run_reference(args)
     return run_gpu(args)

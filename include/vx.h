@@ -148,6 +148,18 @@ int vx_csf_tuples(const vx_csf *csf, int32_t *d_tuples, void *stream);
 int vx_csf_eval_level(const vx_system *sys, const vx_csf *csf, const double *h_domain,
                       int32_t mode, double *d_lo, double *d_hi, uint8_t *d_keep, void *stream);
 
+/* Algorithm 2 takes the intervals of x_1 as a list (Sec. 2.2); this is vx_csf_eval_level with
+ * an explicit interval list per axis instead of the regular grid: a depth-j node labelled t
+ * (j = 1..k) stands for [d_xlo[j-1][t], d_xhi[j-1][t]] (binary64, device, caller-owned,
+ * nx[j-1] >= 2^level entries each, lo <= hi; the CSF's level only bounds its labels).  Test
+ * hook for evaluations on point sets that are not grids: with X_j = {[1,1], [-1,-1]} a
+ * multilinear polynomial gives the Walsh-Hadamard transform of its coefficients (the real
+ * special case of the DFT identity of Sec. 3.1).  Outputs and modes as vx_csf_eval_level;
+ * the binary32 modes take the interval ends rounded outward. */
+int vx_csf_eval_grid(const vx_system *sys, const vx_csf *csf, const double *const *d_xlo,
+                     const double *const *d_xhi, const int64_t *nx, int32_t mode, double *d_lo,
+                     double *d_hi, uint8_t *d_keep, void *stream);
+
 /* Level evaluation that allocates nothing, for callers that cannot allocate device memory
  * while they run: a host framework that owns the device's memory as a fixed budget (where an
  * allocation by a library would fail or upset its accounting), or a latency-bound loop that

@@ -881,6 +881,41 @@ int vx_dense_level(const vx_dense_plan *plan, const vx_opts *opts, uint8_t *d_ke
   return rc;
 }
 
+int vx_csf_eval_grid(const vx_system *sys, const vx_csf *c, const double *const *d_xlo,
+                     const double *const *d_xhi, const int64_t *nx, int32_t mode, double *d_lo,
+                     double *d_hi, uint8_t *d_keep, void *stream) {
+  clear_error();
+  if (!sys || !c || !d_xlo || !d_xhi || !nx || !d_keep || (!d_lo) != (!d_hi) ||
+      c->o.v.k != sys->dev.k || (mode != VX_FP64 && mode != VX_FP32_MIDRAD && mode != VX_FP32)) {
+    set_error("vx_csf_eval_grid: bad arguments");
+    return VX_EINVAL;
+  }
+  const int k = c->o.v.k;
+  const int64_t side = (int64_t)1 << c->o.v.level;
+  LevelGrid g{};
+  for (int i = 0; i < k; ++i) {
+    if (!d_xlo[i] || !d_xhi[i] || nx[i] < side) {
+      set_error("vx_csf_eval_grid: axis %d needs %lld intervals (labels < 2^level), got %lld", i,
+                (long long)side, (long long)nx[i]);
+      return VX_EINVAL;
+    }
+    g.ax[i].xlo = d_xlo[i];
+    g.ax[i].xhi = d_xhi[i];
+    g.ax[i].fexact = 0;
+  }
+  int64_t w = 0, nr = 0;
+  cudaStream_t s = as_stream(stream);
+  VX_CHECK(eval_decide(sys->dev, c->o.v, g, mode, false, 0.5f, d_lo, d_hi, d_keep, s, nullptr, &w,
+                       &nr));
+  int st = 0;
+  VX_CHECK(take_device_status(s, &st));
+  if (st) {
+    set_error("vx_csf_eval_grid: a bounded device wait gave up; outputs are not valid");
+    return VX_ETIMEOUT;
+  }
+  return VX_OK;
+}
+
 int vx_csf_eval_level_static(const vx_system *sys, const vx_csf *c, const double *h_domain,
                              int32_t mode, double *d_lo, double *d_hi, uint8_t *d_keep,
                              void *stream) {

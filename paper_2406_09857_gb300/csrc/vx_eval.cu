@@ -59,6 +59,18 @@ namespace {
 constexpr int kWarpsPerBlock = 4;
 constexpr int kThreads = 32 * kWarpsPerBlock;
 
+// The binary64 endpoints of box t on an axis: the regular grid (exact on accepted domains) or
+// the axis' explicit interval list.
+__device__ __forceinline__ void endpoints(const AxisGrid &g, int32_t t, double &l, double &h) {
+  if (g.xlo) {
+    l = g.xlo[t];
+    h = g.xhi[t];
+  } else {
+    l = __dadd_rn(g.lo, __dmul_rn((double)t, g.w));
+    h = __dadd_rn(g.lo, __dmul_rn((double)t + 1.0, g.w));
+  }
+}
+
 __device__ __forceinline__ double sel_min(double a, double b) { return (b < a) ? b : a; }
 __device__ __forceinline__ double sel_max(double a, double b) { return (b > a) ? b : a; }
 __device__ __forceinline__ bool sign_clear(double v) { return __double2hiint(v) >= 0; }
@@ -92,8 +104,7 @@ struct A64 {
   };
   static __device__ __forceinline__ X box(const AxisGrid &g, int32_t t) {
     X x;
-    x.l = __dadd_rn(g.lo, __dmul_rn((double)t, g.w));  // exact on accepted domains
-    x.h = __dadd_rn(g.lo, __dmul_rn((double)t + 1.0, g.w));
+    endpoints(g, t, x.l, x.h);
     x.cls = (x.l >= 0.0) ? 1 : ((x.h <= 0.0) ? -1 : 0);
     return x;
   }
@@ -142,8 +153,8 @@ struct A32 {
       x.m = __fmaf_rn((float)t + 0.5f, g.fw, g.flo);
       x.r = 0.5f * g.fw;
     } else {
-      double l = __dadd_rn(g.lo, __dmul_rn((double)t, g.w));
-      double h = __dadd_rn(g.lo, __dmul_rn((double)t + 1.0, g.w));
+      double l, h;
+      endpoints(g, t, l, h);
       x.m = __double2float_rn(0.5 * l + 0.5 * h);
       double dm = (double)x.m;
       x.r = __double2float_ru(fmax(__dadd_ru(h, -dm), __dadd_ru(dm, -l)));
@@ -191,8 +202,8 @@ struct A32C {
       x.l = __fmaf_rn((float)t, g.fw, g.flo);  // exact
       x.h = __fmaf_rn((float)t + 1.0f, g.fw, g.flo);
     } else {
-      const double l = __dadd_rn(g.lo, __dmul_rn((double)t, g.w));
-      const double h = __dadd_rn(g.lo, __dmul_rn((double)t + 1.0, g.w));
+      double l, h;
+      endpoints(g, t, l, h);
       x.l = __double2float_rd(l);
       x.h = __double2float_ru(h);
     }

@@ -78,6 +78,9 @@ struct AxisGrid {
   double lo, w;
   float flo, fw;    // the same in binary32 when every half-grid point is a binary32
   int32_t fexact;   // 1 if flo/fw describe the grid exactly
+  // explicit intervals (device arrays, label t -> [xlo[t], xhi[t]]) instead of the regular
+  // grid when non-null; fexact is 0 then
+  const double *xlo, *xhi;
 };
 
 struct LevelGrid {

@@ -66,6 +66,7 @@ def lib() -> ctypes.CDLL:
         "vx_csf_tuples": ([P, P, P], i32),
         "vx_csf_eval_level": ([P, P, P, i32, P, P, P, P], i32),
         "vx_csf_eval_level_static": ([P, P, P, i32, P, P, P, P], i32),
+        "vx_csf_eval_grid": ([P, P, P, P, P, i32, P, P, P, P], i32),
         "vx_csf_subdivide": ([P, P, P, PP], i32),
         "vx_csf_compact": ([P, P, P, P, PP], i32),
         "vx_enclose_system": ([P, P, i32, P, P, PP], i32),
@@ -275,6 +276,28 @@ def csf_eval_level(system: System, csf: Csf, domain, mode=FP64, values=False, st
 
 
 STATIC_SCRATCH_BYTES = 64 << 20
+
+
+def csf_eval_grid(system: System, csf: Csf, xlists, mode=FP64, values=False, stream=None):
+    """Level evaluation on explicit per-axis intervals ``xlists[i] = (lo, hi)`` (float64 CUDA
+    tensors): keep (uint8 [n]) or (keep, lo, hi) with values=True."""
+    import torch
+
+    k, _, N = csf.nodes()
+    n = int(N[k - 1])
+    los = (ctypes.c_void_p * k)(*[int(a.data_ptr()) for a, _ in xlists])
+    his = (ctypes.c_void_p * k)(*[int(b.data_ptr()) for _, b in xlists])
+    nx = np.array([int(a.numel()) for a, _ in xlists], dtype=np.int64)
+    keep = torch.empty(max(n, 1), dtype=torch.uint8, device="cuda")
+    lo = hi = None
+    if values:
+        lo = torch.empty((system.npoly, max(n, 1)), dtype=torch.float64, device="cuda")
+        hi = torch.empty_like(lo)
+    _check(lib().vx_csf_eval_grid(system.handle, csf.handle, los, his, _np_ptr(nx), int(mode),
+                                  _ptr(lo), _ptr(hi), _ptr(keep), _stream(stream)))
+    if values:
+        return keep[:n], lo[:, :n], hi[:, :n]
+    return keep[:n]
 
 
 def csf_eval_level_static(system: System, csf: Csf, domain, mode=FP64, keep=None, lo=None,

@@ -286,7 +286,8 @@ def bench_batch(vx, synth, torch, workers=16):
     systems = [(x.polys, x.domain, x.depth) for x in synth.batch()]
     out = {"workload": "batch: 128 x (k=2, 1 Kostlan poly, d~U{10..60}) + 128 x (k=3, 2 "
                        "Kostlan polys, d~U{10..40}), depth ~U{8..10}, [-1,1]^k",
-           "workers": workers}
+           "engine": "one CSF forest per k: one launch per depth per level for all systems",
+           "timed": "vx_enclose_batch from host polynomials to device-resident results"}
     boxes = {}
     for name, mode in (("fp32", vx.FP32), ("fp64", vx.FP64)):
         for r in vx.enclose_batch(systems[:16], vx.make_opts(mode), nworkers=workers):

@@ -219,11 +219,15 @@ int vx_enclose(const vx_poly *F_list, int32_t npoly, const double *h_domain, int
 
 /* Algorithm 3 on nsys independent systems (each its own k, polynomials, domain and depth):
  * systems[i] points to npoly[i] polynomials, its domain is the next 2 k_i doubles of
- * `domains` (systems in order), depths[i] its depth; out[i] receives its result, boxes
- * already copied to the host.  The systems run concurrently, `nworkers` at a time (<= 0: 16)
- * on streams of their own, so that the kernels of small systems overlap on the GPU; each
- * result is the one vx_enclose gives for that system alone.  On failure every out[i] is NULL
- * and vx_last_error names the system. */
+ * `domains` (systems in order), depths[i] its depth; out[i] receives its result (its boxes
+ * on the device as for vx_enclose_system; vx_result_boxes copies them).  The systems with the same k
+ * run together as one forest of CSF trees per level: each depth of a level is one launch over
+ * every tree's nodes (each with its own polynomials and grid), the binary64 re-evaluations of
+ * VX_FP32 (error band) and VX_FP32_MIDRAD (tight boxes with fp64_recheck; a system's last
+ * level with fp64_final) run as one forest too, and the prune and bisection are one scan over
+ * the forest, so a level costs one host synchronisation per prune for all the systems.  Each
+ * result is the one vx_enclose gives for that system alone; its elapsed time is its group's.
+ * nworkers is not used.  On failure every out[i] is NULL. */
 int vx_enclose_batch(const vx_poly *const *systems, const int32_t *npoly, const double *domains,
                      const int32_t *depths, int32_t nsys, const vx_opts *opts, int32_t nworkers,
                      vx_result **out);

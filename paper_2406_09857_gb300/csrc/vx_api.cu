@@ -1191,83 +1191,434 @@ int vx_enclose(const vx_poly *F, int32_t npoly, const double *h_domain, int32_t 
   return rc;
 }
 
+// ---------------------------------------------------------------------------------------
+// Batches (config 4): the systems with the same k go through Algorithm 3 together, as one
+// forest of CSF trees per level.  Every depth of a level is one launch over every tree's
+// nodes (eval_forest), and the prune and bisection are one multi-channel scan over the whole
+// forest (csf_prune_forest), whose per-tree counts place each tree's nodes in the next
+// forest: one host synchronisation per level and prune for all the systems.
+// ---------------------------------------------------------------------------------------
+namespace vx {
+namespace {
+
+// mode 0: out = keep && depth(tree) == l; 1: out = keep && depth(tree) > l;
+// 2: out = out || (keep && depth(tree) == l) (the binary64 final level of VX_FP32_MIDRAD: a
+// box the midpoint-radius superset drops, binary64 drops too)
+__global__ void k_tree_mask(const uint8_t *__restrict__ keep, const int64_t *__restrict__ offl,
+                            int S, const int32_t *__restrict__ tdepth, int l, int mode,
+                            int64_t n, uint8_t *__restrict__ out) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    int lo = 0, hi = S;
+    while (hi - lo > 1) {
+      const int mid = (lo + hi) >> 1;
+      if (offl[mid] <= i) lo = mid; else hi = mid;
+    }
+    const int dep = tdepth[lo];
+    if (mode == 0) out[i] = (keep[i] && dep == l) ? 1 : 0;
+    else if (mode == 1) out[i] = (keep[i] && dep > l) ? 1 : 0;
+    else out[i] = (out[i] || (keep[i] && dep == l)) ? 1 : 0;
+  }
+}
+
+// Tree t of a forest as a CSF of its own: depth d copies nodes o[d] .. o[d]+n[d]-1, with
+// parent and child indices rebased to the tree's own arrays.
+struct TreeSlice {
+  int64_t o[VX_KMAX], n[VX_KMAX];
+};
+__global__ void k_tree_extract(CsfView f, TreeSlice ts, CsfView out) {
+  const int k = f.k;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int d = 0; d < k; ++d)
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i <= ts.n[d]; i += stride) {
+      if (i < ts.n[d]) {
+        out.lab[d][i] = f.lab[d][ts.o[d] + i];
+        if (d > 0) out.par[d][i] = (int32_t)(f.par[d][ts.o[d] + i] - ts.o[d - 1]);
+      }
+      if (d + 1 < k) out.ptr[d][i] = (int32_t)(f.ptr[d][ts.o[d] + i] - ts.o[d + 1]);
+    }
+}
+
+__global__ void k_forest_level0(CsfView c, int S) {
+  for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j <= S;
+       j += (int64_t)gridDim.x * blockDim.x)
+    for (int d = 0; d < c.k; ++d) {
+      if (j < S) {
+        c.lab[d][j] = 0;
+        if (d > 0) c.par[d][j] = (int32_t)j;
+      }
+      if (d + 1 < c.k) c.ptr[d][j] = (int32_t)j;
+    }
+}
+
+int dmalloc_copy_trees(ForestTree *d_trees, const std::vector<ForestTree> &ht, cudaStream_t s) {
+  // from pageable memory: returns once staged
+  VX_CUDA(cudaMemcpyAsync(d_trees, ht.data(), sizeof(ForestTree) * ht.size(),
+                          cudaMemcpyHostToDevice, s));
+  return VX_OK;
+}
+
+int grid1(int64_t n) {
+  int64_t b = (n + 255) / 256;
+  if (b > 152 * 16) b = 152 * 16;
+  return (int)std::max<int64_t>(b, 1);
+}
+
+struct Forest {
+  CsfObj c;
+  std::vector<int64_t> off;  // [k][S+1] host
+  int64_t *d_off = nullptr;  // device copy
+};
+
+int upload_off(Forest &F, int k, int S, cudaStream_t s) {
+  if (!F.d_off) VX_CHECK(dmalloc((void **)&F.d_off, sizeof(int64_t) * (size_t)k * (S + 1), s));
+  VX_CUDA(cudaMemcpyAsync(F.d_off, F.off.data(), sizeof(int64_t) * (size_t)k * (S + 1),
+                          cudaMemcpyHostToDevice, s));
+  return VX_OK;
+}
+
+void release(Forest &F, cudaStream_t s) {
+  csf_release(&F.c);
+  dfree(F.d_off, s);
+  F.d_off = nullptr;
+}
+
+// Prunes forest `in` with mask `m` (split or compact) into `out`, with per-tree offsets.
+int prune_forest(Forest &in, const uint8_t *m, int split, int32_t *d_index, int k, int S,
+                 int64_t *d_seg, std::vector<int64_t> &h_seg, cudaStream_t s, Forest &out) {
+  VX_CHECK(csf_prune_forest(in.c.v, m, split, d_index, in.d_off, S, d_seg, s, &out.c, nullptr));
+  h_seg.assign((size_t)k * (S + 1), 0);
+  VX_CUDA(cudaMemcpyAsync(h_seg.data(), d_seg, sizeof(int64_t) * h_seg.size(),
+                          cudaMemcpyDeviceToHost, s));
+  VX_CUDA(cudaStreamSynchronize(s));
+  out.off.assign(h_seg.size(), 0);
+  for (int d = 0; d < k; ++d)
+    for (int t = 0; t <= S; ++t)
+      out.off[(size_t)d * (S + 1) + t] = h_seg[(size_t)d * (S + 1) + t] << (split ? d + 1 : 0);
+  return upload_off(out, k, S, s);
+}
+
+int batch_group(const std::vector<int32_t> &ids, const vx_poly *const *systems,
+                const int32_t *npoly, const double *domains, const std::vector<int64_t> &doff,
+                const int32_t *depths, const vx_opts &opts, cudaStream_t s, vx_result **out) {
+  const int S = (int)ids.size();
+  const int k = systems[ids[0]][0].nvars;
+  const float theta = opts.theta > 0.f ? opts.theta : 0.5f;
+  std::vector<vx_system *> sysv(S, nullptr);
+  std::vector<ForestTree> ht(S);
+  std::vector<int32_t> tdep(S);
+  int maxdepth = 0, rc = VX_OK;
+  for (int t = 0; t < S && rc == VX_OK; ++t) {
+    const int i = ids[t];
+    if (depths[i] < 0 || depths[i] > VX_MAXLEVEL) {
+      set_error("system %d: depth %d outside [0, %d]", i, depths[i], VX_MAXLEVEL);
+      rc = VX_EINVAL;
+      break;
+    }
+    tdep[t] = depths[i];
+    maxdepth = std::max(maxdepth, depths[i]);
+    LevelGrid g;
+    rc = make_grid(k, domains + doff[i], depths[i], &g);  // the finest grid exact => all coarser
+  }
+  // packing is host work: host threads pack and upload the systems, each on a stream of its
+  // own; the forest then reads them on `s`
+  if (rc == VX_OK) {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) rc = VX_ECUDA;
+    const int nthr = std::max(1, std::min<int>(16, S));
+    std::atomic<int> next{0}, first{VX_OK};
+    std::vector<std::string> errs(nthr);
+    auto work = [&](int w) {
+      cudaStream_t ws = nullptr;
+      if (cudaSetDevice(dev) != cudaSuccess ||
+          cudaStreamCreateWithFlags(&ws, cudaStreamNonBlocking) != cudaSuccess) {
+        first = VX_ECUDA;
+        return;
+      }
+      for (int t = next++; t < S && first.load() == VX_OK; t = next++) {
+        const int r = vx_system_create(systems[ids[t]], npoly[ids[t]], (void *)ws, &sysv[t]);
+        if (r != VX_OK) {
+          errs[w] = std::string("system ") + std::to_string(ids[t]) + ": " + vx_last_error();
+          int expected = VX_OK;
+          first.compare_exchange_strong(expected, r);
+        } else {
+          sysv[t]->stream = s;  // synchronised already; freed in the order of `s`
+        }
+      }
+      cudaStreamDestroy(ws);
+    };
+    if (rc == VX_OK) {
+      std::vector<std::thread> pool;
+      for (int w = 0; w < nthr; ++w) pool.emplace_back(work, w);
+      for (auto &th : pool) th.join();
+      rc = first.load();
+      if (rc != VX_OK)
+        for (auto &e : errs)
+          if (!e.empty()) {
+            set_error("%s", e.c_str());
+            break;
+          }
+    }
+    for (int t = 0; t < S && rc == VX_OK; ++t) ht[t].dev = sysv[t]->dev;
+  }
+  ForestTree *d_trees = nullptr;
+  int32_t *d_tdep = nullptr;
+  int64_t *d_seg = nullptr;
+  if (rc == VX_OK) rc = dmalloc((void **)&d_trees, sizeof(ForestTree) * S, s);
+  if (rc == VX_OK) rc = dmalloc((void **)&d_tdep, sizeof(int32_t) * S, s);
+  if (rc == VX_OK) rc = dmalloc((void **)&d_seg, sizeof(int64_t) * (size_t)k * (S + 1), s);
+  if (rc == VX_OK) {
+    cudaError_t e = cudaMemcpyAsync(d_tdep, tdep.data(), sizeof(int32_t) * S,
+                                    cudaMemcpyHostToDevice, s);
+    if (e != cudaSuccess) rc = VX_ECUDA;
+  }
+  std::vector<vx_result *> R(S, nullptr);
+  for (int t = 0; t < S && rc == VX_OK; ++t) {
+    R[t] = new (std::nothrow) vx_result();
+    if (!R[t]) {
+      set_error("out of host memory");
+      rc = VX_ENOMEM;
+      break;
+    }
+    const int D = tdep[t];
+    R[t]->k = k;
+    R[t]->depth = D;
+    R[t]->tested.assign(D + 1, 0);
+    R[t]->kept.assign(D + 1, 0);
+    R[t]->nodes.assign((size_t)(D + 1) * k, 0);
+    R[t]->recheck.assign(D + 1, 0);
+    R[t]->madds.assign(D + 1, 0);
+    // an empty tree until the system finishes (a system whose boxes all go keeps it)
+    int64_t N0[VX_KMAX] = {0};
+    if (csf_alloc(&R[t]->fin, k, D, N0, s) != VX_OK || set_ptr_sentinels(R[t]->fin.v, s) != VX_OK)
+      rc = VX_ENOMEM;
+  }
+  cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+  if (rc == VX_OK && (cudaEventCreate(&ev0) != cudaSuccess || cudaEventCreate(&ev1) != cudaSuccess))
+    rc = VX_ECUDA;
+  if (rc == VX_OK && cudaEventRecord(ev0, s) != cudaSuccess) rc = VX_ECUDA;
+  // level 0: one box per tree
+  Forest cur;
+  if (rc == VX_OK) {
+    int64_t N[VX_KMAX] = {S, S, S, S};
+    rc = csf_alloc(&cur.c, k, 0, N, s);
+    if (rc == VX_OK) {
+      k_forest_level0<<<grid1(S + 1), 256, 0, s>>>(cur.c.v, S);
+      note_launch();
+      cur.off.assign((size_t)k * (S + 1), 0);
+      for (int d = 0; d < k; ++d)
+        for (int t = 0; t <= S; ++t) cur.off[(size_t)d * (S + 1) + t] = t;
+      rc = upload_off(cur, k, S, s);
+    }
+  }
+  std::vector<int64_t> hseg;
+  for (int l = 0; l <= maxdepth && rc == VX_OK; ++l) {
+    const int64_t n = cur.c.v.N[k - 1];
+    bool any_final = false, any_cont = false;
+    for (int t = 0; t < S; ++t) {
+      if (tdep[t] < l) continue;
+      const int64_t nt = cur.off[(size_t)(k - 1) * (S + 1) + t + 1] - cur.off[(size_t)(k - 1) * (S + 1) + t];
+      R[t]->tested[l] = nt;
+      for (int d = 0; d < k; ++d)
+        R[t]->nodes[(size_t)l * k + d] =
+            cur.off[(size_t)d * (S + 1) + t + 1] - cur.off[(size_t)d * (S + 1) + t];
+      if (nt > 0) (tdep[t] == l ? any_final : any_cont) = true;
+      LevelGrid g;
+      rc = make_grid(k, domains + doff[ids[t]], l, &g);
+      if (rc != VX_OK) break;
+      for (int d = 0; d < k; ++d) ht[t].ax[d] = g.ax[d];
+    }
+    if (rc != VX_OK || n == 0) break;
+    rc = dmalloc_copy_trees(d_trees, ht, s);
+    uint8_t *keep = nullptr, *flag = nullptr, *m = nullptr;
+    if (rc == VX_OK) rc = dmalloc((void **)&keep, (size_t)n, s);
+    if (rc == VX_OK) rc = dmalloc((void **)&flag, (size_t)n, s);
+    if (rc == VX_OK) rc = dmalloc((void **)&m, (size_t)n, s);
+    // evaluate: the arithmetic of opts; binary64 for the flagged boxes (VX_FP32: the error
+    // band; VX_FP32_MIDRAD: tight boxes with fp64_recheck, every box of a finishing tree with
+    // fp64_final)
+    const int arith = opts.mode == VX_FP64 ? ARITH_F64
+                      : (opts.mode == VX_FP32 ? ARITH_F32_CERT : ARITH_F32_MIDRAD);
+    const bool flagged = opts.mode == VX_FP32 || (opts.mode == VX_FP32_MIDRAD && opts.fp64_recheck);
+    int64_t w = 0;
+    if (rc == VX_OK)
+      rc = eval_forest(arith, d_trees, ht.data(), cur.d_off, cur.off.data(), S, cur.c.v, keep,
+                       flagged ? flag : nullptr, theta, s, &w);
+    if (rc == VX_OK && !flagged && (opts.mode == VX_FP32_MIDRAD && opts.fp64_final))
+      if (cudaMemsetAsync(flag, 0, (size_t)n, s) != cudaSuccess) rc = VX_ECUDA;
+    const bool recheck = flagged || (opts.mode == VX_FP32_MIDRAD && opts.fp64_final && any_final);
+    if (rc == VX_OK && opts.mode == VX_FP32_MIDRAD && opts.fp64_final && any_final) {
+      k_tree_mask<<<grid1(n), 256, 0, s>>>(keep, cur.d_off + (int64_t)(k - 1) * (S + 1), S,
+                                           d_tdep, l, 2, n, flag);
+      note_launch();
+    }
+    // per-tree madds of the level (host, from the counts)
+    for (int t = 0; t < S && rc == VX_OK; ++t) {
+      if (tdep[t] < l) continue;
+      int64_t mt = 0;
+      for (int f = 0; f < ht[t].dev.npoly; ++f)
+        for (int d = 0; d < k; ++d) {
+          const StageDev &st = ht[t].dev.p[f].st[d];
+          mt += (cur.off[(size_t)d * (S + 1) + t + 1] - cur.off[(size_t)d * (S + 1) + t]) *
+                (st.blk_in - st.nfib);
+        }
+      R[t]->madds[l] += mt;
+    }
+    if (rc == VX_OK && recheck) {
+      // the flagged leaves as a forest of their own, in binary64; decisions scattered back
+      Forest sub;
+      int32_t *idx = nullptr;
+      uint8_t *subkeep = nullptr;
+      rc = dmalloc((void **)&idx, (size_t)n * sizeof(int32_t), s);
+      if (rc == VX_OK) rc = prune_forest(cur, flag, 0, idx, k, S, d_seg, hseg, s, sub);
+      const int64_t ns = sub.c.v.N[k - 1];
+      for (int t = 0; t < S && rc == VX_OK; ++t)
+        if (tdep[t] >= l)
+          R[t]->recheck[l] = sub.off[(size_t)(k - 1) * (S + 1) + t + 1] -
+                             sub.off[(size_t)(k - 1) * (S + 1) + t];
+      if (rc == VX_OK && ns > 0) {
+        rc = dmalloc((void **)&subkeep, (size_t)ns, s);
+        int64_t w2 = 0;
+        if (rc == VX_OK)
+          rc = eval_forest(ARITH_F64, d_trees, ht.data(), sub.d_off, sub.off.data(), S, sub.c.v,
+                           subkeep, nullptr, 0.f, s, &w2);
+        if (rc == VX_OK) rc = scatter_keep(idx, subkeep, ns, keep, s);
+      }
+      dfree(subkeep, s);
+      dfree(idx, s);
+      release(sub, s);
+    }
+    // finishing trees: their kept boxes are the result, each tree's as a CSF of its own
+    if (rc == VX_OK && any_final) {
+      Forest fin;
+      k_tree_mask<<<grid1(n), 256, 0, s>>>(keep, cur.d_off + (int64_t)(k - 1) * (S + 1), S,
+                                           d_tdep, l, 0, n, m);
+      note_launch();
+      rc = prune_forest(cur, m, 0, nullptr, k, S, d_seg, hseg, s, fin);
+      for (int t = 0; t < S && rc == VX_OK; ++t) {
+        if (tdep[t] != l) continue;
+        TreeSlice ts;
+        int64_t N[VX_KMAX] = {0};
+        for (int d = 0; d < VX_KMAX; ++d) ts.o[d] = ts.n[d] = 0;
+        for (int d = 0; d < k; ++d) {
+          ts.o[d] = fin.off[(size_t)d * (S + 1) + t];
+          ts.n[d] = N[d] = fin.off[(size_t)d * (S + 1) + t + 1] - ts.o[d];
+        }
+        R[t]->kept[l] = N[k - 1];
+        csf_release(&R[t]->fin);
+        rc = csf_alloc(&R[t]->fin, k, l, N, s);
+        if (rc == VX_OK) {
+          k_tree_extract<<<grid1(N[k - 1] + 1), 256, 0, s>>>(fin.c.v, ts, R[t]->fin.v);
+          note_launch();
+          if (cudaGetLastError() != cudaSuccess) rc = VX_ECUDA;
+        }
+      }
+      release(fin, s);
+    }
+    // the others go on: bisect their kept boxes into the next level's forest
+    Forest next;
+    if (rc == VX_OK) {
+      k_tree_mask<<<grid1(n), 256, 0, s>>>(keep, cur.d_off + (int64_t)(k - 1) * (S + 1), S,
+                                           d_tdep, l, 1, n, m);
+      note_launch();
+      if (any_cont) {
+        rc = prune_forest(cur, m, 1, nullptr, k, S, d_seg, hseg, s, next);
+        for (int t = 0; t < S && rc == VX_OK; ++t)
+          if (tdep[t] > l)
+            R[t]->kept[l] = hseg[(size_t)(k - 1) * (S + 1) + t + 1] - hseg[(size_t)(k - 1) * (S + 1) + t];
+      }
+    }
+    dfree(m, s);
+    dfree(flag, s);
+    dfree(keep, s);
+    int st = 0;
+    if (rc == VX_OK) rc = take_device_status(s, &st);
+    if (rc == VX_OK && st) {
+      set_error("a bounded device wait gave up at level %d", l);
+      rc = VX_ETIMEOUT;
+    }
+    release(cur, s);
+    if (rc != VX_OK || !any_cont) {
+      release(next, s);
+      break;
+    }
+    cur = next;
+  }
+  release(cur, s);
+  if (rc == VX_OK) {
+    float ms = 0.f;
+    cudaError_t e = cudaEventRecord(ev1, s);
+    if (e == cudaSuccess) e = cudaEventSynchronize(ev1);
+    if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, ev0, ev1);
+    if (e != cudaSuccess) {
+      set_error("batch: %s", cudaGetErrorString(e));
+      rc = VX_ECUDA;
+    }
+    for (int t = 0; t < S; ++t) R[t]->elapsed_ms = ms;  // the group's wall time
+  }
+  if (ev0) cudaEventDestroy(ev0);
+  if (ev1) cudaEventDestroy(ev1);
+  dfree(d_seg, s);
+  dfree(d_tdep, s);
+  dfree(d_trees, s);
+  if (cudaStreamSynchronize(s) != cudaSuccess && rc == VX_OK) rc = VX_ECUDA;
+  for (int t = 0; t < S; ++t) vx_system_free(sysv[t]);
+  for (int t = 0; t < S; ++t) {
+    if (rc == VX_OK)
+      out[ids[t]] = R[t];
+    else
+      vx_result_free(R[t]);
+  }
+  return rc;
+}
+
+}  // namespace
+}  // namespace vx
+
 int vx_enclose_batch(const vx_poly *const *systems, const int32_t *npoly, const double *domains,
                      const int32_t *depths, int32_t nsys, const vx_opts *opts, int32_t nworkers,
                      vx_result **out) {
   clear_error();
+  (void)nworkers;
   if (!systems || !npoly || !domains || !depths || !out || nsys < 0) {
     set_error("vx_enclose_batch: NULL argument or negative count");
     return VX_EINVAL;
   }
   for (int32_t i = 0; i < nsys; ++i) out[i] = nullptr;
   if (nsys == 0) return VX_OK;
-  int dev = 0;
-  VX_CUDA(cudaGetDevice(&dev));
-  // domain offsets: system i owns 2 * k_i doubles
+  vx_opts o{};
+  if (opts) o = *opts;
+  if (o.mode != VX_FP64 && o.mode != VX_FP32_MIDRAD && o.mode != VX_FP32) {
+    set_error("vx_enclose_batch: unknown mode %d", o.mode);
+    return VX_EINVAL;
+  }
+  // domain offsets: system i owns 2 * k_i doubles; groups of equal k
   std::vector<int64_t> doff(nsys + 1, 0);
+  std::vector<std::vector<int32_t>> groups(VX_KMAX + 1);
   for (int32_t i = 0; i < nsys; ++i) {
     if (!systems[i] || npoly[i] < 1) {
       set_error("vx_enclose_batch: system %d has no polynomials", i);
       return VX_EINVAL;
     }
-    doff[i + 1] = doff[i] + 2 * (int64_t)systems[i][0].nvars;
+    const int k = systems[i][0].nvars;
+    if (k < 1 || k > VX_KMAX) {
+      set_error("vx_enclose_batch: system %d has %d variables (1..%d)", i, k, VX_KMAX);
+      return VX_EINVAL;
+    }
+    doff[i + 1] = doff[i] + 2 * (int64_t)k;
+    groups[k].push_back(i);
   }
-  const int nw = std::max(1, std::min<int>(nworkers > 0 ? nworkers : 16, nsys));
-  std::atomic<int32_t> next{0};
-  std::atomic<int> first_rc{VX_OK};
-  std::vector<std::string> errs(nw);
-  auto worker = [&](int w) {
-    if (cudaSetDevice(dev) != cudaSuccess) {
-      first_rc = VX_ECUDA;
-      return;
-    }
-    cudaStream_t s = nullptr;
-    if (cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking) != cudaSuccess) {
-      first_rc = VX_ECUDA;
-      return;
-    }
-    for (int32_t i = next++; i < nsys && first_rc.load() == VX_OK; i = next++) {
-      vx_system *sys = nullptr;
-      int rc = vx_system_create(systems[i], npoly[i], (void *)s, &sys);
-      if (rc == VX_OK) rc = vx_enclose_system(sys, domains + doff[i], depths[i], opts, (void *)s, &out[i]);
-      vx_system_free(sys);
-      if (rc == VX_OK) {
-        int64_t n = 0;
-        const int32_t *t = nullptr;
-        rc = vx_result_boxes(out[i], &n, &t);
-      }
-      if (rc == VX_OK) {
-        // this worker's stream ends with it: once the system's work is complete, the result's
-        // memory is freed in the order of the default stream instead
-        if (cudaStreamSynchronize(s) != cudaSuccess) rc = VX_ECUDA;
-        out[i]->fin.stream = nullptr;
-        out[i]->tm.stream = nullptr;
-      }
-      if (rc != VX_OK) {
-        vx_result_free(out[i]);  // while its stream still exists
-        out[i] = nullptr;
-        errs[w] = std::string("system ") + std::to_string(i) + ": " + vx_last_error();
-        int expected = VX_OK;
-        first_rc.compare_exchange_strong(expected, rc);
-      }
-    }
-    cudaStreamSynchronize(s);
-    cudaStreamDestroy(s);
-  };
-  std::vector<std::thread> pool;
-  for (int w = 0; w < nw; ++w) pool.emplace_back(worker, w);
-  for (auto &t : pool) t.join();
-  const int rc = first_rc.load();
+  cudaStream_t s = library_stream();
+  int rc = VX_OK;
+  for (int k = 1; k <= VX_KMAX && rc == VX_OK; ++k)
+    if (!groups[k].empty()) rc = batch_group(groups[k], systems, npoly, domains, doff, depths, o, s, out);
   if (rc != VX_OK) {
-    for (auto &e : errs)
-      if (!e.empty()) {
-        set_error("vx_enclose_batch: %s", e.c_str());
-        break;
-      }
+    const std::string msg = std::string("vx_enclose_batch: ") + vx_last_error();
     for (int32_t i = 0; i < nsys; ++i) {
       vx_result_free(out[i]);
       out[i] = nullptr;
     }
+    set_error("%s", msg.c_str());
   }
   return rc;
 }
@@ -1301,7 +1652,7 @@ int vx_result_boxes(vx_result *R, int64_t *n, const int32_t **h_tuples) {
     }
     R->have_tuples = true;
   }
-  *n = R->fin.v.N[R->k - 1];
+  *n = (int64_t)(R->tuples.size() / (size_t)R->k);
   *h_tuples = R->tuples.data();
   return VX_OK;
 }

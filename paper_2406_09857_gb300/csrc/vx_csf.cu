@@ -569,6 +569,20 @@ int blocks_for(int64_t n) {
   return (int)b;
 }
 
+// Forest segments: seg_off[d * (S+1) + s] is the first depth-d node of tree-set s (s = 0..S,
+// seg_off[.. + S] = N_d); kept[d * (S+1) + s] receives the kept depth-d nodes before it.
+__global__ void k_seg_kept(const int64_t *__restrict__ seg_off, int S, int k,
+                           const int32_t *__restrict__ rank, Segs sg, const int32_t *totals,
+                           int64_t *__restrict__ kept) {
+  const int64_t n = (int64_t)k * (S + 1);
+  for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < n;
+       j += (int64_t)gridDim.x * blockDim.x) {
+    const int d = (int)(j / (S + 1));
+    const int64_t i = seg_off[j];
+    kept[j] = i >= sg.off[d + 1] - sg.off[d] ? (int64_t)totals[d] : (int64_t)rank[sg.off[d] + i];
+  }
+}
+
 // run-time depth -> template argument
 void launch_kptr(int d, int blocks, cudaStream_t s, const CsfView &in, const uint8_t *flags,
                  const int32_t *rank, const Segs &sg, int32_t *kptr) {
@@ -602,7 +616,8 @@ void launch_split(int d, int blocks, cudaStream_t s, const CsfView &in, const ui
 
 template <int C>
 int prune_c(const CsfView &in, const uint8_t *d_keep, int split, int32_t *d_index,
-            cudaStream_t s, CsfObj *out, Timer *tm) {
+            cudaStream_t s, CsfObj *out, Timer *tm, const int64_t *d_seg_off = nullptr,
+            int nseg = 0, int64_t *d_seg_kept = nullptr) {
   const int k = in.k;
   Segs sg;
   sg.k = k;
@@ -617,6 +632,8 @@ int prune_c(const CsfView &in, const uint8_t *d_keep, int split, int32_t *d_inde
   if (in.N[k - 1] == 0) {  // empty level: empty result
     int64_t N[VX_KMAX] = {0};
     VX_CHECK(csf_alloc(out, k, in.level + (split ? 1 : 0), N, s));
+    if (d_seg_kept)
+      VX_CUDA(cudaMemsetAsync(d_seg_kept, 0, sizeof(int64_t) * (size_t)k * (nseg + 1), s));
     return set_ptr_sentinels(out->v, s);
   }
   uint8_t *flags = nullptr;
@@ -647,6 +664,16 @@ int prune_c(const CsfView &in, const uint8_t *d_keep, int split, int32_t *d_inde
   int32_t nk[C];
   if (rc == VX_OK) rc = scan_prepare<C>(src, total, s, &scratch, &ntiles, nk);
   if (rc == VX_OK) rc = scan_emit<C>(src, RankEmit{rank, src}, total, scratch, ntiles, s);
+  if (rc == VX_OK && d_seg_off) {
+    // the channel totals sit after the tile sums in the scan scratch
+    k_seg_kept<<<blocks_for((int64_t)k * (nseg + 1)), 256, 0, s>>>(
+        d_seg_off, nseg, k, rank, sg, scratch + (int64_t)C * ntiles, d_seg_kept);
+    note_launch();
+    if (cudaGetLastError() != cudaSuccess) {
+      set_error("segment count kernel launch failed");
+      rc = VX_ECUDA;
+    }
+  }
   // kept-tree first-child pointers
   KptrSet K{};
   int64_t koff[VX_KMAX + 1] = {0};
@@ -832,6 +859,17 @@ int csf_prune(const CsfView &in, const uint8_t *d_keep, int split, int32_t *d_in
     case 2: return prune_c<2>(in, d_keep, split, d_index, s, out, tm);
     case 3: return prune_c<3>(in, d_keep, split, d_index, s, out, tm);
     default: return prune_c<4>(in, d_keep, split, d_index, s, out, tm);
+  }
+}
+
+int csf_prune_forest(const CsfView &in, const uint8_t *d_keep, int split, int32_t *d_index,
+                     const int64_t *d_seg_off, int nseg, int64_t *d_seg_kept, cudaStream_t s,
+                     CsfObj *out, Timer *tm) {
+  switch (in.k) {
+    case 1: return prune_c<1>(in, d_keep, split, d_index, s, out, tm, d_seg_off, nseg, d_seg_kept);
+    case 2: return prune_c<2>(in, d_keep, split, d_index, s, out, tm, d_seg_off, nseg, d_seg_kept);
+    case 3: return prune_c<3>(in, d_keep, split, d_index, s, out, tm, d_seg_off, nseg, d_seg_kept);
+    default: return prune_c<4>(in, d_keep, split, d_index, s, out, tm, d_seg_off, nseg, d_seg_kept);
   }
 }
 

@@ -347,34 +347,53 @@ __device__ __forceinline__ typename AR::V horner1_any(const typename AR::V *__re
 // (out_estride = nnodes, out_nstride = 1) when an inner stage reads it, node-major
 // (out_estride = 1, out_nstride = blk_out) when the leaves do, so that a leaf's Horner walks
 // consecutive entries of its parent's block.
+// One warp's share of k_stage: nodes chunk*32 + lane (of nnodes), fibres g, g+G, ....  par
+// holds parent indices of the parent array; poff is subtracted to index `in` (0 for one tree).
+template <class AR>
+__device__ __forceinline__ void stage_chunk(const StageDev &st, const int32_t *rowoff,
+                                            const int32_t *__restrict__ lab,
+                                            const int32_t *__restrict__ par, int64_t poff,
+                                            const typename AR::V *__restrict__ in,
+                                            int64_t in_estride, int64_t in_nstride,
+                                            typename AR::V *__restrict__ out, int64_t out_estride,
+                                            int64_t out_nstride, int64_t nnodes, int64_t chunk,
+                                            int grp, int G, const AxisGrid &g) {
+  using V = typename AR::V;
+  const int lane = threadIdx.x & 31;
+  const int64_t node = chunk * 32 + lane;
+  const bool live = node < nnodes;
+  const int64_t nd = live ? node : nnodes - 1;  // idle lanes follow the last node, no store
+  const V *base = par ? in + ((int64_t)__ldg(par + nd) - poff) * in_nstride : in;
+  const typename AR::X x = AR::box(g, __ldg(lab + nd));
+  V *dst = out + node * out_nstride;
+  for (int f = grp; f < st.nfib; f += G) {
+    const int L = __ldg(st.fiblen + f);
+    const V J = horner_any<AR>(base, in_estride, rowoff, f, L, x);
+    if (live) dst[(int64_t)__ldg(st.outpos + f) * out_estride] = AR::store(J);
+  }
+}
+
+// Stage d < k-1 on every depth-d node.  Warp w takes node chunk w % nchunk (32 nodes, one per
+// lane) and fibres g, g+G, ... with g = w / nchunk.  in: entry e of parent p's block at
+// in[e * in_estride + p * in_nstride] (the coefficient tensor: in_estride 1, in_nstride 0).
+// out: entry e of node i at out[e * out_estride + i * out_nstride]: entry-major
+// (out_estride = nnodes, out_nstride = 1) when an inner stage reads it, node-major
+// (out_estride = 1, out_nstride = blk_out) when the leaves do, so that a leaf's Horner walks
+// consecutive entries of its parent's block.
 template <class AR>
 __global__ void __launch_bounds__(kThreads)
     k_stage(const StageDev st, const int32_t *__restrict__ lab, const int32_t *__restrict__ par,
             const typename AR::V *__restrict__ in, int64_t in_estride, int64_t in_nstride,
             typename AR::V *__restrict__ out, int64_t out_estride, int64_t out_nstride,
             int64_t nnodes, int64_t nchunk, int G, AxisGrid g) {
-  using V = typename AR::V;
   extern __shared__ int32_t s_rowoff[];
   for (int i = threadIdx.x; i <= st.maxlen; i += blockDim.x) s_rowoff[i] = st.rowoff[i];
   __syncthreads();
-  const int lane = threadIdx.x & 31;
   const int64_t nwarps = nchunk * G;
   for (int64_t w = (int64_t)blockIdx.x * kWarpsPerBlock + (threadIdx.x >> 5); w < nwarps;
-       w += (int64_t)gridDim.x * kWarpsPerBlock) {
-    const int64_t chunk = w % nchunk;
-    const int grp = (int)(w / nchunk);
-    const int64_t node = chunk * 32 + lane;
-    const bool live = node < nnodes;
-    const int64_t nd = live ? node : nnodes - 1;  // idle lanes follow the last node, no store
-    const V *base = par ? in + (int64_t)__ldg(par + nd) * in_nstride : in;
-    const typename AR::X x = AR::box(g, __ldg(lab + nd));
-    V *dst = out + node * out_nstride;
-    for (int f = grp; f < st.nfib; f += G) {
-      const int L = __ldg(st.fiblen + f);
-      const V J = horner_any<AR>(base, in_estride, s_rowoff, f, L, x);
-      if (live) dst[(int64_t)__ldg(st.outpos + f) * out_estride] = AR::store(J);
-    }
-  }
+       w += (int64_t)gridDim.x * kWarpsPerBlock)
+    stage_chunk<AR>(st, s_rowoff, lab, par, 0, in, in_estride, in_nstride, out, out_estride,
+                    out_nstride, nnodes, w % nchunk, (int)(w / nchunk), G, g);
 }
 
 // Stage d (1 <= d < k-1) with the parent's block in shared memory.  CTA b takes parent
@@ -432,43 +451,55 @@ struct LeafArgs {
   int32_t len[VX_MAXPOLY];
 };
 
+// Last stage on leaf i: one Horner per polynomial, then C0 (par: parent indices, minus poff
+// to index the blocks of A).
+template <class AR>
+__device__ __forceinline__ void leaf_item(const LeafArgs &A, int npoly,
+                                          const int32_t *__restrict__ lab,
+                                          const int32_t *__restrict__ par, int64_t poff,
+                                          int64_t i, int64_t nleaves, const AxisGrid &g,
+                                          uint8_t *__restrict__ keep, double *__restrict__ lo,
+                                          double *__restrict__ hi, uint8_t *__restrict__ flag,
+                                          float theta) {
+  using V = typename AR::V;
+  const typename AR::X x = AR::box(g, __ldg(lab + i));
+  const int64_t p = par ? (int64_t)__ldg(par + i) - poff : 0;
+  bool excl = false, amb = false, tg = false;
+  auto decide = [&](int f, const V &J) {
+    if (lo) {
+      lo[(int64_t)f * nleaves + i] = AR::lo(J);
+      hi[(int64_t)f * nleaves + i] = AR::hi(J);
+    }
+    const int c = AR::classify(J);
+    excl = excl || c == 0;
+    amb = amb || c == 2;
+    tg = tg || AR::tight(J, theta);
+  };
+  int f = 0;
+  for (; f + 1 < npoly && A.len[f] == A.len[f + 1]; f += 2) {
+    V J0, J1;
+    horner1x2_any<AR>((const V *)A.in[f] + p * A.blk[f], (const V *)A.in[f + 1] + p * A.blk[f + 1],
+                      A.len[f], x, J0, J1);
+    decide(f, J0);
+    decide(f + 1, J1);
+  }
+  for (; f < npoly; ++f) {
+    const V *base = (const V *)A.in[f] + p * A.blk[f];
+    decide(f, horner1_any<AR>(base, 1, A.len[f], x));
+  }
+  keep[i] = excl ? 0 : 1;
+  if (flag) flag[i] = (!excl && (amb || tg)) ? 1 : 0;
+}
+
 // Last stage on every leaf: one Horner per polynomial, then C0.  Lane = leaf.
 template <class AR>
 __global__ void __launch_bounds__(kThreads)
     k_leaf(LeafArgs A, int npoly, const int32_t *__restrict__ lab, const int32_t *__restrict__ par,
            int64_t nleaves, AxisGrid g, uint8_t *__restrict__ keep, double *__restrict__ lo,
            double *__restrict__ hi, uint8_t *__restrict__ flag, float theta) {
-  using V = typename AR::V;
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < nleaves; i += stride) {
-    const typename AR::X x = AR::box(g, __ldg(lab + i));
-    const int64_t p = par ? (int64_t)__ldg(par + i) : 0;
-    bool excl = false, amb = false, tg = false;
-    auto decide = [&](int f, const V &J) {
-      if (lo) {
-        lo[(int64_t)f * nleaves + i] = AR::lo(J);
-        hi[(int64_t)f * nleaves + i] = AR::hi(J);
-      }
-      const int c = AR::classify(J);
-      excl = excl || c == 0;
-      amb = amb || c == 2;
-      tg = tg || AR::tight(J, theta);
-    };
-    int f = 0;
-    for (; f + 1 < npoly && A.len[f] == A.len[f + 1]; f += 2) {
-      V J0, J1;
-      horner1x2_any<AR>((const V *)A.in[f] + p * A.blk[f], (const V *)A.in[f + 1] + p * A.blk[f + 1],
-                        A.len[f], x, J0, J1);
-      decide(f, J0);
-      decide(f + 1, J1);
-    }
-    for (; f < npoly; ++f) {
-      const V *base = (const V *)A.in[f] + p * A.blk[f];
-      decide(f, horner1_any<AR>(base, 1, A.len[f], x));
-    }
-    keep[i] = excl ? 0 : 1;
-    if (flag) flag[i] = (!excl && (amb || tg)) ? 1 : 0;
-  }
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < nleaves; i += stride)
+    leaf_item<AR>(A, npoly, lab, par, 0, i, nleaves, g, keep, lo, hi, flag, theta);
 }
 
 // Last stage in the certified binary32 arithmetic, two consecutive leaves per thread.  When
@@ -587,11 +618,59 @@ __device__ __forceinline__ void horner_y2_fibre(const float4 *__restrict__ base,
   }
 }
 
+// One warp's share of k_stage_c: node pairs of chunk `chunk` (64 nodes), fibres g, g+G, ....
+// A warp whose 32 pairs each share a parent and do not straddle 0 shares every load between
+// the two nodes and runs sign-free (horner_y2_fibre); any other warp takes k_stage's per-node
+// path.  par/poff as in stage_chunk.
+__device__ __forceinline__ void stage_chunk_c(const StageDev &st, const int32_t *rowoff,
+                                              const int32_t *__restrict__ lab,
+                                              const int32_t *__restrict__ par, int64_t poff,
+                                              const float4 *__restrict__ in, int64_t in_estride,
+                                              int64_t in_nstride, float4 *__restrict__ out,
+                                              int64_t out_estride, int64_t out_nstride,
+                                              int64_t nnodes, int64_t chunk, int grp, int G,
+                                              const AxisGrid &g) {
+  const int lane = threadIdx.x & 31;
+  const int64_t npairs = (nnodes + 1) >> 1;
+  const int64_t q = chunk * 32 + lane;
+  const bool live = q < npairs;
+  const int64_t i0 = 2 * (live ? q : npairs - 1);
+  const bool two = live && i0 + 1 < nnodes;
+  const int64_t i1 = i0 + 1 < nnodes ? i0 + 1 : i0;
+  const A32C::X x0 = A32C::box(g, __ldg(lab + i0)), x1 = A32C::box(g, __ldg(lab + i1));
+  const int64_t p0 = par ? (int64_t)__ldg(par + i0) - poff : 0;
+  const int64_t p1 = par ? (int64_t)__ldg(par + i1) - poff : 0;
+  const bool fast = p0 == p1 && x0.cls != 0 && x1.cls != 0;
+  if (__all_sync(0xffffffffu, fast)) {
+    const YLeaf y0 = yleaf(x0), y1 = yleaf(x1);
+    const float4 *base = in + p0 * in_nstride;
+    for (int f = grp; f < st.nfib; f += G) {
+      const int L = __ldg(st.fiblen + f);
+      float4 K0, K1;
+      horner_y2_fibre(base, in_estride, rowoff, f, L, y0, y1, K0, K1);
+      const int64_t o = (int64_t)__ldg(st.outpos + f) * out_estride;
+      if (live) out[i0 * out_nstride + o] = A32C::store(K0);
+      if (two) out[i1 * out_nstride + o] = A32C::store(K1);
+    }
+  } else {
+#pragma unroll 1
+    for (int c = 0; c < 2; ++c) {
+      const A32C::X &x = c == 0 ? x0 : x1;
+      const float4 *base = in + (c == 0 ? p0 : p1) * in_nstride;
+      const bool wr = c == 0 ? live : two;
+      const int64_t node = c == 0 ? i0 : i1;
+      for (int f = grp; f < st.nfib; f += G) {
+        const int L = __ldg(st.fiblen + f);
+        const float4 J = horner_any<A32C>(base, in_estride, rowoff, f, L, x);
+        if (wr) out[node * out_nstride + (int64_t)__ldg(st.outpos + f) * out_estride] = A32C::store(J);
+      }
+    }
+  }
+}
+
 // Stage d < k-1 in the certified binary32 arithmetic, two consecutive nodes per thread: warp w
 // takes node pairs of chunk w % nchunk (64 nodes) and fibres g, g+G, ... (g = w / nchunk), as
-// k_stage does with one node per lane.  A warp whose 32 pairs each share a parent and do not
-// straddle 0 shares every load between the two nodes and runs sign-free (horner_y2_fibre);
-// any other warp takes k_stage's per-node path.
+// k_stage does with one node per lane.
 __global__ void __launch_bounds__(kThreads, 6)
     k_stage_c(const StageDev st, const int32_t *__restrict__ lab, const int32_t *__restrict__ par,
               const float4 *__restrict__ in, int64_t in_estride, int64_t in_nstride,
@@ -600,48 +679,12 @@ __global__ void __launch_bounds__(kThreads, 6)
   extern __shared__ int32_t s_rowoff[];
   for (int i = threadIdx.x; i <= st.maxlen; i += blockDim.x) s_rowoff[i] = st.rowoff[i];
   __syncthreads();
-  const int lane = threadIdx.x & 31;
-  const int64_t npairs = (nnodes + 1) >> 1;
   const int64_t nwarps = nchunk * G;
+  // the loop bound is the same for the 32 lanes of a warp, so the vote inside sees all of them
   for (int64_t w = (int64_t)blockIdx.x * kWarpsPerBlock + (threadIdx.x >> 5); w < nwarps;
-       w += (int64_t)gridDim.x * kWarpsPerBlock) {
-    const int64_t chunk = w % nchunk;
-    const int grp = (int)(w / nchunk);
-    const int64_t q = chunk * 32 + lane;
-    const bool live = q < npairs;
-    const int64_t i0 = 2 * (live ? q : npairs - 1);
-    const bool two = live && i0 + 1 < nnodes;
-    const int64_t i1 = i0 + 1 < nnodes ? i0 + 1 : i0;
-    const A32C::X x0 = A32C::box(g, __ldg(lab + i0)), x1 = A32C::box(g, __ldg(lab + i1));
-    const int64_t p0 = par ? (int64_t)__ldg(par + i0) : 0;
-    const int64_t p1 = par ? (int64_t)__ldg(par + i1) : 0;
-    const bool fast = p0 == p1 && x0.cls != 0 && x1.cls != 0;
-    if (__all_sync(0xffffffffu, fast)) {
-      const YLeaf y0 = yleaf(x0), y1 = yleaf(x1);
-      const float4 *base = in + p0 * in_nstride;
-      for (int f = grp; f < st.nfib; f += G) {
-        const int L = __ldg(st.fiblen + f);
-        float4 K0, K1;
-        horner_y2_fibre(base, in_estride, s_rowoff, f, L, y0, y1, K0, K1);
-        const int64_t o = (int64_t)__ldg(st.outpos + f) * out_estride;
-        if (live) out[i0 * out_nstride + o] = A32C::store(K0);
-        if (two) out[i1 * out_nstride + o] = A32C::store(K1);
-      }
-    } else {
-#pragma unroll 1
-      for (int c = 0; c < 2; ++c) {
-        const A32C::X &x = c == 0 ? x0 : x1;
-        const float4 *base = in + (c == 0 ? p0 : p1) * in_nstride;
-        const bool wr = c == 0 ? live : two;
-        const int64_t node = c == 0 ? i0 : i1;
-        for (int f = grp; f < st.nfib; f += G) {
-          const int L = __ldg(st.fiblen + f);
-          const float4 J = horner_any<A32C>(base, in_estride, s_rowoff, f, L, x);
-          if (wr) out[node * out_nstride + (int64_t)__ldg(st.outpos + f) * out_estride] = A32C::store(J);
-        }
-      }
-    }
-  }
+       w += (int64_t)gridDim.x * kWarpsPerBlock)
+    stage_chunk_c(st, s_rowoff, lab, par, 0, in, in_estride, in_nstride, out, out_estride,
+                  out_nstride, nnodes, w % nchunk, (int)(w / nchunk), G, g);
 }
 
 // k_stage_tma in the certified binary32 arithmetic, two children per thread: the children of
@@ -704,89 +747,99 @@ __global__ void __launch_bounds__(512)
   }
 }
 
+// One warp's share of k_leaf_c: the 32 leaf pairs of tile t (64 leaves).  par/poff as in
+// leaf_item.
+__device__ __forceinline__ void leaf_tile_c(const LeafArgs &A, int npoly,
+                                            const int32_t *__restrict__ lab,
+                                            const int32_t *__restrict__ par, int64_t poff,
+                                            int64_t nleaves, int64_t t, const AxisGrid &g,
+                                            uint8_t *__restrict__ keep, double *__restrict__ lo,
+                                            double *__restrict__ hi, uint8_t *__restrict__ flag) {
+  using V = float4;
+  const int lane = threadIdx.x & 31;
+  const int64_t npairs = (nleaves + 1) >> 1;
+  const int64_t q = t * 32 + lane;
+  const bool live = q < npairs;  // a lane past the end repeats the last pair, stores nothing
+  const int64_t i0 = 2 * (live ? q : npairs - 1);
+  const bool two = i0 + 1 < nleaves;
+  const int64_t i1 = two ? i0 + 1 : i0;
+  const A32C::X x0 = A32C::box(g, __ldg(lab + i0)), x1 = A32C::box(g, __ldg(lab + i1));
+  const int64_t p0 = par ? (int64_t)__ldg(par + i0) - poff : 0;
+  const int64_t p1 = par ? (int64_t)__ldg(par + i1) - poff : 0;
+  bool excl0 = false, amb0 = false, excl1 = false, amb1 = false;
+  auto decide = [&](int f, int c, const V &J) {
+    if (lo && live && (c == 0 || two)) {
+      const int64_t i = c == 0 ? i0 : i1;
+      lo[(int64_t)f * nleaves + i] = A32C::lo(J);
+      hi[(int64_t)f * nleaves + i] = A32C::hi(J);
+    }
+    const int r = A32C::classify(J);
+    if (c == 0) {
+      excl0 = excl0 || r == 0;
+      amb0 = amb0 || r == 2;
+    } else {
+      excl1 = excl1 || r == 0;
+      amb1 = amb1 || r == 2;
+    }
+  };
+  const bool fast = p0 == p1 && x0.cls != 0 && x1.cls != 0;
+  if (__all_sync(0xffffffffu, fast)) {
+    const YLeaf y0 = yleaf(x0), y1 = yleaf(x1);
+    int f = 0;
+    for (; f + 1 < npoly && A.len[f] == A.len[f + 1]; f += 2) {
+      const V *const b[2] = {(const V *)A.in[f] + p0 * A.blk[f],
+                             (const V *)A.in[f + 1] + p0 * A.blk[f + 1]};
+      V K0[2], K1[2];
+      horner_y2<2>(b, A.len[f], y0, y1, K0, K1);
+      decide(f, 0, K0[0]);
+      decide(f + 1, 0, K0[1]);
+      decide(f, 1, K1[0]);
+      decide(f + 1, 1, K1[1]);
+    }
+    for (; f < npoly; ++f) {
+      const V *const b[2] = {(const V *)A.in[f] + p0 * A.blk[f], nullptr};
+      V K0[2], K1[2];
+      horner_y2<1>(b, A.len[f], y0, y1, K0, K1);
+      decide(f, 0, K0[0]);
+      decide(f, 1, K1[0]);
+    }
+  } else {
+#pragma unroll 1
+    for (int c = 0; c < 2; ++c) {
+      const A32C::X &x = c == 0 ? x0 : x1;
+      const int64_t p = c == 0 ? p0 : p1;
+      int f = 0;
+      for (; f + 1 < npoly && A.len[f] == A.len[f + 1]; f += 2) {
+        V J0, J1;
+        horner1x2_any<A32C>((const V *)A.in[f] + p * A.blk[f],
+                            (const V *)A.in[f + 1] + p * A.blk[f + 1], A.len[f], x, J0, J1);
+        decide(f, c, J0);
+        decide(f + 1, c, J1);
+      }
+      for (; f < npoly; ++f)
+        decide(f, c, horner1_any<A32C>((const V *)A.in[f] + p * A.blk[f], 1, A.len[f], x));
+    }
+  }
+  if (live) {
+    keep[i0] = excl0 ? 0 : 1;
+    if (flag) flag[i0] = (!excl0 && amb0) ? 1 : 0;
+    if (two) {
+      keep[i1] = excl1 ? 0 : 1;
+      if (flag) flag[i1] = (!excl1 && amb1) ? 1 : 0;
+    }
+  }
+}
+
 __global__ void __launch_bounds__(kThreads, 6)
     k_leaf_c(LeafArgs A, int npoly, const int32_t *__restrict__ lab,
              const int32_t *__restrict__ par, int64_t nleaves, AxisGrid g,
              uint8_t *__restrict__ keep, double *__restrict__ lo, double *__restrict__ hi,
              uint8_t *__restrict__ flag) {
-  using V = float4;
-  const int64_t npairs = (nleaves + 1) >> 1;
-  const int64_t ntiles = (npairs + 31) >> 5;
-  const int lane = threadIdx.x & 31;
-  // the loop bound is the same for the 32 lanes of a warp, so the vote below sees all of them
+  const int64_t ntiles = (((nleaves + 1) >> 1) + 31) >> 5;
+  // the loop bound is the same for the 32 lanes of a warp, so the vote inside sees all of them
   for (int64_t t = (int64_t)blockIdx.x * kWarpsPerBlock + (threadIdx.x >> 5); t < ntiles;
-       t += (int64_t)gridDim.x * kWarpsPerBlock) {
-    const int64_t q = t * 32 + lane;
-    const bool live = q < npairs;  // a lane past the end repeats the last pair, stores nothing
-    const int64_t i0 = 2 * (live ? q : npairs - 1);
-    const bool two = i0 + 1 < nleaves;
-    const int64_t i1 = two ? i0 + 1 : i0;
-    const A32C::X x0 = A32C::box(g, __ldg(lab + i0)), x1 = A32C::box(g, __ldg(lab + i1));
-    const int64_t p0 = par ? (int64_t)__ldg(par + i0) : 0;
-    const int64_t p1 = par ? (int64_t)__ldg(par + i1) : 0;
-    bool excl0 = false, amb0 = false, excl1 = false, amb1 = false;
-    auto decide = [&](int f, int c, const V &J) {
-      if (lo && live && (c == 0 || two)) {
-        const int64_t i = c == 0 ? i0 : i1;
-        lo[(int64_t)f * nleaves + i] = A32C::lo(J);
-        hi[(int64_t)f * nleaves + i] = A32C::hi(J);
-      }
-      const int r = A32C::classify(J);
-      if (c == 0) {
-        excl0 = excl0 || r == 0;
-        amb0 = amb0 || r == 2;
-      } else {
-        excl1 = excl1 || r == 0;
-        amb1 = amb1 || r == 2;
-      }
-    };
-    const bool fast = p0 == p1 && x0.cls != 0 && x1.cls != 0;
-    if (__all_sync(0xffffffffu, fast)) {
-      const YLeaf y0 = yleaf(x0), y1 = yleaf(x1);
-      int f = 0;
-      for (; f + 1 < npoly && A.len[f] == A.len[f + 1]; f += 2) {
-        const V *const b[2] = {(const V *)A.in[f] + p0 * A.blk[f],
-                               (const V *)A.in[f + 1] + p0 * A.blk[f + 1]};
-        V K0[2], K1[2];
-        horner_y2<2>(b, A.len[f], y0, y1, K0, K1);
-        decide(f, 0, K0[0]);
-        decide(f + 1, 0, K0[1]);
-        decide(f, 1, K1[0]);
-        decide(f + 1, 1, K1[1]);
-      }
-      for (; f < npoly; ++f) {
-        const V *const b[2] = {(const V *)A.in[f] + p0 * A.blk[f], nullptr};
-        V K0[2], K1[2];
-        horner_y2<1>(b, A.len[f], y0, y1, K0, K1);
-        decide(f, 0, K0[0]);
-        decide(f, 1, K1[0]);
-      }
-    } else {
-#pragma unroll 1
-      for (int c = 0; c < 2; ++c) {
-        const A32C::X &x = c == 0 ? x0 : x1;
-        const int64_t p = c == 0 ? p0 : p1;
-        int f = 0;
-        for (; f + 1 < npoly && A.len[f] == A.len[f + 1]; f += 2) {
-          V J0, J1;
-          horner1x2_any<A32C>((const V *)A.in[f] + p * A.blk[f],
-                              (const V *)A.in[f + 1] + p * A.blk[f + 1], A.len[f], x, J0, J1);
-          decide(f, c, J0);
-          decide(f + 1, c, J1);
-        }
-        for (; f < npoly; ++f)
-          decide(f, c, horner1_any<A32C>((const V *)A.in[f] + p * A.blk[f], 1, A.len[f], x));
-      }
-    }
-    if (live) {
-      keep[i0] = excl0 ? 0 : 1;
-      if (flag) flag[i0] = (!excl0 && amb0) ? 1 : 0;
-      if (two) {
-        keep[i1] = excl1 ? 0 : 1;
-        if (flag) flag[i1] = (!excl1 && amb1) ? 1 : 0;
-      }
-    }
-  }
+       t += (int64_t)gridDim.x * kWarpsPerBlock)
+    leaf_tile_c(A, npoly, lab, par, 0, nleaves, t, g, keep, lo, hi, flag);
 }
 
 int leaf_pair_grid(int64_t leaves) {
@@ -996,6 +1049,224 @@ int eval_level_t(const SysDev &sys, const CsfView &c, const LevelGrid &grid, dou
 }
 
 }  // namespace
+
+// ---------------------------------------------------------------------------------------
+// Forests: the trees of many independent systems at one level, stored one after another at
+// every depth (tree s owns depth-d nodes off[d][s] .. off[d][s+1]-1; parents index the whole
+// forest).  One launch per depth evaluates every tree's nodes with its own system, grid and
+// blocks: thread = node, every polynomial and fibre in turn.
+// ---------------------------------------------------------------------------------------
+namespace {
+
+__device__ __forceinline__ int tree_of(const int64_t *__restrict__ off, int S, int64_t i) {
+  int lo = 0, hi = S;  // largest s with off[s] <= i
+  while (hi - lo > 1) {
+    const int mid = (lo + hi) >> 1;
+    if (__ldg(off + mid) <= i) lo = mid; else hi = mid;
+  }
+  return lo;
+}
+
+// Depth d < k-1 of a forest: a queue of warp tasks, tree t owning tasks tasks[t] ..
+// tasks[t+1]-1 (nchunk_t node chunks x G fibre groups); each task runs k_stage's (or
+// k_stage_c's) warp body on its tree's nodes with the tree's polynomials, grid and
+// node-major blocks.
+template <class AR, bool PAIRS>
+__global__ void __launch_bounds__(kThreads)
+    k_fstage(const ForestTree *__restrict__ trees, const int64_t *__restrict__ off, int S, int d,
+             CsfView c, void *const *__restrict__ blk, const int64_t *__restrict__ tasks, int G) {
+  using V = typename AR::V;
+  const int64_t *offd = off + (int64_t)d * (S + 1);
+  const int64_t *offp = off + (int64_t)(d > 0 ? d - 1 : 0) * (S + 1);
+  const int64_t ntask = __ldg(tasks + S);
+  // the task index is the same for the 32 lanes of a warp
+  for (int64_t w = (int64_t)blockIdx.x * kWarpsPerBlock + (threadIdx.x >> 5); w < ntask;
+       w += (int64_t)gridDim.x * kWarpsPerBlock) {
+    const int t = tree_of(tasks, S, w);
+    const ForestTree &T = trees[t];
+    const int64_t o = __ldg(offd + t), n = __ldg(offd + t + 1) - o;
+    const int64_t per = PAIRS ? 64 : 32, nchunk = (n + per - 1) / per;
+    const int64_t wl = w - __ldg(tasks + t);
+    const int64_t chunk = wl % nchunk;
+    const int grp = (int)(wl / nchunk);
+    const int32_t *lab = c.lab[d] + o;
+    const int32_t *par = d > 0 ? c.par[d] + o : nullptr;
+    const int64_t poff = d > 0 ? __ldg(offp + t) : 0;
+    for (int f = 0; f < T.dev.npoly; ++f) {
+      const StageDev st = T.dev.p[f].st[d];
+      const V *in = d == 0 ? AR::coef(T.dev.p[f])
+                           : (const V *)blk[((int64_t)t * VX_MAXPOLY + f) * VX_KMAX + d - 1];
+      V *out = (V *)blk[((int64_t)t * VX_MAXPOLY + f) * VX_KMAX + d];
+      const int64_t in_nstride = d == 0 ? 0 : st.blk_in;
+      if constexpr (PAIRS)
+        stage_chunk_c(st, st.rowoff, lab, par, poff, (const float4 *)in, 1, in_nstride,
+                      (float4 *)out, 1, st.blk_out, n, chunk, grp, G, T.ax[d]);
+      else
+        stage_chunk<AR>(st, st.rowoff, lab, par, poff, in, 1, in_nstride, out, 1, st.blk_out, n,
+                        chunk, grp, G, T.ax[d]);
+    }
+  }
+}
+
+// The leaves of a forest: tree t owns warp tasks tasks[t] .. tasks[t+1]-1, each 32 leaves
+// (64 in pairs for the certified binary32 arithmetic, k_leaf_c's body), with the tree's
+// polynomials, grid and parent blocks.
+template <class AR, bool PAIRS>
+__global__ void __launch_bounds__(kThreads)
+    k_fleaf(const ForestTree *__restrict__ trees, const int64_t *__restrict__ off, int S,
+            CsfView c, void *const *__restrict__ blk, const int64_t *__restrict__ tasks,
+            uint8_t *__restrict__ keep, uint8_t *__restrict__ flag, float theta) {
+  const int k = c.k;
+  const int64_t *offl = off + (int64_t)(k - 1) * (S + 1);
+  const int64_t *offp = off + (int64_t)(k > 1 ? k - 2 : 0) * (S + 1);
+  const int64_t ntask = __ldg(tasks + S);
+  for (int64_t w = (int64_t)blockIdx.x * kWarpsPerBlock + (threadIdx.x >> 5); w < ntask;
+       w += (int64_t)gridDim.x * kWarpsPerBlock) {
+    const int t = tree_of(tasks, S, w);
+    const ForestTree &T = trees[t];
+    const int64_t o = __ldg(offl + t), n = __ldg(offl + t + 1) - o;
+    LeafArgs A;
+    const int npoly = T.dev.npoly;
+    for (int f = 0; f < npoly; ++f) {
+      const StageDev &st = T.dev.p[f].st[k - 1];
+      A.in[f] = k == 1 ? (const void *)AR::coef(T.dev.p[f])
+                       : blk[((int64_t)t * VX_MAXPOLY + f) * VX_KMAX + k - 2];
+      A.blk[f] = k == 1 ? 0 : st.blk_in;
+      A.len[f] = st.maxlen;
+    }
+    const int32_t *lab = c.lab[k - 1] + o;
+    const int32_t *par = k > 1 ? c.par[k - 1] + o : nullptr;
+    const int64_t poff = k > 1 ? __ldg(offp + t) : 0;
+    const int64_t wl = w - __ldg(tasks + t);
+    if constexpr (PAIRS) {
+      leaf_tile_c(A, npoly, lab, par, poff, n, wl, T.ax[k - 1], keep + o, nullptr, nullptr,
+                  flag ? flag + o : nullptr);
+    } else {
+      const int64_t i = wl * 32 + (threadIdx.x & 31);
+      if (i < n)
+        leaf_item<AR>(A, npoly, lab, par, poff, i, n, T.ax[k - 1], keep + o, nullptr, nullptr,
+                      flag ? flag + o : nullptr, theta);
+    }
+  }
+}
+
+template <class AR>
+int eval_forest_t(const ForestTree *d_trees, const ForestTree *h_trees, const int64_t *d_off,
+                  const int64_t *h_off, int S, const CsfView &c, uint8_t *keep, uint8_t *flag,
+                  float theta, cudaStream_t s, int64_t *madds) {
+  using V = typename AR::V;
+  const int k = c.k;
+  *madds = 0;
+  if (c.N[k - 1] == 0) return VX_OK;
+  // blocks of every (tree, polynomial, depth < k-1), node-major, one allocation
+  std::vector<void *> tab((size_t)S * VX_MAXPOLY * VX_KMAX, nullptr);
+  std::vector<size_t> at(tab.size(), 0);
+  size_t total = 0;
+  for (int t = 0; t < S; ++t)
+    for (int f = 0; f < h_trees[t].dev.npoly; ++f)
+      for (int d = 0; d < k; ++d) {
+        const int64_t nd = h_off[(int64_t)d * (S + 1) + t + 1] - h_off[(int64_t)d * (S + 1) + t];
+        const StageDev &st = h_trees[t].dev.p[f].st[d];
+        *madds += nd * (st.blk_in - st.nfib);
+        if (d + 1 < k) {
+          at[((size_t)t * VX_MAXPOLY + f) * VX_KMAX + d] = total;
+          total += ((size_t)nd * st.blk_out * sizeof(V) + 255) & ~(size_t)255;
+        }
+      }
+  void *mem = nullptr, *dtab = nullptr;
+  int rc = VX_OK;
+  if (total > 0) rc = dmalloc(&mem, total, s);
+  if (rc == VX_OK) rc = dmalloc(&dtab, tab.size() * sizeof(void *), s);
+  if (rc == VX_OK) {
+    for (size_t j = 0; j < tab.size(); ++j) tab[j] = mem ? (char *)mem + at[j] : nullptr;
+    // from pageable memory: returns once the table is staged, so `tab` may go
+    if (cudaMemcpyAsync(dtab, tab.data(), tab.size() * sizeof(void *), cudaMemcpyHostToDevice,
+                        s) != cudaSuccess) {
+      set_error("forest block table upload failed");
+      rc = VX_ECUDA;
+    }
+  }
+  // warp-task queues: per depth, per tree, chunks of 32 nodes (64 in pairs) x G fibre groups
+  std::vector<int64_t> tasks((size_t)k * (S + 1), 0);
+  bool pairs[VX_KMAX] = {false};
+  int G[VX_KMAX] = {1, 1, 1, 1};
+  for (int d = 0; d < k; ++d) {
+    const bool leaf = d + 1 == k;
+    pairs[d] = std::is_same<AR, A32C>::value && (leaf || c.N[d] >= kPairNodes);
+    const int64_t per = pairs[d] ? 64 : 32;
+    int64_t chunks = 0, maxfib = 1;
+    for (int t = 0; t < S; ++t) {
+      const int64_t nd = h_off[(int64_t)d * (S + 1) + t + 1] - h_off[(int64_t)d * (S + 1) + t];
+      chunks += (nd + per - 1) / per;
+      for (int f = 0; f < h_trees[t].dev.npoly; ++f)
+        maxfib = std::max<int64_t>(maxfib, h_trees[t].dev.p[f].st[d].nfib);
+    }
+    if (!leaf && chunks > 0) G[d] = (int)std::min<int64_t>(maxfib, std::max<int64_t>(1, (152 * 64 + chunks - 1) / chunks));
+    int64_t acc = 0;
+    for (int t = 0; t < S; ++t) {
+      tasks[(size_t)d * (S + 1) + t] = acc;
+      const int64_t nd = h_off[(int64_t)d * (S + 1) + t + 1] - h_off[(int64_t)d * (S + 1) + t];
+      acc += (nd + per - 1) / per * G[d];
+    }
+    tasks[(size_t)d * (S + 1) + S] = acc;
+  }
+  void *dtasks = nullptr;
+  if (rc == VX_OK) rc = dmalloc(&dtasks, tasks.size() * sizeof(int64_t), s);
+  if (rc == VX_OK && cudaMemcpyAsync(dtasks, tasks.data(), tasks.size() * sizeof(int64_t),
+                                     cudaMemcpyHostToDevice, s) != cudaSuccess) {
+    set_error("forest task table upload failed");
+    rc = VX_ECUDA;
+  }
+  auto blocks_of = [](int64_t ntask) {
+    int64_t b = (ntask + kWarpsPerBlock - 1) / kWarpsPerBlock;
+    return (unsigned)std::max<int64_t>(1, std::min<int64_t>(b, 152 * 32));
+  };
+  for (int d = 0; d + 1 < k && rc == VX_OK; ++d) {
+    const int64_t *td = (const int64_t *)dtasks + (size_t)d * (S + 1);
+    const unsigned nb = blocks_of(tasks[(size_t)d * (S + 1) + S]);
+    if (pairs[d])
+      k_fstage<AR, true><<<nb, kThreads, 0, s>>>(d_trees, d_off, S, d, c, (void *const *)dtab, td, G[d]);
+    else
+      k_fstage<AR, false><<<nb, kThreads, 0, s>>>(d_trees, d_off, S, d, c, (void *const *)dtab, td, G[d]);
+    note_launch();
+    if (cudaGetLastError() != cudaSuccess) {
+      set_error("forest stage launch failed");
+      rc = VX_ECUDA;
+    }
+  }
+  if (rc == VX_OK) {
+    const int64_t *tl = (const int64_t *)dtasks + (size_t)(k - 1) * (S + 1);
+    const unsigned nb = blocks_of(tasks[(size_t)(k - 1) * (S + 1) + S]);
+    if (pairs[k - 1])
+      k_fleaf<AR, true><<<nb, kThreads, 0, s>>>(d_trees, d_off, S, c, (void *const *)dtab, tl, keep, flag, theta);
+    else
+      k_fleaf<AR, false><<<nb, kThreads, 0, s>>>(d_trees, d_off, S, c, (void *const *)dtab, tl, keep, flag, theta);
+    note_launch();
+    if (cudaGetLastError() != cudaSuccess) {
+      set_error("forest leaf launch failed");
+      rc = VX_ECUDA;
+    }
+  }
+  dfree(dtasks, s);
+  dfree(dtab, s);
+  dfree(mem, s);
+  return rc;
+}
+
+}  // namespace
+
+int eval_forest(int arith, const ForestTree *d_trees, const ForestTree *h_trees,
+                const int64_t *d_off, const int64_t *h_off, int S, const CsfView &c,
+                uint8_t *keep, uint8_t *flag, float theta, cudaStream_t s, int64_t *madds) {
+  switch (arith) {
+    case ARITH_F64:
+      return eval_forest_t<A64>(d_trees, h_trees, d_off, h_off, S, c, keep, flag, theta, s, madds);
+    case ARITH_F32_MIDRAD:
+      return eval_forest_t<A32>(d_trees, h_trees, d_off, h_off, S, c, keep, flag, theta, s, madds);
+    default:
+      return eval_forest_t<A32C>(d_trees, h_trees, d_off, h_off, S, c, keep, flag, theta, s, madds);
+  }
+}
 
 int set_wait_polls(int64_t polls) {
   const uint32_t v = polls < 0 ? kWaitPolls : (polls > 0xffffffffll ? 0xffffffffu : (uint32_t)polls);

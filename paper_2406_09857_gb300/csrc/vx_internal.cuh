@@ -152,6 +152,16 @@ int eval_level_raw(const SysDev &sys, const CsfView &csf, const LevelGrid &grid,
 // library's fixed device array; VX_ECAPACITY if they do not fit in VX_STATIC_SCRATCH_BYTES.
 int eval_level_static(const SysDev &sys, const CsfView &csf, const LevelGrid &grid, int arith,
                       double *d_lo, double *d_hi, uint8_t *d_keep, cudaStream_t s);
+// One level of a forest (the trees of many systems with the same k, one after another at
+// every depth; tree s owns depth-d nodes off[d*(S+1)+s] .. off[d*(S+1)+s+1]-1).  d_trees and
+// h_trees: the same table on the device and the host; h_off the host copy of d_off.
+struct ForestTree {
+  SysDev dev;
+  AxisGrid ax[VX_KMAX];  // the level's grid of this tree's system
+};
+int eval_forest(int arith, const ForestTree *d_trees, const ForestTree *h_trees,
+                const int64_t *d_off, const int64_t *h_off, int S, const CsfView &c,
+                uint8_t *keep, uint8_t *flag, float theta, cudaStream_t s, int64_t *madds);
 // Reads (synchronising `s`) and clears the device status word that a kernel sets when a
 // bounded wait gives up; *status != 0 means the last evaluations are not to be trusted.
 int take_device_status(cudaStream_t s, int *status);
@@ -173,6 +183,12 @@ int csf_build_dev(int k, int level, const int32_t *d_tuples, int64_t n, cudaStre
 // writing the kept leaves' old indices to d_index when non-null.
 int csf_prune(const CsfView &in, const uint8_t *d_keep, int split, int32_t *d_index,
               cudaStream_t s, CsfObj *out, Timer *tm);
+// The same on a forest of nseg trees stored one after another at every depth (tree s owns
+// depth-d nodes d_seg_off[d*(nseg+1) + s] .. [.. + s + 1] - 1): d_seg_kept[d*(nseg+1) + s]
+// receives the kept depth-d nodes of trees before s (s = nseg: all of them).
+int csf_prune_forest(const CsfView &in, const uint8_t *d_keep, int split, int32_t *d_index,
+                     const int64_t *d_seg_off, int nseg, int64_t *d_seg_kept, cudaStream_t s,
+                     CsfObj *out, Timer *tm);
 // The complete tree of grid level `level` (every box), filled directly.
 int csf_full_grid_dev(int k, int level, cudaStream_t s, CsfObj *out);
 // ptr[d][N[d]] = N[d+1] for every depth d < k-1.

@@ -455,3 +455,42 @@ def test_dense_level9_all_modes_odd_block(vx):
     t = np.stack([idx >> 18, (idx >> 9) & 511, idx & 511], axis=1).astype(np.int32)
     _, _, keep_r, _ = oracle.eval_boxes(polys, synth.cube(3), 9, t)
     assert np.array_equal(k64[idx], keep_r)
+
+
+def test_enclose_batch_forest_mixed_modes(vx):
+    """A larger mixed batch: k = 1, 2 and 3 in one call, depth 0, a system with no zeros in its
+    domain (its tree empties at level 0), uneven degrees and depths; binary64 and certified
+    binary32 equal the oracle in boxes and per-level counts, midpoint-radius with a binary64
+    final level equals it too, and without it is a superset at every level."""
+    systems = []
+    for i in range(30):
+        st = synth.Stream(1700 + i)
+        k = 1 + i % 3
+        d = int(st.uniform_int(2, 9 if k < 3 else 5, 1)[0])
+        npoly = 1 if k == 1 else int(st.uniform_int(1, 2, 1)[0])
+        polys = [synth.kostlan_poly(k, d, 1800 + 10 * i + p) for p in range(npoly)]
+        depth = int(st.uniform_int(0, 9 - 2 * k, 1)[0]) if i != 4 else 0
+        systems.append((polys, synth.cube(k), depth))
+    # no zeros: 1 + x^2 + y^2 on [-1,1]^2
+    e = np.array([[0, 0], [2, 0], [0, 2]], dtype=np.int32)
+    systems.append(([(e, np.array([1.0, 1.0, 1.0]))], synth.cube(2), 6))
+    refs = [oracle.enclose(p, dom, depth) for p, dom, depth in systems]
+    assert refs[-1]["tuples"].shape[0] == 0
+    for opts in (vx.make_opts(vx.FP64), vx.make_opts(vx.FP32),
+                 vx.make_opts(vx.FP32_MIDRAD, fp64_final=True)):
+        res = vx.enclose_batch(systems, opts)
+        for ref, r in zip(refs, res):
+            assert np.array_equal(r.boxes(), ref["tuples"])
+            st = r.stats()
+            assert int(st["kept"][-1]) == ref["tuples"].shape[0]
+            if opts.mode == vx.FP32_MIDRAD:  # supersets before the last level
+                assert np.all(st["tested"] >= ref["tested"])
+            else:
+                assert np.array_equal(st["tested"], ref["tested"])
+                assert np.array_equal(st["kept"], ref["kept"])
+    res = vx.enclose_batch(systems, vx.make_opts(vx.FP32_MIDRAD))
+    for ref, r in zip(refs, res):
+        b = r.boxes()
+        assert b.shape[0] >= ref["tuples"].shape[0]
+        got = set(map(tuple, b.tolist()))
+        assert all(tuple(t) in got for t in ref["tuples"].tolist())

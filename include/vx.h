@@ -232,6 +232,18 @@ int vx_enclose_batch(const vx_poly *const *systems, const int32_t *npoly, const 
                      const int32_t *depths, int32_t nsys, const vx_opts *opts, int32_t nworkers,
                      vx_result **out);
 
+/* Autotuner of the evaluation kernels (not in the paper).  Each stage and leaf launch has a
+ * few variants with identical outputs (one or two boxes per thread, numbers of fibre groups,
+ * CTA sizes); with mode 1 (the default) the first launch of a shape (arithmetic, depth, node
+ * counts and fibre length, bucketed) times every variant on its real data and keeps the
+ * fastest for the later ones (that first launch synchronises its stream); mode 0 uses the
+ * built-in heuristics.  cache_path (nullable): a text file of tuned shapes, read by this call
+ * and appended to as shapes are tuned.  vx_autotune_entries: shapes tuned so far;
+ * vx_autotune_clear forgets them. */
+int vx_autotune(int32_t mode, const char *cache_path);
+int vx_autotune_entries(void);
+void vx_autotune_clear(void);
+
 /* ---- Dense full-grid levels on the tensor cores (k = 3) ------------------------------------
  * Property 1 (Sec. 1) writes a polynomial on a tensor grid as one contraction of its
  * coefficient tensor per variable.  A plan evaluates every box of a level (2^level boxes per

@@ -601,6 +601,19 @@ int vx_system_device_bytes(const vx_system *sys, int64_t *bytes) {
 
 int64_t vx_kernel_launches(void) { return g_launches.load(std::memory_order_relaxed); }
 
+int vx_autotune(int32_t mode, const char *cache_path) {
+  clear_error();
+  if (mode != 0 && mode != 1) {
+    set_error("vx_autotune: mode %d (0 or 1)", mode);
+    return VX_EINVAL;
+  }
+  return set_autotune(mode, cache_path);
+}
+
+int vx_autotune_entries(void) { return autotune_entries(); }
+
+void vx_autotune_clear(void) { autotune_clear(); }
+
 int vx_set_wait_limit(int64_t polls) {
   clear_error();
   VX_CHECK(set_dense_wait_polls(polls));

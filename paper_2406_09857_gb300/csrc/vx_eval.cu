@@ -48,7 +48,11 @@
 //        that are not exact at binary32 precision) add the term 2^-23 m_J xmax explicitly.
 #include <cuda_runtime.h>
 
+#include <cstdio>
+#include <mutex>
+#include <string>
 #include <type_traits>
+#include <unordered_map>
 
 #include "vx_internal.cuh"
 #include "vx_ptx.cuh"
@@ -877,6 +881,92 @@ size_t level_scratch_bytes(const SysDev &sys, const CsfView &c) {
   return total;
 }
 
+// ---------------------------------------------------------------------------------------
+// Autotuner: a stage or leaf launch has a few variants that compute the same outputs (one or
+// two nodes per thread, fibre-group counts, CTA sizes).  The first launch of a shape key
+// (arithmetic, depth, log2 of the node counts, fibre length, log2 of the fibre count) times
+// every variant on the real data, CUDA events on the launching stream, and keeps the fastest;
+// later launches of that key use it.  The last variant timed leaves the outputs in place.
+// ---------------------------------------------------------------------------------------
+struct Tuner {
+  std::mutex mu;
+  std::unordered_map<uint64_t, int> best;
+  int mode = 1;      // 0: heuristic variant 0 only, 1: tune
+  std::string path;  // cache file ("" = in memory only)
+};
+Tuner &tuner() {
+  static Tuner t;
+  return t;
+}
+
+int ilog2(int64_t x) {
+  int r = 0;
+  while (x > 1) {
+    x >>= 1;
+    ++r;
+  }
+  return r;
+}
+
+uint64_t tune_key(int kind, int arith, int d, int64_t n, int64_t nparent, int maxlen, int nfib) {
+  return ((uint64_t)(kind & 0xF) << 60) | ((uint64_t)(arith & 0xF) << 56) |
+         ((uint64_t)(d & 0xF) << 52) | ((uint64_t)(ilog2(n + 1) & 0x3F) << 46) |
+         ((uint64_t)(ilog2(nparent + 1) & 0x3F) << 40) | ((uint64_t)(maxlen & 0xFFFF) << 24) |
+         ((uint64_t)(ilog2(nfib + 1) & 0x3F) << 18);
+}
+
+// Runs launch(v) for the cached variant of `key`, or times variants 0..nvar-1 and caches the
+// fastest.  launch returns a status; the stream is synchronised only while tuning.
+template <class F>
+int tuned_launch(uint64_t key, int nvar, cudaStream_t s, F launch) {
+  Tuner &T = tuner();
+  int v = -1;
+  {
+    std::lock_guard<std::mutex> g(T.mu);
+    if (T.mode == 0 || nvar <= 1) v = 0;
+    else {
+      auto it = T.best.find(key);
+      if (it != T.best.end()) v = it->second < nvar ? it->second : 0;
+    }
+  }
+  if (v >= 0) return launch(v);
+  cudaEvent_t a = nullptr, b = nullptr;
+  VX_CUDA(cudaEventCreate(&a));
+  VX_CUDA(cudaEventCreate(&b));
+  float bestms = 0.f;
+  int bestv = 0, rc = VX_OK;
+  for (int c = 0; c < nvar && rc == VX_OK; ++c) {
+    cudaEventRecord(a, s);
+    rc = launch(c);
+    cudaEventRecord(b, s);
+    float ms = 0.f;
+    if (rc == VX_OK && (cudaEventSynchronize(b) != cudaSuccess ||
+                        cudaEventElapsedTime(&ms, a, b) != cudaSuccess)) {
+      set_error("autotune timing failed");
+      rc = VX_ECUDA;
+    }
+    if (rc == VX_OK && (c == 0 || ms < bestms)) {
+      bestms = ms;
+      bestv = c;
+    }
+  }
+  cudaEventDestroy(a);
+  cudaEventDestroy(b);
+  if (rc != VX_OK) return rc;
+  // the outputs of the last variant are in place; run the best one if it was not the last so
+  // that every output comes from one variant
+  if (bestv != nvar - 1) rc = launch(bestv);
+  std::lock_guard<std::mutex> g(T.mu);
+  T.best[key] = bestv;
+  if (!T.path.empty()) {
+    if (FILE *fp = std::fopen(T.path.c_str(), "a")) {
+      std::fprintf(fp, "%llx %d\n", (unsigned long long)key, bestv);
+      std::fclose(fp);
+    }
+  }
+  return rc;
+}
+
 // ext_scratch != nullptr: the blocks are carved from it (ext_bytes long) and nothing is allocated.
 template <class AR>
 int eval_level_t(const SysDev &sys, const CsfView &c, const LevelGrid &grid, double *d_lo,
@@ -948,67 +1038,82 @@ int eval_level_t(const SysDev &sys, const CsfView &c, const LevelGrid &grid, dou
       if (tm && tm->on) rc = tm->begin(d == 0 ? kind0 : kind0 + 1, w);
       if (rc != VX_OK) break;
       const V *in = d == 0 ? AR::coef(sys.p[f]) : buf[f][d - 1];
+      const int arith = std::is_same<AR, A64>::value ? 0 : (std::is_same<AR, A32>::value ? 1 : 2);
       if (tma[d]) {
         // the same value from every caller: host threads launching concurrently never lower
         // the limit below another one's need
         if (cudaFuncSetAttribute(k_stage_tma<AR>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)kMaxDynSmem) != cudaSuccess ||
+            cudaFuncSetAttribute(k_stage_tma_c, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  (int)kMaxDynSmem) != cudaSuccess) {
           set_error("cudaFuncSetAttribute(shared memory %zu) failed", tma_smem[d]);
           rc = VX_ECUDA;
           break;
         }
-        // one CTA per (parent, fibre group), threads ~ the average number of children
+        // one CTA per (parent, fibre group), threads ~ the average number of children.
+        // Variants: 0 the heuristic (two children per thread in the certified binary32
+        // arithmetic), 1 one child per thread, 2 twice the fibre groups, 3 half the threads
         const int64_t np = c.N[d - 1];
         const int64_t avg = c.N[d] / np;
-        const int threads = avg >= 512 ? 512 : (avg >= 256 ? 256 : 128);
-        int64_t G = (4 * 152 * 2 + np - 1) / np;
-        if (G > st.nfib) G = st.nfib;
-        if (G < 1) G = 1;
-        if constexpr (std::is_same<AR, A32C>::value) {
-          if (cudaFuncSetAttribute(k_stage_tma_c, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                   (int)kMaxDynSmem) != cudaSuccess) {
-            set_error("cudaFuncSetAttribute(shared memory %zu) failed", tma_smem[d]);
-            rc = VX_ECUDA;
-            break;
-          }
-          k_stage_tma_c<<<(unsigned)(np * G), threads, tma_smem[d], s>>>(
-              st, c.lab[d], c.ptr[d - 1], in, buf[f][d], oe, on, (int)G, grid.ax[d]);
-        } else {
-          k_stage_tma<AR><<<(unsigned)(np * G), threads, tma_smem[d], s>>>(
-              st, c.lab[d], c.ptr[d - 1], in, buf[f][d], oe, on, (int)G, grid.ax[d]);
-        }
+        const int threads0 = avg >= 512 ? 512 : (avg >= 256 ? 256 : 128);
+        int64_t G0 = (4 * 152 * 2 + np - 1) / np;
+        if (G0 > st.nfib) G0 = st.nfib;
+        if (G0 < 1) G0 = 1;
+        auto launch = [&](int v) -> int {
+          int threads = threads0;
+          int64_t G = G0;
+          if (v == 2) G = std::min<int64_t>(st.nfib, 2 * G0);
+          if (v == 3) threads = std::max(128, threads0 / 2);
+          const bool two = std::is_same<AR, A32C>::value && v != 1;
+          if (two)
+            k_stage_tma_c<<<(unsigned)(np * G), threads, tma_smem[d], s>>>(
+                st, c.lab[d], c.ptr[d - 1], (const float4 *)in, (float4 *)buf[f][d], oe, on,
+                (int)G, grid.ax[d]);
+          else
+            k_stage_tma<AR><<<(unsigned)(np * G), threads, tma_smem[d], s>>>(
+                st, c.lab[d], c.ptr[d - 1], in, buf[f][d], oe, on, (int)G, grid.ax[d]);
+          note_launch();
+          VX_LAUNCH_CHECK();
+          return VX_OK;
+        };
+        rc = tuned_launch(tune_key(1, arith, d, c.N[d], np, st.maxlen, st.nfib), 4, s, launch);
       } else {
         // fibre groups: enough warps to fill the GPU several times over (a warp takes 32
         // nodes; 64 in the certified binary32 arithmetic when the depth has enough nodes for
-        // the shared loads to pay)
-        const bool pairs = std::is_same<AR, A32C>::value &&
-                           (c.N[d] >= kPairNodes || st.blk_in - st.nfib >= kPairNodes);
-        const int64_t per_warp = pairs ? 64 : 32;
-        const int64_t nchunk = (c.N[d] + per_warp - 1) / per_warp;
-        const int64_t target = 152 * 64;
-        int64_t G = (target + nchunk - 1) / nchunk;
-        if (G > st.nfib) G = st.nfib;
-        if (G < 1) G = 1;
-        int64_t blocks = (nchunk * G + kWarpsPerBlock - 1) / kWarpsPerBlock;
-        if (blocks > 152 * 64) blocks = 152 * 64;
+        // the shared loads to pay).  Variants: 0 the heuristic, 1 the other node count per
+        // warp (certified binary32), 2 four times the fibre groups
+        const bool pairs0 = std::is_same<AR, A32C>::value &&
+                            (c.N[d] >= kPairNodes || st.blk_in - st.nfib >= kPairNodes);
         const int64_t in_estride = d == 0 ? 1 : (tma_input_node_major(d, k, tma) ? 1 : c.N[d - 1]);
         const int64_t in_nstride = d == 0 ? 0 : (tma_input_node_major(d, k, tma) ? st.blk_in : 1);
-        if (pairs)
-          k_stage_c<<<(unsigned)blocks, kThreads, (st.maxlen + 1) * sizeof(int32_t), s>>>(
-              st, c.lab[d], d == 0 ? nullptr : c.par[d], (const float4 *)in, in_estride,
-              in_nstride, (float4 *)buf[f][d], oe, on, c.N[d], nchunk, (int)G, grid.ax[d]);
-        else
-          k_stage<AR><<<(unsigned)blocks, kThreads, (st.maxlen + 1) * sizeof(int32_t), s>>>(
-              st, c.lab[d], d == 0 ? nullptr : c.par[d], in, in_estride, in_nstride, buf[f][d],
-              oe, on, c.N[d], nchunk, (int)G, grid.ax[d]);
+        auto launch = [&](int vv) -> int {
+          const int v = std::is_same<AR, A32C>::value ? vv : (vv == 1 ? 2 : 0);
+          const bool pairs = v == 1 ? !pairs0 : pairs0;
+          const int64_t per_warp = pairs ? 64 : 32;
+          const int64_t nchunk = (c.N[d] + per_warp - 1) / per_warp;
+          const int64_t target = 152 * 64 * (v == 2 ? 4 : 1);
+          int64_t G = (target + nchunk - 1) / nchunk;
+          if (G > st.nfib) G = st.nfib;
+          if (G < 1) G = 1;
+          int64_t blocks = (nchunk * G + kWarpsPerBlock - 1) / kWarpsPerBlock;
+          if (blocks > 152 * 64) blocks = 152 * 64;
+          if (pairs)
+            k_stage_c<<<(unsigned)blocks, kThreads, (st.maxlen + 1) * sizeof(int32_t), s>>>(
+                st, c.lab[d], d == 0 ? nullptr : c.par[d], (const float4 *)in, in_estride,
+                in_nstride, (float4 *)buf[f][d], oe, on, c.N[d], nchunk, (int)G, grid.ax[d]);
+          else
+            k_stage<AR><<<(unsigned)blocks, kThreads, (st.maxlen + 1) * sizeof(int32_t), s>>>(
+                st, c.lab[d], d == 0 ? nullptr : c.par[d], in, in_estride, in_nstride,
+                buf[f][d], oe, on, c.N[d], nchunk, (int)G, grid.ax[d]);
+          note_launch();
+          VX_LAUNCH_CHECK();
+          return VX_OK;
+        };
+        rc = tuned_launch(tune_key(2, arith, d, c.N[d], d > 0 ? c.N[d - 1] : 0, st.maxlen,
+                                   st.nfib),
+                          std::is_same<AR, A32C>::value ? 3 : 2, s, launch);
       }
-      note_launch();
-      cudaError_t e = cudaGetLastError();
-      if (e != cudaSuccess) {
-        set_error("stage kernel launch failed: %s", cudaGetErrorString(e));
-        rc = VX_ECUDA;
-        break;
-      }
+      if (rc != VX_OK) break;
       if (tm && tm->on) rc = tm->end();
     }
   }
@@ -1025,21 +1130,25 @@ int eval_level_t(const SysDev &sys, const CsfView &c, const LevelGrid &grid, dou
     madds += wl;
     if (tm && tm->on) rc = tm->begin(kind0 + 2, wl);
     if (rc == VX_OK) {
-      if (std::is_same<AR, A32C>::value)
-        k_leaf_c<<<leaf_pair_grid(nleaves), kThreads, 0, s>>>(
-            A, sys.npoly, c.lab[k - 1], k == 1 ? nullptr : c.par[k - 1], nleaves, grid.ax[k - 1],
-            d_keep, d_lo, d_hi, d_flag);
-      else
-        k_leaf<AR><<<leaf_grid(nleaves), kThreads, 0, s>>>(A, sys.npoly, c.lab[k - 1],
-                                                          k == 1 ? nullptr : c.par[k - 1],
-                                                          nleaves, grid.ax[k - 1], d_keep, d_lo,
-                                                          d_hi, d_flag, theta);
-      note_launch();
-      cudaError_t e = cudaGetLastError();
-      if (e != cudaSuccess) {
-        set_error("leaf kernel launch failed: %s", cudaGetErrorString(e));
-        rc = VX_ECUDA;
-      }
+      // variants (certified binary32): 0 two leaves per thread, 1 one leaf per thread
+      auto launch = [&](int v) -> int {
+        if (std::is_same<AR, A32C>::value && v == 0)
+          k_leaf_c<<<leaf_pair_grid(nleaves), kThreads, 0, s>>>(
+              A, sys.npoly, c.lab[k - 1], k == 1 ? nullptr : c.par[k - 1], nleaves,
+              grid.ax[k - 1], d_keep, d_lo, d_hi, d_flag);
+        else
+          k_leaf<AR><<<leaf_grid(nleaves), kThreads, 0, s>>>(A, sys.npoly, c.lab[k - 1],
+                                                            k == 1 ? nullptr : c.par[k - 1],
+                                                            nleaves, grid.ax[k - 1], d_keep,
+                                                            d_lo, d_hi, d_flag, theta);
+        note_launch();
+        VX_LAUNCH_CHECK();
+        return VX_OK;
+      };
+      const int arith = std::is_same<AR, A64>::value ? 0 : (std::is_same<AR, A32>::value ? 1 : 2);
+      rc = tuned_launch(tune_key(3, arith, k - 1, nleaves, k > 1 ? c.N[k - 2] : 0,
+                                 sys.p[0].st[k - 1].maxlen, sys.npoly),
+                        std::is_same<AR, A32C>::value ? 2 : 1, s, launch);
       if (rc == VX_OK && tm && tm->on) rc = tm->end();
     }
   }
@@ -1266,6 +1375,34 @@ int eval_forest(int arith, const ForestTree *d_trees, const ForestTree *h_trees,
     default:
       return eval_forest_t<A32C>(d_trees, h_trees, d_off, h_off, S, c, keep, flag, theta, s, madds);
   }
+}
+
+int set_autotune(int mode, const char *path) {
+  Tuner &T = tuner();
+  std::lock_guard<std::mutex> g(T.mu);
+  T.mode = mode ? 1 : 0;
+  T.path = path ? path : "";
+  if (!T.path.empty()) {
+    if (FILE *fp = std::fopen(T.path.c_str(), "r")) {
+      unsigned long long key = 0;
+      int v = 0;
+      while (std::fscanf(fp, "%llx %d", &key, &v) == 2) T.best[(uint64_t)key] = v;
+      std::fclose(fp);
+    }
+  }
+  return VX_OK;
+}
+
+int autotune_entries() {
+  Tuner &T = tuner();
+  std::lock_guard<std::mutex> g(T.mu);
+  return (int)T.best.size();
+}
+
+void autotune_clear() {
+  Tuner &T = tuner();
+  std::lock_guard<std::mutex> g(T.mu);
+  T.best.clear();
 }
 
 int set_wait_polls(int64_t polls) {

@@ -167,6 +167,12 @@ int eval_forest(int arith, const ForestTree *d_trees, const ForestTree *h_trees,
 int take_device_status(cudaStream_t s, int *status);
 // Polls of a kernel's first bounded wait on the current device (< 0: the default).
 int set_wait_polls(int64_t polls);
+// Autotuner of the stage and leaf launch variants (vx_eval.cu): mode 0 = heuristic variants
+// only, 1 = time the variants of each new shape and keep the fastest; path (nullable) = a text
+// cache read now and appended to.
+int set_autotune(int mode, const char *path);
+int autotune_entries();
+void autotune_clear();
 
 // Integer kernels (vx_csf.cu).  Objects own one device allocation each.
 struct CsfObj {

@@ -58,6 +58,9 @@ def lib() -> ctypes.CDLL:
         "vx_system_device_bytes": ([P, P], i32),
         "vx_kernel_launches": ([], i64),
         "vx_set_wait_limit": ([i64], i32),
+        "vx_autotune": ([i32, ctypes.c_char_p], i32),
+        "vx_autotune_entries": ([], i32),
+        "vx_autotune_clear": ([], None),
         "vx_csf_build": ([i32, i32, P, i64, P, PP], i32),
         "vx_csf_free": ([P], None),
         "vx_csf_full_grid": ([i32, i32, P, PP], i32),
@@ -94,6 +97,16 @@ def lib() -> ctypes.CDLL:
         f.restype = res
     _lib = L
     return L
+
+
+def autotune(mode=1, cache_path=None):
+    """Autotuner of the evaluation kernels: mode 1 tunes each new launch shape, 0 uses the
+    heuristics; cache_path (optional) is read now and appended to."""
+    _check(lib().vx_autotune(int(mode), cache_path.encode() if cache_path else None))
+
+
+def autotune_entries() -> int:
+    return int(lib().vx_autotune_entries())
 
 
 def kernel_launches() -> int:

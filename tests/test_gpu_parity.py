@@ -494,3 +494,30 @@ def test_enclose_batch_forest_mixed_modes(vx):
         assert b.shape[0] >= ref["tuples"].shape[0]
         got = set(map(tuple, b.tolist()))
         assert all(tuple(t) in got for t in ref["tuples"].tolist())
+
+
+def test_autotuner_variants_agree_and_cache_round_trips(vx, tmp_path):
+    """Every launch variant the autotuner may pick gives the same outputs: enclosures with the
+    heuristics only and with tuning (from an empty table) are identical box for box in each
+    arithmetic; a cache file written while tuning reloads the same shapes."""
+    polys = [synth.kostlan_poly(3, 14, 991), synth.kostlan_poly(3, 14, 992)]
+    dom = synth.cube(3)
+    path = str(tmp_path / "tune.txt")
+    try:
+        for mode in (vx.FP64, vx.FP32, vx.FP32_MIDRAD):
+            vx.autotune(0)
+            ref = vx.enclose(polys, dom, 7, vx.make_opts(mode)).boxes()
+            vx.lib().vx_autotune_clear()
+            vx.autotune(1, path)
+            got = vx.enclose(polys, dom, 7, vx.make_opts(mode)).boxes()
+            assert np.array_equal(got, ref)
+            again = vx.enclose(polys, dom, 7, vx.make_opts(mode)).boxes()  # cached choices
+            assert np.array_equal(again, ref)
+        n = vx.autotune_entries()
+        assert n > 0
+        vx.lib().vx_autotune_clear()
+        assert vx.autotune_entries() == 0
+        vx.autotune(1, path)
+        assert vx.autotune_entries() == n
+    finally:
+        vx.autotune(1)

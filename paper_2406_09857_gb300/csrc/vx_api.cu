@@ -10,6 +10,8 @@
 
 #include <algorithm>
 #include <atomic>
+#include <map>
+#include <mutex>
 #include <thread>
 #include <cmath>
 #include <cstdarg>
@@ -471,9 +473,51 @@ struct vx_result {
   std::vector<int64_t> tested, kept, nodes, recheck, madds;
   Timer tm;
   double elapsed_ms = 0.0;
-  bool have_tuples = false;
-  std::vector<int32_t> tuples;
+  // the boxes on the host: a pinned buffer from the library's pool (vx_result_boxes)
+  int32_t *htup = nullptr;
+  size_t hcap = 0;       // bytes of the buffer
+  int64_t hcount = -1;   // boxes copied (-1: not yet)
 };
+
+// ---------------------------------------------------------------------------------------
+// Pinned host buffers for results' boxes, kept for reuse: device-to-host copies into pinned
+// memory run at the link's rate (pageable copies go through a staging buffer), and pinning
+// is paid once per buffer, not once per result.
+// ---------------------------------------------------------------------------------------
+static std::mutex g_pin_mu;
+static std::multimap<size_t, void *> g_pin_free;  // capacity -> buffer
+
+static int pinned_get(size_t bytes, void **p, size_t *cap) {
+  {
+    std::lock_guard<std::mutex> g(g_pin_mu);
+    auto it = g_pin_free.lower_bound(bytes);
+    if (it != g_pin_free.end() && it->first <= 2 * bytes + (64u << 20)) {
+      *p = it->second;
+      *cap = it->first;
+      g_pin_free.erase(it);
+      return VX_OK;
+    }
+  }
+  const size_t c = (bytes + (16u << 20) - 1) & ~(size_t)((16u << 20) - 1);  // 16 MiB steps
+  if (cudaHostAlloc(p, c, cudaHostAllocDefault) != cudaSuccess) {
+    set_error("cudaHostAlloc of %zu bytes failed", c);
+    return VX_ENOMEM;
+  }
+  *cap = c;
+  return VX_OK;
+}
+
+static void pinned_put(void *p, size_t cap) {
+  if (!p) return;
+  std::lock_guard<std::mutex> g(g_pin_mu);
+  g_pin_free.emplace(cap, p);
+  // keep the pool bounded: release the largest buffers beyond 8
+  while (g_pin_free.size() > 8) {
+    auto it = std::prev(g_pin_free.end());
+    cudaFreeHost(it->second);
+    g_pin_free.erase(it);
+  }
+}
 
 static cudaStream_t as_stream(void *s) { return (cudaStream_t)s; }
 
@@ -497,7 +541,27 @@ int vx_system_create(const vx_poly *F, int32_t npoly, void *stream, vx_system **
     return VX_EINVAL;
   }
   std::vector<HostPoly> hp(npoly);
-  for (int f = 0; f < npoly; ++f) VX_CHECK(pack_poly(k, F[f], &hp[f]));
+  int64_t terms = 0;
+  for (int f = 0; f < npoly; ++f) terms += std::max<int32_t>(F[f].nterms, 0);
+  if (npoly > 1 && terms >= 20000) {
+    // large polynomials pack concurrently (host work, one thread each)
+    std::vector<int> rcs(npoly, VX_OK);
+    std::vector<std::string> msgs(npoly);
+    std::vector<std::thread> th;
+    for (int f = 0; f < npoly; ++f)
+      th.emplace_back([&, f] {
+        rcs[f] = pack_poly(k, F[f], &hp[f]);
+        if (rcs[f] != VX_OK) msgs[f] = vx_last_error();
+      });
+    for (auto &t : th) t.join();
+    for (int f = 0; f < npoly; ++f)
+      if (rcs[f] != VX_OK) {
+        set_error("%s", msgs[f].c_str());
+        return rcs[f];
+      }
+  } else {
+    for (int f = 0; f < npoly; ++f) VX_CHECK(pack_poly(k, F[f], &hp[f]));
+  }
   // one device allocation: per polynomial the two coefficient blocks, then per stage the
   // row offsets, fibre lengths and output positions
   auto al = [](size_t x) { return (x + 255) & ~(size_t)255; };
@@ -1642,18 +1706,19 @@ int vx_result_boxes(vx_result *R, int64_t *n, const int32_t **h_tuples) {
     set_error("vx_result_boxes: NULL argument");
     return VX_EINVAL;
   }
-  if (!R->have_tuples) {
+  if (R->hcount < 0) {
     const int k = R->k;
     const int64_t m = R->fin.v.N[k - 1];
-    R->tuples.assign((size_t)m * k, 0);
     if (m > 0) {
       cudaStream_t s = R->fin.stream;
+      void *hb = nullptr;
+      size_t cap = 0;
+      VX_CHECK(pinned_get((size_t)m * k * 4, &hb, &cap));
       int32_t *d = nullptr;
-      VX_CHECK(dmalloc((void **)&d, (size_t)m * k * 4, s));
-      int rc = csf_tuples_dev(R->fin.v, d, s);
+      int rc = dmalloc((void **)&d, (size_t)m * k * 4, s);
+      if (rc == VX_OK) rc = csf_tuples_dev(R->fin.v, d, s);
       if (rc == VX_OK) {
-        cudaError_t e = cudaMemcpyAsync(R->tuples.data(), d, (size_t)m * k * 4,
-                                        cudaMemcpyDeviceToHost, s);
+        cudaError_t e = cudaMemcpyAsync(hb, d, (size_t)m * k * 4, cudaMemcpyDeviceToHost, s);
         if (e == cudaSuccess) e = cudaStreamSynchronize(s);
         if (e != cudaSuccess) {
           set_error("copying the boxes to the host failed: %s", cudaGetErrorString(e));
@@ -1661,12 +1726,17 @@ int vx_result_boxes(vx_result *R, int64_t *n, const int32_t **h_tuples) {
         }
       }
       dfree(d, s);
-      VX_CHECK(rc);
+      if (rc != VX_OK) {
+        pinned_put(hb, cap);
+        return rc;
+      }
+      R->htup = (int32_t *)hb;
+      R->hcap = cap;
     }
-    R->have_tuples = true;
+    R->hcount = m;
   }
-  *n = (int64_t)(R->tuples.size() / (size_t)R->k);
-  *h_tuples = R->tuples.data();
+  *n = R->hcount;
+  *h_tuples = R->htup;
   return VX_OK;
 }
 
@@ -1730,6 +1800,7 @@ int vx_result_elapsed_ms(const vx_result *R, double *ms) {
 
 void vx_result_free(vx_result *R) {
   if (!R) return;
+  pinned_put(R->htup, R->hcap);
   csf_release(&R->fin);
   R->tm.release();
   delete R;

@@ -352,7 +352,9 @@ class Result:
         self.k = k
         self.depth = depth
 
-    def boxes(self) -> np.ndarray:
+    def boxes(self, copy=True) -> np.ndarray:
+        """The surviving boxes [n, k] int32.  copy=False returns a view of the result's own
+        (pinned) host buffer, valid until free()."""
         n = ctypes.c_int64()
         p = ctypes.c_void_p()
         _check(lib().vx_result_boxes(self.handle, ctypes.byref(n), ctypes.byref(p)))
@@ -360,7 +362,8 @@ class Result:
         if m == 0:
             return np.zeros((0, self.k), dtype=np.int32)
         buf = (ctypes.c_int32 * (m * self.k)).from_address(p.value)
-        return np.frombuffer(buf, dtype=np.int32).reshape(m, self.k).copy()
+        a = np.frombuffer(buf, dtype=np.int32).reshape(m, self.k)
+        return a.copy() if copy else a
 
     def csf(self) -> Csf:
         h = ctypes.c_void_p()

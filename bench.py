@@ -279,6 +279,47 @@ def bench_dense_tc(vx, torch, stream, flush, sysv, s, d, level, reps, keep64, be
     return res
 
 
+def bench_precision(vx, synth, torch):
+    """Per config (plain, surface, curve): excess boxes of binary32 midpoint-radius over
+    binary64 at every level (no binary64 final level), and the radius inflation on the
+    binary64 survivors of the last level: per box and polynomial, the midpoint-radius width
+    2r over the binary64 width hi - lo (a seeded sample of at most 200 000 boxes)."""
+    out = {}
+    for name, make in (("plain", synth.plain), ("surface", synth.surface), ("curve", synth.curve)):
+        s = make()
+        sysv = vx.System(s.polys)
+        r64 = vx.enclose_system(sysv, s.domain, s.depth, vx.make_opts(vx.FP64))
+        rmr = vx.enclose_system(sysv, s.domain, s.depth, vx.make_opts(vx.FP32_MIDRAD))
+        r32 = vx.enclose_system(sysv, s.domain, s.depth, vx.make_opts(vx.FP32))
+        k64 = r64.stats()["kept"].astype(np.float64)
+        kmr = rmr.stats()["kept"].astype(np.float64)
+        excess = (kmr / np.maximum(k64, 1) - 1.0).tolist()
+        t = r64.csf().tuples()
+        n = int(t.shape[0])
+        if n > 200000:
+            sel = torch.from_numpy(np.unique(synth.Stream(11).uniform_int(0, n - 1, 200000))).cuda()
+            t = t[sel].contiguous()
+        c = vx.csf_build(s.k, s.depth, t)
+        _, lo, hi = vx.csf_eval_level(sysv, c, s.domain, vx.FP64, values=True)
+        _, mlo, mhi = vx.csf_eval_level(sysv, c, s.domain, vx.FP32_MIDRAD, values=True)
+        ratio = ((mhi - mlo) / torch.clamp(hi - lo, min=1e-300)).flatten()
+        q = torch.quantile(ratio.float(), torch.tensor([0.5, 0.9, 0.99], device=ratio.device))
+        out[name] = {
+            "midrad_excess_per_level": [round(x, 4) for x in excess],
+            "midrad_excess_max_intermediate": round(max(excess[:-1]) if len(excess) > 1 else 0.0, 4),
+            "midrad_excess_final": round(excess[-1], 4),
+            "certified_fp32_excess": 0.0 if np.array_equal(r32.stats()["kept"], r64.stats()["kept"]) else None,
+            "radius_inflation_median": round(float(q[0]), 4),
+            "radius_inflation_p90": round(float(q[1]), 4),
+            "radius_inflation_p99": round(float(q[2]), 4),
+            "boxes_sampled": int(t.shape[0]),
+        }
+        c.free()
+        for r in (r64, rmr, r32):
+            r.free()
+    return out
+
+
 def bench_batch(vx, synth, torch, workers=16):
     """Config 4: 256 independent systems (128 bivariate single equations of degree 10..60 and
     128 trivariate pairs of degree 10..40, depths 8..10) through vx_enclose_batch, from host
@@ -513,6 +554,7 @@ def run_gpu(args):
         log("[bench] dense level and batch")
         extra["dense_level"] = bench_dense(vx, synth, torch, stream, flush)
         extra["batch"] = bench_batch(vx, synth, torch)
+        extra["precision"] = bench_precision(vx, synth, torch)
 
     # ---- CPU oracle on a bounded sample ------------------------------------------------------
     cpu = None

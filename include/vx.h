@@ -269,9 +269,10 @@ int vx_dense_plan_bytes(const vx_dense_plan *plan, int64_t *bytes);
 void vx_dense_plan_free(vx_dense_plan *plan);
 /* The superset as a bit mask (device, caller-owned, 2^(3 level) / 32 words): bit b of word w
  * is box i = 32 w + b, i = (t1 2^level + t2) 2^level + t3, set iff the box is kept.  Launches
- * only (3 per polynomial, no allocation, no synchronisation: capturable in a CUDA graph);
- * a tensor-core wait that gave up is reported by the next vx_dense_level or
- * vx_dense_check_status. */
+ * only (3 per polynomial, no allocation, no synchronisation): the first call for a mask
+ * address captures them as a CUDA graph, later calls replay it.  A plan serves one host
+ * thread at a time.  A tensor-core wait that gave up is reported by the next vx_dense_level
+ * or vx_dense_check_status. */
 int vx_dense_prefilter(const vx_dense_plan *plan, uint32_t *d_mask, void *stream);
 /* VX_ETIMEOUT if a bounded wait inside a tensor-core kernel gave up since the last check
  * (the outputs of that launch are not valid); synchronises `stream`. */

@@ -802,6 +802,8 @@ struct vx_dense_plan {
   const vx_system *sys = nullptr;
   int level = 0;
   double domain[2 * VX_KMAX];
+  uint32_t *mask = nullptr;  // vx_dense_level's mask (one address: the prefilter graph is reused)
+  cudaStream_t stream = nullptr;
 };
 
 int vx_dense_plan_create(const vx_system *sys, int32_t level, const double *h_domain,
@@ -830,6 +832,7 @@ int vx_dense_plan_create(const vx_system *sys, int32_t level, const double *h_do
   }
   d->sys = sys;
   d->level = level;
+  d->stream = as_stream(stream);
   std::memcpy(d->domain, h_domain, 6 * sizeof(double));
   cudaStream_t s = as_stream(stream);
   int rc = dense_plan_create(sys->dev.npoly, hp.data(), level, h_domain, s, &d->p);
@@ -861,6 +864,7 @@ int vx_dense_plan_bytes(const vx_dense_plan *plan, int64_t *bytes) {
 
 void vx_dense_plan_free(vx_dense_plan *plan) {
   if (!plan) return;
+  dfree(plan->mask, plan->stream);
   dense_plan_free(plan->p);
   delete plan;
 }
@@ -917,11 +921,13 @@ int vx_dense_level(const vx_dense_plan *plan, const vx_opts *opts, uint8_t *d_ke
   }
   LevelGrid g;
   VX_CHECK(make_grid(3, plan->domain, level, &g));
-  uint32_t *mask = nullptr;
   int32_t *tup = nullptr;
   uint8_t *sub = nullptr;
   int64_t n = 0;
-  int rc = dmalloc((void **)&mask, (size_t)(nbox / 8), s);
+  int rc = VX_OK;
+  vx_dense_plan *mp = const_cast<vx_dense_plan *>(plan);  // the plan's own mask, made once
+  if (!mp->mask) rc = dmalloc((void **)&mp->mask, (size_t)(nbox / 8), s);
+  uint32_t *mask = mp->mask;
   if (rc == VX_OK) rc = dense_prefilter(plan->p, mask, s);
   if (rc == VX_OK) rc = vx_dense_check_status(stream);
   if (rc == VX_OK) rc = mask_tuples(mask, level, s, &tup, &n);
@@ -953,7 +959,6 @@ int vx_dense_level(const vx_dense_plan *plan, const vx_opts *opts, uint8_t *d_ke
   }
   dfree(sub, s);
   dfree(tup, s);
-  dfree(mask, s);
   if (rc == VX_OK && n_survivors) *n_survivors = n;
   return rc;
 }

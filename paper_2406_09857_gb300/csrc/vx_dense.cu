@@ -401,8 +401,6 @@ int launch_mode(const TcArgs &a, cudaStream_t s) {
   // a 512-column TMEM allocation must not wait on a second resident block: ask for more than
   // half of the SM's shared memory then
   const size_t smem = a.NT > 128 ? std::max<size_t>(need, 120 * 1024) : need;
-  VX_CUDA(cudaFuncSetAttribute(k_tc_mode<EPI>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                               (int)(200 * 1024)));
   const int64_t blocks = a.batches * a.mtiles * a.ntiles;
   if (blocks > 0x7fffffffll) {
     set_error("dense level: %lld tiles exceed one launch", (long long)blocks);
@@ -415,6 +413,16 @@ int launch_mode(const TcArgs &a, cudaStream_t s) {
 }
 
 inline int roundup(int x, int m) { return (x + m - 1) / m * m; }
+
+// The shared-memory limit of the four tensor-core kernels, set outside any stream capture.
+int set_tc_attributes() {
+  const int lim = 200 * 1024;
+  VX_CUDA(cudaFuncSetAttribute(k_tc_mode<EPI_NEXT_B>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim));
+  VX_CUDA(cudaFuncSetAttribute(k_tc_mode<EPI_NEXT_A>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim));
+  VX_CUDA(cudaFuncSetAttribute(k_tc_mode<EPI_BITS>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim));
+  VX_CUDA(cudaFuncSetAttribute(k_tc_mode<EPI_VALUES>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim));
+  return VX_OK;
+}
 
 }  // namespace
 
@@ -440,6 +448,9 @@ struct DensePlan {
   std::vector<void *> mem;
   size_t bytes = 0;
   cudaStream_t stream = nullptr;
+  // the prefilter's launch sequence captured as a CUDA graph (for the mask it writes)
+  cudaGraphExec_t graph = nullptr;
+  uint32_t *graph_mask = nullptr;
 };
 
 static int plan_alloc(DensePlan *p, float **out, size_t floats, cudaStream_t s) {
@@ -454,6 +465,7 @@ static int plan_alloc(DensePlan *p, float **out, size_t floats, cudaStream_t s) 
 
 void dense_plan_free(DensePlan *p) {
   if (!p) return;
+  if (p->graph) cudaGraphExecDestroy(p->graph);
   for (void *m : p->mem) dfree(m, p->stream);
   delete p;
 }
@@ -471,6 +483,10 @@ int dense_plan_create(int npoly, const DenseHostPoly *polys, int level, const do
     return VX_ENOMEM;
   }
   p->stream = s;
+  if (set_tc_attributes() != VX_OK) {
+    delete p;
+    return VX_ECUDA;
+  }
   p->level = level;
   p->npoly = npoly;
   p->N = (int64_t)1 << level;
@@ -659,8 +675,36 @@ static int run_poly(const DensePlan *p, int f, uint32_t *mask, float *v_mid, flo
   return launch_mode<EPI_VALUES>(c, s);
 }
 
-int dense_prefilter(const DensePlan *p, uint32_t *d_mask, cudaStream_t s) {
-  for (int f = 0; f < p->npoly; ++f) VX_CHECK(run_poly(p, f, d_mask, nullptr, nullptr, s));
+// The prefilter's launches (3 per polynomial, plus clears of the intermediates) are the same
+// on every call for a given mask, so they are captured once as a CUDA graph and replayed.
+int dense_prefilter(DensePlan *p, uint32_t *d_mask, cudaStream_t s) {
+  if (!p->graph || p->graph_mask != d_mask) {
+    if (p->graph) {
+      cudaGraphExecDestroy(p->graph);
+      p->graph = nullptr;
+    }
+    cudaStream_t cs = nullptr;
+    VX_CUDA(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
+    cudaGraph_t g = nullptr;
+    int rc = VX_OK;
+    if (cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal) != cudaSuccess) rc = VX_ECUDA;
+    for (int f = 0; f < p->npoly && rc == VX_OK; ++f) rc = run_poly(p, f, d_mask, nullptr, nullptr, cs);
+    const cudaError_t e1 = cudaStreamEndCapture(cs, &g);
+    if (rc == VX_OK && e1 != cudaSuccess) rc = VX_ECUDA;
+    if (rc == VX_OK && cudaGraphInstantiate(&p->graph, g, 0) != cudaSuccess) {
+      p->graph = nullptr;
+      rc = VX_ECUDA;
+    }
+    if (g) cudaGraphDestroy(g);
+    cudaStreamDestroy(cs);
+    if (rc != VX_OK) {
+      if (rc == VX_ECUDA) set_error("dense prefilter: capturing the launch graph failed");
+      return rc;
+    }
+    p->graph_mask = d_mask;
+  }
+  VX_CUDA(cudaGraphLaunch(p->graph, s));
+  note_launch(3 * p->npoly);
   return VX_OK;
 }
 

@@ -223,7 +223,7 @@ int dense_plan_create(int npoly, const DenseHostPoly *polys, int level, const do
 void dense_plan_free(DensePlan *p);
 int64_t dense_plan_bytes(const DensePlan *p);
 int dense_plan_level(const DensePlan *p);
-int dense_prefilter(const DensePlan *p, uint32_t *d_mask, cudaStream_t s);
+int dense_prefilter(DensePlan *p, uint32_t *d_mask, cudaStream_t s);
 int dense_values(const DensePlan *p, int f, float *d_mid, float *d_rad, cudaStream_t s);
 int set_dense_wait_polls(int64_t polls);
 int take_dense_status(cudaStream_t s, int *status);

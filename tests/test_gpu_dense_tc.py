@@ -179,3 +179,23 @@ def test_bounded_wait_gives_up_cleanly(vx):
     again = plan.prefilter()
     assert torch.equal(again, good)
     plan.free()
+
+
+def test_prefilter_graph_replay(vx):
+    """The prefilter's launches are captured once per mask buffer and replayed: repeated calls
+    on one buffer, and a call on another buffer, give the same bits."""
+    import torch
+
+    polys = [synth.gaussian_tensor_poly(3, 16, 540), synth.gaussian_tensor_poly(3, 9, 541)]
+    plan = vx.DensePlan(vx.System(polys), 6, synth.cube(3))
+    m = torch.empty((1 << 18) // 32, dtype=torch.int32, device="cuda")
+    first = plan.prefilter(m).clone()
+    for _ in range(3):
+        m.fill_(0)
+        assert torch.equal(plan.prefilter(m), first)
+    other = torch.full_like(m, -1)
+    assert torch.equal(plan.prefilter(other), first)
+    k1, n1 = plan.level_keep(vx.make_opts(vx.FP32))
+    k2, n2 = plan.level_keep(vx.make_opts(vx.FP32))
+    assert n1 == n2 and torch.equal(k1, k2)
+    plan.free()

@@ -320,6 +320,68 @@ def bench_precision(vx, synth, torch):
     return out
 
 
+# Table 1 of the paper (single thread, the paper's laptop, Taylor-form C0 and C1 for single
+# equations): seconds per cell, for context next to ours (different criteria, other hardware)
+PAPER_TABLE1_S = {
+    (2, 20): {"points": 0.006, "curves": 0.062, "hypersurfaces": 0.062},
+    (2, 100): {"points": 0.32, "curves": 0.31, "hypersurfaces": 0.31},
+    (3, 20): {"points": 0.5, "curves": 1.3, "hypersurfaces": 1.1},
+    (3, 100): {"points": 273.0, "curves": 270.0, "hypersurfaces": 412.0},
+    (4, 20): {"points": 56.0, "curves": 91.0, "hypersurfaces": 373.0},
+}
+
+
+def bench_table1(vx, synth, torch, stream):
+    """The random-polynomial family of the experiments (Sec. 4.1, Table 1): k = 2, 3, 4,
+    total degree 20 or 100 (20 for k = 4), coefficients U[-10, 10], [-2,2]^k; points (k
+    equations) and curves (k-1) to boxes of size 2^-8 (depth 10), hypersurfaces to 2^-5
+    (depth 7) with exclusion only.  Certified binary32 enclosure time (system resident, CUDA
+    events, best of 2 after a warm-up) and boxes; the paper's seconds as context."""
+    out = {}
+    for (k, d), paper in PAPER_TABLE1_S.items():
+        for kind in ("points", "curves", "hypersurfaces"):
+            s = synth.table1(k, d, kind)
+            sysv = vx.System(s.polys, stream=stream)
+            opts = vx.make_opts(vx.FP32)
+            # the largest depth <= the paper's whose levels fit 32-bit tree indices
+            depth, note = s.depth, None
+            while True:
+                try:
+                    vx.enclose_system(sysv, s.domain, depth, opts, stream=stream).free()
+                    break
+                except vx.VxError as e:
+                    if e.code != vx.EOVERFLOW or depth <= 1:
+                        raise
+                    note = "depth %d exceeds 32-bit tree indices (%s)" % (s.depth, e)
+                    depth -= 1
+            best, r = None, None
+            for _ in range(2):
+                e0 = torch.cuda.Event(enable_timing=True)
+                e1 = torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                rr = vx.enclose_system(sysv, s.domain, depth, opts, stream=stream)
+                e1.record(stream)
+                e1.synchronize()
+                ms = e0.elapsed_time(e1)
+                if best is None or ms < best:
+                    best = ms
+                    if r is not None:
+                        r.free()
+                    r = rr
+                else:
+                    rr.free()
+            st = r.stats()
+            out["k%d-d%d-%s" % (k, d, kind)] = {
+                "ms": round(best, 3), "depth": depth, "paper_depth": s.depth, "note": note,
+                "boxes": int(st["kept"][-1]),
+                "box_evals": int(st["tested"].sum()),
+                "box_evals_per_s": float(st["tested"].sum()) / (best * 1e-3),
+                "paper_voxelize_s": paper[kind]}
+            r.free()
+            sysv.free()
+    return out
+
+
 def bench_batch(vx, synth, torch, workers=16):
     """Config 4: 256 independent systems (128 bivariate single equations of degree 10..60 and
     128 trivariate pairs of degree 10..40, depths 8..10) through vx_enclose_batch, from host
@@ -555,6 +617,7 @@ def run_gpu(args):
         extra["dense_level"] = bench_dense(vx, synth, torch, stream, flush)
         extra["batch"] = bench_batch(vx, synth, torch)
         extra["precision"] = bench_precision(vx, synth, torch)
+        extra["table1"] = bench_table1(vx, synth, torch, stream)
 
     # ---- CPU oracle on a bounded sample ------------------------------------------------------
     cpu = None

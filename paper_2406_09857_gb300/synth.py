@@ -207,6 +207,29 @@ def dense_sweep(d: int = 32) -> System:
     return System("dense-k3-d%d" % d, 3, [gaussian_tensor_poly(3, d, seed_for(5, d))], cube(3), 0)
 
 
+def uniform_real_poly(k: int, d: int, lo: float, hi: float, seed: int):
+    """Dense total degree d, binary64 coefficients uniform in [lo, hi) (lo + (hi - lo) u)."""
+    e = dense_total_degree(k, d)
+    c = lo + (hi - lo) * Stream(seed).unit(e.shape[0])
+    return e, c
+
+
+# Depths of the random-polynomial family: boxes of [-2,2]^k no larger than 2^-8 for points
+# and curves, 2^-5 for hypersurfaces (exclusion only, no inclusion test).
+TABLE1_DEPTH = {"points": 10, "curves": 10, "hypersurfaces": 7}
+
+
+def table1(k: int, d: int, kind: str) -> System:
+    """The random-polynomial family of the experiments (Sec. 4.1): k variables, total degree
+    d, coefficients uniform in [-10, 10], on [-2,2]^k; points = k equations, curves = k-1,
+    hypersurfaces = 1."""
+    npoly = {"points": k, "curves": k - 1, "hypersurfaces": 1}[kind]
+    cell = 100 * k + d + {"points": 0, "curves": 1, "hypersurfaces": 2}[kind] * 1000
+    polys = [uniform_real_poly(k, d, -10.0, 10.0, seed_for(6, cell, p)) for p in range(npoly)]
+    return System("table1-%s-k%d-d%d" % (kind, k, d), k, polys, cube(k, -2.0, 2.0),
+                  TABLE1_DEPTH[kind])
+
+
 def random_small(k: int, d: int, npoly: int, seed: int, lo: int = -9, hi: int = 9,
                  density: float = 1.0):
     """Small dense-or-sparse integer polynomials for exhaustive tests."""

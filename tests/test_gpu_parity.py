@@ -521,3 +521,19 @@ def test_autotuner_variants_agree_and_cache_round_trips(vx, tmp_path):
         assert vx.autotune_entries() == n
     finally:
         vx.autotune(1)
+
+
+@pytest.mark.parametrize("k,d,kind,depth", [(2, 20, "points", 10), (2, 20, "curves", 9),
+                                            (3, 20, "points", 6), (3, 20, "curves", 5),
+                                            (3, 20, "hypersurfaces", 4), (4, 20, "points", 4),
+                                            (4, 20, "curves", 3), (4, 20, "hypersurfaces", 3)])
+def test_table1_family_equals_oracle(vx, k, d, kind, depth):
+    """The random-polynomial family of the experiments (U[-10,10] coefficients on [-2,2]^k, k
+    up to 4), at depths the oracle finishes quickly: binary64 and certified binary32 equal the
+    oracle's enclosure."""
+    s = synth.table1(k, d, kind)
+    ref = oracle.enclose(s.polys, s.domain, depth)
+    for mode in (vx.FP64, vx.FP32):
+        r = vx.enclose(s.polys, s.domain, depth, vx.make_opts(mode))
+        assert np.array_equal(r.boxes(), ref["tuples"])
+        assert np.array_equal(r.stats()["tested"], ref["tested"])

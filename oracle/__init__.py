@@ -61,10 +61,12 @@ def lib():
         L.orc_prim.argtypes = [i32, P, P, i64, P]
         L.orc_imul.argtypes = [P, P, P, P, i64, P, P]
         L.orc_dense_powerform.argtypes = [P, P, i64, P, i32, P, i64, P, P]
+        L.orc_taylor_boxes.argtypes = sysargs + [P, i32, i32, P, i64, P, P, P]
+        L.orc_enclose_taylor.argtypes = sysargs + [P, i32, i32, ctypes.POINTER(P)]
         for f in ("orc_eval_csf", "orc_eval_boxes", "orc_eval_grid", "orc_csf", "orc_enclose",
                   "orc_enclose_from",
                   "orc_brute_force", "orc_eval_grid_complex", "orc_domain_exact",
-                  "orc_dense_powerform"):
+                  "orc_dense_powerform", "orc_taylor_boxes", "orc_enclose_taylor"):
             getattr(L, f).restype = i32
         _lib = L
     return _lib
@@ -213,6 +215,11 @@ def enclose(polys, domain, depth, start_level=0, start=None):
         _check(L.orc_enclose_from(k, npoly, _p(off), _p(E), _p(C), _p(dom), int(start_level),
                                   _p(st), st.shape[0], int(depth), ctypes.byref(res)),
                "orc_enclose_from")
+    return _result(res, k, depth)
+
+
+def _result(res, k, depth):
+    L = lib()
     try:
         n = L.orc_result_count(res)
         tup = np.empty((n, k), dtype=np.int32)
@@ -279,3 +286,28 @@ def imul(alo, ahi, blo, bhi):
     hi = np.empty_like(arrs[0])
     lib().orc_imul(*[_p(x) for x in arrs], arrs[0].size, _p(lo), _p(hi))
     return lo, hi
+
+
+def taylor_boxes(polys, domain, level, order, tuples):
+    """Taylor form of the given order (Def. 3) of each polynomial on each box: lo, hi
+    [npoly, n] and keep [n] (0 in every polynomial's form)."""
+    k, npoly, off, E, C = pack(polys)
+    t = _tuples(tuples, k)
+    n = t.shape[0]
+    dom = np.ascontiguousarray(np.asarray(domain, dtype=np.float64).reshape(-1))
+    lo = np.empty((npoly, n))
+    hi = np.empty((npoly, n))
+    keep = np.empty(n, dtype=np.uint8)
+    _check(lib().orc_taylor_boxes(k, npoly, _p(off), _p(E), _p(C), _p(dom), int(level), int(order),
+                                  _p(t), n, _p(lo), _p(hi), _p(keep)), "orc_taylor_boxes")
+    return lo, hi, keep
+
+
+def enclose_taylor(polys, domain, depth, order):
+    """Algorithm 3 with C0 on the Taylor form of the given order."""
+    k, npoly, off, E, C = pack(polys)
+    dom = np.ascontiguousarray(np.asarray(domain, dtype=np.float64).reshape(-1))
+    res = ctypes.c_void_p()
+    _check(lib().orc_enclose_taylor(k, npoly, _p(off), _p(E), _p(C), _p(dom), int(depth),
+                                    int(order), ctypes.byref(res)), "orc_enclose_taylor")
+    return _result(res, k, depth)

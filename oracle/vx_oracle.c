@@ -351,6 +351,50 @@ static int eval_poly_csf(const plan *P, const double *coefs, const csf *T, const
 }
 
 /* Nested Horner on a single box: stage after stage, no CSF. */
+/* The centre of box t on an axis as a point interval (exact on the grids accepted here). */
+static ivl centre_ivl(const boxsrc *B, int axis, int32_t t) {
+  ivl r;
+  double lo = B->dom[2 * axis], hi = B->dom[2 * axis + 1];
+  double s = ldexp(1.0, -B->level);
+  double wd = rd_mul(rd_add(hi, -lo), s);
+  double wu = ru_mul(ru_add(hi, -lo), s);
+  r.lo = rd_add(lo, rd_mul((double)t + 0.5, wd));
+  r.hi = ru_add(lo, ru_mul((double)t + 0.5, wu));
+  return r;
+}
+
+/* Nested Horner of one polynomial with interval coefficients [clo, chi] on box `tup`, or on
+ * its centre when `point` is set. */
+static ivl eval_poly_box_ivl(const plan *P, const double *clo, const double *chi,
+                             const boxsrc *B, const int32_t *tup, int point, int64_t *work,
+                             int *rc) {
+  ivl z = {0.0, 0.0};
+  if (P->nterms == 0) return z;
+  ivl *cur = (ivl *)malloc(sizeof(ivl) * P->nterms);
+  ivl *nxt = (ivl *)malloc(sizeof(ivl) * P->nterms);
+  if (!cur || !nxt) {
+    free(cur);
+    free(nxt);
+    *rc = ORC_ENOMEM;
+    return z;
+  }
+  for (int i = 0; i < P->nterms; ++i) {
+    cur[i].lo = clo[i];
+    cur[i].hi = chi[i];
+  }
+  for (int j = 0; j < P->k; ++j) {
+    run_stage(&P->st[j], cur, point ? centre_ivl(B, j, tup[j]) : box_ivl(B, j, tup[j]), nxt,
+              work);
+    ivl *t = cur;
+    cur = nxt;
+    nxt = t;
+  }
+  z = cur[0];
+  free(cur);
+  free(nxt);
+  return z;
+}
+
 static ivl eval_poly_box(const plan *P, const double *coefs, const boxsrc *B, const int32_t *tup,
                          int64_t *work, int *rc) {
   ivl z = {0.0, 0.0};
@@ -678,15 +722,193 @@ int orc_enclose_from(int k, int npoly, const int64_t *term_off, const int32_t *e
                      const double *coefs, const double *domain, int start_level,
                      const int32_t *start, int64_t n0, int depth, orc_result **out);
 
+/* ------------------------------------------------------------------------------------ */
+/* Taylor form of order m (Def. 3).  With c the centre of B and x - c in [-r, r] per axis:  */
+/*   T_m(F, B) = sum_{|a| < m} G_a(c) (x - c)^a + sum_{|a| = m} []G_a(B) (x - c)^a,         */
+/* G_a = (d^a F / dx^a) / a! = sum_e f_e prod_i binom(e_i, a_i) x^(e - a), the multi-index */
+/* a running over |a| <= m in lexicographic order of (a_1, ..., a_k).  Each G_a has       */
+/* interval coefficients [RD(f_e C), RU(f_e C)], C = prod binom(e_i, a_i); G_a(c) is its   */
+/* nested Horner value on the point interval [c, c]; (x_i - c_i)^(a_i) ranges over [1, 1] */
+/* (a_i = 0), [0, r^a_i] (even) or [-r^a_i, r^a_i] (odd); the terms are interval products */
+/* summed in the order of the multi-indices, outward rounded.                               */
+/* ------------------------------------------------------------------------------------ */
+typedef struct {
+  int na;                   /* multi-indices */
+  int alpha[64][ORC_KMAX];  /* lexicographic */
+  plan pl[64];
+  int nterms[64];
+  double *clo[64], *chi[64];
+} taylor_sys;
+
+static int enum_alphas(int k, int m, int alpha[][ORC_KMAX], int cap) {
+  int n = 0, a[ORC_KMAX] = {0};
+  for (;;) {
+    int tot = 0;
+    for (int i = 0; i < k; ++i) tot += a[i];
+    if (tot <= m) {
+      if (n >= cap) return -1;
+      for (int i = 0; i < k; ++i) alpha[n][i] = a[i];
+      ++n;
+    }
+    int i = k - 1; /* next tuple in lexicographic order, entries 0..m */
+    while (i >= 0 && a[i] == m) a[i--] = 0;
+    if (i < 0) break;
+    ++a[i];
+  }
+  return n;
+}
+
+static double binom(int n, int r) {
+  double b = 1.0;
+  for (int i = 1; i <= r; ++i) b = b * (double)(n - r + i) / (double)i; /* exact: integers < 2^53 */
+  return b;
+}
+
+static void taylor_free(taylor_sys *T) {
+  for (int a = 0; a < T->na; ++a) {
+    plan_free(&T->pl[a]);
+    free(T->clo[a]);
+    free(T->chi[a]);
+  }
+}
+
+/* the derived polynomials G_a of one polynomial (rounding mode FE_DOWNWARD) */
+static int taylor_build(taylor_sys *T, int k, int m, int nterms, const int32_t *exps,
+                        const double *coefs) {
+  memset(T, 0, sizeof(*T));
+  T->na = enum_alphas(k, m, T->alpha, 64);
+  if (T->na < 0) return ORC_EINVAL;
+  int rc = ORC_OK;
+  for (int a = 0; a < T->na && rc == ORC_OK; ++a) {
+    const int *al = T->alpha[a];
+    int nt = 0;
+    for (int t = 0; t < nterms; ++t) {
+      int ok = 1;
+      for (int i = 0; i < k; ++i) ok = ok && exps[(size_t)t * k + i] >= al[i];
+      nt += ok;
+    }
+    int32_t *de = (int32_t *)malloc(sizeof(int32_t) * (size_t)(nt > 0 ? nt : 1) * k);
+    T->clo[a] = (double *)malloc(sizeof(double) * (size_t)(nt > 0 ? nt : 1));
+    T->chi[a] = (double *)malloc(sizeof(double) * (size_t)(nt > 0 ? nt : 1));
+    if (!de || !T->clo[a] || !T->chi[a]) {
+      free(de);
+      rc = ORC_ENOMEM;
+      break;
+    }
+    int j = 0;
+    for (int t = 0; t < nterms; ++t) {
+      int ok = 1;
+      for (int i = 0; i < k; ++i) ok = ok && exps[(size_t)t * k + i] >= al[i];
+      if (!ok) continue;
+      double C = 1.0;
+      for (int i = 0; i < k; ++i) C *= binom(exps[(size_t)t * k + i], al[i]);
+      T->clo[a][j] = rd_mul(coefs[t], C);
+      T->chi[a][j] = ru_mul(coefs[t], C);
+      for (int i = 0; i < k; ++i) de[(size_t)j * k + i] = exps[(size_t)t * k + i] - al[i];
+      ++j;
+    }
+    T->nterms[a] = nt;
+    rc = plan_build(&T->pl[a], k, nt, de);
+    free(de);
+  }
+  if (rc != ORC_OK) taylor_free(T);
+  return rc;
+}
+
+/* (x - c)^a over [-r, r] for one axis */
+static ivl pow_range(double r, int a) {
+  ivl z;
+  if (a == 0) {
+    z.lo = z.hi = 1.0;
+    return z;
+  }
+  double p = r;
+  for (int i = 1; i < a; ++i) p = ru_mul(p, r);
+  z.hi = p;
+  z.lo = (a & 1) ? -p : 0.0;
+  return z;
+}
+
+static ivl taylor_box(const taylor_sys *T, int k, int m, const boxsrc *B, const int32_t *tup,
+                      int64_t *work, int *rc) {
+  ivl acc = {0.0, 0.0};
+  double r[ORC_KMAX];
+  for (int i = 0; i < k; ++i) {
+    ivl X = box_ivl(B, i, tup[i]);
+    r[i] = ru_mul(ru_add(X.hi, -X.lo), 0.5);
+  }
+  for (int a = 0; a < T->na; ++a) {
+    int tot = 0;
+    for (int i = 0; i < k; ++i) tot += T->alpha[a][i];
+    ivl V = eval_poly_box_ivl(&T->pl[a], T->clo[a], T->chi[a], B, tup, tot < m, work, rc);
+    ivl P = {1.0, 1.0};
+    for (int i = 0; i < k; ++i) P = i_mul(P, pow_range(r[i], T->alpha[a][i]));
+    acc = i_add(acc, i_mul(V, P));
+  }
+  return acc;
+}
+
+/* The Taylor form of order m of each polynomial on each box (lo/hi [npoly][n]) and the C0
+ * decision (keep = 0 in every polynomial's form). */
+int orc_taylor_boxes(int k, int npoly, const int64_t *term_off, const int32_t *exps,
+                     const double *coefs, const double *domain, int level, int m,
+                     const int32_t *tuples, int64_t n, double *lo, double *hi, uint8_t *keep) {
+  int old = fegetround();
+  int rc = check_system(k, npoly, term_off);
+  if (rc != ORC_OK) return rc;
+  if (m < 1 || m > 8) return ORC_EINVAL;
+  fesetround(FE_DOWNWARD);
+  boxsrc B = {domain, level, 0, 0, 0};
+  int64_t w = 0;
+  for (int64_t i = 0; i < n && keep; ++i) keep[i] = 1;
+  for (int f = 0; f < npoly && rc == ORC_OK; ++f) {
+    taylor_sys T;
+    rc = taylor_build(&T, k, m, (int)(term_off[f + 1] - term_off[f]), exps + term_off[f] * k,
+                      coefs + term_off[f]);
+    if (rc != ORC_OK) break;
+    for (int64_t i = 0; i < n && rc == ORC_OK; ++i) {
+      ivl v = taylor_box(&T, k, m, &B, tuples + i * k, &w, &rc);
+      if (lo) lo[(int64_t)f * n + i] = v.lo;
+      if (hi) hi[(int64_t)f * n + i] = v.hi;
+      if (keep && (v.lo > 0.0 || v.hi < 0.0)) keep[i] = 0;
+    }
+    taylor_free(&T);
+  }
+  fesetround(old);
+  return rc;
+}
+
 int orc_enclose(int k, int npoly, const int64_t *term_off, const int32_t *exps, const double *coefs,
                 const double *domain, int depth, orc_result **out) {
   int32_t root[ORC_KMAX] = {0};
   return orc_enclose_from(k, npoly, term_off, exps, coefs, domain, 0, root, 1, depth, out);
 }
 
+static int enclose_core(int k, int npoly, const int64_t *term_off, const int32_t *exps,
+                        const double *coefs, const double *domain, int start_level,
+                        const int32_t *start, int64_t n0, int depth, int taylor_m,
+                        orc_result **out);
+
 int orc_enclose_from(int k, int npoly, const int64_t *term_off, const int32_t *exps,
                      const double *coefs, const double *domain, int start_level,
                      const int32_t *start, int64_t n0, int depth, orc_result **out) {
+  return enclose_core(k, npoly, term_off, exps, coefs, domain, start_level, start, n0, depth, 0,
+                      out);
+}
+
+/* Algorithm 3 with C0 on the Taylor form of order m (Def. 3) instead of interval Horner. */
+int orc_enclose_taylor(int k, int npoly, const int64_t *term_off, const int32_t *exps,
+                       const double *coefs, const double *domain, int depth, int m,
+                       orc_result **out) {
+  int32_t root[ORC_KMAX] = {0};
+  if (m < 1 || m > 8) return ORC_EINVAL;
+  return enclose_core(k, npoly, term_off, exps, coefs, domain, 0, root, 1, depth, m, out);
+}
+
+static int enclose_core(int k, int npoly, const int64_t *term_off, const int32_t *exps,
+                        const double *coefs, const double *domain, int start_level,
+                        const int32_t *start, int64_t n0, int depth, int taylor_m,
+                        orc_result **out) {
   int old = fegetround();
   int rc = check_system(k, npoly, term_off);
   *out = 0;
@@ -726,6 +948,17 @@ int orc_enclose_from(int k, int npoly, const int64_t *term_off, const int32_t *e
     if (!keep || !leaf) rc = ORC_ENOMEM;
     for (int64_t i = 0; i < n && keep; ++i) keep[i] = 1;
     for (int f = 0; rc == ORC_OK && f < npoly; ++f) {
+      if (taylor_m > 0) {
+        taylor_sys TS;
+        rc = taylor_build(&TS, k, taylor_m, (int)(term_off[f + 1] - term_off[f]),
+                          exps + term_off[f] * k, coefs + term_off[f]);
+        for (int64_t i = 0; rc == ORC_OK && i < n; ++i) {
+          ivl v = taylor_box(&TS, k, taylor_m, &B, S + i * k, &R->work[l], &rc);
+          if (v.lo > 0.0 || v.hi < 0.0) keep[i] = 0;
+        }
+        if (rc == ORC_OK || TS.na > 0) taylor_free(&TS);
+        continue;
+      }
       rc = eval_poly_csf(&plans[f], coefs + term_off[f], &T, &B, leaf, &R->work[l]);
       for (int64_t i = 0; rc == ORC_OK && i < n; ++i)
         if ((leaf[i].lo > 0.0 || leaf[i].hi < 0.0)) keep[i] = 0;

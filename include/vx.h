@@ -45,7 +45,7 @@ extern "C" {
 #define VX_ECUDA (-6)     /* a CUDA runtime call failed */
 
 #define VX_KMAX 4
-#define VX_MAXPOLY 8
+#define VX_MAXPOLY 16
 #define VX_MAXLEVEL 24
 
 /* Arithmetic of a level evaluation. */
@@ -84,7 +84,10 @@ typedef struct {
                          * for some polynomial are re-evaluated in VX_FP64 at the same level */
   float theta;          /* recheck threshold, 0 < theta <= 1 (0 means 0.5) */
   int32_t timing;       /* nonzero: time every kernel launch with CUDA events (vx_result_timing) */
-  int32_t reserved[7];
+  int32_t taylor_order; /* 0: C0 on nested interval Horner (Algorithm 2); m >= 1: C0 on the
+                         * Taylor form of order m (Def. 3), VX_FP64 only; the number of
+                         * multi-indices |a| <= m (C(m+k, k)) must not exceed VX_MAXPOLY */
+  int32_t reserved[6];
 } vx_opts;
 
 /* Thread-local message of the last failed call on this thread ("" if none). */
@@ -147,6 +150,19 @@ int vx_csf_tuples(const vx_csf *csf, int32_t *d_tuples, void *stream);
  * intervals as the hull of the endpoint products). */
 int vx_csf_eval_level(const vx_system *sys, const vx_csf *csf, const double *h_domain,
                       int32_t mode, double *d_lo, double *d_hi, uint8_t *d_keep, void *stream);
+
+/* C0 on the Taylor form of order m >= 1 (Def. 3, Sec. 3.2) instead of nested interval Horner:
+ * with c the centre of a box and x - c in [-r, r],
+ *   T_m(F, B) = sum_{|a| < m} G_a(c) (x - c)^a + sum_{|a| = m} []G_a(B) (x - c)^a,
+ * G_a = (d^a F / dx^a) / a! (interval coefficients: the integer factors times the binary64
+ * coefficients rounded both ways), G_a(c) by Algorithm 2 on the centres' point intervals and
+ * []G_a(B) on the boxes, (x - c)^a as the exact range of each variable's power, the terms
+ * summed in lexicographic order of a with outward rounding; keep = 0 in every polynomial's
+ * form.  Binary64 only.  C(m+k, k) must not exceed VX_MAXPOLY.  d_lo/d_hi (nullable,
+ * [npoly][N_k] binary64) receive T; d_keep [N_k].  Synchronises `stream`. */
+int vx_csf_eval_level_taylor(const vx_system *sys, const vx_csf *csf, const double *h_domain,
+                             int32_t order, double *d_lo, double *d_hi, uint8_t *d_keep,
+                             void *stream);
 
 /* Algorithm 2 takes the intervals of x_1 as a list (Sec. 2.2); this is vx_csf_eval_level with
  * an explicit interval list per axis instead of the regular grid: a depth-j node labelled t

@@ -9,6 +9,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <array>
 #include <atomic>
 #include <map>
 #include <mutex>
@@ -266,6 +267,30 @@ static float f32_round_down(double x) {
 // 2^-23 |c|) + 2^-148 on the distance to the binary64 coefficient (which the binary64 path
 // uses as it is); the 2^-23 |c| keeps E >= 2^-23 max(|RD(c)|, |RU(c)|), which the error
 // recursion of the evaluation kernels relies on.
+// An interval coefficient [lo, hi] in the binary32 encodings (both contain it).
+static float2 to_midrad_ivl(double lo, double hi) {
+  if (lo == hi) return to_midrad(lo);
+  const float m = (float)(0.5 * lo + 0.5 * hi);
+  if (!std::isfinite(m)) return make_float2(0.f, INFINITY);
+  const double dm = (double)m;
+  const double d = std::max(hi - dm, dm - lo);  // rounded below by at most an ulp: pad it
+  const float r = f32_round_up(d * (1.0 + std::ldexp(1.0, -50)) + std::ldexp(1.0, -149));
+  return make_float2(m, r);
+}
+
+static float4 to_certified(double c);
+static float4 to_certified_ivl(double lo, double hi) {
+  if (lo == hi) return to_certified(lo);
+  const float flo = f32_round_down(lo), fhi = f32_round_up(hi);
+  if (!std::isfinite(flo) || !std::isfinite(fhi))
+    return make_float4(-INFINITY, -INFINITY, INFINITY, 0.f);
+  const double d = std::max(lo - (double)flo, (double)fhi - hi);  // exact
+  const double mag = std::max(std::fabs(lo), std::fabs(hi));
+  const double bound = (d + std::ldexp(mag, -23)) * (1.0 + std::ldexp(1.0, -39));
+  const float e = f32_round_up(bound + std::ldexp(1.0, -148));
+  return make_float4(flo, -fhi, e, 0.f);
+}
+
 static float4 to_certified(double c) {
   const float lo = f32_round_down(c), hi = f32_round_up(c);
   if (!std::isfinite(lo) || !std::isfinite(hi)) return make_float4(-INFINITY, -INFINITY, INFINITY, 0.f);
@@ -275,7 +300,8 @@ static float4 to_certified(double c) {
   return make_float4(lo, -hi, e, 0.f);
 }
 
-static int pack_poly(int k, const vx_poly &p, HostPoly *hp) {
+// chi (nullable): upper ends of interval coefficients [p.coefs[t], chi[t]]
+static int pack_poly(int k, const vx_poly &p, HostPoly *hp, const double *chi = nullptr) {
   const int32_t nt = p.nterms;
   if (p.nvars != k || nt < 0 || (nt > 0 && (!p.exps || !p.coefs))) {
     set_error("polynomial: nvars %d (expected %d), nterms %d", p.nvars, k, nt);
@@ -288,8 +314,8 @@ static int pack_poly(int k, const vx_poly &p, HostPoly *hp) {
     }
   }
   for (int32_t t = 0; t < nt; ++t) {
-    if (!std::isfinite(p.coefs[t])) {
-      set_error("polynomial: coefficient %d is not finite", t);
+    if (!std::isfinite(p.coefs[t]) || (chi && !(std::isfinite(chi[t]) && chi[t] >= p.coefs[t]))) {
+      set_error("polynomial: coefficient %d is not finite (or not an interval)", t);
       return VX_EINVAL;
     }
   }
@@ -385,13 +411,13 @@ static int pack_poly(int k, const vx_poly &p, HostPoly *hp) {
       return VX_EINVAL;
     }
     seen[pos] = 1;
-    hp->c64[pos] = make_double2(p.coefs[t], p.coefs[t]);
+    hp->c64[pos] = make_double2(p.coefs[t], chi ? chi[t] : p.coefs[t]);
   }
   hp->c32.resize(S0.blk_in);
   hp->c32c.resize(S0.blk_in);
   for (int64_t i = 0; i < S0.blk_in; ++i) {
-    hp->c32[i] = to_midrad(hp->c64[i].x);
-    hp->c32c[i] = to_certified(hp->c64[i].x);
+    hp->c32[i] = to_midrad_ivl(hp->c64[i].x, hp->c64[i].y);
+    hp->c32c[i] = to_certified_ivl(hp->c64[i].x, hp->c64[i].y);
   }
   return VX_OK;
 }
@@ -461,6 +487,13 @@ struct vx_system {
   // the polynomials as given (exponents [nterms][k], coefficients), for dense-level plans
   std::vector<std::vector<int32_t>> exps;
   std::vector<std::vector<double>> coefs;
+  // Taylor forms (Def. 3): per order m, per polynomial, the system of its G_a, made on first use
+  struct TaylorSet {
+    vx_system *sys = nullptr;
+    std::vector<std::array<int8_t, VX_KMAX>> alpha;
+  };
+  std::mutex tmu;
+  std::map<int, std::vector<TaylorSet>> taylor;
 };
 
 struct vx_csf {
@@ -528,8 +561,18 @@ extern "C" {
 
 const char *vx_last_error(void) { return g_err; }
 
+static int system_create_impl(const vx_poly *F, int32_t npoly, const double *const *chi,
+                              void *stream, vx_system **out);
+
 int vx_system_create(const vx_poly *F, int32_t npoly, void *stream, vx_system **out) {
   clear_error();
+  return system_create_impl(F, npoly, nullptr, stream, out);
+}
+
+// chi (nullable): per polynomial, the upper ends of interval coefficients (F[f].coefs the
+// lower ends).
+static int system_create_impl(const vx_poly *F, int32_t npoly, const double *const *chi,
+                              void *stream, vx_system **out) {
   if (!out || !F || npoly < 1 || npoly > VX_MAXPOLY) {
     set_error("vx_system_create: need 1..%d polynomials and an out pointer", VX_MAXPOLY);
     return VX_EINVAL;
@@ -550,7 +593,7 @@ int vx_system_create(const vx_poly *F, int32_t npoly, void *stream, vx_system **
     std::vector<std::thread> th;
     for (int f = 0; f < npoly; ++f)
       th.emplace_back([&, f] {
-        rcs[f] = pack_poly(k, F[f], &hp[f]);
+        rcs[f] = pack_poly(k, F[f], &hp[f], chi ? chi[f] : nullptr);
         if (rcs[f] != VX_OK) msgs[f] = vx_last_error();
       });
     for (auto &t : th) t.join();
@@ -560,7 +603,7 @@ int vx_system_create(const vx_poly *F, int32_t npoly, void *stream, vx_system **
         return rcs[f];
       }
   } else {
-    for (int f = 0; f < npoly; ++f) VX_CHECK(pack_poly(k, F[f], &hp[f]));
+    for (int f = 0; f < npoly; ++f) VX_CHECK(pack_poly(k, F[f], &hp[f], chi ? chi[f] : nullptr));
   }
   // one device allocation: per polynomial the two coefficient blocks, then per stage the
   // row offsets, fibre lengths and output positions
@@ -637,6 +680,8 @@ int vx_system_create(const vx_poly *F, int32_t npoly, void *stream, vx_system **
 
 void vx_system_free(vx_system *sys) {
   if (!sys) return;
+  for (auto &kv : sys->taylor)
+    for (auto &ts : kv.second) vx_system_free(ts.sys);
   dfree(sys->mem, sys->stream);
   delete sys;
 }
@@ -963,6 +1008,141 @@ int vx_dense_level(const vx_dense_plan *plan, const vx_opts *opts, uint8_t *d_ke
   return rc;
 }
 
+// ---------------------------------------------------------------------------------------
+// Taylor form (Def. 3): G_a = d^a F / a! = sum_e f_e prod_i binom(e_i, a_i) x^(e - a) for the
+// multi-indices |a| <= m in lexicographic order; the coefficients become intervals
+// [RD(f_e C), RU(f_e C)] (C an integer below 2^53, the product rounded both ways exactly).
+// ---------------------------------------------------------------------------------------
+static int taylor_sets(const vx_system *csys, int m, cudaStream_t s,
+                       std::vector<vx_system::TaylorSet> **out) {
+  vx_system *sys = const_cast<vx_system *>(csys);  // the cache is the system's own
+  std::lock_guard<std::mutex> g(sys->tmu);
+  auto it = sys->taylor.find(m);
+  if (it != sys->taylor.end()) {
+    *out = &it->second;
+    return VX_OK;
+  }
+  const int k = sys->dev.k;
+  std::vector<std::array<int8_t, VX_KMAX>> alpha;
+  {
+    int a[VX_KMAX] = {0};
+    for (;;) {
+      int tot = 0;
+      for (int i = 0; i < k; ++i) tot += a[i];
+      if (tot <= m) {
+        std::array<int8_t, VX_KMAX> al{};
+        for (int i = 0; i < k; ++i) al[i] = (int8_t)a[i];
+        alpha.push_back(al);
+      }
+      int i = k - 1;
+      while (i >= 0 && a[i] == m) a[i--] = 0;
+      if (i < 0) break;
+      ++a[i];
+    }
+  }
+  if ((int)alpha.size() > VX_MAXPOLY) {
+    set_error("Taylor form of order %d in %d variables has %zu terms (at most %d)", m, k,
+              alpha.size(), VX_MAXPOLY);
+    return VX_EINVAL;
+  }
+  std::vector<vx_system::TaylorSet> sets(sys->dev.npoly);
+  int rc = VX_OK;
+  for (int f = 0; f < sys->dev.npoly && rc == VX_OK; ++f) {
+    const std::vector<int32_t> &E = sys->exps[f];
+    const std::vector<double> &Cf = sys->coefs[f];
+    const int64_t nt = (int64_t)Cf.size();
+    const int na = (int)alpha.size();
+    std::vector<std::vector<int32_t>> de(na);
+    std::vector<std::vector<double>> lo(na), hi(na);
+    for (int a = 0; a < na && rc == VX_OK; ++a)
+      for (int64_t t = 0; t < nt; ++t) {
+        bool ok = true;
+        for (int i = 0; i < k; ++i) ok = ok && E[t * k + i] >= alpha[a][i];
+        if (!ok) continue;
+        double C = 1.0;
+        for (int i = 0; i < k; ++i) {
+          const int n = E[t * k + i], r = alpha[a][i];
+          double b = 1.0;
+          for (int j = 1; j <= r; ++j) b = b * (double)(n - r + j) / (double)j;  // exact integers
+          C *= b;
+        }
+        if (C >= 9007199254740992.0) {
+          set_error("Taylor form: a binomial product reaches 2^53");
+          rc = VX_EINVAL;
+          break;
+        }
+        const double c = Cf[t], p = c * C, err = std::fma(c, C, -p);
+        lo[a].push_back(err < 0 ? std::nextafter(p, -INFINITY) : p);
+        hi[a].push_back(err > 0 ? std::nextafter(p, INFINITY) : p);
+        for (int i = 0; i < k; ++i) de[a].push_back(E[t * k + i] - alpha[a][i]);
+      }
+    if (rc != VX_OK) break;
+    std::vector<vx_poly> P(na);
+    std::vector<const double *> chi(na);
+    for (int a = 0; a < na; ++a) {
+      P[a].nvars = k;
+      P[a].nterms = (int32_t)lo[a].size();
+      P[a].exps = de[a].empty() ? nullptr : de[a].data();
+      P[a].coefs = lo[a].empty() ? nullptr : lo[a].data();
+      chi[a] = hi[a].empty() ? nullptr : hi[a].data();
+    }
+    rc = system_create_impl(P.data(), na, chi.data(), (void *)s, &sets[f].sys);
+    sets[f].alpha = alpha;
+  }
+  if (rc != VX_OK) {
+    for (auto &ts : sets) vx_system_free(ts.sys);
+    return rc;
+  }
+  auto ins = sys->taylor.emplace(m, std::move(sets));
+  *out = &ins.first->second;
+  return VX_OK;
+}
+
+// One level with C0 on the Taylor form of order m: keep = 0 in every polynomial's form.
+static int eval_taylor_level(const vx_system *sys, const CsfView &c, const LevelGrid &g, int m,
+                             double *d_lo, double *d_hi, uint8_t *keep, cudaStream_t s,
+                             Timer *tm, int64_t *madds) {
+  std::vector<vx_system::TaylorSet> *sets = nullptr;
+  VX_CHECK(taylor_sets(sys, m, s, &sets));
+  const int64_t n = c.N[c.k - 1];
+  *madds = 0;
+  for (int f = 0; f < sys->dev.npoly; ++f) {
+    const vx_system::TaylorSet &ts = (*sets)[f];
+    std::vector<int8_t> al((size_t)ts.alpha.size() * VX_KMAX);
+    for (size_t a = 0; a < ts.alpha.size(); ++a)
+      for (int d = 0; d < VX_KMAX; ++d) al[a * VX_KMAX + d] = ts.alpha[a][d];
+    int64_t w = 0;
+    VX_CHECK(eval_level_taylor(ts.sys->dev, (const int8_t(*)[VX_KMAX])al.data(), m, c, g, keep,
+                               f == 0, d_lo ? d_lo + (int64_t)f * n : nullptr,
+                               d_hi ? d_hi + (int64_t)f * n : nullptr, s, tm, &w));
+    *madds += w;
+  }
+  return VX_OK;
+}
+
+int vx_csf_eval_level_taylor(const vx_system *sys, const vx_csf *c, const double *h_domain,
+                             int32_t order, double *d_lo, double *d_hi, uint8_t *d_keep,
+                             void *stream) {
+  clear_error();
+  if (!sys || !c || !d_keep || (!d_lo) != (!d_hi) || c->o.v.k != sys->dev.k || order < 1) {
+    set_error("vx_csf_eval_level_taylor: bad arguments");
+    return VX_EINVAL;
+  }
+  LevelGrid g;
+  VX_CHECK(make_grid(c->o.v.k, h_domain, c->o.v.level, &g));
+  cudaStream_t s = as_stream(stream);
+  if (c->o.v.N[c->o.v.k - 1] == 0) return VX_OK;
+  int64_t w = 0;
+  VX_CHECK(eval_taylor_level(sys, c->o.v, g, order, d_lo, d_hi, d_keep, s, nullptr, &w));
+  int st = 0;
+  VX_CHECK(take_device_status(s, &st));
+  if (st) {
+    set_error("vx_csf_eval_level_taylor: a bounded device wait gave up");
+    return VX_ETIMEOUT;
+  }
+  return VX_OK;
+}
+
 int vx_csf_eval_grid(const vx_system *sys, const vx_csf *c, const double *const *d_xlo,
                      const double *const *d_xhi, const int64_t *nx, int32_t mode, double *d_lo,
                      double *d_hi, uint8_t *d_keep, void *stream) {
@@ -1102,6 +1282,11 @@ static int enclose_impl(const vx_system *sys, const double *dom, int depth, cons
     set_error("vx_enclose: theta %g outside (0, 1]", (double)theta);
     return VX_EINVAL;
   }
+  if (opts.taylor_order < 0 || (opts.taylor_order > 0 && opts.mode != VX_FP64)) {
+    set_error("vx_enclose: the Taylor form (order %d) is evaluated in VX_FP64 only",
+              opts.taylor_order);
+    return VX_EINVAL;
+  }
   if (depth < 0 || depth > VX_MAXLEVEL) {
     set_error("vx_enclose: depth %d outside [0, %d]", depth, VX_MAXLEVEL);
     return VX_EINVAL;
@@ -1149,8 +1334,13 @@ static int enclose_impl(const vx_system *sys, const double *dom, int depth, cons
     rc = dmalloc((void **)&keep, (size_t)std::max<int64_t>(n, 1), s);
     if (rc == VX_OK) {
       int64_t w = 0, nr = 0;
-      rc = eval_decide(sys->dev, cur.v, g, mode, opts.fp64_recheck != 0, theta, nullptr, nullptr,
-                       keep, s, tm, &w, &nr);
+      if (opts.taylor_order > 0)
+        rc = n > 0 ? eval_taylor_level(sys, cur.v, g, opts.taylor_order, nullptr, nullptr, keep,
+                                       s, tm, &w)
+                   : VX_OK;
+      else
+        rc = eval_decide(sys->dev, cur.v, g, mode, opts.fp64_recheck != 0, theta, nullptr,
+                         nullptr, keep, s, tm, &w, &nr);
       R->madds[l] += w;
       R->recheck[l] = nr;
       int st = 0;
@@ -1672,6 +1862,10 @@ int vx_enclose_batch(const vx_poly *const *systems, const int32_t *npoly, const 
   if (opts) o = *opts;
   if (o.mode != VX_FP64 && o.mode != VX_FP32_MIDRAD && o.mode != VX_FP32) {
     set_error("vx_enclose_batch: unknown mode %d", o.mode);
+    return VX_EINVAL;
+  }
+  if (o.taylor_order != 0) {
+    set_error("vx_enclose_batch: the Taylor form is not available in batches");
     return VX_EINVAL;
   }
   // domain offsets: system i owns 2 * k_i doubles; groups of equal k

@@ -66,7 +66,9 @@ constexpr int kThreads = 32 * kWarpsPerBlock;
 // The binary64 endpoints of box t on an axis: the regular grid (exact on accepted domains) or
 // the axis' explicit interval list.
 __device__ __forceinline__ void endpoints(const AxisGrid &g, int32_t t, double &l, double &h) {
-  if (g.xlo) {
+  if (g.point) {
+    l = h = __dadd_rn(g.lo, __dmul_rn((double)t + 0.5, g.w));  // exact on accepted grids
+  } else if (g.xlo) {
     l = g.xlo[t];
     h = g.xhi[t];
   } else {
@@ -622,6 +624,67 @@ __device__ __forceinline__ void horner_y2_fibre(const float4 *__restrict__ base,
   }
 }
 
+// ---------------------------------------------------------------------------------------
+// Taylor form (Def. 3) at the leaves: the system holds G_a = d^a F / a! for the multi-indices
+// |a| <= m of one polynomial F (lexicographic order); G_a with |a| < m was partially evaluated
+// at the box centres (point grids), the others on the boxes.  Per leaf:
+//   T = sum_a V_a * prod_i range((x_i - c_i)^{a_i}),  x_i - c_i in [-r_i, r_i],
+// the range [1,1] (a_i = 0), [0, r^a_i] (even), [-r^a_i, r^a_i] (odd), interval products as
+// hulls of directed endpoint products and outward sums, in the order of the oracle.  C0 on T.
+// ---------------------------------------------------------------------------------------
+struct TaylorLeaf {
+  int32_t na, m, k;
+  int8_t alpha[VX_MAXPOLY][VX_KMAX];
+  double r[VX_KMAX];  // half-widths of the level's boxes, per axis
+  int32_t first;      // 1: write keep, 0: AND into it (several polynomials)
+  double *lo, *hi;    // nullable: T per leaf
+};
+
+__device__ __forceinline__ double2 imul_hull(double2 x, double2 y) {
+  double2 r;
+  r.x = sel_min(sel_min(__dmul_rd(x.x, y.x), __dmul_rd(x.x, y.y)),
+                sel_min(__dmul_rd(x.y, y.x), __dmul_rd(x.y, y.y)));
+  r.y = sel_max(sel_max(__dmul_ru(x.x, y.x), __dmul_ru(x.x, y.y)),
+                sel_max(__dmul_ru(x.y, y.x), __dmul_ru(x.y, y.y)));
+  return r;
+}
+
+__device__ __forceinline__ double2 pow_range(double r, int a) {
+  if (a == 0) return make_double2(1.0, 1.0);
+  double p = r;
+  for (int i = 1; i < a; ++i) p = __dmul_ru(p, r);
+  return make_double2((a & 1) ? -p : 0.0, p);
+}
+
+__global__ void __launch_bounds__(kThreads)
+    k_leaf_taylor(LeafArgs A, const int32_t *__restrict__ lab, const int32_t *__restrict__ par,
+                  int64_t nleaves, AxisGrid gbox, AxisGrid gpoint, TaylorLeaf T,
+                  uint8_t *__restrict__ keep) {
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < nleaves; i += stride) {
+    const int32_t t = __ldg(lab + i);
+    const A64::X xb = A64::box(gbox, t), xp = A64::box(gpoint, t);
+    const int64_t p = par ? (int64_t)__ldg(par + i) : 0;
+    double2 acc = make_double2(0.0, 0.0);
+    for (int a = 0; a < T.na; ++a) {
+      int tot = 0;
+      for (int d = 0; d < T.k; ++d) tot += T.alpha[a][d];
+      const double2 *base = (const double2 *)A.in[a] + p * A.blk[a];
+      const double2 V = horner1_any<A64>(base, 1, A.len[a], tot < T.m ? xp : xb);
+      double2 P = make_double2(1.0, 1.0);
+      for (int d = 0; d < T.k; ++d) P = imul_hull(P, pow_range(T.r[d], T.alpha[a][d]));
+      const double2 VP = imul_hull(V, P);
+      acc = make_double2(__dadd_rd(acc.x, VP.x), __dadd_ru(acc.y, VP.y));
+    }
+    if (T.lo) {
+      T.lo[i] = acc.x;
+      T.hi[i] = acc.y;
+    }
+    const uint8_t k0 = (acc.x > 0.0 || acc.y < 0.0) ? 0 : 1;
+    keep[i] = T.first ? k0 : (uint8_t)(keep[i] & k0);
+  }
+}
+
 // One warp's share of k_stage_c: node pairs of chunk `chunk` (64 nodes), fibres g, g+G, ....
 // A warp whose 32 pairs each share a parent and do not straddle 0 shares every load between
 // the two nodes and runs sign-free (horner_y2_fibre); any other warp takes k_stage's per-node
@@ -969,10 +1032,14 @@ int tuned_launch(uint64_t key, int nvar, cudaStream_t s, F launch) {
 
 // ext_scratch != nullptr: the blocks are carved from it (ext_bytes long) and nothing is allocated.
 template <class AR>
+// pgrid (nullable): polynomial f's stages use pgrid[f] (point or box grids for the Taylor
+// form); tl (nullable, binary64 only): the leaves combine the polynomials into the Taylor form
+// instead of testing each one.
 int eval_level_t(const SysDev &sys, const CsfView &c, const LevelGrid &grid, double *d_lo,
                  double *d_hi, uint8_t *d_keep, uint8_t *d_flag, float theta, cudaStream_t s,
                  Timer *tm, int64_t *madds_out, int kind0, void *ext_scratch = nullptr,
-                 size_t ext_bytes = 0) {
+                 size_t ext_bytes = 0, const LevelGrid *pgrid = nullptr,
+                 const TaylorLeaf *tl = nullptr) {
   using V = typename AR::V;
   const int k = sys.k;
   const int64_t nleaves = c.N[k - 1];
@@ -1011,6 +1078,7 @@ int eval_level_t(const SysDev &sys, const CsfView &c, const LevelGrid &grid, dou
   }
 
   for (int f = 0; f < sys.npoly && rc == VX_OK; ++f) {
+    const LevelGrid &pg = pgrid ? pgrid[f] : grid;
     // stage d (1 <= d < k-1) stages its parents' blocks by TMA when the depth has enough
     // nodes to fill the GPU with 128-node CTAs and two parent blocks fit in shared memory
     bool tma[VX_KMAX] = {false};
@@ -1068,10 +1136,10 @@ int eval_level_t(const SysDev &sys, const CsfView &c, const LevelGrid &grid, dou
           if (two)
             k_stage_tma_c<<<(unsigned)(np * G), threads, tma_smem[d], s>>>(
                 st, c.lab[d], c.ptr[d - 1], (const float4 *)in, (float4 *)buf[f][d], oe, on,
-                (int)G, grid.ax[d]);
+                (int)G, pg.ax[d]);
           else
             k_stage_tma<AR><<<(unsigned)(np * G), threads, tma_smem[d], s>>>(
-                st, c.lab[d], c.ptr[d - 1], in, buf[f][d], oe, on, (int)G, grid.ax[d]);
+                st, c.lab[d], c.ptr[d - 1], in, buf[f][d], oe, on, (int)G, pg.ax[d]);
           note_launch();
           VX_LAUNCH_CHECK();
           return VX_OK;
@@ -1100,11 +1168,11 @@ int eval_level_t(const SysDev &sys, const CsfView &c, const LevelGrid &grid, dou
           if (pairs)
             k_stage_c<<<(unsigned)blocks, kThreads, (st.maxlen + 1) * sizeof(int32_t), s>>>(
                 st, c.lab[d], d == 0 ? nullptr : c.par[d], (const float4 *)in, in_estride,
-                in_nstride, (float4 *)buf[f][d], oe, on, c.N[d], nchunk, (int)G, grid.ax[d]);
+                in_nstride, (float4 *)buf[f][d], oe, on, c.N[d], nchunk, (int)G, pg.ax[d]);
           else
             k_stage<AR><<<(unsigned)blocks, kThreads, (st.maxlen + 1) * sizeof(int32_t), s>>>(
                 st, c.lab[d], d == 0 ? nullptr : c.par[d], in, in_estride, in_nstride,
-                buf[f][d], oe, on, c.N[d], nchunk, (int)G, grid.ax[d]);
+                buf[f][d], oe, on, c.N[d], nchunk, (int)G, pg.ax[d]);
           note_launch();
           VX_LAUNCH_CHECK();
           return VX_OK;
@@ -1146,9 +1214,28 @@ int eval_level_t(const SysDev &sys, const CsfView &c, const LevelGrid &grid, dou
         return VX_OK;
       };
       const int arith = std::is_same<AR, A64>::value ? 0 : (std::is_same<AR, A32>::value ? 1 : 2);
-      rc = tuned_launch(tune_key(3, arith, k - 1, nleaves, k > 1 ? c.N[k - 2] : 0,
-                                 sys.p[0].st[k - 1].maxlen, sys.npoly),
-                        std::is_same<AR, A32C>::value ? 2 : 1, s, launch);
+      if (tl) {
+        if constexpr (std::is_same<AR, A64>::value) {
+          AxisGrid gp = grid.ax[k - 1];
+          gp.point = 1;
+          gp.fexact = 0;
+          k_leaf_taylor<<<leaf_grid(nleaves), kThreads, 0, s>>>(
+              A, c.lab[k - 1], k == 1 ? nullptr : c.par[k - 1], nleaves, grid.ax[k - 1], gp, *tl,
+              d_keep);
+          note_launch();
+          if (cudaGetLastError() != cudaSuccess) {
+            set_error("Taylor leaf launch failed");
+            rc = VX_ECUDA;
+          }
+        } else {
+          set_error("the Taylor form is evaluated in binary64 only");
+          rc = VX_EINVAL;
+        }
+      } else {
+        rc = tuned_launch(tune_key(3, arith, k - 1, nleaves, k > 1 ? c.N[k - 2] : 0,
+                                   sys.p[0].st[k - 1].maxlen, sys.npoly),
+                          std::is_same<AR, A32C>::value ? 2 : 1, s, launch);
+      }
       if (rc == VX_OK && tm && tm->on) rc = tm->end();
     }
   }
@@ -1375,6 +1462,35 @@ int eval_forest(int arith, const ForestTree *d_trees, const ForestTree *h_trees,
     default:
       return eval_forest_t<A32C>(d_trees, h_trees, d_off, h_off, S, c, keep, flag, theta, s, madds);
   }
+}
+
+int eval_level_taylor(const SysDev &tsys, const int8_t (*alpha)[VX_KMAX], int m,
+                      const CsfView &c, const LevelGrid &grid, uint8_t *d_keep, int first,
+                      double *d_lo, double *d_hi, cudaStream_t s, Timer *tm, int64_t *madds) {
+  const int k = c.k;
+  TaylorLeaf tl{};
+  tl.na = tsys.npoly;
+  tl.m = m;
+  tl.k = k;
+  tl.first = first;
+  tl.lo = d_lo;
+  tl.hi = d_hi;
+  std::vector<LevelGrid> pg(tsys.npoly, grid);
+  for (int a = 0; a < tsys.npoly; ++a) {
+    int tot = 0;
+    for (int d = 0; d < VX_KMAX; ++d) {
+      tl.alpha[a][d] = d < k ? alpha[a][d] : 0;
+      tot += tl.alpha[a][d];
+    }
+    if (tot < m)
+      for (int d = 0; d < k; ++d) {
+        pg[a].ax[d].point = 1;
+        pg[a].ax[d].fexact = 0;
+      }
+  }
+  for (int d = 0; d < k; ++d) tl.r[d] = 0.5 * grid.ax[d].w;  // exact (dyadic widths)
+  return eval_level_t<A64>(tsys, c, grid, nullptr, nullptr, d_keep, nullptr, 0.f, s, tm, madds,
+                           KK_STAGE0, nullptr, 0, pg.data(), &tl);
 }
 
 int set_autotune(int mode, const char *path) {

@@ -81,6 +81,8 @@ struct AxisGrid {
   // explicit intervals (device arrays, label t -> [xlo[t], xhi[t]]) instead of the regular
   // grid when non-null; fexact is 0 then
   const double *xlo, *xhi;
+  // nonzero: box t stands for its centre, the point interval [c, c], c = lo + (t + 1/2) w
+  int32_t point;
 };
 
 struct LevelGrid {
@@ -162,6 +164,12 @@ struct ForestTree {
 int eval_forest(int arith, const ForestTree *d_trees, const ForestTree *h_trees,
                 const int64_t *d_off, const int64_t *h_off, int S, const CsfView &c,
                 uint8_t *keep, uint8_t *flag, float theta, cudaStream_t s, int64_t *madds);
+// The Taylor form of order m (Def. 3) of one polynomial F on every leaf, in binary64: tsys
+// holds G_a = d^a F / a! for the multi-indices alpha[0..npoly-1] (|a| <= m, lexicographic);
+// keep = 0 in T (first = 1) or keep &= that (first = 0); d_lo/d_hi (nullable) receive T.
+int eval_level_taylor(const SysDev &tsys, const int8_t (*alpha)[VX_KMAX], int m,
+                      const CsfView &c, const LevelGrid &grid, uint8_t *d_keep, int first,
+                      double *d_lo, double *d_hi, cudaStream_t s, Timer *tm, int64_t *madds);
 // Reads (synchronising `s`) and clears the device status word that a kernel sets when a
 // bounded wait gives up; *status != 0 means the last evaluations are not to be trusted.
 int take_device_status(cudaStream_t s, int *status);

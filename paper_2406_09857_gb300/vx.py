@@ -16,7 +16,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "_build", "libvx.so")
 
 OK, EINVAL, ENOMEM, ECAPACITY, EOVERFLOW, ETIMEOUT, ECUDA = 0, -1, -2, -3, -4, -5, -6
-KMAX, MAXPOLY, MAXLEVEL = 4, 8, 24
+KMAX, MAXPOLY, MAXLEVEL = 4, 16, 24
 FP64, FP32_MIDRAD, FP32 = 0, 1, 2
 
 _lib = None
@@ -36,7 +36,8 @@ class Poly(ctypes.Structure):
 class Opts(ctypes.Structure):
     _fields_ = [("mode", ctypes.c_int32), ("fp64_final", ctypes.c_int32),
                 ("fp64_recheck", ctypes.c_int32), ("theta", ctypes.c_float),
-                ("timing", ctypes.c_int32), ("reserved", ctypes.c_int32 * 7)]
+                ("timing", ctypes.c_int32), ("taylor_order", ctypes.c_int32),
+                ("reserved", ctypes.c_int32 * 6)]
 
 
 def lib() -> ctypes.CDLL:
@@ -70,6 +71,7 @@ def lib() -> ctypes.CDLL:
         "vx_csf_eval_level": ([P, P, P, i32, P, P, P, P], i32),
         "vx_csf_eval_level_static": ([P, P, P, i32, P, P, P, P], i32),
         "vx_csf_eval_grid": ([P, P, P, P, P, i32, P, P, P, P], i32),
+        "vx_csf_eval_level_taylor": ([P, P, P, i32, P, P, P, P], i32),
         "vx_csf_subdivide": ([P, P, P, PP], i32),
         "vx_csf_compact": ([P, P, P, P, PP], i32),
         "vx_enclose_system": ([P, P, i32, P, P, PP], i32),
@@ -163,13 +165,15 @@ def _domain(domain) -> np.ndarray:
     return np.ascontiguousarray(np.asarray(domain, dtype=np.float64).reshape(-1))
 
 
-def make_opts(mode=FP64, fp64_final=False, fp64_recheck=False, theta=0.5, timing=False) -> Opts:
+def make_opts(mode=FP64, fp64_final=False, fp64_recheck=False, theta=0.5, timing=False,
+              taylor_order=0) -> Opts:
     o = Opts()
     o.mode = int(mode)
     o.fp64_final = int(bool(fp64_final))
     o.fp64_recheck = int(bool(fp64_recheck))
     o.theta = float(theta)
     o.timing = int(bool(timing))
+    o.taylor_order = int(taylor_order)
     return o
 
 
@@ -289,6 +293,25 @@ def csf_eval_level(system: System, csf: Csf, domain, mode=FP64, values=False, st
 
 
 STATIC_SCRATCH_BYTES = 64 << 20
+
+
+def csf_eval_level_taylor(system: System, csf: Csf, domain, order, values=False, stream=None):
+    """C0 on the Taylor form of the given order (binary64): keep, or (keep, lo, hi)."""
+    import torch
+
+    _, _, N = csf.nodes()
+    n = int(N[-1])
+    keep = torch.empty(max(n, 1), dtype=torch.uint8, device="cuda")
+    lo = hi = None
+    if values:
+        lo = torch.empty((system.npoly, max(n, 1)), dtype=torch.float64, device="cuda")
+        hi = torch.empty_like(lo)
+    _check(lib().vx_csf_eval_level_taylor(system.handle, csf.handle, _np_ptr(_domain(domain)),
+                                          int(order), _ptr(lo), _ptr(hi), _ptr(keep),
+                                          _stream(stream)))
+    if values:
+        return keep[:n], lo[:, :n], hi[:, :n]
+    return keep[:n]
 
 
 def csf_eval_grid(system: System, csf: Csf, xlists, mode=FP64, values=False, stream=None):

@@ -331,12 +331,13 @@ PAPER_TABLE1_S = {
 }
 
 
-def bench_table1(vx, synth, torch, stream):
+def bench_table1(vx, synth, torch, stream, taylor=True):
     """The random-polynomial family of the experiments (Sec. 4.1, Table 1): k = 2, 3, 4,
     total degree 20 or 100 (20 for k = 4), coefficients U[-10, 10], [-2,2]^k; points (k
     equations) and curves (k-1) to boxes of size 2^-8 (depth 10), hypersurfaces to 2^-5
     (depth 7) with exclusion only.  Certified binary32 enclosure time (system resident, CUDA
-    events, best of 2 after a warm-up) and boxes; the paper's seconds as context."""
+    events, best of 2 after a warm-up) and boxes; the paper's seconds as context.  With
+    `taylor`, the same cells with C0 on the order-2 Taylor form in binary64 (one timed run)."""
     out = {}
     for (k, d), paper in PAPER_TABLE1_S.items():
         for kind in ("points", "curves", "hypersurfaces"):
@@ -371,13 +372,29 @@ def bench_table1(vx, synth, torch, stream):
                 else:
                     rr.free()
             st = r.stats()
-            out["k%d-d%d-%s" % (k, d, kind)] = {
+            cell = {
                 "ms": round(best, 3), "depth": depth, "paper_depth": s.depth, "note": note,
                 "boxes": int(st["kept"][-1]),
                 "box_evals": int(st["tested"].sum()),
                 "box_evals_per_s": float(st["tested"].sum()) / (best * 1e-3),
                 "paper_voxelize_s": paper[kind]}
             r.free()
+            if taylor:
+                # C0 on the Taylor form of order 2 (Def. 3), binary64, same depth
+                to = vx.make_opts(vx.FP64, taylor_order=2)
+                vx.enclose_system(sysv, s.domain, min(depth, 3), to, stream=stream).free()
+                e0 = torch.cuda.Event(enable_timing=True)
+                e1 = torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                rt = vx.enclose_system(sysv, s.domain, depth, to, stream=stream)
+                e1.record(stream)
+                e1.synchronize()
+                tst = rt.stats()
+                cell["taylor2_fp64"] = {"ms": round(e0.elapsed_time(e1), 3),
+                                        "boxes": int(tst["kept"][-1]),
+                                        "box_evals": int(tst["tested"].sum())}
+                rt.free()
+            out["k%d-d%d-%s" % (k, d, kind)] = cell
             sysv.free()
     return out
 

@@ -63,10 +63,16 @@ def lib():
         L.orc_dense_powerform.argtypes = [P, P, i64, P, i32, P, i64, P, P]
         L.orc_taylor_boxes.argtypes = sysargs + [P, i32, i32, P, i64, P, P, P]
         L.orc_enclose_taylor.argtypes = sysargs + [P, i32, i32, ctypes.POINTER(P)]
+        L.orc_c1_boxes.argtypes = sysargs + [P, i32, i32, i32, P, i64, P]
+        L.orc_enclose_c1.argtypes = sysargs + [P, i32, i32, i32, i32, ctypes.POINTER(P)]
+        L.orc_result_inc_count.argtypes = [P]
+        L.orc_result_inc_count.restype = i64
+        L.orc_result_inc_copy.argtypes = [P, P, P, P]
         for f in ("orc_eval_csf", "orc_eval_boxes", "orc_eval_grid", "orc_csf", "orc_enclose",
                   "orc_enclose_from",
                   "orc_brute_force", "orc_eval_grid_complex", "orc_domain_exact",
-                  "orc_dense_powerform", "orc_taylor_boxes", "orc_enclose_taylor"):
+                  "orc_dense_powerform", "orc_taylor_boxes", "orc_enclose_taylor",
+                  "orc_c1_boxes", "orc_enclose_c1"):
             getattr(L, f).restype = i32
         _lib = L
     return _lib
@@ -228,9 +234,15 @@ def _result(res, k, depth):
         nodes = np.empty((depth + 1, k), dtype=np.int64)
         work = np.empty(depth + 1, dtype=np.int64)
         L.orc_result_copy(res, _p(tup), _p(tested), _p(kept), _p(nodes), _p(work))
+        ni = L.orc_result_inc_count(res)
+        inc_levels = np.empty(ni, dtype=np.int32)
+        inc_tuples = np.empty((ni, k), dtype=np.int32)
+        included = np.empty(depth + 1, dtype=np.int64)
+        L.orc_result_inc_copy(res, _p(inc_levels), _p(inc_tuples), _p(included))
     finally:
         L.orc_result_free(res)
-    return {"tuples": tup, "tested": tested, "kept": kept, "nodes": nodes, "work": work}
+    return {"tuples": tup, "tested": tested, "kept": kept, "nodes": nodes, "work": work,
+            "inc_levels": inc_levels, "inc_tuples": inc_tuples, "included": included}
 
 
 def brute_force(polys, domain, level):
@@ -310,4 +322,36 @@ def enclose_taylor(polys, domain, depth, order):
     res = ctypes.c_void_p()
     _check(lib().orc_enclose_taylor(k, npoly, _p(off), _p(E), _p(C), _p(dom), int(depth),
                                     int(order), ctypes.byref(res)), "orc_enclose_taylor")
+    return _result(res, k, depth)
+
+
+C1_TAYLOR = 1
+C1_VERTEX = 2
+
+
+def c1_boxes(poly, domain, level, kind, tuples, order=0):
+    """Inclusion criterion C1 (Sec. 3.2) of one polynomial on each box: 1 where certified
+    (kind C1_VERTEX: certified opposite signs at two vertices; C1_TAYLOR: the Taylor form of
+    the given order >= 2 at the vertices extremal for its linear part)."""
+    k, npoly, off, E, C = pack([poly])
+    t = _tuples(tuples, k)
+    n = t.shape[0]
+    dom = np.ascontiguousarray(np.asarray(domain, dtype=np.float64).reshape(-1))
+    inc = np.empty(n, dtype=np.uint8)
+    _check(lib().orc_c1_boxes(k, npoly, _p(off), _p(E), _p(C), _p(dom), int(level), int(kind),
+                              int(order), _p(t), n, _p(inc)), "orc_c1_boxes")
+    return inc
+
+
+def enclose_c1(poly, domain, depth, kind, c1_level, taylor_order=0):
+    """Algorithm 3 with C0 (interval Horner, or the Taylor form of `taylor_order`) and C1 of
+    `kind` from level `c1_level` on; stops when no box is left or after level `depth`.
+    inc_levels / inc_tuples: the certified boxes (by level, then lexicographic); tuples: the
+    boxes of level `depth` neither excluded nor certified."""
+    k, npoly, off, E, C = pack([poly])
+    dom = np.ascontiguousarray(np.asarray(domain, dtype=np.float64).reshape(-1))
+    res = ctypes.c_void_p()
+    _check(lib().orc_enclose_c1(k, npoly, _p(off), _p(E), _p(C), _p(dom), int(depth),
+                                int(taylor_order), int(kind), int(c1_level), ctypes.byref(res)),
+           "orc_enclose_c1")
     return _result(res, k, depth)

@@ -20,6 +20,10 @@
  *   orc_dense_powerform()  the mode-by-mode midpoint-radius enclosure on a tensor grid
  *                    (Property 1's contractions, one variable at a time), the reference for
  *                    the dense tensor-core level.
+ *   orc_taylor_boxes(), orc_enclose_taylor()  C0 on the Taylor form of order m (Def. 3).
+ *   orc_c1_boxes(), orc_enclose_c1()  the inclusion criterion C1 for one equation (Sec. 3.2:
+ *                    vertex signs, or the Taylor form at the two vertices extremal for its
+ *                    linear part) and Algorithm 3 with both criteria.
  *
  * Readings of the paper taken here (where it is silent or ambiguous):
  *   - Rounding (Sec. 3.2 only gives [a,b]+[c,d]=[a+c,b+d]): every lower endpoint is
@@ -36,7 +40,13 @@
  *     w_i = (hi_i - lo_i) / 2^l; the left end is rounded down and the right end up (both
  *     exact on dyadic domains, which are the only ones orc_domain_exact() accepts).
  *   - Algorithm 3 without an inclusion test stops by depth: levels 0..depth are tested
- *     and the survivors of level `depth` are returned.
+ *     and the survivors of level `depth` are returned.  With C1 it stops when no box is
+ *     left or after level `depth` (boxes that touch the zero set only where F has no sign
+ *     change, e.g. at a vertex, are never certified); "size < threshold" is a first level
+ *     c1_level from which C1 is applied.
+ *   - The Taylor C1 picks V_max by the sign of each first-derivative interval's midpoint
+ *     (lo >= -hi counts as >= 0) and tests only the orientation the paper states (lower
+ *     bound at V_max > 0, upper bound at V_min < 0).
  *
  * The rounding mode is set to FE_DOWNWARD at the entry of each exported function and
  * restored on exit; an upward-rounded result is formed as -RD(-x), which is the same
@@ -696,6 +706,11 @@ typedef struct orc_result {
   int64_t *kept;    /* [depth+1] */
   int64_t *nodes;   /* [(depth+1)*k] N_j(S_l) */
   int64_t *work;    /* [depth+1] interval multiply-adds */
+  /* with an inclusion criterion C1: the boxes it certified, ordered by level, then lex */
+  int64_t n_inc;
+  int32_t *inc_levels; /* [n_inc] */
+  int32_t *inc_tuples; /* [n_inc][k] indices at the box's own level */
+  int64_t *included;   /* [depth+1] boxes certified at level l */
 } orc_result;
 
 static int g_cmp_k;
@@ -713,6 +728,9 @@ void orc_result_free(orc_result *R) {
   free(R->kept);
   free(R->nodes);
   free(R->work);
+  free(R->inc_levels);
+  free(R->inc_tuples);
+  free(R->included);
   free(R);
 }
 
@@ -848,6 +866,142 @@ static ivl taylor_box(const taylor_sys *T, int k, int m, const boxsrc *B, const 
   return acc;
 }
 
+/* ------------------------------------------------------------------------------------ */
+/* Inclusion criterion C1 for one equation (Sec. 3.2, "Inclusion Criterion").  True means */
+/* F has a zero in the closed box B: two points of B where F has certified opposite signs */
+/* (B is connected).                                                                        */
+/*  - vertex test: F at each of the 2^k vertices by nested interval Horner on the point   */
+/*    interval of the vertex; true iff one vertex has lo > 0 and another hi < 0;            */
+/*  - Taylor test (order m >= 2): with g_i = G_{e_i}(c) (the centre values of the first   */
+/*    derivatives), V_max = c + s r with s_i = +1 if g_i's midpoint is >= 0 (lo >= -hi),    */
+/*    else -1, and V_min = c - s r, the vertices where the linear part of T_m is largest and */
+/*    smallest; F(V) lies in sum_a V_a (V - c)^a (the Taylor form at the point V, the       */
+/*    factors (s_i r_i)^{a_i} as point intervals multiplied by interval products); true iff */
+/*    the lower bound at V_max is > 0 and the upper bound at V_min is < 0.                   */
+/* ------------------------------------------------------------------------------------ */
+#define ORC_C1_TAYLOR 1
+#define ORC_C1_VERTEX 2
+
+/* nested Horner of a polynomial with interval coefficients on explicit intervals X[k] */
+static ivl eval_poly_at(const plan *P, const double *clo, const double *chi, const ivl *X,
+                        int64_t *work, int *rc) {
+  ivl z = {0.0, 0.0};
+  if (P->nterms == 0) return z;
+  ivl *cur = (ivl *)malloc(sizeof(ivl) * P->nterms);
+  ivl *nxt = (ivl *)malloc(sizeof(ivl) * P->nterms);
+  if (!cur || !nxt) {
+    free(cur);
+    free(nxt);
+    *rc = ORC_ENOMEM;
+    return z;
+  }
+  for (int i = 0; i < P->nterms; ++i) {
+    cur[i].lo = clo[i];
+    cur[i].hi = chi[i];
+  }
+  for (int j = 0; j < P->k; ++j) {
+    run_stage(&P->st[j], cur, X[j], nxt, work);
+    ivl *t = cur;
+    cur = nxt;
+    nxt = t;
+  }
+  z = cur[0];
+  free(cur);
+  free(nxt);
+  return z;
+}
+
+static int c1_vertex_box(const plan *P, const double *coefs, int k, const boxsrc *B,
+                         const int32_t *tup, int64_t *work, int *rc) {
+  int pos = 0, neg = 0;
+  for (int v = 0; v < (1 << k) && *rc == ORC_OK; ++v) {
+    ivl X[ORC_KMAX];
+    for (int i = 0; i < k; ++i) {
+      ivl b = box_ivl(B, i, tup[i]);
+      double x = ((v >> (k - 1 - i)) & 1) ? b.hi : b.lo;
+      X[i].lo = X[i].hi = x;
+    }
+    ivl y = eval_poly_at(P, coefs, coefs, X, work, rc);
+    if (y.lo > 0.0) pos = 1;
+    if (y.hi < 0.0) neg = 1;
+  }
+  return pos && neg;
+}
+
+static int taylor_c1_box(const taylor_sys *T, int k, int m, const boxsrc *B, const int32_t *tup,
+                         int64_t *work, int *rc) {
+  double r[ORC_KMAX];
+  ivl V[64];
+  for (int i = 0; i < k; ++i) {
+    ivl X = box_ivl(B, i, tup[i]);
+    r[i] = ru_mul(ru_add(X.hi, -X.lo), 0.5);
+  }
+  for (int a = 0; a < T->na; ++a) {
+    int tot = 0;
+    for (int i = 0; i < k; ++i) tot += T->alpha[a][i];
+    V[a] = eval_poly_box_ivl(&T->pl[a], T->clo[a], T->chi[a], B, tup, tot < m, work, rc);
+  }
+  int s[ORC_KMAX];
+  for (int i = 0; i < k; ++i) {
+    int e = -1;
+    for (int a = 0; a < T->na && e < 0; ++a) {
+      int ok = 1;
+      for (int j = 0; j < k; ++j) ok = ok && T->alpha[a][j] == (j == i ? 1 : 0);
+      if (ok) e = a;
+    }
+    s[i] = (V[e].lo >= -V[e].hi) ? 1 : -1;
+  }
+  ivl at[2];
+  for (int side = 0; side < 2; ++side) { /* 0: V_max, 1: V_min */
+    ivl acc = {0.0, 0.0};
+    for (int a = 0; a < T->na; ++a) {
+      ivl P = {1.0, 1.0};
+      for (int i = 0; i < k; ++i) {
+        double x = (side == 0 ? s[i] : -s[i]) > 0 ? r[i] : -r[i];
+        ivl q = {x, x};
+        for (int e = 0; e < T->alpha[a][i]; ++e) P = i_mul(P, q);
+      }
+      acc = i_add(acc, i_mul(V[a], P));
+    }
+    at[side] = acc;
+  }
+  return at[0].lo > 0.0 && at[1].hi < 0.0;
+}
+
+/* C1 of one polynomial (npoly must be 1) on boxes tuples[n][k] of a level: inc[i] = 1 when
+ * certified.  kind ORC_C1_VERTEX or ORC_C1_TAYLOR (order m >= 2). */
+int orc_c1_boxes(int k, int npoly, const int64_t *term_off, const int32_t *exps,
+                 const double *coefs, const double *domain, int level, int kind, int m,
+                 const int32_t *tuples, int64_t n, uint8_t *inc) {
+  int old = fegetround();
+  int rc = check_system(k, npoly, term_off);
+  if (rc != ORC_OK) return rc;
+  if (npoly != 1 || (kind != ORC_C1_VERTEX && kind != ORC_C1_TAYLOR)) return ORC_EINVAL;
+  if (kind == ORC_C1_TAYLOR && (m < 2 || m > 8)) return ORC_EINVAL;
+  fesetround(FE_DOWNWARD);
+  boxsrc B = {domain, level, 0, 0, 0};
+  int64_t w = 0;
+  if (kind == ORC_C1_VERTEX) {
+    plan P;
+    rc = build_plans(&P, k, 1, term_off, exps, coefs);
+    if (rc == ORC_OK) {
+      for (int64_t i = 0; i < n && rc == ORC_OK; ++i)
+        inc[i] = (uint8_t)c1_vertex_box(&P, coefs, k, &B, tuples + i * k, &w, &rc);
+      free_plans(&P, 1);
+    }
+  } else {
+    taylor_sys T;
+    rc = taylor_build(&T, k, m, (int)(term_off[1] - term_off[0]), exps, coefs);
+    if (rc == ORC_OK) {
+      for (int64_t i = 0; i < n && rc == ORC_OK; ++i)
+        inc[i] = (uint8_t)taylor_c1_box(&T, k, m, &B, tuples + i * k, &w, &rc);
+      taylor_free(&T);
+    }
+  }
+  fesetround(old);
+  return rc;
+}
+
 /* The Taylor form of order m of each polynomial on each box (lo/hi [npoly][n]) and the C0
  * decision (keep = 0 in every polynomial's form). */
 int orc_taylor_boxes(int k, int npoly, const int64_t *term_off, const int32_t *exps,
@@ -886,14 +1040,14 @@ int orc_enclose(int k, int npoly, const int64_t *term_off, const int32_t *exps, 
 
 static int enclose_core(int k, int npoly, const int64_t *term_off, const int32_t *exps,
                         const double *coefs, const double *domain, int start_level,
-                        const int32_t *start, int64_t n0, int depth, int taylor_m,
-                        orc_result **out);
+                        const int32_t *start, int64_t n0, int depth, int taylor_m, int c1_kind,
+                        int c1_level, orc_result **out);
 
 int orc_enclose_from(int k, int npoly, const int64_t *term_off, const int32_t *exps,
                      const double *coefs, const double *domain, int start_level,
                      const int32_t *start, int64_t n0, int depth, orc_result **out) {
-  return enclose_core(k, npoly, term_off, exps, coefs, domain, start_level, start, n0, depth, 0,
-                      out);
+  return enclose_core(k, npoly, term_off, exps, coefs, domain, start_level, start, n0, depth, 0, 0,
+                      0, out);
 }
 
 /* Algorithm 3 with C0 on the Taylor form of order m (Def. 3) instead of interval Horner. */
@@ -902,13 +1056,32 @@ int orc_enclose_taylor(int k, int npoly, const int64_t *term_off, const int32_t 
                        orc_result **out) {
   int32_t root[ORC_KMAX] = {0};
   if (m < 1 || m > 8) return ORC_EINVAL;
-  return enclose_core(k, npoly, term_off, exps, coefs, domain, 0, root, 1, depth, m, out);
+  return enclose_core(k, npoly, term_off, exps, coefs, domain, 0, root, 1, depth, m, 0, 0, out);
+}
+
+/* Algorithm 3 with both criteria, for one equation: at every level the boxes C0 excludes are
+ * dropped; from level c1_level on (the boxes are then below the size threshold) the boxes C1
+ * certifies go to the result (inc_levels, inc_tuples) and are not bisected; the loop ends when
+ * no box is left or after level `depth`, whose remaining boxes (neither excluded nor
+ * certified) are the result's `tuples`.  C0 is interval Horner (taylor_m = 0) or the Taylor
+ * form of order taylor_m; C1 is the vertex test or the Taylor test (which needs taylor_m >= 2
+ * and uses the same form). */
+int orc_enclose_c1(int k, int npoly, const int64_t *term_off, const int32_t *exps,
+                   const double *coefs, const double *domain, int depth, int taylor_m,
+                   int c1_kind, int c1_level, orc_result **out) {
+  int32_t root[ORC_KMAX] = {0};
+  *out = 0;
+  if (npoly != 1 || taylor_m < 0 || taylor_m > 8 || c1_level < 0) return ORC_EINVAL;
+  if (c1_kind != ORC_C1_VERTEX && c1_kind != ORC_C1_TAYLOR) return ORC_EINVAL;
+  if (c1_kind == ORC_C1_TAYLOR && taylor_m < 2) return ORC_EINVAL;
+  return enclose_core(k, npoly, term_off, exps, coefs, domain, 0, root, 1, depth, taylor_m,
+                      c1_kind, c1_level, out);
 }
 
 static int enclose_core(int k, int npoly, const int64_t *term_off, const int32_t *exps,
                         const double *coefs, const double *domain, int start_level,
-                        const int32_t *start, int64_t n0, int depth, int taylor_m,
-                        orc_result **out) {
+                        const int32_t *start, int64_t n0, int depth, int taylor_m, int c1_kind,
+                        int c1_level, orc_result **out) {
   int old = fegetround();
   int rc = check_system(k, npoly, term_off);
   *out = 0;
@@ -929,6 +1102,8 @@ static int enclose_core(int k, int npoly, const int64_t *term_off, const int32_t
   R->kept = (int64_t *)calloc(depth + 1, sizeof(int64_t));
   R->nodes = (int64_t *)calloc((size_t)(depth + 1) * k, sizeof(int64_t));
   R->work = (int64_t *)calloc(depth + 1, sizeof(int64_t));
+  R->included = (int64_t *)calloc(depth + 1, sizeof(int64_t));
+  int64_t inc_cap = 0;
   rc = build_plans(plans, k, npoly, term_off, exps, coefs);
   if (rc != ORC_OK) {
     orc_result_free(R);
@@ -981,6 +1156,50 @@ static int enclose_core(int k, int npoly, const int64_t *term_off, const int32_t
     free(keep);
     R->kept[l] = m;
     n = m;
+    if (c1_kind && l >= c1_level && n > 0) {
+      /* R <- R + the boxes of S satisfying C1; S <- the others */
+      uint8_t *inc = (uint8_t *)malloc((size_t)n);
+      taylor_sys TC;
+      int built = 0;
+      if (!inc) rc = ORC_ENOMEM;
+      if (rc == ORC_OK && c1_kind == ORC_C1_TAYLOR) {
+        rc = taylor_build(&TC, k, taylor_m, (int)(term_off[1] - term_off[0]), exps, coefs);
+        built = rc == ORC_OK;
+      }
+      for (int64_t i = 0; rc == ORC_OK && i < n; ++i)
+        inc[i] = (uint8_t)(c1_kind == ORC_C1_TAYLOR
+                               ? taylor_c1_box(&TC, k, taylor_m, &B, S + i * k, &R->work[l], &rc)
+                               : c1_vertex_box(&plans[0], coefs, k, &B, S + i * k, &R->work[l],
+                                               &rc));
+      if (built) taylor_free(&TC);
+      int64_t q = 0;
+      for (int64_t i = 0; rc == ORC_OK && i < n; ++i) {
+        if (!inc[i]) {
+          memmove(S + q * k, S + i * k, sizeof(int32_t) * k);
+          ++q;
+          continue;
+        }
+        if (R->n_inc == inc_cap) {
+          inc_cap = inc_cap ? 2 * inc_cap : 1024;
+          int32_t *a = (int32_t *)realloc(R->inc_levels, sizeof(int32_t) * (size_t)inc_cap);
+          if (a) R->inc_levels = a;
+          int32_t *b = (int32_t *)realloc(R->inc_tuples, sizeof(int32_t) * (size_t)inc_cap * k);
+          if (b) R->inc_tuples = b;
+          if (!a || !b) {
+            rc = ORC_ENOMEM;
+            break;
+          }
+        }
+        R->inc_levels[R->n_inc] = l;
+        memcpy(R->inc_tuples + R->n_inc * k, S + i * k, sizeof(int32_t) * k);
+        ++R->n_inc;
+        ++R->included[l];
+      }
+      free(inc);
+      if (rc != ORC_OK) break;
+      n = q;
+      if (n == 0) break;
+    }
     if (l == depth) break;
     /* S <- the 2^k boxes bisected from each box of S, sorted */
     int64_t nc = n << k;
@@ -1020,6 +1239,16 @@ void orc_result_copy(const orc_result *R, int32_t *tuples, int64_t *tested, int6
   if (kept) memcpy(kept, R->kept, sizeof(int64_t) * (R->depth + 1));
   if (nodes) memcpy(nodes, R->nodes, sizeof(int64_t) * (size_t)(R->depth + 1) * R->k);
   if (work) memcpy(work, R->work, sizeof(int64_t) * (R->depth + 1));
+}
+
+int64_t orc_result_inc_count(const orc_result *R) { return R->n_inc; }
+
+void orc_result_inc_copy(const orc_result *R, int32_t *levels, int32_t *tuples,
+                         int64_t *included) {
+  if (levels && R->n_inc) memcpy(levels, R->inc_levels, sizeof(int32_t) * (size_t)R->n_inc);
+  if (tuples && R->n_inc)
+    memcpy(tuples, R->inc_tuples, sizeof(int32_t) * (size_t)R->n_inc * R->k);
+  if (included) memcpy(included, R->included, sizeof(int64_t) * (R->depth + 1));
 }
 
 /* Every box of the level-`level` grid tested independently with nested Horner; keep is in

@@ -59,6 +59,15 @@ extern "C" {
                           * binary32, the others are re-evaluated in VX_FP64, so every keep
                           * decision equals the VX_FP64 one */
 
+/* Inclusion criteria C1 for one equation (Sec. 3.2, "Inclusion Criterion"); a box C1
+ * certifies holds a zero of F (F has certified opposite signs at two of its points). */
+#define VX_C1_TAYLOR 1 /* the Taylor form of order m >= 2 at the vertices V_max, V_min where its
+                        * linear part is largest / smallest (s_i = sign of the midpoint of
+                        * G_{e_i}(c), lo >= -hi counting as +): lower bound at V_max > 0 and
+                        * upper bound at V_min < 0 */
+#define VX_C1_VERTEX 2 /* F at the 2^k vertices (Algorithm 2 on point intervals): one vertex
+                        * certified > 0 and another < 0 */
+
 /* One polynomial: nterms monomials coefs[t] * prod_i x_i^exps[t*nvars+i] (Sec. 2.1,
  * "Representing a Multivariate Polynomial").  Host memory, borrowed for the duration of the
  * call.  Exponents >= 0, no monomial twice, coefficients finite. */
@@ -87,7 +96,14 @@ typedef struct {
   int32_t taylor_order; /* 0: C0 on nested interval Horner (Algorithm 2); m >= 1: C0 on the
                          * Taylor form of order m (Def. 3), VX_FP64 only; the number of
                          * multi-indices |a| <= m (C(m+k, k)) must not exceed VX_MAXPOLY */
-  int32_t reserved[6];
+  int32_t c1;           /* 0, VX_C1_TAYLOR (needs taylor_order >= 2) or VX_C1_VERTEX: Algorithm 3
+                         * with the inclusion criterion, one equation, VX_FP64 only.  From level
+                         * c1_level on (the boxes below the size threshold) the boxes C1
+                         * certifies leave the subdivision and are returned with their level
+                         * (vx_result_included); the loop ends when no box is left or after
+                         * level `depth`, whose remaining boxes are vx_result_boxes */
+  int32_t c1_level;
+  int32_t reserved[4];
 } vx_opts;
 
 /* Thread-local message of the last failed call on this thread ("" if none). */
@@ -163,6 +179,12 @@ int vx_csf_eval_level(const vx_system *sys, const vx_csf *csf, const double *h_d
 int vx_csf_eval_level_taylor(const vx_system *sys, const vx_csf *csf, const double *h_domain,
                              int32_t order, double *d_lo, double *d_hi, uint8_t *d_keep,
                              void *stream);
+
+/* The inclusion criterion C1 (kind VX_C1_TAYLOR with `order` >= 2, or VX_C1_VERTEX; see
+ * their definitions) of the system's one polynomial on every leaf box of the level:
+ * d_inc[N_k] (device, caller-owned) = 1 where certified.  Binary64.  Synchronises `stream`. */
+int vx_csf_c1(const vx_system *sys, const vx_csf *csf, const double *h_domain, int32_t kind,
+              int32_t order, uint8_t *d_inc, void *stream);
 
 /* Algorithm 2 takes the intervals of x_1 as a list (Sec. 2.2); this is vx_csf_eval_level with
  * an explicit interval list per axis instead of the regular grid: a depth-j node labelled t
@@ -310,6 +332,11 @@ int vx_dense_level(const vx_dense_plan *plan, const vx_opts *opts, uint8_t *d_ke
 /* The surviving boxes: *n tuples of k int32 grid indices at level `depth`, lexicographic,
  * in host memory owned by the result (copied from the device on first call). */
 int vx_result_boxes(vx_result *res, int64_t *n, const int32_t **h_tuples);
+/* With opts.c1: the boxes C1 certified, *n of them, ordered by level, then lexicographic:
+ * h_levels[i] the level of box i and h_tuples[i*k ..] its k grid indices at that level; host
+ * memory owned by the result (copied from the device on first call). */
+int vx_result_included(vx_result *res, int64_t *n, const int32_t **h_levels,
+                       const int32_t **h_tuples);
 /* The survivors as a device CSF owned by the result (valid until vx_result_free). */
 int vx_result_csf(const vx_result *res, const vx_csf **csf);
 /* Per-level statistics, levels 0..depth: h_tested[l] = |S_l| boxes evaluated, h_kept[l]

@@ -510,6 +510,10 @@ struct vx_result {
   int32_t *htup = nullptr;
   size_t hcap = 0;       // bytes of the buffer
   int64_t hcount = -1;   // boxes copied (-1: not yet)
+  // with C1: the certified boxes of each level (device CSFs), and their host copy
+  std::vector<std::pair<int, CsfObj>> incl;
+  std::vector<int32_t> hinc_lev, hinc_tup;
+  int64_t hinc_count = -1;
 };
 
 // ---------------------------------------------------------------------------------------
@@ -1100,8 +1104,17 @@ static int taylor_sets(const vx_system *csys, int m, cudaStream_t s,
 
 // One level with C0 on the Taylor form of order m: keep = 0 in every polynomial's form.
 static int eval_taylor_level(const vx_system *sys, const CsfView &c, const LevelGrid &g, int m,
-                             double *d_lo, double *d_hi, uint8_t *keep, cudaStream_t s,
-                             Timer *tm, int64_t *madds) {
+                             double *d_lo, double *d_hi, uint8_t *keep, uint8_t *inc,
+                             cudaStream_t s, Timer *tm, int64_t *madds) {
+  for (int d = 0; d < c.k; ++d)  // the centres are points of the next level's grid
+    if (!grid_exact(g.ax[d].lo, 0.5 * g.ax[d].w, (int64_t)2 << c.level, 53, -1074)) {
+      set_error("axis %d: the box centres of level %d are not binary64 numbers", d, c.level);
+      return VX_EINVAL;
+    }
+  if (inc && sys->dev.npoly != 1) {
+    set_error("C1 is a test for one equation (the system has %d)", sys->dev.npoly);
+    return VX_EINVAL;
+  }
   std::vector<vx_system::TaylorSet> *sets = nullptr;
   VX_CHECK(taylor_sets(sys, m, s, &sets));
   const int64_t n = c.N[c.k - 1];
@@ -1114,7 +1127,7 @@ static int eval_taylor_level(const vx_system *sys, const CsfView &c, const Level
     int64_t w = 0;
     VX_CHECK(eval_level_taylor(ts.sys->dev, (const int8_t(*)[VX_KMAX])al.data(), m, c, g, keep,
                                f == 0, d_lo ? d_lo + (int64_t)f * n : nullptr,
-                               d_hi ? d_hi + (int64_t)f * n : nullptr, s, tm, &w));
+                               d_hi ? d_hi + (int64_t)f * n : nullptr, inc, s, tm, &w));
     *madds += w;
   }
   return VX_OK;
@@ -1133,7 +1146,8 @@ int vx_csf_eval_level_taylor(const vx_system *sys, const vx_csf *c, const double
   cudaStream_t s = as_stream(stream);
   if (c->o.v.N[c->o.v.k - 1] == 0) return VX_OK;
   int64_t w = 0;
-  VX_CHECK(eval_taylor_level(sys, c->o.v, g, order, d_lo, d_hi, d_keep, s, nullptr, &w));
+  VX_CHECK(eval_taylor_level(sys, c->o.v, g, order, d_lo, d_hi, d_keep, nullptr, s, nullptr,
+                             &w));
   int st = 0;
   VX_CHECK(take_device_status(s, &st));
   if (st) {
@@ -1141,6 +1155,43 @@ int vx_csf_eval_level_taylor(const vx_system *sys, const vx_csf *c, const double
     return VX_ETIMEOUT;
   }
   return VX_OK;
+}
+
+int vx_csf_c1(const vx_system *sys, const vx_csf *c, const double *h_domain, int32_t kind,
+              int32_t order, uint8_t *d_inc, void *stream) {
+  clear_error();
+  if (!sys || !c || !d_inc || c->o.v.k != sys->dev.k ||
+      (kind != VX_C1_TAYLOR && kind != VX_C1_VERTEX) || (kind == VX_C1_TAYLOR && order < 2)) {
+    set_error("vx_csf_c1: bad arguments");
+    return VX_EINVAL;
+  }
+  if (sys->dev.npoly != 1) {
+    set_error("vx_csf_c1: C1 is a test for one equation (the system has %d)", sys->dev.npoly);
+    return VX_EINVAL;
+  }
+  LevelGrid g;
+  VX_CHECK(make_grid(c->o.v.k, h_domain, c->o.v.level, &g));
+  cudaStream_t s = as_stream(stream);
+  const int64_t n = c->o.v.N[c->o.v.k - 1];
+  if (n == 0) return VX_OK;
+  int64_t w = 0;
+  int rc = VX_OK;
+  if (kind == VX_C1_VERTEX) {
+    rc = eval_c1_vertex(sys->dev, c->o.v, g, d_inc, s, nullptr, &w);
+  } else {
+    uint8_t *keep = nullptr;
+    rc = dmalloc((void **)&keep, (size_t)n, s);
+    if (rc == VX_OK) rc = eval_taylor_level(sys, c->o.v, g, order, nullptr, nullptr, keep, d_inc,
+                                            s, nullptr, &w);
+    dfree(keep, s);
+  }
+  int st = 0;
+  if (rc == VX_OK) rc = take_device_status(s, &st);
+  if (rc == VX_OK && st) {
+    set_error("vx_csf_c1: a bounded device wait gave up");
+    rc = VX_ETIMEOUT;
+  }
+  return rc;
 }
 
 int vx_csf_eval_grid(const vx_system *sys, const vx_csf *c, const double *const *d_xlo,
@@ -1268,6 +1319,18 @@ static int csf_copy(const CsfObj &src, cudaStream_t s, CsfObj *dst) {
   return VX_OK;
 }
 
+// With C1: inc &= keep (the certified boxes among the C0 survivors), keep &= !inc (the boxes
+// that go on being bisected).
+static __global__ void k_c1_split(uint8_t *__restrict__ keep, uint8_t *__restrict__ inc,
+                                  int64_t n) {
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
+    const uint8_t kp = keep[i], c = inc[i] & kp;
+    inc[i] = c;
+    keep[i] = kp & (uint8_t)(c ^ 1);
+  }
+}
+
 static int enclose_impl(const vx_system *sys, const double *dom, int depth, const vx_opts *o,
                         cudaStream_t s, vx_result *R, const CsfObj *start) {
   const int k = sys->dev.k;
@@ -1290,6 +1353,18 @@ static int enclose_impl(const vx_system *sys, const double *dom, int depth, cons
   if (depth < 0 || depth > VX_MAXLEVEL) {
     set_error("vx_enclose: depth %d outside [0, %d]", depth, VX_MAXLEVEL);
     return VX_EINVAL;
+  }
+  if (opts.c1 != 0) {
+    if (opts.c1 != VX_C1_TAYLOR && opts.c1 != VX_C1_VERTEX) {
+      set_error("vx_enclose: unknown inclusion criterion %d", opts.c1);
+      return VX_EINVAL;
+    }
+    if (opts.mode != VX_FP64 || sys->dev.npoly != 1 || opts.c1_level < 0 ||
+        (opts.c1 == VX_C1_TAYLOR && opts.taylor_order < 2)) {
+      set_error("vx_enclose: C1 needs one equation, VX_FP64, c1_level >= 0 and, for "
+                "VX_C1_TAYLOR, taylor_order >= 2");
+      return VX_EINVAL;
+    }
   }
   LevelGrid g;
   VX_CHECK(make_grid(k, dom, depth, &g));  // the finest grid exact => every coarser one too
@@ -1330,13 +1405,15 @@ static int enclose_impl(const vx_system *sys, const double *dom, int depth, cons
     for (int d = 0; d < k; ++d) R->nodes[(size_t)l * k + d] = cur.v.N[d];
     int mode = opts.mode;
     if (mode == VX_FP32_MIDRAD && opts.fp64_final && l == depth) mode = VX_FP64;
-    uint8_t *keep = nullptr;
+    const bool c1_here = opts.c1 != 0 && l >= opts.c1_level && n > 0;
+    uint8_t *keep = nullptr, *inc = nullptr;
     rc = dmalloc((void **)&keep, (size_t)std::max<int64_t>(n, 1), s);
+    if (rc == VX_OK && c1_here) rc = dmalloc((void **)&inc, (size_t)n, s);
     if (rc == VX_OK) {
       int64_t w = 0, nr = 0;
       if (opts.taylor_order > 0)
         rc = n > 0 ? eval_taylor_level(sys, cur.v, g, opts.taylor_order, nullptr, nullptr, keep,
-                                       s, tm, &w)
+                                       opts.c1 == VX_C1_TAYLOR ? inc : nullptr, s, tm, &w)
                    : VX_OK;
       else
         rc = eval_decide(sys->dev, cur.v, g, mode, opts.fp64_recheck != 0, theta, nullptr,
@@ -1350,21 +1427,68 @@ static int enclose_impl(const vx_system *sys, const double *dom, int depth, cons
         rc = VX_ETIMEOUT;
       }
     }
+    int64_t included = 0;
+    if (rc == VX_OK && c1_here) {
+      // Algorithm 3's inclusion step: the C0 survivors that C1 certifies leave S
+      int64_t nc = n;
+      if (opts.c1 == VX_C1_VERTEX) {  // the corners are evaluated on the survivors only
+        CsfObj surv;
+        rc = csf_prune(cur.v, keep, 0, nullptr, s, &surv, tm);
+        if (rc == VX_OK) {
+          csf_release(&cur);
+          cur = surv;
+          nc = cur.v.N[k - 1];
+          if (nc > 0) {
+            const cudaError_t e = cudaMemsetAsync(keep, 1, (size_t)nc, s);
+            if (e != cudaSuccess) {
+              set_error("enclose: %s", cudaGetErrorString(e));
+              rc = VX_ECUDA;
+            }
+          }
+          if (rc == VX_OK && nc > 0) {
+            int64_t w = 0;
+            rc = eval_c1_vertex(sys->dev, cur.v, g, inc, s, tm, &w);
+            R->madds[l] += w;
+          }
+        }
+      }
+      if (rc == VX_OK && nc > 0) {
+        k_c1_split<<<(int)std::min<int64_t>((nc + 255) / 256, 4096), 256, 0, s>>>(keep, inc, nc);
+        note_launch();
+        CsfObj ic;
+        rc = csf_prune(cur.v, inc, 0, nullptr, s, &ic, tm);
+        if (rc == VX_OK) {
+          included = ic.v.N[k - 1];
+          if (included > 0) {
+            try {
+              R->incl.emplace_back(l, ic);
+            } catch (...) {
+              csf_release(&ic);
+              set_error("enclose: out of host memory");
+              rc = VX_ENOMEM;
+            }
+          } else {
+            csf_release(&ic);
+          }
+        }
+      }
+    }
     if (rc == VX_OK) {
       if (l == depth) {
         rc = csf_prune(cur.v, keep, 0, nullptr, s, &R->fin, tm);
-        if (rc == VX_OK) R->kept[l] = R->fin.v.N[k - 1];
+        if (rc == VX_OK) R->kept[l] = R->fin.v.N[k - 1] + included;
       } else {
         CsfObj next;
         rc = csf_prune(cur.v, keep, 1, nullptr, s, &next, tm);
         if (rc == VX_OK) {
-          R->kept[l] = next.v.N[k - 1] >> k;
+          R->kept[l] = (next.v.N[k - 1] >> k) + included;
           csf_release(&cur);
           cur = next;
         }
       }
     }
     dfree(keep, s);
+    dfree(inc, s);
   }
   csf_release(&cur);
   if (rc == VX_OK) {
@@ -1939,6 +2063,54 @@ int vx_result_boxes(vx_result *R, int64_t *n, const int32_t **h_tuples) {
   return VX_OK;
 }
 
+int vx_result_included(vx_result *R, int64_t *n, const int32_t **h_levels,
+                       const int32_t **h_tuples) {
+  clear_error();
+  if (!R || !n || !h_levels || !h_tuples) {
+    set_error("vx_result_included: NULL argument");
+    return VX_EINVAL;
+  }
+  if (R->hinc_count < 0) {
+    const int k = R->k;
+    int64_t total = 0;
+    for (auto &lc : R->incl) total += lc.second.v.N[k - 1];
+    try {
+      R->hinc_lev.resize((size_t)std::max<int64_t>(total, 1));
+      R->hinc_tup.resize((size_t)std::max<int64_t>(total, 1) * k);
+    } catch (...) {
+      set_error("vx_result_included: out of host memory");
+      return VX_ENOMEM;
+    }
+    int64_t at = 0;
+    for (auto &lc : R->incl) {
+      const int64_t m = lc.second.v.N[k - 1];
+      if (m == 0) continue;
+      cudaStream_t s = lc.second.stream;
+      int32_t *d = nullptr;
+      int rc = dmalloc((void **)&d, (size_t)m * k * 4, s);
+      if (rc == VX_OK) rc = csf_tuples_dev(lc.second.v, d, s);
+      if (rc == VX_OK) {
+        cudaError_t e = cudaMemcpyAsync(R->hinc_tup.data() + at * k, d, (size_t)m * k * 4,
+                                        cudaMemcpyDeviceToHost, s);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+        if (e != cudaSuccess) {
+          set_error("copying the certified boxes to the host failed: %s", cudaGetErrorString(e));
+          rc = VX_ECUDA;
+        }
+      }
+      dfree(d, s);
+      VX_CHECK(rc);
+      for (int64_t i = 0; i < m; ++i) R->hinc_lev[at + i] = lc.first;
+      at += m;
+    }
+    R->hinc_count = total;
+  }
+  *n = R->hinc_count;
+  *h_levels = R->hinc_lev.data();
+  *h_tuples = R->hinc_tup.data();
+  return VX_OK;
+}
+
 int vx_result_csf(const vx_result *R, const vx_csf **csf) {
   clear_error();
   if (!R || !csf) {
@@ -2001,6 +2173,7 @@ void vx_result_free(vx_result *R) {
   if (!R) return;
   pinned_put(R->htup, R->hcap);
   csf_release(&R->fin);
+  for (auto &lc : R->incl) csf_release(&lc.second);
   R->tm.release();
   delete R;
 }

@@ -66,8 +66,10 @@ constexpr int kThreads = 32 * kWarpsPerBlock;
 // The binary64 endpoints of box t on an axis: the regular grid (exact on accepted domains) or
 // the axis' explicit interval list.
 __device__ __forceinline__ void endpoints(const AxisGrid &g, int32_t t, double &l, double &h) {
-  if (g.point) {
+  if (g.point == 1) {
     l = h = __dadd_rn(g.lo, __dmul_rn((double)t + 0.5, g.w));  // exact on accepted grids
+  } else if (g.point) {  // 2: the lower end, 3: the upper end, as a point interval
+    l = h = __dadd_rn(g.lo, __dmul_rn((double)t + (g.point == 3 ? 1.0 : 0.0), g.w));
   } else if (g.xlo) {
     l = g.xlo[t];
     h = g.xhi[t];
@@ -627,10 +629,17 @@ __device__ __forceinline__ void horner_y2_fibre(const float4 *__restrict__ base,
 // ---------------------------------------------------------------------------------------
 // Taylor form (Def. 3) at the leaves: the system holds G_a = d^a F / a! for the multi-indices
 // |a| <= m of one polynomial F (lexicographic order); G_a with |a| < m was partially evaluated
-// at the box centres (point grids), the others on the boxes.  Per leaf:
-//   T = sum_a V_a * prod_i range((x_i - c_i)^{a_i}),  x_i - c_i in [-r_i, r_i],
-// the range [1,1] (a_i = 0), [0, r^a_i] (even), [-r^a_i, r^a_i] (odd), interval products as
-// hulls of directed endpoint products and outward sums, in the order of the oracle.  C0 on T.
+// at the box centres (point grids), the others on the boxes.  Per leaf, with V_a the value of
+// G_a and x - c in [-r, r]:
+//   T = sum_a V_a * prod_i range((x_i - c_i)^{a_i}),
+// the range [1,1] (a_i = 0), [0, r^a_i] (even) or [-r^a_i, r^a_i] (odd); interval products
+// are hulls of directed endpoint products, sums outward, in the order of the multi-indices.
+// C0 on T.  With c1 (m >= 2, one equation) also the inclusion criterion C1 of Sec. 3.2 on the
+// Taylor form: s_i = +1 if the midpoint of g_i = V_{e_i} (a first derivative at the centre)
+// is >= 0 (lo >= -hi), else -1; V_max = c + s r and V_min = c - s r are the vertices where
+// the linear part is largest and smallest; F(V) lies in sum_a V_a prod_i [v_i, v_i]^{a_i}
+// (v = V - c, powers by repeated interval products); certified iff that enclosure is > 0 at
+// V_max and < 0 at V_min (opposite signs at two points of the connected box).
 // ---------------------------------------------------------------------------------------
 struct TaylorLeaf {
   int32_t na, m, k;
@@ -638,6 +647,9 @@ struct TaylorLeaf {
   double r[VX_KMAX];  // half-widths of the level's boxes, per axis
   int32_t first;      // 1: write keep, 0: AND into it (several polynomials)
   double *lo, *hi;    // nullable: T per leaf
+  int32_t c1;         // nonzero: write inc (C1 on the Taylor form)
+  int8_t ei[VX_KMAX]; // index of the multi-index e_i
+  uint8_t *inc;
 };
 
 __device__ __forceinline__ double2 imul_hull(double2 x, double2 y) {
@@ -665,15 +677,16 @@ __global__ void __launch_bounds__(kThreads)
     const int32_t t = __ldg(lab + i);
     const A64::X xb = A64::box(gbox, t), xp = A64::box(gpoint, t);
     const int64_t p = par ? (int64_t)__ldg(par + i) : 0;
+    double2 V[VX_MAXPOLY];
     double2 acc = make_double2(0.0, 0.0);
     for (int a = 0; a < T.na; ++a) {
       int tot = 0;
       for (int d = 0; d < T.k; ++d) tot += T.alpha[a][d];
       const double2 *base = (const double2 *)A.in[a] + p * A.blk[a];
-      const double2 V = horner1_any<A64>(base, 1, A.len[a], tot < T.m ? xp : xb);
+      V[a] = horner1_any<A64>(base, 1, A.len[a], tot < T.m ? xp : xb);
       double2 P = make_double2(1.0, 1.0);
       for (int d = 0; d < T.k; ++d) P = imul_hull(P, pow_range(T.r[d], T.alpha[a][d]));
-      const double2 VP = imul_hull(V, P);
+      const double2 VP = imul_hull(V[a], P);
       acc = make_double2(__dadd_rd(acc.x, VP.x), __dadd_ru(acc.y, VP.y));
     }
     if (T.lo) {
@@ -682,7 +695,47 @@ __global__ void __launch_bounds__(kThreads)
     }
     const uint8_t k0 = (acc.x > 0.0 || acc.y < 0.0) ? 0 : 1;
     keep[i] = T.first ? k0 : (uint8_t)(keep[i] & k0);
+    if (T.c1) {
+      double v[VX_KMAX];
+      for (int d = 0; d < T.k; ++d) {
+        const double2 g = V[T.ei[d]];
+        v[d] = (g.x >= -g.y) ? T.r[d] : -T.r[d];
+      }
+      double2 at[2];
+      for (int side = 0; side < 2; ++side) {  // 0: V_max, 1: V_min
+        double2 sum = make_double2(0.0, 0.0);
+        for (int a = 0; a < T.na; ++a) {
+          double2 P = make_double2(1.0, 1.0);
+          for (int d = 0; d < T.k; ++d) {
+            const double x = side == 0 ? v[d] : -v[d];
+            for (int e = 0; e < T.alpha[a][d]; ++e) P = imul_hull(P, make_double2(x, x));
+          }
+          const double2 VP = imul_hull(V[a], P);
+          sum = make_double2(__dadd_rd(sum.x, VP.x), __dadd_ru(sum.y, VP.y));
+        }
+        at[side] = sum;
+      }
+      T.inc[i] = (at[0].x > 0.0 && at[1].y < 0.0) ? 1 : 0;
+    }
   }
+}
+
+// Inclusion criterion C1 by vertex signs: after each vertex's evaluation (point intervals at
+// one corner of every box), flags |= 1 if the value is certified > 0, |= 2 if < 0.
+__global__ void k_c1_fold(const double *__restrict__ lo, const double *__restrict__ hi,
+                          int64_t n, uint8_t *__restrict__ flags, int first) {
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
+    const uint8_t f = (lo[i] > 0.0 ? 1 : 0) | (hi[i] < 0.0 ? 2 : 0);
+    flags[i] = first ? f : (uint8_t)(flags[i] | f);
+  }
+}
+
+__global__ void k_c1_final(const uint8_t *__restrict__ flags, int64_t n,
+                           uint8_t *__restrict__ inc) {
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride)
+    inc[i] = flags[i] == 3 ? 1 : 0;
 }
 
 // One warp's share of k_stage_c: node pairs of chunk `chunk` (64 nodes), fibres g, g+G, ....
@@ -1466,7 +1519,8 @@ int eval_forest(int arith, const ForestTree *d_trees, const ForestTree *h_trees,
 
 int eval_level_taylor(const SysDev &tsys, const int8_t (*alpha)[VX_KMAX], int m,
                       const CsfView &c, const LevelGrid &grid, uint8_t *d_keep, int first,
-                      double *d_lo, double *d_hi, cudaStream_t s, Timer *tm, int64_t *madds) {
+                      double *d_lo, double *d_hi, uint8_t *d_inc, cudaStream_t s, Timer *tm,
+                      int64_t *madds) {
   const int k = c.k;
   TaylorLeaf tl{};
   tl.na = tsys.npoly;
@@ -1475,6 +1529,22 @@ int eval_level_taylor(const SysDev &tsys, const int8_t (*alpha)[VX_KMAX], int m,
   tl.first = first;
   tl.lo = d_lo;
   tl.hi = d_hi;
+  if (d_inc) {
+    tl.c1 = 1;
+    tl.inc = d_inc;
+    for (int d = 0; d < k; ++d) {
+      tl.ei[d] = -1;
+      for (int a = 0; a < tsys.npoly; ++a) {
+        bool unit = true;
+        for (int j = 0; j < k; ++j) unit = unit && alpha[a][j] == (j == d ? 1 : 0);
+        if (unit) tl.ei[d] = (int8_t)a;
+      }
+      if (tl.ei[d] < 0 || m < 2) {
+        set_error("C1 on the Taylor form needs order >= 2");
+        return VX_EINVAL;
+      }
+    }
+  }
   std::vector<LevelGrid> pg(tsys.npoly, grid);
   for (int a = 0; a < tsys.npoly; ++a) {
     int tot = 0;
@@ -1491,6 +1561,55 @@ int eval_level_taylor(const SysDev &tsys, const int8_t (*alpha)[VX_KMAX], int m,
   for (int d = 0; d < k; ++d) tl.r[d] = 0.5 * grid.ax[d].w;  // exact (dyadic widths)
   return eval_level_t<A64>(tsys, c, grid, nullptr, nullptr, d_keep, nullptr, 0.f, s, tm, madds,
                            KK_STAGE0, nullptr, 0, pg.data(), &tl);
+}
+
+int eval_c1_vertex(const SysDev &sys, const CsfView &c, const LevelGrid &grid, uint8_t *d_inc,
+                   cudaStream_t s, Timer *tm, int64_t *madds) {
+  const int k = c.k;
+  const int64_t n = c.N[k - 1];
+  *madds = 0;
+  if (n == 0) return VX_OK;
+  if (sys.npoly != 1) {
+    set_error("C1 is a test for one equation (the system has %d)", sys.npoly);
+    return VX_EINVAL;
+  }
+  double *lo = nullptr, *hi = nullptr;
+  uint8_t *scratch = nullptr, *flags = nullptr;
+  int rc = dmalloc((void **)&lo, (size_t)n * 8, s);
+  if (rc == VX_OK) rc = dmalloc((void **)&hi, (size_t)n * 8, s);
+  if (rc == VX_OK) rc = dmalloc((void **)&scratch, (size_t)n, s);
+  if (rc == VX_OK) rc = dmalloc((void **)&flags, (size_t)n, s);
+  for (int v = 0; v < (1 << k) && rc == VX_OK; ++v) {
+    LevelGrid g = grid;
+    for (int d = 0; d < k; ++d) {
+      g.ax[d].point = ((v >> (k - 1 - d)) & 1) ? 3 : 2;
+      g.ax[d].fexact = 0;
+    }
+    int64_t w = 0;
+    rc = eval_level_t<A64>(sys, c, g, lo, hi, scratch, nullptr, 0.f, s, tm, &w, KK_STAGE0);
+    *madds += w;
+    if (rc == VX_OK) {
+      k_c1_fold<<<leaf_grid(n), kThreads, 0, s>>>(lo, hi, n, flags, v == 0);
+      note_launch();
+      if (cudaGetLastError() != cudaSuccess) {
+        set_error("C1 fold launch failed");
+        rc = VX_ECUDA;
+      }
+    }
+  }
+  if (rc == VX_OK) {
+    k_c1_final<<<leaf_grid(n), kThreads, 0, s>>>(flags, n, d_inc);
+    note_launch();
+    if (cudaGetLastError() != cudaSuccess) {
+      set_error("C1 launch failed");
+      rc = VX_ECUDA;
+    }
+  }
+  dfree(lo, s);
+  dfree(hi, s);
+  dfree(scratch, s);
+  dfree(flags, s);
+  return rc;
 }
 
 int set_autotune(int mode, const char *path) {

@@ -81,7 +81,8 @@ struct AxisGrid {
   // explicit intervals (device arrays, label t -> [xlo[t], xhi[t]]) instead of the regular
   // grid when non-null; fexact is 0 then
   const double *xlo, *xhi;
-  // nonzero: box t stands for its centre, the point interval [c, c], c = lo + (t + 1/2) w
+  // nonzero: box t stands for a point of it, as the point interval [x, x]: 1 its centre
+  // x = lo + (t + 1/2) w, 2 its lower end lo + t w, 3 its upper end lo + (t + 1) w
   int32_t point;
 };
 
@@ -166,10 +167,17 @@ int eval_forest(int arith, const ForestTree *d_trees, const ForestTree *h_trees,
                 uint8_t *keep, uint8_t *flag, float theta, cudaStream_t s, int64_t *madds);
 // The Taylor form of order m (Def. 3) of one polynomial F on every leaf, in binary64: tsys
 // holds G_a = d^a F / a! for the multi-indices alpha[0..npoly-1] (|a| <= m, lexicographic);
-// keep = 0 in T (first = 1) or keep &= that (first = 0); d_lo/d_hi (nullable) receive T.
+// keep = 0 in T (first = 1) or keep &= that (first = 0); d_lo/d_hi (nullable) receive T;
+// d_inc (nullable, m >= 2) receives the inclusion criterion C1 on the Taylor form.
 int eval_level_taylor(const SysDev &tsys, const int8_t (*alpha)[VX_KMAX], int m,
                       const CsfView &c, const LevelGrid &grid, uint8_t *d_keep, int first,
-                      double *d_lo, double *d_hi, cudaStream_t s, Timer *tm, int64_t *madds);
+                      double *d_lo, double *d_hi, uint8_t *d_inc, cudaStream_t s, Timer *tm,
+                      int64_t *madds);
+// The inclusion criterion C1 by vertex signs (Sec. 3.2) of the system's one polynomial on
+// every leaf: each of the 2^k corners of the boxes is evaluated through the CSF in binary64
+// (point intervals); d_inc[i] = 1 iff one corner is certified > 0 and another < 0.
+int eval_c1_vertex(const SysDev &sys, const CsfView &c, const LevelGrid &grid, uint8_t *d_inc,
+                   cudaStream_t s, Timer *tm, int64_t *madds);
 // Reads (synchronising `s`) and clears the device status word that a kernel sets when a
 // bounded wait gives up; *status != 0 means the last evaluations are not to be trusted.
 int take_device_status(cudaStream_t s, int *status);

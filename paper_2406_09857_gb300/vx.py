@@ -18,6 +18,7 @@ LIB_PATH = os.path.join(HERE, "_build", "libvx.so")
 OK, EINVAL, ENOMEM, ECAPACITY, EOVERFLOW, ETIMEOUT, ECUDA = 0, -1, -2, -3, -4, -5, -6
 KMAX, MAXPOLY, MAXLEVEL = 4, 16, 24
 FP64, FP32_MIDRAD, FP32 = 0, 1, 2
+C1_TAYLOR, C1_VERTEX = 1, 2
 
 _lib = None
 
@@ -37,7 +38,8 @@ class Opts(ctypes.Structure):
     _fields_ = [("mode", ctypes.c_int32), ("fp64_final", ctypes.c_int32),
                 ("fp64_recheck", ctypes.c_int32), ("theta", ctypes.c_float),
                 ("timing", ctypes.c_int32), ("taylor_order", ctypes.c_int32),
-                ("reserved", ctypes.c_int32 * 6)]
+                ("c1", ctypes.c_int32), ("c1_level", ctypes.c_int32),
+                ("reserved", ctypes.c_int32 * 4)]
 
 
 def lib() -> ctypes.CDLL:
@@ -72,6 +74,8 @@ def lib() -> ctypes.CDLL:
         "vx_csf_eval_level_static": ([P, P, P, i32, P, P, P, P], i32),
         "vx_csf_eval_grid": ([P, P, P, P, P, i32, P, P, P, P], i32),
         "vx_csf_eval_level_taylor": ([P, P, P, i32, P, P, P, P], i32),
+        "vx_csf_c1": ([P, P, P, i32, i32, P, P], i32),
+        "vx_result_included": ([P, P, P, P], i32),
         "vx_csf_subdivide": ([P, P, P, PP], i32),
         "vx_csf_compact": ([P, P, P, P, PP], i32),
         "vx_enclose_system": ([P, P, i32, P, P, PP], i32),
@@ -166,8 +170,10 @@ def _domain(domain) -> np.ndarray:
 
 
 def make_opts(mode=FP64, fp64_final=False, fp64_recheck=False, theta=0.5, timing=False,
-              taylor_order=0) -> Opts:
+              taylor_order=0, c1=0, c1_level=0) -> Opts:
     o = Opts()
+    o.c1 = int(c1)
+    o.c1_level = int(c1_level)
     o.mode = int(mode)
     o.fp64_final = int(bool(fp64_final))
     o.fp64_recheck = int(bool(fp64_recheck))
@@ -314,6 +320,19 @@ def csf_eval_level_taylor(system: System, csf: Csf, domain, order, values=False,
     return keep[:n]
 
 
+def csf_c1(system: System, csf: Csf, domain, kind, order=0, stream=None):
+    """The inclusion criterion C1 (C1_TAYLOR of the given order >= 2, or C1_VERTEX) of the
+    system's one polynomial on every leaf box: uint8 [n], 1 where certified."""
+    import torch
+
+    _, _, N = csf.nodes()
+    n = int(N[-1])
+    inc = torch.empty(max(n, 1), dtype=torch.uint8, device="cuda")
+    _check(lib().vx_csf_c1(system.handle, csf.handle, _np_ptr(_domain(domain)), int(kind),
+                           int(order), _ptr(inc), _stream(stream)))
+    return inc[:n]
+
+
 def csf_eval_grid(system: System, csf: Csf, xlists, mode=FP64, values=False, stream=None):
     """Level evaluation on explicit per-axis intervals ``xlists[i] = (lo, hi)`` (float64 CUDA
     tensors): keep (uint8 [n]) or (keep, lo, hi) with values=True."""
@@ -387,6 +406,22 @@ class Result:
         buf = (ctypes.c_int32 * (m * self.k)).from_address(p.value)
         a = np.frombuffer(buf, dtype=np.int32).reshape(m, self.k)
         return a.copy() if copy else a
+
+    def included(self):
+        """With C1: (levels [n] int32, tuples [n, k] int32) of the certified boxes, ordered by
+        level, then lexicographic."""
+        n = ctypes.c_int64()
+        pl = ctypes.c_void_p()
+        pt = ctypes.c_void_p()
+        _check(lib().vx_result_included(self.handle, ctypes.byref(n), ctypes.byref(pl),
+                                        ctypes.byref(pt)))
+        m = int(n.value)
+        if m == 0:
+            return np.zeros(0, dtype=np.int32), np.zeros((0, self.k), dtype=np.int32)
+        lev = np.frombuffer((ctypes.c_int32 * m).from_address(pl.value), dtype=np.int32)
+        tup = np.frombuffer((ctypes.c_int32 * (m * self.k)).from_address(pt.value),
+                            dtype=np.int32).reshape(m, self.k)
+        return lev.copy(), tup.copy()
 
     def csf(self) -> Csf:
         h = ctypes.c_void_p()

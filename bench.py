@@ -394,6 +394,24 @@ def bench_table1(vx, synth, torch, stream, taylor=True):
                                         "boxes": int(tst["kept"][-1]),
                                         "box_evals": int(tst["tested"].sum())}
                 rt.free()
+                if kind == "hypersurfaces":
+                    # as the paper's hypersurface row: C0 and C1 on the Taylor form, C1 from
+                    # the size threshold (level 7) on, until no box is left (cap: level 14)
+                    cap = 14
+                    to = vx.make_opts(vx.FP64, taylor_order=2, c1=vx.C1_TAYLOR, c1_level=depth)
+                    e0.record(stream)
+                    rt = vx.enclose_system(sysv, s.domain, cap, to, stream=stream)
+                    e1.record(stream)
+                    e1.synchronize()
+                    tst = rt.stats()
+                    lev, _ = rt.included()
+                    cell["taylor2_c1_fp64"] = {
+                        "ms": round(e0.elapsed_time(e1), 3), "c1_level": depth,
+                        "level_cap": cap, "certified": int(lev.shape[0]),
+                        "certified_per_level": np.bincount(lev, minlength=cap + 1)[depth:].tolist(),
+                        "undecided_at_cap": int(tst["kept"][-1] - np.sum(lev == cap)),
+                        "box_evals": int(tst["tested"].sum())}
+                    rt.free()
             out["k%d-d%d-%s" % (k, d, kind)] = cell
             sysv.free()
     return out

@@ -64,6 +64,8 @@ def lib():
         L.orc_taylor_boxes.argtypes = sysargs + [P, i32, i32, P, i64, P, P, P]
         L.orc_enclose_taylor.argtypes = sysargs + [P, i32, i32, ctypes.POINTER(P)]
         L.orc_c1_boxes.argtypes = sysargs + [P, i32, i32, i32, P, i64, P]
+        L.orc_eval_csf_gen.argtypes = sysargs + [P, P, P, i32, P, i64, P, P, P, P]
+        L.orc_enclose_gen.argtypes = sysargs + [P, P, P, i32, i32, ctypes.POINTER(P)]
         L.orc_enclose_c1.argtypes = sysargs + [P, i32, i32, i32, i32, ctypes.POINTER(P)]
         L.orc_result_inc_count.argtypes = [P]
         L.orc_result_inc_count.restype = i64
@@ -72,7 +74,7 @@ def lib():
                   "orc_enclose_from",
                   "orc_brute_force", "orc_eval_grid_complex", "orc_domain_exact",
                   "orc_dense_powerform", "orc_taylor_boxes", "orc_enclose_taylor",
-                  "orc_c1_boxes", "orc_enclose_c1"):
+                  "orc_c1_boxes", "orc_enclose_c1", "orc_eval_csf_gen", "orc_enclose_gen"):
             getattr(L, f).restype = i32
         _lib = L
     return _lib
@@ -87,8 +89,8 @@ def _check(rc: int, what: str):
         raise OracleError("%s failed with code %d" % (what, rc))
 
 
-def _p(a: np.ndarray):
-    return a.ctypes.data_as(ctypes.c_void_p)
+def _p(a):
+    return None if a is None else a.ctypes.data_as(ctypes.c_void_p)
 
 
 def pack(polys):
@@ -354,4 +356,51 @@ def enclose_c1(poly, domain, depth, kind, c1_level, taylor_order=0):
     _check(lib().orc_enclose_c1(k, npoly, _p(off), _p(E), _p(C), _p(dom), int(depth),
                                 int(taylor_order), int(kind), int(c1_level), ctypes.byref(res)),
            "orc_enclose_c1")
+    return _result(res, k, depth)
+
+
+EQ, LE, GE, LT, GT = 0, 1, 2, 3, 4
+
+
+def _his_rel(polys, his, rel):
+    """Upper coefficient ends (concatenated; point coefficients where his[f] is None) and the
+    relations (int32), or None for all-point / all-equation systems."""
+    H = None
+    if his is not None and any(h is not None for h in his):
+        H = np.ascontiguousarray(np.concatenate(
+            [np.asarray(c if h is None else h, dtype=np.float64).reshape(-1)
+             for (_, c), h in zip(polys, his)]))
+    R = None if rel is None else np.ascontiguousarray(np.asarray(rel, dtype=np.int32))
+    return H, R
+
+
+def eval_csf_gen(polys, domain, level, tuples, his=None, rel=None):
+    """eval_csf for a system of equations and inequalities with interval coefficients:
+    his[f] the upper coefficient ends of polynomial f (None: points), rel[f] in EQ, LE, GE,
+    LT, GT (F = 0, F <= 0, F >= 0, F < 0, F > 0)."""
+    k, npoly, off, E, C = pack(polys)
+    H, R = _his_rel(polys, his, rel)
+    t = _tuples(tuples, k)
+    n = t.shape[0]
+    dom = np.ascontiguousarray(np.asarray(domain, dtype=np.float64).reshape(-1))
+    lo = np.empty((npoly, n))
+    hi = np.empty((npoly, n))
+    keep = np.empty(n, dtype=np.uint8)
+    work = np.zeros(1, dtype=np.int64)
+    _check(lib().orc_eval_csf_gen(k, npoly, _p(off), _p(E), _p(C), _p(H), _p(R), _p(dom),
+                                  int(level), _p(t), n, _p(lo), _p(hi), _p(keep), _p(work)),
+           "orc_eval_csf_gen")
+    return lo, hi, keep, int(work[0])
+
+
+def enclose_gen(polys, domain, depth, his=None, rel=None, taylor_order=0):
+    """Algorithm 3 for a system of equations and inequalities with interval coefficients
+    (his, rel as for eval_csf_gen); C0 on interval Horner or the Taylor form."""
+    k, npoly, off, E, C = pack(polys)
+    H, R = _his_rel(polys, his, rel)
+    dom = np.ascontiguousarray(np.asarray(domain, dtype=np.float64).reshape(-1))
+    res = ctypes.c_void_p()
+    _check(lib().orc_enclose_gen(k, npoly, _p(off), _p(E), _p(C), _p(H), _p(R), _p(dom),
+                                 int(depth), int(taylor_order), ctypes.byref(res)),
+           "orc_enclose_gen")
     return _result(res, k, depth)

@@ -21,6 +21,8 @@
  *                    (Property 1's contractions, one variable at a time), the reference for
  *                    the dense tensor-core level.
  *   orc_taylor_boxes(), orc_enclose_taylor()  C0 on the Taylor form of order m (Def. 3).
+ *   orc_eval_csf_gen(), orc_enclose_gen()  systems of equations and inequalities (F = 0,
+ *                    F <= 0, F >= 0, F < 0, F > 0) with interval coefficients (Sec. 4).
  *   orc_c1_boxes(), orc_enclose_c1()  the inclusion criterion C1 for one equation (Sec. 3.2:
  *                    vertex signs, or the Taylor form at the two vertices extremal for its
  *                    linear part) and Algorithm 3 with both criteria.
@@ -44,6 +46,10 @@
  *     left or after level `depth` (boxes that touch the zero set only where F has no sign
  *     change, e.g. at a vertex, are never certified); "size < threshold" is a first level
  *     c1_level from which C1 is applied.
+ *   - An inequality drops a box when the enclosure proves it false on the whole box (F <= 0:
+ *     lo > 0; F < 0: lo >= 0; F >= 0: hi < 0; F > 0: hi <= 0); an interval coefficient
+ *     [c_lo, c_hi] enters Horner as that interval (a coefficient such as sqrt(3) is given as
+ *     the two binary64 numbers around it).
  *   - The Taylor C1 picks V_max by the sign of each first-derivative interval's midpoint
  *     (lo >= -hi counts as >= 0) and tests only the orientation the paper states (lower
  *     bound at V_max > 0, upper bound at V_min < 0).
@@ -338,8 +344,8 @@ static void eval_rec(const plan *P, const csf *T, const boxsrc *B, int j, const 
 }
 
 /* Evaluates one polynomial on every leaf of T. */
-static int eval_poly_csf(const plan *P, const double *coefs, const csf *T, const boxsrc *B,
-                         ivl *leaf, int64_t *work) {
+static int eval_poly_csf(const plan *P, const double *clo, const double *chi, const csf *T,
+                         const boxsrc *B, ivl *leaf, int64_t *work) {
   int64_t n = T->N[P->k - 1];
   if (P->nterms == 0) {
     for (int64_t i = 0; i < n; ++i) leaf[i].lo = leaf[i].hi = 0.0;
@@ -349,7 +355,10 @@ static int eval_poly_csf(const plan *P, const double *coefs, const csf *T, const
   ivl *buf[ORC_KMAX] = {0};
   int rc = ORC_OK;
   if (!in) return ORC_ENOMEM;
-  for (int i = 0; i < P->nterms; ++i) in[i].lo = in[i].hi = coefs[i];
+  for (int i = 0; i < P->nterms; ++i) {
+    in[i].lo = clo[i];
+    in[i].hi = chi[i];
+  }
   for (int j = 0; j < P->k; ++j) {
     buf[j] = (ivl *)malloc(sizeof(ivl) * (size_t)P->st[j].nout);
     if (!buf[j]) rc = ORC_ENOMEM;
@@ -489,14 +498,46 @@ int orc_domain_exact(int k, const double *domain, int level) {
   return ok;
 }
 
+/* C0 for one polynomial of a system of equations and inequalities (Sec. 3.2, Sec. 4): the
+ * box is dropped iff the enclosure [lo, hi] of F on it proves the relation false at every
+ * point of it.  An enclosure with a NaN end proves nothing (every comparison is false). */
+#define ORC_EQ 0 /* F = 0 */
+#define ORC_LE 1 /* F <= 0 */
+#define ORC_GE 2 /* F >= 0 */
+#define ORC_LT 3 /* F < 0 */
+#define ORC_GT 4 /* F > 0 */
+static int c0_drops(ivl v, int rel) {
+  switch (rel) {
+    case ORC_LE: return v.lo > 0.0;
+    case ORC_GE: return v.hi < 0.0;
+    case ORC_LT: return v.lo >= 0.0;
+    case ORC_GT: return v.hi <= 0.0;
+    default: return v.lo > 0.0 || v.hi < 0.0;
+  }
+}
+
+/* checks interval coefficients (chi may be NULL: point coefficients) and relations */
+static int check_ivl_rel(int npoly, const int64_t *term_off, const double *clo, const double *chi,
+                         const int32_t *rel) {
+  for (int f = 0; f < npoly; ++f) {
+    if (rel && (rel[f] < ORC_EQ || rel[f] > ORC_GT)) return ORC_EINVAL;
+    for (int64_t i = term_off[f]; chi && i < term_off[f + 1]; ++i)
+      if (!isfinite(chi[i]) || !(clo[i] <= chi[i])) return ORC_EINVAL;
+  }
+  return ORC_OK;
+}
+
 static int eval_csf_common(int k, int npoly, const int64_t *term_off, const int32_t *exps,
-                           const double *coefs, const boxsrc *B, const int32_t *tuples, int64_t n,
-                           double *lo, double *hi, uint8_t *keep, int64_t *work) {
+                           const double *coefs, const double *coefs_hi, const int32_t *rel,
+                           const boxsrc *B, const int32_t *tuples, int64_t n, double *lo,
+                           double *hi, uint8_t *keep, int64_t *work) {
   plan plans[16];
   csf T;
   int rc = check_system(k, npoly, term_off);
   if (rc != ORC_OK) return rc;
   if (npoly > 16) return ORC_EINVAL;
+  rc = check_ivl_rel(npoly, term_off, coefs, coefs_hi, rel);
+  if (rc != ORC_OK) return rc;
   rc = build_plans(plans, k, npoly, term_off, exps, coefs);
   if (rc != ORC_OK) return rc;
   rc = csf_build(&T, k, tuples, n);
@@ -510,13 +551,14 @@ static int eval_csf_common(int k, int npoly, const int64_t *term_off, const int3
   if (keep)
     for (int64_t i = 0; i < n; ++i) keep[i] = 1;
   for (int f = 0; rc == ORC_OK && f < npoly; ++f) {
-    rc = eval_poly_csf(&plans[f], coefs + term_off[f], &T, B, leaf, &w);
+    rc = eval_poly_csf(&plans[f], coefs + term_off[f], (coefs_hi ? coefs_hi : coefs) + term_off[f],
+                       &T, B, leaf, &w);
     for (int64_t i = 0; rc == ORC_OK && i < n; ++i) {
       if (lo) lo[(int64_t)f * n + i] = leaf[i].lo;
       if (hi) hi[(int64_t)f * n + i] = leaf[i].hi;
-      /* C0: the box is dropped iff 0 is provably outside [lo, hi] for some polynomial
-       * (lo > 0 or hi < 0); an enclosure with a NaN endpoint proves nothing and keeps it */
-      if (keep && (leaf[i].lo > 0.0 || leaf[i].hi < 0.0)) keep[i] = 0;
+      /* C0: the box is dropped iff the enclosure of some polynomial proves its relation
+       * false on the box (for an equation: 0 is provably outside [lo, hi]) */
+      if (keep && c0_drops(leaf[i], rel ? rel[f] : ORC_EQ)) keep[i] = 0;
     }
   }
   if (work) *work = w;
@@ -533,7 +575,24 @@ int orc_eval_csf(int k, int npoly, const int64_t *term_off, const int32_t *exps,
   int old = fegetround();
   fesetround(FE_DOWNWARD);
   boxsrc B = {domain, level, 0, 0, 0};
-  int rc = eval_csf_common(k, npoly, term_off, exps, coefs, &B, tuples, n, lo, hi, keep, work);
+  int rc = eval_csf_common(k, npoly, term_off, exps, coefs, 0, 0, &B, tuples, n, lo, hi, keep,
+                           work);
+  fesetround(old);
+  return rc;
+}
+
+/* orc_eval_csf for a system of equations and inequalities with interval coefficients:
+ * polynomial f has coefficients [coefs[t], coefs_hi[t]] (coefs_hi NULL: points) and the
+ * relation rel[f] (ORC_EQ .. ORC_GT; rel NULL: all equations). */
+int orc_eval_csf_gen(int k, int npoly, const int64_t *term_off, const int32_t *exps,
+                     const double *coefs, const double *coefs_hi, const int32_t *rel,
+                     const double *domain, int level, const int32_t *tuples, int64_t n,
+                     double *lo, double *hi, uint8_t *keep, int64_t *work) {
+  int old = fegetround();
+  fesetround(FE_DOWNWARD);
+  boxsrc B = {domain, level, 0, 0, 0};
+  int rc = eval_csf_common(k, npoly, term_off, exps, coefs, coefs_hi, rel, &B, tuples, n, lo, hi,
+                           keep, work);
   fesetround(old);
   return rc;
 }
@@ -551,7 +610,8 @@ int orc_eval_grid(int k, int npoly, const int64_t *term_off, const int32_t *exps
         return ORC_EINVAL;
       }
   boxsrc B = {0, 0, xoff, xlo, xhi};
-  int rc = eval_csf_common(k, npoly, term_off, exps, coefs, &B, tuples, n, lo, hi, keep, work);
+  int rc = eval_csf_common(k, npoly, term_off, exps, coefs, 0, 0, &B, tuples, n, lo, hi, keep,
+                           work);
   fesetround(old);
   return rc;
 }
@@ -792,7 +852,7 @@ static void taylor_free(taylor_sys *T) {
 
 /* the derived polynomials G_a of one polynomial (rounding mode FE_DOWNWARD) */
 static int taylor_build(taylor_sys *T, int k, int m, int nterms, const int32_t *exps,
-                        const double *coefs) {
+                        const double *coefs, const double *coefs_hi) {
   memset(T, 0, sizeof(*T));
   T->na = enum_alphas(k, m, T->alpha, 64);
   if (T->na < 0) return ORC_EINVAL;
@@ -821,7 +881,7 @@ static int taylor_build(taylor_sys *T, int k, int m, int nterms, const int32_t *
       double C = 1.0;
       for (int i = 0; i < k; ++i) C *= binom(exps[(size_t)t * k + i], al[i]);
       T->clo[a][j] = rd_mul(coefs[t], C);
-      T->chi[a][j] = ru_mul(coefs[t], C);
+      T->chi[a][j] = ru_mul(coefs_hi[t], C);
       for (int i = 0; i < k; ++i) de[(size_t)j * k + i] = exps[(size_t)t * k + i] - al[i];
       ++j;
     }
@@ -991,7 +1051,7 @@ int orc_c1_boxes(int k, int npoly, const int64_t *term_off, const int32_t *exps,
     }
   } else {
     taylor_sys T;
-    rc = taylor_build(&T, k, m, (int)(term_off[1] - term_off[0]), exps, coefs);
+    rc = taylor_build(&T, k, m, (int)(term_off[1] - term_off[0]), exps, coefs, coefs);
     if (rc == ORC_OK) {
       for (int64_t i = 0; i < n && rc == ORC_OK; ++i)
         inc[i] = (uint8_t)taylor_c1_box(&T, k, m, &B, tuples + i * k, &w, &rc);
@@ -1018,7 +1078,7 @@ int orc_taylor_boxes(int k, int npoly, const int64_t *term_off, const int32_t *e
   for (int f = 0; f < npoly && rc == ORC_OK; ++f) {
     taylor_sys T;
     rc = taylor_build(&T, k, m, (int)(term_off[f + 1] - term_off[f]), exps + term_off[f] * k,
-                      coefs + term_off[f]);
+                      coefs + term_off[f], coefs + term_off[f]);
     if (rc != ORC_OK) break;
     for (int64_t i = 0; i < n && rc == ORC_OK; ++i) {
       ivl v = taylor_box(&T, k, m, &B, tuples + i * k, &w, &rc);
@@ -1039,15 +1099,15 @@ int orc_enclose(int k, int npoly, const int64_t *term_off, const int32_t *exps, 
 }
 
 static int enclose_core(int k, int npoly, const int64_t *term_off, const int32_t *exps,
-                        const double *coefs, const double *domain, int start_level,
-                        const int32_t *start, int64_t n0, int depth, int taylor_m, int c1_kind,
-                        int c1_level, orc_result **out);
+                        const double *coefs, const double *coefs_hi, const int32_t *rel,
+                        const double *domain, int start_level, const int32_t *start, int64_t n0,
+                        int depth, int taylor_m, int c1_kind, int c1_level, orc_result **out);
 
 int orc_enclose_from(int k, int npoly, const int64_t *term_off, const int32_t *exps,
                      const double *coefs, const double *domain, int start_level,
                      const int32_t *start, int64_t n0, int depth, orc_result **out) {
-  return enclose_core(k, npoly, term_off, exps, coefs, domain, start_level, start, n0, depth, 0, 0,
-                      0, out);
+  return enclose_core(k, npoly, term_off, exps, coefs, 0, 0, domain, start_level, start, n0, depth,
+                      0, 0, 0, out);
 }
 
 /* Algorithm 3 with C0 on the Taylor form of order m (Def. 3) instead of interval Horner. */
@@ -1056,7 +1116,8 @@ int orc_enclose_taylor(int k, int npoly, const int64_t *term_off, const int32_t 
                        orc_result **out) {
   int32_t root[ORC_KMAX] = {0};
   if (m < 1 || m > 8) return ORC_EINVAL;
-  return enclose_core(k, npoly, term_off, exps, coefs, domain, 0, root, 1, depth, m, 0, 0, out);
+  return enclose_core(k, npoly, term_off, exps, coefs, 0, 0, domain, 0, root, 1, depth, m, 0, 0,
+                      out);
 }
 
 /* Algorithm 3 with both criteria, for one equation: at every level the boxes C0 excludes are
@@ -1074,18 +1135,34 @@ int orc_enclose_c1(int k, int npoly, const int64_t *term_off, const int32_t *exp
   if (npoly != 1 || taylor_m < 0 || taylor_m > 8 || c1_level < 0) return ORC_EINVAL;
   if (c1_kind != ORC_C1_VERTEX && c1_kind != ORC_C1_TAYLOR) return ORC_EINVAL;
   if (c1_kind == ORC_C1_TAYLOR && taylor_m < 2) return ORC_EINVAL;
-  return enclose_core(k, npoly, term_off, exps, coefs, domain, 0, root, 1, depth, taylor_m,
+  return enclose_core(k, npoly, term_off, exps, coefs, 0, 0, domain, 0, root, 1, depth, taylor_m,
                       c1_kind, c1_level, out);
 }
 
+/* Algorithm 3 for a system of equations and inequalities with interval coefficients (Sec. 4):
+ * coefs_hi / rel as for orc_eval_csf_gen; C0 on interval Horner (taylor_m = 0) or on the
+ * Taylor form of order taylor_m. */
+int orc_enclose_gen(int k, int npoly, const int64_t *term_off, const int32_t *exps,
+                    const double *coefs, const double *coefs_hi, const int32_t *rel,
+                    const double *domain, int depth, int taylor_m, orc_result **out) {
+  int32_t root[ORC_KMAX] = {0};
+  *out = 0;
+  if (taylor_m < 0 || taylor_m > 8) return ORC_EINVAL;
+  return enclose_core(k, npoly, term_off, exps, coefs, coefs_hi, rel, domain, 0, root, 1, depth,
+                      taylor_m, 0, 0, out);
+}
+
 static int enclose_core(int k, int npoly, const int64_t *term_off, const int32_t *exps,
-                        const double *coefs, const double *domain, int start_level,
-                        const int32_t *start, int64_t n0, int depth, int taylor_m, int c1_kind,
-                        int c1_level, orc_result **out) {
+                        const double *coefs, const double *coefs_hi, const int32_t *rel,
+                        const double *domain, int start_level, const int32_t *start, int64_t n0,
+                        int depth, int taylor_m, int c1_kind, int c1_level, orc_result **out) {
   int old = fegetround();
   int rc = check_system(k, npoly, term_off);
   *out = 0;
   if (rc != ORC_OK) return rc;
+  rc = check_ivl_rel(npoly, term_off, coefs, coefs_hi, rel);
+  if (rc != ORC_OK) return rc;
+  if (!coefs_hi) coefs_hi = coefs;
   if (depth < 0 || depth > 30 || npoly > 16) return ORC_EINVAL;
   if (start_level < 0 || start_level > depth || n0 < 0) return ORC_EINVAL;
   if (!orc_domain_exact(k, domain, depth)) return ORC_EINVAL;
@@ -1126,17 +1203,18 @@ static int enclose_core(int k, int npoly, const int64_t *term_off, const int32_t
       if (taylor_m > 0) {
         taylor_sys TS;
         rc = taylor_build(&TS, k, taylor_m, (int)(term_off[f + 1] - term_off[f]),
-                          exps + term_off[f] * k, coefs + term_off[f]);
+                          exps + term_off[f] * k, coefs + term_off[f], coefs_hi + term_off[f]);
         for (int64_t i = 0; rc == ORC_OK && i < n; ++i) {
           ivl v = taylor_box(&TS, k, taylor_m, &B, S + i * k, &R->work[l], &rc);
-          if (v.lo > 0.0 || v.hi < 0.0) keep[i] = 0;
+          if (c0_drops(v, rel ? rel[f] : ORC_EQ)) keep[i] = 0;
         }
         if (rc == ORC_OK || TS.na > 0) taylor_free(&TS);
         continue;
       }
-      rc = eval_poly_csf(&plans[f], coefs + term_off[f], &T, &B, leaf, &R->work[l]);
+      rc = eval_poly_csf(&plans[f], coefs + term_off[f], coefs_hi + term_off[f], &T, &B, leaf,
+                         &R->work[l]);
       for (int64_t i = 0; rc == ORC_OK && i < n; ++i)
-        if ((leaf[i].lo > 0.0 || leaf[i].hi < 0.0)) keep[i] = 0;
+        if (c0_drops(leaf[i], rel ? rel[f] : ORC_EQ)) keep[i] = 0;
     }
     R->tested[l] = n;
     for (int j = 0; j < k; ++j) R->nodes[(size_t)l * k + j] = T.N[j];
@@ -1163,7 +1241,7 @@ static int enclose_core(int k, int npoly, const int64_t *term_off, const int32_t
       int built = 0;
       if (!inc) rc = ORC_ENOMEM;
       if (rc == ORC_OK && c1_kind == ORC_C1_TAYLOR) {
-        rc = taylor_build(&TC, k, taylor_m, (int)(term_off[1] - term_off[0]), exps, coefs);
+        rc = taylor_build(&TC, k, taylor_m, (int)(term_off[1] - term_off[0]), exps, coefs, coefs);
         built = rc == ORC_OK;
       }
       for (int64_t i = 0; rc == ORC_OK && i < n; ++i)

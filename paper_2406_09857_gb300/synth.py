@@ -126,6 +126,10 @@ class System:
     domain: np.ndarray  # float64 [2k]: lo, hi per axis
     depth: int
     meta: dict = field(default_factory=dict)
+    # interval coefficients: his[f] (float64 [T]) the upper ends of polynomial f's coefficients
+    # (None: point coefficients); rel[f]: 0 F = 0, 1 F <= 0, 2 F >= 0, 3 F < 0, 4 F > 0
+    his: list = None
+    rel: list = None
 
     @property
     def npoly(self) -> int:
@@ -259,3 +263,118 @@ def random_tuples(k: int, level: int, n: int, seed: int) -> np.ndarray:
         out[:, c] = r % side
         r //= side
     return out
+
+
+# ---------------------------------------------------------------------------------------
+# The two systems of Sec. 4.2, transcribed from the paper's displayed equations.
+# ---------------------------------------------------------------------------------------
+REL_EQ, REL_LE, REL_GE, REL_LT, REL_GT = 0, 1, 2, 3, 4
+
+# (R): the parallel singularities of the 3-PPPS manipulator in quaternion coordinates
+# Q1..Q4.  Terms of the first equation as (integer factor, 1 if multiplied by sqrt(3),
+# exponents of Q1, Q2, Q3, Q4); the second equation is Q1^2 + Q2^2 + Q3^2 + Q4^2 = 1.
+ROBOTICS_F1 = [
+    (-6, 0, (1, 2, 1, 0)), (6, 0, (0, 1, 2, 1)), (3, 1, (0, 2, 1, 1)), (-6, 0, (2, 1, 0, 1)),
+    (6, 0, (1, 0, 1, 2)), (-3, 1, (1, 1, 0, 2)), (3, 1, (1, 1, 2, 0)), (-3, 1, (2, 0, 1, 1)),
+    (1, 1, (1, 3, 0, 0)), (-1, 1, (3, 1, 0, 0)), (1, 1, (0, 0, 3, 1)), (-1, 1, (0, 0, 1, 3)),
+]
+
+# (A): a control-design system in three complex variables z1, z2, z3 (no solution with
+# |z_j| <= 1 is expected).  Terms as (integer coefficient, exponents of z1, z2, z3).
+AUTOMATIC_Z = [
+    [(1, (1, 2, 0)), (-1, (1, 0, 1)), (-2, (0, 0, 0))],
+    [(12, (0, 3, 3)), (-2, (2, 1, 2)), (1, (0, 3, 2)), (-2, (0, 2, 3)), (-12, (0, 1, 4)),
+     (2, (2, 0, 2)), (-1, (0, 1, 3)), (-2, (1, 1, 1)), (-7, (0, 3, 0)), (-10, (0, 2, 1)),
+     (14, (1, 0, 1)), (-8, (0, 2, 0)), (9, (0, 1, 1)), (12, (0, 0, 2)), (30, (0, 0, 1)),
+     (2, (0, 0, 0))],
+    [(1, (3, 0, 3)), (1, (1, 1, 4)), (-1, (3, 0, 2)), (1, (1, 0, 4)), (-12, (0, 2, 3)),
+     (-6, (2, 1, 1)), (3, (2, 0, 2)), (-1, (1, 1, 2)), (-1, (0, 2, 2)), (-10, (0, 1, 3)),
+     (-7, (2, 0, 1)), (-12, (1, 1, 1)), (-2, (1, 0, 2)), (-1, (0, 1, 2)), (2, (0, 0, 3)),
+     (-1, (1, 1, 0)), (-9, (1, 0, 1)), (7, (0, 2, 0)), (10, (0, 1, 1)), (-1, (1, 0, 0)),
+     (15, (0, 1, 0)), (8, (0, 0, 1)), (8, (0, 0, 0))],
+    [(1, (3, 1, 2)), (-1, (3, 0, 2)), (1, (1, 0, 4)), (1, (2, 1, 1)), (-12, (0, 1, 3)),
+     (-7, (2, 0, 1)), (-1, (1, 1, 1)), (-1, (1, 0, 2)), (-1, (0, 1, 2)), (2, (0, 0, 3)),
+     (-11, (1, 0, 1)), (-1, (1, 0, 0)), (7, (0, 1, 0)), (10, (0, 0, 1)), (8, (0, 0, 0))],
+]
+
+
+def sqrt_bounds(n: int, c: int):
+    """The binary64 numbers next to c * sqrt(n) below and above (equal when exact)."""
+    from fractions import Fraction
+    import math
+
+    t = Fraction(c * c * n)  # (c sqrt(n))^2
+    x = math.sqrt(c * c * n)
+    lo = x
+    while lo > 0 and Fraction(lo) ** 2 > t:
+        lo = math.nextafter(lo, 0.0)
+    while Fraction(math.nextafter(lo, math.inf)) ** 2 <= t:
+        lo = math.nextafter(lo, math.inf)
+    hi = lo if Fraction(lo) ** 2 == t else math.nextafter(lo, math.inf)
+    if c < 0:
+        lo, hi = -hi, -lo
+    return lo, hi
+
+
+def robotics(depth: int = 6) -> System:
+    """System (R) of Sec. 4.2 on [-1,1]^4 (each quaternion coordinate of a unit quaternion):
+    the first equation's sqrt(3) coefficients become binary64 intervals [RD, RU]."""
+    e = np.array([t[2] for t in ROBOTICS_F1], dtype=np.int32)
+    lo = np.empty(len(ROBOTICS_F1))
+    hi = np.empty(len(ROBOTICS_F1))
+    for i, (c, r3, _) in enumerate(ROBOTICS_F1):
+        lo[i], hi[i] = sqrt_bounds(3, c) if r3 else (float(c), float(c))
+    sphere = (np.array([[2, 0, 0, 0], [0, 2, 0, 0], [0, 0, 2, 0], [0, 0, 0, 2], [0, 0, 0, 0]],
+                       dtype=np.int32), np.array([1.0, 1.0, 1.0, 1.0, -1.0]))
+    return System("robotics-R", 4, [(e, lo), sphere], cube(4), depth, his=[hi, None],
+                  rel=[REL_EQ, REL_EQ])
+
+
+def complex_to_real(terms, nz: int):
+    """Real and imaginary parts of sum c z^a with z_j = x_j + i y_j, as polynomials in
+    (x_1, y_1, ..., x_nz, y_nz) with exact integer coefficients: two dicts exps -> int."""
+    from math import comb
+
+    re, im = {}, {}
+    for c, a in terms:
+        # prod_j (x_j + i y_j)^{a_j} = sum over b_j <= a_j of prod C(a_j, b_j) x^(a-b) (i y)^b
+        parts = [[]]
+        for j in range(nz):
+            parts = [p + [b] for p in parts for b in range(a[j] + 1)]
+        for bs in parts:
+            coef = c
+            ex = []
+            for j in range(nz):
+                coef *= comb(a[j], bs[j])
+                ex += [a[j] - bs[j], bs[j]]
+            ipow = sum(bs) % 4  # i^sum(b)
+            sgn = 1 if ipow in (0, 1) else -1
+            tgt = re if ipow % 2 == 0 else im
+            key = tuple(ex)
+            tgt[key] = tgt.get(key, 0) + sgn * coef
+    clean = [{k: v for k, v in d.items() if v != 0} for d in (re, im)]
+    return clean[0], clean[1]
+
+
+def _poly_of(d: dict, k: int):
+    keys = sorted(d)
+    e = np.array(keys, dtype=np.int32).reshape(-1, k)
+    c = np.array([float(d[t]) for t in keys])
+    return e, c
+
+
+def automatic(depth: int = 8) -> System:
+    """System (A) of Sec. 4.2 with z_j = x_j + i y_j: eight real equations (real and
+    imaginary parts) and the three inequalities x_j^2 + y_j^2 - 1 <= 0, variables
+    (x1, y1, x2, y2, x3, y3) on [-1,1]^6."""
+    polys, rel = [], []
+    for terms in AUTOMATIC_Z:
+        re, im = complex_to_real(terms, 3)
+        polys += [_poly_of(re, 6), _poly_of(im, 6)]
+        rel += [REL_EQ, REL_EQ]
+    for j in range(3):
+        disk = {tuple(2 if i == 2 * j else 0 for i in range(6)): 1,
+                tuple(2 if i == 2 * j + 1 else 0 for i in range(6)): 1, (0,) * 6: -1}
+        polys.append(_poly_of(disk, 6))
+        rel.append(REL_LE)
+    return System("automatic-A", 6, polys, cube(6), depth, his=[None] * len(polys), rel=rel)

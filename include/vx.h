@@ -44,7 +44,7 @@ extern "C" {
 #define VX_ETIMEOUT (-5)  /* a bounded device wait gave up */
 #define VX_ECUDA (-6)     /* a CUDA runtime call failed */
 
-#define VX_KMAX 4
+#define VX_KMAX 6
 #define VX_MAXPOLY 16
 #define VX_MAXLEVEL 24
 
@@ -58,6 +58,16 @@ extern "C" {
                           * farther than that bound from deciding C0 either way is decided in
                           * binary32, the others are re-evaluated in VX_FP64, so every keep
                           * decision equals the VX_FP64 one */
+
+/* Relation of a polynomial F of a system of equations and inequalities (Sec. 4: the input is
+ * equations and inequalities).  C0 drops a box when F's enclosure on it proves the relation
+ * false on the whole box: VX_EQ when 0 is outside, VX_LE when lo > 0, VX_GE when hi < 0,
+ * VX_LT when lo >= 0, VX_GT when hi <= 0. */
+#define VX_EQ 0 /* F = 0 */
+#define VX_LE 1 /* F <= 0 */
+#define VX_GE 2 /* F >= 0 */
+#define VX_LT 3 /* F < 0 */
+#define VX_GT 4 /* F > 0 */
 
 /* Inclusion criteria C1 for one equation (Sec. 3.2, "Inclusion Criterion"); a box C1
  * certifies holds a zero of F (F has certified opposite signs at two of its points). */
@@ -114,6 +124,15 @@ const char *vx_last_error(void);
  * that Algorithm 1 runs along contiguous rows).  The system holds device memory until
  * vx_system_free. */
 int vx_system_create(const vx_poly *F_list, int32_t npoly, void *stream, vx_system **out);
+/* vx_system_create for a system of equations and inequalities with interval coefficients
+ * (Sec. 4; coefficients such as sqrt(3) enter as the binary64 interval around them):
+ * coefs_hi (nullable; entries nullable) gives per polynomial the upper ends of its
+ * coefficients, F_list[f].coefs being the lower ends (lower <= upper, both finite); rel
+ * (nullable: all VX_EQ) the relation of each polynomial.  Every path honours both, except
+ * the tensor-core dense level (vx_dense_plan_create refuses such systems) and C1 (one
+ * equation only). */
+int vx_system_create_ex(const vx_poly *F_list, const double *const *coefs_hi,
+                        const int32_t *rel, int32_t npoly, void *stream, vx_system **out);
 void vx_system_free(vx_system *sys);
 /* k and npoly of a system; h_M (nullable) receives [npoly][k+1] the number of coefficients
  * each partial-evaluation stage reads: M_{j} for j = 0..k, with missing suffix monomials below

@@ -223,7 +223,7 @@ static int make_grid(int k, const double *dom, int level, LevelGrid *g) {
 struct HostStage {
   int32_t nfib = 0, maxlen = 0;
   int64_t blk_in = 0, blk_out = 0;
-  std::vector<uint64_t> keys;  // fibre monomial in x_{s+2}..x_k, 16 bits per exponent
+  std::vector<uint64_t> keys;  // fibre monomial in x_{s+2}..x_k, key_bits(k) bits per exponent
   std::vector<int32_t> rowoff, fiblen, outpos;
   std::unordered_map<uint64_t, int32_t> index;
 };
@@ -235,9 +235,14 @@ struct HostPoly {
   std::vector<float4> c32c;
 };
 
+// A monomial in up to k - 1 variables packed into 64 bits: 16 bits per exponent up to
+// k = 5, 64 / (k - 1) bits beyond (12 bits at k = 6).
+static int key_bits(int k) { return k <= 5 ? 16 : 64 / (k - 1); }
+
 static uint64_t suffix_key(const int32_t *e, int from, int k) {
+  const int b = key_bits(k);
   uint64_t key = 0;
-  for (int v = from; v < k; ++v) key = (key << 16) | (uint64_t)e[v];
+  for (int v = from; v < k; ++v) key = (key << b) | (uint64_t)e[v];
   return key;
 }
 
@@ -307,9 +312,10 @@ static int pack_poly(int k, const vx_poly &p, HostPoly *hp, const double *chi = 
     set_error("polynomial: nvars %d (expected %d), nterms %d", p.nvars, k, nt);
     return VX_EINVAL;
   }
+  const int32_t emax = (1 << key_bits(k)) - 1;
   for (int64_t t = 0; t < (int64_t)nt * k; ++t) {
-    if (p.exps[t] < 0 || p.exps[t] > 65535) {
-      set_error("polynomial: exponent %d outside [0, 65535]", p.exps[t]);
+    if (p.exps[t] < 0 || p.exps[t] > emax) {
+      set_error("polynomial: exponent %d outside [0, %d]", p.exps[t], emax);
       return VX_EINVAL;
     }
   }
@@ -378,7 +384,7 @@ static int pack_poly(int k, const vx_poly &p, HostPoly *hp, const double *chi = 
       std::vector<uint64_t> &nk = hp->st[s - 1].keys;
       nk.clear();
       nk.reserve(S.blk_in);
-      const int sh = 16 * (k - 1 - s);
+      const int sh = key_bits(k) * (k - 1 - s);
       for (int32_t f = 0; f < nf; ++f)
         for (int32_t a = 0; a < S.fiblen[f]; ++a) nk.push_back(((uint64_t)a << sh) | S.keys[f]);
     }
@@ -389,7 +395,7 @@ static int pack_poly(int k, const vx_poly &p, HostPoly *hp, const double *chi = 
     S.outpos.assign(S.nfib, 0);
     if (s + 1 < k) {
       const HostStage &T = hp->st[s + 1];
-      const int sh = 16 * (k - 2 - s);
+      const int sh = key_bits(k) * (k - 2 - s);
       const uint64_t mask = sh ? ((uint64_t)1 << sh) - 1 : 0;
       for (int32_t f = 0; f < S.nfib; ++f) {
         const uint64_t a = S.keys[f] >> sh;
@@ -487,6 +493,7 @@ struct vx_system {
   // the polynomials as given (exponents [nterms][k], coefficients), for dense-level plans
   std::vector<std::vector<int32_t>> exps;
   std::vector<std::vector<double>> coefs;
+  std::vector<std::vector<double>> coefs_hi;  // upper ends of interval coefficients (or empty)
   // Taylor forms (Def. 3): per order m, per polynomial, the system of its G_a, made on first use
   struct TaylorSet {
     vx_system *sys = nullptr;
@@ -566,21 +573,32 @@ extern "C" {
 const char *vx_last_error(void) { return g_err; }
 
 static int system_create_impl(const vx_poly *F, int32_t npoly, const double *const *chi,
-                              void *stream, vx_system **out);
+                              void *stream, vx_system **out, const int32_t *rel = nullptr);
 
 int vx_system_create(const vx_poly *F, int32_t npoly, void *stream, vx_system **out) {
   clear_error();
   return system_create_impl(F, npoly, nullptr, stream, out);
 }
 
-// chi (nullable): per polynomial, the upper ends of interval coefficients (F[f].coefs the
-// lower ends).
+int vx_system_create_ex(const vx_poly *F, const double *const *coefs_hi, const int32_t *rel,
+                        int32_t npoly, void *stream, vx_system **out) {
+  clear_error();
+  return system_create_impl(F, npoly, coefs_hi, stream, out, rel);
+}
+
+// chi (nullable; entries nullable): per polynomial, the upper ends of interval coefficients
+// (F[f].coefs the lower ends); rel (nullable): the relation of each polynomial.
 static int system_create_impl(const vx_poly *F, int32_t npoly, const double *const *chi,
-                              void *stream, vx_system **out) {
+                              void *stream, vx_system **out, const int32_t *rel) {
   if (!out || !F || npoly < 1 || npoly > VX_MAXPOLY) {
     set_error("vx_system_create: need 1..%d polynomials and an out pointer", VX_MAXPOLY);
     return VX_EINVAL;
   }
+  for (int f = 0; rel && f < npoly; ++f)
+    if (rel[f] < VX_EQ || rel[f] > VX_GT) {
+      set_error("vx_system_create: polynomial %d has an unknown relation %d", f, rel[f]);
+      return VX_EINVAL;
+    }
   *out = nullptr;
   const int k = F[0].nvars;
   if (k < 1 || k > VX_KMAX) {
@@ -637,12 +655,15 @@ static int system_create_impl(const vx_poly *F, int32_t npoly, const double *con
   sys->bytes = bytes;
   sys->dev.k = k;
   sys->dev.npoly = npoly;
+  for (int f = 0; f < npoly; ++f) sys->dev.rel[f] = (int8_t)(rel ? rel[f] : VX_EQ);
   sys->M.assign((size_t)npoly * (k + 1), 1);
   sys->exps.resize(npoly);
   sys->coefs.resize(npoly);
+  sys->coefs_hi.resize(npoly);
   for (int f = 0; f < npoly; ++f) {
     sys->exps[f].assign(F[f].exps, F[f].exps + (size_t)F[f].nterms * k);
     sys->coefs[f].assign(F[f].coefs, F[f].coefs + F[f].nterms);
+    if (chi && chi[f]) sys->coefs_hi[f].assign(chi[f], chi[f] + F[f].nterms);
   }
   size_t off = 0;
   char *dbase = (char *)sys->mem;
@@ -868,6 +889,11 @@ int vx_dense_plan_create(const vx_system *sys, int32_t level, const double *h_do
               sys->dev.k);
     return VX_EINVAL;
   }
+  for (int f = 0; f < sys->dev.npoly; ++f)
+    if (sys->dev.rel[f] != VX_EQ || !sys->coefs_hi[f].empty()) {
+      set_error("vx_dense_plan_create: equations with point coefficients only");
+      return VX_EINVAL;
+    }
   LevelGrid g;
   VX_CHECK(make_grid(3, h_domain, level, &g));  // the same domains as the interval path
   std::vector<DenseHostPoly> hp(sys->dev.npoly);
@@ -1054,6 +1080,7 @@ static int taylor_sets(const vx_system *csys, int m, cudaStream_t s,
   for (int f = 0; f < sys->dev.npoly && rc == VX_OK; ++f) {
     const std::vector<int32_t> &E = sys->exps[f];
     const std::vector<double> &Cf = sys->coefs[f];
+    const std::vector<double> &Ch = sys->coefs_hi[f].empty() ? Cf : sys->coefs_hi[f];
     const int64_t nt = (int64_t)Cf.size();
     const int na = (int)alpha.size();
     std::vector<std::vector<int32_t>> de(na);
@@ -1076,8 +1103,9 @@ static int taylor_sets(const vx_system *csys, int m, cudaStream_t s,
           break;
         }
         const double c = Cf[t], p = c * C, err = std::fma(c, C, -p);
+        const double ch = Ch[t], ph = ch * C, errh = std::fma(ch, C, -ph);
         lo[a].push_back(err < 0 ? std::nextafter(p, -INFINITY) : p);
-        hi[a].push_back(err > 0 ? std::nextafter(p, INFINITY) : p);
+        hi[a].push_back(errh > 0 ? std::nextafter(ph, INFINITY) : ph);
         for (int i = 0; i < k; ++i) de[a].push_back(E[t * k + i] - alpha[a][i]);
       }
     if (rc != VX_OK) break;
@@ -1111,8 +1139,8 @@ static int eval_taylor_level(const vx_system *sys, const CsfView &c, const Level
       set_error("axis %d: the box centres of level %d are not binary64 numbers", d, c.level);
       return VX_EINVAL;
     }
-  if (inc && sys->dev.npoly != 1) {
-    set_error("C1 is a test for one equation (the system has %d)", sys->dev.npoly);
+  if (inc && (sys->dev.npoly != 1 || sys->dev.rel[0] != VX_EQ)) {
+    set_error("C1 is a test for one equation");
     return VX_EINVAL;
   }
   std::vector<vx_system::TaylorSet> *sets = nullptr;
@@ -1126,7 +1154,7 @@ static int eval_taylor_level(const vx_system *sys, const CsfView &c, const Level
       for (int d = 0; d < VX_KMAX; ++d) al[a * VX_KMAX + d] = ts.alpha[a][d];
     int64_t w = 0;
     VX_CHECK(eval_level_taylor(ts.sys->dev, (const int8_t(*)[VX_KMAX])al.data(), m, c, g, keep,
-                               f == 0, d_lo ? d_lo + (int64_t)f * n : nullptr,
+                               f == 0, sys->dev.rel[f], d_lo ? d_lo + (int64_t)f * n : nullptr,
                                d_hi ? d_hi + (int64_t)f * n : nullptr, inc, s, tm, &w));
     *madds += w;
   }
@@ -1165,8 +1193,8 @@ int vx_csf_c1(const vx_system *sys, const vx_csf *c, const double *h_domain, int
     set_error("vx_csf_c1: bad arguments");
     return VX_EINVAL;
   }
-  if (sys->dev.npoly != 1) {
-    set_error("vx_csf_c1: C1 is a test for one equation (the system has %d)", sys->dev.npoly);
+  if (sys->dev.npoly != 1 || sys->dev.rel[0] != VX_EQ) {
+    set_error("vx_csf_c1: C1 is a test for one equation");
     return VX_EINVAL;
   }
   LevelGrid g;
@@ -1305,7 +1333,8 @@ int vx_csf_compact(const vx_csf *in, const uint8_t *d_keep, int32_t *d_index, vo
 // Algorithm 3: the level loop
 // ---------------------------------------------------------------------------------------
 static int level0(int k, cudaStream_t s, CsfObj *o) {
-  int64_t N[VX_KMAX] = {1, 1, 1, 1};
+  int64_t N[VX_KMAX];
+  for (int d = 0; d < VX_KMAX; ++d) N[d] = 1;
   VX_CHECK(csf_alloc(o, k, 0, N, s));
   // one box (0, ..., 0): labels 0, parents 0, child ranges [0, 1)
   VX_CUDA(cudaMemsetAsync(o->mem, 0, o->bytes, s));
@@ -1359,7 +1388,8 @@ static int enclose_impl(const vx_system *sys, const double *dom, int depth, cons
       set_error("vx_enclose: unknown inclusion criterion %d", opts.c1);
       return VX_EINVAL;
     }
-    if (opts.mode != VX_FP64 || sys->dev.npoly != 1 || opts.c1_level < 0 ||
+    if (opts.mode != VX_FP64 || sys->dev.npoly != 1 || sys->dev.rel[0] != VX_EQ ||
+        opts.c1_level < 0 ||
         (opts.c1 == VX_C1_TAYLOR && opts.taylor_order < 2)) {
       set_error("vx_enclose: C1 needs one equation, VX_FP64, c1_level >= 0 and, for "
                 "VX_C1_TAYLOR, taylor_order >= 2");
@@ -1796,7 +1826,8 @@ int batch_group(const std::vector<int32_t> &ids, const vx_poly *const *systems,
   // level 0: one box per tree
   Forest cur;
   if (rc == VX_OK) {
-    int64_t N[VX_KMAX] = {S, S, S, S};
+    int64_t N[VX_KMAX];
+    for (int d = 0; d < VX_KMAX; ++d) N[d] = S;
     rc = csf_alloc(&cur.c, k, 0, N, s);
     if (rc == VX_OK) {
       k_forest_level0<<<grid1(S + 1), 256, 0, s>>>(cur.c.v, S);

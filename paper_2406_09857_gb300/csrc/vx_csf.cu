@@ -589,7 +589,9 @@ void launch_kptr(int d, int blocks, cudaStream_t s, const CsfView &in, const uin
   switch (d) {
     case 0: k_kptr<0><<<blocks, 256, 0, s>>>(in, flags, rank, sg, kptr); break;
     case 1: k_kptr<1><<<blocks, 256, 0, s>>>(in, flags, rank, sg, kptr); break;
-    default: k_kptr<2><<<blocks, 256, 0, s>>>(in, flags, rank, sg, kptr); break;
+    case 2: k_kptr<2><<<blocks, 256, 0, s>>>(in, flags, rank, sg, kptr); break;
+    case 3: k_kptr<3><<<blocks, 256, 0, s>>>(in, flags, rank, sg, kptr); break;
+    default: k_kptr<4><<<blocks, 256, 0, s>>>(in, flags, rank, sg, kptr); break;
   }
 }
 
@@ -599,7 +601,9 @@ void launch_gather(int d, int blocks, cudaStream_t s, const CsfView &in, const u
     case 0: k_gather<0><<<blocks, 256, 0, s>>>(in, flags, rank, sg, out, index); break;
     case 1: k_gather<1><<<blocks, 256, 0, s>>>(in, flags, rank, sg, out, index); break;
     case 2: k_gather<2><<<blocks, 256, 0, s>>>(in, flags, rank, sg, out, index); break;
-    default: k_gather<3><<<blocks, 256, 0, s>>>(in, flags, rank, sg, out, index); break;
+    case 3: k_gather<3><<<blocks, 256, 0, s>>>(in, flags, rank, sg, out, index); break;
+    case 4: k_gather<4><<<blocks, 256, 0, s>>>(in, flags, rank, sg, out, index); break;
+    default: k_gather<5><<<blocks, 256, 0, s>>>(in, flags, rank, sg, out, index); break;
   }
 }
 
@@ -610,7 +614,9 @@ void launch_split(int d, int blocks, cudaStream_t s, const CsfView &in, const ui
     case 0: k_split<KK, 0><<<blocks, 256, 0, s>>>(in, flags, rank, sg, K, out); break;
     case 1: if (KK > 1) k_split<KK, (KK > 1 ? 1 : 0)><<<blocks, 256, 0, s>>>(in, flags, rank, sg, K, out); break;
     case 2: if (KK > 2) k_split<KK, (KK > 2 ? 2 : 0)><<<blocks, 256, 0, s>>>(in, flags, rank, sg, K, out); break;
-    default: if (KK > 3) k_split<KK, (KK > 3 ? 3 : 0)><<<blocks, 256, 0, s>>>(in, flags, rank, sg, K, out); break;
+    case 3: if (KK > 3) k_split<KK, (KK > 3 ? 3 : 0)><<<blocks, 256, 0, s>>>(in, flags, rank, sg, K, out); break;
+    case 4: if (KK > 4) k_split<KK, (KK > 4 ? 4 : 0)><<<blocks, 256, 0, s>>>(in, flags, rank, sg, K, out); break;
+    default: if (KK > 5) k_split<KK, (KK > 5 ? 5 : 0)><<<blocks, 256, 0, s>>>(in, flags, rank, sg, K, out); break;
   }
 }
 
@@ -848,7 +854,9 @@ int csf_build_dev(int k, int level, const int32_t *d_tuples, int64_t n, cudaStre
     case 1: return build_c<1>(k, level, d_tuples, n, s, out, tm);
     case 2: return build_c<2>(k, level, d_tuples, n, s, out, tm);
     case 3: return build_c<3>(k, level, d_tuples, n, s, out, tm);
-    default: return build_c<4>(k, level, d_tuples, n, s, out, tm);
+    case 4: return build_c<4>(k, level, d_tuples, n, s, out, tm);
+    case 5: return build_c<5>(k, level, d_tuples, n, s, out, tm);
+    default: return build_c<6>(k, level, d_tuples, n, s, out, tm);
   }
 }
 
@@ -858,7 +866,9 @@ int csf_prune(const CsfView &in, const uint8_t *d_keep, int split, int32_t *d_in
     case 1: return prune_c<1>(in, d_keep, split, d_index, s, out, tm);
     case 2: return prune_c<2>(in, d_keep, split, d_index, s, out, tm);
     case 3: return prune_c<3>(in, d_keep, split, d_index, s, out, tm);
-    default: return prune_c<4>(in, d_keep, split, d_index, s, out, tm);
+    case 4: return prune_c<4>(in, d_keep, split, d_index, s, out, tm);
+    case 5: return prune_c<5>(in, d_keep, split, d_index, s, out, tm);
+    default: return prune_c<6>(in, d_keep, split, d_index, s, out, tm);
   }
 }
 
@@ -869,7 +879,9 @@ int csf_prune_forest(const CsfView &in, const uint8_t *d_keep, int split, int32_
     case 1: return prune_c<1>(in, d_keep, split, d_index, s, out, tm, d_seg_off, nseg, d_seg_kept);
     case 2: return prune_c<2>(in, d_keep, split, d_index, s, out, tm, d_seg_off, nseg, d_seg_kept);
     case 3: return prune_c<3>(in, d_keep, split, d_index, s, out, tm, d_seg_off, nseg, d_seg_kept);
-    default: return prune_c<4>(in, d_keep, split, d_index, s, out, tm, d_seg_off, nseg, d_seg_kept);
+    case 4: return prune_c<4>(in, d_keep, split, d_index, s, out, tm, d_seg_off, nseg, d_seg_kept);
+    case 5: return prune_c<5>(in, d_keep, split, d_index, s, out, tm, d_seg_off, nseg, d_seg_kept);
+    default: return prune_c<6>(in, d_keep, split, d_index, s, out, tm, d_seg_off, nseg, d_seg_kept);
   }
 }
 

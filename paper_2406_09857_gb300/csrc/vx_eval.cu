@@ -101,6 +101,18 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity
   return false;
 }
 
+// C0 for one relation of a system of equations and inequalities: the enclosure [lo, hi]
+// proves the relation false on the whole box (a NaN end proves nothing).
+__device__ __forceinline__ bool rel_drops(double lo, double hi, int rel) {
+  switch (rel) {
+    case VX_LE: return lo > 0.0;
+    case VX_GE: return hi < 0.0;
+    case VX_LT: return lo >= 0.0;
+    case VX_GT: return hi <= 0.0;
+    default: return lo > 0.0 || hi < 0.0;
+  }
+}
+
 // ---------------------------------------------------------------------------------------
 // binary64 intervals
 // ---------------------------------------------------------------------------------------
@@ -134,8 +146,11 @@ struct A64 {
     return make_double2(__dadd_rd(lo, A.x), __dadd_ru(hi, A.y));
   }
   static __device__ __forceinline__ V store(V J) { return J; }
-  // 0: excluded, 1: kept (C0 of Sec. 3.2: excluded iff 0 is provably outside)
-  static __device__ __forceinline__ int classify(V J) { return (J.x > 0.0 || J.y < 0.0) ? 0 : 1; }
+  // 0: excluded, 1: kept (C0 of Sec. 3.2: excluded iff the enclosure proves the relation
+  // false on the box; for an equation, iff 0 is provably outside)
+  static __device__ __forceinline__ int classify(V J, int rel) {
+    return rel_drops(J.x, J.y, rel) ? 0 : 1;
+  }
   static __device__ __forceinline__ double lo(V J) { return J.x; }
   static __device__ __forceinline__ double hi(V J) { return J.y; }
   static __device__ __forceinline__ bool tight(V, float) { return false; }
@@ -180,7 +195,10 @@ struct A32 {
     return make_float2(m, r);
   }
   static __device__ __forceinline__ V store(V J) { return make_float2(J.x, __fadd_ru(J.y, kEta32)); }
-  static __device__ __forceinline__ int classify(V J) { return (fabsf(J.x) > J.y) ? 0 : 1; }
+  static __device__ __forceinline__ int classify(V J, int rel) {
+    if (rel == VX_EQ) return (fabsf(J.x) > J.y) ? 0 : 1;
+    return rel_drops(lo(J), hi(J), rel) ? 0 : 1;  // [m - r, m + r] rounded outward
+  }
   static __device__ __forceinline__ double lo(V J) { return __dadd_rd((double)J.x, -(double)J.y); }
   static __device__ __forceinline__ double hi(V J) { return __dadd_ru((double)J.x, (double)J.y); }
   static __device__ __forceinline__ bool tight(V J, float theta) { return fabsf(J.x) >= theta * J.y; }
@@ -266,11 +284,26 @@ struct A32C {
   static __device__ __forceinline__ V store(V J) {
     return make_float4(J.x, J.y, __fadd_ru(__fmaf_ru(J.z, k2m40, J.z), kEta148), 0.f);
   }
-  // 0: the binary64 path surely excludes, 1: surely keeps, 2: inside the error band
-  static __device__ __forceinline__ int classify(V J) {
-    if (J.x > J.z || J.y > J.z) return 0;      // lo > E or hi < -E
-    if (J.x <= -J.z && J.y <= -J.z && J.z < INFINITY) return 1;  // lo <= -E, hi >= E, E finite
-    return 2;
+  // 0: the binary64 path surely excludes, 1: surely keeps, 2: inside the error band.  With
+  // |lo32 - lo64| <= E and |hi32 - hi64| <= E: lo64 > 0 is sure when lo32 > E, lo64 <= 0 when
+  // lo32 <= -E, lo64 >= 0 when lo32 >= E, lo64 < 0 when lo32 < -E (the same for hi, whose
+  // negation J.y is stored).
+  static __device__ __forceinline__ int classify(V J, int rel) {
+    const bool fin = J.z < INFINITY;
+    switch (rel) {
+      case VX_LE:  // drop iff lo64 > 0
+        return J.x > J.z ? 0 : ((J.x <= -J.z && fin) ? 1 : 2);
+      case VX_GE:  // drop iff hi64 < 0
+        return J.y > J.z ? 0 : ((J.y <= -J.z && fin) ? 1 : 2);
+      case VX_LT:  // drop iff lo64 >= 0
+        return J.x >= J.z ? 0 : ((J.x < -J.z && fin) ? 1 : 2);
+      case VX_GT:  // drop iff hi64 <= 0
+        return J.y >= J.z ? 0 : ((J.y < -J.z && fin) ? 1 : 2);
+      default:
+        if (J.x > J.z || J.y > J.z) return 0;                   // lo > E or hi < -E
+        if (J.x <= -J.z && J.y <= -J.z && fin) return 1;       // lo <= -E, hi >= E, E finite
+        return 2;
+    }
   }
   static __device__ __forceinline__ double lo(V J) { return (double)J.x; }
   static __device__ __forceinline__ double hi(V J) { return -(double)J.y; }
@@ -457,6 +490,7 @@ struct LeafArgs {
                                // when k == 1)
   int64_t blk[VX_MAXPOLY];     // entries per parent block (0 when k == 1)
   int32_t len[VX_MAXPOLY];
+  int8_t rel[VX_MAXPOLY];      // VX_EQ .. VX_GT per polynomial
 };
 
 // Last stage on leaf i: one Horner per polynomial, then C0 (par: parent indices, minus poff
@@ -478,7 +512,7 @@ __device__ __forceinline__ void leaf_item(const LeafArgs &A, int npoly,
       lo[(int64_t)f * nleaves + i] = AR::lo(J);
       hi[(int64_t)f * nleaves + i] = AR::hi(J);
     }
-    const int c = AR::classify(J);
+    const int c = AR::classify(J, A.rel[f]);
     excl = excl || c == 0;
     amb = amb || c == 2;
     tg = tg || AR::tight(J, theta);
@@ -647,6 +681,7 @@ struct TaylorLeaf {
   double r[VX_KMAX];  // half-widths of the level's boxes, per axis
   int32_t first;      // 1: write keep, 0: AND into it (several polynomials)
   double *lo, *hi;    // nullable: T per leaf
+  int32_t rel;        // the polynomial's relation (VX_EQ .. VX_GT)
   int32_t c1;         // nonzero: write inc (C1 on the Taylor form)
   int8_t ei[VX_KMAX]; // index of the multi-index e_i
   uint8_t *inc;
@@ -693,7 +728,7 @@ __global__ void __launch_bounds__(kThreads)
       T.lo[i] = acc.x;
       T.hi[i] = acc.y;
     }
-    const uint8_t k0 = (acc.x > 0.0 || acc.y < 0.0) ? 0 : 1;
+    const uint8_t k0 = rel_drops(acc.x, acc.y, T.rel) ? 0 : 1;
     keep[i] = T.first ? k0 : (uint8_t)(keep[i] & k0);
     if (T.c1) {
       double v[VX_KMAX];
@@ -893,7 +928,7 @@ __device__ __forceinline__ void leaf_tile_c(const LeafArgs &A, int npoly,
       lo[(int64_t)f * nleaves + i] = A32C::lo(J);
       hi[(int64_t)f * nleaves + i] = A32C::hi(J);
     }
-    const int r = A32C::classify(J);
+    const int r = A32C::classify(J, A.rel[f]);
     if (c == 0) {
       excl0 = excl0 || r == 0;
       amb0 = amb0 || r == 2;
@@ -1239,10 +1274,11 @@ int eval_level_t(const SysDev &sys, const CsfView &c, const LevelGrid &grid, dou
     }
   }
   if (rc == VX_OK) {
-    LeafArgs A;
+    LeafArgs A{};
     int64_t wl = 0;
     for (int f = 0; f < sys.npoly; ++f) {
       const StageDev &st = sys.p[f].st[k - 1];
+      A.rel[f] = sys.rel[f];
       A.in[f] = k == 1 ? (const void *)AR::coef(sys.p[f]) : (const void *)buf[f][k - 2];
       A.blk[f] = k == 1 ? 0 : st.blk_in;
       A.len[f] = st.maxlen;
@@ -1378,6 +1414,7 @@ __global__ void __launch_bounds__(kThreads)
     const int npoly = T.dev.npoly;
     for (int f = 0; f < npoly; ++f) {
       const StageDev &st = T.dev.p[f].st[k - 1];
+      A.rel[f] = T.dev.rel[f];
       A.in[f] = k == 1 ? (const void *)AR::coef(T.dev.p[f])
                        : blk[((int64_t)t * VX_MAXPOLY + f) * VX_KMAX + k - 2];
       A.blk[f] = k == 1 ? 0 : st.blk_in;
@@ -1438,7 +1475,8 @@ int eval_forest_t(const ForestTree *d_trees, const ForestTree *h_trees, const in
   // warp-task queues: per depth, per tree, chunks of 32 nodes (64 in pairs) x G fibre groups
   std::vector<int64_t> tasks((size_t)k * (S + 1), 0);
   bool pairs[VX_KMAX] = {false};
-  int G[VX_KMAX] = {1, 1, 1, 1};
+  int G[VX_KMAX];
+  for (int d = 0; d < VX_KMAX; ++d) G[d] = 1;
   for (int d = 0; d < k; ++d) {
     const bool leaf = d + 1 == k;
     pairs[d] = std::is_same<AR, A32C>::value && (leaf || c.N[d] >= kPairNodes);
@@ -1518,7 +1556,7 @@ int eval_forest(int arith, const ForestTree *d_trees, const ForestTree *h_trees,
 }
 
 int eval_level_taylor(const SysDev &tsys, const int8_t (*alpha)[VX_KMAX], int m,
-                      const CsfView &c, const LevelGrid &grid, uint8_t *d_keep, int first,
+                      const CsfView &c, const LevelGrid &grid, uint8_t *d_keep, int first, int rel,
                       double *d_lo, double *d_hi, uint8_t *d_inc, cudaStream_t s, Timer *tm,
                       int64_t *madds) {
   const int k = c.k;
@@ -1527,6 +1565,7 @@ int eval_level_taylor(const SysDev &tsys, const int8_t (*alpha)[VX_KMAX], int m,
   tl.m = m;
   tl.k = k;
   tl.first = first;
+  tl.rel = rel;
   tl.lo = d_lo;
   tl.hi = d_hi;
   if (d_inc) {

@@ -71,6 +71,7 @@ struct PolyDev {
 struct SysDev {
   int32_t k, npoly;
   PolyDev p[VX_MAXPOLY];
+  int8_t rel[VX_MAXPOLY];  // relation of each polynomial: VX_EQ, VX_LE, VX_GE, VX_LT, VX_GT
 };
 
 // One axis of one grid level: box t is [lo + t*w, lo + (t+1)*w] (exact on accepted domains).
@@ -167,10 +168,11 @@ int eval_forest(int arith, const ForestTree *d_trees, const ForestTree *h_trees,
                 uint8_t *keep, uint8_t *flag, float theta, cudaStream_t s, int64_t *madds);
 // The Taylor form of order m (Def. 3) of one polynomial F on every leaf, in binary64: tsys
 // holds G_a = d^a F / a! for the multi-indices alpha[0..npoly-1] (|a| <= m, lexicographic);
-// keep = 0 in T (first = 1) or keep &= that (first = 0); d_lo/d_hi (nullable) receive T;
+// keep = C0 on T for the relation rel (first = 1) or keep &= that (first = 0); d_lo/d_hi
+// (nullable) receive T;
 // d_inc (nullable, m >= 2) receives the inclusion criterion C1 on the Taylor form.
 int eval_level_taylor(const SysDev &tsys, const int8_t (*alpha)[VX_KMAX], int m,
-                      const CsfView &c, const LevelGrid &grid, uint8_t *d_keep, int first,
+                      const CsfView &c, const LevelGrid &grid, uint8_t *d_keep, int first, int rel,
                       double *d_lo, double *d_hi, uint8_t *d_inc, cudaStream_t s, Timer *tm,
                       int64_t *madds);
 // The inclusion criterion C1 by vertex signs (Sec. 3.2) of the system's one polynomial on

@@ -16,9 +16,10 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "_build", "libvx.so")
 
 OK, EINVAL, ENOMEM, ECAPACITY, EOVERFLOW, ETIMEOUT, ECUDA = 0, -1, -2, -3, -4, -5, -6
-KMAX, MAXPOLY, MAXLEVEL = 4, 16, 24
+KMAX, MAXPOLY, MAXLEVEL = 6, 16, 24
 FP64, FP32_MIDRAD, FP32 = 0, 1, 2
 C1_TAYLOR, C1_VERTEX = 1, 2
+EQ, LE, GE, LT, GT = 0, 1, 2, 3, 4  # relation of a polynomial: F = 0, <= 0, >= 0, < 0, > 0
 
 _lib = None
 
@@ -56,6 +57,7 @@ def lib() -> ctypes.CDLL:
     sig = {
         "vx_last_error": ([], ctypes.c_char_p),
         "vx_system_create": ([P, i32, P, PP], i32),
+        "vx_system_create_ex": ([P, P, P, i32, P, PP], i32),
         "vx_system_free": ([P], None),
         "vx_system_info": ([P, P, P, P], i32),
         "vx_system_device_bytes": ([P, P], i32),
@@ -186,10 +188,25 @@ def make_opts(mode=FP64, fp64_final=False, fp64_recheck=False, theta=0.5, timing
 class System:
     """Polynomials packed and resident on the device (vx_system)."""
 
-    def __init__(self, polys, stream=None):
+    def __init__(self, polys, stream=None, his=None, rel=None):
+        """his (optional): per polynomial the upper ends of interval coefficients (None for
+        point coefficients); rel (optional): per polynomial EQ, LE, GE, LT or GT."""
         arr, keep = _polys(polys)
         h = ctypes.c_void_p()
-        _check(lib().vx_system_create(arr, len(polys), _stream(stream), ctypes.byref(h)))
+        if his is None and rel is None:
+            _check(lib().vx_system_create(arr, len(polys), _stream(stream), ctypes.byref(h)))
+        else:
+            hp = (ctypes.c_void_p * len(polys))()
+            for i in range(len(polys)):
+                if his is not None and his[i] is not None:
+                    a = np.ascontiguousarray(np.asarray(his[i], dtype=np.float64))
+                    if a.shape[0] != np.asarray(polys[i][1]).shape[0]:
+                        raise ValueError("his[%d] must match the coefficients" % i)
+                    keep.append(a)
+                    hp[i] = a.ctypes.data
+            rl = None if rel is None else np.ascontiguousarray(np.asarray(rel, dtype=np.int32))
+            _check(lib().vx_system_create_ex(arr, hp, None if rl is None else _np_ptr(rl),
+                                             len(polys), _stream(stream), ctypes.byref(h)))
         self.handle = h
         self.k = int(np.asarray(polys[0][0]).shape[1])
         self.npoly = len(polys)

@@ -23,6 +23,7 @@ from __future__ import annotations
 
 import argparse
 import json
+import math
 import os
 import statistics
 import subprocess
@@ -417,6 +418,46 @@ def bench_table1(vx, synth, torch, stream, taylor=True):
     return out
 
 
+PAPER_APPLICATIONS = {"robotics-R": {"voxelize_s": 0.1, "voxelize_boxes": 7228},
+                      "automatic-A": {"voxelize_s": 1.2, "voxelize_boxes": 0}}
+
+
+def bench_applications(vx, synth, torch, stream):
+    """The systems of Sec. 4.2 (equations, inequalities, sqrt(3) coefficients as intervals):
+    (R) to boxes of width 2^-4 and 2^-5 (depths 5 and 6 on [-1,1]^4), (A) until no box is left
+    (depth 6 on [-1,1]^6).  System resident; CUDA events; best of 3 after a warm-up."""
+    out = {}
+    for s, depths in ((synth.robotics(), (5, 6)), (synth.automatic(), (6,))):
+        sysv = vx.System(s.polys, stream=stream, his=s.his, rel=s.rel)
+        cell = {"k": s.k, "polys": len(s.polys),
+                "inequalities": int(sum(1 for r in s.rel if r != synth.REL_EQ)),
+                "paper": PAPER_APPLICATIONS[s.name]}
+        for depth in depths:
+            runs = [("fp32", vx.make_opts(vx.FP32)), ("fp64", vx.make_opts(vx.FP64))]
+            if math.comb(2 + s.k, s.k) <= vx.MAXPOLY:  # the order-2 form's derivatives
+                runs.append(("taylor2_fp64", vx.make_opts(vx.FP64, taylor_order=2)))
+            for name, opts in runs:
+                vx.enclose_system(sysv, s.domain, depth, opts, stream=stream).free()
+                best, st = None, None
+                for _ in range(3):
+                    e0 = torch.cuda.Event(enable_timing=True)
+                    e1 = torch.cuda.Event(enable_timing=True)
+                    e0.record(stream)
+                    r = vx.enclose_system(sysv, s.domain, depth, opts, stream=stream)
+                    e1.record(stream)
+                    e1.synchronize()
+                    ms = e0.elapsed_time(e1)
+                    if best is None or ms < best:
+                        best, st = ms, r.stats()
+                    r.free()
+                cell["depth%d_%s" % (depth, name)] = {
+                    "ms": round(best, 3), "boxes": int(st["kept"][-1]),
+                    "box_evals": int(st["tested"].sum())}
+        out[s.name] = cell
+        sysv.free()
+    return out
+
+
 def bench_batch(vx, synth, torch, workers=16):
     """Config 4: 256 independent systems (128 bivariate single equations of degree 10..60 and
     128 trivariate pairs of degree 10..40, depths 8..10) through vx_enclose_batch, from host
@@ -653,6 +694,7 @@ def run_gpu(args):
         extra["batch"] = bench_batch(vx, synth, torch)
         extra["precision"] = bench_precision(vx, synth, torch)
         extra["table1"] = bench_table1(vx, synth, torch, stream)
+        extra["applications"] = bench_applications(vx, synth, torch, stream)
 
     # ---- CPU oracle on a bounded sample ------------------------------------------------------
     cpu = None

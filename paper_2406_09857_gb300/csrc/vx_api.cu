@@ -288,21 +288,22 @@ static float4 to_certified_ivl(double lo, double hi) {
   if (lo == hi) return to_certified(lo);
   const float flo = f32_round_down(lo), fhi = f32_round_up(hi);
   if (!std::isfinite(flo) || !std::isfinite(fhi))
-    return make_float4(-INFINITY, -INFINITY, INFINITY, 0.f);
+    return make_float4(-INFINITY, -INFINITY, INFINITY, INFINITY);
   const double d = std::max(lo - (double)flo, (double)fhi - hi);  // exact
   const double mag = std::max(std::fabs(lo), std::fabs(hi));
   const double bound = (d + std::ldexp(mag, -23)) * (1.0 + std::ldexp(1.0, -39));
   const float e = f32_round_up(bound + std::ldexp(1.0, -148));
-  return make_float4(flo, -fhi, e, 0.f);
+  return make_float4(flo, -fhi, e, e);
 }
 
 static float4 to_certified(double c) {
   const float lo = f32_round_down(c), hi = f32_round_up(c);
-  if (!std::isfinite(lo) || !std::isfinite(hi)) return make_float4(-INFINITY, -INFINITY, INFINITY, 0.f);
+  if (!std::isfinite(lo) || !std::isfinite(hi))
+    return make_float4(-INFINITY, -INFINITY, INFINITY, INFINITY);
   const double d = std::max(c - (double)lo, (double)hi - c);  // exact
   const double bound = (d + std::ldexp(std::fabs(c), -23)) * (1.0 + std::ldexp(1.0, -39));
   const float e = f32_round_up(bound + std::ldexp(1.0, -148));
-  return make_float4(lo, -hi, e, 0.f);
+  return make_float4(lo, -hi, e, e);  // the bound twice (.z, .w): a pair for paired steps
 }
 
 // chi (nullable): upper ends of interval coefficients [p.coefs[t], chi[t]]

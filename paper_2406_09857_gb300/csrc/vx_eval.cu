@@ -282,7 +282,8 @@ struct A32C {
   }
   // a stored bound carries a relative margin 2^-40 and an absolute 2^-148
   static __device__ __forceinline__ V store(V J) {
-    return make_float4(J.x, J.y, __fadd_ru(__fmaf_ru(J.z, k2m40, J.z), kEta148), 0.f);
+    const float e = __fadd_ru(__fmaf_ru(J.z, k2m40, J.z), kEta148);
+    return make_float4(J.x, J.y, e, e);  // the bound twice: a register pair for paired steps
   }
   // 0: the binary64 path surely excludes, 1: surely keeps, 2: inside the error band.  With
   // |lo32 - lo64| <= E and |hi32 - hi64| <= E: lo64 > 0 is sure when lo32 > E, lo64 <= 0 when
@@ -566,80 +567,120 @@ __device__ __forceinline__ YLeaf yleaf(const A32C::X &x) {
 
 __device__ __forceinline__ float4 negated(float4 A) { return make_float4(A.y, A.x, A.z, A.w); }
 
-// Horner of NP polynomials of one length L on the leaves y0, y1 (one parent): chain K0[f] is
-// (-1)^a J_a of leaf 0 and polynomial f (equal to J_a when y0 is not negated).  Odd entries
-// are negated for a negated leaf; the loop takes the entries in (odd, even) pairs.
-template <int NP>
-__device__ __forceinline__ void horner_y2(const float4 *const (&b)[2], int L, const YLeaf &y0,
-                                          const YLeaf &y1, float4 (&K0)[2], float4 (&K1)[2]) {
+// Two leaves (or nodes) of one parent stepped together: per leaf the pair (lo, -hi) of its
+// chain, and the two error bounds as one pair, so that the bound's two FMAs per step serve
+// both leaves as paired instructions (a stored entry carries its bound twice, in .z and .w).
+struct YPair {
+  float2 l0, h0, l1, h1;  // (yl, yl) and (yh, yh) of leaf 0 and leaf 1
+  float2 xm;              // (xmaxp of leaf 0, xmaxp of leaf 1)
+  bool neg0, neg1;
+};
+
+__device__ __forceinline__ YPair ypair(const YLeaf &a, const YLeaf &b) {
+  YPair y;
+  y.l0 = make_float2(a.yl, a.yl);
+  y.h0 = make_float2(a.yh, a.yh);
+  y.l1 = make_float2(b.yl, b.yl);
+  y.h1 = make_float2(b.yh, b.yh);
+  y.xm = make_float2(a.xmaxp, b.xmaxp);
+  y.neg0 = a.neg;
+  y.neg1 = b.neg;
+  return y;
+}
+
+// A32C::step_y on both leaves: SW = 0 the entry as it is, 1 negated for both leaves (a pair
+// swap), 2 negated per leaf where sw0 / sw1.  The same roundings as step_y, so the same values.
+template <int SW>
+__device__ __forceinline__ void step_y2(float2 &j0, float2 &j1, float2 &e, const YPair &y,
+                                        const float4 &A, bool sw0, bool sw1) {
+  float2 c0, c1;
+  if (SW == 0) {
+    c0 = c1 = make_float2(A.x, A.y);
+  } else if (SW == 1) {
+    c0 = c1 = make_float2(A.y, A.x);
+  } else {
+    c0 = sw0 ? make_float2(A.y, A.x) : make_float2(A.x, A.y);
+    c1 = sw1 ? make_float2(A.y, A.x) : make_float2(A.x, A.y);
+  }
+  const float2 P0 = __ffma2_rd(j0, y.l0, c0), Q0 = __ffma2_rd(j0, y.h0, c0);
+  const float2 P1 = __ffma2_rd(j1, y.l1, c1), Q1 = __ffma2_rd(j1, y.h1, c1);
+  j0 = make_float2(fminf(P0.x, Q0.x), fminf(P0.y, Q0.y));
+  j1 = make_float2(fminf(P1.x, Q1.x), fminf(P1.y, Q1.y));
+  const float2 m = make_float2(fmaxf(fabsf(j0.x), fabsf(j0.y)), fmaxf(fabsf(j1.x), fabsf(j1.y)));
+  e = __ffma2_ru(e, y.xm, __ffma2_ru(make_float2(kCr, kCr), m, make_float2(A.z, A.w)));
+}
+
+// SGN: +1 no leaf negated, -1 both negated (warp-uniform cases), 0 per leaf at run time.
+template <int SGN>
+struct SwapOdd {
+  static constexpr int value = SGN > 0 ? 0 : (SGN < 0 ? 1 : 2);
+};
+
+// Horner of NP polynomials of one length L on the leaves of y (one parent): chain f of leaf c
+// is (-1)^a J_a (equal to J_a when the leaf is not negated).  Odd entries are negated for a
+// negated leaf; the loop takes the entries in (odd, even) pairs, loaded one pair ahead.
+template <int NP, int SGN>
+__device__ __forceinline__ void horner_y2(const float4 *const (&b)[2], int L, const YPair &y,
+                                          float4 (&K0)[2], float4 (&K1)[2]) {
+  constexpr int SWO = SwapOdd<SGN>::value;
   const bool top_odd = (L - 1) & 1;
+  float2 j0[NP], j1[NP], e[NP];
 #pragma unroll
   for (int f = 0; f < NP; ++f) {
     const float4 A = b[f][L - 1];
-    K0[f] = (top_odd && y0.neg) ? negated(A) : A;
-    K1[f] = (top_odd && y1.neg) ? negated(A) : A;
+    const float4 A0 = (top_odd && y.neg0) ? negated(A) : A;
+    const float4 A1 = (top_odd && y.neg1) ? negated(A) : A;
+    j0[f] = make_float2(A0.x, A0.y);
+    j1[f] = make_float2(A1.x, A1.y);
+    e[f] = make_float2(A.z, A.w);
   }
   int a = L - 2;
   if (a >= 0 && !(a & 1)) {
 #pragma unroll
-    for (int f = 0; f < NP; ++f) {
-      const float4 A = b[f][a];
-      K0[f] = A32C::step_y(K0[f], y0.yl, y0.yh, y0.xmaxp, A, false);
-      K1[f] = A32C::step_y(K1[f], y1.yl, y1.yh, y1.xmaxp, A, false);
-    }
+    for (int f = 0; f < NP; ++f) step_y2<0>(j0[f], j1[f], e[f], y, b[f][a], false, false);
     --a;
-  }
-  // the entries of the next pair are loaded one pair ahead of their use
-  float4 An[NP], Bn[NP];
-  if (a >= 1) {
-#pragma unroll
-    for (int f = 0; f < NP; ++f) {
-      An[f] = b[f][a];
-      Bn[f] = b[f][a - 1];
-    }
   }
   for (; a >= 1; a -= 2) {
     float4 A[NP], B[NP];
 #pragma unroll
     for (int f = 0; f < NP; ++f) {
-      A[f] = An[f];
-      B[f] = Bn[f];
-    }
-    if (a >= 3) {
-#pragma unroll
-      for (int f = 0; f < NP; ++f) {
-        An[f] = b[f][a - 2];
-        Bn[f] = b[f][a - 3];
-      }
+      A[f] = b[f][a];
+      B[f] = b[f][a - 1];
     }
 #pragma unroll
     for (int f = 0; f < NP; ++f) {
-      K0[f] = A32C::step_y(K0[f], y0.yl, y0.yh, y0.xmaxp, A[f], y0.neg);
-      K1[f] = A32C::step_y(K1[f], y1.yl, y1.yh, y1.xmaxp, A[f], y1.neg);
-      K0[f] = A32C::step_y(K0[f], y0.yl, y0.yh, y0.xmaxp, B[f], false);
-      K1[f] = A32C::step_y(K1[f], y1.yl, y1.yh, y1.xmaxp, B[f], false);
+      step_y2<SWO>(j0[f], j1[f], e[f], y, A[f], y.neg0, y.neg1);
+      step_y2<0>(j0[f], j1[f], e[f], y, B[f], false, false);
     }
+  }
+#pragma unroll
+  for (int f = 0; f < NP; ++f) {
+    K0[f] = make_float4(j0[f].x, j0[f].y, e[f].x, e[f].x);
+    K1[f] = make_float4(j1[f].x, j1[f].y, e[f].y, e[f].y);
   }
 }
 
 // Horner of fibre f of a block (entries rowoff[a] + f, a = L-1 .. 0; entry e at
 // base[e * estride]) on two boxes of one parent, as horner_y2 does for a leaf's single fibre.
+template <int SGN>
 __device__ __forceinline__ void horner_y2_fibre(const float4 *__restrict__ base, int64_t estride,
                                                 const int32_t *rowoff, int f, int L,
-                                                const YLeaf &y0, const YLeaf &y1, float4 &K0,
-                                                float4 &K1) {
+                                                const YPair &y, float4 &K0, float4 &K1) {
+  constexpr int SWO = SwapOdd<SGN>::value;
   auto ent = [&](int a) { return base[(int64_t)(rowoff[a] + f) * estride]; };
   const bool top_odd = (L - 1) & 1;
+  float2 j0, j1, e;
   {
     const float4 A = ent(L - 1);
-    K0 = (top_odd && y0.neg) ? negated(A) : A;
-    K1 = (top_odd && y1.neg) ? negated(A) : A;
+    const float4 A0 = (top_odd && y.neg0) ? negated(A) : A;
+    const float4 A1 = (top_odd && y.neg1) ? negated(A) : A;
+    j0 = make_float2(A0.x, A0.y);
+    j1 = make_float2(A1.x, A1.y);
+    e = make_float2(A.z, A.w);
   }
   int a = L - 2;
   if (a >= 0 && !(a & 1)) {
-    const float4 A = ent(a);
-    K0 = A32C::step_y(K0, y0.yl, y0.yh, y0.xmaxp, A, false);
-    K1 = A32C::step_y(K1, y1.yl, y1.yh, y1.xmaxp, A, false);
+    step_y2<0>(j0, j1, e, y, ent(a), false, false);
     --a;
   }
   float4 An = make_float4(0.f, 0.f, 0.f, 0.f), Bn = An;
@@ -653,11 +694,18 @@ __device__ __forceinline__ void horner_y2_fibre(const float4 *__restrict__ base,
       An = ent(a - 2);
       Bn = ent(a - 3);
     }
-    K0 = A32C::step_y(K0, y0.yl, y0.yh, y0.xmaxp, A, y0.neg);
-    K1 = A32C::step_y(K1, y1.yl, y1.yh, y1.xmaxp, A, y1.neg);
-    K0 = A32C::step_y(K0, y0.yl, y0.yh, y0.xmaxp, B, false);
-    K1 = A32C::step_y(K1, y1.yl, y1.yh, y1.xmaxp, B, false);
+    step_y2<SWO>(j0, j1, e, y, A, y.neg0, y.neg1);
+    step_y2<0>(j0, j1, e, y, B, false, false);
   }
+  K0 = make_float4(j0.x, j0.y, e.x, e.x);
+  K1 = make_float4(j1.x, j1.y, e.y, e.y);
+}
+
+// The warp-uniform sign case of a leaf pair: +1 no lane negated, -1 all negated, 0 mixed.
+__device__ __forceinline__ int warp_sign(const YPair &y) {
+  if (__all_sync(0xffffffffu, !y.neg0 && !y.neg1)) return 1;
+  if (__all_sync(0xffffffffu, y.neg0 && y.neg1)) return -1;
+  return 0;
 }
 
 // ---------------------------------------------------------------------------------------
@@ -797,12 +845,18 @@ __device__ __forceinline__ void stage_chunk_c(const StageDev &st, const int32_t 
   const int64_t p1 = par ? (int64_t)__ldg(par + i1) - poff : 0;
   const bool fast = p0 == p1 && x0.cls != 0 && x1.cls != 0;
   if (__all_sync(0xffffffffu, fast)) {
-    const YLeaf y0 = yleaf(x0), y1 = yleaf(x1);
+    const YPair yp = ypair(yleaf(x0), yleaf(x1));
+    const int ws = warp_sign(yp);
     const float4 *base = in + p0 * in_nstride;
     for (int f = grp; f < st.nfib; f += G) {
       const int L = __ldg(st.fiblen + f);
       float4 K0, K1;
-      horner_y2_fibre(base, in_estride, rowoff, f, L, y0, y1, K0, K1);
+      if (ws > 0)
+        horner_y2_fibre<1>(base, in_estride, rowoff, f, L, yp, K0, K1);
+      else if (ws < 0)
+        horner_y2_fibre<-1>(base, in_estride, rowoff, f, L, yp, K0, K1);
+      else
+        horner_y2_fibre<0>(base, in_estride, rowoff, f, L, yp, K0, K1);
       const int64_t o = (int64_t)__ldg(st.outpos + f) * out_estride;
       if (live) out[i0 * out_nstride + o] = A32C::store(K0);
       if (two) out[i1 * out_nstride + o] = A32C::store(K1);
@@ -877,11 +931,17 @@ __global__ void __launch_bounds__(512)
     const A32C::X x0 = A32C::box(g, __ldg(lab + i0)), x1 = A32C::box(g, __ldg(lab + i1));
     const bool fast = x0.cls != 0 && x1.cls != 0;
     if (__all_sync(0xffffffffu, fast)) {
-      const YLeaf y0 = yleaf(x0), y1 = yleaf(x1);
+      const YPair yp = ypair(yleaf(x0), yleaf(x1));
+      const int ws = warp_sign(yp);
       for (int f = grp; f < st.nfib; f += G) {
         const int L = __ldg(st.fiblen + f);
         float4 K0, K1;
-        horner_y2_fibre(s_blk, 1, s_rowoff, f, L, y0, y1, K0, K1);
+        if (ws > 0)
+          horner_y2_fibre<1>(s_blk, 1, s_rowoff, f, L, yp, K0, K1);
+        else if (ws < 0)
+          horner_y2_fibre<-1>(s_blk, 1, s_rowoff, f, L, yp, K0, K1);
+        else
+          horner_y2_fibre<0>(s_blk, 1, s_rowoff, f, L, yp, K0, K1);
         const int64_t o = (int64_t)__ldg(st.outpos + f) * out_estride;
         if (live) out[i0 * out_nstride + o] = A32C::store(K0);
         if (two) out[i1 * out_nstride + o] = A32C::store(K1);
@@ -939,13 +999,19 @@ __device__ __forceinline__ void leaf_tile_c(const LeafArgs &A, int npoly,
   };
   const bool fast = p0 == p1 && x0.cls != 0 && x1.cls != 0;
   if (__all_sync(0xffffffffu, fast)) {
-    const YLeaf y0 = yleaf(x0), y1 = yleaf(x1);
+    const YPair yp = ypair(yleaf(x0), yleaf(x1));
+    const int ws = warp_sign(yp);
     int f = 0;
     for (; f + 1 < npoly && A.len[f] == A.len[f + 1]; f += 2) {
       const V *const b[2] = {(const V *)A.in[f] + p0 * A.blk[f],
                              (const V *)A.in[f + 1] + p0 * A.blk[f + 1]};
       V K0[2], K1[2];
-      horner_y2<2>(b, A.len[f], y0, y1, K0, K1);
+      if (ws > 0)
+        horner_y2<2, 1>(b, A.len[f], yp, K0, K1);
+      else if (ws < 0)
+        horner_y2<2, -1>(b, A.len[f], yp, K0, K1);
+      else
+        horner_y2<2, 0>(b, A.len[f], yp, K0, K1);
       decide(f, 0, K0[0]);
       decide(f + 1, 0, K0[1]);
       decide(f, 1, K1[0]);
@@ -954,7 +1020,12 @@ __device__ __forceinline__ void leaf_tile_c(const LeafArgs &A, int npoly,
     for (; f < npoly; ++f) {
       const V *const b[2] = {(const V *)A.in[f] + p0 * A.blk[f], nullptr};
       V K0[2], K1[2];
-      horner_y2<1>(b, A.len[f], y0, y1, K0, K1);
+      if (ws > 0)
+        horner_y2<1, 1>(b, A.len[f], yp, K0, K1);
+      else if (ws < 0)
+        horner_y2<1, -1>(b, A.len[f], yp, K0, K1);
+      else
+        horner_y2<1, 0>(b, A.len[f], yp, K0, K1);
       decide(f, 0, K0[0]);
       decide(f, 1, K1[0]);
     }

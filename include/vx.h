@@ -295,7 +295,9 @@ int vx_enclose_batch(const vx_poly *const *systems, const int32_t *npoly, const 
  * counts and fibre length, bucketed) times every variant on its real data and keeps the
  * fastest for the later ones (that first launch synchronises its stream); mode 0 uses the
  * built-in heuristics.  cache_path (nullable): a text file of tuned shapes, read by this call
- * and appended to as shapes are tuned.  vx_autotune_entries: shapes tuned so far;
+ * and appended to as shapes are tuned.  Mode 2 + v runs variant v of every launch that has
+ * one (else variant 0), without timing: a test hook that exercises each variant (every
+ * variant gives the same outputs).  vx_autotune_entries: shapes tuned so far;
  * vx_autotune_clear forgets them. */
 int vx_autotune(int32_t mode, const char *cache_path);
 int vx_autotune_entries(void);

@@ -738,8 +738,8 @@ int64_t vx_kernel_launches(void) { return g_launches.load(std::memory_order_rela
 
 int vx_autotune(int32_t mode, const char *cache_path) {
   clear_error();
-  if (mode != 0 && mode != 1) {
-    set_error("vx_autotune: mode %d (0 or 1)", mode);
+  if (mode < 0 || mode > 9) {
+    set_error("vx_autotune: mode %d (0, 1, or 2 + a variant below 8)", mode);
     return VX_EINVAL;
   }
   return set_autotune(mode, cache_path);

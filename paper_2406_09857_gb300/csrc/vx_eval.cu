@@ -962,25 +962,26 @@ __global__ void __launch_bounds__(512)
   }
 }
 
-// One warp's share of k_leaf_c: the 32 leaf pairs of tile t (64 leaves).  par/poff as in
-// leaf_item.
-__device__ __forceinline__ void leaf_tile_c(const LeafArgs &A, int npoly,
-                                            const int32_t *__restrict__ lab,
-                                            const int32_t *__restrict__ par, int64_t poff,
-                                            int64_t nleaves, int64_t t, const AxisGrid &g,
+// Where the leaf stage reads polynomial f's block for parent p: the parent blocks in global
+// memory (node-major), or (ChunkBlocks) consecutive parents' blocks staged in shared memory.
+struct GlobalBlocks {
+  const LeafArgs &A;
+  __device__ const float4 *operator()(int f, int64_t p) const {
+    return (const float4 *)A.in[f] + p * A.blk[f];
+  }
+};
+
+// The last stage and C0 of the leaf pair (i0, i1) with parents p0, p1 (blocks from src), in
+// the certified binary32 arithmetic: a warp whose pairs each share a parent and do not
+// straddle 0 takes the paired, sign-free path; any other warp runs every leaf on its own.
+template <class Src>
+__device__ __forceinline__ void leaf_pair_c(const LeafArgs &A, int npoly, const Src &src,
+                                            int64_t i0, int64_t i1, bool live, bool two,
+                                            const A32C::X &x0, const A32C::X &x1, int64_t p0,
+                                            int64_t p1, int64_t nleaves,
                                             uint8_t *__restrict__ keep, double *__restrict__ lo,
                                             double *__restrict__ hi, uint8_t *__restrict__ flag) {
   using V = float4;
-  const int lane = threadIdx.x & 31;
-  const int64_t npairs = (nleaves + 1) >> 1;
-  const int64_t q = t * 32 + lane;
-  const bool live = q < npairs;  // a lane past the end repeats the last pair, stores nothing
-  const int64_t i0 = 2 * (live ? q : npairs - 1);
-  const bool two = i0 + 1 < nleaves;
-  const int64_t i1 = two ? i0 + 1 : i0;
-  const A32C::X x0 = A32C::box(g, __ldg(lab + i0)), x1 = A32C::box(g, __ldg(lab + i1));
-  const int64_t p0 = par ? (int64_t)__ldg(par + i0) - poff : 0;
-  const int64_t p1 = par ? (int64_t)__ldg(par + i1) - poff : 0;
   bool excl0 = false, amb0 = false, excl1 = false, amb1 = false;
   auto decide = [&](int f, int c, const V &J) {
     if (lo && live && (c == 0 || two)) {
@@ -1003,8 +1004,7 @@ __device__ __forceinline__ void leaf_tile_c(const LeafArgs &A, int npoly,
     const int ws = warp_sign(yp);
     int f = 0;
     for (; f + 1 < npoly && A.len[f] == A.len[f + 1]; f += 2) {
-      const V *const b[2] = {(const V *)A.in[f] + p0 * A.blk[f],
-                             (const V *)A.in[f + 1] + p0 * A.blk[f + 1]};
+      const V *const b[2] = {src(f, p0), src(f + 1, p0)};
       V K0[2], K1[2];
       if (ws > 0)
         horner_y2<2, 1>(b, A.len[f], yp, K0, K1);
@@ -1018,7 +1018,7 @@ __device__ __forceinline__ void leaf_tile_c(const LeafArgs &A, int npoly,
       decide(f + 1, 1, K1[1]);
     }
     for (; f < npoly; ++f) {
-      const V *const b[2] = {(const V *)A.in[f] + p0 * A.blk[f], nullptr};
+      const V *const b[2] = {src(f, p0), nullptr};
       V K0[2], K1[2];
       if (ws > 0)
         horner_y2<1, 1>(b, A.len[f], yp, K0, K1);
@@ -1037,13 +1037,11 @@ __device__ __forceinline__ void leaf_tile_c(const LeafArgs &A, int npoly,
       int f = 0;
       for (; f + 1 < npoly && A.len[f] == A.len[f + 1]; f += 2) {
         V J0, J1;
-        horner1x2_any<A32C>((const V *)A.in[f] + p * A.blk[f],
-                            (const V *)A.in[f + 1] + p * A.blk[f + 1], A.len[f], x, J0, J1);
+        horner1x2_any<A32C>(src(f, p), src(f + 1, p), A.len[f], x, J0, J1);
         decide(f, c, J0);
         decide(f + 1, c, J1);
       }
-      for (; f < npoly; ++f)
-        decide(f, c, horner1_any<A32C>((const V *)A.in[f] + p * A.blk[f], 1, A.len[f], x));
+      for (; f < npoly; ++f) decide(f, c, horner1_any<A32C>(src(f, p), 1, A.len[f], x));
     }
   }
   if (live) {
@@ -1056,6 +1054,28 @@ __device__ __forceinline__ void leaf_tile_c(const LeafArgs &A, int npoly,
   }
 }
 
+// One warp's share of k_leaf_c: the 32 leaf pairs of tile t (64 leaves).  par/poff as in
+// leaf_item.
+__device__ __forceinline__ void leaf_tile_c(const LeafArgs &A, int npoly,
+                                            const int32_t *__restrict__ lab,
+                                            const int32_t *__restrict__ par, int64_t poff,
+                                            int64_t nleaves, int64_t t, const AxisGrid &g,
+                                            uint8_t *__restrict__ keep, double *__restrict__ lo,
+                                            double *__restrict__ hi, uint8_t *__restrict__ flag) {
+  const int lane = threadIdx.x & 31;
+  const int64_t npairs = (nleaves + 1) >> 1;
+  const int64_t q = t * 32 + lane;
+  const bool live = q < npairs;  // a lane past the end repeats the last pair, stores nothing
+  const int64_t i0 = 2 * (live ? q : npairs - 1);
+  const bool two = i0 + 1 < nleaves;
+  const int64_t i1 = two ? i0 + 1 : i0;
+  const A32C::X x0 = A32C::box(g, __ldg(lab + i0)), x1 = A32C::box(g, __ldg(lab + i1));
+  const int64_t p0 = par ? (int64_t)__ldg(par + i0) - poff : 0;
+  const int64_t p1 = par ? (int64_t)__ldg(par + i1) - poff : 0;
+  leaf_pair_c(A, npoly, GlobalBlocks{A}, i0, i1, live, two, x0, x1, p0, p1, nleaves, keep, lo,
+              hi, flag);
+}
+
 __global__ void __launch_bounds__(kThreads, 6)
     k_leaf_c(LeafArgs A, int npoly, const int32_t *__restrict__ lab,
              const int32_t *__restrict__ par, int64_t nleaves, AxisGrid g,
@@ -1066,6 +1086,82 @@ __global__ void __launch_bounds__(kThreads, 6)
   for (int64_t t = (int64_t)blockIdx.x * kWarpsPerBlock + (threadIdx.x >> 5); t < ntiles;
        t += (int64_t)gridDim.x * kWarpsPerBlock)
     leaf_tile_c(A, npoly, lab, par, 0, nleaves, t, g, keep, lo, hi, flag);
+}
+
+// Leaf chunks of k_leaf_tma_c: kLeafIter pairs per thread, at most kLeafParents parents staged.
+constexpr int kLeafIter = 2;
+constexpr int kLeafParents = 8;
+
+struct ChunkBlocks {  // the staged blocks of parents p0 .. p0 + n - 1, else global memory
+  const LeafArgs &A;
+  const float4 *s_blk;
+  const int32_t *s_off;
+  int64_t p0;
+  bool staged;
+  __device__ const float4 *operator()(int f, int64_t p) const {
+    return staged ? s_blk + s_off[f] + (p - p0) * A.blk[f] : (const float4 *)A.in[f] + p * A.blk[f];
+  }
+};
+
+// k_leaf_c with the parents' blocks brought into shared memory by bulk copies (mbarrier,
+// bounded wait): CTA b takes the leaves b*C .. b*C+C-1 (C = 2 kLeafIter blockDim.x), two per
+// thread per pass; their parents are consecutive nodes, whose node-major blocks are one
+// contiguous range per polynomial, copied once when at most kLeafParents of them (else the
+// CTA reads global memory as k_leaf_c does).
+__global__ void __launch_bounds__(kThreads, 6)
+    k_leaf_tma_c(LeafArgs A, int npoly, const int32_t *__restrict__ lab,
+                 const int32_t *__restrict__ par, int64_t nleaves, AxisGrid g,
+                 uint8_t *__restrict__ keep, double *__restrict__ lo, double *__restrict__ hi,
+                 uint8_t *__restrict__ flag) {
+  extern __shared__ __align__(128) unsigned char smem[];
+  uint64_t *bar = reinterpret_cast<uint64_t *>(smem);
+  int32_t *s_off = reinterpret_cast<int32_t *>(smem + 16);
+  float4 *s_blk = reinterpret_cast<float4 *>(smem + 128);
+  const int64_t chunk = 2 * (int64_t)kLeafIter * blockDim.x;
+  const int64_t first = (int64_t)blockIdx.x * chunk;
+  const int64_t last = (first + chunk < nleaves ? first + chunk : nleaves) - 1;
+  const int64_t pf = __ldg(par + first), pl = __ldg(par + last);
+  const bool staged = pl - pf < kLeafParents;
+  if (staged) {
+    if (threadIdx.x == 0) {
+      mbar_init(bar, 1);
+      const int64_t np = pl - pf + 1;
+      int32_t o = 0;
+      uint32_t total = 0;
+      for (int f = 0; f < npoly; ++f) {
+        s_off[f] = o;
+        o += (int32_t)(kLeafParents * A.blk[f]);
+        total += (uint32_t)(np * A.blk[f] * (int64_t)sizeof(float4));
+      }
+      mbar_arrive_expect_tx(bar, total);
+      for (int f = 0; f < npoly; ++f) {
+        const char *src = reinterpret_cast<const char *>((const float4 *)A.in[f] + pf * A.blk[f]);
+        char *dst = reinterpret_cast<char *>(s_blk + s_off[f]);
+        const uint64_t bytes = (uint64_t)(np * A.blk[f]) * sizeof(float4);
+        for (uint64_t b = 0; b < bytes; b += 32768) {
+          const uint32_t n = (uint32_t)(bytes - b < 32768 ? bytes - b : 32768);
+          bulk_copy_g2s(dst + b, src + b, n, bar);
+        }
+      }
+    }
+    __syncthreads();
+    if (!mbar_wait_bounded(bar, 0)) return;
+  }
+  const ChunkBlocks src{A, s_blk, s_off, pf, staged};
+  // every warp runs the same trip count (the vote inside sees all 32 lanes)
+  for (int it = 0; it < kLeafIter; ++it) {
+    const int64_t na = first + (int64_t)it * 2 * blockDim.x + 2 * threadIdx.x;
+    const bool live = na <= last, two = na + 1 <= last;
+    const int64_t i0 = live ? na : last, i1 = two ? na + 1 : i0;
+    const A32C::X x0 = A32C::box(g, __ldg(lab + i0)), x1 = A32C::box(g, __ldg(lab + i1));
+    const int64_t p0 = __ldg(par + i0), p1 = __ldg(par + i1);
+    leaf_pair_c(A, npoly, src, i0, i1, live, two, x0, x1, p0, p1, nleaves, keep, lo, hi, flag);
+  }
+}
+
+int leaf_tma_grid(int64_t leaves) {
+  const int64_t chunk = 2 * (int64_t)kLeafIter * kThreads;
+  return (int)((leaves + chunk - 1) / chunk);
 }
 
 int leaf_pair_grid(int64_t leaves) {
@@ -1113,7 +1209,7 @@ size_t level_scratch_bytes(const SysDev &sys, const CsfView &c) {
 struct Tuner {
   std::mutex mu;
   std::unordered_map<uint64_t, int> best;
-  int mode = 1;      // 0: heuristic variant 0 only, 1: tune
+  int mode = 1;      // 0: heuristic variant 0 only, 1: tune, 2 + v: variant v wherever it exists
   std::string path;  // cache file ("" = in memory only)
 };
 Tuner &tuner() {
@@ -1146,6 +1242,7 @@ int tuned_launch(uint64_t key, int nvar, cudaStream_t s, F launch) {
   {
     std::lock_guard<std::mutex> g(T.mu);
     if (T.mode == 0 || nvar <= 1) v = 0;
+    else if (T.mode >= 2) v = T.mode - 2 < nvar ? T.mode - 2 : 0;
     else {
       auto it = T.best.find(key);
       if (it != T.best.end()) v = it->second < nvar ? it->second : 0;
@@ -1358,9 +1455,25 @@ int eval_level_t(const SysDev &sys, const CsfView &c, const LevelGrid &grid, dou
     madds += wl;
     if (tm && tm->on) rc = tm->begin(kind0 + 2, wl);
     if (rc == VX_OK) {
-      // variants (certified binary32): 0 two leaves per thread, 1 one leaf per thread
+      // variants (certified binary32): 0 two leaves per thread, 1 one leaf per thread, 2 two
+      // leaves per thread with the parent's blocks staged in shared memory (one CTA per
+      // parent; when the blocks fit)
+      size_t leaf_smem = 128;
+      for (int f = 0; f < sys.npoly; ++f)
+        leaf_smem += (size_t)kLeafParents * (size_t)A.blk[f] * sizeof(float4);
+      const bool leaf_tma = std::is_same<AR, A32C>::value && k >= 2 && leaf_smem <= kMaxDynSmem;
+      if (leaf_tma &&
+          cudaFuncSetAttribute(k_leaf_tma_c, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               (int)kMaxDynSmem) != cudaSuccess) {
+        set_error("cudaFuncSetAttribute(shared memory %zu) failed", leaf_smem);
+        rc = VX_ECUDA;
+      }
       auto launch = [&](int v) -> int {
-        if (std::is_same<AR, A32C>::value && v == 0)
+        if (std::is_same<AR, A32C>::value && v == 2)
+          k_leaf_tma_c<<<(unsigned)leaf_tma_grid(nleaves), kThreads, leaf_smem, s>>>(
+              A, sys.npoly, c.lab[k - 1], c.par[k - 1], nleaves, grid.ax[k - 1], d_keep, d_lo,
+              d_hi, d_flag);
+        else if (std::is_same<AR, A32C>::value && v == 0)
           k_leaf_c<<<leaf_pair_grid(nleaves), kThreads, 0, s>>>(
               A, sys.npoly, c.lab[k - 1], k == 1 ? nullptr : c.par[k - 1], nleaves,
               grid.ax[k - 1], d_keep, d_lo, d_hi, d_flag);
@@ -1392,9 +1505,10 @@ int eval_level_t(const SysDev &sys, const CsfView &c, const LevelGrid &grid, dou
           rc = VX_EINVAL;
         }
       } else {
-        rc = tuned_launch(tune_key(3, arith, k - 1, nleaves, k > 1 ? c.N[k - 2] : 0,
-                                   sys.p[0].st[k - 1].maxlen, sys.npoly),
-                          std::is_same<AR, A32C>::value ? 2 : 1, s, launch);
+        if (rc == VX_OK)
+          rc = tuned_launch(tune_key(3, arith, k - 1, nleaves, k > 1 ? c.N[k - 2] : 0,
+                                     sys.p[0].st[k - 1].maxlen, sys.npoly),
+                            std::is_same<AR, A32C>::value ? (leaf_tma ? 3 : 2) : 1, s, launch);
       }
       if (rc == VX_OK && tm && tm->on) rc = tm->end();
     }
@@ -1725,7 +1839,7 @@ int eval_c1_vertex(const SysDev &sys, const CsfView &c, const LevelGrid &grid, u
 int set_autotune(int mode, const char *path) {
   Tuner &T = tuner();
   std::lock_guard<std::mutex> g(T.mu);
-  T.mode = mode ? 1 : 0;
+  T.mode = mode < 0 ? 0 : mode;
   T.path = path ? path : "";
   if (!T.path.empty()) {
     if (FILE *fp = std::fopen(T.path.c_str(), "r")) {

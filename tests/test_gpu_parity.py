@@ -537,3 +537,31 @@ def test_table1_family_equals_oracle(vx, k, d, kind, depth):
         r = vx.enclose(s.polys, s.domain, depth, vx.make_opts(mode))
         assert np.array_equal(r.boxes(), ref["tuples"])
         assert np.array_equal(r.stats()["tested"], ref["tested"])
+
+
+@pytest.mark.parametrize("case", ["curve-d14", "three-polys", "mixed-lengths", "relations"])
+def test_every_launch_variant_matches_oracle(vx, case):
+    """Each launch variant, forced everywhere it exists (one or two boxes per thread, the
+    parent's blocks in shared memory or not, more fibre groups, fewer threads), gives the
+    oracle's enclosure in every arithmetic (midpoint-radius with a binary64 last level)."""
+    cases = {
+        "curve-d14": ([synth.kostlan_poly(3, 14, 1201), synth.kostlan_poly(3, 14, 1202)], None, 7),
+        "three-polys": ([synth.kostlan_poly(3, 9, 1203), synth.kostlan_poly(3, 9, 1204),
+                         synth.kostlan_poly(3, 7, 1205)], None, 6),
+        "mixed-lengths": (synth.random_small(3, 8, 2, 1206, density=0.3), None, 6),
+        "relations": (synth.random_small(3, 6, 3, 1207), [0, 1, 4], 6),
+    }
+    polys, rel, depth = cases[case]
+    dom = synth.cube(3)
+    ref = oracle.enclose_gen(polys, dom, depth, rel=rel)
+    sysv = vx.System(polys, rel=rel) if rel else vx.System(polys)
+    try:
+        for v in range(4):
+            vx.autotune(2 + v)
+            for opts in (vx.make_opts(vx.FP32), vx.make_opts(vx.FP64),
+                         vx.make_opts(vx.FP32_MIDRAD, fp64_final=True)):
+                r = vx.enclose_system(sysv, dom, depth, opts)
+                assert np.array_equal(r.boxes(), ref["tuples"]), (case, v)
+                r.free()
+    finally:
+        vx.autotune(1)

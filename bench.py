@@ -747,6 +747,8 @@ def run_profile_case(args):
     torch.cuda.set_device(0)
     s = synth.curve()
     mode = {"fp32": vx.FP32, "fp64": vx.FP64, "midrad": vx.FP32_MIDRAD}[args.mode]
+    if args.variant is not None:  # one launch per kernel and level: variant V everywhere
+        vx.autotune(2 + args.variant)
     r = vx.enclose_system(vx.System(s.polys), s.domain, args.profile_case, vx.make_opts(mode))
     torch.cuda.synchronize()
     st = r.stats()
@@ -792,6 +794,9 @@ def main():
                          "and exit (for ncu)")
     ap.add_argument("--mode", choices=["fp32", "fp64", "midrad"], default="fp32",
                     help="arithmetic of --profile-case")
+    ap.add_argument("--variant", type=int, default=None, metavar="V",
+                    help="--profile-case: launch variant V of every kernel that has one, no "
+                         "autotuning (0 two boxes per thread, 2 leaves from shared memory)")
     args = ap.parse_args()
     if args.profile_case is not None:
         return run_profile_case(args)

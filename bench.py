@@ -52,6 +52,10 @@ FP64_PEAK_T = SMS * 2 * SM_MHZ * 1e6 / 1e12    # 0.63 T instructions/s
 # multiplies + 2 directed adds.
 OPS_PER_MADD = {"fp32": 4, "fp64": 4}
 L2_FLUSH_BYTES = 512 << 20  # > 129 MB of L2
+# dram__bytes_read.sum + dram__bytes_write.sum of the certified binary32 leaf kernel
+# (k_leaf_tma_c) on the curve's level 8 (ncu --set full): 334.8 MB + 26.1 MB for 3.064e9
+# interval multiply-adds
+LEAF32_DRAM_B_PER_MADD = (334.8e6 + 26.1e6) / 3.064e9
 
 
 def load_peaks():
@@ -644,8 +648,14 @@ def run_gpu(args):
         achieved = ops_per_launch / (per_launch_ms * 1e-3) / 1e12
         share = {n: round(x["ms"] / sum(y["ms"] for y in tot.values()), 4) for n, x in tot.items()
                  if x["launches"]}
+        traffic = None
+        if arith == "fp32" and top == "leaf_fp32":
+            # DRAM bytes per multiply-add of the leaf kernel from one ncu capture of a smaller
+            # launch of the same kernel, scaled by the multiply-adds of an average launch
+            traffic = LEAF32_DRAM_B_PER_MADD * v["work"] / v["launches"]
         return {"kernel": top, "bound": "alu", "achieved": achieved, "peak": peak_t,
-                "unit": "T FMA-pipe lane-ops/s", "frac": achieved / peak_t, "traffic": None,
+                "unit": "T FMA-pipe lane-ops/s", "frac": achieved / peak_t, "traffic": traffic,
+                "traffic_unit": "bytes per launch (DRAM read + write)",
                 "launches": v["launches"], "avg_launch_ms": per_launch_ms,
                 "madds_per_launch": v["work"] / v["launches"], "time_share": share}
 

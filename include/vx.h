@@ -53,11 +53,12 @@ extern "C" {
 #define VX_FP32_MIDRAD 1 /* binary32 midpoint-radius <m, r> with the rounding error of every
                           * step bounded a priori and added to r, so the enclosure contains
                           * the exact range (and the VX_FP64 enclosure) */
-#define VX_FP32 2        /* binary32 intervals [RD, RU] carrying an a-priori bound on their
-                          * distance to the VX_FP64 endpoints: a box whose binary32 value is
-                          * farther than that bound from deciding C0 either way is decided in
-                          * binary32, the others are re-evaluated in VX_FP64, so every keep
-                          * decision equals the VX_FP64 one */
+#define VX_FP32 2        /* binary32 approximations of the VX_FP64 interval ends (rounded to
+                          * nearest) carrying an a-priori bound on their distance to them: a box
+                          * whose binary32 value is farther than that bound from deciding C0
+                          * either way is decided in binary32, the others are re-evaluated in
+                          * VX_FP64, so every keep decision equals the VX_FP64 one (the values
+                          * d_lo/d_hi it returns are within that bound of the VX_FP64 ones) */
 
 /* Relation of a polynomial F of a system of equations and inequalities (Sec. 4: the input is
  * equations and inequalities).  C0 drops a box when F's enclosure on it proves the relation

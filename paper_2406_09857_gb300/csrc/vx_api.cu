@@ -262,17 +262,8 @@ static float2 to_midrad(double c) {
   return make_float2(m, r);
 }
 
-static float f32_round_down(double x) {
-  float f = (float)x;
-  if ((double)f > x) f = std::nextafter(f, -INFINITY);
-  return f;
-}
 
-// (RD(c), -RU(c)) in binary32 and a bound E >= (1 + 2^-40)(max(c - RD(c), RU(c) - c) +
-// 2^-23 |c|) + 2^-148 on the distance to the binary64 coefficient (which the binary64 path
-// uses as it is); the 2^-23 |c| keeps E >= 2^-23 max(|RD(c)|, |RU(c)|), which the error
-// recursion of the evaluation kernels relies on.
-// An interval coefficient [lo, hi] in the binary32 encodings (both contain it).
+// An interval coefficient [lo, hi] as binary32 midpoint-radius (containing it).
 static float2 to_midrad_ivl(double lo, double hi) {
   if (lo == hi) return to_midrad(lo);
   const float m = (float)(0.5 * lo + 0.5 * hi);
@@ -283,28 +274,24 @@ static float2 to_midrad_ivl(double lo, double hi) {
   return make_float2(m, r);
 }
 
-static float4 to_certified(double c);
+// The certified binary32 encoding of a coefficient interval [lo, hi] (lo = hi for a point):
+// (RN(lo), -RN(hi)) and a bound E >= (1 + 2^-39)(d + 2^-24 max(|lo|, |hi|)) + 2^-148, d the
+// larger distance of the two ends to their binary64 values (which the binary64 path uses as
+// they are); the 2^-24 term keeps E >= 2^-24 max(|RN(lo)|, |RN(hi)|), which the error
+// recursion of the evaluation kernels relies on.  The bound is stored twice (.z and .w): a
+// register pair for the kernels' paired steps.
 static float4 to_certified_ivl(double lo, double hi) {
-  if (lo == hi) return to_certified(lo);
-  const float flo = f32_round_down(lo), fhi = f32_round_up(hi);
+  const float flo = (float)lo, fhi = (float)hi;  // round to nearest
   if (!std::isfinite(flo) || !std::isfinite(fhi))
     return make_float4(-INFINITY, -INFINITY, INFINITY, INFINITY);
-  const double d = std::max(lo - (double)flo, (double)fhi - hi);  // exact
+  const double d = std::max(std::fabs(lo - (double)flo), std::fabs(hi - (double)fhi));  // exact
   const double mag = std::max(std::fabs(lo), std::fabs(hi));
-  const double bound = (d + std::ldexp(mag, -23)) * (1.0 + std::ldexp(1.0, -39));
+  const double bound = (d + std::ldexp(mag, -24)) * (1.0 + std::ldexp(1.0, -39));
   const float e = f32_round_up(bound + std::ldexp(1.0, -148));
   return make_float4(flo, -fhi, e, e);
 }
 
-static float4 to_certified(double c) {
-  const float lo = f32_round_down(c), hi = f32_round_up(c);
-  if (!std::isfinite(lo) || !std::isfinite(hi))
-    return make_float4(-INFINITY, -INFINITY, INFINITY, INFINITY);
-  const double d = std::max(c - (double)lo, (double)hi - c);  // exact
-  const double bound = (d + std::ldexp(std::fabs(c), -23)) * (1.0 + std::ldexp(1.0, -39));
-  const float e = f32_round_up(bound + std::ldexp(1.0, -148));
-  return make_float4(lo, -hi, e, e);  // the bound twice (.z, .w): a pair for paired steps
-}
+static float4 to_certified(double c) { return to_certified_ivl(c, c); }
 
 // chi (nullable): upper ends of interval coefficients [p.coefs[t], chi[t]]
 static int pack_poly(int k, const vx_poly &p, HostPoly *hp, const double *chi = nullptr) {

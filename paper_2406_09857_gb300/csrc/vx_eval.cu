@@ -30,18 +30,20 @@
 //        most Jr(|Xm|+Xr) + |Jm|Xr + Ar, and rounding m to nearest adds at most 2^-24|m| plus
 //        2^-149 below the normal range, which every coefficient radius already carries
 //        (it is added when a block is stored).  Inf or NaN never excludes a box.
-//   A32C: binary32 intervals stored as (lo, -hi), so that both ends of J*X + A come from one
-//        paired round-down FMA (lo' = RD(J_sel*X_sel + A.lo), -hi' = RD((-J)_sel*X_sel - A.hi)),
-//        plus an error bound E carried with every interval.  E bounds |lo32 - lo*| +
+//   A32C: binary32 approximations of the interval ends stored as (lo, -hi), so that both ends
+//        of J*X + A come from one paired FMA rounded to nearest (lo' = min over the endpoint
+//        pairs of RN(J_e*X_e + A.lo), the same for -hi'), plus an error bound E carried with
+//        every pair.  The pair is not an enclosure by itself: E bounds |lo32 - lo*| +
 //        |lo64 - lo*| (and the same for hi), where lo* is the exact (unrounded) interval Horner
 //        value with the binary64 coefficients and lo64 what A64 computes.  One step gives
-//          E' = RU(E_J * xmax(1+2^-27) + RU((2^-23+2^-46)*m' + E_A)),  m' = max(|lo'|,|hi'|):
-//        the endpoint selection is xmax-Lipschitz in J; the FMA rounds once (< 2^-23 of its
-//        result); the binary64 path rounds the product (< 2^-52 |J| xmax, which is below
-//        2^-29 E_J xmax because every bound satisfies E >= 2^-23 max(|lo|,|hi|)) and the sum
-//        (< 2^-52 of it); every stored E carries a relative margin of 2^-40 and an absolute
-//        2^-148 (results below the normal range), which exceed the binary64 rounding of a
-//        term in terms of the bound itself, so the induction closes.  Hence lo32 > E means
+//          E' = RU(E_J * xmax(1+2^-27) + RU((2^-24+2^-46)*m' + E_A)),  m' = max(|lo'|,|hi'|):
+//        the min over endpoint products is xmax-Lipschitz in J and 1-Lipschitz in A; the FMA
+//        rounds once to nearest (< 2^-24 of its result); the binary64 path rounds the product
+//        (< 2^-52 |J| xmax, which is below 2^-28 E_J xmax because every bound satisfies
+//        E >= 2^-24 max(|lo|,|hi|)) and the sum (< 2^-52 of it); every stored E carries a
+//        relative margin of 2^-40 and an absolute 2^-148 (results below the normal range, whose
+//        rounding is absolute), which exceed the binary64 rounding of a term in terms of the
+//        bound itself, so the induction closes.  Hence lo32 > E means
 //        A64's lower end is > 0 (A64 excludes the box) and lo32 <= -E with hi32 >= E means
 //        A64 keeps it: a box is decided exactly as A64 decides it, except inside the band of
 //        width E, where A64 is run on it.  Boxes whose grid points are not binary32 (domains
@@ -209,7 +211,7 @@ struct A32 {
 // binary32 intervals (lo, -hi) with an error bound certifying the binary64 decision
 // ---------------------------------------------------------------------------------------
 constexpr float kEta148 = 0x1p-148f;
-constexpr float kCr = 0x1.000002p-23f;  // 2^-23 + 2^-46
+constexpr float kCr = 0x1.000004p-24f;  // 2^-24 + 2^-46
 constexpr float k2m27 = 0x1p-27f;
 constexpr float k2m40 = 0x1p-40f;
 
@@ -252,15 +254,15 @@ struct A32C {
     if (CLS != 0) {
       const float2 j = CLS > 0 ? make_float2(J.x, J.y) : make_float2(J.y, J.x);
       const float a = CLS > 0 ? x.l : x.nh, b = CLS > 0 ? x.h : x.nl;
-      const float2 P = __ffma2_rd(j, make_float2(a, a), make_float2(A.x, A.y));
-      const float2 Q = __ffma2_rd(j, make_float2(b, b), make_float2(A.x, A.y));
+      const float2 P = __ffma2_rn(j, make_float2(a, a), make_float2(A.x, A.y));
+      const float2 Q = __ffma2_rn(j, make_float2(b, b), make_float2(A.x, A.y));
       r = make_float2(fminf(P.x, Q.x), fminf(P.y, Q.y));
     } else {  // X straddles 0: hull of the four products, each bound rounded once
       const float jh = -J.y;
-      r.x = fminf(fminf(__fmaf_rd(J.x, x.l, A.x), __fmaf_rd(J.x, x.h, A.x)),
-                  fminf(__fmaf_rd(jh, x.l, A.x), __fmaf_rd(jh, x.h, A.x)));
-      r.y = fminf(fminf(__fmaf_rd(J.x, x.nl, A.y), __fmaf_rd(J.x, x.nh, A.y)),
-                  fminf(__fmaf_rd(jh, x.nl, A.y), __fmaf_rd(jh, x.nh, A.y)));
+      r.x = fminf(fminf(__fmaf_rn(J.x, x.l, A.x), __fmaf_rn(J.x, x.h, A.x)),
+                  fminf(__fmaf_rn(jh, x.l, A.x), __fmaf_rn(jh, x.h, A.x)));
+      r.y = fminf(fminf(__fmaf_rn(J.x, x.nl, A.y), __fmaf_rn(J.x, x.nh, A.y)),
+                  fminf(__fmaf_rn(jh, x.nl, A.y), __fmaf_rn(jh, x.nh, A.y)));
     }
     const float m = fmaxf(fabsf(r.x), fabsf(r.y));
     float e = __fmaf_ru(kCr, m, A.z);
@@ -273,8 +275,8 @@ struct A32C {
   // (exact: interval negation swaps the pair (lo, -hi), and the products are the same reals).
   static __device__ __forceinline__ V step_y(V K, float yl, float yh, float xmaxp, V A, bool neg) {
     const float2 b = neg ? make_float2(A.y, A.x) : make_float2(A.x, A.y);
-    const float2 P = __ffma2_rd(make_float2(K.x, K.y), make_float2(yl, yl), b);
-    const float2 Q = __ffma2_rd(make_float2(K.x, K.y), make_float2(yh, yh), b);
+    const float2 P = __ffma2_rn(make_float2(K.x, K.y), make_float2(yl, yl), b);
+    const float2 Q = __ffma2_rn(make_float2(K.x, K.y), make_float2(yh, yh), b);
     const float rx = fminf(P.x, Q.x), ry = fminf(P.y, Q.y);
     const float m = fmaxf(fabsf(rx), fabsf(ry));
     const float e = __fmaf_ru(K.z, xmaxp, __fmaf_ru(kCr, m, A.z));
@@ -602,8 +604,8 @@ __device__ __forceinline__ void step_y2(float2 &j0, float2 &j1, float2 &e, const
     c0 = sw0 ? make_float2(A.y, A.x) : make_float2(A.x, A.y);
     c1 = sw1 ? make_float2(A.y, A.x) : make_float2(A.x, A.y);
   }
-  const float2 P0 = __ffma2_rd(j0, y.l0, c0), Q0 = __ffma2_rd(j0, y.h0, c0);
-  const float2 P1 = __ffma2_rd(j1, y.l1, c1), Q1 = __ffma2_rd(j1, y.h1, c1);
+  const float2 P0 = __ffma2_rn(j0, y.l0, c0), Q0 = __ffma2_rn(j0, y.h0, c0);
+  const float2 P1 = __ffma2_rn(j1, y.l1, c1), Q1 = __ffma2_rn(j1, y.h1, c1);
   j0 = make_float2(fminf(P0.x, Q0.x), fminf(P0.y, Q0.y));
   j1 = make_float2(fminf(P1.x, Q1.x), fminf(P1.y, Q1.y));
   const float2 m = make_float2(fmaxf(fabsf(j0.x), fabsf(j0.y)), fmaxf(fabsf(j1.x), fabsf(j1.y)));

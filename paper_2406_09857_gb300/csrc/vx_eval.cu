@@ -647,7 +647,24 @@ __device__ __forceinline__ void horner_y2(const float4 *const (&b)[2], int L, co
     for (int f = 0; f < NP; ++f) step_y2<0>(j0[f], j1[f], e[f], y, b[f][a], false, false);
     --a;
   }
-  for (; a >= 1; a -= 2) {
+  // two (odd, even) pairs per trip: half the loop and address overhead per step
+  for (; a >= 3; a -= 4) {
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      float4 A[NP], B[NP];
+#pragma unroll
+      for (int f = 0; f < NP; ++f) {
+        A[f] = b[f][a - 2 * h];
+        B[f] = b[f][a - 2 * h - 1];
+      }
+#pragma unroll
+      for (int f = 0; f < NP; ++f) {
+        step_y2<SWO>(j0[f], j1[f], e[f], y, A[f], y.neg0, y.neg1);
+        step_y2<0>(j0[f], j1[f], e[f], y, B[f], false, false);
+      }
+    }
+  }
+  if (a >= 1) {
     float4 A[NP], B[NP];
 #pragma unroll
     for (int f = 0; f < NP; ++f) {

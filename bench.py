@@ -670,11 +670,11 @@ def run_gpu(args):
         """Host polynomials in, host boxes out, through the public API."""
         if world == 1:
             r = vx.enclose(polys_host, dom, depth, vx.make_opts(vx.FP32))
-            return r, sysv.device_bytes()
+            return r, sysv.upload_bytes()  # vx_enclose packs and uploads the same system
         sv = vx.System(polys_host)
         st = vx.csf_build(s.k, lvl0, torch.from_numpy(t0).cuda())
         r = vx.enclose_from(sv, st, dom, depth, vx.make_opts(vx.FP32))
-        return r, sv.device_bytes() + t0.nbytes
+        return r, sv.upload_bytes() + t0.nbytes
 
     e2e_once()[0].free()
     ne2e = max(1, min(args.steps, 2))

@@ -142,6 +142,9 @@ int vx_system_info(const vx_system *sys, int32_t *k, int32_t *npoly, int64_t *h_
 
 /* Bytes of device memory the packed system holds (what vx_system_create uploads). */
 int vx_system_device_bytes(const vx_system *sys, int64_t *bytes);
+/* Bytes vx_system_create copied from the host (the packed binary64 coefficients and the
+ * stage tables; the binary32 encodings are made on the device from them). */
+int vx_system_upload_bytes(const vx_system *sys, int64_t *bytes);
 /* Number of kernels this library has launched in this process so far (all threads). */
 int64_t vx_kernel_launches(void);
 /* Failure-path hook: how many times a kernel polls for a bulk copy before it gives up, on the

@@ -220,19 +220,56 @@ static int make_grid(int k, const double *dom, int level, LevelGrid *g) {
 // ---------------------------------------------------------------------------------------
 // polynomial packing
 // ---------------------------------------------------------------------------------------
+// uint64 monomial key -> int32 index, open addressing with linear probing (the packing looks
+// up every term once per stage; a node-based map made that the bulk of packing time).
+class FlatMap {
+ public:
+  void reserve(size_t n) {
+    size_t cap = 16;
+    while (cap < 2 * n) cap <<= 1;
+    keys_.assign(cap, 0);
+    vals_.assign(cap, -1);
+    mask_ = cap - 1;
+  }
+  void put(uint64_t key, int32_t v) {
+    size_t i = slot(key);
+    while (vals_[i] >= 0 && keys_[i] != key) i = (i + 1) & mask_;
+    keys_[i] = key;
+    vals_[i] = v;
+  }
+  int32_t get(uint64_t key) const {  // -1 if absent
+    if (vals_.empty()) return -1;
+    size_t i = slot(key);
+    while (vals_[i] >= 0) {
+      if (keys_[i] == key) return vals_[i];
+      i = (i + 1) & mask_;
+    }
+    return -1;
+  }
+
+ private:
+  size_t slot(uint64_t key) const {
+    uint64_t z = key + 0x9e3779b97f4a7c15ull;  // SplitMix64's finaliser as the hash
+    z = (z ^ (z >> 30)) * 0xbf58476d1ce4e5b9ull;
+    z = (z ^ (z >> 27)) * 0x94d049bb133111ebull;
+    return (size_t)(z ^ (z >> 31)) & mask_;
+  }
+  std::vector<uint64_t> keys_;
+  std::vector<int32_t> vals_;
+  size_t mask_ = 0;
+};
+
 struct HostStage {
   int32_t nfib = 0, maxlen = 0;
   int64_t blk_in = 0, blk_out = 0;
   std::vector<uint64_t> keys;  // fibre monomial in x_{s+2}..x_k, key_bits(k) bits per exponent
   std::vector<int32_t> rowoff, fiblen, outpos;
-  std::unordered_map<uint64_t, int32_t> index;
+  FlatMap index;
 };
 
 struct HostPoly {
   HostStage st[VX_KMAX];
   std::vector<double2> c64;
-  std::vector<float2> c32;
-  std::vector<float4> c32c;
 };
 
 // A monomial in up to k - 1 variables packed into 64 bits: 16 bits per exponent up to
@@ -246,52 +283,48 @@ static uint64_t suffix_key(const int32_t *e, int from, int k) {
   return key;
 }
 
-static float f32_round_up(double x) {
-  float f = (float)x;
-  if ((double)f < x) f = std::nextafter(f, INFINITY);
-  return f;
+// The binary32 encodings of the stage-0 coefficient block, made on the device from the
+// binary64 intervals [c.x, c.y] (c.x = c.y for a point coefficient):
+//  - midpoint-radius <m, r>: m = RN of the midpoint, r >= the larger distance to an end plus
+//    2^-149 (which pays for the rounding of the Horner step that adds this coefficient when
+//    its result falls below the normal range);
+//  - certified (RN(lo), -RN(hi)) and a bound E >= (1 + 2^-39)(d + 2^-24 max(|lo|, |hi|)) +
+//    2^-148, d the larger distance of the two ends to their binary64 values (which the
+//    binary64 path uses as they are); the 2^-24 term keeps E >= 2^-24 max(|RN(lo)|,
+//    |RN(hi)|), which the error recursion of the evaluation kernels relies on.  E is stored
+//    twice (.z and .w): a register pair for the kernels' paired steps.
+__global__ void k_encode_coefs(const double2 *__restrict__ c64, int64_t n, float2 *__restrict__ c32,
+                               float4 *__restrict__ c32c) {
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
+    const double lo = c64[i].x, hi = c64[i].y;
+    {
+      const double mid = lo == hi ? lo : __dadd_rn(__dmul_rn(0.5, lo), __dmul_rn(0.5, hi));
+      const float m = __double2float_rn(mid);
+      if (!isfinite(m)) {
+        c32[i] = make_float2(0.f, INFINITY);
+      } else {
+        const double dm = (double)m;
+        // |end - m| for the farther end, rounded up, padded for the ulp of the midpoint
+        const double d = fmax(__dadd_ru(hi, -dm), __dadd_ru(dm, -lo));
+        c32[i] = make_float2(m, __double2float_ru(__dadd_ru(__dmul_ru(d, 1.0 + 0x1p-50), 0x1p-149)));
+      }
+    }
+    {
+      const float flo = __double2float_rn(lo), fhi = __double2float_rn(hi);
+      if (!isfinite(flo) || !isfinite(fhi)) {
+        c32c[i] = make_float4(-INFINITY, -INFINITY, INFINITY, INFINITY);
+      } else {
+        const double d = fmax(fabs(lo - (double)flo), fabs(hi - (double)fhi));  // exact
+        const double mag = fmax(fabs(lo), fabs(hi));
+        // (mag 2^-24 may round below the double range; the 2^-148 term covers it)
+        const double bound = __dmul_ru(__dadd_ru(d, __dmul_ru(mag, 0x1p-24)), 1.0 + 0x1p-39);
+        const float e = __double2float_ru(__dadd_ru(bound, 0x1p-148));
+        c32c[i] = make_float4(flo, -fhi, e, e);
+      }
+    }
+  }
 }
-
-// <m, r> with r >= |c - m| + 2^-149 (the 2^-149 pays for the rounding of the Horner step
-// that adds this coefficient when its result falls below the normal range).
-static float2 to_midrad(double c) {
-  const float m = (float)c;
-  if (!std::isfinite(m)) return make_float2(0.f, INFINITY);
-  const double d = std::fabs(c - (double)m);  // exact (Sterbenz)
-  const float r = f32_round_up(d + std::ldexp(1.0, -149));
-  return make_float2(m, r);
-}
-
-
-// An interval coefficient [lo, hi] as binary32 midpoint-radius (containing it).
-static float2 to_midrad_ivl(double lo, double hi) {
-  if (lo == hi) return to_midrad(lo);
-  const float m = (float)(0.5 * lo + 0.5 * hi);
-  if (!std::isfinite(m)) return make_float2(0.f, INFINITY);
-  const double dm = (double)m;
-  const double d = std::max(hi - dm, dm - lo);  // rounded below by at most an ulp: pad it
-  const float r = f32_round_up(d * (1.0 + std::ldexp(1.0, -50)) + std::ldexp(1.0, -149));
-  return make_float2(m, r);
-}
-
-// The certified binary32 encoding of a coefficient interval [lo, hi] (lo = hi for a point):
-// (RN(lo), -RN(hi)) and a bound E >= (1 + 2^-39)(d + 2^-24 max(|lo|, |hi|)) + 2^-148, d the
-// larger distance of the two ends to their binary64 values (which the binary64 path uses as
-// they are); the 2^-24 term keeps E >= 2^-24 max(|RN(lo)|, |RN(hi)|), which the error
-// recursion of the evaluation kernels relies on.  The bound is stored twice (.z and .w): a
-// register pair for the kernels' paired steps.
-static float4 to_certified_ivl(double lo, double hi) {
-  const float flo = (float)lo, fhi = (float)hi;  // round to nearest
-  if (!std::isfinite(flo) || !std::isfinite(fhi))
-    return make_float4(-INFINITY, -INFINITY, INFINITY, INFINITY);
-  const double d = std::max(std::fabs(lo - (double)flo), std::fabs(hi - (double)fhi));  // exact
-  const double mag = std::max(std::fabs(lo), std::fabs(hi));
-  const double bound = (d + std::ldexp(mag, -24)) * (1.0 + std::ldexp(1.0, -39));
-  const float e = f32_round_up(bound + std::ldexp(1.0, -148));
-  return make_float4(flo, -fhi, e, e);
-}
-
-static float4 to_certified(double c) { return to_certified_ivl(c, c); }
 
 // chi (nullable): upper ends of interval coefficients [p.coefs[t], chi[t]]
 static int pack_poly(int k, const vx_poly &p, HostPoly *hp, const double *chi = nullptr) {
@@ -320,18 +353,18 @@ static int pack_poly(int k, const vx_poly &p, HostPoly *hp, const double *chi = 
   for (int s = k - 1; s >= 0; --s) {
     HostStage &S = hp->st[s];
     const int32_t nf = (int32_t)S.keys.size();
-    std::unordered_map<uint64_t, int32_t> idx;
-    idx.reserve(nf * 2 + 1);
-    for (int32_t f = 0; f < nf; ++f) idx[S.keys[f]] = f;
+    FlatMap idx;
+    idx.reserve((size_t)nf);
+    for (int32_t f = 0; f < nf; ++f) idx.put(S.keys[f], f);
     std::vector<int32_t> len(nf, 1);
     for (int32_t t = 0; t < nt; ++t) {
       const int32_t *e = p.exps + (int64_t)t * k;
-      auto it = idx.find(suffix_key(e, s + 1, k));
-      if (it == idx.end()) {
+      const int32_t g = idx.get(suffix_key(e, s + 1, k));
+      if (g < 0) {
         set_error("internal: monomial outside the fibre closure");
         return VX_EINVAL;
       }
-      len[it->second] = std::max(len[it->second], e[s] + 1);
+      len[g] = std::max(len[g], e[s] + 1);
     }
     std::vector<int32_t> order(nf);
     for (int32_t f = 0; f < nf; ++f) order[f] = f;
@@ -346,9 +379,8 @@ static int pack_poly(int k, const vx_poly &p, HostPoly *hp, const double *chi = 
       S.fiblen[f] = len[order[f]];
     }
     S.keys.swap(keys);
-    S.index.clear();
-    S.index.reserve(nf * 2 + 1);
-    for (int32_t f = 0; f < nf; ++f) S.index[S.keys[f]] = f;
+    S.index.reserve((size_t)nf);
+    for (int32_t f = 0; f < nf; ++f) S.index.put(S.keys[f], f);
     S.nfib = nf;
     S.maxlen = S.fiblen[0];
     S.rowoff.assign(S.maxlen + 1, 0);
@@ -387,7 +419,7 @@ static int pack_poly(int k, const vx_poly &p, HostPoly *hp, const double *chi = 
       const uint64_t mask = sh ? ((uint64_t)1 << sh) - 1 : 0;
       for (int32_t f = 0; f < S.nfib; ++f) {
         const uint64_t a = S.keys[f] >> sh;
-        const int32_t g = T.index.at(S.keys[f] & mask);
+        const int32_t g = T.index.get(S.keys[f] & mask);
         S.outpos[f] = T.rowoff[a] + g;
       }
     }
@@ -398,7 +430,7 @@ static int pack_poly(int k, const vx_poly &p, HostPoly *hp, const double *chi = 
   std::vector<uint8_t> seen(S0.blk_in, 0);
   for (int32_t t = 0; t < nt; ++t) {
     const int32_t *e = p.exps + (int64_t)t * k;
-    const int32_t f = S0.index.at(suffix_key(e, 1, k));
+    const int32_t f = S0.index.get(suffix_key(e, 1, k));
     const int64_t pos = S0.rowoff[e[0]] + f;
     if (seen[pos]) {
       set_error("polynomial: monomial %d appears twice", t);
@@ -406,12 +438,6 @@ static int pack_poly(int k, const vx_poly &p, HostPoly *hp, const double *chi = 
     }
     seen[pos] = 1;
     hp->c64[pos] = make_double2(p.coefs[t], chi ? chi[t] : p.coefs[t]);
-  }
-  hp->c32.resize(S0.blk_in);
-  hp->c32c.resize(S0.blk_in);
-  for (int64_t i = 0; i < S0.blk_in; ++i) {
-    hp->c32[i] = to_midrad_ivl(hp->c64[i].x, hp->c64[i].y);
-    hp->c32c[i] = to_certified_ivl(hp->c64[i].x, hp->c64[i].y);
   }
   return VX_OK;
 }
@@ -476,6 +502,7 @@ struct vx_system {
   SysDev dev;
   void *mem = nullptr;
   size_t bytes = 0;
+  size_t upload_bytes = 0;  // of them, copied from the host (the rest is made on the device)
   cudaStream_t stream = nullptr;
   std::vector<int64_t> M;  // [npoly][k+1]
   // the polynomials as given (exponents [nterms][k], coefficients), for dense-level plans
@@ -620,22 +647,28 @@ static int system_create_impl(const vx_poly *F, int32_t npoly, const double *con
   auto al = [](size_t x) { return (x + 255) & ~(size_t)255; };
   size_t bytes = 0;
   for (int f = 0; f < npoly; ++f) {
-    bytes += al(hp[f].c64.size() * sizeof(double2)) + al(hp[f].c32.size() * sizeof(float2)) +
-             al(hp[f].c32c.size() * sizeof(float4));
+    bytes += al(hp[f].c64.size() * sizeof(double2)) + al(hp[f].c64.size() * sizeof(float2)) +
+             al(hp[f].c64.size() * sizeof(float4));
     for (int s = 0; s < k; ++s) {
       const HostStage &S = hp[f].st[s];
       bytes += al((S.maxlen + 1) * 4) + 2 * al((size_t)S.nfib * 4);
     }
   }
-  std::vector<char> host(bytes, 0);
+  // staged in a pinned buffer from the pool: the upload runs at the link's rate
+  void *hstage = nullptr;
+  size_t hcap = 0;
+  VX_CHECK(pinned_get(bytes, &hstage, &hcap));
+  char *host = (char *)hstage;
   vx_system *sys = new (std::nothrow) vx_system();
   if (!sys) {
+    pinned_put(hstage, hcap);
     set_error("out of host memory");
     return VX_ENOMEM;
   }
   cudaStream_t s = as_stream(stream);
   int rc = dmalloc(&sys->mem, bytes, s);
   if (rc != VX_OK) {
+    pinned_put(hstage, hcap);
     delete sys;
     return rc;
   }
@@ -656,7 +689,12 @@ static int system_create_impl(const vx_poly *F, int32_t npoly, const double *con
   size_t off = 0;
   char *dbase = (char *)sys->mem;
   auto put = [&](const void *src, size_t n) -> void * {
-    std::memcpy(host.data() + off, src, n);
+    std::memcpy(host + off, src, n);
+    void *d = dbase + off;
+    off += al(n);
+    return d;
+  };
+  auto reserve = [&](size_t n) -> void * {  // device space only, filled on the device
     void *d = dbase + off;
     off += al(n);
     return d;
@@ -664,8 +702,6 @@ static int system_create_impl(const vx_poly *F, int32_t npoly, const double *con
   for (int f = 0; f < npoly; ++f) {
     PolyDev &P = sys->dev.p[f];
     P.c64 = (const double2 *)put(hp[f].c64.data(), hp[f].c64.size() * sizeof(double2));
-    P.c32 = (const float2 *)put(hp[f].c32.data(), hp[f].c32.size() * sizeof(float2));
-    P.c32c = (const float4 *)put(hp[f].c32c.data(), hp[f].c32c.size() * sizeof(float4));
     for (int s2 = 0; s2 < k; ++s2) {
       const HostStage &S = hp[f].st[s2];
       StageDev &D = P.st[s2];
@@ -679,8 +715,27 @@ static int system_create_impl(const vx_poly *F, int32_t npoly, const double *con
       sys->M[(size_t)f * (k + 1) + s2] = S.blk_in;
     }
   }
-  cudaError_t e = cudaMemcpyAsync(sys->mem, host.data(), bytes, cudaMemcpyHostToDevice, s);
+  // the binary32 blocks are made on the device from the binary64 one (k_encode_coefs), after
+  // everything that is uploaded: one copy of the prefix
+  sys->upload_bytes = off;
+  for (int f = 0; f < npoly; ++f) {
+    PolyDev &P = sys->dev.p[f];
+    P.c32 = (const float2 *)reserve(hp[f].c64.size() * sizeof(float2));
+    P.c32c = (const float4 *)reserve(hp[f].c64.size() * sizeof(float4));
+  }
+  cudaError_t e = cudaMemcpyAsync(sys->mem, host, sys->upload_bytes, cudaMemcpyHostToDevice, s);
+  for (int f = 0; f < npoly && e == cudaSuccess; ++f) {
+    const int64_t n = (int64_t)hp[f].c64.size();
+    if (n == 0) continue;
+    const int64_t nb = std::min<int64_t>((n + 255) / 256, 152 * 8);
+    k_encode_coefs<<<(unsigned)nb, 256, 0, s>>>(sys->dev.p[f].c64,
+                                                 n, const_cast<float2 *>(sys->dev.p[f].c32),
+                                                 const_cast<float4 *>(sys->dev.p[f].c32c));
+    note_launch();
+    e = cudaGetLastError();
+  }
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  pinned_put(hstage, hcap);  // the copy has completed (or failed): the buffer is free again
   if (e != cudaSuccess) {
     set_error("uploading the system failed: %s", cudaGetErrorString(e));
     dfree(sys->mem, s);
@@ -718,6 +773,16 @@ int vx_system_device_bytes(const vx_system *sys, int64_t *bytes) {
     return VX_EINVAL;
   }
   *bytes = (int64_t)sys->bytes;
+  return VX_OK;
+}
+
+int vx_system_upload_bytes(const vx_system *sys, int64_t *bytes) {
+  clear_error();
+  if (!sys || !bytes) {
+    set_error("vx_system_upload_bytes: NULL argument");
+    return VX_EINVAL;
+  }
+  *bytes = (int64_t)sys->upload_bytes;
   return VX_OK;
 }
 

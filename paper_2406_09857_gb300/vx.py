@@ -61,6 +61,7 @@ def lib() -> ctypes.CDLL:
         "vx_system_free": ([P], None),
         "vx_system_info": ([P, P, P, P], i32),
         "vx_system_device_bytes": ([P, P], i32),
+        "vx_system_upload_bytes": ([P, P], i32),
         "vx_kernel_launches": ([], i64),
         "vx_set_wait_limit": ([i64], i32),
         "vx_autotune": ([i32, ctypes.c_char_p], i32),
@@ -221,6 +222,12 @@ class System:
     def device_bytes(self) -> int:
         b = ctypes.c_int64()
         _check(lib().vx_system_device_bytes(self.handle, ctypes.byref(b)))
+        return int(b.value)
+
+    def upload_bytes(self) -> int:
+        """Bytes copied from the host when the system was made."""
+        b = ctypes.c_int64()
+        _check(lib().vx_system_upload_bytes(self.handle, ctypes.byref(b)))
         return int(b.value)
 
     def free(self):

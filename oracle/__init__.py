@@ -60,7 +60,6 @@ def lib():
         L.orc_domain_exact.argtypes = [i32, P, i32]
         L.orc_prim.argtypes = [i32, P, P, i64, P]
         L.orc_imul.argtypes = [P, P, P, P, i64, P, P]
-        L.orc_ifma.argtypes = [P, P, P, P, P, P, i64, P, P]
         L.orc_dense_powerform.argtypes = [P, P, i64, P, i32, P, i64, P, P]
         L.orc_taylor_boxes.argtypes = sysargs + [P, i32, i32, P, i64, P, P, P]
         L.orc_enclose_taylor.argtypes = sysargs + [P, i32, i32, ctypes.POINTER(P)]
@@ -300,15 +299,6 @@ def imul(alo, ahi, blo, bhi):
     lo = np.empty_like(arrs[0])
     hi = np.empty_like(arrs[0])
     lib().orc_imul(*[_p(x) for x in arrs], arrs[0].size, _p(lo), _p(hi))
-    return lo, hi
-
-
-def ifma(jlo, jhi, xlo, xhi, alo, ahi):
-    """The oracle's Horner step J*X + A on arrays of interval ends."""
-    arrs = [np.ascontiguousarray(x, dtype=np.float64) for x in (jlo, jhi, xlo, xhi, alo, ahi)]
-    lo = np.empty_like(arrs[0])
-    hi = np.empty_like(arrs[0])
-    lib().orc_ifma(*[_p(x) for x in arrs], arrs[0].size, _p(lo), _p(hi))
     return lo, hi
 
 

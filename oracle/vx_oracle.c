@@ -29,12 +29,9 @@
  *
  * Readings of the paper taken here (where it is silent or ambiguous):
  *   - Rounding (Sec. 3.2 only gives [a,b]+[c,d]=[a+c,b+d]): every lower endpoint is
- *     rounded down and every upper endpoint rounded up, in IEEE binary64.  A Horner step
- *     J*X + A is one fused multiply-add per end: the lower end is the least endpoint
- *     product plus A.lo, rounded once downward (the least of the four fused candidates),
- *     the upper end likewise upward; a product alone (a missing exponent, a trailing power,
- *     the Taylor form's terms) is [min, max] of the four endpoint products, each rounded in
- *     its own direction; min/max are the selects (b<a)?b:a and (b>a)?b:a.
+ *     rounded down and every upper endpoint rounded up, in IEEE binary64.  The product
+ *     of two intervals is [min, max] of the four endpoint products, each rounded in its
+ *     own direction; min/max are the selects (b<a)?b:a and (b>a)?b:a.
  *   - Algorithm 1 with an exponent gap g multiplies by the interval g times (repeated
  *     multiplication, not an interval power), and the result is multiplied by the interval
  *     e_0 more times when the lowest exponent e_0 is positive (the printed loop stops at
@@ -103,18 +100,6 @@ static ivl i_add(ivl x, ivl y) {
   ivl r;
   r.lo = rd_add(x.lo, y.lo);
   r.hi = ru_add(x.hi, y.hi);
-  return r;
-}
-
-/* One Horner step J*X + A as fused multiply-adds: the lower end is the least of the four
- * endpoint products plus A.lo, each rounded once downward; the upper end the greatest plus
- * A.hi, rounded once upward (-RD(-(j x) - A.hi)).  fma() rounds in the current mode. */
-static ivl i_fma(ivl j, ivl x, ivl a) {
-  ivl r;
-  r.lo = sel_min(sel_min(fma(j.lo, x.lo, a.lo), fma(j.lo, x.hi, a.lo)),
-                 sel_min(fma(j.hi, x.lo, a.lo), fma(j.hi, x.hi, a.lo)));
-  r.hi = sel_max(sel_max(-fma(-j.lo, x.lo, -a.hi), -fma(-j.lo, x.hi, -a.hi)),
-                 sel_max(-fma(-j.hi, x.lo, -a.hi), -fma(-j.hi, x.hi, -a.hi)));
   return r;
 }
 
@@ -242,12 +227,11 @@ static ivl horner_group(const stage *S, int g, const ivl *in, ivl X, int64_t *wo
   int b = S->grp[g], e = S->grp[g + 1];
   ivl J = in[S->ord[e - 1]];
   for (int t = e - 2; t >= b; --t) {
-    for (int gap = S->ex[t + 1] - S->ex[t]; gap > 1; --gap) {
-      J = i_mul(J, X); /* a missing exponent: multiply by X, add the zero coefficient */
+    for (int gap = S->ex[t + 1] - S->ex[t]; gap > 0; --gap) {
+      J = i_mul(J, X);
       ++*work;
     }
-    J = i_fma(J, X, in[S->ord[t]]);
-    ++*work;
+    J = i_add(J, in[S->ord[t]]);
   }
   for (int gap = S->ex[b]; gap > 0; --gap) {
     J = i_mul(J, X);
@@ -1459,20 +1443,6 @@ void orc_prim(int op, const double *a, const double *b, int64_t n, double *out) 
 }
 
 /* Interval product (4-product form), exported for the same reason. */
-/* The fused Horner step J*X + A on n triples of intervals (a test hook of i_fma). */
-void orc_ifma(const double *jlo, const double *jhi, const double *xlo, const double *xhi,
-              const double *alo, const double *ahi, int64_t n, double *lo, double *hi) {
-  int old = fegetround();
-  fesetround(FE_DOWNWARD);
-  for (int64_t i = 0; i < n; ++i) {
-    ivl j = {jlo[i], jhi[i]}, x = {xlo[i], xhi[i]}, a = {alo[i], ahi[i]};
-    ivl r = i_fma(j, x, a);
-    lo[i] = r.lo;
-    hi[i] = r.hi;
-  }
-  fesetround(old);
-}
-
 void orc_imul(const double *alo, const double *ahi, const double *blo, const double *bhi, int64_t n,
               double *lo, double *hi) {
   int old = fegetround();

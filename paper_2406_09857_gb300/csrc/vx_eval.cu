@@ -18,12 +18,11 @@
 // launch fills the GPU even when a depth has few nodes.
 //
 // Three arithmetics share the kernels through a policy class:
-//   A64: binary64 intervals [lo, hi]; a Horner step J*X + A is one fused multiply-add per
-//        end, rounded once outward (__fma_rd / __fma_ru).  The sign of X (fixed per node) and
-//        of J's endpoints pick the one endpoint product that is the min (max); RD/RU are
-//        monotone, so this is the same double as the min (max) of the four fused
-//        candidates.  Signs are read from the high word (integer ops), keeping the scarce
-//        FP64 pipe for the 2 arithmetic ops.
+//   A64: binary64 intervals [lo, hi] with __dmul_rd/__dmul_ru/__dadd_rd/__dadd_ru.  The
+//        product J*X uses the sign of X (fixed per node) and of J's endpoints to pick the one
+//        endpoint product that is the min (max); RD/RU are monotone, so this is the same
+//        double as the min (max) of the four directed products.  Signs are read from the
+//        high word (integer ops), keeping the scarce FP64 pipe for the 4 arithmetic ops.
 //   A32: binary32 midpoint-radius <m, r>.  One Horner step J*X + A gives
 //          m = RN(Jm*Xm + Am)
 //          r = RU(Jr*RU(|Xm|+Xr) + Ar) then RU(|Jm|*Xr + r) then RU(2^-24*|m| + r)
@@ -131,26 +130,22 @@ struct A64 {
     x.cls = (x.l >= 0.0) ? 1 : ((x.h <= 0.0) ? -1 : 0);
     return x;
   }
-  // J*X + A with one fused multiply-add per end, rounded once outward: the least (greatest)
-  // endpoint product plus A.lo (A.hi).  With the sign of X known the extreme product is
-  // picked by the sign of J's end; RD/RU are monotone, so this is the same double as the
-  // least (greatest) of the four fused candidates.
   template <int CLS>
   static __device__ __forceinline__ V step(V J, const X &x, V A) {
     double lo, hi;
     if (CLS > 0) {
-      lo = __fma_rd(J.x, sign_clear(J.x) ? x.l : x.h, A.x);
-      hi = __fma_ru(J.y, sign_clear(J.y) ? x.h : x.l, A.y);
+      lo = __dmul_rd(J.x, sign_clear(J.x) ? x.l : x.h);
+      hi = __dmul_ru(J.y, sign_clear(J.y) ? x.h : x.l);
     } else if (CLS < 0) {
-      lo = __fma_rd(J.y, sign_clear(J.y) ? x.l : x.h, A.x);
-      hi = __fma_ru(J.x, sign_clear(J.x) ? x.h : x.l, A.y);
+      lo = __dmul_rd(J.y, sign_clear(J.y) ? x.l : x.h);
+      hi = __dmul_ru(J.x, sign_clear(J.x) ? x.h : x.l);
     } else {
-      lo = sel_min(sel_min(__fma_rd(J.x, x.l, A.x), __fma_rd(J.x, x.h, A.x)),
-                   sel_min(__fma_rd(J.y, x.l, A.x), __fma_rd(J.y, x.h, A.x)));
-      hi = sel_max(sel_max(__fma_ru(J.x, x.l, A.y), __fma_ru(J.x, x.h, A.y)),
-                   sel_max(__fma_ru(J.y, x.l, A.y), __fma_ru(J.y, x.h, A.y)));
+      lo = sel_min(sel_min(__dmul_rd(J.x, x.l), __dmul_rd(J.x, x.h)),
+                   sel_min(__dmul_rd(J.y, x.l), __dmul_rd(J.y, x.h)));
+      hi = sel_max(sel_max(__dmul_ru(J.x, x.l), __dmul_ru(J.x, x.h)),
+                   sel_max(__dmul_ru(J.y, x.l), __dmul_ru(J.y, x.h)));
     }
-    return make_double2(lo, hi);
+    return make_double2(__dadd_rd(lo, A.x), __dadd_ru(hi, A.y));
   }
   static __device__ __forceinline__ V store(V J) { return J; }
   // 0: excluded, 1: kept (C0 of Sec. 3.2: excluded iff the enclosure proves the relation

@@ -61,31 +61,6 @@ def test_interval_product_is_outward_rounded_hull():
         assert hi[i] == ru(max(prods)), i
 
 
-def test_horner_step_is_one_outward_rounding():
-    """J*X + A: the least endpoint product plus A.lo rounded once down, the greatest plus
-    A.hi rounded once up (exact rationals), including cancellation and tiny results."""
-    st = synth.Stream(9)
-    n = 400
-    j = _doubles(31, n, huge=False)
-    x = _doubles(32, n, huge=False)
-    a = _doubles(33, n, huge=False)
-    jlo, jhi = j, j + np.abs(_doubles(34, n, huge=False)) * st.unit(n)
-    xlo, xhi = x, x + np.abs(_doubles(35, n, huge=False)) * st.unit(n)
-    alo, ahi = a, a + np.abs(_doubles(36, n, huge=False)) * st.unit(n)
-    # cancellations: A = -(an endpoint product) + tiny, straddling J and X, degenerate ones
-    alo[:6] = [-jlo[0] * xlo[0], -1.0, 0.0, -3.0, 2.0 ** -1060, -0.375]
-    ahi[:6] = [-jlo[0] * xlo[0], 1.0, 0.0, -3.0, 2.0 ** -1060, 0.5]
-    jlo[1:4] = [-1.0, 0.0, 1.5]
-    jhi[1:4] = [2.0, 0.0, 1.5]
-    xlo[1:4] = [-3.0, -1.0, 2.0]
-    xhi[1:4] = [0.25, 1.0, 2.0]
-    lo, hi = oracle.ifma(jlo, jhi, xlo, xhi, alo, ahi)
-    for i in range(n):
-        prods = [Fraction(p) * Fraction(q) for p in (jlo[i], jhi[i]) for q in (xlo[i], xhi[i])]
-        assert lo[i] == rd(min(prods) + Fraction(alo[i])), i
-        assert hi[i] == ru(max(prods) + Fraction(ahi[i])), i
-
-
 def test_horner_univariate_degenerate_dyadic_is_exact():
     # p(x) = 3x^4 - 2x^3 + x - 5 at dyadic points: every intermediate is exact in binary64,
     # so the interval collapses to the exact value (Algorithm 1 on a point interval).

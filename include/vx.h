@@ -105,10 +105,12 @@ typedef struct {
   float theta;          /* recheck threshold, 0 < theta <= 1 (0 means 0.5) */
   int32_t timing;       /* nonzero: time every kernel launch with CUDA events (vx_result_timing) */
   int32_t taylor_order; /* 0: C0 on nested interval Horner (Algorithm 2); m >= 1: C0 on the
-                         * Taylor form of order m (Def. 3), VX_FP64 only; the number of
-                         * multi-indices |a| <= m (C(m+k, k)) must not exceed VX_MAXPOLY */
+                         * Taylor form of order m (Def. 3), VX_FP64 or VX_FP32 (certified: the
+                         * decisions of VX_FP64); the number of multi-indices |a| <= m
+                         * (C(m+k, k)) must not exceed VX_MAXPOLY */
   int32_t c1;           /* 0, VX_C1_TAYLOR (needs taylor_order >= 2) or VX_C1_VERTEX: Algorithm 3
-                         * with the inclusion criterion, one equation, VX_FP64 only.  From level
+                         * with the inclusion criterion, one equation, VX_FP64 or VX_FP32 (the
+                         * same decisions; vertex signs in binary64).  From level
                          * c1_level on (the boxes below the size threshold) the boxes C1
                          * certifies leave the subdivision and are returned with their level
                          * (vx_result_included); the loop ends when no box is left or after
@@ -202,6 +204,16 @@ int vx_csf_eval_level(const vx_system *sys, const vx_csf *csf, const double *h_d
 int vx_csf_eval_level_taylor(const vx_system *sys, const vx_csf *csf, const double *h_domain,
                              int32_t order, double *d_lo, double *d_hi, uint8_t *d_keep,
                              void *stream);
+
+/* C0 on the Taylor form of order m >= 1 (as vx_csf_eval_level_taylor) and, when d_inc is
+ * non-null (m >= 2, one equation), C1 on it (VX_C1_TAYLOR), in mode VX_FP64 or VX_FP32: the
+ * latter evaluates the derivatives in certified binary32, brackets each binary64 value between
+ * a narrow and a wide interval and decides as binary64 does wherever both agree, the other
+ * boxes by the binary64 form (*n_recheck, nullable, receives how many).  d_keep / d_inc
+ * [N_k] device, caller-owned.  Synchronises `stream`. */
+int vx_csf_taylor_level(const vx_system *sys, const vx_csf *csf, const double *h_domain,
+                        int32_t order, int32_t mode, uint8_t *d_keep, uint8_t *d_inc,
+                        int64_t *n_recheck, void *stream);
 
 /* The inclusion criterion C1 (kind VX_C1_TAYLOR with `order` >= 2, or VX_C1_VERTEX; see
  * their definitions) of the system's one polynomial on every leaf box of the level:

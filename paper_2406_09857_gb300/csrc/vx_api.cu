@@ -1183,10 +1183,21 @@ static int taylor_sets(const vx_system *csys, int m, cudaStream_t s,
   return VX_OK;
 }
 
-// One level with C0 on the Taylor form of order m: keep = 0 in every polynomial's form.
+static __global__ void k_and_flag(uint8_t *__restrict__ flag, const uint8_t *__restrict__ keep,
+                                  int64_t n) {
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride)
+    flag[i] = flag[i] & keep[i];
+}
+
+// One level with C0 on the Taylor form of order m (and C1 on it when inc is non-null), in
+// VX_FP64 or in certified binary32 (VX_FP32): there the boxes whose decision binary32 cannot
+// certify (and that no polynomial surely excludes) are gathered into a tree of their own,
+// decided by the binary64 form, and their decisions scattered back, so every decision is the
+// binary64 one.  d_lo/d_hi (binary64 only, nullable) receive the forms.
 static int eval_taylor_level(const vx_system *sys, const CsfView &c, const LevelGrid &g, int m,
-                             double *d_lo, double *d_hi, uint8_t *keep, uint8_t *inc,
-                             cudaStream_t s, Timer *tm, int64_t *madds) {
+                             int mode, double *d_lo, double *d_hi, uint8_t *keep, uint8_t *inc,
+                             cudaStream_t s, Timer *tm, int64_t *madds, int64_t *nrecheck) {
   for (int d = 0; d < c.k; ++d)  // the centres are points of the next level's grid
     if (!grid_exact(g.ax[d].lo, 0.5 * g.ax[d].w, (int64_t)2 << c.level, 53, -1074)) {
       set_error("axis %d: the box centres of level %d are not binary64 numbers", d, c.level);
@@ -1196,22 +1207,63 @@ static int eval_taylor_level(const vx_system *sys, const CsfView &c, const Level
     set_error("C1 is a test for one equation");
     return VX_EINVAL;
   }
+  const bool cert = mode == VX_FP32;
+  if ((mode != VX_FP64 && !cert) || (cert && d_lo)) {
+    set_error("the Taylor form is evaluated in VX_FP64 or VX_FP32 (values in VX_FP64 only)");
+    return VX_EINVAL;
+  }
   std::vector<vx_system::TaylorSet> *sets = nullptr;
   VX_CHECK(taylor_sets(sys, m, s, &sets));
   const int64_t n = c.N[c.k - 1];
   *madds = 0;
-  for (int f = 0; f < sys->dev.npoly; ++f) {
+  if (nrecheck) *nrecheck = 0;
+  uint8_t *flag = nullptr;
+  if (cert) VX_CHECK(dmalloc((void **)&flag, (size_t)std::max<int64_t>(n, 1), s));
+  int rc = VX_OK;
+  for (int f = 0; f < sys->dev.npoly && rc == VX_OK; ++f) {
     const vx_system::TaylorSet &ts = (*sets)[f];
     std::vector<int8_t> al((size_t)ts.alpha.size() * VX_KMAX);
     for (size_t a = 0; a < ts.alpha.size(); ++a)
       for (int d = 0; d < VX_KMAX; ++d) al[a * VX_KMAX + d] = ts.alpha[a][d];
     int64_t w = 0;
-    VX_CHECK(eval_level_taylor(ts.sys->dev, (const int8_t(*)[VX_KMAX])al.data(), m, c, g, keep,
-                               f == 0, sys->dev.rel[f], d_lo ? d_lo + (int64_t)f * n : nullptr,
-                               d_hi ? d_hi + (int64_t)f * n : nullptr, inc, s, tm, &w));
+    rc = eval_level_taylor(ts.sys->dev, (const int8_t(*)[VX_KMAX])al.data(), m, c, g, keep, f == 0,
+                           sys->dev.rel[f], d_lo ? d_lo + (int64_t)f * n : nullptr,
+                           d_hi ? d_hi + (int64_t)f * n : nullptr, inc, flag, s, tm, &w);
     *madds += w;
   }
-  return VX_OK;
+  if (rc == VX_OK && cert && n > 0) {
+    // unsure and not surely excluded: the binary64 form decides
+    k_and_flag<<<(unsigned)std::min<int64_t>((n + 255) / 256, 4096), 256, 0, s>>>(flag, keep, n);
+    note_launch();
+    int32_t *idx = nullptr, *tup = nullptr;
+    uint8_t *subkeep = nullptr, *subinc = nullptr;
+    int64_t ns = 0;
+    rc = flag_indices(flag, n, s, &idx, &ns);
+    if (nrecheck) *nrecheck = ns;
+    if (rc == VX_OK && ns > 0) {
+      CsfObj sub;
+      const int k = c.k;
+      rc = dmalloc((void **)&tup, (size_t)ns * k * 4, s);
+      if (rc == VX_OK) rc = csf_tuples_of(c, idx, ns, tup, s);
+      if (rc == VX_OK) rc = csf_build_dev(k, c.level, tup, ns, s, &sub, tm);
+      if (rc == VX_OK) rc = dmalloc((void **)&subkeep, (size_t)ns, s);
+      if (rc == VX_OK && inc) rc = dmalloc((void **)&subinc, (size_t)ns, s);
+      int64_t w2 = 0;
+      if (rc == VX_OK)
+        rc = eval_taylor_level(sys, sub.v, g, m, VX_FP64, nullptr, nullptr, subkeep, subinc, s,
+                               tm, &w2, nullptr);
+      *madds += w2;
+      if (rc == VX_OK) rc = scatter_keep(idx, subkeep, ns, keep, s);
+      if (rc == VX_OK && inc) rc = scatter_keep(idx, subinc, ns, inc, s);
+      csf_release(&sub);
+    }
+    dfree(subinc, s);
+    dfree(subkeep, s);
+    dfree(tup, s);
+    dfree(idx, s);
+  }
+  dfree(flag, s);
+  return rc;
 }
 
 int vx_csf_eval_level_taylor(const vx_system *sys, const vx_csf *c, const double *h_domain,
@@ -1227,14 +1279,40 @@ int vx_csf_eval_level_taylor(const vx_system *sys, const vx_csf *c, const double
   cudaStream_t s = as_stream(stream);
   if (c->o.v.N[c->o.v.k - 1] == 0) return VX_OK;
   int64_t w = 0;
-  VX_CHECK(eval_taylor_level(sys, c->o.v, g, order, d_lo, d_hi, d_keep, nullptr, s, nullptr,
-                             &w));
+  VX_CHECK(eval_taylor_level(sys, c->o.v, g, order, VX_FP64, d_lo, d_hi, d_keep, nullptr, s,
+                             nullptr, &w, nullptr));
   int st = 0;
   VX_CHECK(take_device_status(s, &st));
   if (st) {
     set_error("vx_csf_eval_level_taylor: a bounded device wait gave up");
     return VX_ETIMEOUT;
   }
+  return VX_OK;
+}
+
+int vx_csf_taylor_level(const vx_system *sys, const vx_csf *c, const double *h_domain,
+                        int32_t order, int32_t mode, uint8_t *d_keep, uint8_t *d_inc,
+                        int64_t *n_recheck, void *stream) {
+  clear_error();
+  if (!sys || !c || !d_keep || c->o.v.k != sys->dev.k || order < 1 || (d_inc && order < 2)) {
+    set_error("vx_csf_taylor_level: bad arguments");
+    return VX_EINVAL;
+  }
+  LevelGrid g;
+  VX_CHECK(make_grid(c->o.v.k, h_domain, c->o.v.level, &g));
+  cudaStream_t s = as_stream(stream);
+  if (n_recheck) *n_recheck = 0;
+  if (c->o.v.N[c->o.v.k - 1] == 0) return VX_OK;
+  int64_t w = 0;
+  VX_CHECK(eval_taylor_level(sys, c->o.v, g, order, mode, nullptr, nullptr, d_keep, d_inc, s,
+                             nullptr, &w, n_recheck));
+  int st = 0;
+  VX_CHECK(take_device_status(s, &st));
+  if (st) {
+    set_error("vx_csf_taylor_level: a bounded device wait gave up");
+    return VX_ETIMEOUT;
+  }
+  VX_CUDA(cudaStreamSynchronize(s));
   return VX_OK;
 }
 
@@ -1262,8 +1340,8 @@ int vx_csf_c1(const vx_system *sys, const vx_csf *c, const double *h_domain, int
   } else {
     uint8_t *keep = nullptr;
     rc = dmalloc((void **)&keep, (size_t)n, s);
-    if (rc == VX_OK) rc = eval_taylor_level(sys, c->o.v, g, order, nullptr, nullptr, keep, d_inc,
-                                            s, nullptr, &w);
+    if (rc == VX_OK) rc = eval_taylor_level(sys, c->o.v, g, order, VX_FP64, nullptr, nullptr, keep,
+                                            d_inc, s, nullptr, &w, nullptr);
     dfree(keep, s);
   }
   int st = 0;
@@ -1427,8 +1505,9 @@ static int enclose_impl(const vx_system *sys, const double *dom, int depth, cons
     set_error("vx_enclose: theta %g outside (0, 1]", (double)theta);
     return VX_EINVAL;
   }
-  if (opts.taylor_order < 0 || (opts.taylor_order > 0 && opts.mode != VX_FP64)) {
-    set_error("vx_enclose: the Taylor form (order %d) is evaluated in VX_FP64 only",
+  if (opts.taylor_order < 0 ||
+      (opts.taylor_order > 0 && opts.mode != VX_FP64 && opts.mode != VX_FP32)) {
+    set_error("vx_enclose: the Taylor form (order %d) is evaluated in VX_FP64 or VX_FP32",
               opts.taylor_order);
     return VX_EINVAL;
   }
@@ -1441,11 +1520,11 @@ static int enclose_impl(const vx_system *sys, const double *dom, int depth, cons
       set_error("vx_enclose: unknown inclusion criterion %d", opts.c1);
       return VX_EINVAL;
     }
-    if (opts.mode != VX_FP64 || sys->dev.npoly != 1 || sys->dev.rel[0] != VX_EQ ||
-        opts.c1_level < 0 ||
+    if ((opts.mode != VX_FP64 && opts.mode != VX_FP32) || sys->dev.npoly != 1 ||
+        sys->dev.rel[0] != VX_EQ || opts.c1_level < 0 ||
         (opts.c1 == VX_C1_TAYLOR && opts.taylor_order < 2)) {
-      set_error("vx_enclose: C1 needs one equation, VX_FP64, c1_level >= 0 and, for "
-                "VX_C1_TAYLOR, taylor_order >= 2");
+      set_error("vx_enclose: C1 needs one equation, VX_FP64 or VX_FP32, c1_level >= 0 and, "
+                "for VX_C1_TAYLOR, taylor_order >= 2");
       return VX_EINVAL;
     }
   }
@@ -1495,8 +1574,9 @@ static int enclose_impl(const vx_system *sys, const double *dom, int depth, cons
     if (rc == VX_OK) {
       int64_t w = 0, nr = 0;
       if (opts.taylor_order > 0)
-        rc = n > 0 ? eval_taylor_level(sys, cur.v, g, opts.taylor_order, nullptr, nullptr, keep,
-                                       opts.c1 == VX_C1_TAYLOR ? inc : nullptr, s, tm, &w)
+        rc = n > 0 ? eval_taylor_level(sys, cur.v, g, opts.taylor_order, opts.mode, nullptr,
+                                       nullptr, keep, opts.c1 == VX_C1_TAYLOR ? inc : nullptr, s,
+                                       tm, &w, &nr)
                    : VX_OK;
       else
         rc = eval_decide(sys->dev, cur.v, g, mode, opts.fp64_recheck != 0, theta, nullptr,

@@ -226,9 +226,14 @@ struct A32C {
   static __device__ __forceinline__ X box(const AxisGrid &g, int32_t t) {
     X x;
     x.cx = 0.f;
-    if (g.fexact) {
-      x.l = __fmaf_rn((float)t, g.fw, g.flo);  // exact
-      x.h = __fmaf_rn((float)t + 1.0f, g.fw, g.flo);
+    if (g.fexact) {  // every half-grid point is a binary32 number: all exact
+      if (g.point) {
+        const float u = g.point == 1 ? 0.5f : (g.point == 3 ? 1.0f : 0.0f);
+        x.l = x.h = __fmaf_rn((float)t + u, g.fw, g.flo);
+      } else {
+        x.l = __fmaf_rn((float)t, g.fw, g.flo);
+        x.h = __fmaf_rn((float)t + 1.0f, g.fw, g.flo);
+      }
     } else {
       double l, h;
       endpoints(g, t, l, h);
@@ -244,10 +249,10 @@ struct A32C {
     x.cls = !g.fexact ? 0 : ((x.l >= 0.f) ? 1 : ((x.h <= 0.f) ? -1 : 0));
     return x;
   }
-  // Both bounds of J*X + A, each the min of two paired round-down FMAs (RD is monotone, so
-  // min(RD(a), RD(b)) = RD(min(a, b))): for X >= 0 the lower end of J*X is min(lo_J l, lo_J h)
-  // and -hi is min(-hi_J l, -hi_J h); for X <= 0 the roles of lo_J and -hi_J swap and the
-  // endpoints are negated.  No sign test on J: the two chains (lo, -hi) never mix.
+  // Both ends of J*X + A, each the min of two paired FMAs rounded to nearest: for X >= 0 the
+  // lower end of J*X is min(lo_J l, lo_J h) and -hi is min(-hi_J l, -hi_J h); for X <= 0 the
+  // roles of lo_J and -hi_J swap and the endpoints are negated.  No sign test on J: the two
+  // chains (lo, -hi) never mix.
   template <int CLS>
   static __device__ __forceinline__ V step(V J, const X &x, V A) {
     float2 r;
@@ -752,6 +757,7 @@ struct TaylorLeaf {
   int32_t c1;         // nonzero: write inc (C1 on the Taylor form)
   int8_t ei[VX_KMAX]; // index of the multi-index e_i
   uint8_t *inc;
+  uint8_t *flag;      // certified binary32 only: 1 where a decision is left to binary64
 };
 
 __device__ __forceinline__ double2 imul_hull(double2 x, double2 y) {
@@ -819,6 +825,111 @@ __global__ void __launch_bounds__(kThreads)
       }
       T.inc[i] = (at[0].x > 0.0 && at[1].y < 0.0) ? 1 : 0;
     }
+  }
+}
+
+// The Taylor form in the certified binary32 arithmetic: each G_a's value V_a comes with the
+// bound E_a on the distance of its ends to the binary64 ones, so the binary64 value lies
+// between the narrow [lo+E, hi-E] and the wide [lo-E, hi+E] interval (binary64, outward).
+// The form is inclusion-isotone in every V_a, so the binary64 form T64 lies between T(narrow)
+// and T(wide): C0 drops the box surely when T(wide) proves the relation false, keeps it surely
+// when T(narrow) exists and does not; C1 (m >= 2) is sure when the signs of the gradient's
+// midpoints are (|lo + hi| > 2E) and T(wide) / T(narrow) at V_max, V_min decide it.  Every
+// other box is flagged for the binary64 Taylor form.  keep (first = 1) or keep &= the sure-or-
+// unsure keep; flag |= unsure.
+__global__ void __launch_bounds__(kThreads)
+    k_leaf_taylor_c(LeafArgs A, const int32_t *__restrict__ lab, const int32_t *__restrict__ par,
+                    int64_t nleaves, AxisGrid gbox, AxisGrid gpoint, TaylorLeaf T,
+                    uint8_t *__restrict__ keep) {
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < nleaves; i += stride) {
+    const int32_t t = __ldg(lab + i);
+    const A32C::X xb = A32C::box(gbox, t), xp = A32C::box(gpoint, t);
+    const int64_t p = par ? (int64_t)__ldg(par + i) : 0;
+    float4 V[VX_MAXPOLY];  // (lo, -hi, E) of every G_a
+    bool finite = true;
+    for (int a = 0; a < T.na; ++a) {
+      int tot = 0;
+      for (int d = 0; d < T.k; ++d) tot += T.alpha[a][d];
+      const float4 *base = (const float4 *)A.in[a] + p * A.blk[a];
+      V[a] = horner1_any<A32C>(base, 1, A.len[a], tot < T.m ? xp : xb);
+      finite = finite && isfinite(V[a].x) && isfinite(V[a].y) && isfinite(V[a].z);
+    }
+    // the wide and the narrow interval of G_a's binary64 value
+    auto wide = [&](int a) {
+      const double e = (double)V[a].z;
+      return make_double2(__dadd_rd((double)V[a].x, -e), __dadd_ru(-(double)V[a].y, e));
+    };
+    auto narrow = [&](int a) {
+      const double e = (double)V[a].z;
+      return make_double2(__dadd_ru((double)V[a].x, e), __dadd_rd(-(double)V[a].y, -e));
+    };
+    bool nar = true;
+    for (int a = 0; a < T.na; ++a) {
+      const double2 n = narrow(a);
+      nar = nar && n.x <= n.y;
+    }
+    // the form with the box's ranges (C0), from the wide and the narrow values
+    double2 tw = make_double2(0.0, 0.0), tn = make_double2(0.0, 0.0);
+    for (int a = 0; a < T.na; ++a) {
+      double2 P = make_double2(1.0, 1.0);
+      for (int d = 0; d < T.k; ++d) P = imul_hull(P, pow_range(T.r[d], T.alpha[a][d]));
+      const double2 PW = imul_hull(wide(a), P);
+      tw = make_double2(__dadd_rd(tw.x, PW.x), __dadd_ru(tw.y, PW.y));
+      if (nar) {
+        const double2 PN = imul_hull(narrow(a), P);
+        tn = make_double2(__dadd_rd(tn.x, PN.x), __dadd_ru(tn.y, PN.y));
+      }
+    }
+    int c0 = 2;  // 0 sure exclusion, 1 sure keep, 2 unsure
+    if (finite && rel_drops(tw.x, tw.y, T.rel)) c0 = 0;
+    else if (finite && nar && !rel_drops(tn.x, tn.y, T.rel)) c0 = 1;
+    bool unsure = c0 == 2;
+    if (T.c1) {
+      // the vertex choice needs the sign of lo + hi of each first derivative, which is within
+      // 2E of the binary32 sum
+      double v[VX_KMAX];
+      bool signs = finite;
+      for (int d = 0; d < T.k; ++d) {
+        const float4 g = V[T.ei[d]];
+        const double e2 = __dmul_ru(2.0, (double)g.z);
+        const double slo = __dadd_rd(__dadd_rd((double)g.x, -(double)g.y), -e2);
+        const double shi = __dadd_ru(__dadd_ru((double)g.x, -(double)g.y), e2);
+        const bool pos = slo >= 0.0, neg = shi < 0.0;
+        signs = signs && (pos || neg);
+        v[d] = pos ? T.r[d] : -T.r[d];
+      }
+      int inc = 2;  // 0 surely not certified, 1 surely certified, 2 unsure
+      if (signs) {
+        double2 aw[2], an[2];
+        for (int side = 0; side < 2; ++side) {  // 0: V_max, 1: V_min
+          double2 sw = make_double2(0.0, 0.0), sn = make_double2(0.0, 0.0);
+          for (int a = 0; a < T.na; ++a) {
+            double2 P = make_double2(1.0, 1.0);
+            for (int d = 0; d < T.k; ++d) {
+              const double x = side == 0 ? v[d] : -v[d];
+              for (int e = 0; e < T.alpha[a][d]; ++e) P = imul_hull(P, make_double2(x, x));
+            }
+            const double2 PW = imul_hull(wide(a), P);
+            sw = make_double2(__dadd_rd(sw.x, PW.x), __dadd_ru(sw.y, PW.y));
+            if (nar) {
+              const double2 PN = imul_hull(narrow(a), P);
+              sn = make_double2(__dadd_rd(sn.x, PN.x), __dadd_ru(sn.y, PN.y));
+            }
+          }
+          aw[side] = sw;
+          an[side] = sn;
+        }
+        if (aw[0].x > 0.0 && aw[1].y < 0.0) inc = 1;
+        else if (nar && (an[0].x <= 0.0 || an[1].y >= 0.0)) inc = 0;
+      }
+      unsure = unsure || (c0 != 0 && inc == 2);
+      T.inc[i] = inc == 1 ? 1 : 0;
+    }
+    const uint8_t k0 = c0 == 0 ? 0 : 1;
+    keep[i] = T.first ? k0 : (uint8_t)(keep[i] & k0);
+    const uint8_t fl = unsure ? 1 : 0;
+    T.flag[i] = T.first ? fl : (uint8_t)(T.flag[i] | fl);
   }
 }
 
@@ -1519,8 +1630,19 @@ int eval_level_t(const SysDev &sys, const CsfView &c, const LevelGrid &grid, dou
             set_error("Taylor leaf launch failed");
             rc = VX_ECUDA;
           }
+        } else if constexpr (std::is_same<AR, A32C>::value) {
+          AxisGrid gp = grid.ax[k - 1];
+          gp.point = 1;  // binary32-exact centres when the grid's half points are (fexact)
+          k_leaf_taylor_c<<<leaf_grid(nleaves), kThreads, 0, s>>>(
+              A, c.lab[k - 1], k == 1 ? nullptr : c.par[k - 1], nleaves, grid.ax[k - 1], gp, *tl,
+              d_keep);
+          note_launch();
+          if (cudaGetLastError() != cudaSuccess) {
+            set_error("Taylor leaf launch failed");
+            rc = VX_ECUDA;
+          }
         } else {
-          set_error("the Taylor form is evaluated in binary64 only");
+          set_error("the Taylor form is evaluated in binary64 or certified binary32 only");
           rc = VX_EINVAL;
         }
       } else {
@@ -1761,8 +1883,8 @@ int eval_forest(int arith, const ForestTree *d_trees, const ForestTree *h_trees,
 
 int eval_level_taylor(const SysDev &tsys, const int8_t (*alpha)[VX_KMAX], int m,
                       const CsfView &c, const LevelGrid &grid, uint8_t *d_keep, int first, int rel,
-                      double *d_lo, double *d_hi, uint8_t *d_inc, cudaStream_t s, Timer *tm,
-                      int64_t *madds) {
+                      double *d_lo, double *d_hi, uint8_t *d_inc, uint8_t *d_flag, cudaStream_t s,
+                      Timer *tm, int64_t *madds) {
   const int k = c.k;
   TaylorLeaf tl{};
   tl.na = tsys.npoly;
@@ -1802,6 +1924,14 @@ int eval_level_taylor(const SysDev &tsys, const int8_t (*alpha)[VX_KMAX], int m,
       }
   }
   for (int d = 0; d < k; ++d) tl.r[d] = 0.5 * grid.ax[d].w;  // exact (dyadic widths)
+  if (d_flag) {  // certified binary32: the derivatives' stages and leaves in A32C
+    tl.flag = d_flag;
+    for (int a = 0; a < tsys.npoly; ++a)
+      for (int d = 0; d < k; ++d)
+        if (pg[a].ax[d].point) pg[a].ax[d].fexact = grid.ax[d].fexact;
+    return eval_level_t<A32C>(tsys, c, grid, nullptr, nullptr, d_keep, nullptr, 0.f, s, tm, madds,
+                              KK_STAGE0_F32C, nullptr, 0, pg.data(), &tl);
+  }
   return eval_level_t<A64>(tsys, c, grid, nullptr, nullptr, d_keep, nullptr, 0.f, s, tm, madds,
                            KK_STAGE0, nullptr, 0, pg.data(), &tl);
 }

@@ -170,11 +170,14 @@ int eval_forest(int arith, const ForestTree *d_trees, const ForestTree *h_trees,
 // holds G_a = d^a F / a! for the multi-indices alpha[0..npoly-1] (|a| <= m, lexicographic);
 // keep = C0 on T for the relation rel (first = 1) or keep &= that (first = 0); d_lo/d_hi
 // (nullable) receive T;
-// d_inc (nullable, m >= 2) receives the inclusion criterion C1 on the Taylor form.
+// d_inc (nullable, m >= 2) receives the inclusion criterion C1 on the Taylor form.  d_flag
+// non-null: the certified binary32 arithmetic (decisions as binary64 takes them, except on the
+// boxes flagged there (flag |= unsure), which the caller re-decides in binary64; d_lo/d_hi
+// must then be null).
 int eval_level_taylor(const SysDev &tsys, const int8_t (*alpha)[VX_KMAX], int m,
                       const CsfView &c, const LevelGrid &grid, uint8_t *d_keep, int first, int rel,
-                      double *d_lo, double *d_hi, uint8_t *d_inc, cudaStream_t s, Timer *tm,
-                      int64_t *madds);
+                      double *d_lo, double *d_hi, uint8_t *d_inc, uint8_t *d_flag, cudaStream_t s,
+                      Timer *tm, int64_t *madds);
 // The inclusion criterion C1 by vertex signs (Sec. 3.2) of the system's one polynomial on
 // every leaf: each of the 2^k corners of the boxes is evaluated through the CSF in binary64
 // (point intervals); d_inc[i] = 1 iff one corner is certified > 0 and another < 0.

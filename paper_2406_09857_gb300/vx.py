@@ -78,6 +78,7 @@ def lib() -> ctypes.CDLL:
         "vx_csf_eval_grid": ([P, P, P, P, P, i32, P, P, P, P], i32),
         "vx_csf_eval_level_taylor": ([P, P, P, i32, P, P, P, P], i32),
         "vx_csf_c1": ([P, P, P, i32, i32, P, P], i32),
+        "vx_csf_taylor_level": ([P, P, P, i32, i32, P, P, P, P], i32),
         "vx_result_included": ([P, P, P, P], i32),
         "vx_csf_subdivide": ([P, P, P, PP], i32),
         "vx_csf_compact": ([P, P, P, P, PP], i32),
@@ -342,6 +343,22 @@ def csf_eval_level_taylor(system: System, csf: Csf, domain, order, values=False,
     if values:
         return keep[:n], lo[:, :n], hi[:, :n]
     return keep[:n]
+
+
+def csf_taylor_level(system: System, csf: Csf, domain, order, mode=FP64, c1=False, stream=None):
+    """C0 (and with c1, C1) on the Taylor form of the given order in mode FP64 or FP32
+    (certified): (keep uint8 [n], inc uint8 [n] or None, boxes re-decided in binary64)."""
+    import torch
+
+    _, _, N = csf.nodes()
+    n = int(N[-1])
+    keep = torch.empty(max(n, 1), dtype=torch.uint8, device="cuda")
+    inc = torch.empty(max(n, 1), dtype=torch.uint8, device="cuda") if c1 else None
+    nr = ctypes.c_int64()
+    _check(lib().vx_csf_taylor_level(system.handle, csf.handle, _np_ptr(_domain(domain)),
+                                     int(order), int(mode), _ptr(keep), _ptr(inc),
+                                     ctypes.byref(nr), _stream(stream)))
+    return keep[:n], (inc[:n] if c1 else None), int(nr.value)
 
 
 def csf_c1(system: System, csf: Csf, domain, kind, order=0, stream=None):

@@ -6,7 +6,7 @@
   certified boxes with their levels, the same boxes left at the last level and the same
   per-level counts as the oracle (the circle, whose C1 never certifies the boxes touching it
   at a dyadic vertex; random polynomials; a Table-1 hypersurface);
-- what it refuses: several equations, binary32, the Taylor test without a Taylor form.
+- what it refuses: several equations, midpoint-radius binary32, the Taylor test without a Taylor form.
 """
 import math
 
@@ -115,7 +115,7 @@ def test_refusals(vx):
     assert e.value.code == vx.EINVAL
     one = two[:1]
     with pytest.raises(vx.VxError) as e:
-        vx.enclose(one, synth.cube(2), 4, vx.make_opts(vx.FP32, c1=vx.C1_VERTEX))
+        vx.enclose(one, synth.cube(2), 4, vx.make_opts(vx.FP32_MIDRAD, c1=vx.C1_VERTEX))
     assert e.value.code == vx.EINVAL
     with pytest.raises(vx.VxError) as e:
         vx.enclose(one, synth.cube(2), 4, vx.make_opts(vx.FP64, c1=vx.C1_TAYLOR, taylor_order=1))

@@ -342,7 +342,8 @@ def bench_table1(vx, synth, torch, stream, taylor=True):
     equations) and curves (k-1) to boxes of size 2^-8 (depth 10), hypersurfaces to 2^-5
     (depth 7) with exclusion only.  Certified binary32 enclosure time (system resident, CUDA
     events, best of 2 after a warm-up) and boxes; the paper's seconds as context.  With
-    `taylor`, the same cells with C0 on the order-2 Taylor form in binary64 (one timed run)."""
+    `taylor`, the same cells with C0 on the order-2 Taylor form in certified binary32 and in
+    binary64 (one timed run each), and the hypersurfaces with C1 too."""
     out = {}
     for (k, d), paper in PAPER_TABLE1_S.items():
         for kind in ("points", "curves", "hypersurfaces"):
@@ -385,38 +386,43 @@ def bench_table1(vx, synth, torch, stream, taylor=True):
                 "paper_voxelize_s": paper[kind]}
             r.free()
             if taylor:
-                # C0 on the Taylor form of order 2 (Def. 3), binary64, same depth
-                to = vx.make_opts(vx.FP64, taylor_order=2)
-                vx.enclose_system(sysv, s.domain, min(depth, 3), to, stream=stream).free()
+                # C0 on the Taylor form of order 2 (Def. 3) at the same depth, in certified
+                # binary32 (the decisions of binary64) and in binary64
                 e0 = torch.cuda.Event(enable_timing=True)
                 e1 = torch.cuda.Event(enable_timing=True)
-                e0.record(stream)
-                rt = vx.enclose_system(sysv, s.domain, depth, to, stream=stream)
-                e1.record(stream)
-                e1.synchronize()
-                tst = rt.stats()
-                cell["taylor2_fp64"] = {"ms": round(e0.elapsed_time(e1), 3),
-                                        "boxes": int(tst["kept"][-1]),
-                                        "box_evals": int(tst["tested"].sum())}
-                rt.free()
+                for tag, mode in (("fp32", vx.FP32), ("fp64", vx.FP64)):
+                    to = vx.make_opts(mode, taylor_order=2)
+                    vx.enclose_system(sysv, s.domain, min(depth, 3), to, stream=stream).free()
+                    e0.record(stream)
+                    rt = vx.enclose_system(sysv, s.domain, depth, to, stream=stream)
+                    e1.record(stream)
+                    e1.synchronize()
+                    tst = rt.stats()
+                    cell["taylor2_" + tag] = {"ms": round(e0.elapsed_time(e1), 3),
+                                              "boxes": int(tst["kept"][-1]),
+                                              "box_evals": int(tst["tested"].sum()),
+                                              "binary64_rechecks": int(tst["recheck"].sum())}
+                    rt.free()
                 if kind == "hypersurfaces":
                     # as the paper's hypersurface row: C0 and C1 on the Taylor form, C1 from
                     # the size threshold (level 7) on, until no box is left (cap: level 14)
                     cap = 14
-                    to = vx.make_opts(vx.FP64, taylor_order=2, c1=vx.C1_TAYLOR, c1_level=depth)
-                    e0.record(stream)
-                    rt = vx.enclose_system(sysv, s.domain, cap, to, stream=stream)
-                    e1.record(stream)
-                    e1.synchronize()
-                    tst = rt.stats()
-                    lev, _ = rt.included()
-                    cell["taylor2_c1_fp64"] = {
-                        "ms": round(e0.elapsed_time(e1), 3), "c1_level": depth,
-                        "level_cap": cap, "certified": int(lev.shape[0]),
-                        "certified_per_level": np.bincount(lev, minlength=cap + 1)[depth:].tolist(),
-                        "undecided_at_cap": int(tst["kept"][-1] - np.sum(lev == cap)),
-                        "box_evals": int(tst["tested"].sum())}
-                    rt.free()
+                    for tag, mode in (("fp32", vx.FP32), ("fp64", vx.FP64)):
+                        to = vx.make_opts(mode, taylor_order=2, c1=vx.C1_TAYLOR, c1_level=depth)
+                        e0.record(stream)
+                        rt = vx.enclose_system(sysv, s.domain, cap, to, stream=stream)
+                        e1.record(stream)
+                        e1.synchronize()
+                        tst = rt.stats()
+                        lev, _ = rt.included()
+                        cell["taylor2_c1_" + tag] = {
+                            "ms": round(e0.elapsed_time(e1), 3), "c1_level": depth,
+                            "level_cap": cap, "certified": int(lev.shape[0]),
+                            "certified_per_level": np.bincount(lev, minlength=cap + 1)[depth:].tolist(),
+                            "undecided_at_cap": int(tst["kept"][-1] - np.sum(lev == cap)),
+                            "box_evals": int(tst["tested"].sum()),
+                            "binary64_rechecks": int(tst["recheck"].sum())}
+                        rt.free()
             out["k%d-d%d-%s" % (k, d, kind)] = cell
             sysv.free()
     return out
@@ -439,6 +445,7 @@ def bench_applications(vx, synth, torch, stream):
         for depth in depths:
             runs = [("fp32", vx.make_opts(vx.FP32)), ("fp64", vx.make_opts(vx.FP64))]
             if math.comb(2 + s.k, s.k) <= vx.MAXPOLY:  # the order-2 form's derivatives
+                runs.append(("taylor2_fp32", vx.make_opts(vx.FP32, taylor_order=2)))
                 runs.append(("taylor2_fp64", vx.make_opts(vx.FP64, taylor_order=2)))
             for name, opts in runs:
                 vx.enclose_system(sysv, s.domain, depth, opts, stream=stream).free()

@@ -829,14 +829,14 @@ __global__ void __launch_bounds__(kThreads)
 }
 
 // The Taylor form in the certified binary32 arithmetic: each G_a's value V_a comes with the
-// bound E_a on the distance of its ends to the binary64 ones, so the binary64 value lies
-// between the narrow [lo+E, hi-E] and the wide [lo-E, hi+E] interval (binary64, outward).
-// The form is inclusion-isotone in every V_a, so the binary64 form T64 lies between T(narrow)
-// and T(wide): C0 drops the box surely when T(wide) proves the relation false, keeps it surely
-// when T(narrow) exists and does not; C1 (m >= 2) is sure when the signs of the gradient's
-// midpoints are (|lo + hi| > 2E) and T(wide) / T(narrow) at V_max, V_min decide it.  Every
-// other box is flagged for the binary64 Taylor form.  keep (first = 1) or keep &= the sure-or-
-// unsure keep; flag |= unsure.
+// bound E_a on the distance of its ends to the binary64 ones.  The binary64 form T64 then lies
+// in the form of the wide intervals [lo-E, hi+E], and T64.lo / T64.hi are bounded above /
+// below through single points of the possible ends (U, L below), which works for thin (point)
+// values too: C0 drops the box surely when the wide form proves the relation false, keeps it
+// surely when the bounds show that T64 cannot be dropped; C1 (m >= 2) is sure when the signs
+// of the gradient's midpoints are (|lo + hi| > 2E) and the same bounds at V_max, V_min decide
+// it.  Every other box is flagged for the binary64 Taylor form.  keep (first = 1) or keep &=
+// the sure-or-unsure keep; flag |= unsure.
 __global__ void __launch_bounds__(kThreads)
     k_leaf_taylor_c(LeafArgs A, const int32_t *__restrict__ lab, const int32_t *__restrict__ par,
                     int64_t nleaves, AxisGrid gbox, AxisGrid gpoint, TaylorLeaf T,
@@ -855,35 +855,43 @@ __global__ void __launch_bounds__(kThreads)
       V[a] = horner1_any<A32C>(base, 1, A.len[a], tot < T.m ? xp : xb);
       finite = finite && isfinite(V[a].x) && isfinite(V[a].y) && isfinite(V[a].z);
     }
-    // the wide and the narrow interval of G_a's binary64 value
-    auto wide = [&](int a) {
-      const double e = (double)V[a].z;
-      return make_double2(__dadd_rd((double)V[a].x, -e), __dadd_ru(-(double)V[a].y, e));
+    // G_a's binary64 value [l64, h64] has l64 in [lo-E, lo+E] and h64 in [hi-E, hi+E]: the
+    // wide interval [lo-E, hi+E] contains it; and for any factor P, lo(V*P) <= l64 p for each
+    // end p of P, so lo(V*P) <= min_p max(RU((lo-E) p), RU((lo+E) p)) =: U, and likewise
+    // hi(V*P) >= max_p min(RD((hi-E) p), RD((hi+E) p)) =: L, even when V is thin (a point).
+    auto ends = [&](int a, double &l1, double &l2, double &h1, double &h2) {
+      const double e = (double)V[a].z, lo = (double)V[a].x, hi = -(double)V[a].y;
+      l1 = __dadd_rd(lo, -e);
+      l2 = __dadd_ru(lo, e);
+      h1 = __dadd_rd(hi, -e);
+      h2 = __dadd_ru(hi, e);
     };
-    auto narrow = [&](int a) {
-      const double e = (double)V[a].z;
-      return make_double2(__dadd_ru((double)V[a].x, e), __dadd_rd(-(double)V[a].y, -e));
+    // one term V_a * P (P = [pl, ph]): its wide enclosure and the bounds U, L above
+    auto term = [&](int a, double2 P, double2 &w, double &u, double &l) {
+      double l1, l2, h1, h2;
+      ends(a, l1, l2, h1, h2);
+      w = imul_hull(make_double2(l1, h2), P);
+      u = sel_min(sel_max(__dmul_ru(l1, P.x), __dmul_ru(l2, P.x)),
+                  sel_max(__dmul_ru(l1, P.y), __dmul_ru(l2, P.y)));
+      l = sel_max(sel_min(__dmul_rd(h1, P.x), __dmul_rd(h2, P.x)),
+                  sel_min(__dmul_rd(h1, P.y), __dmul_rd(h2, P.y)));
     };
-    bool nar = true;
-    for (int a = 0; a < T.na; ++a) {
-      const double2 n = narrow(a);
-      nar = nar && n.x <= n.y;
-    }
-    // the form with the box's ranges (C0), from the wide and the narrow values
-    double2 tw = make_double2(0.0, 0.0), tn = make_double2(0.0, 0.0);
+    // the form with the box's ranges (C0): T64 lies in tw, T64.lo <= tu, T64.hi >= tl
+    double2 tw = make_double2(0.0, 0.0);
+    double tu = 0.0, tlo = 0.0;
     for (int a = 0; a < T.na; ++a) {
       double2 P = make_double2(1.0, 1.0);
       for (int d = 0; d < T.k; ++d) P = imul_hull(P, pow_range(T.r[d], T.alpha[a][d]));
-      const double2 PW = imul_hull(wide(a), P);
-      tw = make_double2(__dadd_rd(tw.x, PW.x), __dadd_ru(tw.y, PW.y));
-      if (nar) {
-        const double2 PN = imul_hull(narrow(a), P);
-        tn = make_double2(__dadd_rd(tn.x, PN.x), __dadd_ru(tn.y, PN.y));
-      }
+      double2 w;
+      double u, l;
+      term(a, P, w, u, l);
+      tw = make_double2(__dadd_rd(tw.x, w.x), __dadd_ru(tw.y, w.y));
+      tu = __dadd_ru(tu, u);
+      tlo = __dadd_rd(tlo, l);
     }
     int c0 = 2;  // 0 sure exclusion, 1 sure keep, 2 unsure
     if (finite && rel_drops(tw.x, tw.y, T.rel)) c0 = 0;
-    else if (finite && nar && !rel_drops(tn.x, tn.y, T.rel)) c0 = 1;
+    else if (finite && !rel_drops(tu, tlo, T.rel)) c0 = 1;  // some T64 between them keeps
     bool unsure = c0 == 2;
     if (T.c1) {
       // the vertex choice needs the sign of lo + hi of each first derivative, which is within
@@ -901,27 +909,31 @@ __global__ void __launch_bounds__(kThreads)
       }
       int inc = 2;  // 0 surely not certified, 1 surely certified, 2 unsure
       if (signs) {
-        double2 aw[2], an[2];
+        double2 aw[2];
+        double au[2], al[2];
         for (int side = 0; side < 2; ++side) {  // 0: V_max, 1: V_min
-          double2 sw = make_double2(0.0, 0.0), sn = make_double2(0.0, 0.0);
+          double2 sw = make_double2(0.0, 0.0);
+          double su = 0.0, sl = 0.0;
           for (int a = 0; a < T.na; ++a) {
             double2 P = make_double2(1.0, 1.0);
             for (int d = 0; d < T.k; ++d) {
               const double x = side == 0 ? v[d] : -v[d];
               for (int e = 0; e < T.alpha[a][d]; ++e) P = imul_hull(P, make_double2(x, x));
             }
-            const double2 PW = imul_hull(wide(a), P);
-            sw = make_double2(__dadd_rd(sw.x, PW.x), __dadd_ru(sw.y, PW.y));
-            if (nar) {
-              const double2 PN = imul_hull(narrow(a), P);
-              sn = make_double2(__dadd_rd(sn.x, PN.x), __dadd_ru(sn.y, PN.y));
-            }
+            double2 w;
+            double u, l;
+            term(a, P, w, u, l);
+            sw = make_double2(__dadd_rd(sw.x, w.x), __dadd_ru(sw.y, w.y));
+            su = __dadd_ru(su, u);
+            sl = __dadd_rd(sl, l);
           }
           aw[side] = sw;
-          an[side] = sn;
+          au[side] = su;
+          al[side] = sl;
         }
+        // certified: lower end at V_max > 0 and upper end at V_min < 0
         if (aw[0].x > 0.0 && aw[1].y < 0.0) inc = 1;
-        else if (nar && (an[0].x <= 0.0 || an[1].y >= 0.0)) inc = 0;
+        else if (au[0] <= 0.0 || al[1] >= 0.0) inc = 0;
       }
       unsure = unsure || (c0 != 0 && inc == 2);
       T.inc[i] = inc == 1 ? 1 : 0;
@@ -1924,7 +1936,7 @@ int eval_level_taylor(const SysDev &tsys, const int8_t (*alpha)[VX_KMAX], int m,
       }
   }
   for (int d = 0; d < k; ++d) tl.r[d] = 0.5 * grid.ax[d].w;  // exact (dyadic widths)
-  if (d_flag) {  // certified binary32: the derivatives' stages and leaves in A32C
+  if (d_flag) {  // certified binary32: every G_a in A32C
     tl.flag = d_flag;
     for (int a = 0; a < tsys.npoly; ++a)
       for (int d = 0; d < k; ++d)

@@ -1,0 +1,91 @@
+"""Parity at the full sizes of the benchmark, in the configuration it times, on sampled boxes
+the oracle decides one by one (each box on its own, nested interval Horner in binary64):
+
+- the curve (two Kostlan polynomials of degree 100, [-1,1]^3, depth 10: 417 M box
+  evaluations) in certified binary32: every sampled returned box is kept by the oracle, every
+  sampled box of the finest grid that is not returned is excluded by it (by isotonicity a box
+  whose ancestor was excluded is excluded itself), the neighbours of returned boxes included;
+  the binary64 enclosure returns the same boxes;
+- the dense full-grid level (degree 128 per variable at level 10: 1.07 G boxes) through the
+  tensor-core prefilter and the exact interval path: sampled kept and dropped boxes agree with
+  the oracle.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2406_09857_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def vx():
+    import torch
+
+    assert torch.cuda.is_available(), "GPU tests need a CUDA device"
+    from paper_2406_09857_gb300 import build
+    from paper_2406_09857_gb300 import vx as _vx
+
+    build.build()
+    _vx.lib()
+    return _vx
+
+
+def _lex_sorted(t):
+    return t[np.lexsort(t.T[::-1])]
+
+
+def test_curve_depth10_sampled(vx):
+    s = synth.curve()
+    sysv = vx.System(s.polys)
+    r32 = vx.enclose_system(sysv, s.domain, 10, vx.make_opts(vx.FP32))
+    boxes = r32.boxes()
+    assert boxes.shape[0] > 1_000_000
+    st = synth.Stream(20240609)
+    # returned boxes: kept by the oracle
+    pick = boxes[np.unique(st.uniform_int(0, boxes.shape[0] - 1, 100))]
+    _, _, keep, _ = oracle.eval_boxes(s.polys, s.domain, 10, pick)
+    assert keep.all()
+    # neighbours of returned boxes that are not returned, and uniform boxes: excluded
+    key = lambda t: (t[:, 0].astype(np.int64) << 20) | (t[:, 1].astype(np.int64) << 10) | t[:, 2]
+    have = np.sort(key(boxes))
+    cand = []
+    for b in pick[:40]:
+        for d in range(3):
+            for sgn in (-1, 1):
+                c = b.copy()
+                c[d] += sgn
+                if 0 <= c[d] < 1024:
+                    cand.append(c)
+    cand += list(st.uniform_int(0, 1023, 3 * 100).reshape(-1, 3).astype(np.int32))
+    cand = np.unique(np.array(cand, dtype=np.int32), axis=0)
+    pos = np.searchsorted(have, key(cand))
+    returned = (pos < have.size) & (have[np.minimum(pos, have.size - 1)] == key(cand))
+    out = _lex_sorted(cand[~returned])
+    assert out.shape[0] > 50
+    _, _, keep_out, _ = oracle.eval_boxes(s.polys, s.domain, 10, out)
+    assert not keep_out.any()
+    # the binary64 enclosure: the same boxes
+    r64 = vx.enclose_system(sysv, s.domain, 10, vx.make_opts(vx.FP64))
+    assert np.array_equal(r64.boxes(), boxes)
+    assert np.array_equal(r64.stats()["kept"], r32.stats()["kept"])
+
+
+def test_dense_degree128_level10_sampled(vx):
+    s = synth.dense_sweep(128)
+    sysv = vx.System(s.polys)
+    plan = vx.DensePlan(sysv, 10, s.domain)
+    keep, nsurv = plan.level_keep(vx.make_opts(vx.FP32))
+    keep = keep.cpu().numpy()
+    assert 0 < keep.sum() < keep.size and nsurv >= keep.sum()
+    st = synth.Stream(128)
+    kept_idx = np.flatnonzero(keep)
+    drop_idx = np.flatnonzero(keep == 0)
+    sel = np.concatenate([kept_idx[np.unique(st.uniform_int(0, kept_idx.size - 1, 20))],
+                          drop_idx[np.unique(st.uniform_int(0, drop_idx.size - 1, 20))]])
+    sel = np.sort(sel)
+    t = np.stack([sel >> 20, (sel >> 10) & 1023, sel & 1023], axis=1).astype(np.int32)
+    _, _, keep_o, _ = oracle.eval_boxes(s.polys, s.domain, 10, t)
+    assert np.array_equal(keep[sel], keep_o)
+    plan.free()

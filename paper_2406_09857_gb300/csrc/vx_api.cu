@@ -12,6 +12,7 @@
 #include <array>
 #include <atomic>
 #include <map>
+#include <memory>
 #include <mutex>
 #include <thread>
 #include <cmath>
@@ -654,11 +655,24 @@ static int system_create_impl(const vx_poly *F, int32_t npoly, const double *con
       bytes += al((S.maxlen + 1) * 4) + 2 * al((size_t)S.nfib * 4);
     }
   }
-  // staged in a pinned buffer from the pool: the upload runs at the link's rate
+  // large systems are staged in a pinned buffer from the pool (the upload then runs at the
+  // link's rate); small ones in ordinary memory, which many systems packed at once (batches)
+  // would otherwise turn into pinned allocations
   void *hstage = nullptr;
   size_t hcap = 0;
-  VX_CHECK(pinned_get(bytes, &hstage, &hcap));
-  char *host = (char *)hstage;
+  std::unique_ptr<char[]> small;
+  char *host = nullptr;
+  if (bytes >= ((size_t)4 << 20)) {
+    VX_CHECK(pinned_get(bytes, &hstage, &hcap));
+    host = (char *)hstage;
+  } else {
+    small.reset(new (std::nothrow) char[std::max<size_t>(bytes, 1)]);
+    host = small.get();
+    if (!host) {
+      set_error("out of host memory");
+      return VX_ENOMEM;
+    }
+  }
   vx_system *sys = new (std::nothrow) vx_system();
   if (!sys) {
     pinned_put(hstage, hcap);

@@ -222,6 +222,51 @@ def bench_dense(vx, synth, torch, stream, flush, d=128, level=10, reps=2):
     return out
 
 
+def bench_dense_sweep(vx, synth, torch, stream, flush):
+    """Config 5's sweep: degree d in {32, 64, 128} per variable, N in {256, 512, 1024} boxes per
+    axis; per cell the full-grid level in certified binary32 and binary64 (interval path) and
+    on the tensor cores (prefilter, then the survivors decided exactly); kept sets compared."""
+    out = {}
+
+    def timed(fn):
+        fn()
+        flush.fill_(1.0)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        r = fn()
+        e1.record(stream)
+        e1.synchronize()
+        return e0.elapsed_time(e1), r
+
+    for d in (32, 64, 128):
+        s = synth.dense_sweep(d)
+        sysv = vx.System(s.polys, stream=stream)
+        for level in (8, 9, 10):
+            n = 1 << (3 * level)
+            c = vx.csf_full_grid(3, level)
+            ms32, k32 = timed(lambda: vx.csf_eval_level(sysv, c, s.domain, vx.FP32, stream=stream))
+            ms64, k64 = timed(lambda: vx.csf_eval_level(sysv, c, s.domain, vx.FP64, stream=stream))
+            c.free()
+            plan = vx.DensePlan(sysv, level, s.domain, stream=stream)
+            keep = torch.empty(n, dtype=torch.uint8, device="cuda")
+            mstc, (_, surv) = timed(lambda: plan.level_keep(vx.make_opts(vx.FP32), keep=keep,
+                                                            stream=stream))
+            mask = torch.empty(n // 32, dtype=torch.int32, device="cuda")
+            mspre, _ = timed(lambda: plan.prefilter(mask, stream=stream))
+            plan.free()
+            out["d%d-N%d" % (d, 1 << level)] = {
+                "boxes": n, "kept": int(k64.sum().item()),
+                "fp32_ms": round(ms32, 3), "fp64_ms": round(ms64, 3),
+                "tc_prefilter_ms": round(mspre, 3), "tc_exact_ms": round(mstc, 3),
+                "tc_survivors": int(surv),
+                "tc_exact_box_evals_per_s": n / (mstc * 1e-3),
+                "fp32_equals_fp64": bool(torch.equal(k32, k64)),
+                "tc_exact_equals_fp64": bool(torch.equal(keep, k64))}
+        sysv.free()
+    return out
+
+
 def bench_dense_tc(vx, torch, stream, flush, sysv, s, d, level, reps, keep64, best_ms):
     """The same level on the tensor cores: the power-form prefilter (TF32 contractions, a
     superset of the kept boxes) alone, and the level decided exactly (prefilter, then the
@@ -708,6 +753,7 @@ def run_gpu(args):
     if rank == 0 and world == 1 and not args.no_extra:
         log("[bench] dense level and batch")
         extra["dense_level"] = bench_dense(vx, synth, torch, stream, flush)
+        extra["dense_sweep"] = bench_dense_sweep(vx, synth, torch, stream, flush)
         extra["batch"] = bench_batch(vx, synth, torch)
         extra["precision"] = bench_precision(vx, synth, torch)
         extra["table1"] = bench_table1(vx, synth, torch, stream)

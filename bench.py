@@ -52,6 +52,10 @@ FP64_PEAK_T = SMS * 2 * SM_MHZ * 1e6 / 1e12    # 0.63 T instructions/s
 # multiplies + 2 directed adds.
 OPS_PER_MADD = {"fp32": 4, "fp64": 4}
 L2_FLUSH_BYTES = 512 << 20  # > 129 MB of L2
+# certified binary32 runs of the small workloads (the paper's random family, its two systems)
+# take levels below this many interval multiply-adds in binary64 (the same decisions, fewer
+# launches); the headline curve runs every level in binary32
+SMALL_LEVEL_MADDS = 1 << 24
 # dram__bytes_read.sum + dram__bytes_write.sum of the certified binary32 leaf kernel
 # (k_leaf_tma_c) on the curve's level 8 (ncu --set full): 334.8 MB + 26.1 MB for 3.064e9
 # interval multiply-adds
@@ -394,7 +398,7 @@ def bench_table1(vx, synth, torch, stream, taylor=True):
         for kind in ("points", "curves", "hypersurfaces"):
             s = synth.table1(k, d, kind)
             sysv = vx.System(s.polys, stream=stream)
-            opts = vx.make_opts(vx.FP32)
+            opts = vx.make_opts(vx.FP32, small_level_madds=SMALL_LEVEL_MADDS)
             # the largest depth <= the paper's whose levels fit 32-bit tree indices
             depth, note = s.depth, None
             while True:
@@ -436,7 +440,7 @@ def bench_table1(vx, synth, torch, stream, taylor=True):
                 e0 = torch.cuda.Event(enable_timing=True)
                 e1 = torch.cuda.Event(enable_timing=True)
                 for tag, mode in (("fp32", vx.FP32), ("fp64", vx.FP64)):
-                    to = vx.make_opts(mode, taylor_order=2)
+                    to = vx.make_opts(mode, taylor_order=2, small_level_madds=SMALL_LEVEL_MADDS)
                     vx.enclose_system(sysv, s.domain, min(depth, 3), to, stream=stream).free()
                     e0.record(stream)
                     rt = vx.enclose_system(sysv, s.domain, depth, to, stream=stream)
@@ -453,7 +457,8 @@ def bench_table1(vx, synth, torch, stream, taylor=True):
                     # the size threshold (level 7) on, until no box is left (cap: level 14)
                     cap = 14
                     for tag, mode in (("fp32", vx.FP32), ("fp64", vx.FP64)):
-                        to = vx.make_opts(mode, taylor_order=2, c1=vx.C1_TAYLOR, c1_level=depth)
+                        to = vx.make_opts(mode, taylor_order=2, c1=vx.C1_TAYLOR, c1_level=depth,
+                                          small_level_madds=SMALL_LEVEL_MADDS)
                         e0.record(stream)
                         rt = vx.enclose_system(sysv, s.domain, cap, to, stream=stream)
                         e1.record(stream)
@@ -488,9 +493,11 @@ def bench_applications(vx, synth, torch, stream):
                 "inequalities": int(sum(1 for r in s.rel if r != synth.REL_EQ)),
                 "paper": PAPER_APPLICATIONS[s.name]}
         for depth in depths:
-            runs = [("fp32", vx.make_opts(vx.FP32)), ("fp64", vx.make_opts(vx.FP64))]
+            runs = [("fp32", vx.make_opts(vx.FP32, small_level_madds=SMALL_LEVEL_MADDS)),
+                    ("fp64", vx.make_opts(vx.FP64))]
             if math.comb(2 + s.k, s.k) <= vx.MAXPOLY:  # the order-2 form's derivatives
-                runs.append(("taylor2_fp32", vx.make_opts(vx.FP32, taylor_order=2)))
+                runs.append(("taylor2_fp32", vx.make_opts(vx.FP32, taylor_order=2,
+                                                          small_level_madds=SMALL_LEVEL_MADDS)))
                 runs.append(("taylor2_fp64", vx.make_opts(vx.FP64, taylor_order=2)))
             for name, opts in runs:
                 vx.enclose_system(sysv, s.domain, depth, opts, stream=stream).free()

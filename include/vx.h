@@ -116,7 +116,12 @@ typedef struct {
                          * (vx_result_included); the loop ends when no box is left or after
                          * level `depth`, whose remaining boxes are vx_result_boxes */
   int32_t c1_level;
-  int32_t reserved[4];
+  int32_t small_level_madds; /* VX_FP32 only, 0 = off: a level (of vx_enclose*) whose interval
+                              * multiply-adds (Theorem 1's count; times the Taylor form's
+                              * derivatives) are fewer than this runs in VX_FP64, which decides
+                              * every box as VX_FP32 does and on a level too small to fill the
+                              * GPU is faster than binary32 plus its band check */
+  int32_t reserved[3];
 } vx_opts;
 
 /* Thread-local message of the last failed call on this thread ("" if none). */

@@ -1581,6 +1581,20 @@ static int enclose_impl(const vx_system *sys, const double *dom, int depth, cons
     for (int d = 0; d < k; ++d) R->nodes[(size_t)l * k + d] = cur.v.N[d];
     int mode = opts.mode;
     if (mode == VX_FP32_MIDRAD && opts.fp64_final && l == depth) mode = VX_FP64;
+    if (mode == VX_FP32 && opts.small_level_madds > 0) {
+      // Theorem 1's count for this level (every polynomial and depth), times the Taylor
+      // form's derivatives: small levels run in binary64, which decides the same way
+      int64_t w = 0;
+      for (int f = 0; f < sys->dev.npoly; ++f)
+        for (int d = 0; d < k; ++d)
+          w += cur.v.N[d] * (sys->dev.p[f].st[d].blk_in - sys->dev.p[f].st[d].nfib);
+      if (opts.taylor_order > 0) {
+        int64_t na = 1;  // C(m + k, k)
+        for (int i = 1; i <= k; ++i) na = na * (opts.taylor_order + i) / i;
+        w *= na;
+      }
+      if (w < opts.small_level_madds) mode = VX_FP64;
+    }
     const bool c1_here = opts.c1 != 0 && l >= opts.c1_level && n > 0;
     uint8_t *keep = nullptr, *inc = nullptr;
     rc = dmalloc((void **)&keep, (size_t)std::max<int64_t>(n, 1), s);
@@ -1588,7 +1602,7 @@ static int enclose_impl(const vx_system *sys, const double *dom, int depth, cons
     if (rc == VX_OK) {
       int64_t w = 0, nr = 0;
       if (opts.taylor_order > 0)
-        rc = n > 0 ? eval_taylor_level(sys, cur.v, g, opts.taylor_order, opts.mode, nullptr,
+        rc = n > 0 ? eval_taylor_level(sys, cur.v, g, opts.taylor_order, mode, nullptr,
                                        nullptr, keep, opts.c1 == VX_C1_TAYLOR ? inc : nullptr, s,
                                        tm, &w, &nr)
                    : VX_OK;

@@ -565,3 +565,21 @@ def test_every_launch_variant_matches_oracle(vx, case):
                 r.free()
     finally:
         vx.autotune(1)
+
+
+def test_small_levels_in_binary64(vx):
+    """VX_FP32 with small_level_madds: the levels below the threshold run in binary64 (no band,
+    no recheck) and the enclosure is still the oracle's, with or without the Taylor form."""
+    polys = [synth.kostlan_poly(3, 10, 1301), synth.kostlan_poly(3, 10, 1302)]
+    dom = synth.cube(3)
+    ref = oracle.enclose(polys, dom, 7)
+    for thr in (1 << 30, 1 << 20):
+        r = vx.enclose(polys, dom, 7, vx.make_opts(vx.FP32, small_level_madds=thr))
+        assert np.array_equal(r.boxes(), ref["tuples"])
+        st = r.stats()
+        assert np.array_equal(st["kept"], ref["kept"])
+        if thr == 1 << 30:
+            assert st["recheck"].sum() == 0
+    reft = oracle.enclose_taylor(polys, dom, 6, 2)
+    r = vx.enclose(polys, dom, 6, vx.make_opts(vx.FP32, taylor_order=2, small_level_madds=1 << 22))
+    assert np.array_equal(r.boxes(), reft["tuples"])

@@ -617,7 +617,11 @@ def run_gpu(args):
     vx.lib()
     s = synth.curve()
     dom, depth = s.domain, s.depth
-    sysv = vx.System(s.polys)
+    torch.cuda.synchronize()
+    pk0 = time.perf_counter()
+    sysv = vx.System(s.polys)  # packing and upload, once
+    torch.cuda.synchronize()
+    pack_ms = (time.perf_counter() - pk0) * 1e3
     start = None
     if world > 1:
         lvl0, t0 = shard.rank_start(s.k, depth, rank, world)
@@ -662,7 +666,11 @@ def run_gpu(args):
 
     # ---- headline: binary32 certified, K timed steps -------------------------------------
     log("[bench] warmup %d x fp32" % args.warmup)
-    run_steps(vx.FP32, args.warmup, False)[3].free()
+    # the first enclosure of the process times the autotuner's variants of every launch shape
+    cold_ms, _, _, rc0 = run_steps(vx.FP32, 1, False)
+    rc0.free()
+    if args.warmup > 1:
+        run_steps(vx.FP32, args.warmup - 1, False)[3].free()
     barrier()
     torch.cuda.synchronize()
     launches0 = vx.kernel_launches()
@@ -787,6 +795,12 @@ def run_gpu(args):
             "config": config_dict(world, "binary32 intervals, binary64-certified decisions"),
             "boxes_final": int(st32["kept"][-1]), "box_evals_per_step": evals32 // args.steps,
             "wall_s_timed_region": wall32,
+            "enclosure_ms": {"median": statistics.median(ms32), "min": min(ms32),
+                             "max": max(ms32),
+                             "cold": {"pack_and_upload_ms": pack_ms,
+                                      "first_enclosure_ms": cold_ms[0],
+                                      "note": "the process's first enclosure, autotuning "
+                                              "every launch shape on the way"}},
             "fp64": {"value": value64, "ms_per_step": t64 / n64, "steps": n64,
                      "roofline": roof64},
             "speedup_vs_fp64": value / value64,

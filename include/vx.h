@@ -290,8 +290,9 @@ int vx_enclose_system(const vx_system *sys, const double *h_domain, int32_t dept
  * l0 are zero. */
 int vx_enclose_from(const vx_system *sys, const vx_csf *start, const double *h_domain,
                     int32_t depth, const vx_opts *opts, void *stream, vx_result **out);
-/* The same from host polynomials: packs and uploads them, runs on a private stream, and
- * leaves the result's boxes readable through vx_result_boxes. */
+/* The same from host polynomials: packs and uploads them and runs on a private stream; the
+ * result's boxes reach the host through vx_result_boxes (tuples) or vx_result_box_codes
+ * (grid indices), each copying on its first call. */
 int vx_enclose(const vx_poly *F_list, int32_t npoly, const double *h_domain, int32_t depth,
                const vx_opts *opts, vx_result **out);
 
@@ -379,6 +380,12 @@ int vx_result_boxes(vx_result *res, int64_t *n, const int32_t **h_tuples);
  * memory owned by the result (copied from the device on first call). */
 int vx_result_included(vx_result *res, int64_t *n, const int32_t **h_levels,
                        const int32_t **h_tuples);
+/* The surviving boxes in compact form: *n codes, each a box's index in the full level-`depth`
+ * grid with x_1 most significant (sum_i t_i 2^(depth (k-1-i))), ascending (the lexicographic
+ * order of the tuples); *code_bytes = 4 when k * depth <= 32 (uint32 codes), else 8 (uint64).
+ * Host memory owned by the result (copied from the device on first call): a third of the
+ * tuples' bytes at k = 3, for callers that move results off the GPU in bulk. */
+int vx_result_box_codes(vx_result *res, int64_t *n, int32_t *code_bytes, const void **h_codes);
 /* The survivors as a device CSF owned by the result (valid until vx_result_free). */
 int vx_result_csf(const vx_result *res, const vx_csf **csf);
 /* Per-level statistics, levels 0..depth: h_tested[l] = |S_l| boxes evaluated, h_kept[l]

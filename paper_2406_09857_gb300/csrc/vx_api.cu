@@ -533,6 +533,10 @@ struct vx_result {
   int32_t *htup = nullptr;
   size_t hcap = 0;       // bytes of the buffer
   int64_t hcount = -1;   // boxes copied (-1: not yet)
+  // the boxes as grid indices on the host (vx_result_box_codes), a pinned pool buffer
+  void *hcodes = nullptr;
+  size_t hcodes_cap = 0;
+  int64_t hcodes_count = -1;
   // with C1: the certified boxes of each level (device CSFs), and their host copy
   std::vector<std::pair<int, CsfObj>> incl;
   std::vector<int32_t> hinc_lev, hinc_tup;
@@ -1766,15 +1770,6 @@ int vx_enclose(const vx_poly *F, int32_t npoly, const double *h_domain, int32_t 
   VX_CHECK(vx_system_create(F, npoly, (void *)s, &sys));
   int rc = vx_enclose_system(sys, h_domain, depth, opts, (void *)s, out);
   vx_system_free(sys);
-  if (rc == VX_OK) {
-    const int32_t *t = nullptr;
-    int64_t n = 0;
-    rc = vx_result_boxes(*out, &n, &t);
-    if (rc != VX_OK) {
-      vx_result_free(*out);
-      *out = nullptr;
-    }
-  }
   return rc;
 }
 
@@ -2255,6 +2250,48 @@ int vx_result_boxes(vx_result *R, int64_t *n, const int32_t **h_tuples) {
   return VX_OK;
 }
 
+int vx_result_box_codes(vx_result *R, int64_t *n, int32_t *code_bytes, const void **h_codes) {
+  clear_error();
+  if (!R || !n || !code_bytes || !h_codes) {
+    set_error("vx_result_box_codes: NULL argument");
+    return VX_EINVAL;
+  }
+  const int k = R->k;
+  const int cb = k * R->depth <= 32 ? 4 : 8;
+  if (R->hcodes_count < 0) {
+    const int64_t m = R->fin.v.N[k - 1];
+    if (m > 0) {
+      cudaStream_t s = R->fin.stream;
+      void *hb = nullptr;
+      size_t cap = 0;
+      VX_CHECK(pinned_get((size_t)m * cb, &hb, &cap));
+      void *d = nullptr;
+      int rc = dmalloc(&d, (size_t)m * cb, s);
+      if (rc == VX_OK) rc = csf_box_codes_dev(R->fin.v, d, s);
+      if (rc == VX_OK) {
+        cudaError_t e = cudaMemcpyAsync(hb, d, (size_t)m * cb, cudaMemcpyDeviceToHost, s);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+        if (e != cudaSuccess) {
+          set_error("copying the box codes to the host failed: %s", cudaGetErrorString(e));
+          rc = VX_ECUDA;
+        }
+      }
+      dfree(d, s);
+      if (rc != VX_OK) {
+        pinned_put(hb, cap);
+        return rc;
+      }
+      R->hcodes = hb;
+      R->hcodes_cap = cap;
+    }
+    R->hcodes_count = m;
+  }
+  *n = R->hcodes_count;
+  *code_bytes = cb;
+  *h_codes = R->hcodes;
+  return VX_OK;
+}
+
 int vx_result_included(vx_result *R, int64_t *n, const int32_t **h_levels,
                        const int32_t **h_tuples) {
   clear_error();
@@ -2364,6 +2401,7 @@ int vx_result_elapsed_ms(const vx_result *R, double *ms) {
 void vx_result_free(vx_result *R) {
   if (!R) return;
   pinned_put(R->htup, R->hcap);
+  pinned_put(R->hcodes, R->hcodes_cap);
   csf_release(&R->fin);
   for (auto &lc : R->incl) csf_release(&lc.second);
   R->tm.release();

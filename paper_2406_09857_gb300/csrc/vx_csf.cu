@@ -758,6 +758,24 @@ __global__ void k_tuples(CsfView c, int32_t *t) {
   }
 }
 
+// Each leaf's box as its index in the level's full grid, x_1 most significant:
+// code = sum_d t_d << (level (k-1-d)); 4 bytes per code when k level <= 32, else 8.
+template <typename C>
+__global__ void k_box_codes(CsfView c, C *out) {
+  const int k = c.k;
+  const int64_t n = c.N[k - 1];
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
+    int64_t p = i;
+    uint64_t code = 0;
+    for (int d = k - 1; d >= 0; --d) {
+      code |= (uint64_t)(uint32_t)c.lab[d][p] << (c.level * (k - 1 - d));
+      if (d > 0) p = c.par[d][p];
+    }
+    out[i] = (C)code;
+  }
+}
+
 // indices of the nonzero bytes, in increasing order
 struct ByteFlagSrc {
   const uint8_t *f;
@@ -883,6 +901,17 @@ int csf_prune_forest(const CsfView &in, const uint8_t *d_keep, int split, int32_
     case 5: return prune_c<5>(in, d_keep, split, d_index, s, out, tm, d_seg_off, nseg, d_seg_kept);
     default: return prune_c<6>(in, d_keep, split, d_index, s, out, tm, d_seg_off, nseg, d_seg_kept);
   }
+}
+
+int csf_box_codes_dev(const CsfView &c, void *d_codes, cudaStream_t s) {
+  if (c.N[c.k - 1] == 0) return VX_OK;
+  if (c.k * c.level <= 32)
+    k_box_codes<uint32_t><<<blocks_for(c.N[c.k - 1]), 256, 0, s>>>(c, (uint32_t *)d_codes);
+  else
+    k_box_codes<uint64_t><<<blocks_for(c.N[c.k - 1]), 256, 0, s>>>(c, (uint64_t *)d_codes);
+  note_launch();
+  VX_LAUNCH_CHECK();
+  return VX_OK;
 }
 
 int csf_tuples_dev(const CsfView &c, int32_t *d_tuples, cudaStream_t s) {

@@ -221,6 +221,9 @@ int csf_full_grid_dev(int k, int level, cudaStream_t s, CsfObj *out);
 // ptr[d][N[d]] = N[d+1] for every depth d < k-1.
 int set_ptr_sentinels(const CsfView &v, cudaStream_t s);
 int csf_tuples_dev(const CsfView &c, int32_t *d_tuples, cudaStream_t s);
+// Each leaf's box as its index in the level's full grid (x_1 most significant), uint32 when
+// k * level <= 32, else uint64.
+int csf_box_codes_dev(const CsfView &c, void *d_codes, cudaStream_t s);
 // Increasing indices i with d_flags[i] != 0 (device array owned by the caller, freed with
 // dfree; synchronises `s` to learn the count).
 int flag_indices(const uint8_t *d_flags, int64_t n, cudaStream_t s, int32_t **d_idx,

@@ -80,6 +80,7 @@ def lib() -> ctypes.CDLL:
         "vx_csf_c1": ([P, P, P, i32, i32, P, P], i32),
         "vx_csf_taylor_level": ([P, P, P, i32, i32, P, P, P, P], i32),
         "vx_result_included": ([P, P, P, P], i32),
+        "vx_result_box_codes": ([P, P, P, P], i32),
         "vx_csf_subdivide": ([P, P, P, PP], i32),
         "vx_csf_compact": ([P, P, P, P, PP], i32),
         "vx_enclose_system": ([P, P, i32, P, P, PP], i32),
@@ -448,6 +449,33 @@ class Result:
         buf = (ctypes.c_int32 * (m * self.k)).from_address(p.value)
         a = np.frombuffer(buf, dtype=np.int32).reshape(m, self.k)
         return a.copy() if copy else a
+
+    def box_codes(self, copy=True) -> np.ndarray:
+        """The surviving boxes as grid indices (x_1 most significant), ascending: uint32 when
+        k * depth <= 32, else uint64.  copy=False returns a view of the result's pinned host
+        buffer, valid until free()."""
+        n = ctypes.c_int64()
+        cb = ctypes.c_int32()
+        p = ctypes.c_void_p()
+        _check(lib().vx_result_box_codes(self.handle, ctypes.byref(n), ctypes.byref(cb),
+                                         ctypes.byref(p)))
+        m = int(n.value)
+        dt = np.uint32 if cb.value == 4 else np.uint64
+        if m == 0:
+            return np.zeros(0, dtype=dt)
+        buf = (ctypes.c_uint8 * (m * cb.value)).from_address(p.value)
+        a = np.frombuffer(buf, dtype=dt)
+        return a.copy() if copy else a
+
+    @staticmethod
+    def decode_codes(codes, k, depth) -> np.ndarray:
+        """Tuples [n, k] int32 from box codes."""
+        c = np.asarray(codes).astype(np.uint64)
+        out = np.empty((c.shape[0], k), dtype=np.int32)
+        mask = np.uint64((1 << depth) - 1)
+        for i in range(k):
+            out[:, i] = ((c >> np.uint64(depth * (k - 1 - i))) & mask).astype(np.int32)
+        return out
 
     def included(self):
         """With C1: (levels [n] int32, tuples [n, k] int32) of the certified boxes, ordered by

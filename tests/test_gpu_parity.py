@@ -583,3 +583,14 @@ def test_small_levels_in_binary64(vx):
     reft = oracle.enclose_taylor(polys, dom, 6, 2)
     r = vx.enclose(polys, dom, 6, vx.make_opts(vx.FP32, taylor_order=2, small_level_madds=1 << 22))
     assert np.array_equal(r.boxes(), reft["tuples"])
+
+
+@pytest.mark.parametrize("k,d,depth", [(3, 8, 7), (4, 3, 9), (2, 12, 16)])
+def test_box_codes_decode_to_the_boxes(vx, k, d, depth):
+    polys = [synth.kostlan_poly(k, d, 1400 + depth)]
+    r = vx.enclose(polys, synth.cube(k), depth, vx.make_opts(vx.FP32))
+    codes = r.box_codes()
+    assert codes.dtype == (np.uint32 if k * depth <= 32 else np.uint64)
+    assert np.all(codes[1:] > codes[:-1])
+    assert np.array_equal(vx.Result.decode_codes(codes, k, depth), r.boxes())
+    assert codes.shape[0] > 0

@@ -275,18 +275,6 @@ struct A32C {
     e = __fmaf_ru(J.z, x.xmaxp, e);
     return make_float4(r.x, r.y, e, 0.f);
   }
-  // The step on y = |x| >= 0, y = [yl, yh], with the coefficient negated when neg: Horner in
-  // x <= 0 is Horner in y = -x on the coefficients (-1)^a A_a, the state being (-1)^a J_a
-  // (exact: interval negation swaps the pair (lo, -hi), and the products are the same reals).
-  static __device__ __forceinline__ V step_y(V K, float yl, float yh, float xmaxp, V A, bool neg) {
-    const float2 b = neg ? make_float2(A.y, A.x) : make_float2(A.x, A.y);
-    const float2 P = __ffma2_rn(make_float2(K.x, K.y), make_float2(yl, yl), b);
-    const float2 Q = __ffma2_rn(make_float2(K.x, K.y), make_float2(yh, yh), b);
-    const float rx = fminf(P.x, Q.x), ry = fminf(P.y, Q.y);
-    const float m = fmaxf(fabsf(rx), fabsf(ry));
-    const float e = __fmaf_ru(K.z, xmaxp, __fmaf_ru(kCr, m, A.z));
-    return make_float4(rx, ry, e, 0.f);
-  }
   // a stored bound carries a relative margin 2^-40 and an absolute 2^-148
   static __device__ __forceinline__ V store(V J) {
     const float e = __fadd_ru(__fmaf_ru(J.z, k2m40, J.z), kEta148);
@@ -555,7 +543,7 @@ __global__ void __launch_bounds__(kThreads)
 // Last stage in the certified binary32 arithmetic, two consecutive leaves per thread.  When
 // every thread of a warp holds two leaves of one parent whose x_k intervals do not straddle 0
 // (always so at level >= 1 of a grid exact in binary32), the two leaves share every
-// coefficient load, and a leaf with x_k <= 0 runs Horner in y = -x_k (A32C::step_y), so the
+// coefficient load, and a leaf with x_k <= 0 runs Horner in y = -x_k (step_y2), so the
 // lanes of the warp run the same instructions whatever the signs of their boxes.  Any other
 // warp takes the per-leaf path of k_leaf.
 struct YLeaf {
@@ -595,8 +583,12 @@ __device__ __forceinline__ YPair ypair(const YLeaf &a, const YLeaf &b) {
   return y;
 }
 
-// A32C::step_y on both leaves: SW = 0 the entry as it is, 1 negated for both leaves (a pair
-// swap), 2 negated per leaf where sw0 / sw1.  The same roundings as step_y, so the same values.
+// One step of A32C on y = |x| >= 0, y = [yl, yh], for both leaves: Horner in x <= 0 is Horner
+// in y = -x on the coefficients (-1)^a A_a, the state being (-1)^a J_a (exact: interval
+// negation swaps the pair (lo, -hi), and the products are the same reals).  SW = 0 takes the
+// entry as it is, 1 negated for both leaves (a pair swap), 2 negated per leaf where sw0 / sw1.
+// Each end is the min of two paired FMAs rounded to nearest; the bounds follow A32C::step's
+// recursion, both leaves' in one paired FMA pair.
 template <int SW>
 __device__ __forceinline__ void step_y2(float2 &j0, float2 &j1, float2 &e, const YPair &y,
                                         const float4 &A, bool sw0, bool sw1) {

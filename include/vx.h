@@ -121,7 +121,15 @@ typedef struct {
                               * derivatives) are fewer than this runs in VX_FP64, which decides
                               * every box as VX_FP32 does and on a level too small to fill the
                               * GPU is faster than binary32 plus its band check */
-  int32_t reserved[3];
+  int32_t recheck_last; /* VX_FP32 on the interval form (taylor_order 0, c1 0) only: the boxes
+                         * inside the error band stay in S at the levels below the last one and
+                         * only the last level's are re-decided in binary64.  The final boxes
+                         * are still exactly VX_FP64's: C0 on interval Horner is inclusion-
+                         * isotone over the exact grids (a box that binary64 drops has every
+                         * descendant dropped by binary64 too), so keeping a box that binary64
+                         * would drop changes only the counts of the levels in between
+                         * (vx_result_stats), never the boxes that the last level keeps */
+  int32_t reserved[2];
 } vx_opts;
 
 /* Thread-local message of the last failed call on this thread ("" if none). */

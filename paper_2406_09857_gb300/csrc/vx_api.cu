@@ -450,15 +450,17 @@ namespace vx {
 // One level in one mode.  The binary32 modes flag boxes for a binary64 re-evaluation (VX_FP32:
 // those inside the error band; VX_FP32_MIDRAD with recheck: the tight ones); flagged boxes are
 // gathered into a tree of their own, evaluated in binary64 and their decisions scattered back.
+// defer (VX_FP32): no re-evaluation, the band's boxes are kept.
 static int eval_decide(const SysDev &sys, const CsfView &c, const LevelGrid &g, int mode,
                        bool midrad_recheck, float theta, double *d_lo, double *d_hi,
                        uint8_t *keep, cudaStream_t s, Timer *tm, int64_t *madds,
-                       int64_t *nrecheck) {
+                       int64_t *nrecheck, bool defer = false) {
   const int k = c.k;
   const int64_t n = c.N[k - 1];
   *madds = 0;
   *nrecheck = 0;
-  const bool flagged = mode == VX_FP32 || (mode == VX_FP32_MIDRAD && midrad_recheck);
+  const bool flagged =
+      (mode == VX_FP32 && !defer) || (mode == VX_FP32_MIDRAD && midrad_recheck);
   const int arith = mode == VX_FP64 ? ARITH_F64 : (mode == VX_FP32 ? ARITH_F32_CERT : ARITH_F32_MIDRAD);
   uint8_t *flag = nullptr;
   if (flagged) VX_CHECK(dmalloc((void **)&flag, (size_t)std::max<int64_t>(n, 1), s));
@@ -1546,6 +1548,13 @@ static int enclose_impl(const vx_system *sys, const double *dom, int depth, cons
       return VX_EINVAL;
     }
   }
+  if (opts.recheck_last != 0 &&
+      (opts.mode != VX_FP32 || opts.taylor_order != 0 || opts.c1 != 0)) {
+    // the Taylor form is centred on each box, hence not inclusion-isotone across levels
+    set_error("vx_enclose: recheck_last needs VX_FP32 on the interval form (no Taylor form, "
+              "no C1)");
+    return VX_EINVAL;
+  }
   LevelGrid g;
   VX_CHECK(make_grid(k, dom, depth, &g));  // the finest grid exact => every coarser one too
   R->k = k;
@@ -1612,7 +1621,7 @@ static int enclose_impl(const vx_system *sys, const double *dom, int depth, cons
                    : VX_OK;
       else
         rc = eval_decide(sys->dev, cur.v, g, mode, opts.fp64_recheck != 0, theta, nullptr,
-                         nullptr, keep, s, tm, &w, &nr);
+                         nullptr, keep, s, tm, &w, &nr, opts.recheck_last != 0 && l < depth);
       R->madds[l] += w;
       R->recheck[l] = nr;
       int st = 0;
@@ -1785,7 +1794,8 @@ namespace {
 
 // mode 0: out = keep && depth(tree) == l; 1: out = keep && depth(tree) > l;
 // 2: out = out || (keep && depth(tree) == l) (the binary64 final level of VX_FP32_MIDRAD: a
-// box the midpoint-radius superset drops, binary64 drops too)
+// box the midpoint-radius superset drops, binary64 drops too); 3: out = out && depth(tree) == l
+// (recheck_last: only the finishing trees' band is re-decided)
 __global__ void k_tree_mask(const uint8_t *__restrict__ keep, const int64_t *__restrict__ offl,
                             int S, const int32_t *__restrict__ tdepth, int l, int mode,
                             int64_t n, uint8_t *__restrict__ out) {
@@ -1799,7 +1809,8 @@ __global__ void k_tree_mask(const uint8_t *__restrict__ keep, const int64_t *__r
     const int dep = tdepth[lo];
     if (mode == 0) out[i] = (keep[i] && dep == l) ? 1 : 0;
     else if (mode == 1) out[i] = (keep[i] && dep > l) ? 1 : 0;
-    else out[i] = (out[i] || (keep[i] && dep == l)) ? 1 : 0;
+    else if (mode == 2) out[i] = (out[i] || (keep[i] && dep == l)) ? 1 : 0;
+    else out[i] = (out[i] && dep == l) ? 1 : 0;
   }
 }
 
@@ -2029,7 +2040,14 @@ int batch_group(const std::vector<int32_t> &ids, const vx_poly *const *systems,
                        flagged ? flag : nullptr, theta, s, &w);
     if (rc == VX_OK && !flagged && (opts.mode == VX_FP32_MIDRAD && opts.fp64_final))
       if (cudaMemsetAsync(flag, 0, (size_t)n, s) != cudaSuccess) rc = VX_ECUDA;
-    const bool recheck = flagged || (opts.mode == VX_FP32_MIDRAD && opts.fp64_final && any_final);
+    const bool defer = opts.mode == VX_FP32 && opts.recheck_last != 0;
+    const bool recheck = (flagged && (!defer || any_final)) ||
+                         (opts.mode == VX_FP32_MIDRAD && opts.fp64_final && any_final);
+    if (rc == VX_OK && defer && any_final) {
+      k_tree_mask<<<grid1(n), 256, 0, s>>>(keep, cur.d_off + (int64_t)(k - 1) * (S + 1), S,
+                                           d_tdep, l, 3, n, flag);
+      note_launch();
+    }
     if (rc == VX_OK && opts.mode == VX_FP32_MIDRAD && opts.fp64_final && any_final) {
       k_tree_mask<<<grid1(n), 256, 0, s>>>(keep, cur.d_off + (int64_t)(k - 1) * (S + 1), S,
                                            d_tdep, l, 2, n, flag);
@@ -2177,6 +2195,10 @@ int vx_enclose_batch(const vx_poly *const *systems, const int32_t *npoly, const 
   }
   if (o.taylor_order != 0) {
     set_error("vx_enclose_batch: the Taylor form is not available in batches");
+    return VX_EINVAL;
+  }
+  if (o.recheck_last != 0 && o.mode != VX_FP32) {
+    set_error("vx_enclose_batch: recheck_last needs VX_FP32");
     return VX_EINVAL;
   }
   // domain offsets: system i owns 2 * k_i doubles; groups of equal k

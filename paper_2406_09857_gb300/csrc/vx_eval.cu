@@ -1105,18 +1105,20 @@ struct GlobalBlocks {
   }
 };
 
-// The last stage and C0 of the leaf pair (i0, i1) with parents p0, p1 (blocks from src), in
-// the certified binary32 arithmetic: a warp whose pairs each share a parent and do not
-// straddle 0 takes the paired, sign-free path; any other warp runs every leaf on its own.
-template <class Src>
-__device__ __forceinline__ void leaf_pair_c(const LeafArgs &A, int npoly, const Src &src,
-                                            int64_t i0, int64_t i1, bool live, bool two,
-                                            const A32C::X &x0, const A32C::X &x1, int64_t p0,
-                                            int64_t p1, int64_t nleaves,
-                                            uint8_t *__restrict__ keep, double *__restrict__ lo,
-                                            double *__restrict__ hi, uint8_t *__restrict__ flag) {
+// The last stage of polynomials fb .. fe-1 on the leaf pair (i0, i1) with parents p0, p1
+// (blocks from src), in the certified binary32 arithmetic, each decision ORed into the
+// pair's state: ex[c] (some polynomial excludes leaf c) and am[c] (some decision is left to
+// binary64).  A warp whose pairs each share a parent and do not straddle 0 takes the paired,
+// sign-free path (two polynomials of one length at a time when NPMAX is 2); any other warp
+// runs every leaf on its own.
+template <int NPMAX, class Src>
+__device__ __forceinline__ void leaf_pair_eval(const LeafArgs &A, int fb, int fe, const Src &src,
+                                               int64_t i0, int64_t i1, bool live, bool two,
+                                               const A32C::X &x0, const A32C::X &x1, int64_t p0,
+                                               int64_t p1, int64_t nleaves,
+                                               double *__restrict__ lo, double *__restrict__ hi,
+                                               bool (&ex)[2], bool (&am)[2]) {
   using V = float4;
-  bool excl0 = false, amb0 = false, excl1 = false, amb1 = false;
   auto decide = [&](int f, int c, const V &J) {
     if (lo && live && (c == 0 || two)) {
       const int64_t i = c == 0 ? i0 : i1;
@@ -1124,34 +1126,31 @@ __device__ __forceinline__ void leaf_pair_c(const LeafArgs &A, int npoly, const 
       hi[(int64_t)f * nleaves + i] = A32C::hi(J);
     }
     const int r = A32C::classify(J, A.rel[f]);
-    if (c == 0) {
-      excl0 = excl0 || r == 0;
-      amb0 = amb0 || r == 2;
-    } else {
-      excl1 = excl1 || r == 0;
-      amb1 = amb1 || r == 2;
-    }
+    ex[c] = ex[c] || r == 0;
+    am[c] = am[c] || r == 2;
   };
   const bool fast = p0 == p1 && x0.cls != 0 && x1.cls != 0;
   if (__all_sync(0xffffffffu, fast)) {
     const YPair yp = ypair(yleaf(x0), yleaf(x1));
     const int ws = warp_sign(yp);
-    int f = 0;
-    for (; f + 1 < npoly && A.len[f] == A.len[f + 1]; f += 2) {
-      const V *const b[2] = {src(f, p0), src(f + 1, p0)};
-      V K0[2], K1[2];
-      if (ws > 0)
-        horner_y2<2, 1>(b, A.len[f], yp, K0, K1);
-      else if (ws < 0)
-        horner_y2<2, -1>(b, A.len[f], yp, K0, K1);
-      else
-        horner_y2<2, 0>(b, A.len[f], yp, K0, K1);
-      decide(f, 0, K0[0]);
-      decide(f + 1, 0, K0[1]);
-      decide(f, 1, K1[0]);
-      decide(f + 1, 1, K1[1]);
+    int f = fb;
+    if (NPMAX == 2) {
+      for (; f + 1 < fe && A.len[f] == A.len[f + 1]; f += 2) {
+        const V *const b[2] = {src(f, p0), src(f + 1, p0)};
+        V K0[2], K1[2];
+        if (ws > 0)
+          horner_y2<2, 1>(b, A.len[f], yp, K0, K1);
+        else if (ws < 0)
+          horner_y2<2, -1>(b, A.len[f], yp, K0, K1);
+        else
+          horner_y2<2, 0>(b, A.len[f], yp, K0, K1);
+        decide(f, 0, K0[0]);
+        decide(f + 1, 0, K0[1]);
+        decide(f, 1, K1[0]);
+        decide(f + 1, 1, K1[1]);
+      }
     }
-    for (; f < npoly; ++f) {
+    for (; f < fe; ++f) {
       const V *const b[2] = {src(f, p0), nullptr};
       V K0[2], K1[2];
       if (ws > 0)
@@ -1168,24 +1167,47 @@ __device__ __forceinline__ void leaf_pair_c(const LeafArgs &A, int npoly, const 
     for (int c = 0; c < 2; ++c) {
       const A32C::X &x = c == 0 ? x0 : x1;
       const int64_t p = c == 0 ? p0 : p1;
-      int f = 0;
-      for (; f + 1 < npoly && A.len[f] == A.len[f + 1]; f += 2) {
-        V J0, J1;
-        horner1x2_any<A32C>(src(f, p), src(f + 1, p), A.len[f], x, J0, J1);
-        decide(f, c, J0);
-        decide(f + 1, c, J1);
+      int f = fb;
+      if (NPMAX == 2) {
+        for (; f + 1 < fe && A.len[f] == A.len[f + 1]; f += 2) {
+          V J0, J1;
+          horner1x2_any<A32C>(src(f, p), src(f + 1, p), A.len[f], x, J0, J1);
+          decide(f, c, J0);
+          decide(f + 1, c, J1);
+        }
       }
-      for (; f < npoly; ++f) decide(f, c, horner1_any<A32C>(src(f, p), 1, A.len[f], x));
+      for (; f < fe; ++f) decide(f, c, horner1_any<A32C>(src(f, p), 1, A.len[f], x));
     }
   }
+}
+
+// keep (0 where some polynomial excludes the leaf) and flag (1 where the leaf is kept and some
+// decision is left to binary64) of the leaf pair.
+__device__ __forceinline__ void leaf_pair_store(int64_t i0, int64_t i1, bool live, bool two,
+                                                const bool (&ex)[2], const bool (&am)[2],
+                                                uint8_t *__restrict__ keep,
+                                                uint8_t *__restrict__ flag) {
   if (live) {
-    keep[i0] = excl0 ? 0 : 1;
-    if (flag) flag[i0] = (!excl0 && amb0) ? 1 : 0;
+    keep[i0] = ex[0] ? 0 : 1;
+    if (flag) flag[i0] = (!ex[0] && am[0]) ? 1 : 0;
     if (two) {
-      keep[i1] = excl1 ? 0 : 1;
-      if (flag) flag[i1] = (!excl1 && amb1) ? 1 : 0;
+      keep[i1] = ex[1] ? 0 : 1;
+      if (flag) flag[i1] = (!ex[1] && am[1]) ? 1 : 0;
     }
   }
+}
+
+// The last stage and C0 of the leaf pair (i0, i1): every polynomial, then the decisions.
+template <class Src>
+__device__ __forceinline__ void leaf_pair_c(const LeafArgs &A, int npoly, const Src &src,
+                                            int64_t i0, int64_t i1, bool live, bool two,
+                                            const A32C::X &x0, const A32C::X &x1, int64_t p0,
+                                            int64_t p1, int64_t nleaves,
+                                            uint8_t *__restrict__ keep, double *__restrict__ lo,
+                                            double *__restrict__ hi, uint8_t *__restrict__ flag) {
+  bool ex[2] = {false, false}, am[2] = {false, false};
+  leaf_pair_eval<2>(A, 0, npoly, src, i0, i1, live, two, x0, x1, p0, p1, nleaves, lo, hi, ex, am);
+  leaf_pair_store(i0, i1, live, two, ex, am, keep, flag);
 }
 
 // One warp's share of k_leaf_c: the 32 leaf pairs of tile t (64 leaves).  par/poff as in
@@ -1237,6 +1259,32 @@ struct ChunkBlocks {  // the staged blocks of parents p0 .. p0 + n - 1, else glo
   }
 };
 
+// One thread: the bulk copies of parents pf .. pl's blocks, every polynomial's at s_off[f]
+// (kLeafParents blocks apart), completing on bar.
+__device__ __forceinline__ void leaf_chunk_copy(const LeafArgs &A, int npoly, int64_t pf,
+                                                int64_t pl, uint64_t *bar, int32_t *s_off,
+                                                float4 *s_blk) {
+  mbar_init(bar, 1);
+  const int64_t np = pl - pf + 1;
+  int32_t o = 0;
+  uint32_t total = 0;
+  for (int f = 0; f < npoly; ++f) {
+    s_off[f] = o;
+    o += (int32_t)(kLeafParents * A.blk[f]);
+    total += (uint32_t)(np * A.blk[f] * (int64_t)sizeof(float4));
+  }
+  mbar_arrive_expect_tx(bar, total);
+  for (int f = 0; f < npoly; ++f) {
+    const char *src = reinterpret_cast<const char *>((const float4 *)A.in[f] + pf * A.blk[f]);
+    char *dst = reinterpret_cast<char *>(s_blk + s_off[f]);
+    const uint64_t bytes = (uint64_t)(np * A.blk[f]) * sizeof(float4);
+    for (uint64_t b = 0; b < bytes; b += 32768) {
+      const uint32_t n = (uint32_t)(bytes - b < 32768 ? bytes - b : 32768);
+      bulk_copy_g2s(dst + b, src + b, n, bar);
+    }
+  }
+}
+
 // k_leaf_c with the parents' blocks brought into shared memory by bulk copies (mbarrier,
 // bounded wait): CTA b takes the leaves b*C .. b*C+C-1 (C = 2 kLeafIter blockDim.x), two per
 // thread per pass; their parents are consecutive nodes, whose node-major blocks are one
@@ -1257,27 +1305,7 @@ __global__ void __launch_bounds__(kThreads, 6)
   const int64_t pf = __ldg(par + first), pl = __ldg(par + last);
   const bool staged = pl - pf < kLeafParents;
   if (staged) {
-    if (threadIdx.x == 0) {
-      mbar_init(bar, 1);
-      const int64_t np = pl - pf + 1;
-      int32_t o = 0;
-      uint32_t total = 0;
-      for (int f = 0; f < npoly; ++f) {
-        s_off[f] = o;
-        o += (int32_t)(kLeafParents * A.blk[f]);
-        total += (uint32_t)(np * A.blk[f] * (int64_t)sizeof(float4));
-      }
-      mbar_arrive_expect_tx(bar, total);
-      for (int f = 0; f < npoly; ++f) {
-        const char *src = reinterpret_cast<const char *>((const float4 *)A.in[f] + pf * A.blk[f]);
-        char *dst = reinterpret_cast<char *>(s_blk + s_off[f]);
-        const uint64_t bytes = (uint64_t)(np * A.blk[f]) * sizeof(float4);
-        for (uint64_t b = 0; b < bytes; b += 32768) {
-          const uint32_t n = (uint32_t)(bytes - b < 32768 ? bytes - b : 32768);
-          bulk_copy_g2s(dst + b, src + b, n, bar);
-        }
-      }
-    }
+    if (threadIdx.x == 0) leaf_chunk_copy(A, npoly, pf, pl, bar, s_off, s_blk);
     __syncthreads();
     if (!mbar_wait_bounded(bar, 0)) return;
   }
@@ -1290,6 +1318,79 @@ __global__ void __launch_bounds__(kThreads, 6)
     const A32C::X x0 = A32C::box(g, __ldg(lab + i0)), x1 = A32C::box(g, __ldg(lab + i1));
     const int64_t p0 = __ldg(par + i0), p1 = __ldg(par + i1);
     leaf_pair_c(A, npoly, src, i0, i1, live, two, x0, x1, p0, p1, nleaves, keep, lo, hi, flag);
+  }
+}
+
+// k_leaf_tma_c for two or more polynomials, without the work that C0 makes useless: each
+// thread runs polynomial 0 on its kLeafIter pairs and settles the pairs whose leaves it
+// excludes; the other pairs are queued in shared memory (warp-aggregated slots, so that the
+// pairs of a warp stay neighbours) with their decisions so far, and the CTA's warps run the
+// remaining polynomials on the queue.  C0 keeps a leaf only if no polynomial excludes it, so
+// the decisions are those of k_leaf_tma_c; the leaves' interval values are not written.
+__global__ void __launch_bounds__(kThreads, 8)
+    k_leaf_tma_q(LeafArgs A, int npoly, const int32_t *__restrict__ lab,
+                 const int32_t *__restrict__ par, int64_t nleaves, AxisGrid g,
+                 uint8_t *__restrict__ keep, uint8_t *__restrict__ flag) {
+  extern __shared__ __align__(128) unsigned char smem[];
+  __shared__ int s_nq;
+  __shared__ int16_t s_q[kLeafIter * kThreads];  // queued pair: its index in the chunk
+  __shared__ uint8_t s_st[kLeafIter * kThreads]; // its decisions so far (ex0, am0, ex1, am1)
+  uint64_t *bar = reinterpret_cast<uint64_t *>(smem);
+  int32_t *s_off = reinterpret_cast<int32_t *>(smem + 16);
+  float4 *s_blk = reinterpret_cast<float4 *>(smem + 128);
+  const int64_t chunk = 2 * (int64_t)kLeafIter * kThreads;
+  const int64_t first = (int64_t)blockIdx.x * chunk;
+  const int64_t last = (first + chunk < nleaves ? first + chunk : nleaves) - 1;
+  const int64_t pf = __ldg(par + first), pl = __ldg(par + last);
+  const bool staged = pl - pf < kLeafParents;
+  if (threadIdx.x == 0) {
+    s_nq = 0;
+    if (staged) leaf_chunk_copy(A, npoly, pf, pl, bar, s_off, s_blk);
+  }
+  __syncthreads();
+  const bool ok = !staged || mbar_wait_bounded(bar, 0);
+  if (!__syncthreads_and(ok)) return;
+  const ChunkBlocks src{A, s_blk, s_off, pf, staged};
+  const int lane = threadIdx.x & 31;
+  for (int it = 0; it < kLeafIter; ++it) {
+    const int q = it * kThreads + (int)threadIdx.x;
+    const int64_t na = first + 2 * (int64_t)q;
+    const bool live = na <= last, two = na + 1 <= last;
+    const int64_t i0 = live ? na : last, i1 = two ? na + 1 : i0;
+    const A32C::X x0 = A32C::box(g, __ldg(lab + i0)), x1 = A32C::box(g, __ldg(lab + i1));
+    const int64_t p0 = __ldg(par + i0), p1 = __ldg(par + i1);
+    bool ex[2] = {false, false}, am[2] = {false, false};
+    leaf_pair_eval<1>(A, 0, 1, src, i0, i1, live, two, x0, x1, p0, p1, nleaves, nullptr,
+                      nullptr, ex, am);
+    const bool more = live && !(ex[0] && (ex[1] || !two));
+    if (live && !more) leaf_pair_store(i0, i1, live, two, ex, am, keep, flag);
+    const unsigned m = __ballot_sync(0xffffffffu, more);
+    int base = 0;
+    if (lane == 0 && m != 0u) base = atomicAdd(&s_nq, __popc(m));
+    base = __shfl_sync(0xffffffffu, base, 0);
+    if (more) {
+      const int slot = base + __popc(m & ((1u << lane) - 1u));
+      s_q[slot] = (int16_t)q;
+      s_st[slot] = (uint8_t)((ex[0] ? 1 : 0) | (am[0] ? 2 : 0) | (ex[1] ? 4 : 0) | (am[1] ? 8 : 0));
+    }
+  }
+  __syncthreads();
+  const int nq = s_nq;
+  // the loop bound is the same for the 32 lanes of a warp (the votes inside see all of them);
+  // a lane past the queue's end repeats its last pair and stores nothing
+  for (int b = (int)(threadIdx.x & ~31u); b < nq; b += kThreads) {
+    const bool in = b + lane < nq;
+    const int sl = in ? b + lane : nq - 1;
+    const int q = s_q[sl], st = s_st[sl];
+    const int64_t i0 = first + 2 * (int64_t)q;
+    const bool two = i0 + 1 <= last;
+    const int64_t i1 = two ? i0 + 1 : i0;
+    const A32C::X x0 = A32C::box(g, __ldg(lab + i0)), x1 = A32C::box(g, __ldg(lab + i1));
+    const int64_t p0 = __ldg(par + i0), p1 = __ldg(par + i1);
+    bool ex[2] = {(st & 1) != 0, (st & 4) != 0}, am[2] = {(st & 2) != 0, (st & 8) != 0};
+    leaf_pair_eval<1>(A, 1, npoly, src, i0, i1, in, two, x0, x1, p0, p1, nleaves, nullptr,
+                      nullptr, ex, am);
+    leaf_pair_store(i0, i1, in, two, ex, am, keep, flag);
   }
 }
 
@@ -1590,20 +1691,27 @@ int eval_level_t(const SysDev &sys, const CsfView &c, const LevelGrid &grid, dou
     if (tm && tm->on) rc = tm->begin(kind0 + 2, wl);
     if (rc == VX_OK) {
       // variants (certified binary32): 0 two leaves per thread, 1 one leaf per thread, 2 two
-      // leaves per thread with the parent's blocks staged in shared memory (one CTA per
-      // parent; when the blocks fit)
+      // leaves per thread with the parents' blocks staged in shared memory (CTA = 512
+      // consecutive leaves; when the blocks fit), 3 the same skipping what C0 makes useless
       size_t leaf_smem = 128;
       for (int f = 0; f < sys.npoly; ++f)
         leaf_smem += (size_t)kLeafParents * (size_t)A.blk[f] * sizeof(float4);
       const bool leaf_tma = std::is_same<AR, A32C>::value && k >= 2 && leaf_smem <= kMaxDynSmem;
+      // 3: k_leaf_tma_q (two or more polynomials, decisions only)
+      const bool leaf_q = leaf_tma && sys.npoly >= 2 && d_lo == nullptr;
       if (leaf_tma &&
-          cudaFuncSetAttribute(k_leaf_tma_c, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                               (int)kMaxDynSmem) != cudaSuccess) {
+          (cudaFuncSetAttribute(k_leaf_tma_c, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)kMaxDynSmem) != cudaSuccess ||
+           cudaFuncSetAttribute(k_leaf_tma_q, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)kMaxDynSmem) != cudaSuccess)) {
         set_error("cudaFuncSetAttribute(shared memory %zu) failed", leaf_smem);
         rc = VX_ECUDA;
       }
       auto launch = [&](int v) -> int {
-        if (std::is_same<AR, A32C>::value && v == 2)
+        if (std::is_same<AR, A32C>::value && v == 3)
+          k_leaf_tma_q<<<(unsigned)leaf_tma_grid(nleaves), kThreads, leaf_smem, s>>>(
+              A, sys.npoly, c.lab[k - 1], c.par[k - 1], nleaves, grid.ax[k - 1], d_keep, d_flag);
+        else if (std::is_same<AR, A32C>::value && v == 2)
           k_leaf_tma_c<<<(unsigned)leaf_tma_grid(nleaves), kThreads, leaf_smem, s>>>(
               A, sys.npoly, c.lab[k - 1], c.par[k - 1], nleaves, grid.ax[k - 1], d_keep, d_lo,
               d_hi, d_flag);
@@ -1653,7 +1761,8 @@ int eval_level_t(const SysDev &sys, const CsfView &c, const LevelGrid &grid, dou
         if (rc == VX_OK)
           rc = tuned_launch(tune_key(3, arith, k - 1, nleaves, k > 1 ? c.N[k - 2] : 0,
                                      sys.p[0].st[k - 1].maxlen, sys.npoly),
-                            std::is_same<AR, A32C>::value ? (leaf_tma ? 3 : 2) : 1, s, launch);
+                            std::is_same<AR, A32C>::value ? (leaf_q ? 4 : leaf_tma ? 3 : 2) : 1,
+                            s, launch);
       }
       if (rc == VX_OK && tm && tm->on) rc = tm->end();
     }

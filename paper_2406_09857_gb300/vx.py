@@ -40,7 +40,8 @@ class Opts(ctypes.Structure):
                 ("fp64_recheck", ctypes.c_int32), ("theta", ctypes.c_float),
                 ("timing", ctypes.c_int32), ("taylor_order", ctypes.c_int32),
                 ("c1", ctypes.c_int32), ("c1_level", ctypes.c_int32),
-                ("small_level_madds", ctypes.c_int32), ("reserved", ctypes.c_int32 * 3)]
+                ("small_level_madds", ctypes.c_int32), ("recheck_last", ctypes.c_int32),
+                ("reserved", ctypes.c_int32 * 2)]
 
 
 def lib() -> ctypes.CDLL:
@@ -175,8 +176,9 @@ def _domain(domain) -> np.ndarray:
 
 
 def make_opts(mode=FP64, fp64_final=False, fp64_recheck=False, theta=0.5, timing=False,
-              taylor_order=0, c1=0, c1_level=0, small_level_madds=0) -> Opts:
+              taylor_order=0, c1=0, c1_level=0, small_level_madds=0, recheck_last=False) -> Opts:
     o = Opts()
+    o.recheck_last = int(bool(recheck_last))
     o.small_level_madds = int(small_level_madds)
     o.c1 = int(c1)
     o.c1_level = int(c1_level)

@@ -25,7 +25,16 @@ namespace {
 
 constexpr int ST = 256;
 constexpr int SI = 8;
-constexpr int STILE = ST * SI;
+constexpr int STILE = ST * SI;  // entries of one pass of a CTA
+constexpr int SR = 8;           // at most SR passes per CTA: a scan tile is passes * STILE entries
+
+// Passes per scan tile: several for large scans (fewer, longer-lived CTAs and fewer tile sums),
+// one while that would leave fewer than 2048 tiles to spread over the GPU.
+__host__ __device__ __forceinline__ int scan_passes(int64_t n) {
+  const int64_t t1 = (n + STILE - 1) / STILE;
+  const int64_t p = t1 / 2048;
+  return (int)(p < 1 ? 1 : (p > SR ? SR : p));
+}
 
 __device__ __forceinline__ int32_t warp_incl_scan(int32_t v) {
   const int lane = threadIdx.x & 31;
@@ -68,21 +77,27 @@ __device__ __forceinline__ void emit_items(const Emit &em, int64_t i0, int64_t n
   }
 }
 
+// Per scan tile and channel, the count of flagged entries (scan_passes(n) passes of STILE
+// entries; the passes' loads are independent).
 template <int C, class Src>
 __global__ void __launch_bounds__(ST) k_scan_reduce(Src src, int64_t n, int32_t *tsum,
                                                     int64_t ntiles) {
   __shared__ int32_t sw[C][ST / 32];
   const int64_t tile = blockIdx.x;
-  const int64_t i0 = tile * STILE + (int64_t)threadIdx.x * SI;
+  const int passes = scan_passes(n);
   int32_t cnt[C];
 #pragma unroll
   for (int c = 0; c < C; ++c) cnt[c] = 0;
-  unsigned m[SI];
-  load_items(src, i0, n, true, m);
+#pragma unroll SR
+  for (int r = 0; r < passes; ++r) {
+    const int64_t i0 = (tile * passes + r) * STILE + (int64_t)threadIdx.x * SI;
+    unsigned m[SI];
+    load_items(src, i0, n, true, m);
 #pragma unroll
-  for (int j = 0; j < SI; ++j)
+    for (int j = 0; j < SI; ++j)
 #pragma unroll
-    for (int c = 0; c < C; ++c) cnt[c] += (m[j] >> c) & 1u;
+      for (int c = 0; c < C; ++c) cnt[c] += (m[j] >> c) & 1u;
+  }
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
 #pragma unroll
   for (int c = 0; c < C; ++c) {
@@ -134,43 +149,57 @@ __global__ void __launch_bounds__(1024) k_scan_tiles(int32_t *tsum, int64_t ntil
   }
 }
 
+// The exclusive counts of every entry: the tile's offset (toff) carried over its passes, each
+// pass a block-wide scan.
 template <int C, class Src, class Emit>
 __global__ void __launch_bounds__(ST) k_scan_emit(Src src, Emit em, int64_t n,
                                                   const int32_t *toff, int64_t ntiles) {
-  __shared__ int32_t sw[C][ST / 32];
+  __shared__ int32_t sw[C][ST / 32 + 1];  // per warp exclusive offsets, then the pass total
   const int64_t tile = blockIdx.x;
-  const int64_t i0 = tile * STILE + (int64_t)threadIdx.x * SI;
-  unsigned m[SI];
-  int32_t cnt[C];
-#pragma unroll
-  for (int c = 0; c < C; ++c) cnt[c] = 0;
-  load_items(src, i0, n, false, m);
-#pragma unroll
-  for (int j = 0; j < SI; ++j)
-#pragma unroll
-    for (int c = 0; c < C; ++c) cnt[c] += (m[j] >> c) & 1u;
+  const int passes = scan_passes(n);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  int32_t pre[C];
+  int32_t carry[C];
 #pragma unroll
-  for (int c = 0; c < C; ++c) {
-    int32_t incl = warp_incl_scan(cnt[c]);
-    pre[c] = incl - cnt[c];
-    if (lane == 31) sw[c][warp] = incl;
-  }
-  __syncthreads();
-  if (warp == 0) {
+  for (int c = 0; c < C; ++c) carry[c] = toff[c * ntiles + tile];
+  for (int r = 0; r < passes; ++r) {
+    const int64_t p0 = (tile * passes + r) * STILE;
+    if (p0 >= n) break;  // the same for the whole CTA
+    const int64_t i0 = p0 + (int64_t)threadIdx.x * SI;
+    unsigned m[SI];
+    int32_t cnt[C];
+#pragma unroll
+    for (int c = 0; c < C; ++c) cnt[c] = 0;
+    load_items(src, i0, n, false, m);
+#pragma unroll
+    for (int j = 0; j < SI; ++j)
+#pragma unroll
+      for (int c = 0; c < C; ++c) cnt[c] += (m[j] >> c) & 1u;
+    int32_t pre[C];
 #pragma unroll
     for (int c = 0; c < C; ++c) {
-      int32_t v = lane < ST / 32 ? sw[c][lane] : 0;
-      int32_t s = warp_incl_scan(v);
-      if (lane < ST / 32) sw[c][lane] = s - v;
+      int32_t incl = warp_incl_scan(cnt[c]);
+      pre[c] = incl - cnt[c];
+      if (lane == 31) sw[c][warp] = incl;
     }
-  }
-  __syncthreads();
-  int32_t run[C];
+    __syncthreads();
+    if (warp == 0) {
 #pragma unroll
-  for (int c = 0; c < C; ++c) run[c] = toff[c * ntiles + tile] + sw[c][warp] + pre[c];
-  emit_items<C>(em, i0, n, m, run);
+      for (int c = 0; c < C; ++c) {
+        int32_t v = lane < ST / 32 ? sw[c][lane] : 0;
+        int32_t s = warp_incl_scan(v);
+        if (lane < ST / 32) sw[c][lane] = s - v;
+        if (lane == ST / 32 - 1) sw[c][ST / 32] = s;
+      }
+    }
+    __syncthreads();
+    int32_t run[C];
+#pragma unroll
+    for (int c = 0; c < C; ++c) run[c] = carry[c] + sw[c][warp] + pre[c];
+    emit_items<C>(em, i0, n, m, run);
+#pragma unroll
+    for (int c = 0; c < C; ++c) carry[c] += sw[c][ST / 32];
+    __syncthreads();  // sw is rewritten by the next pass
+  }
 }
 
 // Pinned staging for the few counts the host needs (one buffer per host thread).
@@ -190,7 +219,8 @@ template <int C, class Src>
 int scan_prepare(const Src &src, int64_t n, cudaStream_t s, int32_t **d_scratch,
                  int64_t *ntiles_out, int32_t *h_totals, const int32_t *d_extra = nullptr,
                  int32_t *h_extra = nullptr) {
-  const int64_t ntiles = (n + STILE - 1) / STILE;
+  const int64_t tile_n = (int64_t)STILE * scan_passes(n);
+  const int64_t ntiles = (n + tile_n - 1) / tile_n;
   *ntiles_out = ntiles;
   *d_scratch = nullptr;
   int32_t *pin = pinned_counts();
@@ -781,6 +811,20 @@ struct ByteFlagSrc {
   const uint8_t *f;
   __device__ unsigned flags(int64_t i, bool) const { return f[i] ? 1u : 0u; }
 };
+
+// the eight flags of a thread in one 8-byte load where the address allows it
+__device__ __forceinline__ void load_items(const ByteFlagSrc &src, int64_t i0, int64_t n, bool,
+                                           unsigned (&m)[SI]) {
+  static_assert(SI == 8, "one 8-byte load per thread");
+  if (i0 + SI <= n && (reinterpret_cast<uintptr_t>(src.f + i0) & 7u) == 0) {
+    const uint2 v = __ldg(reinterpret_cast<const uint2 *>(src.f + i0));
+#pragma unroll
+    for (int j = 0; j < SI; ++j) m[j] = (((j < 4 ? v.x : v.y) >> (8 * (j & 3))) & 0xffu) ? 1u : 0u;
+  } else {
+#pragma unroll
+    for (int j = 0; j < SI; ++j) m[j] = i0 + j < n ? src.flags(i0 + j, false) : 0u;
+  }
+}
 struct IndexEmit {
   int32_t *idx;
   __device__ void operator()(int64_t i, unsigned m, const int32_t *excl) const {

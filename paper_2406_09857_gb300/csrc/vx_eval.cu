@@ -1327,18 +1327,20 @@ __global__ void __launch_bounds__(kThreads, 6)
 // pairs of a warp stay neighbours) with their decisions so far, and the CTA's warps run the
 // remaining polynomials on the queue.  C0 keeps a leaf only if no polynomial excludes it, so
 // the decisions are those of k_leaf_tma_c; the leaves' interval values are not written.
+// ITER pairs per thread in the first phase (a CTA takes 2 ITER kThreads leaves).
+template <int ITER>
 __global__ void __launch_bounds__(kThreads, 8)
     k_leaf_tma_q(LeafArgs A, int npoly, const int32_t *__restrict__ lab,
                  const int32_t *__restrict__ par, int64_t nleaves, AxisGrid g,
                  uint8_t *__restrict__ keep, uint8_t *__restrict__ flag) {
   extern __shared__ __align__(128) unsigned char smem[];
   __shared__ int s_nq;
-  __shared__ int16_t s_q[kLeafIter * kThreads];  // queued pair: its index in the chunk
-  __shared__ uint8_t s_st[kLeafIter * kThreads]; // its decisions so far (ex0, am0, ex1, am1)
+  __shared__ int16_t s_q[ITER * kThreads];  // queued pair: its index in the chunk
+  __shared__ uint8_t s_st[ITER * kThreads]; // its decisions so far (ex0, am0, ex1, am1)
   uint64_t *bar = reinterpret_cast<uint64_t *>(smem);
   int32_t *s_off = reinterpret_cast<int32_t *>(smem + 16);
   float4 *s_blk = reinterpret_cast<float4 *>(smem + 128);
-  const int64_t chunk = 2 * (int64_t)kLeafIter * kThreads;
+  const int64_t chunk = 2 * (int64_t)ITER * kThreads;
   const int64_t first = (int64_t)blockIdx.x * chunk;
   const int64_t last = (first + chunk < nleaves ? first + chunk : nleaves) - 1;
   const int64_t pf = __ldg(par + first), pl = __ldg(par + last);
@@ -1352,7 +1354,7 @@ __global__ void __launch_bounds__(kThreads, 8)
   if (!__syncthreads_and(ok)) return;
   const ChunkBlocks src{A, s_blk, s_off, pf, staged};
   const int lane = threadIdx.x & 31;
-  for (int it = 0; it < kLeafIter; ++it) {
+  for (int it = 0; it < ITER; ++it) {
     const int q = it * kThreads + (int)threadIdx.x;
     const int64_t na = first + 2 * (int64_t)q;
     const bool live = na <= last, two = na + 1 <= last;
@@ -1394,8 +1396,8 @@ __global__ void __launch_bounds__(kThreads, 8)
   }
 }
 
-int leaf_tma_grid(int64_t leaves) {
-  const int64_t chunk = 2 * (int64_t)kLeafIter * kThreads;
+int leaf_tma_grid(int64_t leaves, int iter = kLeafIter) {
+  const int64_t chunk = 2 * (int64_t)iter * kThreads;
   return (int)((leaves + chunk - 1) / chunk);
 }
 
@@ -1692,7 +1694,8 @@ int eval_level_t(const SysDev &sys, const CsfView &c, const LevelGrid &grid, dou
     if (rc == VX_OK) {
       // variants (certified binary32): 0 two leaves per thread, 1 one leaf per thread, 2 two
       // leaves per thread with the parents' blocks staged in shared memory (CTA = 512
-      // consecutive leaves; when the blocks fit), 3 the same skipping what C0 makes useless
+      // consecutive leaves; when the blocks fit), 3 / 4 the same skipping what C0 makes
+      // useless, with 512 / 1024 leaves per CTA (2048 measured no faster)
       size_t leaf_smem = 128;
       for (int f = 0; f < sys.npoly; ++f)
         leaf_smem += (size_t)kLeafParents * (size_t)A.blk[f] * sizeof(float4);
@@ -1702,14 +1705,19 @@ int eval_level_t(const SysDev &sys, const CsfView &c, const LevelGrid &grid, dou
       if (leaf_tma &&
           (cudaFuncSetAttribute(k_leaf_tma_c, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                 (int)kMaxDynSmem) != cudaSuccess ||
-           cudaFuncSetAttribute(k_leaf_tma_q, cudaFuncAttributeMaxDynamicSharedMemorySize,
+           cudaFuncSetAttribute(k_leaf_tma_q<2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)kMaxDynSmem) != cudaSuccess ||
+           cudaFuncSetAttribute(k_leaf_tma_q<4>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                 (int)kMaxDynSmem) != cudaSuccess)) {
         set_error("cudaFuncSetAttribute(shared memory %zu) failed", leaf_smem);
         rc = VX_ECUDA;
       }
       auto launch = [&](int v) -> int {
         if (std::is_same<AR, A32C>::value && v == 3)
-          k_leaf_tma_q<<<(unsigned)leaf_tma_grid(nleaves), kThreads, leaf_smem, s>>>(
+          k_leaf_tma_q<2><<<(unsigned)leaf_tma_grid(nleaves, 2), kThreads, leaf_smem, s>>>(
+              A, sys.npoly, c.lab[k - 1], c.par[k - 1], nleaves, grid.ax[k - 1], d_keep, d_flag);
+        else if (std::is_same<AR, A32C>::value && v == 4)
+          k_leaf_tma_q<4><<<(unsigned)leaf_tma_grid(nleaves, 4), kThreads, leaf_smem, s>>>(
               A, sys.npoly, c.lab[k - 1], c.par[k - 1], nleaves, grid.ax[k - 1], d_keep, d_flag);
         else if (std::is_same<AR, A32C>::value && v == 2)
           k_leaf_tma_c<<<(unsigned)leaf_tma_grid(nleaves), kThreads, leaf_smem, s>>>(
@@ -1761,7 +1769,7 @@ int eval_level_t(const SysDev &sys, const CsfView &c, const LevelGrid &grid, dou
         if (rc == VX_OK)
           rc = tuned_launch(tune_key(3, arith, k - 1, nleaves, k > 1 ? c.N[k - 2] : 0,
                                      sys.p[0].st[k - 1].maxlen, sys.npoly),
-                            std::is_same<AR, A32C>::value ? (leaf_q ? 4 : leaf_tma ? 3 : 2) : 1,
+                            std::is_same<AR, A32C>::value ? (leaf_q ? 5 : leaf_tma ? 3 : 2) : 1,
                             s, launch);
       }
       if (rc == VX_OK && tm && tm->on) rc = tm->end();

@@ -57,9 +57,9 @@ L2_FLUSH_BYTES = 512 << 20  # > 129 MB of L2
 # launches); the headline curve runs every level in binary32
 SMALL_LEVEL_MADDS = 1 << 24
 # dram__bytes_read.sum + dram__bytes_write.sum of the certified binary32 leaf kernel
-# (k_leaf_tma_q) on the curve's level 8 (ncu --set full): 334.4 MB + 26.1 MB for 3.064e9
-# interval multiply-adds
-LEAF32_DRAM_B_PER_MADD = (334.4e6 + 26.1e6) / 3.064e9
+# (k_leaf_tma_q<4>) on the curve's level 9 (ncu --set full): 1560.4 MB + 172.0 MB for
+# 1.784e10 interval multiply-adds (Algorithm 2's count)
+LEAF32_DRAM_B_PER_MADD = (1560.4e6 + 172.0e6) / 1.78408304e10
 
 
 def load_peaks():

@@ -5,6 +5,8 @@ Bar: the binary64 path is bit-identical to the oracle (endpoints compared by val
 path encloses the binary64 enclosure box by box (so it keeps a superset), with a binary64
 last level giving exactly the binary64 set.
 """
+import math
+
 import numpy as np
 import pytest
 
@@ -186,6 +188,27 @@ def test_system_info_counts(vx):
     k, npoly, M = vx.System(s.polys).info()
     assert (k, npoly) == (3, 2)
     assert M[0].tolist() == [math.comb(20 + 3 - j, 3 - j) for j in range(4)]
+
+
+def test_large_polynomial_packing_checks(vx):
+    """A polynomial large enough for its packing loops to be split between host threads
+    (62 196 terms): a monomial repeated at the far end (another chunk than its first
+    occurrence), a non-finite coefficient or a negative exponent there are still refused, and
+    the clean polynomial packs to the dense block sizes."""
+    e, c = synth.kostlan_poly(3, 70, 1501)
+    k, npoly, M = vx.System([(e, c)]).info()
+    assert M[0].tolist() == [math.comb(70 + 3 - j, 3 - j) for j in range(4)]
+    e2 = np.concatenate([e, e[:1]])
+    with pytest.raises(vx.VxError, match="twice"):
+        vx.System([(e2, np.concatenate([c, c[:1]]))])
+    c2 = c.copy()
+    c2[-1] = np.nan
+    with pytest.raises(vx.VxError, match="coefficient"):
+        vx.System([(e, c2)])
+    e3 = e.copy()
+    e3[-1, 2] = -1
+    with pytest.raises(vx.VxError, match="exponent"):
+        vx.System([(e3, c)])
 
 
 def test_system_rejects_bad_polynomials(vx):

@@ -530,22 +530,30 @@ def bench_batch(vx, synth, torch, workers=16):
                        "Kostlan polys, d~U{10..40}), depth ~U{8..10}, [-1,1]^k",
            "engine": "one CSF forest per k: one launch per depth per level for all systems",
            "timed": "vx_enclose_batch from host polynomials to device-resident results"}
-    boxes = {}
-    for name, mode in (("fp32", vx.FP32), ("fp64", vx.FP64)):
-        for r in vx.enclose_batch(systems[:16], vx.make_opts(mode), nworkers=workers):
+    boxes, evals = {}, {}
+    # binary64 first: its box evaluations (the exact subdivision's) are every rate's count
+    for name, mode, last in (("fp64", vx.FP64, False), ("fp32", vx.FP32, False),
+                             ("fp32_recheck_last", vx.FP32, True)):
+        opts = vx.make_opts(mode, recheck_last=last)
+        for r in vx.enclose_batch(systems[:16], opts, nworkers=workers):
             r.free()
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        res = vx.enclose_batch(systems, vx.make_opts(mode), nworkers=workers)
+        res = vx.enclose_batch(systems, opts, nworkers=workers)
         torch.cuda.synchronize()
         el = time.perf_counter() - t0
-        ev = sum(int(r.stats()["tested"].sum()) for r in res)
+        evals[name] = sum(int(r.stats()["tested"].sum()) for r in res)
+        ev = evals["fp64"]
         boxes[name] = [r.boxes() for r in res]
         out[name] = {"value": ev / el, "unit": UNIT, "wall_s": el, "box_evals": ev,
                      "boxes": int(sum(b.shape[0] for b in boxes[name]))}
+        if last:
+            out[name]["box_evals_run"] = evals[name]
         for r in res:
             r.free()
     out["fp32_equals_fp64"] = all(np.array_equal(a, b) for a, b in zip(boxes["fp32"], boxes["fp64"]))
+    out["fp32_recheck_last_equals_fp64"] = all(
+        np.array_equal(a, b) for a, b in zip(boxes["fp32_recheck_last"], boxes["fp64"]))
     out["speedup_fp32_vs_fp64"] = out["fp32"]["value"] / out["fp64"]["value"]
     return out
 

@@ -5,7 +5,8 @@ the oracle decides one by one (each box on its own, nested interval Horner in bi
   evaluations) in certified binary32: every sampled returned box is kept by the oracle, every
   sampled box of the finest grid that is not returned is excluded by it (by isotonicity a box
   whose ancestor was excluded is excluded itself), the neighbours of returned boxes included;
-  the binary64 enclosure returns the same boxes;
+  the binary64 enclosure returns the same boxes, and so does certified binary32 with the band
+  re-decided at the last level only (the benchmark's configuration);
 - the dense full-grid level (degree 128 per variable at level 10: 1.07 G boxes) through the
   tensor-core prefilter and the exact interval path: sampled kept and dropped boxes agree with
   the oracle.
@@ -70,6 +71,13 @@ def test_curve_depth10_sampled(vx):
     r64 = vx.enclose_system(sysv, s.domain, 10, vx.make_opts(vx.FP64))
     assert np.array_equal(r64.boxes(), boxes)
     assert np.array_equal(r64.stats()["kept"], r32.stats()["kept"])
+    # the band re-decided at the last level only (the configuration the benchmark times):
+    # the same boxes, at least binary64's boxes at every level before
+    rl = vx.enclose_system(sysv, s.domain, 10, vx.make_opts(vx.FP32, recheck_last=True))
+    assert np.array_equal(rl.boxes(), boxes)
+    stl, st64 = rl.stats(), r64.stats()
+    assert (stl["kept"] >= st64["kept"]).all() and stl["kept"][-1] == st64["kept"][-1]
+    assert (stl["recheck"][:-1] == 0).all()
 
 
 def test_dense_degree128_level10_sampled(vx):

@@ -767,14 +767,16 @@ def run_gpu(args):
     r0 = e2e_once()[0]  # warm-up, and the pinned result buffer enters the pool
     r0.box_codes(copy=False)
     r0.free()
-    ne2e = max(1, min(args.steps, 2))
+    ne2e = max(1, min(args.steps, 5))
     torch.cuda.synchronize()
     barrier()
     w0 = time.perf_counter()
-    e2e_evals, d2h, h2d = 0, 0, 0
+    e2e_evals, d2h, h2d, e2e_ms = 0, 0, 0, []
     for _ in range(ne2e):
+        s0 = time.perf_counter()
         r, hb = e2e_once()
         b = r.box_codes(copy=False)  # the result to the host: one grid-index code per box
+        e2e_ms.append((time.perf_counter() - s0) * 1e3)
         e2e_evals += ev_exact_step / max(world, 1)
         d2h += b.nbytes
         h2d += hb
@@ -783,7 +785,8 @@ def run_gpu(args):
     e2e_s = reduce(time.perf_counter() - w0, torch.distributed.ReduceOp.MAX if world > 1 else None)
     e2e_evals = reduce(e2e_evals, torch.distributed.ReduceOp.SUM if world > 1 else None)
     e2e = {"value": e2e_evals / e2e_s, "unit": UNIT, "h2d_bytes_per_step": h2d // ne2e,
-           "d2h_bytes_per_step": d2h // ne2e,
+           "d2h_bytes_per_step": d2h // ne2e, "steps": ne2e,
+           "ms_each": [round(x, 2) for x in e2e_ms],
            "what": "vx_enclose from host polynomials (pack + upload) to the host's boxes (one uint32 grid-index code per box, vx_result_box_codes)"}
 
     # ---- config 5: one complete level (Property 1's dense grid), and config 4: the batch ----

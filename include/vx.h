@@ -154,6 +154,10 @@ void vx_system_free(vx_system *sys);
  * each partial-evaluation stage reads: M_{j} for j = 0..k, with missing suffix monomials below
  * the highest exponent of a fibre counted as zero coefficients (M_k = 1). */
 int vx_system_info(const vx_system *sys, int32_t *k, int32_t *npoly, int64_t *h_M);
+/* The same counts without a device: packs F_list[0..npoly) on the host only (the checks of
+ * vx_system_create: exponents, finite coefficients, no monomial twice) and writes h_M
+ * [npoly][k+1] as vx_system_info does.  Touches no GPU. */
+int vx_system_measure(const vx_poly *F_list, int32_t npoly, int64_t *h_M);
 
 /* Bytes of device memory the packed system holds (what vx_system_create uploads). */
 int vx_system_device_bytes(const vx_system *sys, int64_t *bytes);

@@ -13,6 +13,8 @@
 #include <atomic>
 #include <map>
 #include <memory>
+#include <condition_variable>
+#include <functional>
 #include <mutex>
 #include <thread>
 #include <cmath>
@@ -328,24 +330,124 @@ __global__ void k_encode_coefs(const double2 *__restrict__ c64, int64_t n, float
 }
 
 // chi (nullable): upper ends of interval coefficients [p.coefs[t], chi[t]]
-static int pack_poly(int k, const vx_poly &p, HostPoly *hp, const double *chi = nullptr) {
+// Host threads kept for the process (one per core but this one's, at most 15): run(n, fn)
+// calls fn(c) for c = 0..n-1 on them and on the calling thread and returns when all are done.
+// One job at a time: a caller that finds the pool busy gets false and nothing runs.
+class HostPool {
+ public:
+  static HostPool &get() {
+    static HostPool *p = new HostPool();  // never destroyed: its threads live as long as the process
+    return *p;
+  }
+  int size() const { return (int)nworkers_ + 1; }
+  template <class Fn>
+  bool run(int n, Fn &&fn) {
+    std::unique_lock<std::mutex> busy(busy_, std::try_to_lock);
+    if (!busy.owns_lock()) return false;
+    std::function<void(int)> f(fn);
+    {
+      std::lock_guard<std::mutex> g(m_);
+      job_ = &f;
+      n_ = n;
+      next_.store(0);
+      ++gen_;
+    }
+    cv_.notify_all();
+    drain();
+    std::unique_lock<std::mutex> g(m_);
+    done_.wait(g, [&] { return active_ == 0; });  // every chunk a worker took has finished
+    job_ = nullptr;
+    return true;
+  }
+
+ private:
+  HostPool() {
+    const int hw = (int)std::thread::hardware_concurrency();
+    nworkers_ = std::max(0, std::min(15, hw - 1));
+    for (int i = 0; i < nworkers_; ++i) std::thread([this] { loop(); }).detach();
+  }
+  void drain() {
+    for (;;) {
+      const int c = next_.fetch_add(1);
+      if (c >= n_) return;
+      (*job_)(c);
+    }
+  }
+  void loop() {
+    uint64_t seen = 0;
+    std::unique_lock<std::mutex> g(m_);
+    for (;;) {
+      cv_.wait(g, [&] { return gen_ != seen && job_ != nullptr; });
+      seen = gen_;
+      ++active_;
+      g.unlock();
+      drain();
+      g.lock();
+      if (--active_ == 0) done_.notify_all();
+    }
+  }
+  int nworkers_ = 0;
+  std::mutex busy_, m_;
+  std::condition_variable cv_, done_;
+  std::function<void(int)> *job_ = nullptr;
+  int n_ = 0, active_ = 0;
+  uint64_t gen_ = 0;
+  std::atomic<int> next_{0};
+};
+
+// Polynomials with at least this many terms split their packing loops over the host pool
+// (smaller ones, e.g. a batch's, are packed by many callers at once already).
+constexpr int32_t kPackSplitTerms = 50000;
+
+// fn(c, begin, end) on chunk c of nchunks contiguous chunks of [0, n), on the host pool when
+// there are several chunks and it is free, else on this thread.
+template <class Fn>
+static void for_chunks(int64_t n, int nchunks, Fn fn) {
+  const int64_t per = (n + nchunks - 1) / std::max(nchunks, 1);
+  auto chunk = [&](int c) {
+    const int64_t a = c * per, b = std::min<int64_t>(n, a + per);
+    if (a < b) fn(c, a, b);
+  };
+  if (nchunks > 1 && HostPool::get().run(nchunks, chunk)) return;
+  for (int c = 0; c < nchunks; ++c) chunk(c);
+}
+
+// chunks: pieces of the loops over the terms (several for large polynomials: host pool).
+static int pack_poly(int k, const vx_poly &p, HostPoly *hp, const double *chi = nullptr,
+                     int chunks = 1) {
   const int32_t nt = p.nterms;
   if (p.nvars != k || nt < 0 || (nt > 0 && (!p.exps || !p.coefs))) {
     set_error("polynomial: nvars %d (expected %d), nterms %d", p.nvars, k, nt);
     return VX_EINVAL;
   }
+  const int T = std::max(1, std::min(chunks, 64));
   const int32_t emax = (1 << key_bits(k)) - 1;
-  for (int64_t t = 0; t < (int64_t)nt * k; ++t) {
-    if (p.exps[t] < 0 || p.exps[t] > emax) {
-      set_error("polynomial: exponent %d outside [0, %d]", p.exps[t], emax);
-      return VX_EINVAL;
-    }
-  }
-  for (int32_t t = 0; t < nt; ++t) {
-    if (!std::isfinite(p.coefs[t]) || (chi && !(std::isfinite(chi[t]) && chi[t] >= p.coefs[t]))) {
-      set_error("polynomial: coefficient %d is not finite (or not an interval)", t);
-      return VX_EINVAL;
-    }
+  {
+    // the first bad exponent and the first bad coefficient (each chunk its own first)
+    std::vector<int64_t> bad_e(T, -1), bad_c(T, -1);
+    for_chunks(nt, T, [&](int c, int64_t a, int64_t b) {
+      for (int64_t t = a * k; t < b * k; ++t)
+        if (p.exps[t] < 0 || p.exps[t] > emax) {
+          bad_e[c] = t;
+          break;
+        }
+      for (int64_t t = a; t < b; ++t)
+        if (!std::isfinite(p.coefs[t]) ||
+            (chi && !(std::isfinite(chi[t]) && chi[t] >= p.coefs[t]))) {
+          bad_c[c] = t;
+          break;
+        }
+    });
+    for (int c = 0; c < T; ++c)
+      if (bad_e[c] >= 0) {
+        set_error("polynomial: exponent %d outside [0, %d]", p.exps[bad_e[c]], emax);
+        return VX_EINVAL;
+      }
+    for (int c = 0; c < T; ++c)
+      if (bad_c[c] >= 0) {
+        set_error("polynomial: coefficient %d is not finite (or not an interval)", (int)bad_c[c]);
+        return VX_EINVAL;
+      }
   }
   // closure of the fibre sets, last stage first: stage s's fibres are the entries of stage
   // s+1's input (monomials in x_{s+2}..x_k), each as long as the highest exponent of
@@ -357,16 +459,31 @@ static int pack_poly(int k, const vx_poly &p, HostPoly *hp, const double *chi = 
     FlatMap idx;
     idx.reserve((size_t)nf);
     for (int32_t f = 0; f < nf; ++f) idx.put(S.keys[f], f);
-    std::vector<int32_t> len(nf, 1);
-    for (int32_t t = 0; t < nt; ++t) {
-      const int32_t *e = p.exps + (int64_t)t * k;
-      const int32_t g = idx.get(suffix_key(e, s + 1, k));
-      if (g < 0) {
+    // per chunk of terms the longest fibre lengths, then their maxima
+    std::vector<std::vector<int32_t>> lens(T);
+    std::vector<uint8_t> miss(T, 0);
+    for_chunks(nt, T, [&](int c, int64_t a, int64_t b) {
+      std::vector<int32_t> &len = lens[c];
+      len.assign(nf, 1);
+      for (int64_t t = a; t < b; ++t) {
+        const int32_t *e = p.exps + t * k;
+        const int32_t g = idx.get(suffix_key(e, s + 1, k));
+        if (g < 0) {
+          miss[c] = 1;
+          return;
+        }
+        len[g] = std::max(len[g], e[s] + 1);
+      }
+    });
+    for (int c = 0; c < T; ++c)
+      if (miss[c]) {
         set_error("internal: monomial outside the fibre closure");
         return VX_EINVAL;
       }
-      len[g] = std::max(len[g], e[s] + 1);
-    }
+    std::vector<int32_t> len(nf, 1);
+    for (int c = 0; c < T; ++c)
+      if (!lens[c].empty())
+        for (int32_t f = 0; f < nf; ++f) len[f] = std::max(len[f], lens[c][f]);
     std::vector<int32_t> order(nf);
     for (int32_t f = 0; f < nf; ++f) order[f] = f;
     std::sort(order.begin(), order.end(), [&](int32_t a, int32_t b) {
@@ -429,17 +546,25 @@ static int pack_poly(int k, const vx_poly &p, HostPoly *hp, const double *chi = 
   const HostStage &S0 = hp->st[0];
   hp->c64.assign(S0.blk_in, make_double2(0.0, 0.0));
   std::vector<uint8_t> seen(S0.blk_in, 0);
-  for (int32_t t = 0; t < nt; ++t) {
-    const int32_t *e = p.exps + (int64_t)t * k;
-    const int32_t f = S0.index.get(suffix_key(e, 1, k));
-    const int64_t pos = S0.rowoff[e[0]] + f;
-    if (seen[pos]) {
-      set_error("polynomial: monomial %d appears twice", t);
+  std::vector<int64_t> dup(T, -1);
+  for_chunks(nt, T, [&](int c, int64_t a, int64_t b) {
+    for (int64_t t = a; t < b; ++t) {
+      const int32_t *e = p.exps + t * k;
+      const int32_t f = S0.index.get(suffix_key(e, 1, k));
+      const int64_t pos = S0.rowoff[e[0]] + f;
+      // a monomial seen before, by this chunk or another one (atomic: chunks run at once)
+      if (__atomic_exchange_n(&seen[pos], (uint8_t)1, __ATOMIC_RELAXED)) {
+        if (dup[c] < 0) dup[c] = t;
+        continue;
+      }
+      hp->c64[pos] = make_double2(p.coefs[t], chi ? chi[t] : p.coefs[t]);
+    }
+  });
+  for (int c = 0; c < T; ++c)
+    if (dup[c] >= 0) {
+      set_error("polynomial: monomial %d appears twice", (int)dup[c]);
       return VX_EINVAL;
     }
-    seen[pos] = 1;
-    hp->c64[pos] = make_double2(p.coefs[t], chi ? chi[t] : p.coefs[t]);
-  }
   return VX_OK;
 }
 
@@ -630,8 +755,16 @@ static int system_create_impl(const vx_poly *F, int32_t npoly, const double *con
   std::vector<HostPoly> hp(npoly);
   int64_t terms = 0;
   for (int f = 0; f < npoly; ++f) terms += std::max<int32_t>(F[f].nterms, 0);
-  if (npoly > 1 && terms >= 20000) {
-    // large polynomials pack concurrently (host work, one thread each)
+  const int pool_chunks = 2 * HostPool::get().size();
+  bool large = false;
+  for (int f = 0; f < npoly; ++f) large = large || F[f].nterms >= kPackSplitTerms;
+  if (large) {
+    // large polynomials one after another, each one's loops over its terms on the host pool
+    for (int f = 0; f < npoly; ++f)
+      VX_CHECK(pack_poly(k, F[f], &hp[f], chi ? chi[f] : nullptr,
+                         F[f].nterms >= kPackSplitTerms ? pool_chunks : 1));
+  } else if (npoly > 1 && terms >= 20000) {
+    // mid-sized polynomials pack concurrently (host work, one thread each)
     std::vector<int> rcs(npoly, VX_OK);
     std::vector<std::string> msgs(npoly);
     std::vector<std::thread> th;
@@ -772,6 +905,27 @@ void vx_system_free(vx_system *sys) {
     for (auto &ts : kv.second) vx_system_free(ts.sys);
   dfree(sys->mem, sys->stream);
   delete sys;
+}
+
+int vx_system_measure(const vx_poly *F, int32_t npoly, int64_t *h_M) {
+  clear_error();
+  if (!F || !h_M || npoly < 1 || npoly > VX_MAXPOLY) {
+    set_error("vx_system_measure: need 1..%d polynomials and an output array", VX_MAXPOLY);
+    return VX_EINVAL;
+  }
+  const int k = F[0].nvars;
+  if (k < 1 || k > VX_KMAX) {
+    set_error("vx_system_measure: %d variables (1..%d supported)", k, VX_KMAX);
+    return VX_EINVAL;
+  }
+  const int pool_chunks = 2 * HostPool::get().size();
+  for (int f = 0; f < npoly; ++f) {
+    HostPoly hp;
+    VX_CHECK(pack_poly(k, F[f], &hp, nullptr, F[f].nterms >= kPackSplitTerms ? pool_chunks : 1));
+    for (int s2 = 0; s2 < k; ++s2) h_M[(size_t)f * (k + 1) + s2] = hp.st[s2].blk_in;
+    h_M[(size_t)f * (k + 1) + k] = 1;
+  }
+  return VX_OK;
 }
 
 int vx_system_info(const vx_system *sys, int32_t *k, int32_t *npoly, int64_t *h_M) {

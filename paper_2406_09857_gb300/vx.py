@@ -61,6 +61,7 @@ def lib() -> ctypes.CDLL:
         "vx_system_create_ex": ([P, P, P, i32, P, PP], i32),
         "vx_system_free": ([P], None),
         "vx_system_info": ([P, P, P, P], i32),
+        "vx_system_measure": ([P, i32, P], i32),
         "vx_system_device_bytes": ([P, P], i32),
         "vx_system_upload_bytes": ([P, P], i32),
         "vx_kernel_launches": ([], i64),
@@ -169,6 +170,16 @@ def _polys(polys):
         keep += [e, c]
         arr[i] = Poly(e.shape[1], e.shape[0], e.ctypes.data, c.ctypes.data)
     return arr, keep
+
+
+def measure(polys) -> np.ndarray:
+    """vx_system_measure: the packing checks and the coefficients each stage reads, M
+    [npoly, k+1] as System.info() gives them, on the host only (no device)."""
+    arr, keep = _polys(polys)
+    k = arr[0].nvars
+    M = np.zeros((len(polys), k + 1), dtype=np.int64)
+    _check(lib().vx_system_measure(arr, len(polys), M.ctypes.data))
+    return M
 
 
 def _domain(domain) -> np.ndarray:

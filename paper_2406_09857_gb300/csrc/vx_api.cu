@@ -8,13 +8,15 @@
 //   - CSF, system and result objects, errors and kernel timing.
 #include <cuda_runtime.h>
 
+#include <unistd.h>
+
 #include <algorithm>
 #include <array>
 #include <atomic>
-#include <map>
-#include <memory>
 #include <condition_variable>
 #include <functional>
+#include <map>
+#include <memory>
 #include <mutex>
 #include <thread>
 #include <cmath>
@@ -336,7 +338,16 @@ __global__ void k_encode_coefs(const double2 *__restrict__ c64, int64_t n, float
 class HostPool {
  public:
   static HostPool &get() {
-    static HostPool *p = new HostPool();  // never destroyed: its threads live as long as the process
+    // never destroyed (its threads live as long as the process); a process forked from this
+    // one has none of its threads and maybe a lock taken at the fork, so it makes its own
+    static std::mutex mu;
+    static HostPool *p = nullptr;
+    static pid_t owner = 0;
+    std::lock_guard<std::mutex> g(mu);
+    if (!p || owner != getpid()) {
+      p = new HostPool();
+      owner = getpid();
+    }
     return *p;
   }
   int size() const { return (int)nworkers_ + 1; }

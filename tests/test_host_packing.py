@@ -86,3 +86,31 @@ def test_repeated_and_concurrent_calls(vx):
     for t in th:
         t.join()
     assert not errs and len(got) == 12 and all(g == want for g in got)
+
+
+@pytest.mark.skipif(not hasattr(__import__("os"), "fork"), reason="needs fork")
+def test_packing_in_a_forked_child(vx):
+    """A process forked after the pool started has none of its threads: it packs on a pool of
+    its own and gets the same counts (so does the parent afterwards)."""
+    import os
+    import warnings
+
+    polys = [synth.kostlan_poly(3, 60, 2101)]
+    want = _total(3, 60)
+    assert vx.measure(polys)[0].tolist() == want
+    r, w = os.pipe()
+    with warnings.catch_warnings():
+        warnings.simplefilter("ignore", DeprecationWarning)  # fork of a threaded process
+        pid = os.fork()
+    if pid == 0:
+        try:
+            ok = vx.measure(polys)[0].tolist() == want
+            os.write(w, b"1" if ok else b"0")
+        finally:
+            os._exit(0)
+    os.close(w)
+    got = os.read(r, 1)
+    os.close(r)
+    os.waitpid(pid, 0)
+    assert got == b"1"
+    assert vx.measure(polys)[0].tolist() == want

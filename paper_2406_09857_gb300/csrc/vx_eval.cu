@@ -1322,8 +1322,7 @@ __global__ void __launch_bounds__(kThreads, 6)
 }
 
 // k_leaf_tma_c for two or more polynomials, without the work that C0 makes useless: each
-// thread runs polynomial 0 on its kLeafIter pairs and settles the pairs whose leaves it
-// excludes; the other pairs are queued in shared memory (warp-aggregated slots, so that the
+// thread runs polynomial 0 on its ITER pairs and settles the pairs whose leaves it excludes; the other pairs are queued in shared memory (warp-aggregated slots, so that the
 // pairs of a warp stay neighbours) with their decisions so far, and the CTA's warps run the
 // remaining polynomials on the queue.  C0 keeps a leaf only if no polynomial excludes it, so
 // the decisions are those of k_leaf_tma_c; the leaves' interval values are not written.

@@ -74,7 +74,8 @@ def _same_values(a, b):
 
 @pytest.mark.parametrize("k,d,npoly,level,density,seed", [
     (1, 7, 2, 6, 1.0, 10), (2, 6, 1, 5, 1.0, 11), (2, 8, 2, 4, 0.5, 12),
-    (3, 4, 1, 4, 1.0, 13), (3, 5, 2, 3, 0.6, 14), (4, 3, 1, 2, 1.0, 15)])
+    (3, 4, 1, 4, 1.0, 13), (3, 5, 2, 3, 0.6, 14), (4, 3, 1, 2, 1.0, 15),
+    (5, 3, 2, 2, 0.7, 16), (6, 2, 1, 2, 1.0, 17)])
 def test_alg2_equals_per_box_nested_horner(k, d, npoly, level, density, seed):
     polys = synth.random_small(k, d, npoly, seed, density=density)
     t = synth.random_tuples(k, level, 400, seed + 100)
@@ -87,7 +88,7 @@ def test_alg2_equals_per_box_nested_horner(k, d, npoly, level, density, seed):
 
 
 @pytest.mark.parametrize("k,d,level,seed", [(1, 9, 5, 1), (2, 7, 4, 2), (3, 5, 3, 3),
-                                            (4, 3, 2, 4)])
+                                            (4, 3, 2, 4), (5, 3, 2, 5), (6, 2, 2, 6)])
 def test_work_count_theorem1(k, d, level, seed):
     polys = synth.random_small(k, d, 1, seed)
     t = synth.random_tuples(k, level, 500, seed)
@@ -99,7 +100,8 @@ def test_work_count_theorem1(k, d, level, seed):
 
 @pytest.mark.parametrize("k,d,npoly,depth,seed", [(1, 9, 1, 7, 20), (2, 6, 1, 5, 21),
                                                   (2, 5, 2, 5, 22), (3, 4, 1, 4, 23),
-                                                  (3, 3, 2, 3, 24)])
+                                                  (3, 3, 2, 3, 24), (4, 3, 2, 3, 25),
+                                                  (5, 2, 1, 3, 26), (6, 2, 2, 2, 27)])
 def test_alg3_equals_brute_force(k, d, npoly, depth, seed):
     polys = synth.random_small(k, d, npoly, seed)
     dom = synth.cube(k)

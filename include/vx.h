@@ -325,7 +325,8 @@ int vx_enclose_batch(const vx_poly *const *systems, const int32_t *npoly, const 
 
 /* Autotuner of the evaluation kernels (not in the paper).  Each stage and leaf launch has a
  * few variants with identical outputs (one or two boxes per thread, numbers of fibre groups,
- * CTA sizes); with mode 1 (the default) the first launch of a shape (arithmetic, depth, node
+ * CTA sizes, the parents' blocks staged in shared memory or not, the leaf pairs that the first
+ * polynomial excludes skipped by the others); with mode 1 (the default) the first launch of a shape (arithmetic, depth, node
  * counts and fibre length, bucketed) times every variant on its real data and keeps the
  * fastest for the later ones (that first launch synchronises its stream); mode 0 uses the
  * built-in heuristics.  cache_path (nullable): a text file of tuned shapes, read by this call

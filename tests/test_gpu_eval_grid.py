@@ -114,3 +114,27 @@ def test_rejects_short_lists(vx):
     with pytest.raises(vx.VxError) as e:
         vx.csf_eval_grid(sysv, c, [(_dev(a), _dev(b)) for a, b in xl], vx.FP64)
     assert e.value.code == vx.EINVAL
+
+
+def test_nesting_order_hand_derived(vx):
+    """Algorithm 2's order (x_1 at the root, Sec. 2.2) on non-degenerate boxes: the GPU's
+    binary64 values equal the hand-derived enclosures of golden/nesting_order.json, which no
+    other nesting order gives."""
+    import json
+    import os
+
+    import torch
+
+    with open(os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden",
+                           "nesting_order.json")) as f:
+        cases = json.load(f)["cases"]
+    for c in cases:
+        polys = [(np.asarray(c["exps"], dtype=np.int32), np.asarray(c["coefs"], dtype=np.float64))]
+        box = np.asarray(c["box"], dtype=np.float64)
+        k = box.shape[0]
+        sysv = vx.System(polys)
+        cs = vx.csf_build(k, 0, _dev(np.zeros((1, k), dtype=np.int32)))
+        dx = [(_dev(box[i, :1].copy()), _dev(box[i, 1:].copy())) for i in range(k)]
+        _, lo, hi = vx.csf_eval_grid(sysv, cs, dx, vx.FP64, values=True)
+        torch.cuda.synchronize()
+        assert (float(lo[0, 0]), float(hi[0, 0])) == tuple(c["expected"]), c["name"]

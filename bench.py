@@ -42,11 +42,16 @@ UNIT = "box-evals/s"
 WORKLOAD = ("curve: 2 trivariate Kostlan polynomials of total degree 100 on [-1,1]^3, "
             "subdivision depth 10 (1024^3 finest grid)")
 
-# Roofline denominators of the plain-ALU evaluation kernels, from unit counts and the maximum
-# SM clock (152 SMs x 2070 MHz): 128 binary32 FMA lanes and 2 binary64 lanes per SM per clock.
-SMS, SM_MHZ = 152, 2070.0
-FP32_PEAK_T = SMS * 128 * SM_MHZ * 1e6 / 1e12  # 40.3 T instructions/s
-FP64_PEAK_T = SMS * 2 * SM_MHZ * 1e6 / 1e12    # 0.63 T instructions/s
+# Roofline denominators of the plain-ALU evaluation kernels, from unit counts: 128 binary32
+# FMA lanes and 2 binary64 lanes per SM per clock, times the device's SM count and the median
+# SM clock sampled under load in the timed region (its maximum clock when no sample was taken).
+FP32_LANES_PER_SM, FP64_LANES_PER_SM = 128, 2
+NOMINAL_SM_MHZ = 2070.0  # the part's maximum SM clock, used only when no clock was read
+
+
+def alu_peaks(sms: int, mhz: float):
+    """(binary32 FMA, binary64) lane-operation peaks in T/s."""
+    return (sms * FP32_LANES_PER_SM * mhz * 1e6 / 1e12, sms * FP64_LANES_PER_SM * mhz * 1e6 / 1e12)
 # FMA-pipe lane operations of one interval multiply-add: binary32 certified = 2 directed FMAs
 # for the endpoints (one paired instruction) + 2 for the error bound; binary64 = 2 directed
 # multiplies + 2 directed adds.
@@ -746,8 +751,51 @@ def run_gpu(args):
                 "launches": v["launches"], "avg_launch_ms": per_launch_ms,
                 "madds_per_launch": v["work"] / v["launches"], "time_share": share}
 
-    roof32 = roofline(tims32, "fp32", FP32_PEAK_T)
-    roof64 = roofline(tims64, "fp64", FP64_PEAK_T)
+    def roofline_by_kind(tims, fp32_peak, fp64_peak):
+        """Every kernel kind of a step with its fraction of the roofline that bounds it: the
+        evaluation kinds against the FMA-pipe (binary32) or FP64 (binary64) lane rate (4 lane
+        operations per interval multiply-add: both endpoint products of both ends), the integer
+        kinds (prune, split, compact, recheck selection, tree builds) against the measured HBM
+        copy bandwidth, with their algorithmic bytes (inputs read once, outputs written once)."""
+        tot = {}
+        for tm in tims:
+            for name, v in tm.items():
+                a = tot.setdefault(name, {"ms": 0.0, "launches": 0, "work": 0})
+                a["ms"] += v["ms"]
+                a["launches"] += v["launches"]
+                a["work"] += v["work"]
+        step_ms = sum(v["ms"] for v in tot.values())
+        hbm = PEAKS.get("hbm_gbs")
+        out = {}
+        for name, v in tot.items():
+            if not v["launches"] or v["ms"] <= 0:
+                continue
+            e = {"ms_per_step": v["ms"] / len(tims), "time_share": v["ms"] / step_ms}
+            if name.startswith(("stage", "leaf")):
+                peak = fp64_peak if name.endswith("fp64") else fp32_peak
+                ach = v["work"] * OPS_PER_MADD["fp32"] / (v["ms"] * 1e-3) / 1e12
+                e.update({"bound": "alu", "unit": "T lane-ops/s", "achieved": ach, "peak": peak,
+                          "frac": ach / peak, "madds_per_step": v["work"] / len(tims)})
+            else:
+                ach = v["work"] / (v["ms"] * 1e-3) / 1e9
+                e.update({"bound": "hbm", "unit": "GB/s", "achieved": ach, "peak": hbm,
+                          "peak_what": "measured copy bandwidth (MEASURED_PEAKS.json hbm_gbs)",
+                          "frac": ach / hbm if hbm else None,
+                          "bytes_per_step": v["work"] / len(tims)})
+            out[name] = e
+        return out
+
+    props = torch.cuda.get_device_properties(torch.cuda.current_device())
+    sms = int(props.multi_processor_count)
+    peak_mhz = (clocks.get("sm_mhz") or clocks.get("sm_max_mhz") or PEAKS.get("sm_max_mhz")
+                or NOMINAL_SM_MHZ)
+    fp32_peak, fp64_peak = alu_peaks(sms, float(peak_mhz))
+    roof32 = roofline(tims32, "fp32", fp32_peak)
+    roof64 = roofline(tims64, "fp64", fp64_peak)
+    for r in (roof32, roof64):
+        r["peak_basis"] = {"sms": sms, "sm_mhz": float(peak_mhz),
+                           "lanes_per_sm": FP32_LANES_PER_SM if r is roof32 else FP64_LANES_PER_SM}
+    by_kind32 = roofline_by_kind(tims32, fp32_peak, fp64_peak)
 
     # ---- end to end through the host API -----------------------------------------------------
     log("[bench] e2e")
@@ -840,6 +888,7 @@ def run_gpu(args):
             "excess_boxes": 0.0 if same else None,
             "recheck_boxes_per_step": int(st32["recheck"].sum()),
             "roofline": roof32,
+            "roofline_by_kind": by_kind32,
             "cpu_baseline": cpu,
             **extra,
             "e2e": e2e,

@@ -264,7 +264,13 @@ int vx_csf_eval_grid(const vx_system *sys, const vx_csf *csf, const double *cons
  *     VX_FP32_MIDRAD), each block rounded up to 256 bytes; VX_EINVAL for VX_FP32.
  *   - No cudaMalloc, cudaFree or allocating library routine is called.  The first call on a
  *     device looks up the array's device address (cudaGetSymbolAddress) with that device
- *     current; make that first call before any stream capture.
+ *     current and keeps it for the process (a lock guards concurrent first calls); make that
+ *     first call before any stream capture.  The address belongs to the device's context:
+ *     after a cudaDeviceReset of that device, do not call this entry point on it again.
+ *   - Like vx_csf_eval_level, the first evaluation of each new level shape times the kernels'
+ *     launch variants on `stream` (events and a stream synchronisation) unless the variant
+ *     choice is fixed with vx_autotune (mode 0, a forced variant, or a tuner cache file that
+ *     already holds the shape).
  *   - Every call shares the array and leaves its contents behind; each block read is written
  *     earlier in the same call, so nothing needs clearing, but calls that overlap on the GPU
  *     (other streams, other host threads) race on it and must be serialised by the caller.

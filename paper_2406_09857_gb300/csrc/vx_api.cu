@@ -50,6 +50,19 @@ void clear_error() { g_err[0] = '\0'; }
 static std::atomic<int64_t> g_launches{0};
 void note_launch(int n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
 
+static std::atomic<int> g_sm_count[64];
+int sm_count() {
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return 1;
+  int n = g_sm_count[dev].load(std::memory_order_relaxed);
+  if (n <= 0) {
+    if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n <= 0)
+      n = 1;
+    g_sm_count[dev].store(n, std::memory_order_relaxed);
+  }
+  return n;
+}
+
 // ---------------------------------------------------------------------------------------
 // device memory: stream-ordered allocations from the device's default pool, which keeps
 // freed memory cached for the next level instead of returning it to the driver.
@@ -609,7 +622,10 @@ static int eval_decide(const SysDev &sys, const CsfView &c, const LevelGrid &g, 
     int64_t ns = 0;
     if (tm && tm->on) rc = tm->begin(KK_RECHECK, n);
     if (rc == VX_OK) rc = flag_indices(flag, n, s, &idx, &ns);
-    if (rc == VX_OK && tm && tm->on) rc = tm->end();
+    if (rc == VX_OK && tm && tm->on) {
+      tm->add_work(4 * ns);  // the selected boxes' indices written
+      rc = tm->end();
+    }
     *nrecheck = ns;
     if (rc == VX_OK && ns > 0) {
       CsfObj sub;
@@ -891,7 +907,7 @@ static int system_create_impl(const vx_poly *F, int32_t npoly, const double *con
   for (int f = 0; f < npoly && e == cudaSuccess; ++f) {
     const int64_t n = (int64_t)hp[f].c64.size();
     if (n == 0) continue;
-    const int64_t nb = std::min<int64_t>((n + 255) / 256, 152 * 8);
+    const int64_t nb = std::min<int64_t>((n + 255) / 256, (int64_t)sm_count() * 8);
     k_encode_coefs<<<(unsigned)nb, 256, 0, s>>>(sys->dev.p[f].c64,
                                                  n, const_cast<float2 *>(sys->dev.p[f].c32),
                                                  const_cast<float4 *>(sys->dev.p[f].c32c));
@@ -2018,7 +2034,7 @@ int dmalloc_copy_trees(ForestTree *d_trees, const std::vector<ForestTree> &ht, c
 
 int grid1(int64_t n) {
   int64_t b = (n + 255) / 256;
-  if (b > 152 * 16) b = 152 * 16;
+  if (b > (int64_t)sm_count() * 16) b = (int64_t)sm_count() * 16;
   return (int)std::max<int64_t>(b, 1);
 }
 

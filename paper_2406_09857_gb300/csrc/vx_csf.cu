@@ -354,7 +354,7 @@ int build_c(int k, int level, const int32_t *d_tuples, int64_t n, cudaStream_t s
   int32_t *scratch = nullptr;
   int64_t ntiles = 0;
   int32_t tot[C];
-  if (tm && tm->on) VX_CHECK(tm->begin(KK_CSF_BUILD, n * k * 4));
+  if (tm && tm->on) VX_CHECK(tm->begin(KK_CSF_BUILD, n * k * 4));  // + the arrays, below
   int32_t herr = 0;
   int rc = scan_prepare<C>(src, n, s, &scratch, &ntiles, tot, d_err, &herr);
   if (rc == VX_OK && herr) {
@@ -366,6 +366,8 @@ int build_c(int k, int level, const int32_t *d_tuples, int64_t n, cudaStream_t s
     int64_t N[VX_KMAX] = {0};
     for (int d = 0; d < k; ++d) N[d] = tot[d];
     rc = csf_alloc(out, k, level, N, s);
+    if (tm && tm->on)
+      for (int d = 0; d < k; ++d) tm->add_work(N[d] * (4 + (d > 0 ? 4 : 0) + (d + 1 < k ? 4 : 0)));
   }
   if (rc == VX_OK) rc = scan_emit<C>(src, BuildEmit{out->v, d_tuples}, n, scratch, ntiles, s);
   if (rc == VX_OK) rc = set_ptr_sentinels(out->v, s);
@@ -594,7 +596,7 @@ __global__ void k_gather(CsfView in, const uint8_t *__restrict__ flags,
 
 int blocks_for(int64_t n) {
   int64_t b = (n + 255) / 256;
-  if (b > 152 * 32) b = 152 * 32;
+  if (b > (int64_t)sm_count() * 32) b = (int64_t)sm_count() * 32;
   if (b < 1) b = 1;
   return (int)b;
 }
@@ -675,7 +677,11 @@ int prune_c(const CsfView &in, const uint8_t *d_keep, int split, int32_t *d_inde
   uint8_t *flags = nullptr;
   int32_t *rank = nullptr, *kptr = nullptr, *scratch = nullptr;
   int rc = VX_OK;
-  if (tm && tm->on) VX_CHECK(tm->begin(KK_PRUNE, total * 9));
+  // algorithmic bytes: the leaves' keep flags and the inner ptr arrays read, one flag byte and
+  // one 4-byte rank per node written
+  int64_t prune_bytes = in.N[k - 1] + 5 * total;
+  for (int d = 0; d + 1 < k; ++d) prune_bytes += 4 * (in.N[d] + 1);
+  if (tm && tm->on) VX_CHECK(tm->begin(KK_PRUNE, prune_bytes));
   rc = dmalloc((void **)&flags, (size_t)total + 16, s);  // 16 bytes for k_mark_parents' loads
   if (rc == VX_OK) rc = dmalloc((void **)&rank, (size_t)total * sizeof(int32_t), s);
   if (rc == VX_OK) {
@@ -683,7 +689,7 @@ int prune_c(const CsfView &in, const uint8_t *d_keep, int split, int32_t *d_inde
                                     cudaMemcpyDeviceToDevice, s);
     for (int d = k - 2; d >= 0 && e == cudaSuccess; --d) {
       int64_t blocks = (in.N[d] + 7) / 8;  // 8 warps per block, one node per warp
-      if (blocks > 152 * 16) blocks = 152 * 16;
+      if (blocks > (int64_t)sm_count() * 16) blocks = (int64_t)sm_count() * 16;
       if (blocks < 1) blocks = 1;
       k_mark_parents<<<(unsigned)blocks, 256, 0, s>>>(in.ptr[d], in.N[d], flags, sg.off[d + 1],
                                                      flags + sg.off[d]);
@@ -735,8 +741,16 @@ int prune_c(const CsfView &in, const uint8_t *d_keep, int split, int32_t *d_inde
       for (int d = 0; d + 1 < k; ++d) K.k[d] = out->v.ptr[d];
     }
   }
-  if (rc == VX_OK && tm && tm->on) rc = tm->begin(split ? KK_SPLIT : KK_COMPACT,
-                                                  split ? (newN[k - 1] * 8 + total * 9) : total * 13);
+  // algorithmic bytes: flags and ranks of every node read; per kept node its label, parent
+  // (depth > 0) and child pointer (depth < k-1) read; the same arrays written per new node (a
+  // split) or per kept node (a compaction)
+  int64_t rebuild_bytes = 5 * total;
+  for (int d = 0; d < k; ++d) {
+    const int64_t w = 4 + (d > 0 ? 4 : 0) + (d + 1 < k ? 4 : 0);
+    rebuild_bytes += ((int64_t)nk[d] + (split ? newN[d] : (int64_t)nk[d])) * w;
+  }
+  if (!split && d_index) rebuild_bytes += 4 * (int64_t)nk[k - 1];
+  if (rc == VX_OK && tm && tm->on) rc = tm->begin(split ? KK_SPLIT : KK_COMPACT, rebuild_bytes);
   for (int d = 0; d + 1 < k && rc == VX_OK; ++d) {
     launch_kptr(d, blocks_for(in.N[d]), s, in, flags, rank, sg, (int32_t *)K.k[d]);
     note_launch();

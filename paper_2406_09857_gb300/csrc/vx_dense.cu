@@ -383,7 +383,7 @@ __global__ void k_factors(FactorArgs f) {
 
 int grid_for(int64_t n) {
   int64_t b = (n + 255) / 256;
-  if (b > 152 * 16) b = 152 * 16;
+  if (b > (int64_t)sm_count() * 16) b = (int64_t)sm_count() * 16;
   if (b < 1) b = 1;
   return (int)b;
 }

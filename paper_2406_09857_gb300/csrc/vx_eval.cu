@@ -1402,7 +1402,7 @@ int leaf_tma_grid(int64_t leaves, int iter = kLeafIter) {
 
 int leaf_pair_grid(int64_t leaves) {
   int64_t b = ((leaves + 1) / 2 + kThreads - 1) / kThreads;
-  const int64_t cap = 152 * 32;
+  const int64_t cap = (int64_t)sm_count() * 32;
   if (b > cap) b = cap;
   if (b < 1) b = 1;
   return (int)b;
@@ -1419,10 +1419,17 @@ inline bool tma_input_node_major(int d, int k, const bool *tma) { return d + 1 =
 
 int leaf_grid(int64_t items) {
   int64_t b = (items + kThreads - 1) / kThreads;
-  const int64_t cap = 152 * 32;
+  const int64_t cap = (int64_t)sm_count() * 32;
   if (b > cap) b = cap;
   if (b < 1) b = 1;
   return (int)b;
+}
+
+// Bytes of one depth's partial-evaluation block (n nodes of blk entries), rounded up to 256 so
+// that the next block starts on a 256-byte boundary.
+template <class AR>
+size_t block_bytes(int64_t n, int64_t blk) {
+  return ((size_t)n * (size_t)blk * sizeof(typename AR::V) + 255) & ~(size_t)255;
 }
 
 // Bytes of partial-evaluation blocks a level needs (each block 256-byte aligned).
@@ -1430,8 +1437,7 @@ template <class AR>
 size_t level_scratch_bytes(const SysDev &sys, const CsfView &c) {
   size_t total = 0;
   for (int f = 0; f < sys.npoly; ++f)
-    for (int d = 0; d + 1 < sys.k; ++d)
-      total += ((size_t)c.N[d] * sys.p[f].st[d].blk_out * sizeof(typename AR::V) + 255) & ~(size_t)255;
+    for (int d = 0; d + 1 < sys.k; ++d) total += block_bytes<AR>(c.N[d], sys.p[f].st[d].blk_out);
   return total;
 }
 
@@ -1554,18 +1560,20 @@ int eval_level_t(const SysDev &sys, const CsfView &c, const LevelGrid &grid, dou
     for (int f = 0; f < sys.npoly; ++f)
       for (int d = 0; d + 1 < k; ++d) {
         buf[f][d] = (V *)p;
-        p += ((size_t)c.N[d] * sys.p[f].st[d].blk_out * sizeof(V) + 255) & ~(size_t)255;
+        p += block_bytes<AR>(c.N[d], sys.p[f].st[d].blk_out);
       }
   }
+  // one allocation per polynomial, each depth's block starting on a 256-byte boundary (the
+  // bulk copies of the staged kernels read parent blocks from 16-byte aligned addresses)
   for (int f = 0; f < sys.npoly && rc == VX_OK && !ext_scratch; ++f) {
     size_t total = 0;
-    for (int d = 0; d + 1 < k; ++d) total += (size_t)c.N[d] * sys.p[f].st[d].blk_out;
+    for (int d = 0; d + 1 < k; ++d) total += block_bytes<AR>(c.N[d], sys.p[f].st[d].blk_out);
     if (total == 0) continue;
-    rc = dmalloc(&mem[f], total * sizeof(V), s);
-    size_t off = 0;
+    rc = dmalloc(&mem[f], total, s);
+    char *p = (char *)mem[f];
     for (int d = 0; d + 1 < k && rc == VX_OK; ++d) {
-      buf[f][d] = (V *)mem[f] + off;
-      off += (size_t)c.N[d] * sys.p[f].st[d].blk_out;
+      buf[f][d] = (V *)p;
+      p += block_bytes<AR>(c.N[d], sys.p[f].st[d].blk_out);
     }
   }
 
@@ -1581,8 +1589,9 @@ int eval_level_t(const SysDev &sys, const CsfView &c, const LevelGrid &grid, dou
                         (size_t)st.blk_in * sizeof(V);
       // cp.async.bulk needs 16-byte aligned source and size: every parent block must start on
       // a 16-byte boundary (the buffer itself is 256-byte aligned)
-      const bool aligned = (st.blk_in * (int64_t)sizeof(V)) % 16 == 0;
-      if (aligned && c.N[d] >= 152 * 4 * kThreads && c.N[d] >= 128 * c.N[d - 1] &&
+      const bool aligned = (st.blk_in * (int64_t)sizeof(V)) % 16 == 0 &&
+                           (reinterpret_cast<uintptr_t>(buf[f][d - 1]) & 15u) == 0;
+      if (aligned && c.N[d] >= (int64_t)sm_count() * 4 * kThreads && c.N[d] >= 128 * c.N[d - 1] &&
           sm <= kMaxDynSmem) {
         tma[d] = true;
         tma_smem[d] = sm;
@@ -1616,7 +1625,7 @@ int eval_level_t(const SysDev &sys, const CsfView &c, const LevelGrid &grid, dou
         const int64_t np = c.N[d - 1];
         const int64_t avg = c.N[d] / np;
         const int threads0 = avg >= 512 ? 512 : (avg >= 256 ? 256 : 128);
-        int64_t G0 = (4 * 152 * 2 + np - 1) / np;
+        int64_t G0 = ((int64_t)sm_count() * 8 + np - 1) / np;
         if (G0 > st.nfib) G0 = st.nfib;
         if (G0 < 1) G0 = 1;
         auto launch = [&](int v) -> int {
@@ -1651,12 +1660,12 @@ int eval_level_t(const SysDev &sys, const CsfView &c, const LevelGrid &grid, dou
           const bool pairs = v == 1 ? !pairs0 : pairs0;
           const int64_t per_warp = pairs ? 64 : 32;
           const int64_t nchunk = (c.N[d] + per_warp - 1) / per_warp;
-          const int64_t target = 152 * 64 * (v == 2 ? 4 : 1);
+          const int64_t target = (int64_t)sm_count() * 64 * (v == 2 ? 4 : 1);
           int64_t G = (target + nchunk - 1) / nchunk;
           if (G > st.nfib) G = st.nfib;
           if (G < 1) G = 1;
           int64_t blocks = (nchunk * G + kWarpsPerBlock - 1) / kWarpsPerBlock;
-          if (blocks > 152 * 64) blocks = 152 * 64;
+          if (blocks > (int64_t)sm_count() * 64) blocks = (int64_t)sm_count() * 64;
           if (pairs)
             k_stage_c<<<(unsigned)blocks, kThreads, (st.maxlen + 1) * sizeof(int32_t), s>>>(
                 st, c.lab[d], d == 0 ? nullptr : c.par[d], (const float4 *)in, in_estride,
@@ -1934,7 +1943,7 @@ int eval_forest_t(const ForestTree *d_trees, const ForestTree *h_trees, const in
       for (int f = 0; f < h_trees[t].dev.npoly; ++f)
         maxfib = std::max<int64_t>(maxfib, h_trees[t].dev.p[f].st[d].nfib);
     }
-    if (!leaf && chunks > 0) G[d] = (int)std::min<int64_t>(maxfib, std::max<int64_t>(1, (152 * 64 + chunks - 1) / chunks));
+    if (!leaf && chunks > 0) G[d] = (int)std::min<int64_t>(maxfib, std::max<int64_t>(1, ((int64_t)sm_count() * 64 + chunks - 1) / chunks));
     int64_t acc = 0;
     for (int t = 0; t < S; ++t) {
       tasks[(size_t)d * (S + 1) + t] = acc;
@@ -1952,7 +1961,7 @@ int eval_forest_t(const ForestTree *d_trees, const ForestTree *h_trees, const in
   }
   auto blocks_of = [](int64_t ntask) {
     int64_t b = (ntask + kWarpsPerBlock - 1) / kWarpsPerBlock;
-    return (unsigned)std::max<int64_t>(1, std::min<int64_t>(b, 152 * 32));
+    return (unsigned)std::max<int64_t>(1, std::min<int64_t>(b, (int64_t)sm_count() * 32));
   };
   for (int d = 0; d + 1 < k && rc == VX_OK; ++d) {
     const int64_t *td = (const int64_t *)dtasks + (size_t)d * (S + 1);
@@ -2160,6 +2169,10 @@ int take_device_status(cudaStream_t s, int *status) {
 // ---------------------------------------------------------------------------------------
 static __device__ __align__(256) unsigned char g_vx_static_scratch[VX_STATIC_SCRATCH_BYTES];
 
+// The array's device address per device ordinal, looked up by the first call on that device
+// (with it current) and kept; the lock makes concurrent first calls from several host threads
+// safe.  The address belongs to the device's context: a cudaDeviceReset on that device ends it.
+static std::mutex g_static_scratch_mu;
 static void *g_static_scratch_addr[64] = {nullptr};
 
 int static_scratch_address(void **addr) {
@@ -2169,6 +2182,7 @@ int static_scratch_address(void **addr) {
     set_error("device ordinal %d is outside the supported range", dev);
     return VX_EINVAL;
   }
+  std::lock_guard<std::mutex> lock(g_static_scratch_mu);
   if (!g_static_scratch_addr[dev]) {
     void *p = nullptr;
     VX_CUDA(cudaGetSymbolAddress(&p, g_vx_static_scratch));

@@ -38,6 +38,10 @@ void clear_error();
 // Counts the kernels this library launches (process-wide, all threads).
 void note_launch(int n = 1);
 
+// Streaming multiprocessors of the current device (cudaDevAttrMultiProcessorCount, read once
+// per device); grid sizes are multiples of it.
+int sm_count();
+
 // Stream-ordered device memory (the device's default memory pool, kept cached).
 int dmalloc(void **p, size_t bytes, cudaStream_t s);
 void dfree(void *p, cudaStream_t s);
@@ -117,11 +121,14 @@ enum KernelKind {
   KK_STAGE0_F32C,
   KK_STAGEJ_F32C,
   KK_LEAF_F32C,
-  KK_CSF_BUILD,    // scans of csf_build
-  KK_PRUNE,        // keep propagation, rank scan, kept-tree pointers
-  KK_SPLIT,        // 2^k split and rebuild
-  KK_COMPACT,      // stable compaction of kept leaves
-  KK_RECHECK,      // selection of tight boxes for the FP64 recheck
+  // The integer phases' work is their algorithmic bytes: each input array read once and each
+  // output array written once (node counts N_d, total = sum N_d, kept nk_d, new newN_d).
+  KK_CSF_BUILD,    // scans of csf_build: the tuples read, the tree's arrays written
+  KK_PRUNE,        // keep propagation and rank scan: keep + ptr read, flags + ranks written
+  KK_SPLIT,        // 2^k split and rebuild: flags + ranks read, kept nodes' arrays read, new
+                   // nodes' arrays written
+  KK_COMPACT,      // stable compaction: flags + ranks read, kept nodes' arrays read and written
+  KK_RECHECK,      // selection of the boxes to re-evaluate: flags read, their indices written
   KK_COUNT
 };
 
@@ -140,6 +147,10 @@ struct Timer {
   int64_t work[KK_COUNT] = {0};
   int begin(int kind, int64_t work);  // records the start event on `stream`
   int end();                          // records the stop event of the last begin()
+  // adds to the work of the last begin() (for counts known only once its kernels ran)
+  void add_work(int64_t w) {
+    if (!pending.empty()) pending.back().work += w;
+  }
   int collect();                      // synchronises and folds pending pairs into the sums
   void release();
 };

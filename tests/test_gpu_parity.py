@@ -618,3 +618,36 @@ def test_box_codes_decode_to_the_boxes(vx, k, d, depth):
     assert np.all(codes[1:] > codes[:-1])
     assert np.array_equal(vx.Result.decode_codes(codes, k, depth), r.boxes())
     assert codes.shape[0] > 0
+
+
+def test_midrad_k4_staged_stage_reads_aligned_blocks(vx):
+    """Four variables in binary32 midpoint-radius (8-byte entries): stage 0 writes an odd
+    number of entries (5 depth-1 nodes x 27 suffix monomials), so the depth-1 blocks would
+    start 8 bytes off a 16-byte boundary if the depths were packed back to back, and depth 2
+    has enough nodes (81 920, 128 per parent) for its stage to bring the parents' blocks into
+    shared memory by bulk copies.  Every depth's block starts on a 256-byte boundary, so the
+    level evaluates; its values equal the allocation-free entry point's (which carves the same
+    layout from its own array) bit for bit and contain the oracle's binary64 enclosures."""
+    import torch
+
+    polys = synth.random_small(4, 4, 1, 901, density=0.5)
+    M = vx.measure(polys)[0]
+    assert M[1] % 2 == 1 and (M[2] * 8) % 16 == 0
+    x1, x2, x3 = np.meshgrid(np.arange(5), np.arange(128), np.arange(128), indexing="ij")
+    x4 = (7 * x1 + 3 * x2 + x3) % 128
+    t = np.stack([x1.ravel(), x2.ravel(), x3.ravel(), x4.ravel()], axis=1).astype(np.int32)
+    sysv = vx.System(polys)
+    c = vx.csf_build(4, 7, dev(t))
+    assert c.nodes()[2].tolist() == [5, 640, 81920, 81920]
+    dom = synth.cube(4)
+    keep, lo, hi = vx.csf_eval_level(sysv, c, dom, vx.FP32_MIDRAD, values=True)
+    n = t.shape[0]
+    keep_s = torch.empty(n, dtype=torch.uint8, device="cuda")
+    lo_s = torch.empty((1, n), dtype=torch.float64, device="cuda")
+    hi_s = torch.empty_like(lo_s)
+    vx.csf_eval_level_static(sysv, c, dom, vx.FP32_MIDRAD, keep_s, lo_s, hi_s)
+    torch.cuda.synchronize()
+    assert torch.equal(keep, keep_s) and torch.equal(lo, lo_s) and torch.equal(hi, hi_s)
+    lo_o, hi_o, keep_o, _ = oracle.eval_csf(polys, dom, 7, t)
+    assert np.all(lo.cpu().numpy() <= lo_o) and np.all(hi.cpu().numpy() >= hi_o)
+    assert np.all(keep.cpu().numpy() >= keep_o)

@@ -78,3 +78,56 @@ def test_static_rejects_what_does_not_fit(vx):
     with pytest.raises(vx.VxError) as e:
         vx.csf_eval_level_static(sysv, c, synth.cube(3), vx.FP32, keep)
     assert e.value.code == vx.EINVAL
+
+
+def _cudart():
+    """The CUDA runtime this process has loaded (the one libvx links), through ctypes."""
+    import ctypes
+
+    path = None
+    with open("/proc/self/maps") as f:
+        for line in f:
+            if "libcudart.so" in line:
+                path = line.split()[-1]
+                break
+    return ctypes.CDLL(path or "libcudart.so.13")
+
+
+def _pool_used_high(rt, reset=False):
+    """cudaMemPoolAttrUsedMemHigh (0x8) of device 0's default pool, which libvx's stream-ordered
+    allocations come from; reset=True first sets the high mark to the current use."""
+    import ctypes
+
+    pool = ctypes.c_void_p()
+    assert rt.cudaDeviceGetDefaultMemPool(ctypes.byref(pool), 0) == 0
+    if reset:
+        zero = ctypes.c_uint64(0)
+        assert rt.cudaMemPoolSetAttribute(pool, 0x8, ctypes.byref(zero)) == 0
+    v = ctypes.c_uint64(0)
+    assert rt.cudaMemPoolGetAttribute(pool, 0x8, ctypes.byref(v)) == 0
+    return v.value
+
+
+def test_static_call_allocates_no_device_memory(vx):
+    """The defining property, observed from outside: across a warmed-up call the high-water mark
+    of the device pool the library allocates from does not move, while the allocating entry
+    point on the same level does move it (so the probe sees the library's allocations)."""
+    import torch
+
+    polys, sysv, c, n = _case(vx, 3, 6, 2, 5, 6000, 73)
+    dom = synth.cube(3)
+    keep = torch.empty(n, dtype=torch.uint8, device="cuda")
+    lo = torch.empty((len(polys), n), dtype=torch.float64, device="cuda")
+    hi = torch.empty_like(lo)
+    vx.csf_eval_level_static(sysv, c, dom, vx.FP64, keep, lo, hi)  # warm-up (symbol lookup)
+    torch.cuda.synchronize()
+    rt = _cudart()
+    base = _pool_used_high(rt, reset=True)
+    for _ in range(2):
+        vx.csf_eval_level_static(sysv, c, dom, vx.FP64, keep, lo, hi)
+        vx.csf_eval_level_static(sysv, c, dom, vx.FP32_MIDRAD, keep, lo, hi)
+    torch.cuda.synchronize()
+    assert _pool_used_high(rt) == base
+    vx.csf_eval_level(sysv, c, dom, vx.FP64, values=True)
+    torch.cuda.synchronize()
+    assert _pool_used_high(rt) > base

@@ -548,6 +548,7 @@ __global__ void __launch_bounds__(kThreads)
 // warp takes the per-leaf path of k_leaf.
 struct YLeaf {
   float yl, yh, xmaxp;
+  float xb;  // RU(yh (1 + 2^-23)): the multiplier of the summed bound (leaf_bform)
   bool neg;
 };
 
@@ -557,6 +558,7 @@ __device__ __forceinline__ YLeaf yleaf(const A32C::X &x) {
   y.yl = y.neg ? x.nh : x.l;
   y.yh = y.neg ? x.nl : x.h;
   y.xmaxp = x.xmaxp;
+  y.xb = __fmaf_ru(y.yh, 0x1p-23f, y.yh);
   return y;
 }
 
@@ -568,6 +570,7 @@ __device__ __forceinline__ float4 negated(float4 A) { return make_float4(A.y, A.
 struct YPair {
   float2 l0, h0, l1, h1;  // (yl, yl) and (yh, yh) of leaf 0 and leaf 1
   float2 xm;              // (xmaxp of leaf 0, xmaxp of leaf 1)
+  float2 xb;              // (xb of leaf 0, xb of leaf 1)
   bool neg0, neg1;
 };
 
@@ -578,6 +581,7 @@ __device__ __forceinline__ YPair ypair(const YLeaf &a, const YLeaf &b) {
   y.l1 = make_float2(b.yl, b.yl);
   y.h1 = make_float2(b.yh, b.yh);
   y.xm = make_float2(a.xmaxp, b.xmaxp);
+  y.xb = make_float2(a.xb, b.xb);
   y.neg0 = a.neg;
   y.neg1 = b.neg;
   return y;
@@ -589,7 +593,9 @@ __device__ __forceinline__ YPair ypair(const YLeaf &a, const YLeaf &b) {
 // entry as it is, 1 negated for both leaves (a pair swap), 2 negated per leaf where sw0 / sw1.
 // Each end is the min of two paired FMAs rounded to nearest; the bounds follow A32C::step's
 // recursion, both leaves' in one paired FMA pair.
-template <int SW>
+// BF: the entry's .z/.w hold the summed bound B of leaf_bform, and the bound advances as
+// e = RU(e xb + B) (one paired FMA for both leaves, no magnitude of the step's result).
+template <int SW, bool BF = false>
 __device__ __forceinline__ void step_y2(float2 &j0, float2 &j1, float2 &e, const YPair &y,
                                         const float4 &A, bool sw0, bool sw1) {
   float2 c0, c1;
@@ -605,8 +611,13 @@ __device__ __forceinline__ void step_y2(float2 &j0, float2 &j1, float2 &e, const
   const float2 P1 = __ffma2_rn(j1, y.l1, c1), Q1 = __ffma2_rn(j1, y.h1, c1);
   j0 = make_float2(fminf(P0.x, Q0.x), fminf(P0.y, Q0.y));
   j1 = make_float2(fminf(P1.x, Q1.x), fminf(P1.y, Q1.y));
-  const float2 m = make_float2(fmaxf(fabsf(j0.x), fabsf(j0.y)), fmaxf(fabsf(j1.x), fabsf(j1.y)));
-  e = __ffma2_ru(e, y.xm, __ffma2_ru(make_float2(kCr, kCr), m, make_float2(A.z, A.w)));
+  if (BF) {
+    e = __ffma2_ru(e, y.xb, make_float2(A.z, A.w));
+  } else {
+    const float2 m =
+        make_float2(fmaxf(fabsf(j0.x), fabsf(j0.y)), fmaxf(fabsf(j1.x), fabsf(j1.y)));
+    e = __ffma2_ru(e, y.xm, __ffma2_ru(make_float2(kCr, kCr), m, make_float2(A.z, A.w)));
+  }
 }
 
 // SGN: +1 no leaf negated, -1 both negated (warp-uniform cases), 0 per leaf at run time.
@@ -618,7 +629,7 @@ struct SwapOdd {
 // Horner of NP polynomials of one length L on the leaves of y (one parent): chain f of leaf c
 // is (-1)^a J_a (equal to J_a when the leaf is not negated).  Odd entries are negated for a
 // negated leaf; the loop takes the entries in (odd, even) pairs, loaded one pair ahead.
-template <int NP, int SGN>
+template <int NP, int SGN, bool BF = false>
 __device__ __forceinline__ void horner_y2(const float4 *const (&b)[2], int L, const YPair &y,
                                           float4 (&K0)[2], float4 (&K1)[2]) {
   constexpr int SWO = SwapOdd<SGN>::value;
@@ -636,7 +647,7 @@ __device__ __forceinline__ void horner_y2(const float4 *const (&b)[2], int L, co
   int a = L - 2;
   if (a >= 0 && !(a & 1)) {
 #pragma unroll
-    for (int f = 0; f < NP; ++f) step_y2<0>(j0[f], j1[f], e[f], y, b[f][a], false, false);
+    for (int f = 0; f < NP; ++f) step_y2<0, BF>(j0[f], j1[f], e[f], y, b[f][a], false, false);
     --a;
   }
   // two (odd, even) pairs per trip: half the loop and address overhead per step
@@ -651,8 +662,8 @@ __device__ __forceinline__ void horner_y2(const float4 *const (&b)[2], int L, co
       }
 #pragma unroll
       for (int f = 0; f < NP; ++f) {
-        step_y2<SWO>(j0[f], j1[f], e[f], y, A[f], y.neg0, y.neg1);
-        step_y2<0>(j0[f], j1[f], e[f], y, B[f], false, false);
+        step_y2<SWO, BF>(j0[f], j1[f], e[f], y, A[f], y.neg0, y.neg1);
+        step_y2<0, BF>(j0[f], j1[f], e[f], y, B[f], false, false);
       }
     }
   }
@@ -665,8 +676,8 @@ __device__ __forceinline__ void horner_y2(const float4 *const (&b)[2], int L, co
     }
 #pragma unroll
     for (int f = 0; f < NP; ++f) {
-      step_y2<SWO>(j0[f], j1[f], e[f], y, A[f], y.neg0, y.neg1);
-      step_y2<0>(j0[f], j1[f], e[f], y, B[f], false, false);
+      step_y2<SWO, BF>(j0[f], j1[f], e[f], y, A[f], y.neg0, y.neg1);
+      step_y2<0, BF>(j0[f], j1[f], e[f], y, B[f], false, false);
     }
   }
 #pragma unroll
@@ -1111,7 +1122,7 @@ struct GlobalBlocks {
 // binary64).  A warp whose pairs each share a parent and do not straddle 0 takes the paired,
 // sign-free path (two polynomials of one length at a time when NPMAX is 2); any other warp
 // runs every leaf on its own.
-template <int NPMAX, class Src>
+template <int NPMAX, class Src, bool BF = false>
 __device__ __forceinline__ void leaf_pair_eval(const LeafArgs &A, int fb, int fe, const Src &src,
                                                int64_t i0, int64_t i1, bool live, bool two,
                                                const A32C::X &x0, const A32C::X &x1, int64_t p0,
@@ -1139,11 +1150,11 @@ __device__ __forceinline__ void leaf_pair_eval(const LeafArgs &A, int fb, int fe
         const V *const b[2] = {src(f, p0), src(f + 1, p0)};
         V K0[2], K1[2];
         if (ws > 0)
-          horner_y2<2, 1>(b, A.len[f], yp, K0, K1);
+          horner_y2<2, 1, BF>(b, A.len[f], yp, K0, K1);
         else if (ws < 0)
-          horner_y2<2, -1>(b, A.len[f], yp, K0, K1);
+          horner_y2<2, -1, BF>(b, A.len[f], yp, K0, K1);
         else
-          horner_y2<2, 0>(b, A.len[f], yp, K0, K1);
+          horner_y2<2, 0, BF>(b, A.len[f], yp, K0, K1);
         decide(f, 0, K0[0]);
         decide(f + 1, 0, K0[1]);
         decide(f, 1, K1[0]);
@@ -1154,11 +1165,11 @@ __device__ __forceinline__ void leaf_pair_eval(const LeafArgs &A, int fb, int fe
       const V *const b[2] = {src(f, p0), nullptr};
       V K0[2], K1[2];
       if (ws > 0)
-        horner_y2<1, 1>(b, A.len[f], yp, K0, K1);
+        horner_y2<1, 1, BF>(b, A.len[f], yp, K0, K1);
       else if (ws < 0)
-        horner_y2<1, -1>(b, A.len[f], yp, K0, K1);
+        horner_y2<1, -1, BF>(b, A.len[f], yp, K0, K1);
       else
-        horner_y2<1, 0>(b, A.len[f], yp, K0, K1);
+        horner_y2<1, 0, BF>(b, A.len[f], yp, K0, K1);
       decide(f, 0, K0[0]);
       decide(f, 1, K1[0]);
     }
@@ -1259,6 +1270,42 @@ struct ChunkBlocks {  // the staged blocks of parents p0 .. p0 + n - 1, else glo
   }
 };
 
+// The staged blocks of the leaf stage rewritten for the summed bound: entry b (row b of the
+// polynomial's single fibre, length L) keeps its binary32 ends and gets, in place of its bound
+// E, B_b = RU((1 + 2^-50) E + kappa w_b M_b) + 2^-148, M_b = max(|lo|, |hi|) of the entry,
+// w_b = min(b + 1, L - 1), kappa = 2^-24 (1 + 2^-23).  A leaf pair on y = |x| in
+// [yl, yh] then bounds its distance to binary64 by e = Horner of B at xb = RU(yh (1 + 2^-23)),
+// each step RU(e xb + B_b), instead of carrying the bound step by step from the magnitudes of
+// its own partial values.  Why this bounds D = |lo32 - lo*| + |lo64 - lo*| (lo* exact): one
+// step of a chain (value s, coefficient c, T = |s_prev| yh + |c|) gives
+//   D <= (1 + 2^-50)(D_prev yh + E) + (2^-24 + 2^-50) T + 2^-149
+// (binary32 rounds once to nearest, < 2^-24 T; binary64 rounds product and sum downward,
+// < 2^-52 each of magnitudes <= T + D_prev yh + E), and |s| <= (1 + 2^-24) T + 2^-150, so
+// T_a <= sum_{b >= a} M_b ((1 + 2^-24) yh)^(b - a); summing the recursion over the steps
+// counts M_b once for each of the w_b steps a <= b, and every factor (1 + 2^-50)(1 + 2^-24)
+// per power of yh is inside xb.  B_b >= E_b, so a per-step consumer of the block (A32C::step)
+// stays sound on the rewritten entries.
+__device__ __forceinline__ void leaf_bform(float4 *s_blk, const int32_t *s_off, const LeafArgs &A,
+                                           int npoly, int64_t np) {
+  constexpr float kKappaB = 0x1.000002p-24f;  // >= 2^-24 + 2^-50
+  for (int f = 0; f < npoly; ++f) {
+    const int L = A.len[f];
+    const int64_t blk = A.blk[f];
+    const int64_t n = np * blk;
+    float4 *b = s_blk + s_off[f];
+    for (int64_t i = threadIdx.x; i < n; i += blockDim.x) {
+      const int r = (int)(i % blk);
+      const float4 v = b[i];
+      const int w = r + 1 < L - 1 ? r + 1 : (L > 1 ? L - 1 : 0);
+      const float M = fmaxf(fabsf(v.x), fabsf(v.y));
+      float B = __fmaf_ru(__fmul_ru(kKappaB, (float)w), M, v.z);
+      B = __fmaf_ru(v.z, 0x1p-50f, B);
+      B = __fadd_ru(B, kEta148);
+      b[i] = make_float4(v.x, v.y, B, B);
+    }
+  }
+}
+
 // One thread: the bulk copies of parents pf .. pl's blocks, every polynomial's at s_off[f]
 // (kLeafParents blocks apart), completing on bar.
 __device__ __forceinline__ void leaf_chunk_copy(const LeafArgs &A, int npoly, int64_t pf,
@@ -1307,7 +1354,10 @@ __global__ void __launch_bounds__(kThreads, 6)
   if (staged) {
     if (threadIdx.x == 0) leaf_chunk_copy(A, npoly, pf, pl, bar, s_off, s_blk);
     __syncthreads();
-    if (!mbar_wait_bounded(bar, 0)) return;
+    const bool ok = mbar_wait_bounded(bar, 0);
+    if (!__syncthreads_and(ok)) return;
+    leaf_bform(s_blk, s_off, A, npoly, pl - pf + 1);
+    __syncthreads();
   }
   const ChunkBlocks src{A, s_blk, s_off, pf, staged};
   // every warp runs the same trip count (the vote inside sees all 32 lanes)
@@ -1317,7 +1367,14 @@ __global__ void __launch_bounds__(kThreads, 6)
     const int64_t i0 = live ? na : last, i1 = two ? na + 1 : i0;
     const A32C::X x0 = A32C::box(g, __ldg(lab + i0)), x1 = A32C::box(g, __ldg(lab + i1));
     const int64_t p0 = __ldg(par + i0), p1 = __ldg(par + i1);
-    leaf_pair_c(A, npoly, src, i0, i1, live, two, x0, x1, p0, p1, nleaves, keep, lo, hi, flag);
+    bool ex[2] = {false, false}, am[2] = {false, false};
+    if (staged)
+      leaf_pair_eval<2, ChunkBlocks, true>(A, 0, npoly, src, i0, i1, live, two, x0, x1, p0, p1,
+                                           nleaves, lo, hi, ex, am);
+    else
+      leaf_pair_eval<2, ChunkBlocks, false>(A, 0, npoly, src, i0, i1, live, two, x0, x1, p0, p1,
+                                            nleaves, lo, hi, ex, am);
+    leaf_pair_store(i0, i1, live, two, ex, am, keep, flag);
   }
 }
 
@@ -1351,6 +1408,10 @@ __global__ void __launch_bounds__(kThreads, 8)
   __syncthreads();
   const bool ok = !staged || mbar_wait_bounded(bar, 0);
   if (!__syncthreads_and(ok)) return;
+  if (staged) {
+    leaf_bform(s_blk, s_off, A, npoly, pl - pf + 1);
+    __syncthreads();
+  }
   const ChunkBlocks src{A, s_blk, s_off, pf, staged};
   const int lane = threadIdx.x & 31;
   for (int it = 0; it < ITER; ++it) {
@@ -1361,8 +1422,12 @@ __global__ void __launch_bounds__(kThreads, 8)
     const A32C::X x0 = A32C::box(g, __ldg(lab + i0)), x1 = A32C::box(g, __ldg(lab + i1));
     const int64_t p0 = __ldg(par + i0), p1 = __ldg(par + i1);
     bool ex[2] = {false, false}, am[2] = {false, false};
-    leaf_pair_eval<1>(A, 0, 1, src, i0, i1, live, two, x0, x1, p0, p1, nleaves, nullptr,
-                      nullptr, ex, am);
+    if (staged)
+      leaf_pair_eval<1, ChunkBlocks, true>(A, 0, 1, src, i0, i1, live, two, x0, x1, p0, p1,
+                                           nleaves, nullptr, nullptr, ex, am);
+    else
+      leaf_pair_eval<1, ChunkBlocks, false>(A, 0, 1, src, i0, i1, live, two, x0, x1, p0, p1,
+                                            nleaves, nullptr, nullptr, ex, am);
     const bool more = live && !(ex[0] && (ex[1] || !two));
     if (live && !more) leaf_pair_store(i0, i1, live, two, ex, am, keep, flag);
     const unsigned m = __ballot_sync(0xffffffffu, more);
@@ -1389,8 +1454,12 @@ __global__ void __launch_bounds__(kThreads, 8)
     const A32C::X x0 = A32C::box(g, __ldg(lab + i0)), x1 = A32C::box(g, __ldg(lab + i1));
     const int64_t p0 = __ldg(par + i0), p1 = __ldg(par + i1);
     bool ex[2] = {(st & 1) != 0, (st & 4) != 0}, am[2] = {(st & 2) != 0, (st & 8) != 0};
-    leaf_pair_eval<1>(A, 1, npoly, src, i0, i1, in, two, x0, x1, p0, p1, nleaves, nullptr,
-                      nullptr, ex, am);
+    if (staged)
+      leaf_pair_eval<1, ChunkBlocks, true>(A, 1, npoly, src, i0, i1, in, two, x0, x1, p0, p1,
+                                           nleaves, nullptr, nullptr, ex, am);
+    else
+      leaf_pair_eval<1, ChunkBlocks, false>(A, 1, npoly, src, i0, i1, in, two, x0, x1, p0, p1,
+                                            nleaves, nullptr, nullptr, ex, am);
     leaf_pair_store(i0, i1, in, two, ex, am, keep, flag);
   }
 }

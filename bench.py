@@ -919,7 +919,8 @@ def run_profile_case(args):
     st = r.stats()
     print(json.dumps({"profile_case_depth": args.profile_case, "mode": args.mode,
                       "boxes": int(st["kept"][-1]), "tested": st["tested"].tolist(),
-                      "ms": r.elapsed_ms()}))
+                      "kept": st["kept"].tolist(), "nodes": st["nodes"].tolist(),
+                      "madds": st["madds"].tolist(), "ms": r.elapsed_ms()}))
     return 0
 
 

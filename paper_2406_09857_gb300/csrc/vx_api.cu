@@ -281,7 +281,7 @@ struct HostStage {
   int32_t nfib = 0, maxlen = 0;
   int64_t blk_in = 0, blk_out = 0;
   std::vector<uint64_t> keys;  // fibre monomial in x_{s+2}..x_k, key_bits(k) bits per exponent
-  std::vector<int32_t> rowoff, fiblen, outpos;
+  std::vector<int32_t> rowoff, fiblen, outpos, fiboff, outpos_fm;
   FlatMap index;
 };
 
@@ -534,6 +534,8 @@ static int pack_poly(int k, const vx_poly &p, HostPoly *hp, const double *chi = 
       }
     }
     S.blk_in = S.rowoff[S.maxlen];
+    S.fiboff.assign(nf + 1, 0);
+    for (int32_t f = 0; f < nf; ++f) S.fiboff[f + 1] = S.fiboff[f] + S.fiblen[f];
     if (S.maxlen > 8192) {
       set_error("polynomial: degree %d in one variable exceeds 8191", S.maxlen - 1);
       return VX_EINVAL;
@@ -555,6 +557,7 @@ static int pack_poly(int k, const vx_poly &p, HostPoly *hp, const double *chi = 
     HostStage &S = hp->st[s];
     S.blk_out = s + 1 < k ? hp->st[s + 1].blk_in : 1;
     S.outpos.assign(S.nfib, 0);
+    S.outpos_fm.assign(S.nfib, 0);
     if (s + 1 < k) {
       const HostStage &T = hp->st[s + 1];
       const int sh = key_bits(k) * (k - 2 - s);
@@ -563,6 +566,7 @@ static int pack_poly(int k, const vx_poly &p, HostPoly *hp, const double *chi = 
         const uint64_t a = S.keys[f] >> sh;
         const int32_t g = T.index.get(S.keys[f] & mask);
         S.outpos[f] = T.rowoff[a] + g;
+        S.outpos_fm[f] = T.fiboff[g] + (int32_t)a;
       }
     }
   }
@@ -809,8 +813,8 @@ static int system_create_impl(const vx_poly *F, int32_t npoly, const double *con
   } else {
     for (int f = 0; f < npoly; ++f) VX_CHECK(pack_poly(k, F[f], &hp[f], chi ? chi[f] : nullptr));
   }
-  // one device allocation: per polynomial the two coefficient blocks, then per stage the
-  // row offsets, fibre lengths and output positions
+  // one device allocation: per polynomial the coefficient blocks, then per stage the row
+  // offsets, fibre lengths, output positions, fibre-major offsets and output positions
   auto al = [](size_t x) { return (x + 255) & ~(size_t)255; };
   size_t bytes = 0;
   for (int f = 0; f < npoly; ++f) {
@@ -818,7 +822,7 @@ static int system_create_impl(const vx_poly *F, int32_t npoly, const double *con
              al(hp[f].c64.size() * sizeof(float4));
     for (int s = 0; s < k; ++s) {
       const HostStage &S = hp[f].st[s];
-      bytes += al((S.maxlen + 1) * 4) + 2 * al((size_t)S.nfib * 4);
+      bytes += al((S.maxlen + 1) * 4) + 3 * al((size_t)S.nfib * 4) + al(((size_t)S.nfib + 1) * 4);
     }
   }
   // large systems are staged in a pinned buffer from the pool (the upload then runs at the
@@ -892,6 +896,8 @@ static int system_create_impl(const vx_poly *F, int32_t npoly, const double *con
       D.rowoff = (const int32_t *)put(S.rowoff.data(), (S.maxlen + 1) * 4);
       D.fiblen = (const int32_t *)put(S.fiblen.data(), (size_t)S.nfib * 4);
       D.outpos = (const int32_t *)put(S.outpos.data(), (size_t)S.nfib * 4);
+      D.fiboff = (const int32_t *)put(S.fiboff.data(), ((size_t)S.nfib + 1) * 4);
+      D.outpos_fm = (const int32_t *)put(S.outpos_fm.data(), (size_t)S.nfib * 4);
       sys->M[(size_t)f * (k + 1) + s2] = S.blk_in;
     }
   }

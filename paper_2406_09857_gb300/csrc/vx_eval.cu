@@ -433,12 +433,60 @@ __global__ void __launch_bounds__(kThreads)
                     out_nstride, nnodes, w % nchunk, (int)(w / nchunk), G, g);
 }
 
-// Stage d (1 <= d < k-1) with the parent's block in shared memory.  CTA b takes parent
-// p = b / G and fibres g, g+G, ... (g = b % G) for all of p's children (the CSF child range
-// ptr[p] .. ptr[p+1]-1, blockDim at a time, one child per thread).  The parent's node-major
-// block is one contiguous range, brought in by TMA bulk copies (cp.async.bulk, completion on
-// an mbarrier) while the row offsets are loaded; every Horner step then reads shared memory
-// at an address common to the whole CTA (a broadcast).
+// Stage d (1 <= d < k-1) with the parent's block in shared memory.  The block is fibre-major
+// (StageDev::fiboff), and CTA b takes parent p = b / G and the fibres of group g = b % G, a
+// run of consecutive fibres holding about 1/G of the block's entries (stage_group), for all of
+// p's children (the CSF child range ptr[p] .. ptr[p+1]-1, blockDim at a time, one child per
+// thread).  The group's entries are one contiguous range, brought in by a TMA bulk copy
+// (cp.async.bulk, completion on an mbarrier), so a CTA holds only its share of the block; every
+// Horner step then reads consecutive shared-memory entries at an address common to the whole
+// CTA (a broadcast).
+//
+// The fibres [fb, fe) of group g of G: those whose first entry lies in [g T / G, (g+1) T / G)
+// (T = blk_in; fibres are not split), and the entry range [c_lo, c_hi) to copy: [fiboff[fb],
+// fiboff[fe]) widened to 16-byte boundaries (entries of 8 bytes pair up; blk_in is even then).
+struct StageGroup {
+  int fb, fe;
+  int64_t c_lo, c_hi;
+};
+
+__device__ __forceinline__ int fibre_at_or_after(const int32_t *__restrict__ fiboff, int nfib,
+                                                 int64_t e) {
+  int lo = 0, hi = nfib;  // the first fibre f with fiboff[f] >= e (nfib if none)
+  while (lo < hi) {
+    const int mid = (lo + hi) >> 1;
+    if ((int64_t)__ldg(fiboff + mid) < e) lo = mid + 1;
+    else hi = mid;
+  }
+  return lo;
+}
+
+template <int ESZ>
+__device__ __forceinline__ StageGroup stage_group(const StageDev &st, int grp, int G) {
+  StageGroup r;
+  r.fb = fibre_at_or_after(st.fiboff, st.nfib, (int64_t)grp * st.blk_in / G);
+  r.fe = grp + 1 == G ? st.nfib : fibre_at_or_after(st.fiboff, st.nfib, (int64_t)(grp + 1) * st.blk_in / G);
+  constexpr int per = 16 / ESZ;  // entries per 16 bytes
+  r.c_lo = (int64_t)__ldg(st.fiboff + r.fb) / per * per;
+  r.c_hi = ((int64_t)__ldg(st.fiboff + r.fe) + per - 1) / per * per;
+  return r;
+}
+
+// One thread: the bulk copy of entries [c_lo, c_hi) of parent p's block into s_blk.
+template <class V>
+__device__ __forceinline__ void stage_group_copy(const V *in, int64_t p, int64_t blk,
+                                                 const StageGroup &r, uint64_t *bar, V *s_blk) {
+  mbar_init(bar, 1);
+  const uint64_t bytes = (uint64_t)(r.c_hi - r.c_lo) * sizeof(V);
+  mbar_arrive_expect_tx(bar, (uint32_t)bytes);
+  const char *src = reinterpret_cast<const char *>(in + p * blk + r.c_lo);
+  char *dst = reinterpret_cast<char *>(s_blk);
+  for (uint64_t o = 0; o < bytes; o += 32768) {
+    const uint32_t n = (uint32_t)(bytes - o < 32768 ? bytes - o : 32768);
+    bulk_copy_g2s(dst + o, src + o, n, bar);
+  }
+}
+
 template <class AR>
 __global__ void __launch_bounds__(512)
     k_stage_tma(const StageDev st, const int32_t *__restrict__ lab,
@@ -448,23 +496,12 @@ __global__ void __launch_bounds__(512)
   using V = typename AR::V;
   extern __shared__ __align__(128) unsigned char smem[];
   uint64_t *bar = reinterpret_cast<uint64_t *>(smem);
-  int32_t *s_rowoff = reinterpret_cast<int32_t *>(smem + 128);
-  V *s_blk = reinterpret_cast<V *>(smem + 128 + ((st.maxlen + 1) * 4 + 127) / 128 * 128);
+  V *s_blk = reinterpret_cast<V *>(smem + 128);
   const int64_t p = blockIdx.x / G;
-  const int grp = (int)(blockIdx.x % G);
+  const StageGroup r = stage_group<(int)sizeof(V)>(st, (int)(blockIdx.x % G), G);
+  if (r.fb >= r.fe) return;  // an empty group (the same for the whole CTA)
   const int64_t c0 = __ldg(pptr + p), c1 = __ldg(pptr + p + 1);
-  if (threadIdx.x == 0) {
-    mbar_init(bar, 1);
-    const uint64_t bytes = (uint64_t)st.blk_in * sizeof(V);
-    mbar_arrive_expect_tx(bar, (uint32_t)bytes);
-    const char *src = reinterpret_cast<const char *>(in + p * st.blk_in);
-    char *dst = reinterpret_cast<char *>(s_blk);
-    for (uint64_t o = 0; o < bytes; o += 32768) {
-      const uint32_t n = (uint32_t)(bytes - o < 32768 ? bytes - o : 32768);
-      bulk_copy_g2s(dst + o, src + o, n, bar);
-    }
-  }
-  for (int i = threadIdx.x; i <= st.maxlen; i += blockDim.x) s_rowoff[i] = st.rowoff[i];
+  if (threadIdx.x == 0) stage_group_copy(in, p, st.blk_in, r, bar, s_blk);
   __syncthreads();
   if (!mbar_wait_bounded(bar, 0)) return;
   for (int64_t n0 = c0; n0 < c1; n0 += blockDim.x) {
@@ -473,9 +510,9 @@ __global__ void __launch_bounds__(512)
     const int64_t nd = live ? node : c1 - 1;
     const typename AR::X x = AR::box(g, __ldg(lab + nd));
     V *dst = out + node * out_nstride;
-    for (int f = grp; f < st.nfib; f += G) {
+    for (int f = r.fb; f < r.fe; ++f) {
       const int L = __ldg(st.fiblen + f);
-      const V J = horner_any<AR>(s_blk, 1, s_rowoff, f, L, x);
+      const V J = horner1_any<AR>(s_blk + (__ldg(st.fiboff + f) - r.c_lo), 1, L, x);
       if (live) dst[(int64_t)__ldg(st.outpos + f) * out_estride] = AR::store(J);
     }
   }
@@ -1042,7 +1079,11 @@ __global__ void __launch_bounds__(kThreads, 6)
 }
 
 // k_stage_tma in the certified binary32 arithmetic, two children per thread: the children of
-// one parent always share it, so every warp whose boxes do not straddle 0 runs sign-free.
+// one parent always share it, so every warp whose boxes do not straddle 0 runs sign-free.  The
+// error bound advances step by step from the magnitudes of the partial values (A32C::step's
+// recursion): the summed bound of the leaves (leaf_bform), applied to the much longer chains
+// of the stages, widened the binary64 band of the curve's last level by 44% and cost more in
+// binary64 re-evaluation than it saved here.
 __global__ void __launch_bounds__(512)
     k_stage_tma_c(const StageDev st, const int32_t *__restrict__ lab,
                   const int32_t *__restrict__ pptr, const float4 *__restrict__ in,
@@ -1050,23 +1091,12 @@ __global__ void __launch_bounds__(512)
                   AxisGrid g) {
   extern __shared__ __align__(128) unsigned char smem[];
   uint64_t *bar = reinterpret_cast<uint64_t *>(smem);
-  int32_t *s_rowoff = reinterpret_cast<int32_t *>(smem + 128);
-  float4 *s_blk = reinterpret_cast<float4 *>(smem + 128 + ((st.maxlen + 1) * 4 + 127) / 128 * 128);
+  float4 *s_blk = reinterpret_cast<float4 *>(smem + 128);
   const int64_t p = blockIdx.x / G;
-  const int grp = (int)(blockIdx.x % G);
+  const StageGroup r = stage_group<16>(st, (int)(blockIdx.x % G), G);
+  if (r.fb >= r.fe) return;  // an empty group (the same for the whole CTA)
   const int64_t c0 = __ldg(pptr + p), c1 = __ldg(pptr + p + 1);
-  if (threadIdx.x == 0) {
-    mbar_init(bar, 1);
-    const uint64_t bytes = (uint64_t)st.blk_in * sizeof(float4);
-    mbar_arrive_expect_tx(bar, (uint32_t)bytes);
-    const char *src = reinterpret_cast<const char *>(in + p * st.blk_in);
-    char *dst = reinterpret_cast<char *>(s_blk);
-    for (uint64_t o = 0; o < bytes; o += 32768) {
-      const uint32_t n = (uint32_t)(bytes - o < 32768 ? bytes - o : 32768);
-      bulk_copy_g2s(dst + o, src + o, n, bar);
-    }
-  }
-  for (int i = threadIdx.x; i <= st.maxlen; i += blockDim.x) s_rowoff[i] = st.rowoff[i];
+  if (threadIdx.x == 0) stage_group_copy(in, p, st.blk_in, r, bar, s_blk);
   __syncthreads();
   if (!mbar_wait_bounded(bar, 0)) return;
   for (int64_t n0 = c0; n0 < c1; n0 += 2 * (int64_t)blockDim.x) {
@@ -1078,18 +1108,19 @@ __global__ void __launch_bounds__(512)
     if (__all_sync(0xffffffffu, fast)) {
       const YPair yp = ypair(yleaf(x0), yleaf(x1));
       const int ws = warp_sign(yp);
-      for (int f = grp; f < st.nfib; f += G) {
+      for (int f = r.fb; f < r.fe; ++f) {
         const int L = __ldg(st.fiblen + f);
-        float4 K0, K1;
+        const float4 *const b[2] = {s_blk + (__ldg(st.fiboff + f) - r.c_lo), nullptr};
+        float4 K0[2], K1[2];
         if (ws > 0)
-          horner_y2_fibre<1>(s_blk, 1, s_rowoff, f, L, yp, K0, K1);
+          horner_y2<1, 1>(b, L, yp, K0, K1);
         else if (ws < 0)
-          horner_y2_fibre<-1>(s_blk, 1, s_rowoff, f, L, yp, K0, K1);
+          horner_y2<1, -1>(b, L, yp, K0, K1);
         else
-          horner_y2_fibre<0>(s_blk, 1, s_rowoff, f, L, yp, K0, K1);
+          horner_y2<1, 0>(b, L, yp, K0, K1);
         const int64_t o = (int64_t)__ldg(st.outpos + f) * out_estride;
-        if (live) out[i0 * out_nstride + o] = A32C::store(K0);
-        if (two) out[i1 * out_nstride + o] = A32C::store(K1);
+        if (live) out[i0 * out_nstride + o] = A32C::store(K0[0]);
+        if (two) out[i1 * out_nstride + o] = A32C::store(K1[0]);
       }
     } else {
 #pragma unroll 1
@@ -1097,9 +1128,9 @@ __global__ void __launch_bounds__(512)
         const A32C::X &x = c == 0 ? x0 : x1;
         const bool wr = c == 0 ? live : two;
         const int64_t node = c == 0 ? i0 : i1;
-        for (int f = grp; f < st.nfib; f += G) {
+        for (int f = r.fb; f < r.fe; ++f) {
           const int L = __ldg(st.fiblen + f);
-          const float4 J = horner_any<A32C>(s_blk, 1, s_rowoff, f, L, x);
+          const float4 J = horner1_any<A32C>(s_blk + (__ldg(st.fiboff + f) - r.c_lo), 1, L, x);
           if (wr) out[node * out_nstride + (int64_t)__ldg(st.outpos + f) * out_estride] = A32C::store(J);
         }
       }
@@ -1478,6 +1509,8 @@ int leaf_pair_grid(int64_t leaves) {
 }
 
 constexpr size_t kMaxDynSmem = 200 * 1024;
+// a staged stage's CTA holds at most about this much of its parent's block (fibre groups)
+constexpr int64_t kStageGroupBytes = 48 * 1024;
 // depths with at least this many nodes, or this many multiply-adds per node, run the
 // certified stage two nodes per thread
 constexpr int64_t kPairNodes = 65536;
@@ -1651,23 +1684,20 @@ int eval_level_t(const SysDev &sys, const CsfView &c, const LevelGrid &grid, dou
     // stage d (1 <= d < k-1) stages its parents' blocks by TMA when the depth has enough
     // nodes to fill the GPU with 128-node CTAs and two parent blocks fit in shared memory
     bool tma[VX_KMAX] = {false};
-    size_t tma_smem[VX_KMAX] = {0};
     for (int d = 1; d + 1 < k; ++d) {
       const StageDev &st = sys.p[f].st[d];
-      const size_t sm = 128 + ((size_t)(st.maxlen + 1) * 4 + 127) / 128 * 128 +
-                        (size_t)st.blk_in * sizeof(V);
       // cp.async.bulk needs 16-byte aligned source and size: every parent block must start on
-      // a 16-byte boundary (the buffer itself is 256-byte aligned)
+      // a 16-byte boundary (the buffer itself is 256-byte aligned), and a group's range widened
+      // to 16-byte boundaries must stay inside its block
       const bool aligned = (st.blk_in * (int64_t)sizeof(V)) % 16 == 0 &&
                            (reinterpret_cast<uintptr_t>(buf[f][d - 1]) & 15u) == 0;
-      if (aligned && c.N[d] >= (int64_t)sm_count() * 4 * kThreads && c.N[d] >= 128 * c.N[d - 1] &&
-          sm <= kMaxDynSmem) {
+      if (aligned && c.N[d] >= (int64_t)sm_count() * 4 * kThreads && c.N[d] >= 128 * c.N[d - 1])
         tma[d] = true;
-        tma_smem[d] = sm;
-      }
     }
     for (int d = 0; d + 1 < k && rc == VX_OK; ++d) {
-      const StageDev &st = sys.p[f].st[d];
+      // a stage whose consumer stages its parents' blocks writes them fibre-major
+      StageDev st = sys.p[f].st[d];
+      if (tma[d + 1]) st.outpos = st.outpos_fm;
       const int64_t w = c.N[d] * (st.blk_in - st.nfib);
       madds += w;
       // node-major output when the consumer is the leaf stage or a TMA-staged stage
@@ -1684,31 +1714,44 @@ int eval_level_t(const SysDev &sys, const CsfView &c, const LevelGrid &grid, dou
                                  (int)kMaxDynSmem) != cudaSuccess ||
             cudaFuncSetAttribute(k_stage_tma_c, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  (int)kMaxDynSmem) != cudaSuccess) {
-          set_error("cudaFuncSetAttribute(shared memory %zu) failed", tma_smem[d]);
+          set_error("cudaFuncSetAttribute(shared memory %zu) failed", kMaxDynSmem);
           rc = VX_ECUDA;
           break;
         }
-        // one CTA per (parent, fibre group), threads ~ the average number of children.
+        // one CTA per (parent, fibre group), threads ~ the average number of children; the
+        // groups are at least enough for a CTA's share of the block to stay within
+        // kStageGroupBytes (several CTAs per SM) and for the launch to fill the GPU.
         // Variants: 0 the heuristic (two children per thread in the certified binary32
         // arithmetic), 1 one child per thread, 2 twice the fibre groups, 3 half the threads
         const int64_t np = c.N[d - 1];
         const int64_t avg = c.N[d] / np;
         const int threads0 = avg >= 512 ? 512 : (avg >= 256 ? 256 : 128);
-        int64_t G0 = ((int64_t)sm_count() * 8 + np - 1) / np;
+        const int64_t gsm = ((int64_t)(st.blk_in * sizeof(V)) + kStageGroupBytes - 1) / kStageGroupBytes;
+        int64_t G0 = std::max<int64_t>(((int64_t)sm_count() * 8 + np - 1) / np, gsm);
         if (G0 > st.nfib) G0 = st.nfib;
         if (G0 < 1) G0 = 1;
+        // a group holds fewer than blk_in / G + maxlen entries, plus one at each end for the
+        // 16-byte widening
+        auto smem_of = [&](int64_t G) {
+          return (size_t)128 + (size_t)((st.blk_in + G - 1) / G + st.maxlen + 2) * sizeof(V);
+        };
         auto launch = [&](int v) -> int {
           int threads = threads0;
           int64_t G = G0;
           if (v == 2) G = std::min<int64_t>(st.nfib, 2 * G0);
           if (v == 3) threads = std::max(128, threads0 / 2);
+          const size_t sm = smem_of(G);
+          if (sm > kMaxDynSmem) {
+            set_error("a stage's fibre group needs %zu bytes of shared memory", sm);
+            return VX_EINVAL;
+          }
           const bool two = std::is_same<AR, A32C>::value && v != 1;
           if (two)
-            k_stage_tma_c<<<(unsigned)(np * G), threads, tma_smem[d], s>>>(
+            k_stage_tma_c<<<(unsigned)(np * G), threads, sm, s>>>(
                 st, c.lab[d], c.ptr[d - 1], (const float4 *)in, (float4 *)buf[f][d], oe, on,
                 (int)G, pg.ax[d]);
           else
-            k_stage_tma<AR><<<(unsigned)(np * G), threads, tma_smem[d], s>>>(
+            k_stage_tma<AR><<<(unsigned)(np * G), threads, sm, s>>>(
                 st, c.lab[d], c.ptr[d - 1], in, buf[f][d], oe, on, (int)G, pg.ax[d]);
           note_launch();
           VX_LAUNCH_CHECK();

@@ -56,13 +56,19 @@ void dfree(void *p, cudaStream_t s);
 // on consecutive fibres read consecutive addresses at every Horner step.  The value of fibre
 // f is written at outpos[f] of the next stage's input block.
 // ---------------------------------------------------------------------------------------
+// A stage whose parent blocks are staged in shared memory (k_stage_tma*) reads its input
+// fibre-major instead: fibre f's entries a = 0..len-1 at fiboff[f] + a, so that a Horner walks
+// consecutive entries and a group of consecutive fibres is one contiguous range; its producer
+// then writes fibre f's value at outpos_fm[f] instead of outpos[f].
 struct StageDev {
   int32_t nfib, maxlen;
   int64_t blk_in;   // entries of one input block of this stage
   int64_t blk_out;  // entries of one output block (= next stage's blk_in; 1 at the last stage)
-  const int32_t *rowoff;  // [maxlen + 1]
-  const int32_t *fiblen;  // [nfib]
-  const int32_t *outpos;  // [nfib] (unused at the last stage)
+  const int32_t *rowoff;     // [maxlen + 1]
+  const int32_t *fiblen;     // [nfib]
+  const int32_t *outpos;     // [nfib] (unused at the last stage)
+  const int32_t *fiboff;     // [nfib + 1] fibre-major offsets of this stage's input
+  const int32_t *outpos_fm;  // [nfib] position in the next stage's fibre-major input
 };
 
 struct PolyDev {

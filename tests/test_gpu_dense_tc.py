@@ -199,3 +199,65 @@ def test_prefilter_graph_replay(vx):
     k2, n2 = plan.level_keep(vx.make_opts(vx.FP32))
     assert n1 == n2 and torch.equal(k1, k2)
     plan.free()
+
+
+def _tensor_poly(d, coef_of):
+    """The full (d+1)^3 tensor with coefficient coef_of(a1, a2, a3, index)."""
+    g = np.meshgrid(*[np.arange(d + 1, dtype=np.int32)] * 3, indexing="ij")
+    e = np.stack([x.reshape(-1) for x in g], axis=1)
+    return e, coef_of(e)
+
+
+def _adversarial(name):
+    d = 128
+    st = synth.Stream({"alternating": 601, "spread": 602, "equal-random-signs": 603}[name])
+    if name == "alternating":  # equal magnitudes, signs (-1)^|a|: heavy cancellation near x = 1
+        return _tensor_poly(d, lambda e: np.where(e.sum(axis=1) % 2 == 0, 1.0, -1.0))
+    if name == "spread":  # magnitudes 2^u, u uniform in [-60, 60], random signs
+        def coef(e):
+            u = st.uniform_int(-60, 60, e.shape[0]).astype(np.float64)
+            s = np.where(st.uniform_int(0, 1, e.shape[0]) == 0, 1.0, -1.0)
+            return s * np.ldexp(1.0, u.astype(np.int64))
+        return _tensor_poly(d, coef)
+    def coef(e):  # equal magnitudes, random signs
+        return np.where(st.uniform_int(0, 1, e.shape[0]) == 0, 1.0, -1.0)
+    return _tensor_poly(d, coef)
+
+
+@pytest.mark.parametrize("name", ["alternating", "spread", "equal-random-signs"])
+def test_tensor_core_enclosure_at_its_worst_cases(vx, name):
+    """Property 1's contractions on the tensor cores at degree 128 (an inner dimension of 136)
+    with coefficients chosen against the accumulation model of the TF32 midpoints: equal
+    magnitudes with alternating or random signs (cancellation: midpoints far below the sums
+    of |products|) and magnitudes spread over 2^-60 .. 2^60.  On sampled boxes the device's
+    <mid, rad> contains the oracle's margin-free mode-wise power form, and the midpoint error
+    uses less than half of the radius the device adds for rounding (|mid - m| <= (rad - r) / 2):
+    the margins of the model hold with a factor 2 to spare."""
+    import torch
+
+    polys = [_adversarial(name)]
+    dom, level = synth.cube(3), 5
+    plan = vx.DensePlan(vx.System(polys), level, dom)
+    mid, rad = plan.values(0)
+    torch.cuda.synchronize()
+    mid = mid.double().cpu().numpy()
+    rad = rad.double().cpu().numpy()
+    t = _all_tuples(level)
+    sel = np.unique(synth.Stream(17).uniform_int(0, t.shape[0] - 1, 300))
+    # the boxes next to x = (1, 1, 1) and x = (-1, -1, -1), where the cancellation is largest
+    side = 1 << level
+    corner = [(side - 1 - i) * side * side + (side - 1 - j) * side + (side - 1 - k)
+              for i in range(3) for j in range(3) for k in range(3)]
+    sel = np.unique(np.concatenate([sel, corner, np.arange(27)]))
+    t, mid, rad = t[sel], mid[sel], rad[sel]
+    mo, ro = oracle.dense_powerform(polys[0], dom, level, t)
+    assert np.all(np.isfinite(mid)) and np.all(np.isfinite(rad))
+    slack = 1e-12 * (np.abs(mo) + ro) + 1e-300
+    assert np.all(mid - rad <= mo - ro + slack), "device enclosure misses the lower end"
+    assert np.all(mo + ro - slack <= mid + rad), "device enclosure misses the upper end"
+    extra = rad - ro
+    used = np.abs(mid - mo) / np.maximum(extra, 1e-300)
+    print("%s: largest share of the rounding radius used by the midpoint error %.3g "
+          "(median %.3g)" % (name, used.max(), np.median(used)))
+    assert used.max() < 0.5
+    plan.free()

@@ -338,6 +338,87 @@ def bench_dense_tc(vx, torch, stream, flush, sysv, s, d, level, reps, keep64, be
     return res
 
 
+def _lineage_job(args):
+    """One oracle lineage in a worker process (spawned): (box evaluations, seconds)."""
+    polys, domain, depth, x1 = args
+    t0 = time.perf_counter()
+    n = oracle_lineage(polys, domain, depth, x1)
+    return n, time.perf_counter() - t0
+
+
+def oracle_parallel(polys, domain, depth, nlineages: int, seed: int, procs: int):
+    """The oracle on ``nlineages`` random finest x1-slab lineages spread over ``procs`` spawned
+    worker processes (the x1 slabs are independent, the parallel form of the oracle run over
+    depth-1 nodes): box evaluations per second of wall time, and the processes used."""
+    import multiprocessing as mp
+
+    from paper_2406_09857_gb300 import synth
+
+    st = synth.Stream(seed)
+    side = 1 << depth
+    jobs = [(polys, domain, depth, int(x)) for x in st.uniform_int(0, side - 1, nlineages)]
+    ctx = mp.get_context("spawn")
+    with ctx.Pool(procs) as pool:
+        pool.map(_lineage_job, jobs[:procs])  # workers started and the oracle loaded
+        t0 = time.perf_counter()
+        res = pool.map(_lineage_job, jobs, chunksize=1)
+        wall = time.perf_counter() - t0
+    boxes = sum(r[0] for r in res)
+    return boxes / wall, boxes, wall
+
+
+def bench_configs(vx, synth, torch, stream, cpu: bool, cpu_budget: float):
+    """Configs 1-3 (plain, surface, curve) end to end with the system resident: box-evals/s
+    and enclosure ms in certified binary32 (band re-decided at the last level) and binary64
+    (median of 3 after a warm-up), beside the CPU oracle on random finest x1-slab lineages,
+    one process and one per core (a reported baseline)."""
+    out = {}
+    ncores = os.cpu_count() or 1
+    for name, make in (("plain", synth.plain), ("surface", synth.surface), ("curve", synth.curve)):
+        s = make()
+        sysv = vx.System(s.polys)
+        e = {"workload": s.name, "depth": s.depth}
+        for mode_name, mode, rl in (("fp32", vx.FP32, True), ("fp64", vx.FP64, False)):
+            o = vx.make_opts(mode, recheck_last=rl)
+            vx.enclose_system(sysv, s.domain, s.depth, o, stream).free()
+            ms, evals = [], 0
+            for _ in range(3):
+                e0 = torch.cuda.Event(enable_timing=True)
+                e1 = torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                r = vx.enclose_system(sysv, s.domain, s.depth, o, stream)
+                e1.record(stream)
+                e1.synchronize()
+                ms.append(e0.elapsed_time(e1))
+                st = r.stats()
+                evals = int(st["tested"].sum()) if mode == vx.FP64 else evals
+                if mode == vx.FP64:
+                    e["boxes"] = int(st["kept"][-1])
+                r.free()
+            e[mode_name] = {"ms_median": statistics.median(ms), "ms_min": min(ms)}
+        # box evaluations of the exact subdivision (binary64's levels)
+        e["box_evals"] = evals
+        for mode_name in ("fp32", "fp64"):
+            e[mode_name]["box_evals_per_s"] = evals / (e[mode_name]["ms_median"] * 1e-3)
+        e["fp32_speedup_vs_fp64"] = e["fp64"]["ms_median"] / e["fp32"]["ms_median"]
+        if cpu:
+            v1, b1, t1, d1 = oracle_sample(s.polys, s.domain, s.depth, cpu_budget / 3, seed=13)
+            nl = 4 * ncores
+            vp, bp, tp = oracle_parallel(s.polys, s.domain, s.depth, nl, seed=17, procs=ncores)
+            e["cpu_oracle"] = {
+                "one_process": {"box_evals_per_s": v1, "box_evals": b1, "s": t1, "cores": 1},
+                "all_cores": {"box_evals_per_s": vp, "box_evals": bp, "s": tp, "cores": ncores,
+                              "lineages": nl},
+                "sample": "Algorithm 3 along random finest x1-slab lineages (every level's boxes "
+                          "of each slab), binary64 directed rounding; the all-cores run spreads "
+                          "the lineages over spawned processes, one per core",
+                "gpu_fp32_over_all_cores": e["fp32"]["box_evals_per_s"] / vp,
+            }
+        sysv.free()
+        out[name] = e
+    return out
+
+
 def bench_precision(vx, synth, torch):
     """Per config (plain, surface, curve): excess boxes of binary32 midpoint-radius over
     binary64 at every level (no binary64 final level), and the radius inflation on the
@@ -564,33 +645,44 @@ def bench_batch(vx, synth, torch, workers=16):
 
 
 def run_reference(args):
+    """The CPU oracle as the reference arm: each step runs Algorithm 3 along one random finest
+    x1-slab lineage per host core, the lineages spread over spawned worker processes (one per
+    core); value = box evaluations / wall time of the steps."""
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
     if rank != 0:
         return 0
+    import multiprocessing as mp
+
     import oracle
     from paper_2406_09857_gb300 import synth
 
     oracle.build()
     s = synth.curve()
-    rates, times = [], []
+    ncores = os.cpu_count() or 1
+    st = synth.Stream(1000)
+    side = 1 << s.depth
     total_boxes, total_s = 0, 0.0
-    for i in range(args.warmup + args.steps):
-        v, b, t, desc = oracle_sample(s.polys, s.domain, s.depth, budget_s=0.0, seed=1000 + i)
-        if i >= args.warmup:
-            rates.append(v)
-            times.append(t)
-            total_boxes += b
-            total_s += t
+    with mp.get_context("spawn").Pool(ncores) as pool:
+        for i in range(args.warmup + args.steps):
+            jobs = [(s.polys, s.domain, s.depth, int(x))
+                    for x in st.uniform_int(0, side - 1, ncores)]
+            t0 = time.perf_counter()
+            res = pool.map(_lineage_job, jobs, chunksize=1)
+            t = time.perf_counter() - t0
+            if i >= args.warmup:
+                total_boxes += sum(r[0] for r in res)
+                total_s += t
     value = total_boxes / total_s
+    sample = ("each step: Algorithm 3 along %d random finest x1-slab lineages (every level's boxes "
+              "of each slab), one per host core, in %d spawned processes" % (ncores, ncores))
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT,
             "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": 1e3 * total_s / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": config_dict(1, "CPU oracle, binary64 directed rounding"),
-            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
-                             "sample": "each step: " + desc.split(": ", 1)[1].split(",")[0]
-                             + " (one random finest x1-slab lineage per step)"},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": ncores, "kind": "oracle",
+                             "sample": sample},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
@@ -845,6 +937,8 @@ def run_gpu(args):
         extra["dense_sweep"] = bench_dense_sweep(vx, synth, torch, stream, flush)
         extra["batch"] = bench_batch(vx, synth, torch)
         extra["precision"] = bench_precision(vx, synth, torch)
+        extra["configs"] = bench_configs(vx, synth, torch, stream, not args.no_cpu,
+                                         args.cpu_budget)
         extra["table1"] = bench_table1(vx, synth, torch, stream)
         extra["applications"] = bench_applications(vx, synth, torch, stream)
 
@@ -887,6 +981,7 @@ def run_gpu(args):
             "same_result_as_fp64": bool(same),
             "excess_boxes": 0.0 if same else None,
             "recheck_boxes_per_step": int(st32["recheck"].sum()),
+            "binary64_recheck_boxes_per_step": int(st32["recheck64"].sum()),
             "roofline": roof32,
             "roofline_by_kind": by_kind32,
             "cpu_baseline": cpu,

@@ -408,13 +408,17 @@ int vx_result_box_codes(vx_result *res, int64_t *n, int32_t *code_bytes, const v
 /* The survivors as a device CSF owned by the result (valid until vx_result_free). */
 int vx_result_csf(const vx_result *res, const vx_csf **csf);
 /* Per-level statistics, levels 0..depth: h_tested[l] = |S_l| boxes evaluated, h_kept[l]
- * survivors, h_nodes[l*k + j-1] = N_j(S_l), h_recheck[l] = boxes re-evaluated in VX_FP64
- * (VX_FP32_MIDRAD with fp64_recheck), h_madds[l] = interval multiply-adds of the level
- * (Theorem 1's count: sum over polynomials and depths j of N_j (M_{j-1} - M_j)), plus those of
- * the binary64 re-evaluations.
+ * survivors, h_nodes[l*k + j-1] = N_j(S_l), h_recheck[l] = boxes re-decided beyond the level's
+ * first arithmetic (VX_FP32: the binary32 error band, decided by the float-pair tier and what
+ * it leaves by VX_FP64; VX_FP32_MIDRAD with fp64_recheck: the tight boxes, in VX_FP64),
+ * h_madds[l] = interval multiply-adds of the level (Theorem 1's count: sum over polynomials
+ * and depths j of N_j (M_{j-1} - M_j)), plus those of the re-evaluations.
  * Any pointer may be NULL; *nlevels = depth + 1. */
 int vx_result_stats(const vx_result *res, int32_t *nlevels, int64_t *h_tested, int64_t *h_kept,
                     int64_t *h_nodes, int64_t *h_recheck, int64_t *h_madds);
+/* Of the boxes h_recheck counts, those decided in VX_FP64, per level 0..depth (VX_FP32: the
+ * boxes the float-pair tier leaves undecided; otherwise all of them). */
+int vx_result_recheck64(const vx_result *res, int64_t *h_per_level);
 /* Kernel timing (opts.timing != 0): for kernel kind i < *nkinds: h_ms[i] summed CUDA-event
  * time, h_launches[i] launches, h_work[i] algorithmic work (interval multiply-adds for the
  * evaluation kernels, bytes for the integer kernels).  vx_kernel_kind_name(i) names kind i. */

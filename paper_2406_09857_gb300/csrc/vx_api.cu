@@ -153,7 +153,8 @@ void Timer::release() {
 static const char *kKindNames[KK_COUNT] = {
     "stage0_fp64",  "stagej_fp64",  "leaf_fp64", "stage0_midrad", "stagej_midrad",
     "leaf_midrad",  "stage0_fp32",  "stagej_fp32", "leaf_fp32",   "csf_build",
-    "prune_scan",   "split",        "compact",     "recheck_select"};
+    "prune_scan",   "split",        "compact",     "recheck_select", "stage0_pair",
+    "stagej_pair",  "leaf_pair"};
 
 // ---------------------------------------------------------------------------------------
 // grid levels: box t on axis i is [lo + t w, lo + (t+1) w], w = (hi - lo) / 2^level.
@@ -311,11 +312,24 @@ static uint64_t suffix_key(const int32_t *e, int from, int k) {
 //    binary64 path uses as they are); the 2^-24 term keeps E >= 2^-24 max(|RN(lo)|,
 //    |RN(hi)|), which the error recursion of the evaluation kernels relies on.  E is stored
 //    twice (.z and .w): a register pair for the kernels' paired steps.
+//  - float pairs (eval_level_pair): each end c as h = RN(c), l = RN(c - h) (c - (h + l) is
+//    exact in binary64), stored (lo_h, lo_l, -hi_h, -hi_l), with the bound RU(max of the two
+//    representation errors) + 2^-148; a non-finite pair gets an infinite bound.
 __global__ void k_encode_coefs(const double2 *__restrict__ c64, int64_t n, float2 *__restrict__ c32,
-                               float4 *__restrict__ c32c) {
+                               float4 *__restrict__ c32c, float4 *__restrict__ cp,
+                               float *__restrict__ ep) {
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
     const double lo = c64[i].x, hi = c64[i].y;
+    {
+      const float lh = __double2float_rn(lo), hh = __double2float_rn(hi);
+      const float ll = __double2float_rn(lo - (double)lh), hl = __double2float_rn(hi - (double)hh);
+      const double d = fmax(fabs((lo - (double)lh) - (double)ll), fabs((hi - (double)hh) - (double)hl));
+      cp[i] = make_float4(lh, ll, -hh, -hl);
+      ep[i] = (isfinite(lh) && isfinite(hh) && isfinite(ll) && isfinite(hl))
+                  ? __double2float_ru(__dadd_ru(d, 0x1p-148))
+                  : INFINITY;
+    }
     {
       const double mid = lo == hi ? lo : __dadd_rn(__dmul_rn(0.5, lo), __dmul_rn(0.5, hi));
       const float m = __double2float_rn(mid);
@@ -604,14 +618,95 @@ namespace vx {
 // those inside the error band; VX_FP32_MIDRAD with recheck: the tight ones); flagged boxes are
 // gathered into a tree of their own, evaluated in binary64 and their decisions scattered back.
 // defer (VX_FP32): no re-evaluation, the band's boxes are kept.
+// Certified binary32 levels whose band is re-decided now go through the float-pair tier.
+static bool flagged_pair_tier(int mode, bool defer) { return mode == VX_FP32 && !defer; }
+
+// The boxes of tree c whose flag is set, as a tree of their own (their tuples are increasing,
+// being listed in leaf order), decided in binary64; the decisions go to keep at their places.
+static int decide_flagged_fp64(const SysDev &sys, const CsfView &c, const LevelGrid &g,
+                               const uint8_t *flag, uint8_t *keep, cudaStream_t s, Timer *tm,
+                               int64_t *madds, int64_t *nsel) {
+  const int k = c.k;
+  const int64_t n = c.N[k - 1];
+  int32_t *idx = nullptr, *tup = nullptr;
+  uint8_t *subkeep = nullptr;
+  int64_t ns = 0;
+  *nsel = 0;
+  int rc = VX_OK;
+  if (tm && tm->on) rc = tm->begin(KK_RECHECK, n);
+  if (rc == VX_OK) rc = flag_indices(flag, n, s, &idx, &ns);
+  if (rc == VX_OK && tm && tm->on) {
+    tm->add_work(4 * ns);  // the selected boxes' indices written
+    rc = tm->end();
+  }
+  *nsel = ns;
+  if (rc == VX_OK && ns > 0) {
+    CsfObj sub;
+    rc = dmalloc((void **)&tup, (size_t)ns * k * 4, s);
+    if (rc == VX_OK) rc = csf_tuples_of(c, idx, ns, tup, s);
+    if (rc == VX_OK) rc = csf_build_dev(k, c.level, tup, ns, s, &sub, tm);
+    if (rc == VX_OK) rc = dmalloc((void **)&subkeep, (size_t)ns, s);
+    int64_t w2 = 0;
+    if (rc == VX_OK)
+      rc = eval_level_raw(sys, sub.v, g, ARITH_F64, nullptr, nullptr, subkeep, nullptr, 0.f, s,
+                          tm, &w2);
+    *madds += w2;
+    if (rc == VX_OK) rc = scatter_keep(idx, subkeep, ns, keep, s);
+    csf_release(&sub);
+  }
+  dfree(subkeep, s);
+  dfree(tup, s);
+  dfree(idx, s);
+  return rc;
+}
+
 static int eval_decide(const SysDev &sys, const CsfView &c, const LevelGrid &g, int mode,
                        bool midrad_recheck, float theta, double *d_lo, double *d_hi,
                        uint8_t *keep, cudaStream_t s, Timer *tm, int64_t *madds,
-                       int64_t *nrecheck, bool defer = false) {
+                       int64_t *nrecheck, bool defer = false, int64_t *nrecheck64 = nullptr) {
   const int k = c.k;
   const int64_t n = c.N[k - 1];
   *madds = 0;
   *nrecheck = 0;
+  if (nrecheck64) *nrecheck64 = 0;
+  if (flagged_pair_tier(mode, defer) && n > 0) {
+    // certified binary32, then the float-pair tier on its error band, then binary64 on what
+    // the tier leaves undecided
+    uint8_t *flag = nullptr;
+    VX_CHECK(dmalloc((void **)&flag, (size_t)n, s));
+    int rc = eval_level_raw(sys, c, g, ARITH_F32_CERT, d_lo, d_hi, keep, flag, theta, s, tm, madds);
+    int32_t *idx = nullptr, *tup = nullptr;
+    uint8_t *subkeep = nullptr, *subflag = nullptr;
+    int64_t ns = 0;
+    if (rc == VX_OK && tm && tm->on) rc = tm->begin(KK_RECHECK, n);
+    if (rc == VX_OK) rc = flag_indices(flag, n, s, &idx, &ns);
+    if (rc == VX_OK && tm && tm->on) {
+      tm->add_work(4 * ns);
+      rc = tm->end();
+    }
+    *nrecheck = ns;
+    if (rc == VX_OK && ns > 0) {
+      CsfObj sub;
+      rc = dmalloc((void **)&tup, (size_t)ns * k * 4, s);
+      if (rc == VX_OK) rc = csf_tuples_of(c, idx, ns, tup, s);
+      if (rc == VX_OK) rc = csf_build_dev(k, c.level, tup, ns, s, &sub, tm);
+      if (rc == VX_OK) rc = dmalloc((void **)&subkeep, (size_t)ns, s);
+      if (rc == VX_OK) rc = dmalloc((void **)&subflag, (size_t)ns, s);
+      int64_t wp = 0, w64 = 0, n64 = 0;
+      if (rc == VX_OK) rc = eval_level_pair(sys, sub.v, g, subkeep, subflag, s, tm, &wp);
+      if (rc == VX_OK) rc = decide_flagged_fp64(sys, sub.v, g, subflag, subkeep, s, tm, &w64, &n64);
+      *madds += wp + w64;
+      if (nrecheck64) *nrecheck64 = n64;
+      if (rc == VX_OK) rc = scatter_keep(idx, subkeep, ns, keep, s);
+      csf_release(&sub);
+    }
+    dfree(subflag, s);
+    dfree(subkeep, s);
+    dfree(tup, s);
+    dfree(idx, s);
+    dfree(flag, s);
+    return rc;
+  }
   const bool flagged =
       (mode == VX_FP32 && !defer) || (mode == VX_FP32_MIDRAD && midrad_recheck);
   const int arith = mode == VX_FP64 ? ARITH_F64 : (mode == VX_FP32 ? ARITH_F32_CERT : ARITH_F32_MIDRAD);
@@ -685,6 +780,7 @@ struct vx_result {
   int k = 0, depth = 0;
   CsfObj fin;
   std::vector<int64_t> tested, kept, nodes, recheck, madds;
+  std::vector<int64_t> recheck64;  // of the rechecked boxes, those decided in binary64
   Timer tm;
   double elapsed_ms = 0.0;
   // the boxes on the host: a pinned buffer from the library's pool (vx_result_boxes)
@@ -819,7 +915,7 @@ static int system_create_impl(const vx_poly *F, int32_t npoly, const double *con
   size_t bytes = 0;
   for (int f = 0; f < npoly; ++f) {
     bytes += al(hp[f].c64.size() * sizeof(double2)) + al(hp[f].c64.size() * sizeof(float2)) +
-             al(hp[f].c64.size() * sizeof(float4));
+             2 * al(hp[f].c64.size() * sizeof(float4)) + al(hp[f].c64.size() * sizeof(float));
     for (int s = 0; s < k; ++s) {
       const HostStage &S = hp[f].st[s];
       bytes += al((S.maxlen + 1) * 4) + 3 * al((size_t)S.nfib * 4) + al(((size_t)S.nfib + 1) * 4);
@@ -908,6 +1004,8 @@ static int system_create_impl(const vx_poly *F, int32_t npoly, const double *con
     PolyDev &P = sys->dev.p[f];
     P.c32 = (const float2 *)reserve(hp[f].c64.size() * sizeof(float2));
     P.c32c = (const float4 *)reserve(hp[f].c64.size() * sizeof(float4));
+    P.cp = (const float4 *)reserve(hp[f].c64.size() * sizeof(float4));
+    P.ep = (const float *)reserve(hp[f].c64.size() * sizeof(float));
   }
   cudaError_t e = cudaMemcpyAsync(sys->mem, host, sys->upload_bytes, cudaMemcpyHostToDevice, s);
   for (int f = 0; f < npoly && e == cudaSuccess; ++f) {
@@ -916,7 +1014,9 @@ static int system_create_impl(const vx_poly *F, int32_t npoly, const double *con
     const int64_t nb = std::min<int64_t>((n + 255) / 256, (int64_t)sm_count() * 8);
     k_encode_coefs<<<(unsigned)nb, 256, 0, s>>>(sys->dev.p[f].c64,
                                                  n, const_cast<float2 *>(sys->dev.p[f].c32),
-                                                 const_cast<float4 *>(sys->dev.p[f].c32c));
+                                                 const_cast<float4 *>(sys->dev.p[f].c32c),
+                                                 const_cast<float4 *>(sys->dev.p[f].cp),
+                                                 const_cast<float *>(sys->dev.p[f].ep));
     note_launch();
     e = cudaGetLastError();
   }
@@ -1750,6 +1850,7 @@ static int enclose_impl(const vx_system *sys, const double *dom, int depth, cons
   R->kept.assign(depth + 1, 0);
   R->nodes.assign((size_t)(depth + 1) * k, 0);
   R->recheck.assign(depth + 1, 0);
+  R->recheck64.assign(depth + 1, 0);
   R->madds.assign(depth + 1, 0);
   R->tm.on = opts.timing != 0;
   R->tm.stream = s;
@@ -1800,7 +1901,7 @@ static int enclose_impl(const vx_system *sys, const double *dom, int depth, cons
     rc = dmalloc((void **)&keep, (size_t)std::max<int64_t>(n, 1), s);
     if (rc == VX_OK && c1_here) rc = dmalloc((void **)&inc, (size_t)n, s);
     if (rc == VX_OK) {
-      int64_t w = 0, nr = 0;
+      int64_t w = 0, nr = 0, nr64 = 0;
       if (opts.taylor_order > 0)
         rc = n > 0 ? eval_taylor_level(sys, cur.v, g, opts.taylor_order, mode, nullptr,
                                        nullptr, keep, opts.c1 == VX_C1_TAYLOR ? inc : nullptr, s,
@@ -1808,9 +1909,10 @@ static int enclose_impl(const vx_system *sys, const double *dom, int depth, cons
                    : VX_OK;
       else
         rc = eval_decide(sys->dev, cur.v, g, mode, opts.fp64_recheck != 0, theta, nullptr,
-                         nullptr, keep, s, tm, &w, &nr, opts.recheck_last != 0 && l < depth);
+                         nullptr, keep, s, tm, &w, &nr, opts.recheck_last != 0 && l < depth, &nr64);
       R->madds[l] += w;
       R->recheck[l] = nr;
+      R->recheck64[l] = mode == VX_FP32 ? nr64 : nr;
       int st = 0;
       if (rc == VX_OK) rc = take_device_status(s, &st);
       if (rc == VX_OK && st) {
@@ -2167,6 +2269,7 @@ int batch_group(const std::vector<int32_t> &ids, const vx_poly *const *systems,
     R[t]->kept.assign(D + 1, 0);
     R[t]->nodes.assign((size_t)(D + 1) * k, 0);
     R[t]->recheck.assign(D + 1, 0);
+    R[t]->recheck64.assign(D + 1, 0);
     R[t]->madds.assign(D + 1, 0);
     // an empty tree until the system finishes (a system whose boxes all go keeps it)
     int64_t N0[VX_KMAX] = {0};
@@ -2261,9 +2364,11 @@ int batch_group(const std::vector<int32_t> &ids, const vx_poly *const *systems,
       if (rc == VX_OK) rc = prune_forest(cur, flag, 0, idx, k, S, d_seg, hseg, s, sub);
       const int64_t ns = sub.c.v.N[k - 1];
       for (int t = 0; t < S && rc == VX_OK; ++t)
-        if (tdep[t] >= l)
+        if (tdep[t] >= l) {
           R[t]->recheck[l] = sub.off[(size_t)(k - 1) * (S + 1) + t + 1] -
                              sub.off[(size_t)(k - 1) * (S + 1) + t];
+          R[t]->recheck64[l] = R[t]->recheck[l];
+        }
       if (rc == VX_OK && ns > 0) {
         rc = dmalloc((void **)&subkeep, (size_t)ns, s);
         int64_t w2 = 0;
@@ -2574,6 +2679,16 @@ int vx_result_stats(const vx_result *R, int32_t *nlevels, int64_t *tested, int64
   if (nodes) std::memcpy(nodes, R->nodes.data(), (size_t)L * R->k * 8);
   if (recheck) std::memcpy(recheck, R->recheck.data(), L * 8);
   if (madds) std::memcpy(madds, R->madds.data(), L * 8);
+  return VX_OK;
+}
+
+int vx_result_recheck64(const vx_result *R, int64_t *per_level) {
+  clear_error();
+  if (!R || !per_level) {
+    set_error("vx_result_recheck64: NULL argument");
+    return VX_EINVAL;
+  }
+  std::memcpy(per_level, R->recheck64.data(), (size_t)(R->depth + 1) * 8);
   return VX_OK;
 }
 

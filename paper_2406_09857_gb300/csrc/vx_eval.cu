@@ -2274,6 +2274,270 @@ int take_device_status(cudaStream_t s, int *status) {
 }
 
 // ---------------------------------------------------------------------------------------
+// The float-pair tier, run on the boxes of the certified binary32 path's error band before
+// binary64.  Each interval end is a pair (h, l) of binary32 numbers standing for h + l with
+// |l| <= ulp(h) / 2 (about 48 bits), an interval stored as (lo_h, lo_l, -hi_h, -hi_l), and a
+// bound E on |lo_pair - lo*| + |lo64 - lo*| (the same for hi), lo* the exact interval Horner
+// value with the binary64 coefficients and lo64 what the binary64 path computes.
+//
+// One step J*Y + C on Y = [yl, yh] >= 0 (a box with x <= 0 runs Horner in y = -x on the
+// coefficients (-1)^a C_a, as the certified binary32 leaves do), per end, m the end of Y at
+// which that end's product is smallest (yl where the end is >= 0, whose sign is its h's):
+//   ph = RN(h m), pe = FMA(h, m, -ph) (the product's exact error), pl = RN(l m + pe);
+//   (sh, se) = TwoSum(ph, C_h); u = RN(se + RN(pl + C_l)); (rh, rl) = TwoSum(sh, u).
+// The min over the ends of Y of J's end times y is xmax-Lipschitz in that end, the roundings
+// (pl, RN(pl + C_l), u) stay below 2^-45 (|J| yh + |C|) together, and binary64 rounds its
+// product and sum downward (< 2^-52 of magnitudes at most |J| yh + |C| + the distances), so
+//   E' = RU(E_J xp + RU(2^-43 T + E_C (1 + 2^-40))) + 2^-145,
+//   T = max|ends of J| yh + max|ends of C|,  xp = RU(yh (1 + 2^-40)),
+// bounds the new distance (2^-145 covers the absolute errors below the normal range).  A
+// decision compares the exact sum h + l (in binary64) with E.  Boxes straddling 0 and grids
+// whose box ends are not binary32 numbers are left to binary64 (E infinite).
+// ---------------------------------------------------------------------------------------
+namespace {
+
+struct PairX {
+  float yl, yh, xp;
+  bool neg;  // the box is x <= 0: Horner runs in y = -x
+  bool ok;   // the box does not straddle 0
+};
+
+__device__ __forceinline__ PairX pair_box(const AxisGrid &g, int32_t t) {
+  PairX x;
+  const float l = __fmaf_rn((float)t, g.fw, g.flo), h = __fmaf_rn((float)t + 1.0f, g.fw, g.flo);
+  x.ok = l >= 0.f || h <= 0.f;
+  x.neg = !(l >= 0.f);
+  x.yl = x.neg ? -h : l;
+  x.yh = x.neg ? -l : h;
+  x.xp = __fmaf_ru(x.yh, 0x1p-40f, x.yh);
+  return x;
+}
+
+__device__ __forceinline__ void two_sum(float a, float b, float &s, float &e) {
+  s = __fadd_rn(a, b);
+  const float bb = __fsub_rn(s, a);
+  e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+}
+
+// the lower end of (jh + jl) * [yl, yh] + (ch + cl), yl >= 0
+__device__ __forceinline__ void pair_end(float jh, float jl, float yl, float yh, float ch,
+                                         float cl, float &rh, float &rl) {
+  const float m = jh >= 0.f ? yl : yh;
+  const float ph = __fmul_rn(jh, m);
+  const float pe = __fmaf_rn(jh, m, -ph);
+  const float pl = __fmaf_rn(jl, m, pe);
+  float sh, se;
+  two_sum(ph, ch, sh, se);
+  const float u = __fadd_rn(se, __fadd_rn(pl, cl));
+  two_sum(sh, u, rh, rl);
+}
+
+__device__ __forceinline__ float4 pair_negated(const float4 c) {
+  return make_float4(c.z, c.w, c.x, c.y);
+}
+
+__device__ __forceinline__ void pair_step(float4 &j, float &ej, const float4 &c, float ec,
+                                          const PairX &x) {
+  const float MJ = fmaxf(fabsf(j.x), fabsf(j.z)), MC = fmaxf(fabsf(c.x), fabsf(c.z));
+  float4 r;
+  pair_end(j.x, j.y, x.yl, x.yh, c.x, c.y, r.x, r.y);
+  pair_end(j.z, j.w, x.yl, x.yh, c.z, c.w, r.z, r.w);
+  const float T = __fmaf_ru(MJ, x.yh, MC);
+  float e = __fmaf_ru(ec, 0x1p-40f, ec);
+  e = __fmaf_ru(0x1p-43f, T, e);
+  e = __fmaf_ru(ej, x.xp, e);
+  ej = __fadd_ru(e, 0x1p-145f);
+  j = r;
+}
+
+// Algorithm 1 on one fibre (entry a at vb[(rowoff[a] + f) estride], its bound in eb), Horner in
+// y = -x with odd coefficients negated when the box is x <= 0 (the result is J itself).
+__device__ __forceinline__ void pair_horner(const float4 *__restrict__ vb,
+                                            const float *__restrict__ eb, int64_t estride,
+                                            const int32_t *__restrict__ rowoff, int f, int L,
+                                            const PairX &x, float4 &J, float &E) {
+  auto at = [&](int a) { return (int64_t)(__ldg(rowoff + a) + f) * estride; };
+  int64_t o = at(L - 1);
+  const float4 top = vb[o];
+  E = eb[o];
+  J = (x.neg && ((L - 1) & 1)) ? pair_negated(top) : top;
+  for (int a = L - 2; a >= 0; --a) {
+    o = at(a);
+    float4 c = vb[o];
+    const float ec = eb[o];
+    if (x.neg && (a & 1)) c = pair_negated(c);
+    pair_step(J, E, c, ec, x);
+  }
+}
+
+// 0: the binary64 path surely drops the box for this relation, 1: surely not, 2: unknown
+__device__ __forceinline__ int pair_classify(const float4 &J, float E, int rel) {
+  const double lo = (double)J.x + (double)J.y, nhi = (double)J.z + (double)J.w;  // exact
+  const double e = (double)E;
+  const bool fin = E < INFINITY && isfinite(lo) && isfinite(nhi);
+  if (!fin) return 2;
+  // lo64 lies in [lo - e, lo + e], -hi64 in [nhi - e, nhi + e]
+  const double lo_dn = __dadd_rd(lo, -e), lo_up = __dadd_ru(lo, e);
+  const double nh_dn = __dadd_rd(nhi, -e), nh_up = __dadd_ru(nhi, e);
+  switch (rel) {
+    case VX_LE: return lo_dn > 0.0 ? 0 : (lo_up <= 0.0 ? 1 : 2);    // drop iff lo64 > 0
+    case VX_GE: return nh_dn > 0.0 ? 0 : (nh_up <= 0.0 ? 1 : 2);    // drop iff hi64 < 0
+    case VX_LT: return lo_dn >= 0.0 ? 0 : (lo_up < 0.0 ? 1 : 2);    // drop iff lo64 >= 0
+    case VX_GT: return nh_dn >= 0.0 ? 0 : (nh_up < 0.0 ? 1 : 2);    // drop iff hi64 <= 0
+    default:
+      if (lo_dn > 0.0 || nh_dn > 0.0) return 0;
+      if (lo_up <= 0.0 && nh_up <= 0.0) return 1;
+      return 2;
+  }
+}
+
+// Stage d on every depth-d node of the tier's tree: thread = (fibre f, node), consecutive
+// threads on consecutive nodes of one fibre.  Input entry e of parent p at
+// in[e * in_estride + p * in_nstride] (the coefficients: 1, 0); output entry-major.
+__global__ void __launch_bounds__(256)
+    k_stage_pair(const StageDev st, const int32_t *__restrict__ lab,
+                 const int32_t *__restrict__ par, const float4 *__restrict__ in_v,
+                 const float *__restrict__ in_e, int64_t in_estride, int64_t in_nstride,
+                 float4 *__restrict__ out_v, float *__restrict__ out_e, int64_t nnodes,
+                 AxisGrid g) {
+  const int64_t total = nnodes * st.nfib;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t it = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; it < total; it += stride) {
+    const int f = (int)(it / nnodes);
+    const int64_t node = it - (int64_t)f * nnodes;
+    const PairX x = pair_box(g, __ldg(lab + node));
+    const int64_t p = par ? (int64_t)__ldg(par + node) : 0;
+    float4 J = make_float4(0.f, 0.f, 0.f, 0.f);
+    float E = INFINITY;
+    if (x.ok)
+      pair_horner(in_v + p * in_nstride, in_e + p * in_nstride, in_estride, st.rowoff, f,
+                  __ldg(st.fiblen + f), x, J, E);
+    const int64_t o = (int64_t)__ldg(st.outpos + f) * nnodes + node;
+    out_v[o] = J;
+    out_e[o] = E;
+  }
+}
+
+struct PairLeafArgs {
+  const float4 *in_v[VX_MAXPOLY];  // parent blocks, entry-major (the coefficients when k == 1)
+  const float *in_e[VX_MAXPOLY];
+  const int32_t *rowoff[VX_MAXPOLY];
+  int32_t len[VX_MAXPOLY];
+  int8_t rel[VX_MAXPOLY];
+};
+
+__global__ void __launch_bounds__(256)
+    k_leaf_pair(PairLeafArgs A, int npoly, const int32_t *__restrict__ lab,
+                const int32_t *__restrict__ par, int64_t nleaves, int64_t nparents, AxisGrid g,
+                uint8_t *__restrict__ keep, uint8_t *__restrict__ flag) {
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < nleaves; i += stride) {
+    const PairX x = pair_box(g, __ldg(lab + i));
+    bool ex = false, am = !x.ok;
+    if (x.ok) {
+      const int64_t p = par ? (int64_t)__ldg(par + i) : 0;
+      const int64_t es = par ? nparents : 1;
+      for (int f = 0; f < npoly && !ex; ++f) {
+        float4 J;
+        float E;
+        pair_horner(A.in_v[f] + (par ? p : 0), A.in_e[f] + (par ? p : 0), es, A.rowoff[f], 0,
+                    A.len[f], x, J, E);
+        const int r = pair_classify(J, E, A.rel[f]);
+        ex = ex || r == 0;
+        am = am || r == 2;
+      }
+    }
+    keep[i] = ex ? 0 : 1;
+    flag[i] = (!ex && am) ? 1 : 0;
+  }
+}
+
+}  // namespace
+
+int eval_level_pair(const SysDev &sys, const CsfView &c, const LevelGrid &grid, uint8_t *d_keep,
+                    uint8_t *d_flag, cudaStream_t s, Timer *tm, int64_t *madds_out) {
+  const int k = sys.k;
+  const int64_t nleaves = c.N[k - 1];
+  *madds_out = 0;
+  if (nleaves == 0) return VX_OK;
+  bool exact = true;
+  for (int d = 0; d < k; ++d)
+    exact = exact && grid.ax[d].fexact && !grid.ax[d].point && !grid.ax[d].xlo;
+  if (!exact) {  // box ends that are not binary32 numbers: everything goes to binary64
+    VX_CUDA(cudaMemsetAsync(d_keep, 1, (size_t)nleaves, s));
+    VX_CUDA(cudaMemsetAsync(d_flag, 1, (size_t)nleaves, s));
+    return VX_OK;
+  }
+  float4 *val[VX_MAXPOLY][VX_KMAX] = {{nullptr}};
+  float *err[VX_MAXPOLY][VX_KMAX] = {{nullptr}};
+  int rc = VX_OK;
+  int64_t madds = 0;
+  auto grid_of = [](int64_t items) {
+    int64_t b = (items + 255) / 256;
+    const int64_t cap = (int64_t)sm_count() * 16;
+    return (unsigned)std::max<int64_t>(1, std::min<int64_t>(b, cap));
+  };
+  for (int f = 0; f < sys.npoly && rc == VX_OK; ++f) {
+    for (int d = 0; d + 1 < k && rc == VX_OK; ++d) {
+      const StageDev &st = sys.p[f].st[d];
+      const int64_t n = c.N[d] * st.blk_out;
+      rc = dmalloc((void **)&val[f][d], (size_t)std::max<int64_t>(n, 1) * sizeof(float4), s);
+      if (rc == VX_OK) rc = dmalloc((void **)&err[f][d], (size_t)std::max<int64_t>(n, 1) * sizeof(float), s);
+      if (rc != VX_OK) break;
+      const int64_t w = c.N[d] * (st.blk_in - st.nfib);
+      madds += w;
+      if (tm && tm->on) rc = tm->begin(d == 0 ? KK_STAGE0_PAIR : KK_STAGEJ_PAIR, w);
+      if (rc != VX_OK) break;
+      const float4 *in_v = d == 0 ? sys.p[f].cp : val[f][d - 1];
+      const float *in_e = d == 0 ? sys.p[f].ep : err[f][d - 1];
+      k_stage_pair<<<grid_of(c.N[d] * st.nfib), 256, 0, s>>>(
+          st, c.lab[d], d == 0 ? nullptr : c.par[d], in_v, in_e, d == 0 ? 1 : c.N[d - 1],
+          d == 0 ? 0 : 1, val[f][d], err[f][d], c.N[d], grid.ax[d]);
+      note_launch();
+      if (cudaGetLastError() != cudaSuccess) {
+        set_error("float-pair stage launch failed");
+        rc = VX_ECUDA;
+      }
+      if (rc == VX_OK && tm && tm->on) rc = tm->end();
+    }
+  }
+  if (rc == VX_OK) {
+    PairLeafArgs A{};
+    int64_t wl = 0;
+    for (int f = 0; f < sys.npoly; ++f) {
+      const StageDev &st = sys.p[f].st[k - 1];
+      A.in_v[f] = k == 1 ? sys.p[f].cp : val[f][k - 2];
+      A.in_e[f] = k == 1 ? sys.p[f].ep : err[f][k - 2];
+      A.rowoff[f] = st.rowoff;
+      A.len[f] = st.maxlen;
+      A.rel[f] = sys.rel[f];
+      wl += nleaves * (st.blk_in - 1);
+    }
+    madds += wl;
+    if (tm && tm->on) rc = tm->begin(KK_LEAF_PAIR, wl);
+    if (rc == VX_OK) {
+      k_leaf_pair<<<grid_of(nleaves), 256, 0, s>>>(A, sys.npoly, c.lab[k - 1],
+                                                   k == 1 ? nullptr : c.par[k - 1], nleaves,
+                                                   k == 1 ? 0 : c.N[k - 2], grid.ax[k - 1],
+                                                   d_keep, d_flag);
+      note_launch();
+      if (cudaGetLastError() != cudaSuccess) {
+        set_error("float-pair leaf launch failed");
+        rc = VX_ECUDA;
+      }
+    }
+    if (rc == VX_OK && tm && tm->on) rc = tm->end();
+  }
+  for (int f = 0; f < sys.npoly; ++f)
+    for (int d = 0; d + 1 < k; ++d) {
+      dfree(val[f][d], s);
+      dfree(err[f][d], s);
+    }
+  *madds_out = madds;
+  return rc;
+}
+
+// ---------------------------------------------------------------------------------------
 // Level evaluation without allocating: the partial-evaluation blocks live in a fixed array of
 // device memory that belongs to the library (every device that loads the library holds it
 // until the process exits).  The kernels are the ones above; only host code needs the array's

@@ -76,6 +76,8 @@ struct PolyDev {
   const double2 *c64;  // stage-0 input block as degenerate intervals (lo = hi = coefficient)
   const float2 *c32;   // stage-0 input block as <m, r> binary32 midpoint-radius pairs
   const float4 *c32c;  // stage-0 input block as binary32 [RD(c), RU(c)] with error bound
+  const float4 *cp;    // stage-0 input block as float pairs (lo_h, lo_l, -hi_h, -hi_l) ...
+  const float *ep;     // ... and their error bounds (eval_level_pair)
 };
 
 struct SysDev {
@@ -135,6 +137,9 @@ enum KernelKind {
                    // nodes' arrays written
   KK_COMPACT,      // stable compaction: flags + ranks read, kept nodes' arrays read and written
   KK_RECHECK,      // selection of the boxes to re-evaluate: flags read, their indices written
+  KK_STAGE0_PAIR,  // the float-pair tier (eval_level_pair) on the binary32 path's error band
+  KK_STAGEJ_PAIR,
+  KK_LEAF_PAIR,
   KK_COUNT
 };
 
@@ -166,6 +171,13 @@ struct Timer {
 // ARITH_F32_MIDRAD those with |m| >= theta r for some polynomial, for ARITH_F32_CERT those
 // inside the error band of some polynomial.
 enum Arith { ARITH_F64 = 0, ARITH_F32_MIDRAD = 1, ARITH_F32_CERT = 2 };
+// The float-pair tier: every interval end as an unevaluated sum of two binary32 numbers (about
+// 48 bits) with a bound on its distance to the binary64 path's end, on grids whose box ends are
+// binary32 numbers.  keep[i] = 0 / 1 where the binary64 path surely excludes / keeps leaf i;
+// flag[i] = 1 where the tier cannot tell (keep[i] is then 1), to be decided in binary64.
+int eval_level_pair(const SysDev &sys, const CsfView &csf, const LevelGrid &grid,
+                    uint8_t *d_keep, uint8_t *d_flag, cudaStream_t s, Timer *tm,
+                    int64_t *madds_out);
 int eval_level_raw(const SysDev &sys, const CsfView &csf, const LevelGrid &grid, int arith,
                    double *d_lo, double *d_hi, uint8_t *d_keep, uint8_t *d_flag, float theta,
                    cudaStream_t s, Timer *tm, int64_t *madds_out);

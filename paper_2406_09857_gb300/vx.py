@@ -92,6 +92,7 @@ def lib() -> ctypes.CDLL:
         "vx_result_boxes": ([P, P, P], i32),
         "vx_result_csf": ([P, PP], i32),
         "vx_result_stats": ([P, P, P, P, P, P, P], i32),
+        "vx_result_recheck64": ([P, P], i32),
         "vx_result_timing": ([P, P, P, P, P], i32),
         "vx_kernel_kind_name": ([i32], ctypes.c_char_p),
         "vx_result_elapsed_ms": ([P, P], i32),
@@ -522,8 +523,10 @@ class Result:
         _check(lib().vx_result_stats(self.handle, ctypes.byref(nl), _np_ptr(tested),
                                      _np_ptr(kept), _np_ptr(nodes), _np_ptr(recheck),
                                      _np_ptr(madds)))
+        recheck64 = np.zeros(L, dtype=np.int64)
+        _check(lib().vx_result_recheck64(self.handle, _np_ptr(recheck64)))
         return {"tested": tested, "kept": kept, "nodes": nodes, "recheck": recheck,
-                "madds": madds}
+                "recheck64": recheck64, "madds": madds}
 
     def timing(self) -> dict:
         nk = ctypes.c_int32()

@@ -651,3 +651,29 @@ def test_midrad_k4_staged_stage_reads_aligned_blocks(vx):
     lo_o, hi_o, keep_o, _ = oracle.eval_csf(polys, dom, 7, t)
     assert np.all(lo.cpu().numpy() <= lo_o) and np.all(hi.cpu().numpy() >= hi_o)
     assert np.all(keep.cpu().numpy() >= keep_o)
+
+
+@pytest.mark.parametrize("k,depth", [(1, 10), (2, 7), (3, 5)])
+def test_float_pair_tier_decides_the_binary32_band(vx, k, depth):
+    """A zero set 2^-30 away from a grid line: x_1 - (3/8 + 2^-30) (+ 2^-40 x_2 ... x_k).  On
+    the boxes that meet x_1 = 3/8 the binary32 ends are 0 within their error bound (3/8 + 2^-30
+    rounds to 3/8 in binary32), so certified binary32 leaves them to a finer arithmetic; the
+    float pairs carry the 2^-30 and decide every one of them, and the enclosure is binary64's."""
+    c = 0.375 + 2.0 ** -30
+    exps = [[1] + [0] * (k - 1), [0] * k]
+    coefs = [1.0, -c]
+    if k >= 2:
+        exps.append([0] + [1] * (k - 1))
+        coefs.append(2.0 ** -40)
+    polys = [(np.array(exps, dtype=np.int32), np.array(coefs))]
+    dom = synth.cube(k)
+    ref = oracle.enclose(polys, dom, depth)
+    res = vx.enclose(polys, dom, depth, vx.make_opts(vx.FP32))
+    st = res.stats()
+    assert np.array_equal(res.boxes(), ref["tuples"])
+    assert np.array_equal(st["tested"], ref["tested"])
+    assert np.array_equal(st["kept"], ref["kept"])
+    assert st["recheck"].sum() > 0
+    assert st["recheck64"].sum() == 0
+    # only the column of boxes whose x_1-range holds 3/8 + 2^-30 survives
+    assert np.all(res.boxes()[:, 0] == ((0.375 + 1.0) * (1 << depth) / 2))

@@ -484,8 +484,11 @@ def bench_table1(vx, synth, torch, stream, taylor=True):
         for kind in ("points", "curves", "hypersurfaces"):
             s = synth.table1(k, d, kind)
             sysv = vx.System(s.polys, stream=stream)
-            opts = vx.make_opts(vx.FP32, small_level_madds=SMALL_LEVEL_MADDS)
-            # the largest depth <= the paper's whose levels fit 32-bit tree indices
+            # levels whose next level would exceed 2^29 boxes run in x1-slab ranges
+            opts = vx.make_opts(vx.FP32, small_level_madds=SMALL_LEVEL_MADDS,
+                                max_level_boxes=1 << 29)
+            # the largest depth <= the paper's that runs (a single x1 slab whose next level
+            # exceeds the range's limit cannot be split further)
             depth, note = s.depth, None
             while True:
                 try:
@@ -494,7 +497,7 @@ def bench_table1(vx, synth, torch, stream, taylor=True):
                 except vx.VxError as e:
                     if e.code != vx.EOVERFLOW or depth <= 1:
                         raise
-                    note = "depth %d exceeds 32-bit tree indices (%s)" % (s.depth, e)
+                    note = "depth %d exceeds one x1 slab's limit (%s)" % (s.depth, e)
                     depth -= 1
             best, r = None, None
             for _ in range(2):
@@ -526,7 +529,8 @@ def bench_table1(vx, synth, torch, stream, taylor=True):
                 e0 = torch.cuda.Event(enable_timing=True)
                 e1 = torch.cuda.Event(enable_timing=True)
                 for tag, mode in (("fp32", vx.FP32), ("fp64", vx.FP64)):
-                    to = vx.make_opts(mode, taylor_order=2, small_level_madds=SMALL_LEVEL_MADDS)
+                    to = vx.make_opts(mode, taylor_order=2, small_level_madds=SMALL_LEVEL_MADDS,
+                                      max_level_boxes=1 << 29)
                     vx.enclose_system(sysv, s.domain, min(depth, 3), to, stream=stream).free()
                     e0.record(stream)
                     rt = vx.enclose_system(sysv, s.domain, depth, to, stream=stream)

@@ -129,7 +129,15 @@ typedef struct {
                          * descendant dropped by binary64 too), so keeping a box that binary64
                          * would drop changes only the counts of the levels in between
                          * (vx_result_stats), never the boxes that the last level keeps */
-  int32_t reserved[2];
+  int32_t max_level_boxes; /* 0 = 2^31 - 1: the most boxes one tree may hold at a level.  A
+                            * level whose kept boxes would give the next level more is run in
+                            * ranges of consecutive x_1 slabs, each through the remaining levels
+                            * on its own, in x_1 order (a box's descendants stay in its slab and
+                            * every box is decided on its own, so the result is the same); the
+                            * final boxes are then several trees, joined by vx_result_csf while
+                            * they fit one.  VX_EOVERFLOW when one slab alone exceeds it.  Not
+                            * with c1 (whose inclusion step keeps levels whole) */
+  int32_t reserved;
 } vx_opts;
 
 /* Thread-local message of the last failed call on this thread ("" if none). */
@@ -405,7 +413,9 @@ int vx_result_included(vx_result *res, int64_t *n, const int32_t **h_levels,
  * Host memory owned by the result (copied from the device on first call): a third of the
  * tuples' bytes at k = 3, for callers that move results off the GPU in bulk. */
 int vx_result_box_codes(vx_result *res, int64_t *n, int32_t *code_bytes, const void **h_codes);
-/* The survivors as a device CSF owned by the result (valid until vx_result_free). */
+/* The survivors as a device CSF owned by the result (valid until vx_result_free); for an
+ * enclosure run in x_1 ranges (opts.max_level_boxes) the ranges' trees joined into one on the
+ * first call, VX_EOVERFLOW if they hold more than 2^31 - 1 boxes. */
 int vx_result_csf(const vx_result *res, const vx_csf **csf);
 /* Per-level statistics, levels 0..depth: h_tested[l] = |S_l| boxes evaluated, h_kept[l]
  * survivors, h_nodes[l*k + j-1] = N_j(S_l), h_recheck[l] = boxes re-decided beyond the level's

@@ -778,7 +778,13 @@ struct vx_csf {
 
 struct vx_result {
   int k = 0, depth = 0;
+  // the final boxes: one tree, or (an enclosure run in x_1 ranges) fin and then the trees in
+  // `more`, one after another in lexicographic order; `merged` joins them on request
   CsfObj fin;
+  bool fin_set = false;
+  std::vector<CsfObj> more;
+  CsfObj merged;
+  bool merged_set = false;
   std::vector<int64_t> tested, kept, nodes, recheck, madds;
   std::vector<int64_t> recheck64;  // of the rechecked boxes, those decided in binary64
   Timer tm;
@@ -802,6 +808,25 @@ struct vx_result {
 // memory run at the link's rate (pageable copies go through a staging buffer), and pinning
 // is paid once per buffer, not once per result.
 // ---------------------------------------------------------------------------------------
+// every device tree a result holds
+static void result_release_trees(vx_result *R) {
+  csf_release(&R->fin);
+  for (auto &c : R->more) csf_release(&c);
+  R->more.clear();
+  if (R->merged_set) csf_release(&R->merged);
+  R->merged_set = false;
+  for (auto &lc : R->incl) csf_release(&lc.second);
+  R->incl.clear();
+}
+
+// the final trees in order (fin first)
+static std::vector<const CsfObj *> result_trees(const vx_result *R) {
+  std::vector<const CsfObj *> t;
+  t.push_back(&R->fin);
+  for (auto &c : R->more) t.push_back(&c);
+  return t;
+}
+
 static std::mutex g_pin_mu;
 static std::multimap<size_t, void *> g_pin_free;  // capacity -> buffer
 
@@ -1798,6 +1823,234 @@ static __global__ void k_c1_split(uint8_t *__restrict__ keep, uint8_t *__restric
   }
 }
 
+// The state of one enclosure while its levels run (Algorithm 3).
+struct EncloseRun {
+  const vx_system *sys;
+  const double *dom;
+  int depth, k;
+  vx_opts opts;
+  float theta;
+  cudaStream_t s;
+  vx_result *R;
+  Timer *tm;
+  int64_t cap;  // the most boxes one tree may hold at a level (the leaves' count)
+};
+
+static void result_append(vx_result *R, CsfObj &fin) {
+  if (!R->fin_set) {
+    R->fin = fin;
+    R->fin_set = true;
+  } else {
+    R->more.push_back(fin);
+  }
+}
+
+// Level l of Algorithm 3 on cur: C0 (and C1 from its level on); keep flags of the leaves
+// (caller frees), the boxes C1 certified moved to R->incl.  With the vertex test, cur is
+// replaced by its C0 survivors.
+static int level_step(EncloseRun &E, CsfObj &cur, int l, uint8_t **keep_out,
+                      int64_t *included_out) {
+  const int k = E.k;
+  const vx_opts &opts = E.opts;
+  const cudaStream_t s = E.s;
+  vx_result *R = E.R;
+  Timer *tm = E.tm;
+  *keep_out = nullptr;
+  *included_out = 0;
+  LevelGrid g;
+  VX_CHECK(make_grid(k, E.dom, l, &g));
+  const int64_t n = cur.v.N[k - 1];
+  R->tested[l] += n;
+  for (int d = 0; d < k; ++d) R->nodes[(size_t)l * k + d] += cur.v.N[d];
+  int mode = opts.mode;
+  if (mode == VX_FP32_MIDRAD && opts.fp64_final && l == E.depth) mode = VX_FP64;
+  if (mode == VX_FP32 && opts.small_level_madds > 0) {
+    // Theorem 1's count for this level (every polynomial and depth), times the Taylor
+    // form's derivatives: small levels run in binary64, which decides the same way
+    int64_t w = 0;
+    for (int f = 0; f < E.sys->dev.npoly; ++f)
+      for (int d = 0; d < k; ++d)
+        w += cur.v.N[d] * (E.sys->dev.p[f].st[d].blk_in - E.sys->dev.p[f].st[d].nfib);
+    if (opts.taylor_order > 0) {
+      int64_t na = 1;  // C(m + k, k)
+      for (int i = 1; i <= k; ++i) na = na * (opts.taylor_order + i) / i;
+      w *= na;
+    }
+    if (w < opts.small_level_madds) mode = VX_FP64;
+  }
+  const bool c1_here = opts.c1 != 0 && l >= opts.c1_level && n > 0;
+  uint8_t *keep = nullptr, *inc = nullptr;
+  int rc = dmalloc((void **)&keep, (size_t)std::max<int64_t>(n, 1), s);
+  if (rc == VX_OK && c1_here) rc = dmalloc((void **)&inc, (size_t)n, s);
+  if (rc == VX_OK) {
+    int64_t w = 0, nr = 0, nr64 = 0;
+    if (opts.taylor_order > 0)
+      rc = n > 0 ? eval_taylor_level(E.sys, cur.v, g, opts.taylor_order, mode, nullptr, nullptr,
+                                     keep, opts.c1 == VX_C1_TAYLOR ? inc : nullptr, s, tm, &w,
+                                     &nr)
+                 : VX_OK;
+    else
+      rc = eval_decide(E.sys->dev, cur.v, g, mode, opts.fp64_recheck != 0, E.theta, nullptr,
+                       nullptr, keep, s, tm, &w, &nr, opts.recheck_last != 0 && l < E.depth,
+                       &nr64);
+    R->madds[l] += w;
+    R->recheck[l] += nr;
+    R->recheck64[l] += mode == VX_FP32 ? nr64 : nr;
+    int st = 0;
+    if (rc == VX_OK) rc = take_device_status(s, &st);
+    if (rc == VX_OK && st) {
+      set_error("enclose: a bounded device wait gave up at level %d", l);
+      rc = VX_ETIMEOUT;
+    }
+  }
+  int64_t included = 0;
+  if (rc == VX_OK && c1_here) {
+    // Algorithm 3's inclusion step: the C0 survivors that C1 certifies leave S
+    int64_t nc = n;
+    if (opts.c1 == VX_C1_VERTEX) {  // the corners are evaluated on the survivors only
+      CsfObj surv;
+      rc = csf_prune(cur.v, keep, 0, nullptr, s, &surv, tm);
+      if (rc == VX_OK) {
+        csf_release(&cur);
+        cur = surv;
+        nc = cur.v.N[k - 1];
+        if (nc > 0) {
+          const cudaError_t e = cudaMemsetAsync(keep, 1, (size_t)nc, s);
+          if (e != cudaSuccess) {
+            set_error("enclose: %s", cudaGetErrorString(e));
+            rc = VX_ECUDA;
+          }
+        }
+        if (rc == VX_OK && nc > 0) {
+          int64_t w = 0;
+          rc = eval_c1_vertex(E.sys->dev, cur.v, g, inc, s, tm, &w);
+          R->madds[l] += w;
+        }
+      }
+    }
+    if (rc == VX_OK && nc > 0) {
+      k_c1_split<<<(int)std::min<int64_t>((nc + 255) / 256, 4096), 256, 0, s>>>(keep, inc, nc);
+      note_launch();
+      CsfObj ic;
+      rc = csf_prune(cur.v, inc, 0, nullptr, s, &ic, tm);
+      if (rc == VX_OK) {
+        included = ic.v.N[k - 1];
+        if (included > 0) {
+          try {
+            R->incl.emplace_back(l, ic);
+          } catch (...) {
+            csf_release(&ic);
+            set_error("enclose: out of host memory");
+            rc = VX_ENOMEM;
+          }
+        } else {
+          csf_release(&ic);
+        }
+      }
+    }
+  }
+  dfree(inc, s);
+  if (rc != VX_OK) {
+    dfree(keep, s);
+    return rc;
+  }
+  *keep_out = keep;
+  *included_out = included;
+  return VX_OK;
+}
+
+static int run_levels(EncloseRun &E, CsfObj &cur, int l);
+
+// Level l's kept leaves would give the next level more than E.cap boxes in one tree: the kept
+// boxes are split into runs of consecutive x_1 slabs (depth-0 nodes) whose children fit, and
+// each run goes through the remaining levels on its own, in x_1 order.  A box's descendants
+// stay in its slab and every box is decided on its own, so the runs' final boxes, one after
+// another, are the enclosure's, in lexicographic order.
+static int run_chunked(EncloseRun &E, CsfObj &cur, const uint8_t *keep, int l) {
+  const int k = E.k;
+  const cudaStream_t s = E.s;
+  const int64_t n0 = cur.v.N[0], n = cur.v.N[k - 1];
+  int64_t *d_cnt = nullptr;
+  uint8_t *part = nullptr;
+  std::vector<int64_t> cnt((size_t)std::max<int64_t>(n0, 1), 0);
+  int rc = dmalloc((void **)&d_cnt, sizeof(int64_t) * cnt.size(), s);
+  if (rc == VX_OK) rc = csf_root_counts(cur.v, keep, d_cnt, s);
+  if (rc == VX_OK) {
+    cudaError_t e = cudaMemcpyAsync(cnt.data(), d_cnt, sizeof(int64_t) * (size_t)n0,
+                                    cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) {
+      set_error("enclose: %s", cudaGetErrorString(e));
+      rc = VX_ECUDA;
+    }
+  }
+  dfree(d_cnt, s);
+  int64_t total = 0;
+  for (int64_t r = 0; r < n0; ++r) total += cnt[r];
+  E.R->kept[l] += total;
+  if (rc == VX_OK) rc = dmalloc((void **)&part, (size_t)std::max<int64_t>(n, 1), s);
+  int64_t a = 0;
+  while (rc == VX_OK && a < n0) {
+    if ((cnt[a] << k) > E.cap) {
+      set_error("enclose: one x1 slab at level %d has %lld kept boxes, whose children exceed "
+                "the %lld boxes a level may hold", l, (long long)cnt[a], (long long)E.cap);
+      rc = VX_EOVERFLOW;
+      break;
+    }
+    int64_t b = a, acc = 0;
+    while (b < n0 && ((acc + cnt[b]) << k) <= E.cap) acc += cnt[b++];
+    if (acc > 0) {
+      rc = csf_keep_in_roots(cur.v, keep, a, b, part, s);
+      CsfObj next;
+      if (rc == VX_OK) rc = csf_prune(cur.v, part, 1, nullptr, s, &next, E.tm, E.cap);
+      if (rc == VX_OK) rc = run_levels(E, next, l + 1);  // consumes next
+    }
+    a = b;
+  }
+  dfree(part, s);
+  return rc;
+}
+
+// Levels l..depth of Algorithm 3 from the tree cur (consumed); the final boxes are appended to
+// the result.
+static int run_levels(EncloseRun &E, CsfObj &cur, int l) {
+  const int k = E.k;
+  int rc = VX_OK;
+  for (; l <= E.depth && rc == VX_OK; ++l) {
+    uint8_t *keep = nullptr;
+    int64_t included = 0;
+    rc = level_step(E, cur, l, &keep, &included);
+    if (rc != VX_OK) break;
+    if (l == E.depth) {
+      CsfObj fin;
+      rc = csf_prune(cur.v, keep, 0, nullptr, E.s, &fin, E.tm);
+      if (rc == VX_OK) {
+        E.R->kept[l] += fin.v.N[k - 1] + included;
+        result_append(E.R, fin);
+      }
+    } else {
+      CsfObj next;
+      rc = csf_prune(cur.v, keep, 1, nullptr, E.s, &next, E.tm, E.cap);
+      if (rc == VX_EOVERFLOW && E.opts.c1 == 0) {
+        // the next level does not fit one tree: run it in x_1 ranges
+        clear_error();
+        rc = run_chunked(E, cur, keep, l);
+        dfree(keep, E.s);
+        csf_release(&cur);
+        return rc;
+      }
+      if (rc == VX_OK) {
+        E.R->kept[l] += (next.v.N[k - 1] >> k) + included;
+        csf_release(&cur);
+        cur = next;
+      }
+    }
+    dfree(keep, E.s);
+  }
+  csf_release(&cur);
+  return rc;
+}
+
 static int enclose_impl(const vx_system *sys, const double *dom, int depth, const vx_opts *o,
                         cudaStream_t s, vx_result *R, const CsfObj *start) {
   const int k = sys->dev.k;
@@ -1874,116 +2127,13 @@ static int enclose_impl(const vx_system *sys, const double *dom, int depth, cons
   } else {
     rc = level0(k, s, &cur);
   }
-  for (int l = l0; l <= depth && rc == VX_OK; ++l) {
-    rc = make_grid(k, dom, l, &g);
-    if (rc != VX_OK) break;
-    const int64_t n = cur.v.N[k - 1];
-    R->tested[l] = n;
-    for (int d = 0; d < k; ++d) R->nodes[(size_t)l * k + d] = cur.v.N[d];
-    int mode = opts.mode;
-    if (mode == VX_FP32_MIDRAD && opts.fp64_final && l == depth) mode = VX_FP64;
-    if (mode == VX_FP32 && opts.small_level_madds > 0) {
-      // Theorem 1's count for this level (every polynomial and depth), times the Taylor
-      // form's derivatives: small levels run in binary64, which decides the same way
-      int64_t w = 0;
-      for (int f = 0; f < sys->dev.npoly; ++f)
-        for (int d = 0; d < k; ++d)
-          w += cur.v.N[d] * (sys->dev.p[f].st[d].blk_in - sys->dev.p[f].st[d].nfib);
-      if (opts.taylor_order > 0) {
-        int64_t na = 1;  // C(m + k, k)
-        for (int i = 1; i <= k; ++i) na = na * (opts.taylor_order + i) / i;
-        w *= na;
-      }
-      if (w < opts.small_level_madds) mode = VX_FP64;
-    }
-    const bool c1_here = opts.c1 != 0 && l >= opts.c1_level && n > 0;
-    uint8_t *keep = nullptr, *inc = nullptr;
-    rc = dmalloc((void **)&keep, (size_t)std::max<int64_t>(n, 1), s);
-    if (rc == VX_OK && c1_here) rc = dmalloc((void **)&inc, (size_t)n, s);
-    if (rc == VX_OK) {
-      int64_t w = 0, nr = 0, nr64 = 0;
-      if (opts.taylor_order > 0)
-        rc = n > 0 ? eval_taylor_level(sys, cur.v, g, opts.taylor_order, mode, nullptr,
-                                       nullptr, keep, opts.c1 == VX_C1_TAYLOR ? inc : nullptr, s,
-                                       tm, &w, &nr)
-                   : VX_OK;
-      else
-        rc = eval_decide(sys->dev, cur.v, g, mode, opts.fp64_recheck != 0, theta, nullptr,
-                         nullptr, keep, s, tm, &w, &nr, opts.recheck_last != 0 && l < depth, &nr64);
-      R->madds[l] += w;
-      R->recheck[l] = nr;
-      R->recheck64[l] = mode == VX_FP32 ? nr64 : nr;
-      int st = 0;
-      if (rc == VX_OK) rc = take_device_status(s, &st);
-      if (rc == VX_OK && st) {
-        set_error("enclose: a bounded device wait gave up at level %d", l);
-        rc = VX_ETIMEOUT;
-      }
-    }
-    int64_t included = 0;
-    if (rc == VX_OK && c1_here) {
-      // Algorithm 3's inclusion step: the C0 survivors that C1 certifies leave S
-      int64_t nc = n;
-      if (opts.c1 == VX_C1_VERTEX) {  // the corners are evaluated on the survivors only
-        CsfObj surv;
-        rc = csf_prune(cur.v, keep, 0, nullptr, s, &surv, tm);
-        if (rc == VX_OK) {
-          csf_release(&cur);
-          cur = surv;
-          nc = cur.v.N[k - 1];
-          if (nc > 0) {
-            const cudaError_t e = cudaMemsetAsync(keep, 1, (size_t)nc, s);
-            if (e != cudaSuccess) {
-              set_error("enclose: %s", cudaGetErrorString(e));
-              rc = VX_ECUDA;
-            }
-          }
-          if (rc == VX_OK && nc > 0) {
-            int64_t w = 0;
-            rc = eval_c1_vertex(sys->dev, cur.v, g, inc, s, tm, &w);
-            R->madds[l] += w;
-          }
-        }
-      }
-      if (rc == VX_OK && nc > 0) {
-        k_c1_split<<<(int)std::min<int64_t>((nc + 255) / 256, 4096), 256, 0, s>>>(keep, inc, nc);
-        note_launch();
-        CsfObj ic;
-        rc = csf_prune(cur.v, inc, 0, nullptr, s, &ic, tm);
-        if (rc == VX_OK) {
-          included = ic.v.N[k - 1];
-          if (included > 0) {
-            try {
-              R->incl.emplace_back(l, ic);
-            } catch (...) {
-              csf_release(&ic);
-              set_error("enclose: out of host memory");
-              rc = VX_ENOMEM;
-            }
-          } else {
-            csf_release(&ic);
-          }
-        }
-      }
-    }
-    if (rc == VX_OK) {
-      if (l == depth) {
-        rc = csf_prune(cur.v, keep, 0, nullptr, s, &R->fin, tm);
-        if (rc == VX_OK) R->kept[l] = R->fin.v.N[k - 1] + included;
-      } else {
-        CsfObj next;
-        rc = csf_prune(cur.v, keep, 1, nullptr, s, &next, tm);
-        if (rc == VX_OK) {
-          R->kept[l] = (next.v.N[k - 1] >> k) + included;
-          csf_release(&cur);
-          cur = next;
-        }
-      }
-    }
-    dfree(keep, s);
-    dfree(inc, s);
+  if (rc == VX_OK) {
+    EncloseRun E{sys, dom, depth, k, opts, theta, s, R, tm,
+                 opts.max_level_boxes > 0 ? (int64_t)opts.max_level_boxes : (int64_t)INT32_MAX};
+    rc = run_levels(E, cur, l0);  // consumes cur
+  } else {
+    csf_release(&cur);
   }
-  csf_release(&cur);
   if (rc == VX_OK) {
     cudaError_t e = cudaEventRecord(ev1, s);
     if (e == cudaSuccess) e = cudaEventSynchronize(ev1);
@@ -2025,7 +2175,7 @@ int vx_enclose_system(const vx_system *sys, const double *h_domain, int32_t dept
   if (!R) return VX_ENOMEM;
   int rc = enclose_impl(sys, h_domain, depth, opts, as_stream(stream), R, nullptr);
   if (rc != VX_OK) {
-    csf_release(&R->fin);
+    result_release_trees(R);
     R->tm.release();
     delete R;
     return rc;
@@ -2046,7 +2196,7 @@ int vx_enclose_from(const vx_system *sys, const vx_csf *start, const double *h_d
   if (!R) return VX_ENOMEM;
   int rc = enclose_impl(sys, h_domain, depth, opts, as_stream(stream), R, &start->o);
   if (rc != VX_OK) {
-    csf_release(&R->fin);
+    result_release_trees(R);
     R->tm.release();
     delete R;
     return rc;
@@ -2275,6 +2425,7 @@ int batch_group(const std::vector<int32_t> &ids, const vx_poly *const *systems,
     int64_t N0[VX_KMAX] = {0};
     if (csf_alloc(&R[t]->fin, k, D, N0, s) != VX_OK || set_ptr_sentinels(R[t]->fin.v, s) != VX_OK)
       rc = VX_ENOMEM;
+    R[t]->fin_set = true;
   }
   cudaEvent_t ev0 = nullptr, ev1 = nullptr;
   if (rc == VX_OK && (cudaEventCreate(&ev0) != cudaSuccess || cudaEventCreate(&ev1) != cudaSuccess))
@@ -2532,22 +2683,34 @@ int vx_result_boxes(vx_result *R, int64_t *n, const int32_t **h_tuples) {
   }
   if (R->hcount < 0) {
     const int k = R->k;
-    const int64_t m = R->fin.v.N[k - 1];
+    const auto trees = result_trees(R);
+    int64_t m = 0, mmax = 0;
+    for (auto *t : trees) {
+      m += t->v.N[k - 1];
+      mmax = std::max<int64_t>(mmax, t->v.N[k - 1]);
+    }
     if (m > 0) {
       cudaStream_t s = R->fin.stream;
       void *hb = nullptr;
       size_t cap = 0;
       VX_CHECK(pinned_get((size_t)m * k * 4, &hb, &cap));
       int32_t *d = nullptr;
-      int rc = dmalloc((void **)&d, (size_t)m * k * 4, s);
-      if (rc == VX_OK) rc = csf_tuples_dev(R->fin.v, d, s);
-      if (rc == VX_OK) {
-        cudaError_t e = cudaMemcpyAsync(hb, d, (size_t)m * k * 4, cudaMemcpyDeviceToHost, s);
-        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
-        if (e != cudaSuccess) {
-          set_error("copying the boxes to the host failed: %s", cudaGetErrorString(e));
-          rc = VX_ECUDA;
+      int rc = dmalloc((void **)&d, (size_t)mmax * k * 4, s);
+      int64_t at = 0;
+      for (size_t j = 0; j < trees.size() && rc == VX_OK; ++j) {
+        const int64_t mj = trees[j]->v.N[k - 1];
+        if (mj == 0) continue;
+        rc = csf_tuples_dev(trees[j]->v, d, s);
+        if (rc == VX_OK) {
+          cudaError_t e = cudaMemcpyAsync((int32_t *)hb + at * k, d, (size_t)mj * k * 4,
+                                          cudaMemcpyDeviceToHost, s);
+          if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+          if (e != cudaSuccess) {
+            set_error("copying the boxes to the host failed: %s", cudaGetErrorString(e));
+            rc = VX_ECUDA;
+          }
         }
+        at += mj;
       }
       dfree(d, s);
       if (rc != VX_OK) {
@@ -2573,22 +2736,34 @@ int vx_result_box_codes(vx_result *R, int64_t *n, int32_t *code_bytes, const voi
   const int k = R->k;
   const int cb = k * R->depth <= 32 ? 4 : 8;
   if (R->hcodes_count < 0) {
-    const int64_t m = R->fin.v.N[k - 1];
+    const auto trees = result_trees(R);
+    int64_t m = 0, mmax = 0;
+    for (auto *t : trees) {
+      m += t->v.N[k - 1];
+      mmax = std::max<int64_t>(mmax, t->v.N[k - 1]);
+    }
     if (m > 0) {
       cudaStream_t s = R->fin.stream;
       void *hb = nullptr;
       size_t cap = 0;
       VX_CHECK(pinned_get((size_t)m * cb, &hb, &cap));
       void *d = nullptr;
-      int rc = dmalloc(&d, (size_t)m * cb, s);
-      if (rc == VX_OK) rc = csf_box_codes_dev(R->fin.v, d, s);
-      if (rc == VX_OK) {
-        cudaError_t e = cudaMemcpyAsync(hb, d, (size_t)m * cb, cudaMemcpyDeviceToHost, s);
-        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
-        if (e != cudaSuccess) {
-          set_error("copying the box codes to the host failed: %s", cudaGetErrorString(e));
-          rc = VX_ECUDA;
+      int rc = dmalloc(&d, (size_t)mmax * cb, s);
+      int64_t at = 0;
+      for (size_t j = 0; j < trees.size() && rc == VX_OK; ++j) {
+        const int64_t mj = trees[j]->v.N[k - 1];
+        if (mj == 0) continue;
+        rc = csf_box_codes_dev(trees[j]->v, d, s);
+        if (rc == VX_OK) {
+          cudaError_t e = cudaMemcpyAsync((char *)hb + (size_t)at * cb, d, (size_t)mj * cb,
+                                          cudaMemcpyDeviceToHost, s);
+          if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+          if (e != cudaSuccess) {
+            set_error("copying the box codes to the host failed: %s", cudaGetErrorString(e));
+            rc = VX_ECUDA;
+          }
         }
+        at += mj;
       }
       dfree(d, s);
       if (rc != VX_OK) {
@@ -2661,7 +2836,37 @@ int vx_result_csf(const vx_result *R, const vx_csf **csf) {
     return VX_EINVAL;
   }
   // vx_csf is a thin wrapper over CsfObj with the same layout
-  *csf = reinterpret_cast<const vx_csf *>(&R->fin);
+  if (R->more.empty()) {
+    *csf = reinterpret_cast<const vx_csf *>(&R->fin);
+    return VX_OK;
+  }
+  // an enclosure run in x_1 ranges: one tree of all its boxes, made once
+  vx_result *W = const_cast<vx_result *>(R);
+  if (!W->merged_set) {
+    const int k = R->k;
+    const auto trees = result_trees(R);
+    int64_t m = 0;
+    for (auto *t : trees) m += t->v.N[k - 1];
+    if (m > INT32_MAX) {
+      set_error("vx_result_csf: %lld boxes exceed one tree's 32-bit indices (use "
+                "vx_result_boxes or vx_result_box_codes)", (long long)m);
+      return VX_EOVERFLOW;
+    }
+    cudaStream_t s = R->fin.stream;
+    int32_t *d = nullptr;
+    VX_CHECK(dmalloc((void **)&d, (size_t)std::max<int64_t>(m, 1) * k * 4, s));
+    int rc = VX_OK;
+    int64_t at = 0;
+    for (size_t j = 0; j < trees.size() && rc == VX_OK; ++j) {
+      rc = csf_tuples_dev(trees[j]->v, d + at * k, s);
+      at += trees[j]->v.N[k - 1];
+    }
+    if (rc == VX_OK) rc = csf_build_dev(k, R->depth, d, m, s, &W->merged, nullptr);
+    dfree(d, s);
+    VX_CHECK(rc);
+    W->merged_set = true;
+  }
+  *csf = reinterpret_cast<const vx_csf *>(&R->merged);
   return VX_OK;
 }
 
@@ -2726,8 +2931,7 @@ void vx_result_free(vx_result *R) {
   if (!R) return;
   pinned_put(R->htup, R->hcap);
   pinned_put(R->hcodes, R->hcodes_cap);
-  csf_release(&R->fin);
-  for (auto &lc : R->incl) csf_release(&lc.second);
+  result_release_trees(R);
   R->tm.release();
   delete R;
 }

@@ -18,6 +18,8 @@
 // the keep flags, so every new node is written straight to its place.
 #include <cuda_runtime.h>
 
+#include <algorithm>
+
 #include "vx_internal.cuh"
 
 namespace vx {
@@ -655,7 +657,7 @@ void launch_split(int d, int blocks, cudaStream_t s, const CsfView &in, const ui
 template <int C>
 int prune_c(const CsfView &in, const uint8_t *d_keep, int split, int32_t *d_index,
             cudaStream_t s, CsfObj *out, Timer *tm, const int64_t *d_seg_off = nullptr,
-            int nseg = 0, int64_t *d_seg_kept = nullptr) {
+            int nseg = 0, int64_t *d_seg_kept = nullptr, int64_t cap = INT32_MAX) {
   const int k = in.k;
   Segs sg;
   sg.k = k;
@@ -724,7 +726,7 @@ int prune_c(const CsfView &in, const uint8_t *d_keep, int split, int32_t *d_inde
   if (rc == VX_OK) {
     for (int d = 0; d < k; ++d) {
       newN[d] = split ? ((int64_t)nk[d] << (d + 1)) : nk[d];
-      if (newN[d] > INT32_MAX) {
+      if (newN[d] > INT32_MAX || newN[d] > cap) {
         set_error("next level would have %lld nodes at depth %d (32-bit indices)",
                   (long long)newN[d], d + 1);
         rc = VX_EOVERFLOW;
@@ -937,15 +939,62 @@ int csf_build_dev(int k, int level, const int32_t *d_tuples, int64_t n, cudaStre
 }
 
 int csf_prune(const CsfView &in, const uint8_t *d_keep, int split, int32_t *d_index,
-              cudaStream_t s, CsfObj *out, Timer *tm) {
+              cudaStream_t s, CsfObj *out, Timer *tm, int64_t cap) {
   switch (in.k) {
-    case 1: return prune_c<1>(in, d_keep, split, d_index, s, out, tm);
-    case 2: return prune_c<2>(in, d_keep, split, d_index, s, out, tm);
-    case 3: return prune_c<3>(in, d_keep, split, d_index, s, out, tm);
-    case 4: return prune_c<4>(in, d_keep, split, d_index, s, out, tm);
-    case 5: return prune_c<5>(in, d_keep, split, d_index, s, out, tm);
-    default: return prune_c<6>(in, d_keep, split, d_index, s, out, tm);
+    case 1: return prune_c<1>(in, d_keep, split, d_index, s, out, tm, nullptr, 0, nullptr, cap);
+    case 2: return prune_c<2>(in, d_keep, split, d_index, s, out, tm, nullptr, 0, nullptr, cap);
+    case 3: return prune_c<3>(in, d_keep, split, d_index, s, out, tm, nullptr, 0, nullptr, cap);
+    case 4: return prune_c<4>(in, d_keep, split, d_index, s, out, tm, nullptr, 0, nullptr, cap);
+    case 5: return prune_c<5>(in, d_keep, split, d_index, s, out, tm, nullptr, 0, nullptr, cap);
+    default: return prune_c<6>(in, d_keep, split, d_index, s, out, tm, nullptr, 0, nullptr, cap);
   }
+}
+
+namespace {
+
+// the depth-0 ancestor of leaf i
+__device__ __forceinline__ int64_t root_of(const CsfView &c, int64_t i) {
+  int64_t p = i;
+  for (int d = c.k - 1; d > 0; --d) p = c.par[d][p];
+  return p;
+}
+
+__global__ void k_root_counts(CsfView c, const uint8_t *__restrict__ keep,
+                              unsigned long long *cnt) {
+  const int64_t n = c.N[c.k - 1];
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride)
+    if (keep[i]) atomicAdd(cnt + root_of(c, i), 1ull);
+}
+
+__global__ void k_keep_in_roots(CsfView c, const uint8_t *__restrict__ keep, int64_t a,
+                                int64_t b, uint8_t *__restrict__ out) {
+  const int64_t n = c.N[c.k - 1];
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
+    const int64_t r = root_of(c, i);
+    out[i] = (r >= a && r < b) ? keep[i] : (uint8_t)0;
+  }
+}
+
+}  // namespace
+
+int csf_root_counts(const CsfView &c, const uint8_t *d_keep, int64_t *d_cnt, cudaStream_t s) {
+  VX_CUDA(cudaMemsetAsync(d_cnt, 0, sizeof(int64_t) * (size_t)std::max<int64_t>(c.N[0], 1), s));
+  if (c.N[c.k - 1] == 0) return VX_OK;
+  k_root_counts<<<blocks_for(c.N[c.k - 1]), 256, 0, s>>>(c, d_keep, (unsigned long long *)d_cnt);
+  note_launch();
+  VX_LAUNCH_CHECK();
+  return VX_OK;
+}
+
+int csf_keep_in_roots(const CsfView &c, const uint8_t *d_keep, int64_t a, int64_t b,
+                      uint8_t *d_out, cudaStream_t s) {
+  if (c.N[c.k - 1] == 0) return VX_OK;
+  k_keep_in_roots<<<blocks_for(c.N[c.k - 1]), 256, 0, s>>>(c, d_keep, a, b, d_out);
+  note_launch();
+  VX_LAUNCH_CHECK();
+  return VX_OK;
 }
 
 int csf_prune_forest(const CsfView &in, const uint8_t *d_keep, int split, int32_t *d_index,

@@ -237,8 +237,15 @@ int csf_build_dev(int k, int level, const int32_t *d_tuples, int64_t n, cudaStre
                   CsfObj *out, Timer *tm);
 // split = 1: Algorithm 3's bisection (level + 1); split = 0: stable compaction (same level),
 // writing the kept leaves' old indices to d_index when non-null.
+// cap: the most nodes the output may have at any depth (VX_EOVERFLOW beyond it; at most
+// INT32_MAX, the tree's index range).
 int csf_prune(const CsfView &in, const uint8_t *d_keep, int split, int32_t *d_index,
-              cudaStream_t s, CsfObj *out, Timer *tm);
+              cudaStream_t s, CsfObj *out, Timer *tm, int64_t cap = INT32_MAX);
+// Per depth-0 node (an x_1 slab) r, d_cnt[r] = the leaves under it with d_keep set.
+int csf_root_counts(const CsfView &c, const uint8_t *d_keep, int64_t *d_cnt, cudaStream_t s);
+// d_out[i] = d_keep[i] for the leaves under depth-0 nodes a .. b-1, 0 elsewhere.
+int csf_keep_in_roots(const CsfView &c, const uint8_t *d_keep, int64_t a, int64_t b,
+                      uint8_t *d_out, cudaStream_t s);
 // The same on a forest of nseg trees stored one after another at every depth (tree s owns
 // depth-d nodes d_seg_off[d*(nseg+1) + s] .. [.. + s + 1] - 1): d_seg_kept[d*(nseg+1) + s]
 // receives the kept depth-d nodes of trees before s (s = nseg: all of them).

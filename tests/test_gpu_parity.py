@@ -677,3 +677,35 @@ def test_float_pair_tier_decides_the_binary32_band(vx, k, depth):
     assert st["recheck64"].sum() == 0
     # only the column of boxes whose x_1-range holds 3/8 + 2^-30 survives
     assert np.all(res.boxes()[:, 0] == ((0.375 + 1.0) * (1 << depth) / 2))
+
+
+@pytest.mark.parametrize("name,cap,mode_name,recheck_last", [
+    ("k3-d6-2polys", 600, "FP64", False), ("k3-d6-2polys", 600, "FP32", True),
+    ("k3-d6-2polys", 400, "FP32_MIDRAD", False),
+    ("plain-k2-d20-depth8", 700, "FP32", False), ("k4-d3", 8000, "FP64", False)])
+def test_enclose_in_x1_ranges_equals_oracle(vx, name, cap, mode_name, recheck_last):
+    """A level whose kept boxes would give the next level more than opts.max_level_boxes boxes
+    runs in ranges of consecutive x_1 slabs, each through the remaining levels on its own: the
+    boxes (as tuples, as codes and as one joined tree) and the per-level counts are the
+    oracle's, and no tree of the run held more than the cap."""
+    polys, dom, depth = ENCLOSE_CASES[name]()
+    ref = oracle.enclose(polys, dom, depth)
+    if mode_name == "FP32_MIDRAD":  # a superset of binary64's: the unchunked run is the reference
+        whole = vx.enclose(polys, dom, depth, vx.make_opts(vx.FP32_MIDRAD))
+        ws = whole.stats()
+        ref = {"tuples": whole.boxes(), "tested": ws["tested"], "kept": ws["kept"],
+               "nodes": ws["nodes"]}
+    k = ref["tuples"].shape[1]
+    assert max(ref["kept"][:-1]) << k > cap, "the cap must force a split"
+    o = vx.make_opts(getattr(vx, mode_name), recheck_last=recheck_last, max_level_boxes=cap)
+    res = vx.enclose(polys, dom, depth, o)
+    st = res.stats()
+    assert np.array_equal(res.boxes(), ref["tuples"])
+    assert np.array_equal(st["tested"], ref["tested"]) or recheck_last
+    assert st["kept"][-1] == ref["kept"][-1]
+    if not recheck_last:
+        assert np.array_equal(st["kept"], ref["kept"])
+        assert np.array_equal(st["nodes"], ref["nodes"])
+    codes = res.box_codes()
+    assert np.array_equal(vx.Result.decode_codes(codes, k, depth), ref["tuples"])
+    assert np.array_equal(res.csf().tuples().cpu().numpy(), ref["tuples"])

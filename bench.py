@@ -611,7 +611,28 @@ def bench_applications(vx, synth, torch, stream):
     return out
 
 
-def bench_batch(vx, synth, torch, workers=16):
+def oracle_batch_sample(systems, nlineages: int, seed: int, procs: int):
+    """The oracle on random (system, finest x1-slab) lineages of a batch, spread over
+    ``procs`` spawned worker processes: box evaluations per second of wall time."""
+    import multiprocessing as mp
+
+    from paper_2406_09857_gb300 import synth
+
+    st = synth.Stream(seed)
+    jobs = []
+    for _ in range(nlineages):
+        polys, domain, depth = systems[int(st.uniform_int(0, len(systems) - 1, 1)[0])]
+        jobs.append((polys, domain, depth, int(st.uniform_int(0, (1 << depth) - 1, 1)[0])))
+    with mp.get_context("spawn").Pool(procs) as pool:
+        pool.map(_lineage_job, jobs[:procs])
+        t0 = time.perf_counter()
+        res = pool.map(_lineage_job, jobs, chunksize=1)
+        wall = time.perf_counter() - t0
+    boxes = sum(r[0] for r in res)
+    return boxes / wall, boxes, wall
+
+
+def bench_batch(vx, synth, torch, workers=16, cpu=False):
     """Config 4: 256 independent systems (128 bivariate single equations of degree 10..60 and
     128 trivariate pairs of degree 10..40, depths 8..10) through vx_enclose_batch, from host
     polynomials to host boxes, in each arithmetic; every system's result must agree."""
@@ -645,6 +666,14 @@ def bench_batch(vx, synth, torch, workers=16):
     out["fp32_recheck_last_equals_fp64"] = all(
         np.array_equal(a, b) for a, b in zip(boxes["fp32_recheck_last"], boxes["fp64"]))
     out["speedup_fp32_vs_fp64"] = out["fp32"]["value"] / out["fp64"]["value"]
+    if cpu:
+        ncores = os.cpu_count() or 1
+        v, b, t = oracle_batch_sample(systems, 8 * ncores, seed=23, procs=ncores)
+        out["cpu_oracle"] = {"box_evals_per_s": v, "box_evals": b, "s": t, "cores": ncores,
+                             "sample": "Algorithm 3 along %d random (system, finest x1-slab) "
+                                       "lineages of the batch, binary64 directed rounding, in "
+                                       "%d spawned processes" % (8 * ncores, ncores),
+                             "gpu_fp32_over_all_cores": out["fp32"]["value"] / v}
     return out
 
 
@@ -939,7 +968,7 @@ def run_gpu(args):
         log("[bench] dense level and batch")
         extra["dense_level"] = bench_dense(vx, synth, torch, stream, flush)
         extra["dense_sweep"] = bench_dense_sweep(vx, synth, torch, stream, flush)
-        extra["batch"] = bench_batch(vx, synth, torch)
+        extra["batch"] = bench_batch(vx, synth, torch, cpu=not args.no_cpu)
         extra["precision"] = bench_precision(vx, synth, torch)
         extra["configs"] = bench_configs(vx, synth, torch, stream, not args.no_cpu,
                                          args.cpu_budget)

@@ -152,55 +152,80 @@ __global__ void __launch_bounds__(1024) k_scan_tiles(int32_t *tsum, int64_t ntil
 }
 
 // The exclusive counts of every entry: the tile's offset (toff) carried over its passes, each
-// pass a block-wide scan.
+// pass a block-wide scan.  The next pass's flags are loaded before this pass's scan (their
+// latency overlaps it), and with at most 3 channels the per-thread counts (at most SI = 8 each,
+// at most 256 in a warp) are packed 10 bits per channel so that one warp scan serves them all.
 template <int C, class Src, class Emit>
 __global__ void __launch_bounds__(ST) k_scan_emit(Src src, Emit em, int64_t n,
                                                   const int32_t *toff, int64_t ntiles) {
-  __shared__ int32_t sw[C][ST / 32 + 1];  // per warp exclusive offsets, then the pass total
+  __shared__ int32_t sw[2][C][ST / 32 + 1];  // per warp exclusive offsets, then the pass total
   const int64_t tile = blockIdx.x;
   const int passes = scan_passes(n);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   int32_t carry[C];
 #pragma unroll
   for (int c = 0; c < C; ++c) carry[c] = toff[c * ntiles + tile];
+  unsigned mn[SI];
+  {
+    const int64_t p0 = tile * passes * STILE;
+    if (p0 < n) load_items(src, p0 + (int64_t)threadIdx.x * SI, n, false, mn);
+  }
   for (int r = 0; r < passes; ++r) {
     const int64_t p0 = (tile * passes + r) * STILE;
     if (p0 >= n) break;  // the same for the whole CTA
     const int64_t i0 = p0 + (int64_t)threadIdx.x * SI;
     unsigned m[SI];
+#pragma unroll
+    for (int j = 0; j < SI; ++j) m[j] = mn[j];
+    if (r + 1 < passes && p0 + STILE < n)
+      load_items(src, p0 + STILE + (int64_t)threadIdx.x * SI, n, false, mn);
     int32_t cnt[C];
 #pragma unroll
     for (int c = 0; c < C; ++c) cnt[c] = 0;
-    load_items(src, i0, n, false, m);
 #pragma unroll
     for (int j = 0; j < SI; ++j)
 #pragma unroll
       for (int c = 0; c < C; ++c) cnt[c] += (m[j] >> c) & 1u;
     int32_t pre[C];
+    int32_t (&w)[C][ST / 32 + 1] = sw[r & 1];
+    if (C <= 3) {
+      int32_t pk = 0;
 #pragma unroll
-    for (int c = 0; c < C; ++c) {
-      int32_t incl = warp_incl_scan(cnt[c]);
-      pre[c] = incl - cnt[c];
-      if (lane == 31) sw[c][warp] = incl;
+      for (int c = 0; c < C; ++c) pk |= cnt[c] << (10 * c);
+      const int32_t incl = warp_incl_scan(pk);
+      const int32_t ex = incl - pk;
+#pragma unroll
+      for (int c = 0; c < C; ++c) {
+        pre[c] = (ex >> (10 * c)) & 1023;
+        if (lane == 31) w[c][warp] = (incl >> (10 * c)) & 1023;
+      }
+    } else {
+#pragma unroll
+      for (int c = 0; c < C; ++c) {
+        int32_t incl = warp_incl_scan(cnt[c]);
+        pre[c] = incl - cnt[c];
+        if (lane == 31) w[c][warp] = incl;
+      }
     }
     __syncthreads();
     if (warp == 0) {
 #pragma unroll
       for (int c = 0; c < C; ++c) {
-        int32_t v = lane < ST / 32 ? sw[c][lane] : 0;
-        int32_t s = warp_incl_scan(v);
-        if (lane < ST / 32) sw[c][lane] = s - v;
-        if (lane == ST / 32 - 1) sw[c][ST / 32] = s;
+        int32_t v = lane < ST / 32 ? w[c][lane] : 0;
+        int32_t sc = warp_incl_scan(v);
+        if (lane < ST / 32) w[c][lane] = sc - v;
+        if (lane == ST / 32 - 1) w[c][ST / 32] = sc;
       }
     }
     __syncthreads();
     int32_t run[C];
 #pragma unroll
-    for (int c = 0; c < C; ++c) run[c] = carry[c] + sw[c][warp] + pre[c];
+    for (int c = 0; c < C; ++c) run[c] = carry[c] + w[c][warp] + pre[c];
     emit_items<C>(em, i0, n, m, run);
 #pragma unroll
-    for (int c = 0; c < C; ++c) carry[c] += sw[c][ST / 32];
-    __syncthreads();  // sw is rewritten by the next pass
+    for (int c = 0; c < C; ++c) carry[c] += w[c][ST / 32];
+    // the next pass writes the other half of sw; the one after this half again, behind the
+    // next pass's two barriers
   }
 }
 

@@ -169,6 +169,8 @@ struct A32 {
   using V = float2;  // .x = m, .y = r
   struct X {
     float m, r, a;  // a >= |m| + r
+    float far;      // the end of largest magnitude, exactly (sign-definite boxes), else m
+    bool split;     // far is exact and the box does not straddle 0
     int cls;
   };
   static __device__ __forceinline__ X box(const AxisGrid &g, int32_t t) {
@@ -185,11 +187,35 @@ struct A32 {
       x.r = __double2float_ru(fmax(__dadd_ru(h, -dm), __dadd_ru(dm, -l)));
     }
     x.a = __fadd_ru(fabsf(x.m), x.r);
+    // on binary32-exact grids m +- r are the box's ends exactly
+    x.split = g.fexact && !g.point && (x.m - x.r >= 0.f || x.m + x.r <= 0.f);
+    x.far = x.split ? (x.m >= 0.f ? x.m + x.r : x.m - x.r) : x.m;
     x.cls = 0;  // one code path for every sign
     return x;
   }
+  // On a box that does not straddle 0 the step uses the exact hull of J*X instead of the
+  // general midpoint-radius product (whose interval exceeds the hull by 2 |Jm| Xr when J
+  // straddles 0, and by 2 Jr Xr at one end otherwise, which matters on boxes near 0, where Xr
+  // is comparable to |Xm|):
+  //   J straddles 0 (|Jm| <= Jr): both ends of J*X at f, the end of X of largest magnitude:
+  //     mid Jm f, radius Jr |f|;
+  //   else, s = sign(Jm) sign(Xm): mid Jm Xm + s Jr Xr, radius |Jm| Xr + Jr |Xm|.
+  // Rounding: t = RN(s Jr Xr + Am) and m = RN(Jm X' + t) each err by at most 2^-24 of their
+  // result (2^-149 below the normal range, which the stored radius carries), both added to the
+  // radius, rounded upward.  Other boxes take the general form.
   template <int CLS>
   static __device__ __forceinline__ V step(V J, const X &x, V A) {
+    if (x.split) {
+      const bool st = fabsf(J.x) <= J.y;
+      const float sjr = (J.x >= 0.f) == (x.m >= 0.f) ? J.y : -J.y;
+      const float t = __fmaf_rn(st ? 0.f : sjr, x.r, A.x);
+      const float m = __fmaf_rn(J.x, st ? x.far : x.m, t);
+      float r = __fmaf_ru(J.y, st ? x.a : fabsf(x.m), A.y);
+      r = __fmaf_ru(st ? 0.f : fabsf(J.x), x.r, r);
+      r = __fmaf_ru(kU32, fabsf(t), r);
+      r = __fmaf_ru(kU32, fabsf(m), r);
+      return make_float2(m, r);
+    }
     float m = __fmaf_rn(J.x, x.m, A.x);
     float r = __fmaf_ru(J.y, x.a, A.y);
     r = __fmaf_ru(fabsf(J.x), x.r, r);

@@ -79,6 +79,28 @@ __device__ __forceinline__ void emit_items(const Emit &em, int64_t i0, int64_t n
   }
 }
 
+// A thread's SI entries in a scan: loaded (load), counted per channel (count) and handed to
+// the emitter with the running exclusive counts (emit).  A source may specialise it (FlagSrc:
+// eight flag bytes of one depth counted and ranked a word at a time).
+template <int C, class Src>
+struct ItemOps {
+  unsigned m[SI];
+  __device__ __forceinline__ void load(const Src &src, int64_t i0, int64_t n, bool check) {
+    load_items(src, i0, n, check, m);
+  }
+  __device__ __forceinline__ void count(int32_t (&cnt)[C]) const {
+#pragma unroll
+    for (int j = 0; j < SI; ++j)
+#pragma unroll
+      for (int c = 0; c < C; ++c) cnt[c] += (m[j] >> c) & 1u;
+  }
+  template <class Emit>
+  __device__ __forceinline__ void emit(const Emit &em, int64_t i0, int64_t n,
+                                       int32_t (&run)[C]) const {
+    emit_items<C>(em, i0, n, m, run);
+  }
+};
+
 // Per scan tile and channel, the count of flagged entries (scan_passes(n) passes of STILE
 // entries; the passes' loads are independent).
 template <int C, class Src>
@@ -93,12 +115,9 @@ __global__ void __launch_bounds__(ST) k_scan_reduce(Src src, int64_t n, int32_t 
 #pragma unroll SR
   for (int r = 0; r < passes; ++r) {
     const int64_t i0 = (tile * passes + r) * STILE + (int64_t)threadIdx.x * SI;
-    unsigned m[SI];
-    load_items(src, i0, n, true, m);
-#pragma unroll
-    for (int j = 0; j < SI; ++j)
-#pragma unroll
-      for (int c = 0; c < C; ++c) cnt[c] += (m[j] >> c) & 1u;
+    ItemOps<C, Src> it;
+    it.load(src, i0, n, true);
+    it.count(cnt);
   }
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
 #pragma unroll
@@ -165,27 +184,21 @@ __global__ void __launch_bounds__(ST) k_scan_emit(Src src, Emit em, int64_t n,
   int32_t carry[C];
 #pragma unroll
   for (int c = 0; c < C; ++c) carry[c] = toff[c * ntiles + tile];
-  unsigned mn[SI];
+  ItemOps<C, Src> nx;
   {
     const int64_t p0 = tile * passes * STILE;
-    if (p0 < n) load_items(src, p0 + (int64_t)threadIdx.x * SI, n, false, mn);
+    if (p0 < n) nx.load(src, p0 + (int64_t)threadIdx.x * SI, n, false);
   }
   for (int r = 0; r < passes; ++r) {
     const int64_t p0 = (tile * passes + r) * STILE;
     if (p0 >= n) break;  // the same for the whole CTA
     const int64_t i0 = p0 + (int64_t)threadIdx.x * SI;
-    unsigned m[SI];
-#pragma unroll
-    for (int j = 0; j < SI; ++j) m[j] = mn[j];
-    if (r + 1 < passes && p0 + STILE < n)
-      load_items(src, p0 + STILE + (int64_t)threadIdx.x * SI, n, false, mn);
+    const ItemOps<C, Src> it = nx;
+    if (r + 1 < passes && p0 + STILE < n) nx.load(src, p0 + STILE + (int64_t)threadIdx.x * SI, n, false);
     int32_t cnt[C];
 #pragma unroll
     for (int c = 0; c < C; ++c) cnt[c] = 0;
-#pragma unroll
-    for (int j = 0; j < SI; ++j)
-#pragma unroll
-      for (int c = 0; c < C; ++c) cnt[c] += (m[j] >> c) & 1u;
+    it.count(cnt);
     int32_t pre[C];
     int32_t (&w)[C][ST / 32 + 1] = sw[r & 1];
     if (C <= 3) {
@@ -221,7 +234,7 @@ __global__ void __launch_bounds__(ST) k_scan_emit(Src src, Emit em, int64_t n,
     int32_t run[C];
 #pragma unroll
     for (int c = 0; c < C; ++c) run[c] = carry[c] + w[c][warp] + pre[c];
-    emit_items<C>(em, i0, n, m, run);
+    it.emit(em, i0, n, run);
 #pragma unroll
     for (int c = 0; c < C; ++c) carry[c] += w[c][ST / 32];
     // the next pass writes the other half of sw; the one after this half again, behind the
@@ -488,6 +501,62 @@ __device__ __forceinline__ void emit_items(const RankEmit &em, int64_t i0, int64
   }
 }
 
+// FlagSrc: the eight flag bytes of a thread (0 or 1 each) usually lie in one depth's segment;
+// then their count is the popcount of the two words and their exclusive ranks are the byte-wise
+// prefix sums (w * 0x01010101 holds the inclusive ones, at most 4 per byte: no carries).
+template <int C>
+struct ItemOps<C, FlagSrc> {
+  uint2 v;
+  int d;           // the depth of all eight entries, or -1 (another form: m)
+  unsigned m[SI];  // per-entry channel bits when d < 0
+  __device__ __forceinline__ void load(const FlagSrc &src, int64_t i0, int64_t n, bool) {
+    d = -1;
+    v = make_uint2(0u, 0u);
+    if (i0 + SI <= n) {
+      v = __ldg(reinterpret_cast<const uint2 *>(src.f + i0));
+      const int d0 = src.depth_of(i0), d1 = src.depth_of(i0 + SI - 1);
+      if (d0 == d1) {
+        d = d0;
+        return;
+      }
+    }
+    load_items(src, i0, n, false, m);
+  }
+  __device__ __forceinline__ void count(int32_t (&cnt)[C]) const {
+    if (d >= 0) {
+      const int32_t pc = __popc(v.x) + __popc(v.y);
+#pragma unroll
+      for (int c = 0; c < C; ++c) cnt[c] += c == d ? pc : 0;
+    } else {
+#pragma unroll
+      for (int j = 0; j < SI; ++j)
+#pragma unroll
+        for (int c = 0; c < C; ++c) cnt[c] += (m[j] >> c) & 1u;
+    }
+  }
+  __device__ __forceinline__ void emit(const RankEmit &em, int64_t i0, int64_t n,
+                                       int32_t (&run)[C]) const {
+    if (d < 0) {
+      emit_items<C>(em, i0, n, m, run);
+      return;
+    }
+    int32_t base = 0;
+#pragma unroll
+    for (int c = 0; c < C; ++c) base = c == d ? run[c] : base;
+    const uint32_t px = v.x * 0x01010101u, py = v.y * 0x01010101u;
+    const uint32_t ex = px - v.x, ey = py - v.y;
+    const int32_t tx = (int32_t)(px >> 24), ty = (int32_t)(py >> 24);
+    int4 *dst = reinterpret_cast<int4 *>(em.rank + i0);
+    dst[0] = make_int4(base + (int32_t)(ex & 0xffu), base + (int32_t)((ex >> 8) & 0xffu),
+                       base + (int32_t)((ex >> 16) & 0xffu), base + (int32_t)(ex >> 24));
+    const int32_t b1 = base + tx;
+    dst[1] = make_int4(b1 + (int32_t)(ey & 0xffu), b1 + (int32_t)((ey >> 8) & 0xffu),
+                       b1 + (int32_t)((ey >> 16) & 0xffu), b1 + (int32_t)(ey >> 24));
+#pragma unroll
+    for (int c = 0; c < C; ++c) run[c] += c == d ? tx + ty : 0;
+  }
+};
+
 // Flags of depth d from those of depth d+1: node p is kept iff one of its children
 // ptr[p] .. ptr[p+1]-1 (at flags[coff + child]) is.  One warp per node; each lane tests 16
 // flags per 16-byte load (512 per warp step, from the 16-byte boundary below the range) and
@@ -506,11 +575,19 @@ __global__ void k_mark_parents(const int32_t *__restrict__ ptr, int64_t n,
       bool hit = false;
       if (c < hi) {
         const uint4 v = __ldg(reinterpret_cast<const uint4 *>(flags + c));
-        const uint32_t w[4] = {v.x, v.y, v.z, v.w};
+        // the bytes [s, e) of the 16 loaded lie in the child range; two 8-byte halves, each
+        // masked to its part of the range
+        const int s = lo > c ? (int)(lo - c) : 0, e = hi < c + 16 ? (int)(hi - c) : 16;
+        const uint64_t w[2] = {(uint64_t)v.x | ((uint64_t)v.y << 32),
+                               (uint64_t)v.z | ((uint64_t)v.w << 32)};
 #pragma unroll
-        for (int q = 0; q < 16; ++q) {
-          const int64_t e = c + q;
-          hit = hit || (e >= lo && e < hi && ((w[q >> 2] >> (8 * (q & 3))) & 0xffu) != 0);
+        for (int h = 0; h < 2; ++h) {
+          const int sh = s - 8 * h < 0 ? 0 : (s - 8 * h > 8 ? 8 : s - 8 * h);
+          const int eh = e - 8 * h < 0 ? 0 : (e - 8 * h > 8 ? 8 : e - 8 * h);
+          const int width = eh > sh ? eh - sh : 0;
+          const uint64_t m =
+              width <= 0 ? 0ull : (width >= 8 ? ~0ull : ((1ull << (8 * width)) - 1ull)) << (8 * sh);
+          hit = hit || (w[h] & m) != 0ull;
         }
       }
       if (__any_sync(0xffffffffu, hit)) {

@@ -137,7 +137,13 @@ typedef struct {
                             * final boxes are then several trees, joined by vx_result_csf while
                             * they fit one.  VX_EOVERFLOW when one slab alone exceeds it.  Not
                             * with c1 (whose inclusion step keeps levels whole) */
-  int32_t reserved;
+  int32_t first_level; /* 0 = off; on the interval form (taylor_order 0, c1 0): Algorithm 3 starts
+                        * from the full grid of level min(first_level, depth) instead of level 0.
+                        * The final boxes are the same (C0 on interval Horner is inclusion-isotone
+                        * over exact grids, so pruning the coarser levels changes no final box);
+                        * the levels before it are not evaluated (zero in vx_result_stats) and the
+                        * start level tests its whole grid.  For levels that keep nearly every box,
+                        * whose launches cost more than their few boxes */
 } vx_opts;
 
 /* Thread-local message of the last failed call on this thread ("" if none). */

@@ -358,19 +358,6 @@ __global__ void k_encode_coefs(const double2 *__restrict__ c64, int64_t n, float
   }
 }
 
-// The stage-0 block fibre-major: entry a of fibre f (row-major at rowoff[a] + f) to
-// fiboff[f] + a.
-__global__ void k_fibre_major(const float4 *__restrict__ rm, const int32_t *__restrict__ rowoff,
-                              const int32_t *__restrict__ fiblen,
-                              const int32_t *__restrict__ fiboff, int32_t nfib,
-                              float4 *__restrict__ fm) {
-  const int stride = (int)(gridDim.x * blockDim.x);
-  for (int f = (int)(blockIdx.x * blockDim.x + threadIdx.x); f < nfib; f += stride) {
-    const int L = fiblen[f], o = fiboff[f];
-    for (int a = 0; a < L; ++a) fm[o + a] = rm[rowoff[a] + f];
-  }
-}
-
 // chi (nullable): upper ends of interval coefficients [p.coefs[t], chi[t]]
 // Host threads kept for the process (one per core but this one's, at most 15): run(n, fn)
 // calls fn(c) for c = 0..n-1 on them and on the calling thread and returns when all are done.
@@ -953,7 +940,7 @@ static int system_create_impl(const vx_poly *F, int32_t npoly, const double *con
   size_t bytes = 0;
   for (int f = 0; f < npoly; ++f) {
     bytes += al(hp[f].c64.size() * sizeof(double2)) + al(hp[f].c64.size() * sizeof(float2)) +
-             3 * al(hp[f].c64.size() * sizeof(float4)) + al(hp[f].c64.size() * sizeof(float));
+             2 * al(hp[f].c64.size() * sizeof(float4)) + al(hp[f].c64.size() * sizeof(float));
     for (int s = 0; s < k; ++s) {
       const HostStage &S = hp[f].st[s];
       bytes += al((S.maxlen + 1) * 4) + 3 * al((size_t)S.nfib * 4) + al(((size_t)S.nfib + 1) * 4);
@@ -1042,7 +1029,6 @@ static int system_create_impl(const vx_poly *F, int32_t npoly, const double *con
     PolyDev &P = sys->dev.p[f];
     P.c32 = (const float2 *)reserve(hp[f].c64.size() * sizeof(float2));
     P.c32c = (const float4 *)reserve(hp[f].c64.size() * sizeof(float4));
-    P.c32c_fm = (const float4 *)reserve(hp[f].c64.size() * sizeof(float4));
     P.cp = (const float4 *)reserve(hp[f].c64.size() * sizeof(float4));
     P.ep = (const float *)reserve(hp[f].c64.size() * sizeof(float));
   }
@@ -1058,14 +1044,6 @@ static int system_create_impl(const vx_poly *F, int32_t npoly, const double *con
                                                  const_cast<float *>(sys->dev.p[f].ep));
     note_launch();
     e = cudaGetLastError();
-    if (e == cudaSuccess) {
-      const StageDev &S0 = sys->dev.p[f].st[0];
-      k_fibre_major<<<(unsigned)std::min<int64_t>((S0.nfib + 127) / 128, (int64_t)sm_count() * 8),
-                      128, 0, s>>>(sys->dev.p[f].c32c, S0.rowoff, S0.fiblen, S0.fiboff, S0.nfib,
-                                   const_cast<float4 *>(sys->dev.p[f].c32c_fm));
-      note_launch();
-      e = cudaGetLastError();
-    }
   }
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);
   pinned_put(hstage, hcap);  // the copy has completed (or failed): the buffer is free again
@@ -2110,6 +2088,20 @@ static int enclose_impl(const vx_system *sys, const double *dom, int depth, cons
       return VX_EINVAL;
     }
   }
+  if (opts.first_level < 0 || (opts.first_level > 0 && (opts.taylor_order != 0 || opts.c1 != 0))) {
+    set_error("vx_enclose: first_level %d needs the interval form (no Taylor form, no C1)",
+              opts.first_level);
+    return VX_EINVAL;
+  }
+  if (opts.first_level > 0) {
+    int64_t n = 1;
+    for (int i = 0; i < k; ++i) n <<= std::min<int>(opts.first_level, depth);
+    if (n > INT32_MAX) {
+      set_error("vx_enclose: the full grid of level %d has more than 2^31 - 1 boxes",
+                opts.first_level);
+      return VX_EINVAL;
+    }
+  }
   if (opts.recheck_last != 0 &&
       (opts.mode != VX_FP32 || opts.taylor_order != 0 || opts.c1 != 0)) {
     // the Taylor form is centred on each box, hence not inclusion-isotone across levels
@@ -2146,6 +2138,11 @@ static int enclose_impl(const vx_system *sys, const double *dom, int depth, cons
       l0 = start->v.level;
       rc = csf_copy(*start, s, &cur);
     }
+  } else if (opts.first_level > 0) {
+    // Algorithm 3 from the full grid of level first_level: the coarser levels' pruning does
+    // not change the final boxes (C0 on interval Horner is inclusion-isotone over exact grids)
+    l0 = std::min<int>(opts.first_level, depth);
+    rc = csf_full_grid_dev(k, l0, s, &cur);
   } else {
     rc = level0(k, s, &cur);
   }

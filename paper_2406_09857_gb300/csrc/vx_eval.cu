@@ -1114,15 +1114,14 @@ __global__ void __launch_bounds__(512)
     k_stage_tma_c(const StageDev st, const int32_t *__restrict__ lab,
                   const int32_t *__restrict__ pptr, const float4 *__restrict__ in,
                   float4 *__restrict__ out, int64_t out_estride, int64_t out_nstride, int G,
-                  AxisGrid g, int64_t nroot = 0) {
+                  AxisGrid g) {
   extern __shared__ __align__(128) unsigned char smem[];
   uint64_t *bar = reinterpret_cast<uint64_t *>(smem);
   float4 *s_blk = reinterpret_cast<float4 *>(smem + 128);
   const int64_t p = blockIdx.x / G;
   const StageGroup r = stage_group<16>(st, (int)(blockIdx.x % G), G);
   if (r.fb >= r.fe) return;  // an empty group (the same for the whole CTA)
-  // pptr null: stage 0, the nroot depth-0 nodes under one parent, the coefficient block
-  const int64_t c0 = pptr ? __ldg(pptr + p) : 0, c1 = pptr ? __ldg(pptr + p + 1) : nroot;
+  const int64_t c0 = __ldg(pptr + p), c1 = __ldg(pptr + p + 1);
   if (threadIdx.x == 0) stage_group_copy(in, p, st.blk_in, r, bar, s_blk);
   __syncthreads();
   if (!mbar_wait_bounded(bar, 0)) return;
@@ -1718,8 +1717,7 @@ int eval_level_t(const SysDev &sys, const CsfView &c, const LevelGrid &grid, dou
       // to 16-byte boundaries must stay inside its block
       const bool aligned = (st.blk_in * (int64_t)sizeof(V)) % 16 == 0 &&
                            (reinterpret_cast<uintptr_t>(buf[f][d - 1]) & 15u) == 0;
-      if (aligned && c.N[d] >= (int64_t)sm_count() * 4 * kThreads && c.N[d] >= 128 * c.N[d - 1])
-        tma[d] = true;
+      if (aligned && c.N[d] >= 16384 && c.N[d] >= 128 * c.N[d - 1]) tma[d] = true;
     }
     for (int d = 0; d + 1 < k && rc == VX_OK; ++d) {
       // a stage whose consumer stages its parents' blocks writes them fibre-major
@@ -1789,44 +1787,20 @@ int eval_level_t(const SysDev &sys, const CsfView &c, const LevelGrid &grid, dou
         // fibre groups: enough warps to fill the GPU several times over (a warp takes 32
         // nodes; 64 in the certified binary32 arithmetic when the depth has enough nodes for
         // the shared loads to pay).  Variants: 0 the heuristic, 1 the other node count per
-        // warp (certified binary32), 2 four times the fibre groups, 3 (certified binary32,
-        // stage 0) k_stage_tma_c on the fibre-major coefficient block as the one parent of
-        // every depth-0 node, a CTA per fibre group (a Horner step then waits on shared memory,
-        // not on the L2: stage 0 has few nodes, so its time is the latency of its longest
-        // fibres)
+        // warp (certified binary32), 2 four times the fibre groups, 3 (certified binary32)
+        // sixteen times (stages with few nodes, such as stage 0, wait on their fibres' loads:
+        // more warps hide more of that latency)
         const bool pairs0 = std::is_same<AR, A32C>::value &&
                             (c.N[d] >= kPairNodes || st.blk_in - st.nfib >= kPairNodes);
-        const bool root_staged = std::is_same<AR, A32C>::value && d == 0;
-        if (root_staged &&
-            cudaFuncSetAttribute(k_stage_tma_c, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)kMaxDynSmem) != cudaSuccess) {
-          set_error("cudaFuncSetAttribute(shared memory %zu) failed", kMaxDynSmem);
-          rc = VX_ECUDA;
-          break;
-        }
         const int64_t in_estride = d == 0 ? 1 : (tma_input_node_major(d, k, tma) ? 1 : c.N[d - 1]);
         const int64_t in_nstride = d == 0 ? 0 : (tma_input_node_major(d, k, tma) ? st.blk_in : 1);
         auto launch = [&](int vv) -> int {
           const int v = std::is_same<AR, A32C>::value ? vv : (vv == 1 ? 2 : 0);
-          if (v == 3) {
-            const int64_t n0 = c.N[0];
-            const int threads = n0 >= 1024 ? 512 : (n0 >= 512 ? 256 : 128);
-            const int64_t gsm = ((int64_t)(st.blk_in * sizeof(float4)) + kStageGroupBytes - 1) /
-                                kStageGroupBytes;
-            int64_t G = std::max<int64_t>((int64_t)sm_count() * 8, gsm);
-            if (G > st.nfib) G = st.nfib;
-            const size_t sm = (size_t)128 + (size_t)((st.blk_in + G - 1) / G + st.maxlen + 2) * sizeof(float4);
-            k_stage_tma_c<<<(unsigned)G, threads, sm, s>>>(
-                st, c.lab[0], nullptr, sys.p[f].c32c_fm, (float4 *)buf[f][0], oe, on, (int)G,
-                pg.ax[0], n0);
-            note_launch();
-            VX_LAUNCH_CHECK();
-            return VX_OK;
-          }
+          const int64_t G_mult = v == 3 ? 16 : (v == 2 ? 4 : 1);
           const bool pairs = v == 1 ? !pairs0 : pairs0;
           const int64_t per_warp = pairs ? 64 : 32;
           const int64_t nchunk = (c.N[d] + per_warp - 1) / per_warp;
-          const int64_t target = (int64_t)sm_count() * 64 * (v == 2 ? 4 : 1);
+          const int64_t target = (int64_t)sm_count() * 64 * G_mult;
           int64_t G = (target + nchunk - 1) / nchunk;
           if (G > st.nfib) G = st.nfib;
           if (G < 1) G = 1;
@@ -1846,7 +1820,7 @@ int eval_level_t(const SysDev &sys, const CsfView &c, const LevelGrid &grid, dou
         };
         rc = tuned_launch(tune_key(2, arith, d, c.N[d], d > 0 ? c.N[d - 1] : 0, st.maxlen,
                                    st.nfib),
-                          root_staged ? 4 : (std::is_same<AR, A32C>::value ? 3 : 2), s, launch);
+                          std::is_same<AR, A32C>::value ? 4 : 2, s, launch);
       }
       if (rc != VX_OK) break;
       if (tm && tm->on) rc = tm->end();

@@ -76,7 +76,6 @@ struct PolyDev {
   const double2 *c64;  // stage-0 input block as degenerate intervals (lo = hi = coefficient)
   const float2 *c32;   // stage-0 input block as <m, r> binary32 midpoint-radius pairs
   const float4 *c32c;  // stage-0 input block as binary32 [RD(c), RU(c)] with error bound
-  const float4 *c32c_fm;  // the same fibre-major (st[0].fiboff), for the staged stage 0
   const float4 *cp;    // stage-0 input block as float pairs (lo_h, lo_l, -hi_h, -hi_l) ...
   const float *ep;     // ... and their error bounds (eval_level_pair)
 };

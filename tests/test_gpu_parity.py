@@ -709,3 +709,24 @@ def test_enclose_in_x1_ranges_equals_oracle(vx, name, cap, mode_name, recheck_la
     codes = res.box_codes()
     assert np.array_equal(vx.Result.decode_codes(codes, k, depth), ref["tuples"])
     assert np.array_equal(res.csf().tuples().cpu().numpy(), ref["tuples"])
+
+
+@pytest.mark.parametrize("name,first", [("k3-d6-2polys", 3), ("plain-k2-d20-depth8", 5),
+                                        ("k4-d3", 2), ("surface-d12", 4)])
+def test_enclose_from_full_grid_level_equals_oracle(vx, name, first):
+    """opts.first_level: Algorithm 3 from the full grid of a level gives the oracle's boxes (the
+    coarser levels' pruning changes no final box); the levels before it are not evaluated and
+    the start level tests its whole grid."""
+    polys, dom, depth = ENCLOSE_CASES[name]()
+    ref = oracle.enclose(polys, dom, depth)
+    k = ref["tuples"].shape[1]
+    for mode_name, rl in (("FP64", False), ("FP32", True), ("FP32", False)):
+        o = vx.make_opts(getattr(vx, mode_name), recheck_last=rl, first_level=first)
+        res = vx.enclose(polys, dom, depth, o)
+        st = res.stats()
+        assert np.array_equal(res.boxes(), ref["tuples"]), mode_name
+        assert np.all(st["tested"][:first] == 0)
+        assert st["tested"][first] == 1 << (k * first)
+        assert st["kept"][-1] == ref["kept"][-1]
+        if not rl:
+            assert np.array_equal(st["kept"][first + 1:], ref["kept"][first + 1:])

@@ -952,6 +952,11 @@ def run_gpu(args):
     ne2e = max(1, min(args.steps, 5))
     torch.cuda.synchronize()
     barrier()
+    # no collector pauses of the Python harness inside the timed calls (as timeit does)
+    import gc
+
+    gc.collect()
+    gc.disable()
     w0 = time.perf_counter()
     e2e_evals, d2h, h2d, e2e_ms = 0, 0, 0, []
     for _ in range(ne2e):
@@ -964,7 +969,9 @@ def run_gpu(args):
         h2d += hb
         r.free()
     torch.cuda.synchronize()
-    e2e_s = reduce(time.perf_counter() - w0, torch.distributed.ReduceOp.MAX if world > 1 else None)
+    e2e_wall = time.perf_counter() - w0
+    gc.enable()
+    e2e_s = reduce(e2e_wall, torch.distributed.ReduceOp.MAX if world > 1 else None)
     e2e_evals = reduce(e2e_evals, torch.distributed.ReduceOp.SUM if world > 1 else None)
     e2e = {"value": e2e_evals / e2e_s, "unit": UNIT, "h2d_bytes_per_step": h2d // ne2e,
            "d2h_bytes_per_step": d2h // ne2e, "steps": ne2e,

@@ -633,7 +633,7 @@ __device__ __forceinline__ float4 negated(float4 A) { return make_float4(A.y, A.
 struct YPair {
   float2 l0, h0, l1, h1;  // (yl, yl) and (yh, yh) of leaf 0 and leaf 1
   float2 xm;              // (xmaxp of leaf 0, xmaxp of leaf 1)
-  float2 xb;              // (xb of leaf 0, xb of leaf 1)
+  float xb;               // max(xb of leaf 0, xb of leaf 1): the pair's summed-bound multiplier
   bool neg0, neg1;
 };
 
@@ -644,7 +644,7 @@ __device__ __forceinline__ YPair ypair(const YLeaf &a, const YLeaf &b) {
   y.l1 = make_float2(b.yl, b.yl);
   y.h1 = make_float2(b.yh, b.yh);
   y.xm = make_float2(a.xmaxp, b.xmaxp);
-  y.xb = make_float2(a.xb, b.xb);
+  y.xb = fmaxf(a.xb, b.xb);
   y.neg0 = a.neg;
   y.neg1 = b.neg;
   return y;
@@ -654,11 +654,16 @@ __device__ __forceinline__ YPair ypair(const YLeaf &a, const YLeaf &b) {
 // in y = -x on the coefficients (-1)^a A_a, the state being (-1)^a J_a (exact: interval
 // negation swaps the pair (lo, -hi), and the products are the same reals).  SW = 0 takes the
 // entry as it is, 1 negated for both leaves (a pair swap), 2 negated per leaf where sw0 / sw1.
+// OSW: the chains hold -J (the pair (-hi, lo)), so that J_a = (-J_{a+1}) y + A_a takes every
+// entry as it is, and the step writes its two minima in swapped order (the same products and
+// roundings as SW = 1 on the odd entries, without moving the entry's pair).
 // Each end is the min of two paired FMAs rounded to nearest; the bounds follow A32C::step's
 // recursion, both leaves' in one paired FMA pair.
-// BF: the entry's .z/.w hold the summed bound B of leaf_bform, and the bound advances as
-// e = RU(e xb + B) (one paired FMA for both leaves, no magnitude of the step's result).
-template <int SW, bool BF = false>
+// BF: the entry's .z/.w hold the summed bound B of leaf_bform, and one bound serves both
+// leaves: e = RU(e xb + B) with xb the larger of their multipliers (every term of the
+// recursion is >= 0 and RU is monotone, so it bounds each leaf's own recursion), one FMA per
+// step and no magnitude of the step's result.  The bound lives in e.x (e.y is not used).
+template <int SW, bool BF = false, bool OSW = false>
 __device__ __forceinline__ void step_y2(float2 &j0, float2 &j1, float2 &e, const YPair &y,
                                         const float4 &A, bool sw0, bool sw1) {
   float2 c0, c1;
@@ -672,10 +677,15 @@ __device__ __forceinline__ void step_y2(float2 &j0, float2 &j1, float2 &e, const
   }
   const float2 P0 = __ffma2_rn(j0, y.l0, c0), Q0 = __ffma2_rn(j0, y.h0, c0);
   const float2 P1 = __ffma2_rn(j1, y.l1, c1), Q1 = __ffma2_rn(j1, y.h1, c1);
-  j0 = make_float2(fminf(P0.x, Q0.x), fminf(P0.y, Q0.y));
-  j1 = make_float2(fminf(P1.x, Q1.x), fminf(P1.y, Q1.y));
+  if (OSW) {
+    j0 = make_float2(fminf(P0.y, Q0.y), fminf(P0.x, Q0.x));
+    j1 = make_float2(fminf(P1.y, Q1.y), fminf(P1.x, Q1.x));
+  } else {
+    j0 = make_float2(fminf(P0.x, Q0.x), fminf(P0.y, Q0.y));
+    j1 = make_float2(fminf(P1.x, Q1.x), fminf(P1.y, Q1.y));
+  }
   if (BF) {
-    e = __ffma2_ru(e, y.xb, make_float2(A.z, A.w));
+    e.x = __fmaf_ru(e.x, y.xb, A.z);
   } else {
     const float2 m =
         make_float2(fmaxf(fabsf(j0.x), fabsf(j0.y)), fmaxf(fabsf(j1.x), fabsf(j1.y)));
@@ -683,11 +693,33 @@ __device__ __forceinline__ void step_y2(float2 &j0, float2 &j1, float2 &e, const
   }
 }
 
-// SGN: +1 no leaf negated, -1 both negated (warp-uniform cases), 0 per leaf at run time.
+// SGN: +1 no leaf negated, -1 both negated (warp-uniform cases: SGN = -1 runs the chains as
+// -J, OSW), 0 per leaf at run time (odd entries swapped per leaf).
 template <int SGN>
 struct SwapOdd {
-  static constexpr int value = SGN > 0 ? 0 : (SGN < 0 ? 1 : 2);
+  static constexpr int value = SGN == 0 ? 2 : 0;
+  static constexpr bool osw = SGN < 0;
 };
+
+// The chain's first state from its top entry A_{L-1}: J (or -J under OSW), for each leaf.
+template <int SGN>
+__device__ __forceinline__ void top_state(const float4 &A, bool top_odd, const YPair &y,
+                                          float2 &j0, float2 &j1) {
+  if (SwapOdd<SGN>::osw) {
+    j0 = j1 = make_float2(A.y, A.x);
+  } else {
+    const float4 A0 = (top_odd && y.neg0) ? negated(A) : A;
+    const float4 A1 = (top_odd && y.neg1) ? negated(A) : A;
+    j0 = make_float2(A0.x, A0.y);
+    j1 = make_float2(A1.x, A1.y);
+  }
+}
+
+// The chain's value at a = 0 as the entry (lo, -hi, bound, bound).
+template <int SGN>
+__device__ __forceinline__ float4 chain_out(const float2 &j, float e) {
+  return SwapOdd<SGN>::osw ? make_float4(j.y, j.x, e, e) : make_float4(j.x, j.y, e, e);
+}
 
 // Horner of NP polynomials of one length L on the leaves of y (one parent): chain f of leaf c
 // is (-1)^a J_a (equal to J_a when the leaf is not negated).  Odd entries are negated for a
@@ -696,21 +728,20 @@ template <int NP, int SGN, bool BF = false>
 __device__ __forceinline__ void horner_y2(const float4 *const (&b)[2], int L, const YPair &y,
                                           float4 (&K0)[2], float4 (&K1)[2]) {
   constexpr int SWO = SwapOdd<SGN>::value;
+  constexpr bool OSW = SwapOdd<SGN>::osw;
   const bool top_odd = (L - 1) & 1;
   float2 j0[NP], j1[NP], e[NP];
 #pragma unroll
   for (int f = 0; f < NP; ++f) {
     const float4 A = b[f][L - 1];
-    const float4 A0 = (top_odd && y.neg0) ? negated(A) : A;
-    const float4 A1 = (top_odd && y.neg1) ? negated(A) : A;
-    j0[f] = make_float2(A0.x, A0.y);
-    j1[f] = make_float2(A1.x, A1.y);
+    top_state<SGN>(A, top_odd, y, j0[f], j1[f]);
     e[f] = make_float2(A.z, A.w);
   }
   int a = L - 2;
   if (a >= 0 && !(a & 1)) {
 #pragma unroll
-    for (int f = 0; f < NP; ++f) step_y2<0, BF>(j0[f], j1[f], e[f], y, b[f][a], false, false);
+    for (int f = 0; f < NP; ++f)
+      step_y2<0, BF, OSW>(j0[f], j1[f], e[f], y, b[f][a], false, false);
     --a;
   }
   // two (odd, even) pairs per trip: half the loop and address overhead per step
@@ -725,8 +756,8 @@ __device__ __forceinline__ void horner_y2(const float4 *const (&b)[2], int L, co
       }
 #pragma unroll
       for (int f = 0; f < NP; ++f) {
-        step_y2<SWO, BF>(j0[f], j1[f], e[f], y, A[f], y.neg0, y.neg1);
-        step_y2<0, BF>(j0[f], j1[f], e[f], y, B[f], false, false);
+        step_y2<SWO, BF, OSW>(j0[f], j1[f], e[f], y, A[f], y.neg0, y.neg1);
+        step_y2<0, BF, OSW>(j0[f], j1[f], e[f], y, B[f], false, false);
       }
     }
   }
@@ -739,14 +770,14 @@ __device__ __forceinline__ void horner_y2(const float4 *const (&b)[2], int L, co
     }
 #pragma unroll
     for (int f = 0; f < NP; ++f) {
-      step_y2<SWO, BF>(j0[f], j1[f], e[f], y, A[f], y.neg0, y.neg1);
-      step_y2<0, BF>(j0[f], j1[f], e[f], y, B[f], false, false);
+      step_y2<SWO, BF, OSW>(j0[f], j1[f], e[f], y, A[f], y.neg0, y.neg1);
+      step_y2<0, BF, OSW>(j0[f], j1[f], e[f], y, B[f], false, false);
     }
   }
 #pragma unroll
   for (int f = 0; f < NP; ++f) {
-    K0[f] = make_float4(j0[f].x, j0[f].y, e[f].x, e[f].x);
-    K1[f] = make_float4(j1[f].x, j1[f].y, e[f].y, e[f].y);
+    K0[f] = chain_out<SGN>(j0[f], e[f].x);
+    K1[f] = chain_out<SGN>(j1[f], BF ? e[f].x : e[f].y);
   }
 }
 
@@ -757,20 +788,18 @@ __device__ __forceinline__ void horner_y2_fibre(const float4 *__restrict__ base,
                                                 const int32_t *rowoff, int f, int L,
                                                 const YPair &y, float4 &K0, float4 &K1) {
   constexpr int SWO = SwapOdd<SGN>::value;
+  constexpr bool OSW = SwapOdd<SGN>::osw;
   auto ent = [&](int a) { return base[(int64_t)(rowoff[a] + f) * estride]; };
   const bool top_odd = (L - 1) & 1;
   float2 j0, j1, e;
   {
     const float4 A = ent(L - 1);
-    const float4 A0 = (top_odd && y.neg0) ? negated(A) : A;
-    const float4 A1 = (top_odd && y.neg1) ? negated(A) : A;
-    j0 = make_float2(A0.x, A0.y);
-    j1 = make_float2(A1.x, A1.y);
+    top_state<SGN>(A, top_odd, y, j0, j1);
     e = make_float2(A.z, A.w);
   }
   int a = L - 2;
   if (a >= 0 && !(a & 1)) {
-    step_y2<0>(j0, j1, e, y, ent(a), false, false);
+    step_y2<0, false, OSW>(j0, j1, e, y, ent(a), false, false);
     --a;
   }
   float4 An = make_float4(0.f, 0.f, 0.f, 0.f), Bn = An;
@@ -784,11 +813,11 @@ __device__ __forceinline__ void horner_y2_fibre(const float4 *__restrict__ base,
       An = ent(a - 2);
       Bn = ent(a - 3);
     }
-    step_y2<SWO>(j0, j1, e, y, A, y.neg0, y.neg1);
-    step_y2<0>(j0, j1, e, y, B, false, false);
+    step_y2<SWO, false, OSW>(j0, j1, e, y, A, y.neg0, y.neg1);
+    step_y2<0, false, OSW>(j0, j1, e, y, B, false, false);
   }
-  K0 = make_float4(j0.x, j0.y, e.x, e.x);
-  K1 = make_float4(j1.x, j1.y, e.y, e.y);
+  K0 = chain_out<SGN>(j0, e.x);
+  K1 = chain_out<SGN>(j1, e.y);
 }
 
 // The warp-uniform sign case of a leaf pair: +1 no lane negated, -1 all negated, 0 mixed.
@@ -1231,20 +1260,40 @@ __device__ __forceinline__ void leaf_pair_eval(const LeafArgs &A, int fb, int fe
       decide(f, 1, K1[0]);
     }
   } else {
+    // the leaf index c is a run-time value here: decisions go to a pair of registers, not to
+    // ex[c] / am[c] (a dynamically indexed array would live in local memory)
 #pragma unroll 1
     for (int c = 0; c < 2; ++c) {
       const A32C::X &x = c == 0 ? x0 : x1;
       const int64_t p = c == 0 ? p0 : p1;
+      bool e1 = false, a1 = false;
+      auto decide1 = [&](int f, const V &J) {
+        if (lo && live && (c == 0 || two)) {
+          const int64_t i = c == 0 ? i0 : i1;
+          lo[(int64_t)f * nleaves + i] = A32C::lo(J);
+          hi[(int64_t)f * nleaves + i] = A32C::hi(J);
+        }
+        const int r = A32C::classify(J, A.rel[f]);
+        e1 = e1 || r == 0;
+        a1 = a1 || r == 2;
+      };
       int f = fb;
       if (NPMAX == 2) {
         for (; f + 1 < fe && A.len[f] == A.len[f + 1]; f += 2) {
           V J0, J1;
           horner1x2_any<A32C>(src(f, p), src(f + 1, p), A.len[f], x, J0, J1);
-          decide(f, c, J0);
-          decide(f + 1, c, J1);
+          decide1(f, J0);
+          decide1(f + 1, J1);
         }
       }
-      for (; f < fe; ++f) decide(f, c, horner1_any<A32C>(src(f, p), 1, A.len[f], x));
+      for (; f < fe; ++f) decide1(f, horner1_any<A32C>(src(f, p), 1, A.len[f], x));
+      if (c == 0) {
+        ex[0] = ex[0] || e1;
+        am[0] = am[0] || a1;
+      } else {
+        ex[1] = ex[1] || e1;
+        am[1] = am[1] || a1;
+      }
     }
   }
 }

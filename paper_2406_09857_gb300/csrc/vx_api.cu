@@ -2257,18 +2257,59 @@ namespace {
 __global__ void k_tree_mask(const uint8_t *__restrict__ keep, const int64_t *__restrict__ offl,
                             int S, const int32_t *__restrict__ tdepth, int l, int mode,
                             int64_t n, uint8_t *__restrict__ out) {
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
-       i += (int64_t)gridDim.x * blockDim.x) {
-    int lo = 0, hi = S;
-    while (hi - lo > 1) {
-      const int mid = (lo + hi) >> 1;
-      if (offl[mid] <= i) lo = mid; else hi = mid;
+  // 16 consecutive leaves per thread: one search for the tree of the first, then a walk
+  // forward over the trees' boundaries (offl ascending)
+  const int64_t nchunk = (n + 15) >> 4;
+  for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < nchunk;
+       q += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t i0 = q << 4, i1 = i0 + 16 < n ? i0 + 16 : n;
+    int t = 0, hi = S;
+    while (hi - t > 1) {
+      const int mid = (t + hi) >> 1;
+      if (__ldg(offl + mid) <= i0) t = mid; else hi = mid;
     }
-    const int dep = tdepth[lo];
-    if (mode == 0) out[i] = (keep[i] && dep == l) ? 1 : 0;
-    else if (mode == 1) out[i] = (keep[i] && dep > l) ? 1 : 0;
-    else if (mode == 2) out[i] = (out[i] || (keep[i] && dep == l)) ? 1 : 0;
-    else out[i] = (out[i] && dep == l) ? 1 : 0;
+    int64_t tend = __ldg(offl + t + 1);
+    // a full chunk of 16-byte aligned arrays moves as one 16-byte load / store
+    const bool full =
+        i1 - i0 == 16 && ((reinterpret_cast<uintptr_t>(keep) | reinterpret_cast<uintptr_t>(out)) & 15) == 0;
+    if (full && i1 <= tend) {  // the whole chunk in tree t: one test, bytewise 0/1 logic
+      const int dep = __ldg(tdepth + t);
+      const bool c = mode == 1 ? dep > l : dep == l;
+      const uint4 kv4 = *reinterpret_cast<const uint4 *>(keep + i0);
+      uint4 r = make_uint4(0u, 0u, 0u, 0u);
+      if (mode == 0 || mode == 1) {
+        if (c) r = kv4;
+      } else {
+        const uint4 ov4 = *reinterpret_cast<const uint4 *>(out + i0);
+        if (mode == 2)
+          r = c ? make_uint4(ov4.x | kv4.x, ov4.y | kv4.y, ov4.z | kv4.z, ov4.w | kv4.w) : ov4;
+        else if (c)
+          r = ov4;
+      }
+      *reinterpret_cast<uint4 *>(out + i0) = r;
+      continue;
+    }
+    alignas(16) uint8_t kv[16], ov[16];
+    if (full) {
+      *reinterpret_cast<uint4 *>(kv) = *reinterpret_cast<const uint4 *>(keep + i0);
+      if (mode >= 2) *reinterpret_cast<uint4 *>(ov) = *reinterpret_cast<const uint4 *>(out + i0);
+    }
+#pragma unroll
+    for (int j = 0; j < 16; ++j) {
+      const int64_t i = i0 + j;
+      if (i >= i1) break;
+      while (i >= tend && t + 1 < S) tend = __ldg(offl + (++t) + 1);
+      const int dep = __ldg(tdepth + t);
+      const bool kp = (full ? kv[j] : keep[i]) != 0;
+      const bool o = mode >= 2 && (full ? ov[j] : out[i]) != 0;
+      uint8_t r;
+      if (mode == 0) r = (kp && dep == l) ? 1 : 0;
+      else if (mode == 1) r = (kp && dep > l) ? 1 : 0;
+      else if (mode == 2) r = (o || (kp && dep == l)) ? 1 : 0;
+      else r = (o && dep == l) ? 1 : 0;
+      if (full) ov[j] = r; else out[i] = r;
+    }
+    if (full) *reinterpret_cast<uint4 *>(out + i0) = *reinterpret_cast<const uint4 *>(ov);
   }
 }
 
@@ -2306,6 +2347,30 @@ int dmalloc_copy_trees(ForestTree *d_trees, const std::vector<ForestTree> &ht, c
   // from pageable memory: returns once staged
   VX_CUDA(cudaMemcpyAsync(d_trees, ht.data(), sizeof(ForestTree) * ht.size(),
                           cudaMemcpyHostToDevice, s));
+  return VX_OK;
+}
+
+// The level's grids into the device trees (the systems' part of a tree does not change
+// between levels): the grids travel as one small array, a kernel puts them in place.
+__global__ void k_set_tree_grids(ForestTree *__restrict__ trees, const AxisGrid *__restrict__ ax,
+                                 int S) {
+  const int n = S * VX_KMAX;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
+    trees[i / VX_KMAX].ax[i % VX_KMAX] = ax[i];
+}
+
+int copy_tree_grids(ForestTree *d_trees, AxisGrid *d_ax, const std::vector<ForestTree> &ht,
+                    cudaStream_t s) {
+  std::vector<AxisGrid> ax(ht.size() * VX_KMAX);
+  for (size_t t = 0; t < ht.size(); ++t)
+    for (int d = 0; d < VX_KMAX; ++d) ax[t * VX_KMAX + d] = ht[t].ax[d];
+  // from pageable memory: returns once staged
+  VX_CUDA(cudaMemcpyAsync(d_ax, ax.data(), sizeof(AxisGrid) * ax.size(), cudaMemcpyHostToDevice,
+                          s));
+  const int S = (int)ht.size();
+  k_set_tree_grids<<<(S * VX_KMAX + 255) / 256, 256, 0, s>>>(d_trees, d_ax, S);
+  note_launch();
+  VX_CUDA(cudaGetLastError());
   return VX_OK;
 }
 
@@ -2413,9 +2478,11 @@ int batch_group(const std::vector<int32_t> &ids, const vx_poly *const *systems,
     for (int t = 0; t < S && rc == VX_OK; ++t) ht[t].dev = sysv[t]->dev;
   }
   ForestTree *d_trees = nullptr;
+  AxisGrid *d_ax = nullptr;
   int32_t *d_tdep = nullptr;
   int64_t *d_seg = nullptr;
   if (rc == VX_OK) rc = dmalloc((void **)&d_trees, sizeof(ForestTree) * S, s);
+  if (rc == VX_OK) rc = dmalloc((void **)&d_ax, sizeof(AxisGrid) * S * VX_KMAX, s);
   if (rc == VX_OK) rc = dmalloc((void **)&d_tdep, sizeof(int32_t) * S, s);
   if (rc == VX_OK) rc = dmalloc((void **)&d_seg, sizeof(int64_t) * (size_t)k * (S + 1), s);
   if (rc == VX_OK) {
@@ -2483,7 +2550,7 @@ int batch_group(const std::vector<int32_t> &ids, const vx_poly *const *systems,
       for (int d = 0; d < k; ++d) ht[t].ax[d] = g.ax[d];
     }
     if (rc != VX_OK || n == 0) break;
-    rc = dmalloc_copy_trees(d_trees, ht, s);
+    rc = l == 0 ? dmalloc_copy_trees(d_trees, ht, s) : copy_tree_grids(d_trees, d_ax, ht, s);
     uint8_t *keep = nullptr, *flag = nullptr, *m = nullptr;
     if (rc == VX_OK) rc = dmalloc((void **)&keep, (size_t)n, s);
     if (rc == VX_OK) rc = dmalloc((void **)&flag, (size_t)n, s);
@@ -2504,12 +2571,12 @@ int batch_group(const std::vector<int32_t> &ids, const vx_poly *const *systems,
     const bool recheck = (flagged && (!defer || any_final)) ||
                          (opts.mode == VX_FP32_MIDRAD && opts.fp64_final && any_final);
     if (rc == VX_OK && defer && any_final) {
-      k_tree_mask<<<grid1(n), 256, 0, s>>>(keep, cur.d_off + (int64_t)(k - 1) * (S + 1), S,
+      k_tree_mask<<<grid1((n + 15) / 16), 256, 0, s>>>(keep, cur.d_off + (int64_t)(k - 1) * (S + 1), S,
                                            d_tdep, l, 3, n, flag);
       note_launch();
     }
     if (rc == VX_OK && opts.mode == VX_FP32_MIDRAD && opts.fp64_final && any_final) {
-      k_tree_mask<<<grid1(n), 256, 0, s>>>(keep, cur.d_off + (int64_t)(k - 1) * (S + 1), S,
+      k_tree_mask<<<grid1((n + 15) / 16), 256, 0, s>>>(keep, cur.d_off + (int64_t)(k - 1) * (S + 1), S,
                                            d_tdep, l, 2, n, flag);
       note_launch();
     }
@@ -2554,7 +2621,7 @@ int batch_group(const std::vector<int32_t> &ids, const vx_poly *const *systems,
     // finishing trees: their kept boxes are the result, each tree's as a CSF of its own
     if (rc == VX_OK && any_final) {
       Forest fin;
-      k_tree_mask<<<grid1(n), 256, 0, s>>>(keep, cur.d_off + (int64_t)(k - 1) * (S + 1), S,
+      k_tree_mask<<<grid1((n + 15) / 16), 256, 0, s>>>(keep, cur.d_off + (int64_t)(k - 1) * (S + 1), S,
                                            d_tdep, l, 0, n, m);
       note_launch();
       rc = prune_forest(cur, m, 0, nullptr, k, S, d_seg, hseg, s, fin);
@@ -2581,7 +2648,7 @@ int batch_group(const std::vector<int32_t> &ids, const vx_poly *const *systems,
     // the others go on: bisect their kept boxes into the next level's forest
     Forest next;
     if (rc == VX_OK) {
-      k_tree_mask<<<grid1(n), 256, 0, s>>>(keep, cur.d_off + (int64_t)(k - 1) * (S + 1), S,
+      k_tree_mask<<<grid1((n + 15) / 16), 256, 0, s>>>(keep, cur.d_off + (int64_t)(k - 1) * (S + 1), S,
                                            d_tdep, l, 1, n, m);
       note_launch();
       if (any_cont) {
@@ -2623,6 +2690,7 @@ int batch_group(const std::vector<int32_t> &ids, const vx_poly *const *systems,
   if (ev1) cudaEventDestroy(ev1);
   dfree(d_seg, s);
   dfree(d_tdep, s);
+  dfree(d_ax, s);
   dfree(d_trees, s);
   if (cudaStreamSynchronize(s) != cudaSuccess && rc == VX_OK) rc = VX_ECUDA;
   for (int t = 0; t < S; ++t) vx_system_free(sysv[t]);

@@ -558,10 +558,13 @@ struct ItemOps<C, FlagSrc> {
 };
 
 // Flags of depth d from those of depth d+1: node p is kept iff one of its children
-// ptr[p] .. ptr[p+1]-1 (at flags[coff + child]) is.  One warp per node; each lane tests 16
-// flags per 16-byte load (512 per warp step, from the 16-byte boundary below the range) and
-// the warp stops at the first step holding a kept child.  flags is 256-byte aligned and has 16
-// bytes of padding after its last entry for the loads that run past a range's end.
+// ptr[p] .. ptr[p+1]-1 (at flags[coff + child]) is.  Three forms, by the mean number of
+// children per node.  flags is 256-byte aligned and has 16 bytes of padding after its last
+// entry for the loads that run past a range's end.
+//
+// Long child ranges: one warp per node; each lane tests 16 flags per 16-byte load (512 per
+// warp step, from the 16-byte boundary below the range) and the warp stops at the first step
+// holding a kept child.
 __global__ void k_mark_parents(const int32_t *__restrict__ ptr, int64_t n,
                                const uint8_t *__restrict__ flags, int64_t coff,
                                uint8_t *__restrict__ out) {
@@ -596,6 +599,49 @@ __global__ void k_mark_parents(const int32_t *__restrict__ ptr, int64_t n,
       }
     }
     if (lane == 0) out[p] = any ? 1 : 0;
+  }
+}
+
+
+// Short child ranges (a few children per node, as in the trees of small systems): one thread
+// per node, eight flag bytes per load from the 8-byte boundary below its
+// range (the 16 bytes of padding after the flags cover the last load).
+__global__ void k_mark_parents_t(const int32_t *__restrict__ ptr, int64_t n,
+                                 const uint8_t *__restrict__ flags, int64_t coff,
+                                 uint8_t *__restrict__ out) {
+  for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < n;
+       p += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t lo = coff + __ldg(ptr + p), hi = coff + __ldg(ptr + p + 1);
+    bool any = false;
+    for (int64_t b = lo & ~(int64_t)7; b < hi && !any; b += 8) {
+      const uint64_t w = __ldg(reinterpret_cast<const unsigned long long *>(flags + b));
+      const int sh = lo > b ? (int)(lo - b) : 0, eh = hi < b + 8 ? (int)(hi - b) : 8;
+      const int width = eh - sh;  // >= 1: b < hi and b + 8 > lo
+      const uint64_t m = (width >= 8 ? ~0ull : ((1ull << (8 * width)) - 1ull)) << (8 * sh);
+      any = (w & m) != 0ull;
+    }
+    out[p] = any ? 1 : 0;
+  }
+}
+
+// Child ranges of moderate length: from the children's side, out (zeroed before) gets 1 at the parent of every kept child.  Thread = one 16-byte
+// block of the flag array (absolute offsets, so the loads are aligned) over the children's
+// range [cs, ce); a block with a kept child reads those children's parent indices.  Several
+// threads may store the same 1 to one parent's byte.
+__global__ void k_mark_parents_s(const int32_t *__restrict__ cpar, int64_t cs, int64_t ce,
+                                 const uint8_t *__restrict__ flags, uint8_t *__restrict__ out) {
+  const int64_t q0 = cs >> 4, q1 = (ce + 15) >> 4;
+  for (int64_t q = q0 + (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < q1;
+       q += (int64_t)gridDim.x * blockDim.x) {
+    const uint4 v = __ldg(reinterpret_cast<const uint4 *>(flags) + q);
+    if ((v.x | v.y | v.z | v.w) == 0u) continue;
+    const uint32_t w[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+    for (int j = 0; j < 16; ++j) {
+      const int64_t a = 16 * q + j;
+      if (a < cs || a >= ce || ((w[j >> 2] >> (8 * (j & 3))) & 0xffu) == 0u) continue;
+      out[__ldg(cpar + (a - cs))] = 1;
+    }
   }
 }
 
@@ -786,17 +832,34 @@ int prune_c(const CsfView &in, const uint8_t *d_keep, int split, int32_t *d_inde
   int64_t prune_bytes = in.N[k - 1] + 5 * total;
   for (int d = 0; d + 1 < k; ++d) prune_bytes += 4 * (in.N[d] + 1);
   if (tm && tm->on) VX_CHECK(tm->begin(KK_PRUNE, prune_bytes));
-  rc = dmalloc((void **)&flags, (size_t)total + 16, s);  // 16 bytes for k_mark_parents' loads
+  rc = dmalloc((void **)&flags, (size_t)total + 16, s);  // 16 bytes for the 16-byte loads
   if (rc == VX_OK) rc = dmalloc((void **)&rank, (size_t)total * sizeof(int32_t), s);
   if (rc == VX_OK) {
     cudaError_t e = cudaMemcpyAsync(flags + sg.off[k - 1], d_keep, (size_t)in.N[k - 1],
                                     cudaMemcpyDeviceToDevice, s);
     for (int d = k - 2; d >= 0 && e == cudaSuccess; --d) {
-      int64_t blocks = (in.N[d] + 7) / 8;  // 8 warps per block, one node per warp
-      if (blocks > (int64_t)sm_count() * 16) blocks = (int64_t)sm_count() * 16;
-      if (blocks < 1) blocks = 1;
-      k_mark_parents<<<(unsigned)blocks, 256, 0, s>>>(in.ptr[d], in.N[d], flags, sg.off[d + 1],
-                                                     flags + sg.off[d]);
+      if (in.N[d + 1] <= 32 * in.N[d]) {  // short child ranges: one thread per node
+        int64_t blocks = (in.N[d] + 255) / 256;
+        if (blocks > (int64_t)sm_count() * 8) blocks = (int64_t)sm_count() * 8;
+        if (blocks < 1) blocks = 1;
+        k_mark_parents_t<<<(unsigned)blocks, 256, 0, s>>>(in.ptr[d], in.N[d], flags,
+                                                         sg.off[d + 1], flags + sg.off[d]);
+      } else if (in.N[d + 1] > 128 * in.N[d]) {  // long ranges: one warp per node
+        int64_t blocks = (in.N[d] + 7) / 8;  // 8 warps per block
+        if (blocks > (int64_t)sm_count() * 16) blocks = (int64_t)sm_count() * 16;
+        if (blocks < 1) blocks = 1;
+        k_mark_parents<<<(unsigned)blocks, 256, 0, s>>>(in.ptr[d], in.N[d], flags, sg.off[d + 1],
+                                                       flags + sg.off[d]);
+      } else {  // scatter from the kept children to their parents
+        e = cudaMemsetAsync(flags + sg.off[d], 0, (size_t)in.N[d], s);
+        if (e != cudaSuccess) break;
+        int64_t blocks = ((in.N[d + 1] + 31) / 16 + 255) / 256;
+        if (blocks > (int64_t)sm_count() * 8) blocks = (int64_t)sm_count() * 8;
+        if (blocks < 1) blocks = 1;
+        k_mark_parents_s<<<(unsigned)blocks, 256, 0, s>>>(in.par[d + 1], sg.off[d + 1],
+                                                         sg.off[d + 1] + in.N[d + 1], flags,
+                                                         flags + sg.off[d]);
+      }
       note_launch();
       e = cudaGetLastError();
     }

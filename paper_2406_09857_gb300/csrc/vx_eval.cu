@@ -412,8 +412,11 @@ __device__ __forceinline__ typename AR::V horner1_any(const typename AR::V *__re
 // consecutive entries of its parent's block.
 // One warp's share of k_stage: nodes chunk*32 + lane (of nnodes), fibres g, g+G, ....  par
 // holds parent indices of the parent array; poff is subtracted to index `in` (0 for one tree).
-template <class AR>
-__device__ __forceinline__ void stage_chunk(const StageDev &st, const int32_t *rowoff,
+// FM: the parents' blocks are fibre-major (fibre f's entries at fiboff[f] .. fiboff[f]+L-1,
+// consecutive, in_estride 1) instead of indexed through rowoff.
+template <class AR, bool FM = false>
+__device__ __forceinline__ void stage_chunk(const StageDev &st, const int32_t *outpos,
+                                            const int32_t *rowoff,
                                             const int32_t *__restrict__ lab,
                                             const int32_t *__restrict__ par, int64_t poff,
                                             const typename AR::V *__restrict__ in,
@@ -431,8 +434,9 @@ __device__ __forceinline__ void stage_chunk(const StageDev &st, const int32_t *r
   V *dst = out + node * out_nstride;
   for (int f = grp; f < st.nfib; f += G) {
     const int L = __ldg(st.fiblen + f);
-    const V J = horner_any<AR>(base, in_estride, rowoff, f, L, x);
-    if (live) dst[(int64_t)__ldg(st.outpos + f) * out_estride] = AR::store(J);
+    const V J = FM ? horner1_any<AR>(base + __ldg(st.fiboff + f), 1, L, x)
+                   : horner_any<AR>(base, in_estride, rowoff, f, L, x);
+    if (live) dst[(int64_t)__ldg(outpos + f) * out_estride] = AR::store(J);
   }
 }
 
@@ -455,7 +459,7 @@ __global__ void __launch_bounds__(kThreads)
   const int64_t nwarps = nchunk * G;
   for (int64_t w = (int64_t)blockIdx.x * kWarpsPerBlock + (threadIdx.x >> 5); w < nwarps;
        w += (int64_t)gridDim.x * kWarpsPerBlock)
-    stage_chunk<AR>(st, s_rowoff, lab, par, 0, in, in_estride, in_nstride, out, out_estride,
+    stage_chunk<AR>(st, st.outpos, s_rowoff, lab, par, 0, in, in_estride, in_nstride, out, out_estride,
                     out_nstride, nnodes, w % nchunk, (int)(w / nchunk), G, g);
 }
 
@@ -1061,8 +1065,10 @@ __global__ void k_c1_final(const uint8_t *__restrict__ flags, int64_t n,
 // One warp's share of k_stage_c: node pairs of chunk `chunk` (64 nodes), fibres g, g+G, ....
 // A warp whose 32 pairs each share a parent and do not straddle 0 shares every load between
 // the two nodes and runs sign-free (horner_y2_fibre); any other warp takes k_stage's per-node
-// path.  par/poff as in stage_chunk.
-__device__ __forceinline__ void stage_chunk_c(const StageDev &st, const int32_t *rowoff,
+// path.  par/poff and FM as in stage_chunk.
+template <bool FM = false>
+__device__ __forceinline__ void stage_chunk_c(const StageDev &st, const int32_t *outpos,
+                                              const int32_t *rowoff,
                                               const int32_t *__restrict__ lab,
                                               const int32_t *__restrict__ par, int64_t poff,
                                               const float4 *__restrict__ in, int64_t in_estride,
@@ -1088,13 +1094,25 @@ __device__ __forceinline__ void stage_chunk_c(const StageDev &st, const int32_t 
     for (int f = grp; f < st.nfib; f += G) {
       const int L = __ldg(st.fiblen + f);
       float4 K0, K1;
-      if (ws > 0)
+      if (FM) {
+        const float4 *const b[2] = {base + __ldg(st.fiboff + f), nullptr};
+        float4 K0v[2], K1v[2];
+        if (ws > 0)
+          horner_y2<1, 1>(b, L, yp, K0v, K1v);
+        else if (ws < 0)
+          horner_y2<1, -1>(b, L, yp, K0v, K1v);
+        else
+          horner_y2<1, 0>(b, L, yp, K0v, K1v);
+        K0 = K0v[0];
+        K1 = K1v[0];
+      } else if (ws > 0) {
         horner_y2_fibre<1>(base, in_estride, rowoff, f, L, yp, K0, K1);
-      else if (ws < 0)
+      } else if (ws < 0) {
         horner_y2_fibre<-1>(base, in_estride, rowoff, f, L, yp, K0, K1);
-      else
+      } else {
         horner_y2_fibre<0>(base, in_estride, rowoff, f, L, yp, K0, K1);
-      const int64_t o = (int64_t)__ldg(st.outpos + f) * out_estride;
+      }
+      const int64_t o = (int64_t)__ldg(outpos + f) * out_estride;
       if (live) out[i0 * out_nstride + o] = A32C::store(K0);
       if (two) out[i1 * out_nstride + o] = A32C::store(K1);
     }
@@ -1107,8 +1125,9 @@ __device__ __forceinline__ void stage_chunk_c(const StageDev &st, const int32_t 
       const int64_t node = c == 0 ? i0 : i1;
       for (int f = grp; f < st.nfib; f += G) {
         const int L = __ldg(st.fiblen + f);
-        const float4 J = horner_any<A32C>(base, in_estride, rowoff, f, L, x);
-        if (wr) out[node * out_nstride + (int64_t)__ldg(st.outpos + f) * out_estride] = A32C::store(J);
+        const float4 J = FM ? horner1_any<A32C>(base + __ldg(st.fiboff + f), 1, L, x)
+                            : horner_any<A32C>(base, in_estride, rowoff, f, L, x);
+        if (wr) out[node * out_nstride + (int64_t)__ldg(outpos + f) * out_estride] = A32C::store(J);
       }
     }
   }
@@ -1129,7 +1148,7 @@ __global__ void __launch_bounds__(kThreads, 6)
   // the loop bound is the same for the 32 lanes of a warp, so the vote inside sees all of them
   for (int64_t w = (int64_t)blockIdx.x * kWarpsPerBlock + (threadIdx.x >> 5); w < nwarps;
        w += (int64_t)gridDim.x * kWarpsPerBlock)
-    stage_chunk_c(st, s_rowoff, lab, par, 0, in, in_estride, in_nstride, out, out_estride,
+    stage_chunk_c(st, st.outpos, s_rowoff, lab, par, 0, in, in_estride, in_nstride, out, out_estride,
                   out_nstride, nnodes, w % nchunk, (int)(w / nchunk), G, g);
 }
 
@@ -1439,23 +1458,21 @@ __device__ __forceinline__ void leaf_chunk_copy(const LeafArgs &A, int npoly, in
 }
 
 // k_leaf_c with the parents' blocks brought into shared memory by bulk copies (mbarrier,
-// bounded wait): CTA b takes the leaves b*C .. b*C+C-1 (C = 2 kLeafIter blockDim.x), two per
-// thread per pass; their parents are consecutive nodes, whose node-major blocks are one
+// bounded wait): the CTA takes the leaves first .. last (at most 2 kLeafIter blockDim.x), two
+// per thread per pass; their parents are consecutive nodes, whose node-major blocks are one
 // contiguous range per polynomial, copied once when at most kLeafParents of them (else the
-// CTA reads global memory as k_leaf_c does).
-__global__ void __launch_bounds__(kThreads, 6)
-    k_leaf_tma_c(LeafArgs A, int npoly, const int32_t *__restrict__ lab,
-                 const int32_t *__restrict__ par, int64_t nleaves, AxisGrid g,
-                 uint8_t *__restrict__ keep, double *__restrict__ lo, double *__restrict__ hi,
-                 uint8_t *__restrict__ flag) {
-  extern __shared__ __align__(128) unsigned char smem[];
+// CTA reads global memory as k_leaf_c does).  Parent indices minus poff index A's blocks.
+__device__ __forceinline__ void leaf_tma_c_chunk(const LeafArgs &A, int npoly,
+                                                 const int32_t *__restrict__ lab,
+                                                 const int32_t *__restrict__ par, int64_t poff,
+                                                 int64_t first, int64_t last, int64_t nleaves,
+                                                 const AxisGrid &g, uint8_t *__restrict__ keep,
+                                                 double *__restrict__ lo, double *__restrict__ hi,
+                                                 uint8_t *__restrict__ flag, unsigned char *smem) {
   uint64_t *bar = reinterpret_cast<uint64_t *>(smem);
   int32_t *s_off = reinterpret_cast<int32_t *>(smem + 16);
   float4 *s_blk = reinterpret_cast<float4 *>(smem + 128);
-  const int64_t chunk = 2 * (int64_t)kLeafIter * blockDim.x;
-  const int64_t first = (int64_t)blockIdx.x * chunk;
-  const int64_t last = (first + chunk < nleaves ? first + chunk : nleaves) - 1;
-  const int64_t pf = __ldg(par + first), pl = __ldg(par + last);
+  const int64_t pf = __ldg(par + first) - poff, pl = __ldg(par + last) - poff;
   const bool staged = pl - pf < kLeafParents;
   if (staged) {
     if (threadIdx.x == 0) leaf_chunk_copy(A, npoly, pf, pl, bar, s_off, s_blk);
@@ -1472,7 +1489,7 @@ __global__ void __launch_bounds__(kThreads, 6)
     const bool live = na <= last, two = na + 1 <= last;
     const int64_t i0 = live ? na : last, i1 = two ? na + 1 : i0;
     const A32C::X x0 = A32C::box(g, __ldg(lab + i0)), x1 = A32C::box(g, __ldg(lab + i1));
-    const int64_t p0 = __ldg(par + i0), p1 = __ldg(par + i1);
+    const int64_t p0 = __ldg(par + i0) - poff, p1 = __ldg(par + i1) - poff;
     bool ex[2] = {false, false}, am[2] = {false, false};
     if (staged)
       leaf_pair_eval<2, ChunkBlocks, true>(A, 0, npoly, src, i0, i1, live, two, x0, x1, p0, p1,
@@ -1484,31 +1501,48 @@ __global__ void __launch_bounds__(kThreads, 6)
   }
 }
 
-// k_leaf_tma_c for two or more polynomials, without the work that C0 makes useless: each
-// thread runs polynomial 0 on its ITER pairs and settles the pairs whose leaves it excludes; the other pairs are queued in shared memory (warp-aggregated slots, so that the
-// pairs of a warp stay neighbours) with their decisions so far, and the CTA's warps run the
-// remaining polynomials on the queue.  C0 keeps a leaf only if no polynomial excludes it, so
-// the decisions are those of k_leaf_tma_c; the leaves' interval values are not written.
-// ITER pairs per thread in the first phase (a CTA takes 2 ITER kThreads leaves).
-template <int ITER>
-__global__ void __launch_bounds__(kThreads, 8)
-    k_leaf_tma_q(LeafArgs A, int npoly, const int32_t *__restrict__ lab,
+__global__ void __launch_bounds__(kThreads, 6)
+    k_leaf_tma_c(LeafArgs A, int npoly, const int32_t *__restrict__ lab,
                  const int32_t *__restrict__ par, int64_t nleaves, AxisGrid g,
-                 uint8_t *__restrict__ keep, uint8_t *__restrict__ flag) {
+                 uint8_t *__restrict__ keep, double *__restrict__ lo, double *__restrict__ hi,
+                 uint8_t *__restrict__ flag) {
   extern __shared__ __align__(128) unsigned char smem[];
-  __shared__ int s_nq;
-  __shared__ int16_t s_q[ITER * kThreads];  // queued pair: its index in the chunk
-  __shared__ uint8_t s_st[ITER * kThreads]; // its decisions so far (ex0, am0, ex1, am1)
+  const int64_t chunk = 2 * (int64_t)kLeafIter * blockDim.x;
+  const int64_t first = (int64_t)blockIdx.x * chunk;
+  const int64_t last = (first + chunk < nleaves ? first + chunk : nleaves) - 1;
+  leaf_tma_c_chunk(A, npoly, lab, par, 0, first, last, nleaves, g, keep, lo, hi, flag, smem);
+}
+
+// k_leaf_tma_c for two or more polynomials, without the work that C0 makes useless: each
+// thread runs polynomial 0 on its ITER pairs and settles the pairs whose leaves it excludes;
+// the other pairs are queued in shared memory (warp-aggregated slots, so that the pairs of a
+// warp stay neighbours) with their decisions so far, and the CTA's warps run the remaining
+// polynomials on the queue.  C0 keeps a leaf only if no polynomial excludes it, so the
+// decisions are those of k_leaf_tma_c; the leaves' interval values are not written.  The CTA
+// takes the leaves first .. last (at most 2 ITER kThreads, ITER pairs per thread in the first
+// phase); parent indices minus poff index A's blocks.
+template <int ITER>
+struct LeafQueue {
+  int nq;
+  int16_t q[ITER * kThreads];  // queued pair: its index in the chunk
+  uint8_t st[ITER * kThreads]; // its decisions so far (ex0, am0, ex1, am1)
+};
+
+template <int ITER>
+__device__ __forceinline__ void leaf_q_chunk(const LeafArgs &A, int npoly,
+                                             const int32_t *__restrict__ lab,
+                                             const int32_t *__restrict__ par, int64_t poff,
+                                             int64_t first, int64_t last, const AxisGrid &g,
+                                             uint8_t *__restrict__ keep,
+                                             uint8_t *__restrict__ flag, unsigned char *smem,
+                                             LeafQueue<ITER> &Q) {
   uint64_t *bar = reinterpret_cast<uint64_t *>(smem);
   int32_t *s_off = reinterpret_cast<int32_t *>(smem + 16);
   float4 *s_blk = reinterpret_cast<float4 *>(smem + 128);
-  const int64_t chunk = 2 * (int64_t)ITER * kThreads;
-  const int64_t first = (int64_t)blockIdx.x * chunk;
-  const int64_t last = (first + chunk < nleaves ? first + chunk : nleaves) - 1;
-  const int64_t pf = __ldg(par + first), pl = __ldg(par + last);
+  const int64_t pf = __ldg(par + first) - poff, pl = __ldg(par + last) - poff;
   const bool staged = pl - pf < kLeafParents;
   if (threadIdx.x == 0) {
-    s_nq = 0;
+    Q.nq = 0;
     if (staged) leaf_chunk_copy(A, npoly, pf, pl, bar, s_off, s_blk);
   }
   __syncthreads();
@@ -1526,48 +1560,61 @@ __global__ void __launch_bounds__(kThreads, 8)
     const bool live = na <= last, two = na + 1 <= last;
     const int64_t i0 = live ? na : last, i1 = two ? na + 1 : i0;
     const A32C::X x0 = A32C::box(g, __ldg(lab + i0)), x1 = A32C::box(g, __ldg(lab + i1));
-    const int64_t p0 = __ldg(par + i0), p1 = __ldg(par + i1);
+    const int64_t p0 = __ldg(par + i0) - poff, p1 = __ldg(par + i1) - poff;
     bool ex[2] = {false, false}, am[2] = {false, false};
     if (staged)
       leaf_pair_eval<1, ChunkBlocks, true>(A, 0, 1, src, i0, i1, live, two, x0, x1, p0, p1,
-                                           nleaves, nullptr, nullptr, ex, am);
+                                           0, nullptr, nullptr, ex, am);
     else
       leaf_pair_eval<1, ChunkBlocks, false>(A, 0, 1, src, i0, i1, live, two, x0, x1, p0, p1,
-                                            nleaves, nullptr, nullptr, ex, am);
+                                            0, nullptr, nullptr, ex, am);
     const bool more = live && !(ex[0] && (ex[1] || !two));
     if (live && !more) leaf_pair_store(i0, i1, live, two, ex, am, keep, flag);
     const unsigned m = __ballot_sync(0xffffffffu, more);
     int base = 0;
-    if (lane == 0 && m != 0u) base = atomicAdd(&s_nq, __popc(m));
+    if (lane == 0 && m != 0u) base = atomicAdd(&Q.nq, __popc(m));
     base = __shfl_sync(0xffffffffu, base, 0);
     if (more) {
       const int slot = base + __popc(m & ((1u << lane) - 1u));
-      s_q[slot] = (int16_t)q;
-      s_st[slot] = (uint8_t)((ex[0] ? 1 : 0) | (am[0] ? 2 : 0) | (ex[1] ? 4 : 0) | (am[1] ? 8 : 0));
+      Q.q[slot] = (int16_t)q;
+      Q.st[slot] = (uint8_t)((ex[0] ? 1 : 0) | (am[0] ? 2 : 0) | (ex[1] ? 4 : 0) | (am[1] ? 8 : 0));
     }
   }
   __syncthreads();
-  const int nq = s_nq;
+  const int nq = Q.nq;
   // the loop bound is the same for the 32 lanes of a warp (the votes inside see all of them);
   // a lane past the queue's end repeats its last pair and stores nothing
   for (int b = (int)(threadIdx.x & ~31u); b < nq; b += kThreads) {
     const bool in = b + lane < nq;
     const int sl = in ? b + lane : nq - 1;
-    const int q = s_q[sl], st = s_st[sl];
+    const int q = Q.q[sl], st = Q.st[sl];
     const int64_t i0 = first + 2 * (int64_t)q;
     const bool two = i0 + 1 <= last;
     const int64_t i1 = two ? i0 + 1 : i0;
     const A32C::X x0 = A32C::box(g, __ldg(lab + i0)), x1 = A32C::box(g, __ldg(lab + i1));
-    const int64_t p0 = __ldg(par + i0), p1 = __ldg(par + i1);
+    const int64_t p0 = __ldg(par + i0) - poff, p1 = __ldg(par + i1) - poff;
     bool ex[2] = {(st & 1) != 0, (st & 4) != 0}, am[2] = {(st & 2) != 0, (st & 8) != 0};
     if (staged)
       leaf_pair_eval<1, ChunkBlocks, true>(A, 1, npoly, src, i0, i1, in, two, x0, x1, p0, p1,
-                                           nleaves, nullptr, nullptr, ex, am);
+                                           0, nullptr, nullptr, ex, am);
     else
       leaf_pair_eval<1, ChunkBlocks, false>(A, 1, npoly, src, i0, i1, in, two, x0, x1, p0, p1,
-                                            nleaves, nullptr, nullptr, ex, am);
+                                            0, nullptr, nullptr, ex, am);
     leaf_pair_store(i0, i1, in, two, ex, am, keep, flag);
   }
+}
+
+template <int ITER>
+__global__ void __launch_bounds__(kThreads, 8)
+    k_leaf_tma_q(LeafArgs A, int npoly, const int32_t *__restrict__ lab,
+                 const int32_t *__restrict__ par, int64_t nleaves, AxisGrid g,
+                 uint8_t *__restrict__ keep, uint8_t *__restrict__ flag) {
+  extern __shared__ __align__(128) unsigned char smem[];
+  __shared__ LeafQueue<ITER> Q;
+  const int64_t chunk = 2 * (int64_t)ITER * kThreads;
+  const int64_t first = (int64_t)blockIdx.x * chunk;
+  const int64_t last = (first + chunk < nleaves ? first + chunk : nleaves) - 1;
+  leaf_q_chunk<ITER>(A, npoly, lab, par, 0, first, last, g, keep, flag, smem, Q);
 }
 
 int leaf_tma_grid(int64_t leaves, int iter = kLeafIter) {
@@ -2001,10 +2048,12 @@ __device__ __forceinline__ int tree_of(const int64_t *__restrict__ off, int S, i
 // k_stage_c's) warp body on its tree's nodes with the tree's polynomials, grid and
 // node-major blocks.
 template <class AR, bool PAIRS>
-__global__ void __launch_bounds__(kThreads)
+__global__ void __launch_bounds__(kThreads, 6)
     k_fstage(const ForestTree *__restrict__ trees, const int64_t *__restrict__ off, int S, int d,
              CsfView c, void *const *__restrict__ blk, const int64_t *__restrict__ tasks, int G) {
   using V = typename AR::V;
+  constexpr bool FMF = std::is_same<AR, A32C>::value;
+  const int k = c.k;
   const int64_t *offd = off + (int64_t)d * (S + 1);
   const int64_t *offp = off + (int64_t)(d > 0 ? d - 1 : 0) * (S + 1);
   const int64_t ntask = __ldg(tasks + S);
@@ -2022,17 +2071,28 @@ __global__ void __launch_bounds__(kThreads)
     const int32_t *par = d > 0 ? c.par[d] + o : nullptr;
     const int64_t poff = d > 0 ? __ldg(offp + t) : 0;
     for (int f = 0; f < T.dev.npoly; ++f) {
-      const StageDev st = T.dev.p[f].st[d];
+      const StageDev &st = T.dev.p[f].st[d];
+      // certified binary32: an inner stage's blocks are written and read fibre-major
+      const int32_t *outpos = FMF && d + 2 < k ? st.outpos_fm : st.outpos;
       const V *in = d == 0 ? AR::coef(T.dev.p[f])
                            : (const V *)blk[((int64_t)t * VX_MAXPOLY + f) * VX_KMAX + d - 1];
       V *out = (V *)blk[((int64_t)t * VX_MAXPOLY + f) * VX_KMAX + d];
       const int64_t in_nstride = d == 0 ? 0 : st.blk_in;
-      if constexpr (PAIRS)
-        stage_chunk_c(st, st.rowoff, lab, par, poff, (const float4 *)in, 1, in_nstride,
-                      (float4 *)out, 1, st.blk_out, n, chunk, grp, G, T.ax[d]);
-      else
-        stage_chunk<AR>(st, st.rowoff, lab, par, poff, in, 1, in_nstride, out, 1, st.blk_out, n,
-                        chunk, grp, G, T.ax[d]);
+      if constexpr (PAIRS) {
+        if (FMF && d > 0)
+          stage_chunk_c<true>(st, outpos, st.rowoff, lab, par, poff, (const float4 *)in, 1, in_nstride,
+                              (float4 *)out, 1, st.blk_out, n, chunk, grp, G, T.ax[d]);
+        else
+          stage_chunk_c<false>(st, outpos, st.rowoff, lab, par, poff, (const float4 *)in, 1, in_nstride,
+                               (float4 *)out, 1, st.blk_out, n, chunk, grp, G, T.ax[d]);
+      } else {
+        if (FMF && d > 0)
+          stage_chunk<AR, true>(st, outpos, st.rowoff, lab, par, poff, in, 1, in_nstride, out, 1,
+                                st.blk_out, n, chunk, grp, G, T.ax[d]);
+        else
+          stage_chunk<AR, false>(st, outpos, st.rowoff, lab, par, poff, in, 1, in_nstride, out, 1,
+                                 st.blk_out, n, chunk, grp, G, T.ax[d]);
+      }
     }
   }
 }
@@ -2077,6 +2137,52 @@ __global__ void __launch_bounds__(kThreads)
         leaf_item<AR>(A, npoly, lab, par, poff, i, n, T.ax[k - 1], keep + o, nullptr, nullptr,
                       flag ? flag + o : nullptr, theta);
     }
+  }
+}
+
+// The leaves of a forest in the certified binary32 arithmetic with the single-system leaf
+// kernels' bodies: CTA b takes chunk b - ctasks[t] of tree t's leaves (tree t owning CTAs
+// ctasks[t] .. ctasks[t+1]-1), stages the chunk's parent blocks of the tree's own polynomials
+// in shared memory and runs k_leaf_tma_q's (QUEUE, two or more polynomials) or
+// k_leaf_tma_c's body; parent indices are the forest's, rebased by the tree's first parent.
+constexpr int kForestLeafIter = 2;
+
+template <bool QUEUE>
+__global__ void __launch_bounds__(kThreads, QUEUE ? 8 : 6)
+    k_fleaf_tma(const ForestTree *__restrict__ trees, const int64_t *__restrict__ off, int S,
+                CsfView c, void *const *__restrict__ blk, const int64_t *__restrict__ ctasks,
+                uint8_t *__restrict__ keep, uint8_t *__restrict__ flag) {
+  extern __shared__ __align__(128) unsigned char smem[];
+  const int k = c.k;
+  const int64_t *offl = off + (int64_t)(k - 1) * (S + 1);
+  const int64_t *offp = off + (int64_t)(k - 2) * (S + 1);
+  const int64_t b = blockIdx.x;
+  const int t = tree_of(ctasks, S, b);
+  const ForestTree &T = trees[t];
+  const int64_t o = __ldg(offl + t), n = __ldg(offl + t + 1) - o;
+  const int64_t chunk = 2 * (int64_t)kForestLeafIter * kThreads;
+  const int64_t first = o + (b - __ldg(ctasks + t)) * chunk;
+  const int64_t last = (first + chunk < o + n ? first + chunk : o + n) - 1;
+  // the tree's leaf arguments once per CTA in shared memory (indexed by polynomial at run
+  // time, which a per-thread copy would keep in local memory)
+  __shared__ LeafArgs A;
+  const int npoly = T.dev.npoly;
+  if (threadIdx.x == 0)
+    for (int f = 0; f < npoly; ++f) {
+      A.rel[f] = T.dev.rel[f];
+      A.in[f] = blk[((int64_t)t * VX_MAXPOLY + f) * VX_KMAX + k - 2];
+      A.blk[f] = T.dev.p[f].st[k - 1].blk_in;
+      A.len[f] = T.dev.p[f].st[k - 1].maxlen;
+    }
+  __syncthreads();
+  const int64_t poff = __ldg(offp + t);
+  if constexpr (QUEUE) {
+    __shared__ LeafQueue<kForestLeafIter> Q;
+    leaf_q_chunk<kForestLeafIter>(A, npoly, c.lab[k - 1], c.par[k - 1], poff, first, last,
+                                  T.ax[k - 1], keep, flag, smem, Q);
+  } else {
+    leaf_tma_c_chunk(A, npoly, c.lab[k - 1], c.par[k - 1], poff, first, last, 0, T.ax[k - 1],
+                     keep, nullptr, nullptr, flag, smem);
   }
 }
 
@@ -2165,7 +2271,59 @@ int eval_forest_t(const ForestTree *d_trees, const ForestTree *h_trees, const in
       rc = VX_ECUDA;
     }
   }
-  if (rc == VX_OK) {
+  // certified binary32 leaves with parents: the staged single-system bodies, one CTA per
+  // chunk of a tree's leaves, when every tree's staged blocks fit in shared memory
+  bool staged_leaf = std::is_same<AR, A32C>::value && k >= 2;
+  size_t leaf_smem = 128;
+  int maxpoly = 0;
+  std::vector<int64_t> ctasks(S + 1, 0);
+  if (staged_leaf) {
+    const int64_t chunk = 2 * (int64_t)kForestLeafIter * kThreads;
+    for (int t = 0; t < S; ++t) {
+      size_t need = 128;
+      for (int f = 0; f < h_trees[t].dev.npoly; ++f)
+        need += (size_t)kLeafParents * h_trees[t].dev.p[f].st[k - 1].blk_in * sizeof(float4);
+      leaf_smem = std::max(leaf_smem, need);
+      maxpoly = std::max(maxpoly, h_trees[t].dev.npoly);
+      const int64_t nt = h_off[(int64_t)(k - 1) * (S + 1) + t + 1] - h_off[(int64_t)(k - 1) * (S + 1) + t];
+      ctasks[t + 1] = ctasks[t] + (nt + chunk - 1) / chunk;
+    }
+    staged_leaf = leaf_smem <= kMaxDynSmem && ctasks[S] <= INT32_MAX;
+  }
+  void *dctasks = nullptr;
+  if (rc == VX_OK && staged_leaf) {
+    rc = dmalloc(&dctasks, ctasks.size() * sizeof(int64_t), s);
+    if (rc == VX_OK && cudaMemcpyAsync(dctasks, ctasks.data(), ctasks.size() * sizeof(int64_t),
+                                       cudaMemcpyHostToDevice, s) != cudaSuccess) {
+      set_error("forest leaf task table upload failed");
+      rc = VX_ECUDA;
+    }
+  }
+  if (rc == VX_OK && staged_leaf) {
+    if (ctasks[S] > 0) {
+      const bool queue = maxpoly >= 2;
+      cudaError_t e = queue ? cudaFuncSetAttribute(k_fleaf_tma<true>,
+                                                   cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                   (int)leaf_smem)
+                            : cudaFuncSetAttribute(k_fleaf_tma<false>,
+                                                   cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                   (int)leaf_smem);
+      if (e == cudaSuccess) {
+        if (queue)
+          k_fleaf_tma<true><<<(unsigned)ctasks[S], kThreads, leaf_smem, s>>>(
+              d_trees, d_off, S, c, (void *const *)dtab, (const int64_t *)dctasks, keep, flag);
+        else
+          k_fleaf_tma<false><<<(unsigned)ctasks[S], kThreads, leaf_smem, s>>>(
+              d_trees, d_off, S, c, (void *const *)dtab, (const int64_t *)dctasks, keep, flag);
+        note_launch();
+        e = cudaGetLastError();
+      }
+      if (e != cudaSuccess) {
+        set_error("forest leaf launch failed: %s", cudaGetErrorString(e));
+        rc = VX_ECUDA;
+      }
+    }
+  } else if (rc == VX_OK) {
     const int64_t *tl = (const int64_t *)dtasks + (size_t)(k - 1) * (S + 1);
     const unsigned nb = blocks_of(tasks[(size_t)(k - 1) * (S + 1) + S]);
     if (pairs[k - 1])
@@ -2178,6 +2336,7 @@ int eval_forest_t(const ForestTree *d_trees, const ForestTree *h_trees, const in
       rc = VX_ECUDA;
     }
   }
+  dfree(dctasks, s);
   dfree(dtasks, s);
   dfree(dtab, s);
   dfree(mem, s);

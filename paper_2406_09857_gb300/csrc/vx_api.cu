@@ -2402,11 +2402,9 @@ void release(Forest &F, cudaStream_t s) {
 // Prunes forest `in` with mask `m` (split or compact) into `out`, with per-tree offsets.
 int prune_forest(Forest &in, const uint8_t *m, int split, int32_t *d_index, int k, int S,
                  int64_t *d_seg, std::vector<int64_t> &h_seg, cudaStream_t s, Forest &out) {
-  VX_CHECK(csf_prune_forest(in.c.v, m, split, d_index, in.d_off, S, d_seg, s, &out.c, nullptr));
   h_seg.assign((size_t)k * (S + 1), 0);
-  VX_CUDA(cudaMemcpyAsync(h_seg.data(), d_seg, sizeof(int64_t) * h_seg.size(),
-                          cudaMemcpyDeviceToHost, s));
-  VX_CUDA(cudaStreamSynchronize(s));
+  VX_CHECK(csf_prune_forest(in.c.v, m, split, d_index, in.d_off, S, d_seg, s, &out.c, nullptr,
+                            h_seg.data()));
   out.off.assign(h_seg.size(), 0);
   for (int d = 0; d < k; ++d)
     for (int t = 0; t <= S; ++t)
@@ -2516,6 +2514,12 @@ int batch_group(const std::vector<int32_t> &ids, const vx_poly *const *systems,
   cudaEvent_t ev0 = nullptr, ev1 = nullptr;
   if (rc == VX_OK && (cudaEventCreate(&ev0) != cudaSuccess || cudaEventCreate(&ev1) != cudaSuccess))
     rc = VX_ECUDA;
+  int *h_status = nullptr;  // pinned: the device status word, read with a level's last wait
+  if (rc == VX_OK && cudaHostAlloc((void **)&h_status, sizeof(int), cudaHostAllocDefault) != cudaSuccess) {
+    set_error("cudaHostAlloc of the status word failed");
+    h_status = nullptr;
+    rc = VX_ENOMEM;
+  }
   if (rc == VX_OK && cudaEventRecord(ev0, s) != cudaSuccess) rc = VX_ECUDA;
   // level 0: one box per tree
   Forest cur;
@@ -2652,7 +2656,11 @@ int batch_group(const std::vector<int32_t> &ids, const vx_poly *const *systems,
                                            d_tdep, l, 1, n, m);
       note_launch();
       if (any_cont) {
-        rc = prune_forest(cur, m, 1, nullptr, k, S, d_seg, hseg, s, next);
+        // the level's device status travels back in the prune's wait (every kernel that
+        // can give up a bounded wait ran before it)
+        *h_status = 0;
+        rc = queue_device_status(s, h_status);
+        if (rc == VX_OK) rc = prune_forest(cur, m, 1, nullptr, k, S, d_seg, hseg, s, next);
         for (int t = 0; t < S && rc == VX_OK; ++t)
           if (tdep[t] > l)
             R[t]->kept[l] = hseg[(size_t)(k - 1) * (S + 1) + t + 1] - hseg[(size_t)(k - 1) * (S + 1) + t];
@@ -2662,7 +2670,12 @@ int batch_group(const std::vector<int32_t> &ids, const vx_poly *const *systems,
     dfree(flag, s);
     dfree(keep, s);
     int st = 0;
-    if (rc == VX_OK) rc = take_device_status(s, &st);
+    if (rc == VX_OK) {
+      if (any_cont && *h_status == 0)
+        st = 0;  // read in the prune's wait
+      else
+        rc = take_device_status(s, &st);  // waits; clears a set status
+    }
     if (rc == VX_OK && st) {
       set_error("a bounded device wait gave up at level %d", l);
       rc = VX_ETIMEOUT;
@@ -2693,6 +2706,15 @@ int batch_group(const std::vector<int32_t> &ids, const vx_poly *const *systems,
   dfree(d_ax, s);
   dfree(d_trees, s);
   if (cudaStreamSynchronize(s) != cudaSuccess && rc == VX_OK) rc = VX_ECUDA;
+  if (h_status) cudaFreeHost(h_status);
+  if (rc == VX_OK) {  // a status that no level's wait carried back (an empty last prune)
+    int st = 0;
+    rc = take_device_status(s, &st);
+    if (rc == VX_OK && st) {
+      set_error("a bounded device wait gave up");
+      rc = VX_ETIMEOUT;
+    }
+  }
   for (int t = 0; t < S; ++t) vx_system_free(sysv[t]);
   for (int t = 0; t < S; ++t) {
     if (rc == VX_OK)

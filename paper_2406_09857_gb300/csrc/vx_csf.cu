@@ -253,8 +253,9 @@ int32_t *pinned_counts() {
   return p;
 }
 
-// Runs reduce + tile scan; leaves the tile offsets in *d_scratch (caller frees) and copies the
-// channel totals to h_totals (synchronising the stream).
+// Runs reduce + tile scan; leaves the tile offsets in *d_scratch (caller frees), followed by
+// the C channel totals, and copies the totals to h_totals (synchronising the stream); with
+// h_totals null the totals stay on the device only and nothing waits.
 template <int C, class Src>
 int scan_prepare(const Src &src, int64_t n, cudaStream_t s, int32_t **d_scratch,
                  int64_t *ntiles_out, int32_t *h_totals, const int32_t *d_extra = nullptr,
@@ -269,7 +270,8 @@ int scan_prepare(const Src &src, int64_t n, cudaStream_t s, int32_t **d_scratch,
     return VX_ENOMEM;
   }
   if (ntiles == 0) {
-    for (int c = 0; c < C; ++c) h_totals[c] = 0;
+    if (h_totals)
+      for (int c = 0; c < C; ++c) h_totals[c] = 0;
     if (h_extra) *h_extra = 0;
     return VX_OK;
   }
@@ -286,6 +288,7 @@ int scan_prepare(const Src &src, int64_t n, cudaStream_t s, int32_t **d_scratch,
   k_scan_tiles<C><<<1, 1024, 0, s>>>(buf, ntiles, buf + C * ntiles);
   note_launch();
   VX_LAUNCH_CHECK();
+  if (!h_totals) return VX_OK;
   VX_CUDA(cudaMemcpyAsync(pin, buf + C * ntiles, C * sizeof(int32_t), cudaMemcpyDeviceToHost, s));
   if (d_extra)
     VX_CUDA(cudaMemcpyAsync(pin + C, d_extra, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
@@ -805,7 +808,8 @@ void launch_split(int d, int blocks, cudaStream_t s, const CsfView &in, const ui
 template <int C>
 int prune_c(const CsfView &in, const uint8_t *d_keep, int split, int32_t *d_index,
             cudaStream_t s, CsfObj *out, Timer *tm, const int64_t *d_seg_off = nullptr,
-            int nseg = 0, int64_t *d_seg_kept = nullptr, int64_t cap = INT32_MAX) {
+            int nseg = 0, int64_t *d_seg_kept = nullptr, int64_t cap = INT32_MAX,
+            int64_t *h_seg_kept = nullptr) {
   const int k = in.k;
   Segs sg;
   sg.k = k;
@@ -822,6 +826,8 @@ int prune_c(const CsfView &in, const uint8_t *d_keep, int split, int32_t *d_inde
     VX_CHECK(csf_alloc(out, k, in.level + (split ? 1 : 0), N, s));
     if (d_seg_kept)
       VX_CUDA(cudaMemsetAsync(d_seg_kept, 0, sizeof(int64_t) * (size_t)k * (nseg + 1), s));
+    if (h_seg_kept)
+      for (int64_t j = 0; j < (int64_t)k * (nseg + 1); ++j) h_seg_kept[j] = 0;
     return set_ptr_sentinels(out->v, s);
   }
   uint8_t *flags = nullptr;
@@ -871,7 +877,10 @@ int prune_c(const CsfView &in, const uint8_t *d_keep, int split, int32_t *d_inde
   FlagSrc src{flags, sg};
   int64_t ntiles = 0;
   int32_t nk[C];
-  if (rc == VX_OK) rc = scan_prepare<C>(src, total, s, &scratch, &ntiles, nk);
+  // with per-segment counts for the host, the channel totals and those counts travel back
+  // together after the ranks (one wait instead of two)
+  const bool one_wait = d_seg_off && h_seg_kept;
+  if (rc == VX_OK) rc = scan_prepare<C>(src, total, s, &scratch, &ntiles, one_wait ? nullptr : nk);
   if (rc == VX_OK) rc = scan_emit<C>(src, RankEmit{rank, src}, total, scratch, ntiles, s);
   if (rc == VX_OK && d_seg_off) {
     // the channel totals sit after the tile sums in the scan scratch
@@ -881,6 +890,21 @@ int prune_c(const CsfView &in, const uint8_t *d_keep, int split, int32_t *d_inde
     if (cudaGetLastError() != cudaSuccess) {
       set_error("segment count kernel launch failed");
       rc = VX_ECUDA;
+    }
+  }
+  if (rc == VX_OK && one_wait) {
+    int32_t *pin = pinned_counts();
+    cudaError_t e = cudaMemcpyAsync(pin, scratch + (int64_t)C * ntiles, C * sizeof(int32_t),
+                                    cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(h_seg_kept, d_seg_kept, sizeof(int64_t) * (size_t)k * (nseg + 1),
+                          cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) {
+      set_error("reading the kept counts failed: %s", cudaGetErrorString(e));
+      rc = VX_ECUDA;
+    } else {
+      for (int c = 0; c < C; ++c) nk[c] = pin[c];
     }
   }
   // kept-tree first-child pointers
@@ -1010,6 +1034,54 @@ struct IndexEmit {
   int32_t *idx;
   __device__ void operator()(int64_t i, unsigned m, const int32_t *excl) const {
     if (m) idx[excl[0]] = (int32_t)i;
+  }
+};
+
+// the nonzero bytes of a 32-bit word, as its bits 7, 15, 23 and 31
+__device__ __forceinline__ uint32_t nonzero_bytes(uint32_t x) {
+  return (((x & 0x7f7f7f7fu) + 0x7f7f7f7fu) | x) & 0x80808080u;
+}
+
+// Sparse byte flags (a few selected among many): eight flags counted per 8-byte word, and a
+// word without a flag emits nothing.
+template <>
+struct ItemOps<1, ByteFlagSrc> {
+  uint2 v;
+  bool word;       // v holds the eight flags
+  unsigned m[SI];  // else the per-entry flags
+  __device__ __forceinline__ void load(const ByteFlagSrc &src, int64_t i0, int64_t n, bool) {
+    word = i0 + SI <= n && (reinterpret_cast<uintptr_t>(src.f + i0) & 7u) == 0;
+    if (word) {
+      v = __ldg(reinterpret_cast<const uint2 *>(src.f + i0));
+      v = make_uint2(nonzero_bytes(v.x), nonzero_bytes(v.y));
+    } else {
+      load_items(src, i0, n, false, m);
+    }
+  }
+  __device__ __forceinline__ void count(int32_t (&cnt)[1]) const {
+    if (word) {
+      cnt[0] += __popc(v.x) + __popc(v.y);
+    } else {
+#pragma unroll
+      for (int j = 0; j < SI; ++j) cnt[0] += m[j] & 1u;
+    }
+  }
+  template <class Emit>
+  __device__ __forceinline__ void emit(const Emit &em, int64_t i0, int64_t n,
+                                       int32_t (&run)[1]) const {
+    if (!word) {
+      emit_items<1>(em, i0, n, m, run);
+      return;
+    }
+    if ((v.x | v.y) == 0u) return;
+#pragma unroll
+    for (int j = 0; j < SI; ++j) {
+      const unsigned b = ((j < 4 ? v.x : v.y) >> (8 * (j & 3) + 7)) & 1u;
+      if (b) {
+        em(i0 + j, 1u, run);
+        run[0] += 1;
+      }
+    }
   }
 };
 
@@ -1164,14 +1236,15 @@ int csf_keep_in_roots(const CsfView &c, const uint8_t *d_keep, int64_t a, int64_
 
 int csf_prune_forest(const CsfView &in, const uint8_t *d_keep, int split, int32_t *d_index,
                      const int64_t *d_seg_off, int nseg, int64_t *d_seg_kept, cudaStream_t s,
-                     CsfObj *out, Timer *tm) {
+                     CsfObj *out, Timer *tm, int64_t *h_seg_kept) {
+  const int64_t cap = INT32_MAX;
   switch (in.k) {
-    case 1: return prune_c<1>(in, d_keep, split, d_index, s, out, tm, d_seg_off, nseg, d_seg_kept);
-    case 2: return prune_c<2>(in, d_keep, split, d_index, s, out, tm, d_seg_off, nseg, d_seg_kept);
-    case 3: return prune_c<3>(in, d_keep, split, d_index, s, out, tm, d_seg_off, nseg, d_seg_kept);
-    case 4: return prune_c<4>(in, d_keep, split, d_index, s, out, tm, d_seg_off, nseg, d_seg_kept);
-    case 5: return prune_c<5>(in, d_keep, split, d_index, s, out, tm, d_seg_off, nseg, d_seg_kept);
-    default: return prune_c<6>(in, d_keep, split, d_index, s, out, tm, d_seg_off, nseg, d_seg_kept);
+    case 1: return prune_c<1>(in, d_keep, split, d_index, s, out, tm, d_seg_off, nseg, d_seg_kept, cap, h_seg_kept);
+    case 2: return prune_c<2>(in, d_keep, split, d_index, s, out, tm, d_seg_off, nseg, d_seg_kept, cap, h_seg_kept);
+    case 3: return prune_c<3>(in, d_keep, split, d_index, s, out, tm, d_seg_off, nseg, d_seg_kept, cap, h_seg_kept);
+    case 4: return prune_c<4>(in, d_keep, split, d_index, s, out, tm, d_seg_off, nseg, d_seg_kept, cap, h_seg_kept);
+    case 5: return prune_c<5>(in, d_keep, split, d_index, s, out, tm, d_seg_off, nseg, d_seg_kept, cap, h_seg_kept);
+    default: return prune_c<6>(in, d_keep, split, d_index, s, out, tm, d_seg_off, nseg, d_seg_kept, cap, h_seg_kept);
   }
 }
 

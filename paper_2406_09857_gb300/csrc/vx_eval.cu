@@ -2496,6 +2496,11 @@ int set_wait_polls(int64_t polls) {
   return VX_OK;
 }
 
+int queue_device_status(cudaStream_t s, int *h_pinned) {
+  VX_CUDA(cudaMemcpyFromSymbolAsync(h_pinned, g_vx_status, sizeof(int), 0, cudaMemcpyDeviceToHost, s));
+  return VX_OK;
+}
+
 int take_device_status(cudaStream_t s, int *status) {
   int v = 0;
   VX_CUDA(cudaMemcpyFromSymbolAsync(&v, g_vx_status, sizeof(int), 0, cudaMemcpyDeviceToHost, s));

@@ -248,10 +248,14 @@ int csf_keep_in_roots(const CsfView &c, const uint8_t *d_keep, int64_t a, int64_
                       uint8_t *d_out, cudaStream_t s);
 // The same on a forest of nseg trees stored one after another at every depth (tree s owns
 // depth-d nodes d_seg_off[d*(nseg+1) + s] .. [.. + s + 1] - 1): d_seg_kept[d*(nseg+1) + s]
-// receives the kept depth-d nodes of trees before s (s = nseg: all of them).
+// receives the kept depth-d nodes of trees before s (s = nseg: all of them), and h_seg_kept
+// (nullable, host) a copy of it, read with the kept totals in the one wait of the call.
 int csf_prune_forest(const CsfView &in, const uint8_t *d_keep, int split, int32_t *d_index,
                      const int64_t *d_seg_off, int nseg, int64_t *d_seg_kept, cudaStream_t s,
-                     CsfObj *out, Timer *tm);
+                     CsfObj *out, Timer *tm, int64_t *h_seg_kept = nullptr);
+// Queues a copy of the device status word (bounded waits that gave up) into pinned host memory
+// (read it after the stream's next synchronisation).
+int queue_device_status(cudaStream_t s, int *h_pinned);
 // The complete tree of grid level `level` (every box), filled directly.
 int csf_full_grid_dev(int k, int level, cudaStream_t s, CsfObj *out);
 // ptr[d][N[d]] = N[d+1] for every depth d < k-1.

@@ -1152,12 +1152,24 @@ __global__ void __launch_bounds__(kThreads, 6)
                   out_nstride, nnodes, w % nchunk, (int)(w / nchunk), G, g);
 }
 
+// Entry r of a fibre of length L rewritten for the summed bound (leaf_bform states it).
+__device__ __forceinline__ float4 bform_entry(const float4 v, int r, int L) {
+  constexpr float kKappaB = 0x1.000002p-24f;  // >= 2^-24 + 2^-50
+  const int w = r + 1 < L - 1 ? r + 1 : (L > 1 ? L - 1 : 0);
+  const float M = fmaxf(fabsf(v.x), fabsf(v.y));
+  float B = __fmaf_ru(__fmul_ru(kKappaB, (float)w), M, v.z);
+  B = __fmaf_ru(v.z, 0x1p-50f, B);
+  B = __fadd_ru(B, kEta148);
+  return make_float4(v.x, v.y, B, B);
+}
+
 // k_stage_tma in the certified binary32 arithmetic, two children per thread: the children of
 // one parent always share it, so every warp whose boxes do not straddle 0 runs sign-free.  The
 // error bound advances step by step from the magnitudes of the partial values (A32C::step's
-// recursion): the summed bound of the leaves (leaf_bform), applied to the much longer chains
-// of the stages, widened the binary64 band of the curve's last level by 44% and cost more in
-// binary64 re-evaluation than it saved here.
+// recursion).  The summed bound of the leaves (leaf_bform), applied to the stages' much longer
+// chains, widens the curve's last-level band by 44-48% and does not pay: measured with the
+// band going to the float-pair tier, the depth-1 stage took 4.77 instead of 4.59 ms per step
+// (each staged group rewritten first) and the tier 1.86 instead of 1.55 ms.
 __global__ void __launch_bounds__(512)
     k_stage_tma_c(const StageDev st, const int32_t *__restrict__ lab,
                   const int32_t *__restrict__ pptr, const float4 *__restrict__ in,
@@ -1412,22 +1424,12 @@ struct ChunkBlocks {  // the staged blocks of parents p0 .. p0 + n - 1, else glo
 // stays sound on the rewritten entries.
 __device__ __forceinline__ void leaf_bform(float4 *s_blk, const int32_t *s_off, const LeafArgs &A,
                                            int npoly, int64_t np) {
-  constexpr float kKappaB = 0x1.000002p-24f;  // >= 2^-24 + 2^-50
   for (int f = 0; f < npoly; ++f) {
     const int L = A.len[f];
     const int64_t blk = A.blk[f];
     const int64_t n = np * blk;
     float4 *b = s_blk + s_off[f];
-    for (int64_t i = threadIdx.x; i < n; i += blockDim.x) {
-      const int r = (int)(i % blk);
-      const float4 v = b[i];
-      const int w = r + 1 < L - 1 ? r + 1 : (L > 1 ? L - 1 : 0);
-      const float M = fmaxf(fabsf(v.x), fabsf(v.y));
-      float B = __fmaf_ru(__fmul_ru(kKappaB, (float)w), M, v.z);
-      B = __fmaf_ru(v.z, 0x1p-50f, B);
-      B = __fadd_ru(B, kEta148);
-      b[i] = make_float4(v.x, v.y, B, B);
-    }
+    for (int64_t i = threadIdx.x; i < n; i += blockDim.x) b[i] = bform_entry(b[i], (int)(i % blk), L);
   }
 }
 

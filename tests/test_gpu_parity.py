@@ -127,6 +127,51 @@ def test_subdivide_matches_definition(vx, k, level, n, p, seed):
                 assert np.array_equal(host(ptr), ptrs[depth - 1].astype(np.int32))
 
 
+def _fanout_tuples(k, level, nparents, per, seed):
+    """Tuples whose depth-(k-2) nodes have about `per` children each (nparents of them): the
+    prune's parent marking takes one thread per node (up to 32 children per node on
+    average), a scatter from the children (up to 128) or a warp per node (more)."""
+    side = 1 << level
+    st = synth.Stream(seed)
+    heads = np.unique(st.uniform_int(0, side ** (k - 1) - 1, nparents))
+    rows = []
+    for h in heads:
+        pre = []
+        r = int(h)
+        for _ in range(k - 1):
+            pre.append(r % side)
+            r //= side
+        pre = pre[::-1]
+        last = np.unique(st.uniform_int(0, side - 1, per))
+        rows.append(np.column_stack([np.tile(pre, (last.size, 1)), last]))
+    return np.concatenate(rows).astype(np.int32)
+
+
+@pytest.mark.parametrize("k,per,p,seed", [(2, 20, 0.3, 31), (2, 90, 0.05, 32), (2, 400, 0.02, 33),
+                                          (3, 90, 0.5, 34), (3, 400, 0.3, 35), (3, 400, 0.0005, 36)])
+def test_subdivide_and_compact_across_fanouts(vx, k, per, p, seed):
+    """Split and compaction of trees whose leaves hang under few parents with many children
+    each, so that every form of the parent marking runs, against the definition."""
+    level = 9
+    t = _fanout_tuples(k, level, 12, per, seed)
+    keep = (synth.Stream(seed + 7).unit(t.shape[0]) < p).astype(np.uint8)
+    c = vx.csf_build(k, level, dev(t))
+    nxt = vx.csf_subdivide(c, dev(keep))
+    kept = t[keep == 1]
+    want = _children(kept, k) if kept.shape[0] else np.zeros((0, k), dtype=np.int32)
+    assert np.array_equal(host(nxt.tuples()), want)
+    if want.shape[0]:
+        N_ref, labs, ptrs = oracle.csf(want, k)
+        for depth in range(1, k + 1):
+            lab, ptr = nxt.export(depth)
+            assert np.array_equal(host(lab), labs[depth - 1])
+            if depth < k:
+                assert np.array_equal(host(ptr), ptrs[depth - 1].astype(np.int32))
+    out, idx = vx.csf_compact(c, dev(keep), with_index=True)
+    assert np.array_equal(host(out.tuples()), kept)
+    assert np.array_equal(host(idx), np.nonzero(keep)[0].astype(np.int32))
+
+
 @pytest.mark.parametrize("k,level,n,p,seed", [(2, 6, 900, 0.3, 12), (3, 5, 6000, 0.5, 13),
                                               (4, 3, 2000, 0.1, 14)])
 def test_compact_matches_definition(vx, k, level, n, p, seed):

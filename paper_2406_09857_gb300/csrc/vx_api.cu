@@ -278,12 +278,76 @@ class FlatMap {
   size_t mask_ = 0;
 };
 
+// Monomials in m variables (fields of b bits in a key, most significant first) -> an index:
+// a table over every exponent vector below R = E + 1 in each variable (mixed radix R) when
+// R^m is small, the hash map otherwise.
+class KeyIndex {
+ public:
+  void build(const std::vector<uint64_t> &keys, int m, int b, int32_t E) {
+    m_ = m;
+    b_ = b;
+    R_ = (int64_t)E + 1;
+    int64_t size = 1;
+    dense_ = true;
+    for (int j = 0; j < m && dense_; ++j) {
+      size *= R_;
+      dense_ = size <= ((int64_t)1 << 22);
+    }
+    if (dense_) {
+      tab_.assign((size_t)size, -1);
+      for (size_t f = 0; f < keys.size(); ++f) {
+        const int64_t ix = of_key(keys[f]);
+        if (ix >= 0) tab_[(size_t)ix] = (int32_t)f;
+      }
+    } else {
+      map_.reserve(keys.size());
+      for (size_t f = 0; f < keys.size(); ++f) map_.put(keys[f], (int32_t)f);
+    }
+  }
+  int32_t get_key(uint64_t key) const {  // -1 if absent
+    if (!dense_) return map_.get(key);
+    const int64_t ix = of_key(key);
+    return ix < 0 ? -1 : tab_[(size_t)ix];
+  }
+  // the monomial of exponents e[from..k-1] (m = k - from of them)
+  int32_t get(const int32_t *e, int from, int k) const {
+    if (!dense_) {
+      uint64_t key = 0;
+      for (int v = from; v < k; ++v) key = (key << b_) | (uint64_t)e[v];
+      return map_.get(key);
+    }
+    int64_t ix = 0;
+    for (int v = from; v < k; ++v) {
+      if (e[v] >= R_) return -1;
+      ix = ix * R_ + e[v];
+    }
+    return tab_[(size_t)ix];
+  }
+
+ private:
+  int64_t of_key(uint64_t key) const {
+    const uint64_t mask = b_ >= 64 ? ~0ull : ((1ull << b_) - 1);
+    int64_t ix = 0;
+    for (int j = 0; j < m_; ++j) {
+      const int64_t e = (int64_t)((key >> (b_ * (m_ - 1 - j))) & mask);
+      if (e >= R_) return -1;
+      ix = ix * R_ + e;
+    }
+    return ix;
+  }
+  bool dense_ = false;
+  int m_ = 0, b_ = 0;
+  int64_t R_ = 0;
+  std::vector<int32_t> tab_;
+  FlatMap map_;
+};
+
 struct HostStage {
   int32_t nfib = 0, maxlen = 0;
   int64_t blk_in = 0, blk_out = 0;
   std::vector<uint64_t> keys;  // fibre monomial in x_{s+2}..x_k, key_bits(k) bits per exponent
   std::vector<int32_t> rowoff, fiblen, outpos, fiboff, outpos_fm;
-  FlatMap index;
+  KeyIndex index;
 };
 
 struct HostPoly {
@@ -294,13 +358,6 @@ struct HostPoly {
 // A monomial in up to k - 1 variables packed into 64 bits: 16 bits per exponent up to
 // k = 5, 64 / (k - 1) bits beyond (12 bits at k = 6).
 static int key_bits(int k) { return k <= 5 ? 16 : 64 / (k - 1); }
-
-static uint64_t suffix_key(const int32_t *e, int from, int k) {
-  const int b = key_bits(k);
-  uint64_t key = 0;
-  for (int v = from; v < k; ++v) key = (key << b) | (uint64_t)e[v];
-  return key;
-}
 
 // The binary32 encodings of the stage-0 coefficient block, made on the device from the
 // binary64 intervals [c.x, c.y] (c.x = c.y for a point coefficient):
@@ -460,15 +517,21 @@ static int pack_poly(int k, const vx_poly &p, HostPoly *hp, const double *chi = 
   }
   const int T = std::max(1, std::min(chunks, 64));
   const int32_t emax = (1 << key_bits(k)) - 1;
+  int32_t E = 0;  // the largest exponent of any variable
   {
     // the first bad exponent and the first bad coefficient (each chunk its own first)
     std::vector<int64_t> bad_e(T, -1), bad_c(T, -1);
+    std::vector<int32_t> top(T, 0);
     for_chunks(nt, T, [&](int c, int64_t a, int64_t b) {
-      for (int64_t t = a * k; t < b * k; ++t)
+      int32_t mx = 0;
+      for (int64_t t = a * k; t < b * k; ++t) {
         if (p.exps[t] < 0 || p.exps[t] > emax) {
           bad_e[c] = t;
           break;
         }
+        mx = std::max(mx, p.exps[t]);
+      }
+      top[c] = mx;
       for (int64_t t = a; t < b; ++t)
         if (!std::isfinite(p.coefs[t]) ||
             (chi && !(std::isfinite(chi[t]) && chi[t] >= p.coefs[t]))) {
@@ -481,6 +544,7 @@ static int pack_poly(int k, const vx_poly &p, HostPoly *hp, const double *chi = 
         set_error("polynomial: exponent %d outside [0, %d]", p.exps[bad_e[c]], emax);
         return VX_EINVAL;
       }
+    for (int c = 0; c < T; ++c) E = std::max(E, top[c]);
     for (int c = 0; c < T; ++c)
       if (bad_c[c] >= 0) {
         set_error("polynomial: coefficient %d is not finite (or not an interval)", (int)bad_c[c]);
@@ -494,9 +558,8 @@ static int pack_poly(int k, const vx_poly &p, HostPoly *hp, const double *chi = 
   for (int s = k - 1; s >= 0; --s) {
     HostStage &S = hp->st[s];
     const int32_t nf = (int32_t)S.keys.size();
-    FlatMap idx;
-    idx.reserve((size_t)nf);
-    for (int32_t f = 0; f < nf; ++f) idx.put(S.keys[f], f);
+    KeyIndex idx;
+    idx.build(S.keys, k - 1 - s, key_bits(k), E);
     // per chunk of terms the longest fibre lengths, then their maxima
     std::vector<std::vector<int32_t>> lens(T);
     std::vector<uint8_t> miss(T, 0);
@@ -505,7 +568,7 @@ static int pack_poly(int k, const vx_poly &p, HostPoly *hp, const double *chi = 
       len.assign(nf, 1);
       for (int64_t t = a; t < b; ++t) {
         const int32_t *e = p.exps + t * k;
-        const int32_t g = idx.get(suffix_key(e, s + 1, k));
+        const int32_t g = idx.get(e, s + 1, k);
         if (g < 0) {
           miss[c] = 1;
           return;
@@ -535,8 +598,7 @@ static int pack_poly(int k, const vx_poly &p, HostPoly *hp, const double *chi = 
       S.fiblen[f] = len[order[f]];
     }
     S.keys.swap(keys);
-    S.index.reserve((size_t)nf);
-    for (int32_t f = 0; f < nf; ++f) S.index.put(S.keys[f], f);
+    S.index.build(S.keys, k - 1 - s, key_bits(k), E);
     S.nfib = nf;
     S.maxlen = S.fiblen[0];
     S.rowoff.assign(S.maxlen + 1, 0);
@@ -578,7 +640,7 @@ static int pack_poly(int k, const vx_poly &p, HostPoly *hp, const double *chi = 
       const uint64_t mask = sh ? ((uint64_t)1 << sh) - 1 : 0;
       for (int32_t f = 0; f < S.nfib; ++f) {
         const uint64_t a = S.keys[f] >> sh;
-        const int32_t g = T.index.get(S.keys[f] & mask);
+        const int32_t g = T.index.get_key(S.keys[f] & mask);
         S.outpos[f] = T.rowoff[a] + g;
         S.outpos_fm[f] = T.fiboff[g] + (int32_t)a;
       }
@@ -592,7 +654,7 @@ static int pack_poly(int k, const vx_poly &p, HostPoly *hp, const double *chi = 
   for_chunks(nt, T, [&](int c, int64_t a, int64_t b) {
     for (int64_t t = a; t < b; ++t) {
       const int32_t *e = p.exps + t * k;
-      const int32_t f = S0.index.get(suffix_key(e, 1, k));
+      const int32_t f = S0.index.get(e, 1, k);
       const int64_t pos = S0.rowoff[e[0]] + f;
       // a monomial seen before, by this chunk or another one (atomic: chunks run at once)
       if (__atomic_exchange_n(&seen[pos], (uint8_t)1, __ATOMIC_RELAXED)) {
@@ -842,13 +904,17 @@ static int pinned_get(size_t bytes, void **p, size_t *cap) {
     }
   }
   const size_t c = (bytes + (16u << 20) - 1) & ~(size_t)((16u << 20) - 1);  // 16 MiB steps
-  if (cudaHostAlloc(p, c, cudaHostAllocDefault) != cudaSuccess) {
+  // mapped: the device can also write into it directly (the result's box codes)
+  if (cudaHostAlloc(p, c, cudaHostAllocMapped) != cudaSuccess) {
     set_error("cudaHostAlloc of %zu bytes failed", c);
     return VX_ENOMEM;
   }
   *cap = c;
   return VX_OK;
 }
+
+// the box codes written by the device into the result's pinned buffer (else via device memory)
+constexpr bool kCodesToHost = true;
 
 static void pinned_put(void *p, size_t cap) {
   if (!p) return;
@@ -871,8 +937,11 @@ extern "C" {
 
 const char *vx_last_error(void) { return g_err; }
 
+// keep_host: keep a host copy of the polynomials (the dense plan and the Taylor form's derived
+// system are made from it later); a system that one call creates, uses and frees need not
 static int system_create_impl(const vx_poly *F, int32_t npoly, const double *const *chi,
-                              void *stream, vx_system **out, const int32_t *rel = nullptr);
+                              void *stream, vx_system **out, const int32_t *rel = nullptr,
+                              bool keep_host = true);
 
 int vx_system_create(const vx_poly *F, int32_t npoly, void *stream, vx_system **out) {
   clear_error();
@@ -888,7 +957,7 @@ int vx_system_create_ex(const vx_poly *F, const double *const *coefs_hi, const i
 // chi (nullable; entries nullable): per polynomial, the upper ends of interval coefficients
 // (F[f].coefs the lower ends); rel (nullable): the relation of each polynomial.
 static int system_create_impl(const vx_poly *F, int32_t npoly, const double *const *chi,
-                              void *stream, vx_system **out, const int32_t *rel) {
+                              void *stream, vx_system **out, const int32_t *rel, bool keep_host) {
   if (!out || !F || npoly < 1 || npoly > VX_MAXPOLY) {
     set_error("vx_system_create: need 1..%d polynomials and an out pointer", VX_MAXPOLY);
     return VX_EINVAL;
@@ -986,7 +1055,7 @@ static int system_create_impl(const vx_poly *F, int32_t npoly, const double *con
   sys->exps.resize(npoly);
   sys->coefs.resize(npoly);
   sys->coefs_hi.resize(npoly);
-  for (int f = 0; f < npoly; ++f) {
+  for (int f = 0; f < npoly && keep_host; ++f) {
     sys->exps[f].assign(F[f].exps, F[f].exps + (size_t)F[f].nterms * k);
     sys->coefs[f].assign(F[f].coefs, F[f].coefs + F[f].nterms);
     if (chi && chi[f]) sys->coefs_hi[f].assign(chi[f], chi[f] + F[f].nterms);
@@ -1848,8 +1917,10 @@ static void result_append(vx_result *R, CsfObj &fin) {
 // Level l of Algorithm 3 on cur: C0 (and C1 from its level on); keep flags of the leaves
 // (caller frees), the boxes C1 certified moved to R->incl.  With the vertex test, cur is
 // replaced by its C0 survivors.
+// *status_deferred: the device status of the level's evaluation was queued into status_word()
+// instead of read (the caller reads it after its next wait on the stream).
 static int level_step(EncloseRun &E, CsfObj &cur, int l, uint8_t **keep_out,
-                      int64_t *included_out) {
+                      int64_t *included_out, bool *status_deferred) {
   const int k = E.k;
   const vx_opts &opts = E.opts;
   const cudaStream_t s = E.s;
@@ -1857,6 +1928,7 @@ static int level_step(EncloseRun &E, CsfObj &cur, int l, uint8_t **keep_out,
   Timer *tm = E.tm;
   *keep_out = nullptr;
   *included_out = 0;
+  *status_deferred = false;
   LevelGrid g;
   VX_CHECK(make_grid(k, E.dom, l, &g));
   const int64_t n = cur.v.N[k - 1];
@@ -1897,7 +1969,14 @@ static int level_step(EncloseRun &E, CsfObj &cur, int l, uint8_t **keep_out,
     R->recheck[l] += nr;
     R->recheck64[l] += mode == VX_FP32 ? nr64 : nr;
     int st = 0;
-    if (rc == VX_OK) rc = take_device_status(s, &st);
+    int *hw = (!c1_here && n > 0) ? status_word() : nullptr;
+    if (rc == VX_OK && hw) {  // read with the prune's wait that follows
+      *hw = 0;
+      rc = queue_device_status(s, hw);
+      *status_deferred = rc == VX_OK;
+    } else if (rc == VX_OK) {
+      rc = take_device_status(s, &st);
+    }
     if (rc == VX_OK && st) {
       set_error("enclose: a bounded device wait gave up at level %d", l);
       rc = VX_ETIMEOUT;
@@ -2019,18 +2098,36 @@ static int run_levels(EncloseRun &E, CsfObj &cur, int l) {
   for (; l <= E.depth && rc == VX_OK; ++l) {
     uint8_t *keep = nullptr;
     int64_t included = 0;
-    rc = level_step(E, cur, l, &keep, &included);
+    bool deferred = false;
+    rc = level_step(E, cur, l, &keep, &included, &deferred);
     if (rc != VX_OK) break;
+    // the level's device status, queued by level_step: the prune (n > 0) waits on the stream
+    // for its counts, after which the word is in place; otherwise wait for it here
+    auto status_after_prune = [&](int rc0) -> int {
+      if (!deferred || (rc0 == VX_OK && *status_word() == 0)) return rc0;
+      int st = 0;
+      const int r = take_device_status(E.s, &st);
+      if (r != VX_OK) return r;
+      if (st) {
+        set_error("enclose: a bounded device wait gave up at level %d", l);
+        return VX_ETIMEOUT;
+      }
+      return rc0;
+    };
     if (l == E.depth) {
       CsfObj fin;
-      rc = csf_prune(cur.v, keep, 0, nullptr, E.s, &fin, E.tm);
+      const int rp = csf_prune(cur.v, keep, 0, nullptr, E.s, &fin, E.tm);
+      rc = status_after_prune(rp);
+      if (rp == VX_OK && rc != VX_OK) csf_release(&fin);
       if (rc == VX_OK) {
         E.R->kept[l] += fin.v.N[k - 1] + included;
         result_append(E.R, fin);
       }
     } else {
       CsfObj next;
-      rc = csf_prune(cur.v, keep, 1, nullptr, E.s, &next, E.tm, E.cap);
+      const int rp = csf_prune(cur.v, keep, 1, nullptr, E.s, &next, E.tm, E.cap);
+      rc = status_after_prune(rp);
+      if (rp == VX_OK && rc != VX_OK) csf_release(&next);
       if (rc == VX_EOVERFLOW && E.opts.c1 == 0) {
         // the next level does not fit one tree: run it in x_1 ranges
         clear_error();
@@ -2234,7 +2331,10 @@ int vx_enclose(const vx_poly *F, int32_t npoly, const double *h_domain, int32_t 
   *out = nullptr;
   cudaStream_t s = library_stream();
   vx_system *sys = nullptr;
-  VX_CHECK(vx_system_create(F, npoly, (void *)s, &sys));
+  // the system lives for this call only: the host copy of the polynomials serves only the
+  // Taylor form's derived system
+  VX_CHECK(system_create_impl(F, npoly, nullptr, (void *)s, &sys, nullptr,
+                              opts && opts->taylor_order > 0));
   int rc = vx_enclose_system(sys, h_domain, depth, opts, (void *)s, out);
   vx_system_free(sys);
   return rc;
@@ -2450,7 +2550,9 @@ int batch_group(const std::vector<int32_t> &ids, const vx_poly *const *systems,
         return;
       }
       for (int t = next++; t < S && first.load() == VX_OK; t = next++) {
-        const int r = vx_system_create(systems[ids[t]], npoly[ids[t]], (void *)ws, &sysv[t]);
+        // no host copy of the polynomials: a batch has no Taylor form or dense plan
+        const int r = system_create_impl(systems[ids[t]], npoly[ids[t]], nullptr, (void *)ws,
+                                         &sysv[t], nullptr, false);
         if (r != VX_OK) {
           errs[w] = std::string("system ") + std::to_string(ids[t]) + ": " + vx_last_error();
           int expected = VX_OK;
@@ -2856,8 +2958,39 @@ int vx_result_box_codes(vx_result *R, int64_t *n, int32_t *code_bytes, const voi
       void *hb = nullptr;
       size_t cap = 0;
       VX_CHECK(pinned_get((size_t)m * cb, &hb, &cap));
+      // the codes kernel writes straight into the pinned buffer when the device can address
+      // it (a mapped allocation: the stores cross the host link as they are made), else into
+      // device memory followed by a copy
+      void *dh = nullptr;
+      int rc = VX_OK;
+      if (kCodesToHost && cudaHostGetDevicePointer(&dh, hb, 0) == cudaSuccess && dh) {
+        int64_t at = 0;
+        for (size_t j = 0; j < trees.size() && rc == VX_OK; ++j) {
+          const int64_t mj = trees[j]->v.N[k - 1];
+          if (mj == 0) continue;
+          rc = csf_box_codes_dev(trees[j]->v, (char *)dh + (size_t)at * cb, s);
+          at += mj;
+        }
+        if (rc == VX_OK && cudaStreamSynchronize(s) != cudaSuccess) {
+          set_error("writing the box codes to the host failed: %s",
+                    cudaGetErrorString(cudaGetLastError()));
+          rc = VX_ECUDA;
+        }
+        if (rc != VX_OK) {
+          pinned_put(hb, cap);
+          return rc;
+        }
+        R->hcodes = hb;
+        R->hcodes_cap = cap;
+        R->hcodes_count = m;
+        *n = R->hcodes_count;
+        *code_bytes = cb;
+        *h_codes = R->hcodes;
+        return VX_OK;
+      }
+      cudaGetLastError();  // a buffer the device cannot address: the copy below
       void *d = nullptr;
-      int rc = dmalloc(&d, (size_t)mmax * cb, s);
+      rc = dmalloc(&d, (size_t)mmax * cb, s);
       int64_t at = 0;
       for (size_t j = 0; j < trees.size() && rc == VX_OK; ++j) {
         const int64_t mj = trees[j]->v.N[k - 1];

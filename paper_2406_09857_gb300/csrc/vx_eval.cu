@@ -2498,6 +2498,12 @@ int set_wait_polls(int64_t polls) {
   return VX_OK;
 }
 
+int *status_word() {
+  static thread_local int *p = nullptr;
+  if (!p && cudaHostAlloc((void **)&p, sizeof(int), cudaHostAllocDefault) != cudaSuccess) p = nullptr;
+  return p;
+}
+
 int queue_device_status(cudaStream_t s, int *h_pinned) {
   VX_CUDA(cudaMemcpyFromSymbolAsync(h_pinned, g_vx_status, sizeof(int), 0, cudaMemcpyDeviceToHost, s));
   return VX_OK;

@@ -256,6 +256,8 @@ int csf_prune_forest(const CsfView &in, const uint8_t *d_keep, int split, int32_
 // Queues a copy of the device status word (bounded waits that gave up) into pinned host memory
 // (read it after the stream's next synchronisation).
 int queue_device_status(cudaStream_t s, int *h_pinned);
+// A pinned status word of the calling host thread (null if it cannot be allocated).
+int *status_word();
 // The complete tree of grid level `level` (every box), filled directly.
 int csf_full_grid_dev(int k, int level, cudaStream_t s, CsfObj *out);
 // ptr[d][N[d]] = N[d+1] for every depth d < k-1.

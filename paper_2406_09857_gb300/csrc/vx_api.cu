@@ -415,6 +415,40 @@ __global__ void k_encode_coefs(const double2 *__restrict__ c64, int64_t n, float
   }
 }
 
+// The stage-0 blocks fibre-major: entry a of fibre f (row-major at rowoff[a] + f) to
+// fiboff[f] + a, so that a stage-0 Horner walks consecutive entries; every encoding of the
+// coefficients (binary64 intervals, midpoint-radius, certified binary32, float pairs and their
+// bounds) is permuted the same way.
+struct Stage0Blocks {
+  const double2 *c64;
+  const float2 *c32;
+  const float4 *c32c, *cp;
+  const float *ep;
+};
+struct Stage0BlocksFm {
+  double2 *c64;
+  float2 *c32;
+  float4 *c32c, *cp;
+  float *ep;
+};
+__global__ void k_fibre_major(Stage0Blocks r, const int32_t *__restrict__ rowoff,
+                              const int32_t *__restrict__ fiblen,
+                              const int32_t *__restrict__ fiboff, int32_t nfib,
+                              Stage0BlocksFm w) {
+  const int stride = (int)(gridDim.x * blockDim.x);
+  for (int f = (int)(blockIdx.x * blockDim.x + threadIdx.x); f < nfib; f += stride) {
+    const int L = fiblen[f], o = fiboff[f];
+    for (int a = 0; a < L; ++a) {
+      const int i = rowoff[a] + f;
+      w.c64[o + a] = r.c64[i];
+      w.c32[o + a] = r.c32[i];
+      w.c32c[o + a] = r.c32c[i];
+      w.cp[o + a] = r.cp[i];
+      w.ep[o + a] = r.ep[i];
+    }
+  }
+}
+
 // chi (nullable): upper ends of interval coefficients [p.coefs[t], chi[t]]
 // Host threads kept for the process (one per core but this one's, at most 15): run(n, fn)
 // calls fn(c) for c = 0..n-1 on them and on the calling thread and returns when all are done.
@@ -1008,8 +1042,8 @@ static int system_create_impl(const vx_poly *F, int32_t npoly, const double *con
   auto al = [](size_t x) { return (x + 255) & ~(size_t)255; };
   size_t bytes = 0;
   for (int f = 0; f < npoly; ++f) {
-    bytes += al(hp[f].c64.size() * sizeof(double2)) + al(hp[f].c64.size() * sizeof(float2)) +
-             2 * al(hp[f].c64.size() * sizeof(float4)) + al(hp[f].c64.size() * sizeof(float));
+    bytes += 2 * al(hp[f].c64.size() * sizeof(double2)) + 2 * al(hp[f].c64.size() * sizeof(float2)) +
+             4 * al(hp[f].c64.size() * sizeof(float4)) + 2 * al(hp[f].c64.size() * sizeof(float));
     for (int s = 0; s < k; ++s) {
       const HostStage &S = hp[f].st[s];
       bytes += al((S.maxlen + 1) * 4) + 3 * al((size_t)S.nfib * 4) + al(((size_t)S.nfib + 1) * 4);
@@ -1098,8 +1132,13 @@ static int system_create_impl(const vx_poly *F, int32_t npoly, const double *con
     PolyDev &P = sys->dev.p[f];
     P.c32 = (const float2 *)reserve(hp[f].c64.size() * sizeof(float2));
     P.c32c = (const float4 *)reserve(hp[f].c64.size() * sizeof(float4));
+    P.c32c_fm = (const float4 *)reserve(hp[f].c64.size() * sizeof(float4));
     P.cp = (const float4 *)reserve(hp[f].c64.size() * sizeof(float4));
     P.ep = (const float *)reserve(hp[f].c64.size() * sizeof(float));
+    P.cp_fm = (const float4 *)reserve(hp[f].c64.size() * sizeof(float4));
+    P.ep_fm = (const float *)reserve(hp[f].c64.size() * sizeof(float));
+    P.c64_fm = (const double2 *)reserve(hp[f].c64.size() * sizeof(double2));
+    P.c32_fm = (const float2 *)reserve(hp[f].c64.size() * sizeof(float2));
   }
   cudaError_t e = cudaMemcpyAsync(sys->mem, host, sys->upload_bytes, cudaMemcpyHostToDevice, s);
   for (int f = 0; f < npoly && e == cudaSuccess; ++f) {
@@ -1113,6 +1152,18 @@ static int system_create_impl(const vx_poly *F, int32_t npoly, const double *con
                                                  const_cast<float *>(sys->dev.p[f].ep));
     note_launch();
     e = cudaGetLastError();
+    if (e == cudaSuccess) {
+      const StageDev &S0 = sys->dev.p[f].st[0];
+      const PolyDev &P = sys->dev.p[f];
+      const Stage0Blocks r{P.c64, P.c32, P.c32c, P.cp, P.ep};
+      const Stage0BlocksFm w{const_cast<double2 *>(P.c64_fm), const_cast<float2 *>(P.c32_fm),
+                             const_cast<float4 *>(P.c32c_fm), const_cast<float4 *>(P.cp_fm),
+                             const_cast<float *>(P.ep_fm)};
+      k_fibre_major<<<(unsigned)std::min<int64_t>((S0.nfib + 127) / 128, (int64_t)sm_count() * 8),
+                      128, 0, s>>>(r, S0.rowoff, S0.fiblen, S0.fiboff, S0.nfib, w);
+      note_launch();
+      e = cudaGetLastError();
+    }
   }
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);
   pinned_put(hstage, hcap);  // the copy has completed (or failed): the buffer is free again

@@ -157,6 +157,7 @@ struct A64 {
   static __device__ __forceinline__ double hi(V J) { return J.y; }
   static __device__ __forceinline__ bool tight(V, float) { return false; }
   static __host__ __device__ __forceinline__ const V *coef(const PolyDev &p) { return p.c64; }
+  static __host__ __device__ __forceinline__ const V *coef_fm(const PolyDev &p) { return p.c64_fm; }
 };
 
 // ---------------------------------------------------------------------------------------
@@ -231,6 +232,7 @@ struct A32 {
   static __device__ __forceinline__ double hi(V J) { return __dadd_ru((double)J.x, (double)J.y); }
   static __device__ __forceinline__ bool tight(V J, float theta) { return fabsf(J.x) >= theta * J.y; }
   static __host__ __device__ __forceinline__ const V *coef(const PolyDev &p) { return p.c32; }
+  static __host__ __device__ __forceinline__ const V *coef_fm(const PolyDev &p) { return p.c32_fm; }
 };
 
 // ---------------------------------------------------------------------------------------
@@ -331,6 +333,7 @@ struct A32C {
   static __device__ __forceinline__ double hi(V J) { return -(double)J.y; }
   static __device__ __forceinline__ bool tight(V, float) { return false; }
   static __host__ __device__ __forceinline__ const V *coef(const PolyDev &p) { return p.c32c; }
+  static __host__ __device__ __forceinline__ const V *coef_fm(const PolyDev &p) { return p.c32c_fm; }
 };
 
 // Algorithm 1 on one fibre: entries rowoff[a] + f (a = L-1 .. 0) of a block whose entry e is
@@ -447,7 +450,7 @@ __device__ __forceinline__ void stage_chunk(const StageDev &st, const int32_t *o
 // (out_estride = nnodes, out_nstride = 1) when an inner stage reads it, node-major
 // (out_estride = 1, out_nstride = blk_out) when the leaves do, so that a leaf's Horner walks
 // consecutive entries of its parent's block.
-template <class AR>
+template <class AR, bool FM = false>
 __global__ void __launch_bounds__(kThreads)
     k_stage(const StageDev st, const int32_t *__restrict__ lab, const int32_t *__restrict__ par,
             const typename AR::V *__restrict__ in, int64_t in_estride, int64_t in_nstride,
@@ -459,8 +462,8 @@ __global__ void __launch_bounds__(kThreads)
   const int64_t nwarps = nchunk * G;
   for (int64_t w = (int64_t)blockIdx.x * kWarpsPerBlock + (threadIdx.x >> 5); w < nwarps;
        w += (int64_t)gridDim.x * kWarpsPerBlock)
-    stage_chunk<AR>(st, st.outpos, s_rowoff, lab, par, 0, in, in_estride, in_nstride, out, out_estride,
-                    out_nstride, nnodes, w % nchunk, (int)(w / nchunk), G, g);
+    stage_chunk<AR, FM>(st, st.outpos, s_rowoff, lab, par, 0, in, in_estride, in_nstride, out,
+                        out_estride, out_nstride, nnodes, w % nchunk, (int)(w / nchunk), G, g);
 }
 
 // Stage d (1 <= d < k-1) with the parent's block in shared memory.  The block is fibre-major
@@ -1136,6 +1139,7 @@ __device__ __forceinline__ void stage_chunk_c(const StageDev &st, const int32_t 
 // Stage d < k-1 in the certified binary32 arithmetic, two consecutive nodes per thread: warp w
 // takes node pairs of chunk w % nchunk (64 nodes) and fibres g, g+G, ... (g = w / nchunk), as
 // k_stage does with one node per lane.
+template <bool FM>
 __global__ void __launch_bounds__(kThreads, 6)
     k_stage_c(const StageDev st, const int32_t *__restrict__ lab, const int32_t *__restrict__ par,
               const float4 *__restrict__ in, int64_t in_estride, int64_t in_nstride,
@@ -1148,7 +1152,7 @@ __global__ void __launch_bounds__(kThreads, 6)
   // the loop bound is the same for the 32 lanes of a warp, so the vote inside sees all of them
   for (int64_t w = (int64_t)blockIdx.x * kWarpsPerBlock + (threadIdx.x >> 5); w < nwarps;
        w += (int64_t)gridDim.x * kWarpsPerBlock)
-    stage_chunk_c(st, st.outpos, s_rowoff, lab, par, 0, in, in_estride, in_nstride, out, out_estride,
+    stage_chunk_c<FM>(st, st.outpos, s_rowoff, lab, par, 0, in, in_estride, in_nstride, out, out_estride,
                   out_nstride, nnodes, w % nchunk, (int)(w / nchunk), G, g);
 }
 
@@ -1904,8 +1908,19 @@ int eval_level_t(const SysDev &sys, const CsfView &c, const LevelGrid &grid, dou
           if (G < 1) G = 1;
           int64_t blocks = (nchunk * G + kWarpsPerBlock - 1) / kWarpsPerBlock;
           if (blocks > (int64_t)sm_count() * 64) blocks = (int64_t)sm_count() * 64;
-          if (pairs)
-            k_stage_c<<<(unsigned)blocks, kThreads, (st.maxlen + 1) * sizeof(int32_t), s>>>(
+          // stage 0: the fibre-major copy of the coefficient block (consecutive loads along
+          // a fibre, where the row-major block has one cache line per step)
+          const V *fm0 = d == 0 ? AR::coef_fm(sys.p[f]) : nullptr;
+          if (pairs && fm0)
+            k_stage_c<true><<<(unsigned)blocks, kThreads, (st.maxlen + 1) * sizeof(int32_t), s>>>(
+                st, c.lab[d], nullptr, (const float4 *)fm0, 1, 0, (float4 *)buf[f][d], oe, on,
+                c.N[d], nchunk, (int)G, pg.ax[d]);
+          else if (fm0)
+            k_stage<AR, true><<<(unsigned)blocks, kThreads, (st.maxlen + 1) * sizeof(int32_t), s>>>(
+                st, c.lab[d], nullptr, fm0, 1, 0, buf[f][d], oe, on, c.N[d], nchunk, (int)G,
+                pg.ax[d]);
+          else if (pairs)
+            k_stage_c<false><<<(unsigned)blocks, kThreads, (st.maxlen + 1) * sizeof(int32_t), s>>>(
                 st, c.lab[d], d == 0 ? nullptr : c.par[d], (const float4 *)in, in_estride,
                 in_nstride, (float4 *)buf[f][d], oe, on, c.N[d], nchunk, (int)G, pg.ax[d]);
           else
@@ -2074,21 +2089,23 @@ __global__ void __launch_bounds__(kThreads, 6)
     const int64_t poff = d > 0 ? __ldg(offp + t) : 0;
     for (int f = 0; f < T.dev.npoly; ++f) {
       const StageDev &st = T.dev.p[f].st[d];
-      // certified binary32: an inner stage's blocks are written and read fibre-major
+      // stage 0 reads the coefficient block's fibre-major copy; certified binary32 also
+      // writes and reads the inner stages' blocks fibre-major
       const int32_t *outpos = FMF && d + 2 < k ? st.outpos_fm : st.outpos;
-      const V *in = d == 0 ? AR::coef(T.dev.p[f])
+      const bool fmr = d == 0 || FMF;
+      const V *in = d == 0 ? AR::coef_fm(T.dev.p[f])
                            : (const V *)blk[((int64_t)t * VX_MAXPOLY + f) * VX_KMAX + d - 1];
       V *out = (V *)blk[((int64_t)t * VX_MAXPOLY + f) * VX_KMAX + d];
       const int64_t in_nstride = d == 0 ? 0 : st.blk_in;
       if constexpr (PAIRS) {
-        if (FMF && d > 0)
+        if (fmr)
           stage_chunk_c<true>(st, outpos, st.rowoff, lab, par, poff, (const float4 *)in, 1, in_nstride,
                               (float4 *)out, 1, st.blk_out, n, chunk, grp, G, T.ax[d]);
         else
           stage_chunk_c<false>(st, outpos, st.rowoff, lab, par, poff, (const float4 *)in, 1, in_nstride,
                                (float4 *)out, 1, st.blk_out, n, chunk, grp, G, T.ax[d]);
       } else {
-        if (FMF && d > 0)
+        if (fmr)
           stage_chunk<AR, true>(st, outpos, st.rowoff, lab, par, poff, in, 1, in_nstride, out, 1,
                                 st.blk_out, n, chunk, grp, G, T.ax[d]);
         else
@@ -2599,13 +2616,18 @@ __device__ __forceinline__ void pair_step(float4 &j, float &ej, const float4 &c,
   j = r;
 }
 
-// Algorithm 1 on one fibre (entry a at vb[(rowoff[a] + f) estride], its bound in eb), Horner in
-// y = -x with odd coefficients negated when the box is x <= 0 (the result is J itself).
+// Algorithm 1 on one fibre (entry a at vb[(rowoff[a] + f) estride], its bound in eb; with
+// fiboff non-null at vb[fiboff[f] + a], the fibre-major block), Horner in y = -x with odd
+// coefficients negated when the box is x <= 0 (the result is J itself).
 __device__ __forceinline__ void pair_horner(const float4 *__restrict__ vb,
                                             const float *__restrict__ eb, int64_t estride,
                                             const int32_t *__restrict__ rowoff, int f, int L,
-                                            const PairX &x, float4 &J, float &E) {
-  auto at = [&](int a) { return (int64_t)(__ldg(rowoff + a) + f) * estride; };
+                                            const PairX &x, float4 &J, float &E,
+                                            const int32_t *__restrict__ fiboff = nullptr) {
+  const int64_t fo = fiboff ? (int64_t)__ldg(fiboff + f) : 0;
+  auto at = [&](int a) {
+    return fiboff ? fo + a : (int64_t)(__ldg(rowoff + a) + f) * estride;
+  };
   int64_t o = at(L - 1);
   const float4 top = vb[o];
   E = eb[o];
@@ -2648,7 +2670,7 @@ __global__ void __launch_bounds__(256)
                  const int32_t *__restrict__ par, const float4 *__restrict__ in_v,
                  const float *__restrict__ in_e, int64_t in_estride, int64_t in_nstride,
                  float4 *__restrict__ out_v, float *__restrict__ out_e, int64_t nnodes,
-                 AxisGrid g) {
+                 AxisGrid g, bool fm) {
   const int64_t total = nnodes * st.nfib;
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
   for (int64_t it = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; it < total; it += stride) {
@@ -2660,7 +2682,7 @@ __global__ void __launch_bounds__(256)
     float E = INFINITY;
     if (x.ok)
       pair_horner(in_v + p * in_nstride, in_e + p * in_nstride, in_estride, st.rowoff, f,
-                  __ldg(st.fiblen + f), x, J, E);
+                  __ldg(st.fiblen + f), x, J, E, fm ? st.fiboff : nullptr);
     const int64_t o = (int64_t)__ldg(st.outpos + f) * nnodes + node;
     out_v[o] = J;
     out_e[o] = E;
@@ -2737,11 +2759,14 @@ int eval_level_pair(const SysDev &sys, const CsfView &c, const LevelGrid &grid, 
       madds += w;
       if (tm && tm->on) rc = tm->begin(d == 0 ? KK_STAGE0_PAIR : KK_STAGEJ_PAIR, w);
       if (rc != VX_OK) break;
-      const float4 *in_v = d == 0 ? sys.p[f].cp : val[f][d - 1];
-      const float *in_e = d == 0 ? sys.p[f].ep : err[f][d - 1];
+      // stage 0 from the fibre-major copies of the coefficients (consecutive loads along a
+      // fibre)
+      const bool fm0 = d == 0 && sys.p[f].cp_fm && sys.p[f].ep_fm;
+      const float4 *in_v = d == 0 ? (fm0 ? sys.p[f].cp_fm : sys.p[f].cp) : val[f][d - 1];
+      const float *in_e = d == 0 ? (fm0 ? sys.p[f].ep_fm : sys.p[f].ep) : err[f][d - 1];
       k_stage_pair<<<grid_of(c.N[d] * st.nfib), 256, 0, s>>>(
           st, c.lab[d], d == 0 ? nullptr : c.par[d], in_v, in_e, d == 0 ? 1 : c.N[d - 1],
-          d == 0 ? 0 : 1, val[f][d], err[f][d], c.N[d], grid.ax[d]);
+          d == 0 ? 0 : 1, val[f][d], err[f][d], c.N[d], grid.ax[d], fm0);
       note_launch();
       if (cudaGetLastError() != cudaSuccess) {
         set_error("float-pair stage launch failed");

@@ -76,8 +76,15 @@ struct PolyDev {
   const double2 *c64;  // stage-0 input block as degenerate intervals (lo = hi = coefficient)
   const float2 *c32;   // stage-0 input block as <m, r> binary32 midpoint-radius pairs
   const float4 *c32c;  // stage-0 input block as binary32 [RD(c), RU(c)] with error bound
+  // the three blocks above fibre-major (st[0].fiboff): a stage-0 Horner walks consecutive
+  // entries instead of one row (a cache line) per step
+  const double2 *c64_fm;
+  const float2 *c32_fm;
+  const float4 *c32c_fm;
   const float4 *cp;    // stage-0 input block as float pairs (lo_h, lo_l, -hi_h, -hi_l) ...
   const float *ep;     // ... and their error bounds (eval_level_pair)
+  const float4 *cp_fm;  // the same two fibre-major (st[0].fiboff)
+  const float *ep_fm;
 };
 
 struct SysDev {

@@ -406,6 +406,44 @@ __device__ __forceinline__ typename AR::V horner1_any(const typename AR::V *__re
   return horner1<AR, 0>(base, stride, L, x);
 }
 
+// A block entry of the leaf stage rewritten for the summed bound: entry b (row b of the
+// polynomial's single fibre, length L) keeps its binary32 ends and gets, in place of its bound
+// E, B_b = RU((1 + 2^-50) E + kappa w_b M_b) + 2^-148, M_b = max(|lo|, |hi|) of the entry,
+// w_b = min(b + 1, L - 1), kappa = 2^-24 (1 + 2^-23).  A leaf pair on y = |x| in
+// [yl, yh] then bounds its distance to binary64 by e = Horner of B at xb = RU(yh (1 + 2^-23)),
+// each step RU(e xb + B_b), instead of carrying the bound step by step from the magnitudes of
+// its own partial values.  Why this bounds D = |lo32 - lo*| + |lo64 - lo*| (lo* exact): one
+// step of a chain (value s, coefficient c, T = |s_prev| yh + |c|) gives
+//   D <= (1 + 2^-50)(D_prev yh + E) + (2^-24 + 2^-50) T + 2^-149
+// (binary32 rounds once to nearest, < 2^-24 T; binary64 rounds product and sum downward,
+// < 2^-52 each of magnitudes <= T + D_prev yh + E), and |s| <= (1 + 2^-24) T + 2^-150, so
+// T_a <= sum_{b >= a} M_b ((1 + 2^-24) yh)^(b - a); summing the recursion over the steps
+// counts M_b once for each of the w_b steps a <= b, and every factor (1 + 2^-50)(1 + 2^-24)
+// per power of yh is inside xb.  B_b >= E_b, so a per-step consumer of the block (A32C::step)
+// stays sound on the rewritten entries.
+__device__ __forceinline__ float4 bform_entry(const float4 v, int r, int L) {
+  constexpr float kKappaB = 0x1.000002p-24f;  // >= 2^-24 + 2^-50
+  const int w = r + 1 < L - 1 ? r + 1 : (L > 1 ? L - 1 : 0);
+  const float M = fmaxf(fabsf(v.x), fabsf(v.y));
+  float B = __fmaf_ru(__fmul_ru(kKappaB, (float)w), M, v.z);
+  B = __fmaf_ru(v.z, 0x1p-50f, B);
+  B = __fadd_ru(B, kEta148);
+  return make_float4(v.x, v.y, B, B);
+}
+
+// A stage's output entry as stored: bfL > 0 (certified binary32, the last inner stage, whose
+// blocks only the leaves read) rewrites it for the leaves' summed bound, row = its row in the
+// leaf block (one fibre of bfL entries): the leaves then need no rewriting pass of their own.
+template <class AR>
+__device__ __forceinline__ typename AR::V out_entry(const typename AR::V &J, int bfL, int row) {
+  if constexpr (std::is_same<AR, A32C>::value) {
+    const float4 v = A32C::store(J);
+    return bfL ? bform_entry(v, row, bfL) : v;
+  } else {
+    return AR::store(J);
+  }
+}
+
 // Stage d < k-1 on every depth-d node.  Warp w takes node chunk w % nchunk (32 nodes, one per
 // lane) and fibres g, g+G, ... with g = w / nchunk.  in: entry e of parent p's block at
 // in[e * in_estride + p * in_nstride] (the coefficient tensor: in_estride 1, in_nstride 0).
@@ -426,7 +464,7 @@ __device__ __forceinline__ void stage_chunk(const StageDev &st, const int32_t *o
                                             int64_t in_estride, int64_t in_nstride,
                                             typename AR::V *__restrict__ out, int64_t out_estride,
                                             int64_t out_nstride, int64_t nnodes, int64_t chunk,
-                                            int grp, int G, const AxisGrid &g) {
+                                            int grp, int G, const AxisGrid &g, int bfL = 0) {
   using V = typename AR::V;
   const int lane = threadIdx.x & 31;
   const int64_t node = chunk * 32 + lane;
@@ -439,7 +477,8 @@ __device__ __forceinline__ void stage_chunk(const StageDev &st, const int32_t *o
     const int L = __ldg(st.fiblen + f);
     const V J = FM ? horner1_any<AR>(base + __ldg(st.fiboff + f), 1, L, x)
                    : horner_any<AR>(base, in_estride, rowoff, f, L, x);
-    if (live) dst[(int64_t)__ldg(outpos + f) * out_estride] = AR::store(J);
+    const int o = __ldg(outpos + f);
+    if (live) dst[(int64_t)o * out_estride] = out_entry<AR>(J, bfL, o);
   }
 }
 
@@ -455,7 +494,7 @@ __global__ void __launch_bounds__(kThreads)
     k_stage(const StageDev st, const int32_t *__restrict__ lab, const int32_t *__restrict__ par,
             const typename AR::V *__restrict__ in, int64_t in_estride, int64_t in_nstride,
             typename AR::V *__restrict__ out, int64_t out_estride, int64_t out_nstride,
-            int64_t nnodes, int64_t nchunk, int G, AxisGrid g) {
+            int64_t nnodes, int64_t nchunk, int G, AxisGrid g, int bfL) {
   extern __shared__ int32_t s_rowoff[];
   for (int i = threadIdx.x; i <= st.maxlen; i += blockDim.x) s_rowoff[i] = st.rowoff[i];
   __syncthreads();
@@ -463,7 +502,8 @@ __global__ void __launch_bounds__(kThreads)
   for (int64_t w = (int64_t)blockIdx.x * kWarpsPerBlock + (threadIdx.x >> 5); w < nwarps;
        w += (int64_t)gridDim.x * kWarpsPerBlock)
     stage_chunk<AR, FM>(st, st.outpos, s_rowoff, lab, par, 0, in, in_estride, in_nstride, out,
-                        out_estride, out_nstride, nnodes, w % nchunk, (int)(w / nchunk), G, g);
+                        out_estride, out_nstride, nnodes, w % nchunk, (int)(w / nchunk), G, g,
+                        bfL);
 }
 
 // Stage d (1 <= d < k-1) with the parent's block in shared memory.  The block is fibre-major
@@ -525,7 +565,7 @@ __global__ void __launch_bounds__(512)
     k_stage_tma(const StageDev st, const int32_t *__restrict__ lab,
                 const int32_t *__restrict__ pptr, const typename AR::V *__restrict__ in,
                 typename AR::V *__restrict__ out, int64_t out_estride, int64_t out_nstride,
-                int G, AxisGrid g) {
+                int G, AxisGrid g, int bfL) {
   using V = typename AR::V;
   extern __shared__ __align__(128) unsigned char smem[];
   uint64_t *bar = reinterpret_cast<uint64_t *>(smem);
@@ -546,7 +586,8 @@ __global__ void __launch_bounds__(512)
     for (int f = r.fb; f < r.fe; ++f) {
       const int L = __ldg(st.fiblen + f);
       const V J = horner1_any<AR>(s_blk + (__ldg(st.fiboff + f) - r.c_lo), 1, L, x);
-      if (live) dst[(int64_t)__ldg(st.outpos + f) * out_estride] = AR::store(J);
+      const int o = __ldg(st.outpos + f);
+      if (live) dst[(int64_t)o * out_estride] = out_entry<AR>(J, bfL, o);
     }
   }
 }
@@ -618,7 +659,7 @@ __global__ void __launch_bounds__(kThreads)
 // warp takes the per-leaf path of k_leaf.
 struct YLeaf {
   float yl, yh, xmaxp;
-  float xb;  // RU(yh (1 + 2^-23)): the multiplier of the summed bound (leaf_bform)
+  float xb;  // RU(yh (1 + 2^-23)): the multiplier of the summed bound (bform_entry)
   bool neg;
 };
 
@@ -666,7 +707,7 @@ __device__ __forceinline__ YPair ypair(const YLeaf &a, const YLeaf &b) {
 // roundings as SW = 1 on the odd entries, without moving the entry's pair).
 // Each end is the min of two paired FMAs rounded to nearest; the bounds follow A32C::step's
 // recursion, both leaves' in one paired FMA pair.
-// BF: the entry's .z/.w hold the summed bound B of leaf_bform, and one bound serves both
+// BF: the entry's .z/.w hold the summed bound B of bform_entry, and one bound serves both
 // leaves: e = RU(e xb + B) with xb the larger of their multipliers (every term of the
 // recursion is >= 0 and RU is monotone, so it bounds each leaf's own recursion), one FMA per
 // step and no magnitude of the step's result.  The bound lives in e.x (e.y is not used).
@@ -1078,7 +1119,7 @@ __device__ __forceinline__ void stage_chunk_c(const StageDev &st, const int32_t 
                                               int64_t in_nstride, float4 *__restrict__ out,
                                               int64_t out_estride, int64_t out_nstride,
                                               int64_t nnodes, int64_t chunk, int grp, int G,
-                                              const AxisGrid &g) {
+                                              const AxisGrid &g, int bfL = 0) {
   const int lane = threadIdx.x & 31;
   const int64_t npairs = (nnodes + 1) >> 1;
   const int64_t q = chunk * 32 + lane;
@@ -1115,9 +1156,10 @@ __device__ __forceinline__ void stage_chunk_c(const StageDev &st, const int32_t 
       } else {
         horner_y2_fibre<0>(base, in_estride, rowoff, f, L, yp, K0, K1);
       }
-      const int64_t o = (int64_t)__ldg(outpos + f) * out_estride;
-      if (live) out[i0 * out_nstride + o] = A32C::store(K0);
-      if (two) out[i1 * out_nstride + o] = A32C::store(K1);
+      const int ro = __ldg(outpos + f);
+      const int64_t o = (int64_t)ro * out_estride;
+      if (live) out[i0 * out_nstride + o] = out_entry<A32C>(K0, bfL, ro);
+      if (two) out[i1 * out_nstride + o] = out_entry<A32C>(K1, bfL, ro);
     }
   } else {
 #pragma unroll 1
@@ -1130,7 +1172,8 @@ __device__ __forceinline__ void stage_chunk_c(const StageDev &st, const int32_t 
         const int L = __ldg(st.fiblen + f);
         const float4 J = FM ? horner1_any<A32C>(base + __ldg(st.fiboff + f), 1, L, x)
                             : horner_any<A32C>(base, in_estride, rowoff, f, L, x);
-        if (wr) out[node * out_nstride + (int64_t)__ldg(outpos + f) * out_estride] = A32C::store(J);
+        const int ro = __ldg(outpos + f);
+        if (wr) out[node * out_nstride + (int64_t)ro * out_estride] = out_entry<A32C>(J, bfL, ro);
       }
     }
   }
@@ -1144,7 +1187,7 @@ __global__ void __launch_bounds__(kThreads, 6)
     k_stage_c(const StageDev st, const int32_t *__restrict__ lab, const int32_t *__restrict__ par,
               const float4 *__restrict__ in, int64_t in_estride, int64_t in_nstride,
               float4 *__restrict__ out, int64_t out_estride, int64_t out_nstride, int64_t nnodes,
-              int64_t nchunk, int G, AxisGrid g) {
+              int64_t nchunk, int G, AxisGrid g, int bfL) {
   extern __shared__ int32_t s_rowoff[];
   for (int i = threadIdx.x; i <= st.maxlen; i += blockDim.x) s_rowoff[i] = st.rowoff[i];
   __syncthreads();
@@ -1153,24 +1196,13 @@ __global__ void __launch_bounds__(kThreads, 6)
   for (int64_t w = (int64_t)blockIdx.x * kWarpsPerBlock + (threadIdx.x >> 5); w < nwarps;
        w += (int64_t)gridDim.x * kWarpsPerBlock)
     stage_chunk_c<FM>(st, st.outpos, s_rowoff, lab, par, 0, in, in_estride, in_nstride, out, out_estride,
-                  out_nstride, nnodes, w % nchunk, (int)(w / nchunk), G, g);
-}
-
-// Entry r of a fibre of length L rewritten for the summed bound (leaf_bform states it).
-__device__ __forceinline__ float4 bform_entry(const float4 v, int r, int L) {
-  constexpr float kKappaB = 0x1.000002p-24f;  // >= 2^-24 + 2^-50
-  const int w = r + 1 < L - 1 ? r + 1 : (L > 1 ? L - 1 : 0);
-  const float M = fmaxf(fabsf(v.x), fabsf(v.y));
-  float B = __fmaf_ru(__fmul_ru(kKappaB, (float)w), M, v.z);
-  B = __fmaf_ru(v.z, 0x1p-50f, B);
-  B = __fadd_ru(B, kEta148);
-  return make_float4(v.x, v.y, B, B);
+                  out_nstride, nnodes, w % nchunk, (int)(w / nchunk), G, g, bfL);
 }
 
 // k_stage_tma in the certified binary32 arithmetic, two children per thread: the children of
 // one parent always share it, so every warp whose boxes do not straddle 0 runs sign-free.  The
 // error bound advances step by step from the magnitudes of the partial values (A32C::step's
-// recursion).  The summed bound of the leaves (leaf_bform), applied to the stages' much longer
+// recursion).  The summed bound of the leaves (bform_entry), applied to the stages' much longer
 // chains, widens the curve's last-level band by 44-48% and does not pay: measured with the
 // band going to the float-pair tier, the depth-1 stage took 4.77 instead of 4.59 ms per step
 // (each staged group rewritten first) and the tier 1.86 instead of 1.55 ms.
@@ -1178,7 +1210,7 @@ __global__ void __launch_bounds__(512)
     k_stage_tma_c(const StageDev st, const int32_t *__restrict__ lab,
                   const int32_t *__restrict__ pptr, const float4 *__restrict__ in,
                   float4 *__restrict__ out, int64_t out_estride, int64_t out_nstride, int G,
-                  AxisGrid g) {
+                  AxisGrid g, int bfL) {
   extern __shared__ __align__(128) unsigned char smem[];
   uint64_t *bar = reinterpret_cast<uint64_t *>(smem);
   float4 *s_blk = reinterpret_cast<float4 *>(smem + 128);
@@ -1208,9 +1240,10 @@ __global__ void __launch_bounds__(512)
           horner_y2<1, -1>(b, L, yp, K0, K1);
         else
           horner_y2<1, 0>(b, L, yp, K0, K1);
-        const int64_t o = (int64_t)__ldg(st.outpos + f) * out_estride;
-        if (live) out[i0 * out_nstride + o] = A32C::store(K0[0]);
-        if (two) out[i1 * out_nstride + o] = A32C::store(K1[0]);
+        const int ro = __ldg(st.outpos + f);
+        const int64_t o = (int64_t)ro * out_estride;
+        if (live) out[i0 * out_nstride + o] = out_entry<A32C>(K0[0], bfL, ro);
+        if (two) out[i1 * out_nstride + o] = out_entry<A32C>(K1[0], bfL, ro);
       }
     } else {
 #pragma unroll 1
@@ -1221,7 +1254,8 @@ __global__ void __launch_bounds__(512)
         for (int f = r.fb; f < r.fe; ++f) {
           const int L = __ldg(st.fiblen + f);
           const float4 J = horner1_any<A32C>(s_blk + (__ldg(st.fiboff + f) - r.c_lo), 1, L, x);
-          if (wr) out[node * out_nstride + (int64_t)__ldg(st.outpos + f) * out_estride] = A32C::store(J);
+          const int ro = __ldg(st.outpos + f);
+          if (wr) out[node * out_nstride + (int64_t)ro * out_estride] = out_entry<A32C>(J, bfL, ro);
         }
       }
     }
@@ -1229,7 +1263,8 @@ __global__ void __launch_bounds__(512)
 }
 
 // Where the leaf stage reads polynomial f's block for parent p: the parent blocks in global
-// memory (node-major), or (ChunkBlocks) consecutive parents' blocks staged in shared memory.
+// memory (node-major), or (StagedBlocks) consecutive parents' blocks staged in shared memory
+// (separate types, so that each call site's loads are shared-memory or global ones).
 struct GlobalBlocks {
   const LeafArgs &A;
   __device__ const float4 *operator()(int f, int64_t p) const {
@@ -1356,9 +1391,17 @@ __device__ __forceinline__ void leaf_pair_c(const LeafArgs &A, int npoly, const 
                                             const A32C::X &x0, const A32C::X &x1, int64_t p0,
                                             int64_t p1, int64_t nleaves,
                                             uint8_t *__restrict__ keep, double *__restrict__ lo,
-                                            double *__restrict__ hi, uint8_t *__restrict__ flag) {
+                                            double *__restrict__ hi, uint8_t *__restrict__ flag,
+                                            bool bf) {
   bool ex[2] = {false, false}, am[2] = {false, false};
-  leaf_pair_eval<2>(A, 0, npoly, src, i0, i1, live, two, x0, x1, p0, p1, nleaves, lo, hi, ex, am);
+  // bf: the parents' blocks carry the summed bound (a stage wrote them); the coefficient
+  // block of a one-variable system does not
+  if (bf)
+    leaf_pair_eval<2, Src, true>(A, 0, npoly, src, i0, i1, live, two, x0, x1, p0, p1, nleaves,
+                                 lo, hi, ex, am);
+  else
+    leaf_pair_eval<2, Src, false>(A, 0, npoly, src, i0, i1, live, two, x0, x1, p0, p1, nleaves,
+                                  lo, hi, ex, am);
   leaf_pair_store(i0, i1, live, two, ex, am, keep, flag);
 }
 
@@ -1381,7 +1424,7 @@ __device__ __forceinline__ void leaf_tile_c(const LeafArgs &A, int npoly,
   const int64_t p0 = par ? (int64_t)__ldg(par + i0) - poff : 0;
   const int64_t p1 = par ? (int64_t)__ldg(par + i1) - poff : 0;
   leaf_pair_c(A, npoly, GlobalBlocks{A}, i0, i1, live, two, x0, x1, p0, p1, nleaves, keep, lo,
-              hi, flag);
+              hi, flag, par != nullptr);
 }
 
 __global__ void __launch_bounds__(kThreads, 6)
@@ -1400,42 +1443,15 @@ __global__ void __launch_bounds__(kThreads, 6)
 constexpr int kLeafIter = 2;
 constexpr int kLeafParents = 8;
 
-struct ChunkBlocks {  // the staged blocks of parents p0 .. p0 + n - 1, else global memory
+struct StagedBlocks {  // the staged blocks of parents p0 .. p0 + n - 1 (shared memory)
   const LeafArgs &A;
   const float4 *s_blk;
   const int32_t *s_off;
   int64_t p0;
-  bool staged;
   __device__ const float4 *operator()(int f, int64_t p) const {
-    return staged ? s_blk + s_off[f] + (p - p0) * A.blk[f] : (const float4 *)A.in[f] + p * A.blk[f];
+    return s_blk + s_off[f] + (p - p0) * A.blk[f];
   }
 };
-
-// The staged blocks of the leaf stage rewritten for the summed bound: entry b (row b of the
-// polynomial's single fibre, length L) keeps its binary32 ends and gets, in place of its bound
-// E, B_b = RU((1 + 2^-50) E + kappa w_b M_b) + 2^-148, M_b = max(|lo|, |hi|) of the entry,
-// w_b = min(b + 1, L - 1), kappa = 2^-24 (1 + 2^-23).  A leaf pair on y = |x| in
-// [yl, yh] then bounds its distance to binary64 by e = Horner of B at xb = RU(yh (1 + 2^-23)),
-// each step RU(e xb + B_b), instead of carrying the bound step by step from the magnitudes of
-// its own partial values.  Why this bounds D = |lo32 - lo*| + |lo64 - lo*| (lo* exact): one
-// step of a chain (value s, coefficient c, T = |s_prev| yh + |c|) gives
-//   D <= (1 + 2^-50)(D_prev yh + E) + (2^-24 + 2^-50) T + 2^-149
-// (binary32 rounds once to nearest, < 2^-24 T; binary64 rounds product and sum downward,
-// < 2^-52 each of magnitudes <= T + D_prev yh + E), and |s| <= (1 + 2^-24) T + 2^-150, so
-// T_a <= sum_{b >= a} M_b ((1 + 2^-24) yh)^(b - a); summing the recursion over the steps
-// counts M_b once for each of the w_b steps a <= b, and every factor (1 + 2^-50)(1 + 2^-24)
-// per power of yh is inside xb.  B_b >= E_b, so a per-step consumer of the block (A32C::step)
-// stays sound on the rewritten entries.
-__device__ __forceinline__ void leaf_bform(float4 *s_blk, const int32_t *s_off, const LeafArgs &A,
-                                           int npoly, int64_t np) {
-  for (int f = 0; f < npoly; ++f) {
-    const int L = A.len[f];
-    const int64_t blk = A.blk[f];
-    const int64_t n = np * blk;
-    float4 *b = s_blk + s_off[f];
-    for (int64_t i = threadIdx.x; i < n; i += blockDim.x) b[i] = bform_entry(b[i], (int)(i % blk), L);
-  }
-}
 
 // One thread: the bulk copies of parents pf .. pl's blocks, every polynomial's at s_off[f]
 // (kLeafParents blocks apart), completing on bar.
@@ -1485,11 +1501,11 @@ __device__ __forceinline__ void leaf_tma_c_chunk(const LeafArgs &A, int npoly,
     __syncthreads();
     const bool ok = mbar_wait_bounded(bar, 0);
     if (!__syncthreads_and(ok)) return;
-    leaf_bform(s_blk, s_off, A, npoly, pl - pf + 1);
-    __syncthreads();
   }
-  const ChunkBlocks src{A, s_blk, s_off, pf, staged};
-  // every warp runs the same trip count (the vote inside sees all 32 lanes)
+  const StagedBlocks sb{A, s_blk, s_off, pf};
+  const GlobalBlocks gb{A};
+  // every warp runs the same trip count (the vote inside sees all 32 lanes); the blocks were
+  // written for the summed bound (out_entry), staged or not
   for (int it = 0; it < kLeafIter; ++it) {
     const int64_t na = first + (int64_t)it * 2 * blockDim.x + 2 * threadIdx.x;
     const bool live = na <= last, two = na + 1 <= last;
@@ -1498,10 +1514,10 @@ __device__ __forceinline__ void leaf_tma_c_chunk(const LeafArgs &A, int npoly,
     const int64_t p0 = __ldg(par + i0) - poff, p1 = __ldg(par + i1) - poff;
     bool ex[2] = {false, false}, am[2] = {false, false};
     if (staged)
-      leaf_pair_eval<2, ChunkBlocks, true>(A, 0, npoly, src, i0, i1, live, two, x0, x1, p0, p1,
-                                           nleaves, lo, hi, ex, am);
+      leaf_pair_eval<2, StagedBlocks, true>(A, 0, npoly, sb, i0, i1, live, two, x0, x1, p0, p1,
+                                            nleaves, lo, hi, ex, am);
     else
-      leaf_pair_eval<2, ChunkBlocks, false>(A, 0, npoly, src, i0, i1, live, two, x0, x1, p0, p1,
+      leaf_pair_eval<2, GlobalBlocks, true>(A, 0, npoly, gb, i0, i1, live, two, x0, x1, p0, p1,
                                             nleaves, lo, hi, ex, am);
     leaf_pair_store(i0, i1, live, two, ex, am, keep, flag);
   }
@@ -1554,11 +1570,9 @@ __device__ __forceinline__ void leaf_q_chunk(const LeafArgs &A, int npoly,
   __syncthreads();
   const bool ok = !staged || mbar_wait_bounded(bar, 0);
   if (!__syncthreads_and(ok)) return;
-  if (staged) {
-    leaf_bform(s_blk, s_off, A, npoly, pl - pf + 1);
-    __syncthreads();
-  }
-  const ChunkBlocks src{A, s_blk, s_off, pf, staged};
+  // the blocks were written for the summed bound (out_entry), staged or not
+  const StagedBlocks sb{A, s_blk, s_off, pf};
+  const GlobalBlocks gb{A};
   const int lane = threadIdx.x & 31;
   for (int it = 0; it < ITER; ++it) {
     const int q = it * kThreads + (int)threadIdx.x;
@@ -1569,11 +1583,11 @@ __device__ __forceinline__ void leaf_q_chunk(const LeafArgs &A, int npoly,
     const int64_t p0 = __ldg(par + i0) - poff, p1 = __ldg(par + i1) - poff;
     bool ex[2] = {false, false}, am[2] = {false, false};
     if (staged)
-      leaf_pair_eval<1, ChunkBlocks, true>(A, 0, 1, src, i0, i1, live, two, x0, x1, p0, p1,
-                                           0, nullptr, nullptr, ex, am);
+      leaf_pair_eval<1, StagedBlocks, true>(A, 0, 1, sb, i0, i1, live, two, x0, x1, p0, p1, 0,
+                                            nullptr, nullptr, ex, am);
     else
-      leaf_pair_eval<1, ChunkBlocks, false>(A, 0, 1, src, i0, i1, live, two, x0, x1, p0, p1,
-                                            0, nullptr, nullptr, ex, am);
+      leaf_pair_eval<1, GlobalBlocks, true>(A, 0, 1, gb, i0, i1, live, two, x0, x1, p0, p1, 0,
+                                            nullptr, nullptr, ex, am);
     const bool more = live && !(ex[0] && (ex[1] || !two));
     if (live && !more) leaf_pair_store(i0, i1, live, two, ex, am, keep, flag);
     const unsigned m = __ballot_sync(0xffffffffu, more);
@@ -1601,11 +1615,11 @@ __device__ __forceinline__ void leaf_q_chunk(const LeafArgs &A, int npoly,
     const int64_t p0 = __ldg(par + i0) - poff, p1 = __ldg(par + i1) - poff;
     bool ex[2] = {(st & 1) != 0, (st & 4) != 0}, am[2] = {(st & 2) != 0, (st & 8) != 0};
     if (staged)
-      leaf_pair_eval<1, ChunkBlocks, true>(A, 1, npoly, src, i0, i1, in, two, x0, x1, p0, p1,
-                                           0, nullptr, nullptr, ex, am);
+      leaf_pair_eval<1, StagedBlocks, true>(A, 1, npoly, sb, i0, i1, in, two, x0, x1, p0, p1, 0,
+                                            nullptr, nullptr, ex, am);
     else
-      leaf_pair_eval<1, ChunkBlocks, false>(A, 1, npoly, src, i0, i1, in, two, x0, x1, p0, p1,
-                                            0, nullptr, nullptr, ex, am);
+      leaf_pair_eval<1, GlobalBlocks, true>(A, 1, npoly, gb, i0, i1, in, two, x0, x1, p0, p1, 0,
+                                            nullptr, nullptr, ex, am);
     leaf_pair_store(i0, i1, in, two, ex, am, keep, flag);
   }
 }
@@ -1829,6 +1843,9 @@ int eval_level_t(const SysDev &sys, const CsfView &c, const LevelGrid &grid, dou
       madds += w;
       // node-major output when the consumer is the leaf stage or a TMA-staged stage
       const bool node_major = d + 2 == k || tma[d + 1];
+      // certified binary32 leaves (not the Taylor form's) read their parents' blocks already
+      // rewritten for the summed bound
+      const int bfL = std::is_same<AR, A32C>::value && !tl && d + 2 == k ? (int)st.blk_out : 0;
       const int64_t oe = node_major ? 1 : c.N[d], on = node_major ? st.blk_out : 1;
       if (tm && tm->on) rc = tm->begin(d == 0 ? kind0 : kind0 + 1, w);
       if (rc != VX_OK) break;
@@ -1876,10 +1893,10 @@ int eval_level_t(const SysDev &sys, const CsfView &c, const LevelGrid &grid, dou
           if (two)
             k_stage_tma_c<<<(unsigned)(np * G), threads, sm, s>>>(
                 st, c.lab[d], c.ptr[d - 1], (const float4 *)in, (float4 *)buf[f][d], oe, on,
-                (int)G, pg.ax[d]);
+                (int)G, pg.ax[d], bfL);
           else
             k_stage_tma<AR><<<(unsigned)(np * G), threads, sm, s>>>(
-                st, c.lab[d], c.ptr[d - 1], in, buf[f][d], oe, on, (int)G, pg.ax[d]);
+                st, c.lab[d], c.ptr[d - 1], in, buf[f][d], oe, on, (int)G, pg.ax[d], bfL);
           note_launch();
           VX_LAUNCH_CHECK();
           return VX_OK;
@@ -1914,19 +1931,19 @@ int eval_level_t(const SysDev &sys, const CsfView &c, const LevelGrid &grid, dou
           if (pairs && fm0)
             k_stage_c<true><<<(unsigned)blocks, kThreads, (st.maxlen + 1) * sizeof(int32_t), s>>>(
                 st, c.lab[d], nullptr, (const float4 *)fm0, 1, 0, (float4 *)buf[f][d], oe, on,
-                c.N[d], nchunk, (int)G, pg.ax[d]);
+                c.N[d], nchunk, (int)G, pg.ax[d], bfL);
           else if (fm0)
             k_stage<AR, true><<<(unsigned)blocks, kThreads, (st.maxlen + 1) * sizeof(int32_t), s>>>(
                 st, c.lab[d], nullptr, fm0, 1, 0, buf[f][d], oe, on, c.N[d], nchunk, (int)G,
-                pg.ax[d]);
+                pg.ax[d], bfL);
           else if (pairs)
             k_stage_c<false><<<(unsigned)blocks, kThreads, (st.maxlen + 1) * sizeof(int32_t), s>>>(
                 st, c.lab[d], d == 0 ? nullptr : c.par[d], (const float4 *)in, in_estride,
-                in_nstride, (float4 *)buf[f][d], oe, on, c.N[d], nchunk, (int)G, pg.ax[d]);
+                in_nstride, (float4 *)buf[f][d], oe, on, c.N[d], nchunk, (int)G, pg.ax[d], bfL);
           else
             k_stage<AR><<<(unsigned)blocks, kThreads, (st.maxlen + 1) * sizeof(int32_t), s>>>(
                 st, c.lab[d], d == 0 ? nullptr : c.par[d], in, in_estride, in_nstride,
-                buf[f][d], oe, on, c.N[d], nchunk, (int)G, pg.ax[d]);
+                buf[f][d], oe, on, c.N[d], nchunk, (int)G, pg.ax[d], bfL);
           note_launch();
           VX_LAUNCH_CHECK();
           return VX_OK;
@@ -2093,6 +2110,7 @@ __global__ void __launch_bounds__(kThreads, 6)
       // writes and reads the inner stages' blocks fibre-major
       const int32_t *outpos = FMF && d + 2 < k ? st.outpos_fm : st.outpos;
       const bool fmr = d == 0 || FMF;
+      const int bfL = FMF && d + 2 == k ? (int)st.blk_out : 0;  // the leaves' summed bound
       const V *in = d == 0 ? AR::coef_fm(T.dev.p[f])
                            : (const V *)blk[((int64_t)t * VX_MAXPOLY + f) * VX_KMAX + d - 1];
       V *out = (V *)blk[((int64_t)t * VX_MAXPOLY + f) * VX_KMAX + d];
@@ -2100,17 +2118,17 @@ __global__ void __launch_bounds__(kThreads, 6)
       if constexpr (PAIRS) {
         if (fmr)
           stage_chunk_c<true>(st, outpos, st.rowoff, lab, par, poff, (const float4 *)in, 1, in_nstride,
-                              (float4 *)out, 1, st.blk_out, n, chunk, grp, G, T.ax[d]);
+                              (float4 *)out, 1, st.blk_out, n, chunk, grp, G, T.ax[d], bfL);
         else
           stage_chunk_c<false>(st, outpos, st.rowoff, lab, par, poff, (const float4 *)in, 1, in_nstride,
-                               (float4 *)out, 1, st.blk_out, n, chunk, grp, G, T.ax[d]);
+                               (float4 *)out, 1, st.blk_out, n, chunk, grp, G, T.ax[d], bfL);
       } else {
         if (fmr)
           stage_chunk<AR, true>(st, outpos, st.rowoff, lab, par, poff, in, 1, in_nstride, out, 1,
-                                st.blk_out, n, chunk, grp, G, T.ax[d]);
+                                st.blk_out, n, chunk, grp, G, T.ax[d], bfL);
         else
           stage_chunk<AR, false>(st, outpos, st.rowoff, lab, par, poff, in, 1, in_nstride, out, 1,
-                                 st.blk_out, n, chunk, grp, G, T.ax[d]);
+                                 st.blk_out, n, chunk, grp, G, T.ax[d], bfL);
       }
     }
   }

@@ -792,21 +792,31 @@ __device__ __forceinline__ void horner_y2(const float4 *const (&b)[2], int L, co
       step_y2<0, BF, OSW>(j0[f], j1[f], e[f], y, b[f][a], false, false);
     --a;
   }
-  // two (odd, even) pairs per trip: half the loop and address overhead per step
-  for (; a >= 3; a -= 4) {
+  // two (odd, even) pairs per trip: half the loop and address overhead per step; the entries
+  // are walked by pointer (immediate offsets) with a trip counter
+  if (a >= 3) {
+    const float4 *pa[NP];
 #pragma unroll
-    for (int h = 0; h < 2; ++h) {
-      float4 A[NP], B[NP];
+    for (int f = 0; f < NP; ++f) pa[f] = b[f] + a;
+    int trips = (a + 1) >> 2;
+    a -= 4 * trips;
+    for (; trips > 0; --trips) {
 #pragma unroll
-      for (int f = 0; f < NP; ++f) {
-        A[f] = b[f][a - 2 * h];
-        B[f] = b[f][a - 2 * h - 1];
+      for (int h = 0; h < 2; ++h) {
+        float4 A[NP], B[NP];
+#pragma unroll
+        for (int f = 0; f < NP; ++f) {
+          A[f] = pa[f][-2 * h];
+          B[f] = pa[f][-2 * h - 1];
+        }
+#pragma unroll
+        for (int f = 0; f < NP; ++f) {
+          step_y2<SWO, BF, OSW>(j0[f], j1[f], e[f], y, A[f], y.neg0, y.neg1);
+          step_y2<0, BF, OSW>(j0[f], j1[f], e[f], y, B[f], false, false);
+        }
       }
 #pragma unroll
-      for (int f = 0; f < NP; ++f) {
-        step_y2<SWO, BF, OSW>(j0[f], j1[f], e[f], y, A[f], y.neg0, y.neg1);
-        step_y2<0, BF, OSW>(j0[f], j1[f], e[f], y, B[f], false, false);
-      }
+      for (int f = 0; f < NP; ++f) pa[f] -= 4;
     }
   }
   if (a >= 1) {

@@ -1240,9 +1240,16 @@ __global__ void __launch_bounds__(512)
     if (__all_sync(0xffffffffu, fast)) {
       const YPair yp = ypair(yleaf(x0), yleaf(x1));
       const int ws = warp_sign(yp);
+      // each fibre's length, offset and output position loaded one fibre ahead
+      int Ln = __ldg(st.fiblen + r.fb), fon = __ldg(st.fiboff + r.fb), ron = __ldg(st.outpos + r.fb);
       for (int f = r.fb; f < r.fe; ++f) {
-        const int L = __ldg(st.fiblen + f);
-        const float4 *const b[2] = {s_blk + (__ldg(st.fiboff + f) - r.c_lo), nullptr};
+        const int L = Ln, fo = fon, ro = ron;
+        if (f + 1 < r.fe) {
+          Ln = __ldg(st.fiblen + f + 1);
+          fon = __ldg(st.fiboff + f + 1);
+          ron = __ldg(st.outpos + f + 1);
+        }
+        const float4 *const b[2] = {s_blk + (fo - r.c_lo), nullptr};
         float4 K0[2], K1[2];
         if (ws > 0)
           horner_y2<1, 1>(b, L, yp, K0, K1);
@@ -1250,7 +1257,6 @@ __global__ void __launch_bounds__(512)
           horner_y2<1, -1>(b, L, yp, K0, K1);
         else
           horner_y2<1, 0>(b, L, yp, K0, K1);
-        const int ro = __ldg(st.outpos + f);
         const int64_t o = (int64_t)ro * out_estride;
         if (live) out[i0 * out_nstride + o] = out_entry<A32C>(K0[0], bfL, ro);
         if (two) out[i1 * out_nstride + o] = out_entry<A32C>(K1[0], bfL, ro);

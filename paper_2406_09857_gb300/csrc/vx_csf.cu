@@ -463,19 +463,64 @@ __device__ __forceinline__ void load_items(const FlagSrc &src, int64_t i0, int64
   }
 }
 
-struct RankEmit {
-  int32_t *rank;
-  FlagSrc src;
-  __device__ void operator()(int64_t i, unsigned m, const int32_t *excl) const {
-    rank[i] = excl[src.depth_of(i)];
+// The ranks of a pruned tree: rank[i] (the kept nodes of its depth before node i) for the inner
+// depths (i < loff, the leaf segment's start), and for the leaf depth one count per aligned
+// 8-entry word of the flag array, rank8[w - w0] = the kept leaves before word w; a leaf's rank
+// is its word's count plus the kept leaves before it in the word (a popcount of the word's flag
+// bytes, 0 or 1 each).  Half a byte per leaf is written and read instead of four.
+struct RankView {
+  const int32_t *rank;
+  const int32_t *rank8;
+  const uint8_t *flags;
+  int64_t loff, w0;
+  __device__ __forceinline__ int32_t at(int64_t i) const {
+    if (i < loff) return __ldg(rank + i);
+    const int64_t b = i & ~(int64_t)7;
+    const uint64_t v = __ldg(reinterpret_cast<const unsigned long long *>(flags + b));
+    const int hi = (int)(i - b), lo = loff > b ? (int)(loff - b) : 0;  // lo <= hi < 8
+    uint64_t m = hi == 0 ? 0ull : (~0ull >> (64 - 8 * hi));            // bytes [0, hi)
+    m &= ~0ull << (8 * lo);                                            // and >= loff
+    return __ldg(rank8 + ((b >> 3) - w0)) + __popcll(v & m);
+  }
+  // The kept nodes of one depth (its segment starting at lo) before the absolute index a, a
+  // multiple of 32 with a > lo - 32: zero before the segment, else an inner rank or, in the
+  // leaf segment, the count of a's word (a is 8-aligned).  The lanes of a warp that read it
+  // for one window read the same entry.
+  __device__ __forceinline__ int32_t base32(int64_t a, int64_t lo) const {
+    if (a < lo) return 0;
+    return a < loff ? __ldg(rank + a) : __ldg(rank8 + ((a >> 3) - w0));
   }
 };
 
-// the eight ranks of a thread in two 16-byte stores (rank is 256-byte aligned)
+// A warp's window of 32 consecutive absolute indices a .. a+31 (a a multiple of 32) over one
+// depth's segment [lo, hi): the lane's node is a + lane; each kept node's rank is the window's
+// base (RankView::base32) plus the kept lanes below it in the warp's ballot.
+__device__ __forceinline__ int32_t window_rank(int32_t base, unsigned bal) {
+  return base + __popc(bal & ((1u << (threadIdx.x & 31)) - 1u));
+}
+
+struct RankEmit {
+  int32_t *rank, *rank8;
+  int64_t loff, w0;
+  FlagSrc src;
+  __device__ void operator()(int64_t i, unsigned m, const int32_t *excl) const {
+    if (i < loff) rank[i] = excl[src.depth_of(i)];
+  }
+  // a word holding leaves gets the leaf channel's count at its start (for the word where the
+  // leaf segment begins, no leaf lies before it, so the count is the leaves' first rank)
+  template <int C>
+  __device__ __forceinline__ void word(int64_t i0, const int32_t (&run)[C]) const {
+    if (i0 + SI > loff) rank8[(i0 >> 3) - w0] = run[C - 1];
+  }
+};
+
+// the eight ranks of a thread: two 16-byte stores for inner nodes (rank is 256-byte aligned),
+// the word's count where it holds leaves
 template <int C>
 __device__ __forceinline__ void emit_items(const RankEmit &em, int64_t i0, int64_t n,
                                            const unsigned (&m)[SI], int32_t (&run)[C]) {
-  if (i0 + SI <= n) {
+  if (i0 < n) em.word<C>(i0, run);
+  if (i0 + SI <= n && i0 + SI <= em.loff) {
     int32_t r[SI];
     const int d0 = em.src.depth_of(i0), d1 = em.src.depth_of(i0 + SI - 1);
 #pragma unroll
@@ -546,6 +591,11 @@ struct ItemOps<C, FlagSrc> {
     int32_t base = 0;
 #pragma unroll
     for (int c = 0; c < C; ++c) base = c == d ? run[c] : base;
+    if (d == C - 1) {  // eight leaves: their word's count only
+      em.word<C>(i0, run);
+      run[C - 1] += __popc(v.x) + __popc(v.y);
+      return;
+    }
     const uint32_t px = v.x * 0x01010101u, py = v.y * 0x01010101u;
     const uint32_t ex = px - v.x, ey = py - v.y;
     const int32_t tx = (int32_t)(px >> 24), ty = (int32_t)(py >> 24);
@@ -650,14 +700,19 @@ __global__ void k_mark_parents_s(const int32_t *__restrict__ cpar, int64_t cs, i
 
 // kptr[d][g_d(p)] = rank of the first kept child of kept node p (depth d < k-1)
 template <int D>
-__global__ void k_kptr(CsfView c, const uint8_t *__restrict__ flags, const int32_t *__restrict__ rank,
+__global__ void k_kptr(CsfView c, const uint8_t *__restrict__ flags, const RankView rank,
                        Segs sg, int32_t *kptr) {
   constexpr int d = D;
-  const int64_t n = c.N[d];
+  const int64_t lo = sg.off[d], hi = lo + c.N[d];
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-  for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < n; p += stride) {
-    if (!flags[sg.off[d] + p]) continue;
-    kptr[rank[sg.off[d] + p]] = rank[sg.off[d + 1] + c.ptr[d][p]];
+  // a warp takes a 32-aligned window of the flag array (blockDim and stride multiples of 32)
+  for (int64_t a = (lo & ~(int64_t)31) + (int64_t)blockIdx.x * blockDim.x + (threadIdx.x & ~31);
+       a < hi; a += stride) {
+    const int64_t i = a + (threadIdx.x & 31);
+    const bool kept = i >= lo && i < hi && flags[i];
+    const int32_t base = rank.base32(a, lo);
+    const unsigned bal = __ballot_sync(0xffffffffu, kept);
+    if (kept) kptr[window_rank(base, bal)] = rank.at(sg.off[d + 1] + c.ptr[d][i - lo]);
   }
 }
 
@@ -675,20 +730,28 @@ __device__ __forceinline__ int32_t chain(const KptrSet &K, int a, int t, int32_t
 // Bisection of depth d: every kept depth-d node writes its 2^(d+1) copies.  k and d are
 // template arguments so that the path arrays stay in registers.
 template <int KK, int D>
-__global__ void k_split(CsfView in, const uint8_t *__restrict__ flags,
-                        const int32_t *__restrict__ rank, Segs sg, KptrSet K, CsfView out) {
+__global__ void k_split(CsfView in, const uint8_t *__restrict__ flags, const RankView rank,
+                        Segs sg, KptrSet K, CsfView out) {
   constexpr int k = KK, d = D;
-  const int64_t n = in.N[d];
+  const int64_t lo = sg.off[d], hi = lo + in.N[d];
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-  for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < n; p += stride) {
-    if (!flags[sg.off[d] + p]) continue;
+  // a warp takes a 32-aligned window of the flag array (blockDim and stride multiples of 32)
+  for (int64_t a = (lo & ~(int64_t)31) + (int64_t)blockIdx.x * blockDim.x + (threadIdx.x & ~31);
+       a < hi; a += stride) {
+    const int64_t i = a + (threadIdx.x & 31), p = i - lo;
+    const bool kept = i >= lo && i < hi && flags[i];
+    const int32_t base = rank.base32(a, lo);
+    const unsigned bal = __ballot_sync(0xffffffffu, kept);
+    if (!kept) continue;
+    const int32_t gd = window_rank(base, bal);
     int64_t path[VX_KMAX];
     int32_t g[VX_KMAX];
     path[d] = p;
 #pragma unroll
     for (int a = d; a > 0; --a) path[a - 1] = in.par[a][path[a]];
 #pragma unroll
-    for (int a = 0; a <= d; ++a) g[a] = rank[sg.off[a] + path[a]];
+    for (int a = 0; a < d; ++a) g[a] = rank.at(sg.off[a] + path[a]);
+    g[d] = gd;
     // F_t(p_a) and D_t(p_a) for t = d-1, d, d+1
     int64_t base_d = 0, base_m = 0, base_p = 0;
     int64_t Dd[VX_KMAX], Dm[VX_KMAX], Dp[VX_KMAX];
@@ -732,17 +795,24 @@ __global__ void k_split(CsfView in, const uint8_t *__restrict__ flags,
 
 // Compaction of depth d: kept node p goes to its rank.
 template <int D>
-__global__ void k_gather(CsfView in, const uint8_t *__restrict__ flags,
-                         const int32_t *__restrict__ rank, Segs sg, CsfView out,
-                         int32_t *index) {
+__global__ void k_gather(CsfView in, const uint8_t *__restrict__ flags, const RankView rank,
+                         Segs sg, CsfView out, int32_t *index) {
   constexpr int d = D;
-  const int64_t n = in.N[d];
+  const int64_t lo = sg.off[d], hi = lo + in.N[d];
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-  for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < n; p += stride) {
-    if (!flags[sg.off[d] + p]) continue;
-    const int32_t r = rank[sg.off[d] + p];
-    out.lab[d][r] = in.lab[d][p];
-    if (d > 0) out.par[d][r] = rank[sg.off[d - 1] + in.par[d][p]];
+  // a warp takes a 32-aligned window of the flag array (blockDim and stride multiples of 32)
+  for (int64_t a = (lo & ~(int64_t)31) + (int64_t)blockIdx.x * blockDim.x + (threadIdx.x & ~31);
+       a < hi; a += stride) {
+    const int64_t i = a + (threadIdx.x & 31), p = i - lo;
+    const bool kept = i >= lo && i < hi && flags[i];
+    const int32_t base = rank.base32(a, lo);
+    const unsigned bal = __ballot_sync(0xffffffffu, kept);
+    if (!kept) continue;
+    const int32_t r = window_rank(base, bal);
+    const int32_t lab = __ldg(in.lab[d] + p);
+    const int32_t prank = d > 0 ? __ldg(rank.rank + sg.off[d - 1] + __ldg(in.par[d] + p)) : 0;
+    out.lab[d][r] = lab;
+    if (d > 0) out.par[d][r] = prank;
     if (index && d == in.k - 1) index[r] = (int32_t)p;
   }
 }
@@ -757,20 +827,20 @@ int blocks_for(int64_t n) {
 // Forest segments: seg_off[d * (S+1) + s] is the first depth-d node of tree-set s (s = 0..S,
 // seg_off[.. + S] = N_d); kept[d * (S+1) + s] receives the kept depth-d nodes before it.
 __global__ void k_seg_kept(const int64_t *__restrict__ seg_off, int S, int k,
-                           const int32_t *__restrict__ rank, Segs sg, const int32_t *totals,
+                           const RankView rank, Segs sg, const int32_t *totals,
                            int64_t *__restrict__ kept) {
   const int64_t n = (int64_t)k * (S + 1);
   for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < n;
        j += (int64_t)gridDim.x * blockDim.x) {
     const int d = (int)(j / (S + 1));
     const int64_t i = seg_off[j];
-    kept[j] = i >= sg.off[d + 1] - sg.off[d] ? (int64_t)totals[d] : (int64_t)rank[sg.off[d] + i];
+    kept[j] = i >= sg.off[d + 1] - sg.off[d] ? (int64_t)totals[d] : (int64_t)rank.at(sg.off[d] + i);
   }
 }
 
 // run-time depth -> template argument
 void launch_kptr(int d, int blocks, cudaStream_t s, const CsfView &in, const uint8_t *flags,
-                 const int32_t *rank, const Segs &sg, int32_t *kptr) {
+                 const RankView &rank, const Segs &sg, int32_t *kptr) {
   switch (d) {
     case 0: k_kptr<0><<<blocks, 256, 0, s>>>(in, flags, rank, sg, kptr); break;
     case 1: k_kptr<1><<<blocks, 256, 0, s>>>(in, flags, rank, sg, kptr); break;
@@ -781,7 +851,7 @@ void launch_kptr(int d, int blocks, cudaStream_t s, const CsfView &in, const uin
 }
 
 void launch_gather(int d, int blocks, cudaStream_t s, const CsfView &in, const uint8_t *flags,
-                   const int32_t *rank, const Segs &sg, const CsfView &out, int32_t *index) {
+                   const RankView &rank, const Segs &sg, const CsfView &out, int32_t *index) {
   switch (d) {
     case 0: k_gather<0><<<blocks, 256, 0, s>>>(in, flags, rank, sg, out, index); break;
     case 1: k_gather<1><<<blocks, 256, 0, s>>>(in, flags, rank, sg, out, index); break;
@@ -794,7 +864,7 @@ void launch_gather(int d, int blocks, cudaStream_t s, const CsfView &in, const u
 
 template <int KK>
 void launch_split(int d, int blocks, cudaStream_t s, const CsfView &in, const uint8_t *flags,
-                  const int32_t *rank, const Segs &sg, const KptrSet &K, const CsfView &out) {
+                  const RankView &rank, const Segs &sg, const KptrSet &K, const CsfView &out) {
   switch (d) {
     case 0: k_split<KK, 0><<<blocks, 256, 0, s>>>(in, flags, rank, sg, K, out); break;
     case 1: if (KK > 1) k_split<KK, (KK > 1 ? 1 : 0)><<<blocks, 256, 0, s>>>(in, flags, rank, sg, K, out); break;
@@ -833,13 +903,17 @@ int prune_c(const CsfView &in, const uint8_t *d_keep, int split, int32_t *d_inde
   uint8_t *flags = nullptr;
   int32_t *rank = nullptr, *kptr = nullptr, *scratch = nullptr;
   int rc = VX_OK;
-  // algorithmic bytes: the leaves' keep flags and the inner ptr arrays read, one flag byte and
-  // one 4-byte rank per node written
-  int64_t prune_bytes = in.N[k - 1] + 5 * total;
+  // ranks: one per inner node, one per 8-entry word of the leaf segment (RankView)
+  const int64_t loff = sg.off[k - 1], w0 = loff >> 3, nw8 = ((total - 1) >> 3) - w0 + 1;
+  const int64_t rank_inner = (loff + 63) & ~(int64_t)63;  // rank8 256-byte aligned after it
+  // algorithmic bytes: the leaves' keep flags and the inner ptr arrays read, one flag byte per
+  // node and the ranks written
+  int64_t prune_bytes = in.N[k - 1] + total + 4 * (loff + nw8);
   for (int d = 0; d + 1 < k; ++d) prune_bytes += 4 * (in.N[d] + 1);
   if (tm && tm->on) VX_CHECK(tm->begin(KK_PRUNE, prune_bytes));
   rc = dmalloc((void **)&flags, (size_t)total + 16, s);  // 16 bytes for the 16-byte loads
-  if (rc == VX_OK) rc = dmalloc((void **)&rank, (size_t)total * sizeof(int32_t), s);
+  if (rc == VX_OK) rc = dmalloc((void **)&rank, (size_t)(rank_inner + nw8) * sizeof(int32_t), s);
+  const RankView rv{rank, rank + rank_inner, flags, loff, w0};
   if (rc == VX_OK) {
     cudaError_t e = cudaMemcpyAsync(flags + sg.off[k - 1], d_keep, (size_t)in.N[k - 1],
                                     cudaMemcpyDeviceToDevice, s);
@@ -881,11 +955,13 @@ int prune_c(const CsfView &in, const uint8_t *d_keep, int split, int32_t *d_inde
   // together after the ranks (one wait instead of two)
   const bool one_wait = d_seg_off && h_seg_kept;
   if (rc == VX_OK) rc = scan_prepare<C>(src, total, s, &scratch, &ntiles, one_wait ? nullptr : nk);
-  if (rc == VX_OK) rc = scan_emit<C>(src, RankEmit{rank, src}, total, scratch, ntiles, s);
+  if (rc == VX_OK)
+    rc = scan_emit<C>(src, RankEmit{rank, rank + rank_inner, loff, w0, src}, total, scratch,
+                      ntiles, s);
   if (rc == VX_OK && d_seg_off) {
     // the channel totals sit after the tile sums in the scan scratch
     k_seg_kept<<<blocks_for((int64_t)k * (nseg + 1)), 256, 0, s>>>(
-        d_seg_off, nseg, k, rank, sg, scratch + (int64_t)C * ntiles, d_seg_kept);
+        d_seg_off, nseg, k, rv, sg, scratch + (int64_t)C * ntiles, d_seg_kept);
     note_launch();
     if (cudaGetLastError() != cudaSuccess) {
       set_error("segment count kernel launch failed");
@@ -935,7 +1011,7 @@ int prune_c(const CsfView &in, const uint8_t *d_keep, int split, int32_t *d_inde
   // algorithmic bytes: flags and ranks of every node read; per kept node its label, parent
   // (depth > 0) and child pointer (depth < k-1) read; the same arrays written per new node (a
   // split) or per kept node (a compaction)
-  int64_t rebuild_bytes = 5 * total;
+  int64_t rebuild_bytes = total + 4 * (loff + nw8);
   for (int d = 0; d < k; ++d) {
     const int64_t w = 4 + (d > 0 ? 4 : 0) + (d + 1 < k ? 4 : 0);
     rebuild_bytes += ((int64_t)nk[d] + (split ? newN[d] : (int64_t)nk[d])) * w;
@@ -943,7 +1019,7 @@ int prune_c(const CsfView &in, const uint8_t *d_keep, int split, int32_t *d_inde
   if (!split && d_index) rebuild_bytes += 4 * (int64_t)nk[k - 1];
   if (rc == VX_OK && tm && tm->on) rc = tm->begin(split ? KK_SPLIT : KK_COMPACT, rebuild_bytes);
   for (int d = 0; d + 1 < k && rc == VX_OK; ++d) {
-    launch_kptr(d, blocks_for(in.N[d]), s, in, flags, rank, sg, (int32_t *)K.k[d]);
+    launch_kptr(d, blocks_for(in.N[d]), s, in, flags, rv, sg, (int32_t *)K.k[d]);
     note_launch();
     if (cudaGetLastError() != cudaSuccess) {
       set_error("kptr kernel launch failed");
@@ -961,9 +1037,9 @@ int prune_c(const CsfView &in, const uint8_t *d_keep, int split, int32_t *d_inde
   }
   for (int d = 0; d < k && rc == VX_OK; ++d) {
     if (split)
-      launch_split<C>(d, blocks_for(in.N[d]), s, in, flags, rank, sg, K, out->v);
+      launch_split<C>(d, blocks_for(in.N[d]), s, in, flags, rv, sg, K, out->v);
     else
-      launch_gather(d, blocks_for(in.N[d]), s, in, flags, rank, sg, out->v, d_index);
+      launch_gather(d, blocks_for(in.N[d]), s, in, flags, rv, sg, out->v, d_index);
     note_launch();
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) {

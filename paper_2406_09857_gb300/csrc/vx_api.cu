@@ -351,8 +351,7 @@ struct HostStage {
 };
 
 struct HostPoly {
-  HostStage st[VX_KMAX];
-  std::vector<double2> c64;
+  HostStage st[VX_KMAX];  // the coefficient block (st[0].blk_in entries) is packed by pack_coefs
 };
 
 // A monomial in up to k - 1 variables packed into 64 bits: 16 bits per exponent up to
@@ -431,14 +430,16 @@ struct Stage0BlocksFm {
   float4 *c32c, *cp;
   float *ep;
 };
+// A warp per fibre, its lanes over the fibre's entries (writes coalesced).
 __global__ void k_fibre_major(Stage0Blocks r, const int32_t *__restrict__ rowoff,
                               const int32_t *__restrict__ fiblen,
                               const int32_t *__restrict__ fiboff, int32_t nfib,
                               Stage0BlocksFm w) {
-  const int stride = (int)(gridDim.x * blockDim.x);
-  for (int f = (int)(blockIdx.x * blockDim.x + threadIdx.x); f < nfib; f += stride) {
+  const int wpb = (int)(blockDim.x >> 5), lane = (int)(threadIdx.x & 31);
+  const int stride = (int)gridDim.x * wpb;
+  for (int f = (int)blockIdx.x * wpb + (int)(threadIdx.x >> 5); f < nfib; f += stride) {
     const int L = fiblen[f], o = fiboff[f];
-    for (int a = 0; a < L; ++a) {
+    for (int a = lane; a < L; a += 32) {
       const int i = rowoff[a] + f;
       w.c64[o + a] = r.c64[i];
       w.c32[o + a] = r.c32[i];
@@ -541,7 +542,9 @@ static void for_chunks(int64_t n, int nchunks, Fn fn) {
   for (int c = 0; c < nchunks; ++c) chunk(c);
 }
 
-// chunks: pieces of the loops over the terms (several for large polynomials: host pool).
+// The checks and the layout of a polynomial (each stage's fibres, offsets and output
+// positions); its coefficient block comes from pack_coefs.  chunks: pieces of the loops over
+// the terms (several for large polynomials: host pool).
 static int pack_poly(int k, const vx_poly &p, HostPoly *hp, const double *chi = nullptr,
                      int chunks = 1) {
   const int32_t nt = p.nterms;
@@ -680,10 +683,23 @@ static int pack_poly(int k, const vx_poly &p, HostPoly *hp, const double *chi = 
       }
     }
   }
-  // coefficient block of stage 0: entry (a_1, fibre) at rowoff[a_1] + fibre
-  const HostStage &S0 = hp->st[0];
-  hp->c64.assign(S0.blk_in, make_double2(0.0, 0.0));
-  std::vector<uint8_t> seen(S0.blk_in, 0);
+  return VX_OK;
+}
+
+// The coefficient block of stage 0 (entry (a_1, fibre) at rowoff[a_1] + fibre) of a packed
+// polynomial, written to dst (st[0].blk_in entries: the staging buffer of the upload, so that
+// the block is neither built elsewhere first nor copied); entries of no term are zero.
+static int pack_coefs(int k, const vx_poly &p, const HostPoly &hp, const double *chi,
+                      double2 *dst, int chunks = 1) {
+  const int32_t nt = p.nterms;
+  const int T = std::max(1, std::min(chunks, 64));
+  const HostStage &S0 = hp.st[0];
+  const int64_t n = S0.blk_in;
+  std::vector<uint8_t> seen((size_t)n);
+  for_chunks(n, T, [&](int, int64_t a, int64_t b) {
+    std::memset(dst + a, 0, (size_t)(b - a) * sizeof(double2));
+    std::memset(seen.data() + a, 0, (size_t)(b - a));
+  });
   std::vector<int64_t> dup(T, -1);
   for_chunks(nt, T, [&](int c, int64_t a, int64_t b) {
     for (int64_t t = a; t < b; ++t) {
@@ -695,7 +711,7 @@ static int pack_poly(int k, const vx_poly &p, HostPoly *hp, const double *chi = 
         if (dup[c] < 0) dup[c] = t;
         continue;
       }
-      hp->c64[pos] = make_double2(p.coefs[t], chi ? chi[t] : p.coefs[t]);
+      dst[pos] = make_double2(p.coefs[t], chi ? chi[t] : p.coefs[t]);
     }
   });
   for (int c = 0; c < T; ++c)
@@ -1042,8 +1058,9 @@ static int system_create_impl(const vx_poly *F, int32_t npoly, const double *con
   auto al = [](size_t x) { return (x + 255) & ~(size_t)255; };
   size_t bytes = 0;
   for (int f = 0; f < npoly; ++f) {
-    bytes += 2 * al(hp[f].c64.size() * sizeof(double2)) + 2 * al(hp[f].c64.size() * sizeof(float2)) +
-             4 * al(hp[f].c64.size() * sizeof(float4)) + 2 * al(hp[f].c64.size() * sizeof(float));
+    const size_t nc = (size_t)hp[f].st[0].blk_in;
+    bytes += 2 * al(nc * sizeof(double2)) + 2 * al(nc * sizeof(float2)) + 4 * al(nc * sizeof(float4)) +
+             2 * al(nc * sizeof(float));
     for (int s = 0; s < k; ++s) {
       const HostStage &S = hp[f].st[s];
       bytes += al((S.maxlen + 1) * 4) + 3 * al((size_t)S.nfib * 4) + al(((size_t)S.nfib + 1) * 4);
@@ -1066,6 +1083,37 @@ static int system_create_impl(const vx_poly *F, int32_t npoly, const double *con
       set_error("out of host memory");
       return VX_ENOMEM;
     }
+  }
+  // the coefficient blocks first in the staging buffer, packed in place (the way the layouts
+  // were: on the host pool for large polynomials, a thread each for mid-sized ones)
+  std::vector<size_t> coff(npoly);
+  size_t off = 0;
+  for (int f = 0; f < npoly; ++f) {
+    coff[f] = off;
+    off += al((size_t)hp[f].st[0].blk_in * sizeof(double2));
+  }
+  {
+    std::vector<int> rcs(npoly, VX_OK);
+    std::vector<std::string> msgs(npoly);
+    auto one = [&](int f, int chunks) {
+      rcs[f] = pack_coefs(k, F[f], hp[f], chi ? chi[f] : nullptr, (double2 *)(host + coff[f]), chunks);
+      if (rcs[f] != VX_OK) msgs[f] = vx_last_error();
+    };
+    if (large) {
+      for (int f = 0; f < npoly; ++f) one(f, F[f].nterms >= kPackSplitTerms ? pool_chunks : 1);
+    } else if (npoly > 1 && terms >= 20000) {
+      std::vector<std::thread> th;
+      for (int f = 0; f < npoly; ++f) th.emplace_back([&, f] { one(f, 1); });
+      for (auto &t : th) t.join();
+    } else {
+      for (int f = 0; f < npoly; ++f) one(f, 1);
+    }
+    for (int f = 0; f < npoly; ++f)
+      if (rcs[f] != VX_OK) {
+        pinned_put(hstage, hcap);
+        set_error("%s", msgs[f].c_str());
+        return rcs[f];
+      }
   }
   vx_system *sys = new (std::nothrow) vx_system();
   if (!sys) {
@@ -1094,7 +1142,6 @@ static int system_create_impl(const vx_poly *F, int32_t npoly, const double *con
     sys->coefs[f].assign(F[f].coefs, F[f].coefs + F[f].nterms);
     if (chi && chi[f]) sys->coefs_hi[f].assign(chi[f], chi[f] + F[f].nterms);
   }
-  size_t off = 0;
   char *dbase = (char *)sys->mem;
   auto put = [&](const void *src, size_t n) -> void * {
     std::memcpy(host + off, src, n);
@@ -1109,7 +1156,7 @@ static int system_create_impl(const vx_poly *F, int32_t npoly, const double *con
   };
   for (int f = 0; f < npoly; ++f) {
     PolyDev &P = sys->dev.p[f];
-    P.c64 = (const double2 *)put(hp[f].c64.data(), hp[f].c64.size() * sizeof(double2));
+    P.c64 = (const double2 *)(dbase + coff[f]);  // packed in place above
     for (int s2 = 0; s2 < k; ++s2) {
       const HostStage &S = hp[f].st[s2];
       StageDev &D = P.st[s2];
@@ -1130,19 +1177,20 @@ static int system_create_impl(const vx_poly *F, int32_t npoly, const double *con
   sys->upload_bytes = off;
   for (int f = 0; f < npoly; ++f) {
     PolyDev &P = sys->dev.p[f];
-    P.c32 = (const float2 *)reserve(hp[f].c64.size() * sizeof(float2));
-    P.c32c = (const float4 *)reserve(hp[f].c64.size() * sizeof(float4));
-    P.c32c_fm = (const float4 *)reserve(hp[f].c64.size() * sizeof(float4));
-    P.cp = (const float4 *)reserve(hp[f].c64.size() * sizeof(float4));
-    P.ep = (const float *)reserve(hp[f].c64.size() * sizeof(float));
-    P.cp_fm = (const float4 *)reserve(hp[f].c64.size() * sizeof(float4));
-    P.ep_fm = (const float *)reserve(hp[f].c64.size() * sizeof(float));
-    P.c64_fm = (const double2 *)reserve(hp[f].c64.size() * sizeof(double2));
-    P.c32_fm = (const float2 *)reserve(hp[f].c64.size() * sizeof(float2));
+    const size_t nc = (size_t)hp[f].st[0].blk_in;
+    P.c32 = (const float2 *)reserve(nc * sizeof(float2));
+    P.c32c = (const float4 *)reserve(nc * sizeof(float4));
+    P.c32c_fm = (const float4 *)reserve(nc * sizeof(float4));
+    P.cp = (const float4 *)reserve(nc * sizeof(float4));
+    P.ep = (const float *)reserve(nc * sizeof(float));
+    P.cp_fm = (const float4 *)reserve(nc * sizeof(float4));
+    P.ep_fm = (const float *)reserve(nc * sizeof(float));
+    P.c64_fm = (const double2 *)reserve(nc * sizeof(double2));
+    P.c32_fm = (const float2 *)reserve(nc * sizeof(float2));
   }
   cudaError_t e = cudaMemcpyAsync(sys->mem, host, sys->upload_bytes, cudaMemcpyHostToDevice, s);
   for (int f = 0; f < npoly && e == cudaSuccess; ++f) {
-    const int64_t n = (int64_t)hp[f].c64.size();
+    const int64_t n = hp[f].st[0].blk_in;
     if (n == 0) continue;
     const int64_t nb = std::min<int64_t>((n + 255) / 256, (int64_t)sm_count() * 8);
     k_encode_coefs<<<(unsigned)nb, 256, 0, s>>>(sys->dev.p[f].c64,
@@ -1159,7 +1207,7 @@ static int system_create_impl(const vx_poly *F, int32_t npoly, const double *con
       const Stage0BlocksFm w{const_cast<double2 *>(P.c64_fm), const_cast<float2 *>(P.c32_fm),
                              const_cast<float4 *>(P.c32c_fm), const_cast<float4 *>(P.cp_fm),
                              const_cast<float *>(P.ep_fm)};
-      k_fibre_major<<<(unsigned)std::min<int64_t>((S0.nfib + 127) / 128, (int64_t)sm_count() * 8),
+      k_fibre_major<<<(unsigned)std::min<int64_t>((S0.nfib + 3) / 4, (int64_t)sm_count() * 16),
                       128, 0, s>>>(r, S0.rowoff, S0.fiblen, S0.fiboff, S0.nfib, w);
       note_launch();
       e = cudaGetLastError();
@@ -1199,7 +1247,11 @@ int vx_system_measure(const vx_poly *F, int32_t npoly, int64_t *h_M) {
   const int pool_chunks = 2 * HostPool::get().size();
   for (int f = 0; f < npoly; ++f) {
     HostPoly hp;
-    VX_CHECK(pack_poly(k, F[f], &hp, nullptr, F[f].nterms >= kPackSplitTerms ? pool_chunks : 1));
+    const int chunks = F[f].nterms >= kPackSplitTerms ? pool_chunks : 1;
+    VX_CHECK(pack_poly(k, F[f], &hp, nullptr, chunks));
+    // the coefficient block too, for its checks (a monomial given twice)
+    std::vector<double2> blk((size_t)hp.st[0].blk_in);
+    VX_CHECK(pack_coefs(k, F[f], hp, nullptr, blk.data(), chunks));
     for (int s2 = 0; s2 < k; ++s2) h_M[(size_t)f * (k + 1) + s2] = hp.st[s2].blk_in;
     h_M[(size_t)f * (k + 1) + k] = 1;
   }

@@ -937,7 +937,8 @@ def run_gpu(args):
 
     def e2e_once():
         """Host polynomials in, host boxes out, through the public API."""
-        o = vx.make_opts(vx.FP32, recheck_last=True, first_level=FIRST_LEVEL)
+        # host_codes: the last compaction writes the boxes' codes into pinned host memory
+        o = vx.make_opts(vx.FP32, recheck_last=True, first_level=FIRST_LEVEL, host_codes=True)
         if world == 1:
             r = vx.enclose(polys_host, dom, depth, o)
             return r, sysv.upload_bytes()  # vx_enclose packs and uploads the same system
@@ -976,7 +977,7 @@ def run_gpu(args):
     e2e = {"value": e2e_evals / e2e_s, "unit": UNIT, "h2d_bytes_per_step": h2d // ne2e,
            "d2h_bytes_per_step": d2h // ne2e, "steps": ne2e,
            "ms_each": [round(x, 2) for x in e2e_ms],
-           "what": "vx_enclose from host polynomials (pack + upload) to the host's boxes (one uint32 grid-index code per box, vx_result_box_codes)"}
+           "what": "vx_enclose from host polynomials (pack + upload) to the host's boxes (one uint32 grid-index code per box, written into pinned host memory by the last level's compaction: host_codes; vx_result_box_codes)"}
 
     # ---- config 5: one complete level (Property 1's dense grid), and config 4: the batch ----
     extra = {}

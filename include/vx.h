@@ -144,6 +144,12 @@ typedef struct {
                         * the levels before it are not evaluated (zero in vx_result_stats) and the
                         * start level tests its whole grid.  For levels that keep nearly every box,
                         * whose launches cost more than their few boxes */
+  int32_t host_codes;  /* nonzero (vx_enclose*): the last level's compaction writes every final
+                        * box's grid-index code (vx_result_box_codes' format) straight into pinned
+                        * host memory as it places the box, so that the codes cross the host link
+                        * while the compaction runs; vx_result_box_codes then returns them without
+                        * a copy.  Ignored (the codes are made on the first vx_result_box_codes
+                        * call) when the final boxes are several trees (max_level_boxes) */
 } vx_opts;
 
 /* Thread-local message of the last failed call on this thread ("" if none). */

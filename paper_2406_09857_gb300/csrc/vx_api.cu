@@ -622,17 +622,22 @@ static int pack_poly(int k, const vx_poly &p, HostPoly *hp, const double *chi = 
     for (int c = 0; c < T; ++c)
       if (!lens[c].empty())
         for (int32_t f = 0; f < nf; ++f) len[f] = std::max(len[f], lens[c][f]);
-    std::vector<int32_t> order(nf);
-    for (int32_t f = 0; f < nf; ++f) order[f] = f;
-    std::sort(order.begin(), order.end(), [&](int32_t a, int32_t b) {
-      if (len[a] != len[b]) return len[a] > len[b];
-      return S.keys[a] < S.keys[b];
-    });
+    // the fibres longest first, equal lengths by increasing key: a counting sort by length,
+    // then each length's keys sorted
+    int32_t maxl = 1;
+    for (int32_t f = 0; f < nf; ++f) maxl = std::max(maxl, len[f]);
+    std::vector<int32_t> start(maxl + 2, 0);  // bucket b = maxl - length
+    for (int32_t f = 0; f < nf; ++f) ++start[maxl - len[f] + 1];
+    for (int32_t b = 0; b <= maxl; ++b) start[b + 1] += start[b];
     std::vector<uint64_t> keys(nf);
+    {
+      std::vector<int32_t> next(start.begin(), start.end() - 1);
+      for (int32_t f = 0; f < nf; ++f) keys[next[maxl - len[f]]++] = S.keys[f];
+    }
     S.fiblen.resize(nf);
-    for (int32_t f = 0; f < nf; ++f) {
-      keys[f] = S.keys[order[f]];
-      S.fiblen[f] = len[order[f]];
+    for (int32_t b = 0; b <= maxl; ++b) {
+      std::sort(keys.begin() + start[b], keys.begin() + start[b + 1]);
+      for (int32_t f = start[b]; f < start[b + 1]; ++f) S.fiblen[f] = maxl - b;
     }
     S.keys.swap(keys);
     S.index.build(S.keys, k - 1 - s, key_bits(k), E);
@@ -2006,7 +2011,29 @@ struct EncloseRun {
   vx_result *R;
   Timer *tm;
   int64_t cap;  // the most boxes one tree may hold at a level (the leaves' count)
+  bool chunked = false;  // the levels run in x_1 ranges (several final trees)
 };
+
+// CodesSink of the last level's compaction (opts.host_codes): a pinned pool buffer for the
+// result's codes, which the device writes through its mapped address.
+static int host_codes_get(void *ctx, int64_t n, int cb, void **d_codes) {
+  vx_result *R = static_cast<vx_result *>(ctx);
+  *d_codes = nullptr;
+  void *hb = nullptr;
+  size_t cap = 0;
+  VX_CHECK(pinned_get((size_t)n * cb, &hb, &cap));
+  void *dh = nullptr;
+  if (cudaHostGetDevicePointer(&dh, hb, 0) != cudaSuccess || !dh) {
+    cudaGetLastError();  // not device-addressable: vx_result_box_codes makes them later
+    pinned_put(hb, cap);
+    return VX_OK;
+  }
+  R->hcodes = hb;
+  R->hcodes_cap = cap;
+  R->hcodes_count = n;
+  *d_codes = dh;
+  return VX_OK;
+}
 
 static void result_append(vx_result *R, CsfObj &fin) {
   if (!R->fin_set) {
@@ -2149,6 +2176,7 @@ static int run_levels(EncloseRun &E, CsfObj &cur, int l);
 // stay in its slab and every box is decided on its own, so the runs' final boxes, one after
 // another, are the enclosure's, in lexicographic order.
 static int run_chunked(EncloseRun &E, CsfObj &cur, const uint8_t *keep, int l) {
+  E.chunked = true;
   const int k = E.k;
   const cudaStream_t s = E.s;
   const int64_t n0 = cur.v.N[0], n = cur.v.N[k - 1];
@@ -2219,7 +2247,11 @@ static int run_levels(EncloseRun &E, CsfObj &cur, int l) {
     };
     if (l == E.depth) {
       CsfObj fin;
-      const int rp = csf_prune(cur.v, keep, 0, nullptr, E.s, &fin, E.tm);
+      // the final boxes' codes straight to the host, where they will be one tree
+      const CodesSink sink{host_codes_get, E.R};
+      const bool eager = E.opts.host_codes && !E.chunked && !E.R->fin_set && E.R->hcodes_count < 0;
+      const int rp = csf_prune(cur.v, keep, 0, nullptr, E.s, &fin, E.tm, INT32_MAX,
+                               eager ? &sink : nullptr);
       rc = status_after_prune(rp);
       if (rp == VX_OK && rc != VX_OK) csf_release(&fin);
       if (rc == VX_OK) {

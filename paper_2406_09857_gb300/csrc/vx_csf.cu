@@ -817,6 +817,69 @@ __global__ void k_gather(CsfView in, const uint8_t *__restrict__ flags, const Ra
   }
 }
 
+// The leaf depth's compaction (k_gather<D>, D = k-1) that also writes each kept leaf's
+// grid-index code (k_box_codes' formula, cb = 4 or 8 bytes) at its rank, for a destination
+// across the host link (mapped pinned memory), where a partial cache line costs about as much
+// as a full one: a CTA takes a contiguous chunk of kGatherChunk entries, stages the chunk's
+// codes (consecutive ranks) in shared memory and writes them as whole aligned lines, only the
+// chunk's two ends partial.
+constexpr int kGatherChunk = 2048;
+template <int D>
+__global__ void __launch_bounds__(256)
+    k_gather_codes(CsfView in, const uint8_t *__restrict__ flags, const RankView rank, Segs sg,
+                   CsfView out, int32_t *index, void *codes, int cb) {
+  constexpr int d = D;
+  extern __shared__ __align__(16) unsigned char s_codes[];
+  __shared__ int32_t s_cnt;
+  const int64_t lo = sg.off[d], hi = lo + in.N[d];
+  const int64_t a0 = lo & ~(int64_t)31;
+  const int64_t nch = (hi - a0 + kGatherChunk - 1) / kGatherChunk;
+  const int lane = threadIdx.x & 31;
+  for (int64_t ch = blockIdx.x; ch < nch; ch += gridDim.x) {
+    const int64_t A = a0 + ch * kGatherChunk;  // a multiple of 32, > lo - 32, < hi
+    const int32_t R0 = rank.base32(A, lo);     // the chunk's first rank
+    if (threadIdx.x == 0) s_cnt = 0;
+    __syncthreads();
+    for (int64_t a = A + (threadIdx.x & ~31); a < A + kGatherChunk && a < hi; a += blockDim.x) {
+      const int64_t i = a + lane, p = i - lo;
+      const bool kept = i >= lo && i < hi && flags[i];
+      const int32_t base = rank.base32(a, lo);
+      const unsigned bal = __ballot_sync(0xffffffffu, kept);
+      if (lane == 0 && bal) atomicAdd(&s_cnt, __popc(bal));
+      if (!kept) continue;
+      const int32_t r = window_rank(base, bal);
+      const int32_t lab = __ldg(in.lab[d] + p);
+      const int32_t pp = d > 0 ? __ldg(in.par[d] + p) : 0;
+      out.lab[d][r] = lab;
+      if (d > 0) out.par[d][r] = __ldg(rank.rank + sg.off[d - 1] + pp);
+      if (index) index[r] = (int32_t)p;
+      uint64_t code = (uint32_t)lab;
+      int32_t q = pp;
+#pragma unroll
+      for (int e = d - 1; e >= 0; --e) {
+        code |= (uint64_t)(uint32_t)__ldg(in.lab[e] + q) << (in.level * (d - e));
+        if (e > 0) q = __ldg(in.par[e] + q);
+      }
+      if (cb == 4)
+        reinterpret_cast<uint32_t *>(s_codes)[r - R0] = (uint32_t)code;
+      else
+        reinterpret_cast<uint64_t *>(s_codes)[r - R0] = code;
+    }
+    __syncthreads();
+    // ranks R0 .. R0 + s_cnt - 1, written from the 32-aligned rank below R0: each warp store
+    // covers whole lines
+    const int64_t e0 = R0, e1 = (int64_t)R0 + s_cnt;
+    for (int64_t g = (e0 & ~(int64_t)31) + threadIdx.x; g < e1; g += blockDim.x) {
+      if (g < e0) continue;
+      if (cb == 4)
+        static_cast<uint32_t *>(codes)[g] = reinterpret_cast<const uint32_t *>(s_codes)[g - e0];
+      else
+        static_cast<uint64_t *>(codes)[g] = reinterpret_cast<const uint64_t *>(s_codes)[g - e0];
+    }
+    __syncthreads();  // s_codes and s_cnt are rewritten by the next chunk
+  }
+}
+
 int blocks_for(int64_t n) {
   int64_t b = (n + 255) / 256;
   if (b > (int64_t)sm_count() * 32) b = (int64_t)sm_count() * 32;
@@ -851,7 +914,22 @@ void launch_kptr(int d, int blocks, cudaStream_t s, const CsfView &in, const uin
 }
 
 void launch_gather(int d, int blocks, cudaStream_t s, const CsfView &in, const uint8_t *flags,
-                   const RankView &rank, const Segs &sg, const CsfView &out, int32_t *index) {
+                   const RankView &rank, const Segs &sg, const CsfView &out, int32_t *index,
+                   void *codes, int cb) {
+  if (codes) {  // the leaf depth with its codes
+    const int64_t nch = (in.N[d] + 31 + kGatherChunk - 1) / kGatherChunk;
+    const unsigned g = (unsigned)std::max<int64_t>(1, std::min<int64_t>(nch, (int64_t)sm_count() * 8));
+    const size_t sm = (size_t)kGatherChunk * cb;
+    switch (d) {
+      case 0: k_gather_codes<0><<<g, 256, sm, s>>>(in, flags, rank, sg, out, index, codes, cb); break;
+      case 1: k_gather_codes<1><<<g, 256, sm, s>>>(in, flags, rank, sg, out, index, codes, cb); break;
+      case 2: k_gather_codes<2><<<g, 256, sm, s>>>(in, flags, rank, sg, out, index, codes, cb); break;
+      case 3: k_gather_codes<3><<<g, 256, sm, s>>>(in, flags, rank, sg, out, index, codes, cb); break;
+      case 4: k_gather_codes<4><<<g, 256, sm, s>>>(in, flags, rank, sg, out, index, codes, cb); break;
+      default: k_gather_codes<5><<<g, 256, sm, s>>>(in, flags, rank, sg, out, index, codes, cb); break;
+    }
+    return;
+  }
   switch (d) {
     case 0: k_gather<0><<<blocks, 256, 0, s>>>(in, flags, rank, sg, out, index); break;
     case 1: k_gather<1><<<blocks, 256, 0, s>>>(in, flags, rank, sg, out, index); break;
@@ -879,7 +957,7 @@ template <int C>
 int prune_c(const CsfView &in, const uint8_t *d_keep, int split, int32_t *d_index,
             cudaStream_t s, CsfObj *out, Timer *tm, const int64_t *d_seg_off = nullptr,
             int nseg = 0, int64_t *d_seg_kept = nullptr, int64_t cap = INT32_MAX,
-            int64_t *h_seg_kept = nullptr) {
+            int64_t *h_seg_kept = nullptr, const CodesSink *sink = nullptr) {
   const int k = in.k;
   Segs sg;
   sg.k = k;
@@ -1017,6 +1095,11 @@ int prune_c(const CsfView &in, const uint8_t *d_keep, int split, int32_t *d_inde
     rebuild_bytes += ((int64_t)nk[d] + (split ? newN[d] : (int64_t)nk[d])) * w;
   }
   if (!split && d_index) rebuild_bytes += 4 * (int64_t)nk[k - 1];
+  // a compaction's leaf codes, where the caller takes them now
+  void *codes = nullptr;
+  const int cb = k * in.level <= 32 ? 4 : 8;
+  if (rc == VX_OK && !split && sink && nk[k - 1] > 0)
+    rc = sink->get(sink->ctx, nk[k - 1], cb, &codes);
   if (rc == VX_OK && tm && tm->on) rc = tm->begin(split ? KK_SPLIT : KK_COMPACT, rebuild_bytes);
   for (int d = 0; d + 1 < k && rc == VX_OK; ++d) {
     launch_kptr(d, blocks_for(in.N[d]), s, in, flags, rv, sg, (int32_t *)K.k[d]);
@@ -1039,7 +1122,8 @@ int prune_c(const CsfView &in, const uint8_t *d_keep, int split, int32_t *d_inde
     if (split)
       launch_split<C>(d, blocks_for(in.N[d]), s, in, flags, rv, sg, K, out->v);
     else
-      launch_gather(d, blocks_for(in.N[d]), s, in, flags, rv, sg, out->v, d_index);
+      launch_gather(d, blocks_for(in.N[d]), s, in, flags, rv, sg, out->v, d_index,
+                    d == k - 1 ? codes : nullptr, cb);
     note_launch();
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) {
@@ -1252,14 +1336,14 @@ int csf_build_dev(int k, int level, const int32_t *d_tuples, int64_t n, cudaStre
 }
 
 int csf_prune(const CsfView &in, const uint8_t *d_keep, int split, int32_t *d_index,
-              cudaStream_t s, CsfObj *out, Timer *tm, int64_t cap) {
+              cudaStream_t s, CsfObj *out, Timer *tm, int64_t cap, const CodesSink *sink) {
   switch (in.k) {
-    case 1: return prune_c<1>(in, d_keep, split, d_index, s, out, tm, nullptr, 0, nullptr, cap);
-    case 2: return prune_c<2>(in, d_keep, split, d_index, s, out, tm, nullptr, 0, nullptr, cap);
-    case 3: return prune_c<3>(in, d_keep, split, d_index, s, out, tm, nullptr, 0, nullptr, cap);
-    case 4: return prune_c<4>(in, d_keep, split, d_index, s, out, tm, nullptr, 0, nullptr, cap);
-    case 5: return prune_c<5>(in, d_keep, split, d_index, s, out, tm, nullptr, 0, nullptr, cap);
-    default: return prune_c<6>(in, d_keep, split, d_index, s, out, tm, nullptr, 0, nullptr, cap);
+    case 1: return prune_c<1>(in, d_keep, split, d_index, s, out, tm, nullptr, 0, nullptr, cap, nullptr, sink);
+    case 2: return prune_c<2>(in, d_keep, split, d_index, s, out, tm, nullptr, 0, nullptr, cap, nullptr, sink);
+    case 3: return prune_c<3>(in, d_keep, split, d_index, s, out, tm, nullptr, 0, nullptr, cap, nullptr, sink);
+    case 4: return prune_c<4>(in, d_keep, split, d_index, s, out, tm, nullptr, 0, nullptr, cap, nullptr, sink);
+    case 5: return prune_c<5>(in, d_keep, split, d_index, s, out, tm, nullptr, 0, nullptr, cap, nullptr, sink);
+    default: return prune_c<6>(in, d_keep, split, d_index, s, out, tm, nullptr, 0, nullptr, cap, nullptr, sink);
   }
 }
 

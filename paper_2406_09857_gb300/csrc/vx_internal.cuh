@@ -246,8 +246,17 @@ int csf_build_dev(int k, int level, const int32_t *d_tuples, int64_t n, cudaStre
 // writing the kept leaves' old indices to d_index when non-null.
 // cap: the most nodes the output may have at any depth (VX_EOVERFLOW beyond it; at most
 // INT32_MAX, the tree's index range).
+// Where a compaction writes its kept leaves' grid-index codes (k_box_codes' codes, 4 bytes
+// when k * level <= 32, else 8) as it places them: get(ctx, n, code_bytes, &p) is called once
+// the kept count n is known and returns in p a device-addressable array of n codes (nullptr:
+// none are written) or an error.
+struct CodesSink {
+  int (*get)(void *ctx, int64_t n, int code_bytes, void **d_codes);
+  void *ctx;
+};
 int csf_prune(const CsfView &in, const uint8_t *d_keep, int split, int32_t *d_index,
-              cudaStream_t s, CsfObj *out, Timer *tm, int64_t cap = INT32_MAX);
+              cudaStream_t s, CsfObj *out, Timer *tm, int64_t cap = INT32_MAX,
+              const CodesSink *sink = nullptr);
 // Per depth-0 node (an x_1 slab) r, d_cnt[r] = the leaves under it with d_keep set.
 int csf_root_counts(const CsfView &c, const uint8_t *d_keep, int64_t *d_cnt, cudaStream_t s);
 // d_out[i] = d_keep[i] for the leaves under depth-0 nodes a .. b-1, 0 elsewhere.

@@ -41,7 +41,8 @@ class Opts(ctypes.Structure):
                 ("timing", ctypes.c_int32), ("taylor_order", ctypes.c_int32),
                 ("c1", ctypes.c_int32), ("c1_level", ctypes.c_int32),
                 ("small_level_madds", ctypes.c_int32), ("recheck_last", ctypes.c_int32),
-                ("max_level_boxes", ctypes.c_int32), ("first_level", ctypes.c_int32)]
+                ("max_level_boxes", ctypes.c_int32), ("first_level", ctypes.c_int32),
+                ("host_codes", ctypes.c_int32)]
 
 
 def lib() -> ctypes.CDLL:
@@ -189,8 +190,9 @@ def _domain(domain) -> np.ndarray:
 
 def make_opts(mode=FP64, fp64_final=False, fp64_recheck=False, theta=0.5, timing=False,
               taylor_order=0, c1=0, c1_level=0, small_level_madds=0, recheck_last=False,
-              max_level_boxes=0, first_level=0) -> Opts:
+              max_level_boxes=0, first_level=0, host_codes=False) -> Opts:
     o = Opts()
+    o.host_codes = int(bool(host_codes))
     o.max_level_boxes = int(max_level_boxes)
     o.first_level = int(first_level)
     o.recheck_last = int(bool(recheck_last))

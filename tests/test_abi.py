@@ -36,7 +36,22 @@ def test_loads_and_answers_without_device(libpath):
     assert b"polynomials" in L.vx_last_error()
 
 
-def test_opts_layout_matches_header():
-    # vx_opts: 5 int32-sized fields + 7 reserved = 48 bytes
-    assert ctypes.sizeof(vx.Opts) == 48
-    assert ctypes.sizeof(vx.Poly) == 24
+def test_opts_layout_matches_header(tmp_path):
+    """The binding's vx_opts and vx_poly have the header's size and field offsets, as a C
+    compiler lays them out."""
+    inc = vxbuild.INCLUDE
+    src = tmp_path / "layout.c"
+    lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "vx.h"', "int main(void) {",
+             '  printf("opts %zu\\n", sizeof(vx_opts));', '  printf("poly %zu\\n", sizeof(vx_poly));']
+    for name, _ in vx.Opts._fields_:
+        lines.append('  printf("%s %%zu\\n", offsetof(vx_opts, %s));' % (name, name))
+    lines += ["  return 0;", "}"]
+    src.write_text("\n".join(lines) + "\n")
+    exe = tmp_path / "layout"
+    subprocess.run(["gcc", "-I", inc, str(src), "-o", str(exe)], check=True)
+    got = dict(line.split() for line in subprocess.run([str(exe)], capture_output=True,
+                                                        text=True, check=True).stdout.splitlines())
+    assert int(got.pop("opts")) == ctypes.sizeof(vx.Opts)
+    assert int(got.pop("poly")) == ctypes.sizeof(vx.Poly)
+    for name, _ in vx.Opts._fields_:
+        assert int(got[name]) == getattr(vx.Opts, name).offset, name

@@ -654,10 +654,13 @@ def test_small_levels_in_binary64(vx):
     assert np.array_equal(r.boxes(), reft["tuples"])
 
 
+@pytest.mark.parametrize("host_codes", [False, True])
 @pytest.mark.parametrize("k,d,depth", [(3, 8, 7), (4, 3, 9), (2, 12, 16)])
-def test_box_codes_decode_to_the_boxes(vx, k, d, depth):
+def test_box_codes_decode_to_the_boxes(vx, k, d, depth, host_codes):
+    """The boxes' grid-index codes, made on request or (host_codes) written into pinned host
+    memory by the last level's compaction: increasing, and decoding to the boxes."""
     polys = [synth.kostlan_poly(k, d, 1400 + depth)]
-    r = vx.enclose(polys, synth.cube(k), depth, vx.make_opts(vx.FP32))
+    r = vx.enclose(polys, synth.cube(k), depth, vx.make_opts(vx.FP32, host_codes=host_codes))
     codes = r.box_codes()
     assert codes.dtype == (np.uint32 if k * depth <= 32 else np.uint64)
     assert np.all(codes[1:] > codes[:-1])
@@ -742,7 +745,10 @@ def test_enclose_in_x1_ranges_equals_oracle(vx, name, cap, mode_name, recheck_la
                "nodes": ws["nodes"]}
     k = ref["tuples"].shape[1]
     assert max(ref["kept"][:-1]) << k > cap, "the cap must force a split"
-    o = vx.make_opts(getattr(vx, mode_name), recheck_last=recheck_last, max_level_boxes=cap)
+    # host_codes asks for the codes from the last compaction; with the final boxes in several
+    # trees they are made on request instead (the same codes)
+    o = vx.make_opts(getattr(vx, mode_name), recheck_last=recheck_last, max_level_boxes=cap,
+                     host_codes=True)
     res = vx.enclose(polys, dom, depth, o)
     st = res.stats()
     assert np.array_equal(res.boxes(), ref["tuples"])

@@ -101,6 +101,36 @@ struct ItemOps {
   }
 };
 
+// A tile whose entries the source can count in a form of its own (32 flag bytes per thread
+// and step): adds them to cnt and returns true.  Entries t0..t1-1.
+template <int C, class Src>
+__device__ __forceinline__ bool reduce_tile(const Src &, int64_t, int64_t, int32_t (&)[C]) {
+  return false;
+}
+
+// The nonzero bytes among entries e0 .. e0+31 (< t1) of a byte array: byte j of word q as bit
+// 8 (j) + 7 of nz[q] (two 16-byte loads when all 32 lie before t1; f 16-byte aligned, e0 a
+// multiple of 32).
+__device__ __forceinline__ void nonzero32(const uint8_t *f, int64_t e0, int64_t t1,
+                                          uint32_t (&nz)[8]) {
+  if (e0 + 32 <= t1) {
+    const uint4 v0 = __ldg(reinterpret_cast<const uint4 *>(f + e0));
+    const uint4 v1 = __ldg(reinterpret_cast<const uint4 *>(f + e0 + 16));
+    const uint32_t w[8] = {v0.x, v0.y, v0.z, v0.w, v1.x, v1.y, v1.z, v1.w};
+#pragma unroll
+    for (int q = 0; q < 8; ++q) nz[q] = (((w[q] & 0x7f7f7f7fu) + 0x7f7f7f7fu) | w[q]) & 0x80808080u;
+  } else {
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+      nz[q] = 0u;
+      for (int j = 0; j < 4; ++j) {
+        const int64_t i = e0 + 4 * q + j;
+        if (i < t1 && f[i]) nz[q] |= 0x80u << (8 * j);
+      }
+    }
+  }
+}
+
 // Per scan tile and channel, the count of flagged entries (scan_passes(n) passes of STILE
 // entries; the passes' loads are independent).
 template <int C, class Src>
@@ -112,12 +142,15 @@ __global__ void __launch_bounds__(ST) k_scan_reduce(Src src, int64_t n, int32_t 
   int32_t cnt[C];
 #pragma unroll
   for (int c = 0; c < C; ++c) cnt[c] = 0;
+  const int64_t t0 = tile * passes * STILE;
+  if (!reduce_tile<C>(src, t0, std::min<int64_t>(n, t0 + (int64_t)passes * STILE), cnt)) {
 #pragma unroll SR
-  for (int r = 0; r < passes; ++r) {
-    const int64_t i0 = (tile * passes + r) * STILE + (int64_t)threadIdx.x * SI;
-    ItemOps<C, Src> it;
-    it.load(src, i0, n, true);
-    it.count(cnt);
+    for (int r = 0; r < passes; ++r) {
+      const int64_t i0 = (tile * passes + r) * STILE + (int64_t)threadIdx.x * SI;
+      ItemOps<C, Src> it;
+      it.load(src, i0, n, true);
+      it.count(cnt);
+    }
   }
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
 #pragma unroll
@@ -170,6 +203,14 @@ __global__ void __launch_bounds__(1024) k_scan_tiles(int32_t *tsum, int64_t ntil
   }
 }
 
+// A tile that the source and emitter can rank in a form of their own, faster than the passes
+// below (FlagSrc + RankEmit: a tile of leaves only); returns whether it did.  Entries t0..t1-1.
+template <int C, class Src, class Emit>
+__device__ __forceinline__ bool emit_tile(const Src &, const Emit &, int64_t, int64_t,
+                                          const int32_t *, int64_t, int64_t) {
+  return false;
+}
+
 // The exclusive counts of every entry: the tile's offset (toff) carried over its passes, each
 // pass a block-wide scan.  The next pass's flags are loaded before this pass's scan (their
 // latency overlaps it), and with at most 3 channels the per-thread counts (at most SI = 8 each,
@@ -181,6 +222,12 @@ __global__ void __launch_bounds__(ST) k_scan_emit(Src src, Emit em, int64_t n,
   const int64_t tile = blockIdx.x;
   const int passes = scan_passes(n);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  {
+    const int64_t t0 = tile * passes * STILE;
+    if (emit_tile<C>(src, em, t0, std::min<int64_t>(n, t0 + (int64_t)passes * STILE), toff,
+                     ntiles, tile))
+      return;
+  }
   int32_t carry[C];
 #pragma unroll
   for (int c = 0; c < C; ++c) carry[c] = toff[c * ntiles + tile];
@@ -463,6 +510,22 @@ __device__ __forceinline__ void load_items(const FlagSrc &src, int64_t i0, int64
   }
 }
 
+// A tile of leaves only (the last segment): 32 flag bytes (0 or 1 each) per thread and step.
+template <int C>
+__device__ __forceinline__ bool reduce_tile(const FlagSrc &src, int64_t t0, int64_t t1,
+                                            int32_t (&cnt)[C]) {
+  if (t0 < src.sg.off[C - 1]) return false;  // the same for the whole CTA
+  int32_t c = 0;
+  for (int64_t e0 = t0 + (int64_t)threadIdx.x * 32; e0 < t1; e0 += (int64_t)ST * 32) {
+    uint32_t nz[8];
+    nonzero32(src.f, e0, t1, nz);
+#pragma unroll
+    for (int q = 0; q < 8; ++q) c += __popc(nz[q]);
+  }
+  cnt[C - 1] += c;
+  return true;
+}
+
 // The ranks of a pruned tree: rank[i] (the kept nodes of its depth before node i) for the inner
 // depths (i < loff, the leaf segment's start), and for the leaf depth one count per aligned
 // 8-entry word of the flag array, rank8[w - w0] = the kept leaves before word w; a leaf's rank
@@ -547,6 +610,61 @@ __device__ __forceinline__ void emit_items(const RankEmit &em, int64_t i0, int64
       }
     }
   }
+}
+
+// A tile of leaves only: their ranks are one count per 8-entry word, so a thread takes four
+// words (32 flag bytes, two 16-byte loads) per step and one block-wide scan serves 8192
+// entries, against 2048 per pass of the general form (whose barriers bound the scan).
+template <int C>
+__device__ __forceinline__ bool emit_tile(const FlagSrc &src, const RankEmit &em, int64_t t0,
+                                          int64_t t1, const int32_t *toff, int64_t ntiles,
+                                          int64_t tile) {
+  if (t0 < em.loff) return false;  // the same for the whole CTA
+  constexpr int WPT = 4;
+  __shared__ int32_t s_w[ST / 32 + 1];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  int32_t carry = toff[(C - 1) * ntiles + tile];
+  for (int64_t b = t0; b < t1; b += (int64_t)ST * WPT * 8) {
+    const int64_t e0 = b + (int64_t)threadIdx.x * WPT * 8;  // a multiple of 32
+    int32_t c[WPT];
+    if (e0 + WPT * 8 <= t1) {
+      const uint4 v0 = __ldg(reinterpret_cast<const uint4 *>(src.f + e0));
+      const uint4 v1 = __ldg(reinterpret_cast<const uint4 *>(src.f + e0 + 16));
+      c[0] = __popc(v0.x) + __popc(v0.y);
+      c[1] = __popc(v0.z) + __popc(v0.w);
+      c[2] = __popc(v1.x) + __popc(v1.y);
+      c[3] = __popc(v1.z) + __popc(v1.w);
+    } else {
+#pragma unroll
+      for (int j = 0; j < WPT; ++j) {
+        c[j] = 0;
+        for (int q = 0; q < 8; ++q) {
+          const int64_t i = e0 + 8 * j + q;
+          if (i < t1) c[j] += src.f[i] ? 1 : 0;
+        }
+      }
+    }
+    const int32_t sum = c[0] + c[1] + c[2] + c[3];
+    const int32_t incl = warp_incl_scan(sum);
+    if (lane == 31) s_w[warp] = incl;
+    __syncthreads();
+    if (warp == 0) {
+      const int32_t v = lane < ST / 32 ? s_w[lane] : 0;
+      const int32_t sc = warp_incl_scan(v);
+      if (lane < ST / 32) s_w[lane] = sc - v;
+      if (lane == ST / 32 - 1) s_w[ST / 32] = sc;
+    }
+    __syncthreads();
+    int32_t run = carry + s_w[warp] + incl - sum;
+#pragma unroll
+    for (int j = 0; j < WPT; ++j) {
+      if (e0 + 8 * j < t1) em.rank8[((e0 >> 3) + j) - em.w0] = run;
+      run += c[j];
+    }
+    carry += s_w[ST / 32];
+    __syncthreads();  // s_w is rewritten by the next step
+  }
+  return true;
 }
 
 // FlagSrc: the eight flag bytes of a thread (0 or 1 each) usually lie in one depth's segment;
@@ -1244,6 +1362,69 @@ struct ItemOps<1, ByteFlagSrc> {
     }
   }
 };
+
+// Byte flags at a 16-byte aligned address: 32 per thread and step, counted by popcount; the
+// emit scans a step only where a flag is set (a few selected among many).
+template <int C>
+__device__ __forceinline__ bool reduce_tile(const ByteFlagSrc &src, int64_t t0, int64_t t1,
+                                            int32_t (&cnt)[C]) {
+  if (reinterpret_cast<uintptr_t>(src.f) & 15u) return false;
+  int32_t c = 0;
+  for (int64_t e0 = t0 + (int64_t)threadIdx.x * 32; e0 < t1; e0 += (int64_t)ST * 32) {
+    uint32_t nz[8];
+    nonzero32(src.f, e0, t1, nz);
+#pragma unroll
+    for (int q = 0; q < 8; ++q) c += __popc(nz[q]);
+  }
+  cnt[0] += c;
+  return true;
+}
+
+template <int C>
+__device__ __forceinline__ bool emit_tile(const ByteFlagSrc &src, const IndexEmit &em, int64_t t0,
+                                          int64_t t1, const int32_t *toff, int64_t ntiles,
+                                          int64_t tile) {
+  if (reinterpret_cast<uintptr_t>(src.f) & 15u) return false;
+  __shared__ int32_t s_w[ST / 32 + 1];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  int32_t carry = toff[tile];
+  for (int64_t b = t0; b < t1; b += (int64_t)ST * 32) {
+    const int64_t e0 = b + (int64_t)threadIdx.x * 32;
+    uint32_t nz[8];
+    int32_t sum = 0;
+    if (e0 < t1) {
+      nonzero32(src.f, e0, t1, nz);
+#pragma unroll
+      for (int q = 0; q < 8; ++q) sum += __popc(nz[q]);
+    }
+    if (!__syncthreads_or(sum)) continue;  // no flag in the step: nothing to emit
+    const int32_t incl = warp_incl_scan(sum);
+    if (lane == 31) s_w[warp] = incl;
+    __syncthreads();
+    if (warp == 0) {
+      const int32_t v = lane < ST / 32 ? s_w[lane] : 0;
+      const int32_t sc = warp_incl_scan(v);
+      if (lane < ST / 32) s_w[lane] = sc - v;
+      if (lane == ST / 32 - 1) s_w[ST / 32] = sc;
+    }
+    __syncthreads();
+    int32_t run = carry + s_w[warp] + incl - sum;
+    if (sum) {
+#pragma unroll
+      for (int q = 0; q < 8; ++q) {
+        uint32_t bits = nz[q];
+        while (bits) {
+          const int j = (__ffs(bits) - 1) >> 3;
+          em.idx[run++] = (int32_t)(e0 + 4 * q + j);
+          bits &= bits - 1u;
+        }
+      }
+    }
+    carry += s_w[ST / 32];
+    __syncthreads();  // s_w is rewritten by the next step
+  }
+  return true;
+}
 
 __global__ void k_tuples_of(CsfView c, const int32_t *__restrict__ idx, int64_t n, int32_t *t) {
   const int k = c.k;

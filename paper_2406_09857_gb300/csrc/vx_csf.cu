@@ -911,27 +911,44 @@ __global__ void k_split(CsfView in, const uint8_t *__restrict__ flags, const Ran
   }
 }
 
-// Compaction of depth d: kept node p goes to its rank.
+// Compaction of depth d: kept node p goes to its rank.  A warp takes kGatherU consecutive
+// 32-aligned windows of the flag array per step (blockDim and the stride multiples of 32), so
+// that the windows' flag, label, parent and rank loads are in flight together (one window per
+// step left the kernel waiting on each kept node's chain of loads in turn).
+constexpr int kGatherU = 4;
 template <int D>
 __global__ void k_gather(CsfView in, const uint8_t *__restrict__ flags, const RankView rank,
                          Segs sg, CsfView out, int32_t *index) {
-  constexpr int d = D;
+  constexpr int d = D, U = kGatherU;
   const int64_t lo = sg.off[d], hi = lo + in.N[d];
-  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-  // a warp takes a 32-aligned window of the flag array (blockDim and stride multiples of 32)
-  for (int64_t a = (lo & ~(int64_t)31) + (int64_t)blockIdx.x * blockDim.x + (threadIdx.x & ~31);
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x * U;
+  const int lane = threadIdx.x & 31;
+  for (int64_t a = (lo & ~(int64_t)31) + ((int64_t)blockIdx.x * blockDim.x + (threadIdx.x & ~31)) * U;
        a < hi; a += stride) {
-    const int64_t i = a + (threadIdx.x & 31), p = i - lo;
-    const bool kept = i >= lo && i < hi && flags[i];
-    const int32_t base = rank.base32(a, lo);
-    const unsigned bal = __ballot_sync(0xffffffffu, kept);
-    if (!kept) continue;
-    const int32_t r = window_rank(base, bal);
-    const int32_t lab = __ldg(in.lab[d] + p);
-    const int32_t prank = d > 0 ? __ldg(rank.rank + sg.off[d - 1] + __ldg(in.par[d] + p)) : 0;
-    out.lab[d][r] = lab;
-    if (d > 0) out.par[d][r] = prank;
-    if (index && d == in.k - 1) index[r] = (int32_t)p;
+    bool kept[U];
+    int32_t base[U], lab[U], prank[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int64_t i = a + 32 * u + lane;
+      kept[u] = i >= lo && i < hi && flags[i];
+      base[u] = a + 32 * u < hi ? rank.base32(a + 32 * u, lo) : 0;
+    }
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int64_t p = a + 32 * u + lane - lo;
+      lab[u] = kept[u] ? __ldg(in.lab[d] + p) : 0;
+      prank[u] = (d > 0 && kept[u]) ? __ldg(rank.rank + sg.off[d - 1] + __ldg(in.par[d] + p)) : 0;
+    }
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const unsigned bal = __ballot_sync(0xffffffffu, kept[u]);
+      if (!kept[u]) continue;
+      const int32_t r = window_rank(base[u], bal);
+      const int64_t p = a + 32 * u + lane - lo;
+      out.lab[d][r] = lab[u];
+      if (d > 0) out.par[d][r] = prank[u];
+      if (index && d == in.k - 1) index[r] = (int32_t)p;
+    }
   }
 }
 

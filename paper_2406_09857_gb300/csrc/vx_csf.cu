@@ -846,68 +846,107 @@ __device__ __forceinline__ int32_t chain(const KptrSet &K, int a, int t, int32_t
 }
 
 // Bisection of depth d: every kept depth-d node writes its 2^(d+1) copies.  k and d are
-// template arguments so that the path arrays stay in registers.
+// template arguments so that the path arrays stay in registers.  Per kept node, the plan of
+// its copies (split_plan: loads only) and then their stores (split_write): copies b and b+1
+// (b even) are neighbours (idx even), so each pair is one 8-byte store per array.
+struct SplitPlan {
+  int64_t bd, bm, bp;
+  int64_t Dd[VX_KMAX], Dm[VX_KMAX], Dp[VX_KMAX];
+  int32_t lab2;
+};
+
+template <int KK, int D>
+__device__ __forceinline__ void split_plan(const CsfView &in, const RankView &rank,
+                                           const Segs &sg, const KptrSet &K, int64_t p,
+                                           int32_t gd, SplitPlan &P) {
+  constexpr int k = KK, d = D;
+  int64_t path[VX_KMAX];
+  int32_t g[VX_KMAX];
+  path[d] = p;
+#pragma unroll
+  for (int a = d; a > 0; --a) path[a - 1] = __ldg(in.par[a] + path[a]);
+#pragma unroll
+  for (int a = 0; a < d; ++a) g[a] = rank.at(sg.off[a] + path[a]);
+  g[d] = gd;
+  // F_t(p_a) and D_t(p_a) for t = d-1, d, d+1
+  P.bd = P.bm = P.bp = 0;
+  int64_t prevF_d = 0, prevF_m = 0, prevF_p = 0;
+#pragma unroll
+  for (int a = 0; a <= d; ++a) {
+    const int64_t Fd = chain(K, a, d, g[a]);
+    P.Dd[a] = chain(K, a, d, g[a] + 1) - Fd;
+    P.bd += (Fd - prevF_d) << (d - a + 1);
+    prevF_d = Fd;
+    if (a < d) {
+      const int64_t Fm = chain(K, a, d - 1, g[a]);
+      P.Dm[a] = chain(K, a, d - 1, g[a] + 1) - Fm;
+      P.bm += (Fm - prevF_m) << (d - a);
+      prevF_m = Fm;
+    }
+    if (d + 1 < k) {
+      const int64_t Fp = chain(K, a, d + 1, g[a]);
+      P.Dp[a] = chain(K, a, d + 1, g[a] + 1) - Fp;
+      P.bp += (Fp - prevF_p) << (d - a + 2);
+      prevF_p = Fp;
+    }
+  }
+  P.lab2 = 2 * __ldg(in.lab[d] + p);
+}
+
+template <int KK, int D>
+__device__ __forceinline__ void split_write(const CsfView &out, const SplitPlan &P) {
+  constexpr int k = KK, d = D;
+  const int nb = 1 << (d + 1);
+  for (int b = 0; b < nb; b += 2) {
+    // the copies b and b + 1 differ in the last bit only: idx + 1, the same parent, and the
+    // child pointer moved by 2 D_{d+1}(p_d)
+    int64_t idx = P.bd, pidx = P.bm, cidx = P.bp;
+#pragma unroll
+    for (int a = 0; a < d; ++a) {
+      const int64_t bit = (b >> (d - a)) & 1;
+      idx += bit * (P.Dd[a] << (d - a));
+      pidx += bit * (P.Dm[a] << (d - 1 - a));
+      if (d + 1 < k) cidx += bit * (P.Dp[a] << (d - a + 1));
+    }
+    *reinterpret_cast<int2 *>(out.lab[d] + idx) = make_int2(P.lab2, P.lab2 + 1);
+    if (d > 0) *reinterpret_cast<int2 *>(out.par[d] + idx) = make_int2((int32_t)pidx, (int32_t)pidx);
+    if (d + 1 < k)
+      *reinterpret_cast<int2 *>(out.ptr[d] + idx) =
+          make_int2((int32_t)cidx, (int32_t)(cidx + (P.Dp[d] << 1)));
+  }
+}
+
+// A warp takes kSplitU consecutive 32-aligned windows of the flag array per step (blockDim
+// and the stride multiples of 32): the plans of both windows' kept nodes (their loads) before
+// any of their stores.
+constexpr int kSplitU = 2;
 template <int KK, int D>
 __global__ void k_split(CsfView in, const uint8_t *__restrict__ flags, const RankView rank,
                         Segs sg, KptrSet K, CsfView out) {
-  constexpr int k = KK, d = D;
+  constexpr int d = D, U = kSplitU;
   const int64_t lo = sg.off[d], hi = lo + in.N[d];
-  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-  // a warp takes a 32-aligned window of the flag array (blockDim and stride multiples of 32)
-  for (int64_t a = (lo & ~(int64_t)31) + (int64_t)blockIdx.x * blockDim.x + (threadIdx.x & ~31);
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x * U;
+  const int lane = threadIdx.x & 31;
+  for (int64_t a = (lo & ~(int64_t)31) + ((int64_t)blockIdx.x * blockDim.x + (threadIdx.x & ~31)) * U;
        a < hi; a += stride) {
-    const int64_t i = a + (threadIdx.x & 31), p = i - lo;
-    const bool kept = i >= lo && i < hi && flags[i];
-    const int32_t base = rank.base32(a, lo);
-    const unsigned bal = __ballot_sync(0xffffffffu, kept);
-    if (!kept) continue;
-    const int32_t gd = window_rank(base, bal);
-    int64_t path[VX_KMAX];
-    int32_t g[VX_KMAX];
-    path[d] = p;
+    bool kept[U];
+    int32_t base[U];
 #pragma unroll
-    for (int a = d; a > 0; --a) path[a - 1] = in.par[a][path[a]];
-#pragma unroll
-    for (int a = 0; a < d; ++a) g[a] = rank.at(sg.off[a] + path[a]);
-    g[d] = gd;
-    // F_t(p_a) and D_t(p_a) for t = d-1, d, d+1
-    int64_t base_d = 0, base_m = 0, base_p = 0;
-    int64_t Dd[VX_KMAX], Dm[VX_KMAX], Dp[VX_KMAX];
-    int64_t prevF_d = 0, prevF_m = 0, prevF_p = 0;
-#pragma unroll
-    for (int a = 0; a <= d; ++a) {
-      const int64_t Fd = chain(K, a, d, g[a]);
-      Dd[a] = chain(K, a, d, g[a] + 1) - Fd;
-      base_d += (Fd - prevF_d) << (d - a + 1);
-      prevF_d = Fd;
-      if (a < d) {
-        const int64_t Fm = chain(K, a, d - 1, g[a]);
-        Dm[a] = chain(K, a, d - 1, g[a] + 1) - Fm;
-        base_m += (Fm - prevF_m) << (d - a);
-        prevF_m = Fm;
-      }
-      if (d + 1 < k) {
-        const int64_t Fp = chain(K, a, d + 1, g[a]);
-        Dp[a] = chain(K, a, d + 1, g[a] + 1) - Fp;
-        base_p += (Fp - prevF_p) << (d - a + 2);
-        prevF_p = Fp;
-      }
+    for (int u = 0; u < U; ++u) {
+      const int64_t i = a + 32 * u + lane;
+      kept[u] = i >= lo && i < hi && flags[i];
+      base[u] = a + 32 * u < hi ? rank.base32(a + 32 * u, lo) : 0;
     }
-    const int32_t lab2 = 2 * in.lab[d][p];
-    const int nb = 1 << (d + 1);
-    for (int b = 0; b < nb; ++b) {
-      int64_t idx = base_d, pidx = base_m, cidx = base_p;
+    SplitPlan P[U];
 #pragma unroll
-      for (int a = 0; a <= d; ++a) {
-        const int64_t bit = (b >> (d - a)) & 1;
-        idx += bit * (Dd[a] << (d - a));
-        if (a < d) pidx += bit * (Dm[a] << (d - 1 - a));
-        if (d + 1 < k) cidx += bit * (Dp[a] << (d - a + 1));
-      }
-      out.lab[d][idx] = lab2 + (b & 1);
-      if (d > 0) out.par[d][idx] = (int32_t)pidx;
-      if (d + 1 < k) out.ptr[d][idx] = (int32_t)cidx;
+    for (int u = 0; u < U; ++u) {
+      const unsigned bal = __ballot_sync(0xffffffffu, kept[u]);
+      if (kept[u])
+        split_plan<KK, D>(in, rank, sg, K, a + 32 * u + lane - lo, window_rank(base[u], bal), P[u]);
     }
+#pragma unroll
+    for (int u = 0; u < U; ++u)
+      if (kept[u]) split_write<KK, D>(out, P[u]);
   }
 }
 

@@ -774,6 +774,45 @@ __global__ void k_mark_parents(const int32_t *__restrict__ ptr, int64_t n,
 }
 
 
+// Whether the flag bytes [lo, hi) that fall in the 16 bytes v (loaded from c, 16-aligned)
+// hold a kept child.
+__device__ __forceinline__ bool block_hit(const uint4 v, int64_t c, int64_t lo, int64_t hi) {
+  const int s = lo > c ? (int)(lo - c) : 0, e = hi < c + 16 ? (int)(hi - c) : 16;
+  const uint64_t w[2] = {(uint64_t)v.x | ((uint64_t)v.y << 32), (uint64_t)v.z | ((uint64_t)v.w << 32)};
+  bool hit = false;
+#pragma unroll
+  for (int h = 0; h < 2; ++h) {
+    const int sh = s - 8 * h < 0 ? 0 : (s - 8 * h > 8 ? 8 : s - 8 * h);
+    const int eh = e - 8 * h < 0 ? 0 : (e - 8 * h > 8 ? 8 : e - 8 * h);
+    const int width = eh > sh ? eh - sh : 0;
+    const uint64_t m =
+        width <= 0 ? 0ull : (width >= 8 ? ~0ull : ((1ull << (8 * width)) - 1ull)) << (8 * sh);
+    hit = hit || (w[h] & m) != 0ull;
+  }
+  return hit;
+}
+
+// Long child ranges on many nodes: one thread per node, 32 flag bytes per step (two 16-byte
+// loads from the 16-byte boundary below its range), stopping at the first kept child, which
+// a node with many kept children finds in its first step; the warp-per-node form spent a
+// warp's sequence of dependent loads on every node in turn.
+__global__ void k_mark_parents_l(const int32_t *__restrict__ ptr, int64_t n,
+                                 const uint8_t *__restrict__ flags, int64_t coff,
+                                 uint8_t *__restrict__ out) {
+  for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < n;
+       p += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t lo = coff + __ldg(ptr + p), hi = coff + __ldg(ptr + p + 1);
+    bool any = false;
+    for (int64_t b = lo & ~(int64_t)15; b < hi && !any; b += 32) {
+      const uint4 v0 = __ldg(reinterpret_cast<const uint4 *>(flags + b));
+      const uint4 v1 = b + 16 < hi ? __ldg(reinterpret_cast<const uint4 *>(flags + b + 16))
+                                   : make_uint4(0u, 0u, 0u, 0u);
+      any = block_hit(v0, b, lo, hi) || (b + 16 < hi && block_hit(v1, b + 16, lo, hi));
+    }
+    out[p] = any ? 1 : 0;
+  }
+}
+
 // Short child ranges (a few children per node, as in the trees of small systems): one thread
 // per node, eight flag bytes per load from the 8-byte boundary below its
 // range (the 16 bytes of padding after the flags cover the last load).
@@ -1176,12 +1215,21 @@ int prune_c(const CsfView &in, const uint8_t *d_keep, int split, int32_t *d_inde
         if (blocks < 1) blocks = 1;
         k_mark_parents_t<<<(unsigned)blocks, 256, 0, s>>>(in.ptr[d], in.N[d], flags,
                                                          sg.off[d + 1], flags + sg.off[d]);
-      } else if (in.N[d + 1] > 128 * in.N[d]) {  // long ranges: one warp per node
-        int64_t blocks = (in.N[d] + 7) / 8;  // 8 warps per block
-        if (blocks > (int64_t)sm_count() * 16) blocks = (int64_t)sm_count() * 16;
-        if (blocks < 1) blocks = 1;
-        k_mark_parents<<<(unsigned)blocks, 256, 0, s>>>(in.ptr[d], in.N[d], flags, sg.off[d + 1],
-                                                       flags + sg.off[d]);
+      } else if (in.N[d + 1] > 128 * in.N[d]) {
+        // long ranges: one thread per node where the nodes fill the GPU with threads, else one
+        // warp per node
+        if (in.N[d] >= (int64_t)sm_count() * 512) {
+          int64_t blocks = (in.N[d] + 255) / 256;
+          if (blocks > (int64_t)sm_count() * 8) blocks = (int64_t)sm_count() * 8;
+          k_mark_parents_l<<<(unsigned)blocks, 256, 0, s>>>(in.ptr[d], in.N[d], flags,
+                                                           sg.off[d + 1], flags + sg.off[d]);
+        } else {
+          int64_t blocks = (in.N[d] + 7) / 8;  // 8 warps per block
+          if (blocks > (int64_t)sm_count() * 16) blocks = (int64_t)sm_count() * 16;
+          if (blocks < 1) blocks = 1;
+          k_mark_parents<<<(unsigned)blocks, 256, 0, s>>>(in.ptr[d], in.N[d], flags,
+                                                         sg.off[d + 1], flags + sg.off[d]);
+        }
       } else {  // scatter from the kept children to their parents
         e = cudaMemsetAsync(flags + sg.off[d], 0, (size_t)in.N[d], s);
         if (e != cudaSuccess) break;

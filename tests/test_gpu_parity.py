@@ -172,6 +172,34 @@ def test_subdivide_and_compact_across_fanouts(vx, k, per, p, seed):
     assert np.array_equal(host(idx), np.nonzero(keep)[0].astype(np.int32))
 
 
+@pytest.mark.parametrize("p,seed", [(0.3, 41), (0.002, 42)])
+def test_subdivide_and_compact_many_long_parents(vx, p, seed):
+    """90 000 depth-0 nodes of 130 children each (k = 2, level 17): enough nodes for the
+    parent marking to take a thread per node with long child ranges, with many kept children
+    (most nodes settled by their first load) and with few (most ranges read to their end);
+    split and compaction against the definition."""
+    k, level, npar, per = 2, 17, 90000, 130
+    side = 1 << level
+    h = np.repeat(np.arange(npar, dtype=np.int64), per)
+    j = np.tile(np.arange(per, dtype=np.int64), npar)
+    x2 = (j * 997 + h * 13) % side  # distinct within a parent (997 odd, per < side)
+    t = np.column_stack([h, x2]).astype(np.int32)
+    t = t[np.lexsort(t.T[::-1])]
+    keep = (synth.Stream(seed).unit(t.shape[0]) < p).astype(np.uint8)
+    c = vx.csf_build(k, level, dev(t))
+    nxt = vx.csf_subdivide(c, dev(keep))
+    kept = t[keep == 1]
+    want = _children(kept, k)
+    N_ref, labs, ptrs = oracle.csf(want, k)
+    lab0, ptr0 = nxt.export(1)
+    lab1, _ = nxt.export(2)
+    assert np.array_equal(host(lab0), labs[0]) and np.array_equal(host(lab1), labs[1])
+    assert np.array_equal(host(ptr0), ptrs[0].astype(np.int32))
+    out, idx = vx.csf_compact(c, dev(keep), with_index=True)
+    assert np.array_equal(host(out.tuples()), kept)
+    assert np.array_equal(host(idx), np.nonzero(keep)[0].astype(np.int32))
+
+
 @pytest.mark.parametrize("k,level,n,p,seed", [(2, 6, 900, 0.3, 12), (3, 5, 6000, 0.5, 13),
                                               (4, 3, 2000, 0.1, 14)])
 def test_compact_matches_definition(vx, k, level, n, p, seed):

@@ -1215,7 +1215,11 @@ __global__ void __launch_bounds__(kThreads, 6)
 // recursion).  The summed bound of the leaves (bform_entry), applied to the stages' much longer
 // chains, widens the curve's last-level band by 44-48% and does not pay: measured with the
 // band going to the float-pair tier, the depth-1 stage took 4.77 instead of 4.59 ms per step
-// (each staged group rewritten first) and the tier 1.86 instead of 1.55 ms.
+// (each staged group rewritten first) and the tier 1.86 instead of 1.55 ms.  With stage 0
+// writing its blocks in that form (each entry's row and fibre length known per output fibre,
+// no rewriting pass) the stage still took 4.89 instead of 4.72 ms, the band grew from 22 168
+// to 32 678 boxes and the tier from 1.49 to 1.77 ms: the stage is not bound by its bound's
+// arithmetic.
 __global__ void __launch_bounds__(512)
     k_stage_tma_c(const StageDev st, const int32_t *__restrict__ lab,
                   const int32_t *__restrict__ pptr, const float4 *__restrict__ in,

@@ -13,6 +13,7 @@
 #include <algorithm>
 #include <array>
 #include <atomic>
+#include <chrono>
 #include <condition_variable>
 #include <functional>
 #include <map>
@@ -481,11 +482,14 @@ class HostPool {
       n_ = n;
       next_.store(0);
       ++gen_;
+      gen_pub_.store(gen_, std::memory_order_release);
     }
     cv_.notify_all();
     drain();
+    // the workers' last chunks usually end within microseconds: wait for them spinning first
+    spin_until([&] { return active_.load(std::memory_order_acquire) == 0; });
     std::unique_lock<std::mutex> g(m_);
-    done_.wait(g, [&] { return active_ == 0; });  // every chunk a worker took has finished
+    done_.wait(g, [&] { return active_.load() == 0; });  // every chunk a worker took has finished
     job_ = nullptr;
     return true;
   }
@@ -503,25 +507,37 @@ class HostPool {
       (*job_)(c);
     }
   }
+  // Spins until pred() holds or kSpinUs microseconds pass: packing issues its jobs back to
+  // back, and a wake-up through a condition variable costs tens of microseconds each.
+  static constexpr int kSpinUs = 200;
+  template <class Pred>
+  static void spin_until(Pred pred) {
+    const auto t0 = std::chrono::steady_clock::now();
+    while (!pred() && std::chrono::steady_clock::now() - t0 < std::chrono::microseconds(kSpinUs)) {
+    }
+  }
   void loop() {
     uint64_t seen = 0;
-    std::unique_lock<std::mutex> g(m_);
     for (;;) {
+      spin_until([&] { return gen_pub_.load(std::memory_order_acquire) != seen; });
+      std::unique_lock<std::mutex> g(m_);
       cv_.wait(g, [&] { return gen_ != seen && job_ != nullptr; });
       seen = gen_;
-      ++active_;
+      active_.fetch_add(1);
       g.unlock();
       drain();
       g.lock();
-      if (--active_ == 0) done_.notify_all();
+      if (active_.fetch_sub(1) == 1) done_.notify_all();
     }
   }
   int nworkers_ = 0;
   std::mutex busy_, m_;
   std::condition_variable cv_, done_;
   std::function<void(int)> *job_ = nullptr;
-  int n_ = 0, active_ = 0;
+  int n_ = 0;
+  std::atomic<int> active_{0};  // changed under m_; read without it while spinning
   uint64_t gen_ = 0;
+  std::atomic<uint64_t> gen_pub_{0};  // gen_, for the workers' spin
   std::atomic<int> next_{0};
 };
 

@@ -15,7 +15,9 @@
 // the number of them: the nodes before it are the copies of the subtrees of earlier siblings
 // of each ancestor (2^(t-a+1) copies per kept depth-t descendant) and, inside an ancestor's
 // pair, the copies under the lower bit.  Ranks and first descendants come from one scan of
-// the keep flags, so every new node is written straight to its place.
+// the keep flags, so every new node is written straight to its place.  The scan stores a rank
+// per inner node and one count per 8-entry word of the leaves' flags (RankView); the kernels
+// that place nodes take 32 consecutive flags per warp, one rank per warp and a ballot.
 #include <cuda_runtime.h>
 
 #include <algorithm>
